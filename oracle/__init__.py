@@ -1,0 +1,28 @@
+"""FP64 CPU oracle of the Fullwave 2 time step (arXiv 2106.11476).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import, call, link or run anything in this
+package.  The product path (``paper_2106_11476_gb300``) never touches it, and
+the two share no code: the oracle builds its own coefficients from the paper's
+closed forms (``oracle.coefficients``), steps the fields with plain C loops
+(``fw2_oracle.c`` through ``oracle.core``) and evaluates the paper's analytic
+relations (``oracle.analytic``).
+
+Parity status per function (pins live in ``tests/test_oracle_pins.py``):
+
+* relaxation a, b (Eqs. relaxation_a / relaxation_b): pinned by quadrature of
+  the kernel zeta and by its DC integral.
+* recursion (Eq. relaxation_psi) inside the stepper: pinned by a brute-force
+  convolution of the derivative history.
+* staggered operator (Sec. 3.1): pinned by exactness on polynomials and by the
+  symbol of a sampled sinusoid.
+* lossless stepper: pinned by discrete energy conservation and by the
+  closed-form discrete dispersion relation.
+* attenuating stepper: pinned by the fully discrete dispersion relation of
+  the scheme, by the paper's attenuation / phase-velocity claims for its
+  Table 2 parameters and by the classical-PML special case.
+* C-PML profiles (Table 1): parity unpinned (reflection pin pending).
+* nonlinear term (Eq. general6): parity unpinned (Burgers pin pending).
+* staggered-grid placement of rho, kappa and the PML coordinate (not printed
+  in the paper): parity unpinned beyond the readings stated in the design notes.
+"""

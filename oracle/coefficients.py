@@ -1,0 +1,216 @@
+"""FP64 coefficient construction for the oracle (test infrastructure only).
+
+Builds, from a ``synth.Problem``, every per-point and per-axis coefficient the
+time step uses, straight from the paper's closed forms:
+
+* b = exp(-(d/kappa + alpha) dt), a = d (b - 1) / (kappa (d + kappa alpha))
+  -- Eqs. (relaxation_a), (relaxation_b), Sec. 3.2;
+* the two-stage C-PML with transition layer -- Sec. 3.3, Table 1 and the
+  polynomial / linear / cosine transition functions with
+  X(x) = (X_target - X_0) g(x) + X_0;
+* K = rho c^2, the nonlinear coefficient chi -- Eq. (general6);
+* dt = CFL h / c_max with c_max the high-frequency speed c / sqrt(kappa1 kappa2)
+  implied by Eq. (dispersion_relations) -- Sec. 3.4 (CFL 0.4).
+
+Readings where the paper is silent (placement on the staggered grid):
+rho at a face is the mean of the two adjacent cells (the cell itself at a
+non-periodic outer edge); the relaxation parameters of a face are those of
+its lower-index cell; the PML profile is evaluated at the exact staggered
+coordinate of each point.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Optional
+
+import numpy as np
+
+
+def taylor_staggered_taps(M: int = 4):
+    """Taylor coefficients g_1..g_M of the 2M-th order staggered first derivative.
+
+    Solves sum_i g_i (2i-1)^(2m-1) = delta_{m,1}, m = 1..M, in exact rational
+    arithmetic (Gauss-Jordan on fractions).  For M = 4 this gives
+    1225/1024, -245/3072, 49/5120, -5/7168.
+    """
+    from fractions import Fraction
+    A = [[Fraction((2 * i - 1) ** (2 * m - 1)) for i in range(1, M + 1)] for m in range(1, M + 1)]
+    b = [Fraction(1 if m == 1 else 0) for m in range(1, M + 1)]
+    n = M
+    for col in range(n):
+        piv = next(r for r in range(col, n) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        b[col], b[piv] = b[piv], b[col]
+        inv = 1 / A[col][col]
+        A[col] = [x * inv for x in A[col]]
+        b[col] *= inv
+        for r in range(n):
+            if r != col and A[r][col] != 0:
+                f = A[r][col]
+                A[r] = [x - f * y for x, y in zip(A[r], A[col])]
+                b[r] -= f * b[col]
+    return b  # list of Fractions, g_1..g_M (the system is scaled so h = 1, D = sum g_i * diff / h)
+
+
+def relaxation_ab(d, alpha, kappa, dt):
+    """Recursion coefficients of Eqs. (relaxation_a), (relaxation_b), FP64.
+
+    b = exp(-(d/kappa + alpha) dt);  a = d / (kappa (d + kappa alpha)) (b - 1).
+    a is 0 where d = 0 (no memory contribution).
+    """
+    d = np.asarray(d, np.float64)
+    alpha = np.asarray(alpha, np.float64)
+    kappa = np.asarray(kappa, np.float64)
+    b = np.exp(-(d / kappa + alpha) * dt)
+    denom = kappa * (d + kappa * alpha)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        a = np.where(d == 0.0, 0.0, d / np.where(denom == 0.0, 1.0, denom) * (b - 1.0))
+    return a, b
+
+
+def high_frequency_speed(c, kappa1, kappa2):
+    """c / sqrt(kappa1 kappa2): the omega -> infinity phase speed of Eq. (dispersion_relations)."""
+    c = np.asarray(c, np.float64)
+    if kappa1 is None:
+        return c
+    return c / np.sqrt(np.asarray(kappa1, np.float64) * np.asarray(kappa2, np.float64))
+
+
+def cfl_time_step(prob, cfl: float = 0.4) -> float:
+    """dt = CFL h / c_max (Sec. 3.4), c_max over the medium at high frequency."""
+    return float(cfl * prob.h / high_frequency_speed(prob.c, prob.kappa1, prob.kappa2).max())
+
+
+def boundary_depth(n: int, L: int, staggered: bool) -> np.ndarray:
+    """Depth into the boundary region (in cells, 0..L) of each point on one axis.
+
+    Cell centres sit at x = i, faces at x = i + 1/2.  The region occupies the
+    outer L cells of each side: on the low side its inner edge is x = L - 1/2
+    and its outer edge x = -1/2; on the high side x = n - L - 1/2 and n - 1/2.
+    """
+    x = np.arange(n, dtype=np.float64) + (0.5 if staggered else 0.0)
+    depth = np.zeros(n, np.float64)
+    if L <= 0:
+        return depth
+    lo_in = L - 0.5
+    hi_in = n - L - 0.5
+    depth = np.where(x < lo_in, lo_in - x, depth)
+    depth = np.where(x > hi_in, x - hi_in, depth)
+    return np.minimum(depth, float(L))
+
+
+def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
+                     LT: int, LB: int, npow: float, d_target: float, reading: str) -> np.ndarray:
+    """Relaxation parameter inside the two-stage C-PML (Sec. 3.3, Table 1).
+
+    X(x) = (X_target - X0) g(x) + X0 with
+      nu = 1, d    : polynomial g = (x/L)^npow toward d_target
+      nu = 1, alpha: linear     g = x/L      toward 0
+      nu >= 2      : cosine     g = (1 - cos(pi x / L_T)) / 2 toward 0 over
+                     the transition layer, 0 beyond it.
+    Reading A: the nu = 1 ramps span the whole boundary L_T + L_B.
+    Reading B: the nu = 1 ramps span only the outer L_B cells.
+    `nu` is 1-based as in the paper; `which` is "d" or "alpha".
+    """
+    X0 = np.asarray(X0, np.float64)
+    L = LT + LB
+    out = X0.copy()
+    inside = depth > 0
+    if not np.any(inside) or L == 0:
+        return out
+    if nu == 1:
+        if reading.upper() == "A":
+            s = depth / L
+            active = inside
+        else:
+            s = np.where(depth > LT, (depth - LT) / max(LB, 1), 0.0)
+            active = depth > LT
+        if which == "d":
+            g = s ** npow
+            tgt = d_target
+        else:
+            g = s
+            tgt = 0.0
+        out = np.where(active, (tgt - X0) * g + X0, X0)
+    else:
+        if LT > 0:
+            g = np.where(depth < LT, 0.5 * (1.0 - np.cos(np.pi * depth / LT)), 1.0)
+        else:
+            g = np.ones_like(depth)
+        out = np.where(inside, (0.0 - X0) * g + X0, X0)
+    return out
+
+
+def build(prob, round_to: Optional[str] = None) -> Dict[str, object]:
+    """All coefficient arrays of the oracle step, FP64 (flat, x fastest).
+
+    Keys: K, chi (or None), buoy[q], ik1[q], a1[q] (N, n), b1[q], ik2[q],
+    a2[q], b2[q], dt, taps (g1..g4, g11).
+    `round_to` = "f32" rounds every stored coefficient map to float32 first
+    (models coefficient maps kept in single precision).
+    """
+    nd = prob.ndim
+    shape = list(prob.shape) + [1] * (3 - nd)
+    n = prob.n_pts
+    gshape = tuple(reversed(shape))           # (nz, ny, nx)
+    c = np.asarray(prob.c, np.float64).reshape(gshape)
+    rho = np.asarray(prob.rho, np.float64).reshape(gshape)
+    N = prob.nrelax
+    dt = float(prob.dt) if prob.dt and prob.dt > 0 else cfl_time_step(prob)
+    K = rho * c * c
+    chi = None
+    if prob.nl_mode != "off":
+        beta = np.asarray(prob.beta, np.float64).reshape(gshape)
+        kappa0 = 1.0 / K
+        if prob.nl_mode == "pressure":
+            chi = kappa0 * (1.0 - 2.0 * beta)        # Eq. (general6) factor
+        elif prob.nl_mode == "westervelt":
+            chi = -2.0 * beta * kappa0
+        else:
+            raise ValueError(prob.nl_mode)
+    taps = prob.taps
+    if taps is None:
+        g = [float(x) for x in taylor_staggered_taps(4)]
+        taps = (g[0], g[1], g[2], g[3], 0.0)
+    out: Dict[str, object] = {"dt": dt, "taps": tuple(float(t) for t in taps), "K": K.ravel(),
+                              "chi": None if chi is None else chi.ravel()}
+    periodic = [prob.bc[q] == "periodic" for q in range(3)]
+    axis_of = {0: 2, 1: 1, 2: 0}  # problem axis q -> numpy axis
+    k1 = np.asarray(prob.kappa1, np.float64).reshape(gshape) if N else np.ones(gshape)
+    k2 = np.asarray(prob.kappa2, np.float64).reshape(gshape) if N else np.ones(gshape)
+    LT, LB = int(prob.pml_transition), int(prob.pml_bound)
+    L = LT + LB
+    cp = float(prob.pml_cp) if prob.pml_cp and prob.pml_cp > 0 else float(c.max())
+    d_target = -(prob.pml_npow + 1.0) * cp * math.log(prob.pml_rc) / (2.0 * L * prob.h) if L > 0 else 0.0
+    for q in range(nd):
+        ax = axis_of[q]
+        # rho at the +1/2 face: mean of the cell and its +1 neighbour
+        nb = np.roll(rho, -1, axis=ax)
+        if not periodic[q]:
+            last = [slice(None)] * 3
+            last[ax] = slice(shape[q] - 1, shape[q])
+            nb[tuple(last)] = rho[tuple(last)]
+        out[f"buoy{q}"] = (1.0 / (0.5 * (rho + nb))).ravel()
+        out[f"ik1{q}"] = (1.0 / k1).ravel()
+        out[f"ik2{q}"] = (1.0 / k2).ravel()
+        a1 = np.zeros((N, n)); b1 = np.zeros((N, n)); a2 = np.zeros((N, n)); b2 = np.zeros((N, n))
+        for stag, (dname, aname, kap, A, B) in ((True, ("d1", "alpha1", k1, a1, b1)),
+                                                  (False, ("d2", "alpha2", k2, a2, b2))):
+            depth1 = boundary_depth(shape[q], L, staggered=stag)
+            bshape = [1, 1, 1]; bshape[ax] = shape[q]
+            depth = np.broadcast_to(depth1.reshape(bshape), gshape)
+            for nu in range(N):
+                d0 = np.asarray(getattr(prob, dname)[nu], np.float64).reshape(gshape)
+                al0 = np.asarray(getattr(prob, aname)[nu], np.float64).reshape(gshape)
+                d = boundary_profile(d0, depth, nu + 1, "d", LT, LB, prob.pml_npow, d_target, prob.pml_reading)
+                al = boundary_profile(al0, depth, nu + 1, "alpha", LT, LB, prob.pml_npow, d_target, prob.pml_reading)
+                a, b = relaxation_ab(d, al, kap, dt)
+                A[nu] = a.ravel(); B[nu] = b.ravel()
+        out[f"a1{q}"], out[f"b1{q}"], out[f"a2{q}"], out[f"b2{q}"] = a1, b1, a2, b2
+    if round_to == "f32":
+        for k, v in list(out.items()):
+            if isinstance(v, np.ndarray):
+                out[k] = v.astype(np.float32).astype(np.float64)
+    elif round_to is not None:
+        raise ValueError(round_to)
+    return out
