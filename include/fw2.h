@@ -1,0 +1,210 @@
+/*
+ * fw2.h -- C ABI of the GB300 Fullwave 2 time stepper (libfw2.so).
+ *
+ * The library advances the stretched first-order pressure / particle-velocity
+ * system of Sode & Pinton, "Fullwave 2" (arXiv 2106.11476), Eqs. (wave1),
+ * (wave2) and their nonlinear form Eqs. (general5), (general6), on the
+ * staggered grid of Sec. 3.1.  Every spatial derivative is stretched through
+ * N relaxation memory variables (Eqs. relaxation1-3, relaxation4, advanced by
+ * the recursion Eq. relaxation_psi with the coefficients of Eqs. relaxation_a,
+ * relaxation_b).  The same recursion provides interior power-law attenuation
+ * and the two-stage C-PML with its transition layer (Sec. 3.3, Table 1).
+ *
+ * Conventions shared by every call
+ *  - Grids are nx x ny (x nz) cells, x fastest; a flat cell index is
+ *    i + nx * (j + ny * k).  The boundary region lies inside the grid.
+ *    p lives at cell centres, v_q at the +1/2 face of axis q of each cell.
+ *  - Array arguments are plain pointers; `mem_space` says whether they are
+ *    host (FW2_MEM_HOST) or device (FW2_MEM_DEVICE) memory of the current
+ *    CUDA device.  Inputs are copied before the call returns (for device
+ *    inputs: enqueued on the context stream, then synchronised), so the
+ *    caller may free or reuse them afterwards.
+ *  - Output buffers passed to fw2_record are caller-owned device memory and
+ *    must stay valid while fw2_step calls that write them are in flight.
+ *  - Every call returns an fw2_status; no exception or exit crosses the ABI.
+ *    On failure fw2_last_error(ctx) describes the cause.  A context is not
+ *    thread-safe; distinct contexts are independent.
+ *  - All device work of a context runs on the stream given in fw2_config
+ *    (NULL: the legacy default stream).  fw2_step is asynchronous.
+ */
+#ifndef FW2_H
+#define FW2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fw2_ctx fw2_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  FW2_OK = 0,
+  FW2_EINVAL = 1,       /* bad argument, size, layout or unstable time step */
+  FW2_ENOMEM = 2,       /* device or host allocation failed */
+  FW2_ECUDA = 3,        /* a CUDA runtime call failed (no device, launch error) */
+  FW2_ESTATE = 4,       /* call out of order (e.g. step before set_medium) */
+  FW2_EUNSTABLE = 5,    /* non-finite or exploding field detected */
+  FW2_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
+  FW2_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} fw2_status;
+
+enum { FW2_MEM_HOST = 0, FW2_MEM_DEVICE = 1 };
+enum { FW2_BC_ZERO = 0, FW2_BC_PERIODIC = 1 };
+/* nonlinear factor chi of the pressure update p -= dt K div / (1 + chi p):
+ * OFF: chi = 0; PRESSURE: chi = kappa0 (1 - 2 beta), the factor printed in
+ * Eq. (general6); WESTERVELT: chi = -2 beta kappa0 (kappa0 = 1 / (rho c^2)). */
+enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2 };
+enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1 };
+/* C-PML geometry (Sec. 3.3): A: the nu = 1 ramps span L_T + L_B cells;
+ * B: they span only the outer L_B cells.  In both, nu >= 2 parameters fall
+ * to zero over the inner L_T cells with the cosine transition. */
+enum { FW2_PML_A = 0, FW2_PML_B = 1 };
+/* time alignment of the memory term in Eq. (relaxation_psi): CENTRED uses
+ * the mean of the memory variable before and after its update (D^{n-1/2}
+ * estimated by (D^n + D^{n-1}) / 2); ENDPOINT uses the updated value. */
+enum { FW2_MEM_CENTRED = 0, FW2_MEM_ENDPOINT = 1 };
+enum { FW2_SRC_P = 0, FW2_SRC_VX = 1, FW2_SRC_VY = 2, FW2_SRC_VZ = 3 };
+enum {
+  FW2_FIELD_P = 0, FW2_FIELD_VX = 1, FW2_FIELD_VY = 2, FW2_FIELD_VZ = 3,
+  FW2_FIELD_PSI1X = 4, FW2_FIELD_PSI1Y = 5, FW2_FIELD_PSI1Z = 6,
+  FW2_FIELD_PSI2X = 7, FW2_FIELD_PSI2Y = 8, FW2_FIELD_PSI2Z = 9
+};
+
+typedef struct {
+  int32_t ndim;          /* 2 or 3 */
+  int32_t n_relax;       /* N relaxation mechanisms, 0..4 */
+  int64_t n[3];          /* nx, ny, nz (nz = 1 in 2D); boundary region included */
+  double h;              /* grid spacing [m] */
+  double dt;             /* time step [s]; <= 0: cfl * h / c_max, with c_max the
+                            largest c / sqrt(kappa1 kappa2) of the medium */
+  double cfl;            /* used when dt <= 0 (Sec. 3.4 uses 0.4) */
+  double g[5];           /* g_{1,0}..g_{4,0}, g_{1,1} of the staggered operator
+                            (Sec. 3.1); all zero: 8th-order Taylor set
+                            1225/1024, -245/3072, 49/5120, -5/7168, g11 = 0 */
+  int32_t pml_transition;/* L_T, cells per side (Sec. 3.3) */
+  int32_t pml_bound;     /* L_B, cells per side */
+  int32_t pml_reading;   /* FW2_PML_A (default) or FW2_PML_B */
+  int32_t map_precision; /* FW2_MAP_F32 or FW2_MAP_BF16 storage of coefficient maps */
+  double pml_rc;         /* reflection target R_c of Table 1 (default 1e-3) */
+  double pml_npow;       /* polynomial order of the d ramp (default 2) */
+  double pml_cp;         /* c_p of Table 1 [m/s]; <= 0: largest c of the medium */
+  int32_t nl_mode;       /* FW2_NL_* */
+  int32_t mem_alignment; /* FW2_MEM_CENTRED (default) or FW2_MEM_ENDPOINT */
+  int32_t bc[3];         /* FW2_BC_* per axis */
+  int32_t reserved_;
+  void *stream;          /* cudaStream_t, borrowed; NULL = default stream */
+} fw2_config;
+
+typedef struct {
+  /* Interior relaxation parameters of every cell (Sec. 3.2, 2 + 4N values):
+   * kappa1, kappa2: [n_pts]; d1, alpha1, d2, alpha2: [N][n_pts] in 1/s.
+   * Inside the boundary region the library ramps d and alpha per axis
+   * following Table 1; kappa is kept. */
+  const float *kappa1;
+  const float *kappa2;
+  const float *d1;
+  const float *alpha1;
+  const float *d2;
+  const float *alpha2;
+  int32_t mem_space;
+} fw2_relax_desc;
+
+/* Fill *cfg with defaults (2D, N = 0, Taylor taps, CFL 0.4, R_c = 1e-3,
+ * npow = 2, reading A, FP32 maps, linear, centred memory term, zero BC). */
+fw2_status fw2_config_init(fw2_config *cfg);
+
+/* Create a context for one grid (Sec. 3.1 staggered layout) and allocate its
+ * device state: p, v_q and the 2 * ndim * N memory variables (Sec. 3.2),
+ * zero-initialised.  EINVAL for bad sizes, ECUDA without a usable device. */
+fw2_status fw2_create(const fw2_config *cfg, fw2_ctx **out);
+
+/* Material of every cell (Eqs. wave1-wave2, general5-general6): sound speed
+ * c [m/s], density rho [kg/m^3] and, when nl_mode != OFF, the coefficient of
+ * nonlinearity beta = 1 + B/2A (nullable otherwise).  Each [n_pts]. */
+fw2_status fw2_set_medium(fw2_ctx *ctx, const float *c, const float *rho,
+                          const float *beta, int32_t mem_space);
+
+/* Relaxation parameters (Sec. 3.2, Table 2 shape); required when N > 0.
+ * The coefficient maps (b = exp(-(d/kappa + alpha) dt),
+ * a = d (b - 1) / (kappa (d + kappa alpha)), Eqs. relaxation_a/b; the C-PML
+ * ramps of Table 1) are built on the device in FP64 at the first fw2_step
+ * (or fw2_get_dt) after medium and relaxation are set. */
+fw2_status fw2_set_relaxation(fw2_ctx *ctx, const fw2_relax_desc *desc);
+
+/* Add an additive source (the paper's transmit events, Sec. 4 and the
+ * appendices): `kind` FW2_SRC_*; n_pts cell indices idx[] each fed by signal
+ * column group[] (NULL: all column 0); signal is [n_steps][n_groups] and row n
+ * is added to the field right after the half step of time step n.  Steps past
+ * n_steps inject nothing.  May be called several times; entries accumulate. */
+fw2_status fw2_add_source(fw2_ctx *ctx, int32_t kind, int64_t n_pts,
+                          const int64_t *idx, const int32_t *group,
+                          const float *signal, int64_t n_groups,
+                          int64_t n_steps, int32_t mem_space);
+
+/* Record p after every time step (sensor traces): trace row n, column g, is
+ * the mean of p^{n+1} over the cells of group g (group NULL: one cell per
+ * group, n_groups = n_pts).  out is caller-owned device memory of
+ * [n_steps][n_groups] floats; row n is written by step n for n < n_steps.
+ * idx/group follow mem_space.  Replaces any previous recording. */
+fw2_status fw2_record(fw2_ctx *ctx, int64_t n_pts, const int64_t *idx,
+                      const int32_t *group, int64_t n_groups, float *out,
+                      int64_t n_steps, int32_t mem_space);
+
+/* Advance n_steps time steps (Sec. 3.1 update order): velocity half step
+ * with the nabla_1 memory variables, velocity sources, pressure half step
+ * with the nabla_2 memory variables and the nonlinear factor, pressure
+ * sources, recording.  Asynchronous on the context stream.  EINVAL when the
+ * time step violates the stability limit of the staggered scheme. */
+fw2_status fw2_step(fw2_ctx *ctx, int64_t n_steps);
+
+/* Release every resource of the context (safe on NULL). */
+fw2_status fw2_destroy(fw2_ctx *ctx);
+
+/* ---- helpers ---------------------------------------------------------- */
+
+/* Time step in use (builds the coefficient maps if needed). */
+fw2_status fw2_get_dt(fw2_ctx *ctx, double *dt);
+/* Number of time steps taken so far. */
+fw2_status fw2_get_step(fw2_ctx *ctx, int64_t *step);
+/* Set the step counter (source row and trace row of the next step); with
+ * fw2_set_field this restores a checkpoint taken with fw2_get_step and
+ * fw2_get_field. EINVAL when negative. */
+fw2_status fw2_set_step(fw2_ctx *ctx, int64_t step);
+/* Copy a state array out (dense, x fastest; memory variables [N][n_pts]).
+ * Synchronises the context stream. */
+fw2_status fw2_get_field(fw2_ctx *ctx, int32_t field, float *out, int32_t mem_space);
+/* Overwrite a state array (same layout); used for checkpoint / restore. */
+fw2_status fw2_set_field(fw2_ctx *ctx, int32_t field, const float *in, int32_t mem_space);
+/* Zero every state array and the step counter. */
+fw2_status fw2_reset(fw2_ctx *ctx);
+/* Wait for the context stream. */
+fw2_status fw2_synchronize(fw2_ctx *ctx);
+/* Scan p for non-finite values or |p| > bound (a numerical blow-up such as
+ * the C-PML instability with N >= 2 and no transition layer, Sec. 3.3).
+ * Synchronising.  *max_abs receives max |p| (inf if non-finite); returns
+ * FW2_EUNSTABLE when the field fails, FW2_OK otherwise. */
+fw2_status fw2_check_field(fw2_ctx *ctx, float bound, float *max_abs);
+/* Bytes of device memory held by the context. */
+fw2_status fw2_device_bytes(fw2_ctx *ctx, int64_t *bytes);
+/* Launches of library kernels since creation (all kinds). */
+fw2_status fw2_kernel_launches(fw2_ctx *ctx, int64_t *count);
+/* Per-kernel timing: with enable = 1, fw2_step brackets every velocity and
+ * pressure kernel launch with CUDA events on the context stream. */
+fw2_status fw2_profile(fw2_ctx *ctx, int32_t enable);
+/* Synchronise and return the summed event time [ms] and launch counts of the
+ * velocity and pressure kernels since profiling was enabled; clears them. */
+fw2_status fw2_profile_read(fw2_ctx *ctx, double *vel_ms, int64_t *vel_launches,
+                            double *prs_ms, int64_t *prs_launches);
+/* Last error message of the context (or of the last failed fw2_create when
+ * ctx is NULL); never NULL. */
+const char *fw2_last_error(const fw2_ctx *ctx);
+/* ABI version of this header (incremented on incompatible change). */
+int32_t fw2_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FW2_H */

@@ -141,26 +141,40 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
     return out
 
 
-def build(prob, round_to: Optional[str] = None) -> Dict[str, object]:
+def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object]:
     """All coefficient arrays of the oracle step, FP64 (flat, x fastest).
 
     Keys: K, chi (or None), buoy[q], ik1[q], a1[q] (N, n), b1[q], ik2[q],
     a2[q], b2[q], dt, taps (g1..g4, g11).
     `round_to` = "f32" rounds every stored coefficient map to float32 first
     (models coefficient maps kept in single precision).
+    `window` = ((x0, x1), (y0, y1)[, (z0, z1)]) builds the coefficients of that
+    sub-box of the grid only, with the boundary profiles and face densities of
+    its global position.
     """
     nd = prob.ndim
     shape = list(prob.shape) + [1] * (3 - nd)
-    n = prob.n_pts
     gshape = tuple(reversed(shape))           # (nz, ny, nx)
-    c = np.asarray(prob.c, np.float64).reshape(gshape)
-    rho = np.asarray(prob.rho, np.float64).reshape(gshape)
+    if window is None:
+        window = [(0, s) for s in prob.shape]
+    win = [tuple(w) for w in window] + [(0, 1)] * (3 - nd)
+    wshape = [w[1] - w[0] for w in win]
+    wg = tuple(reversed(wshape))
+    n = int(np.prod(wshape))
+    # numpy slices of the window in the global arrays
+    sl = tuple(slice(win[q][0], win[q][1]) for q in (2, 1, 0))
+    def crop(a):
+        return np.asarray(a, np.float64).reshape(gshape)[sl]
+    c_full = np.asarray(prob.c, np.float64).reshape(gshape)
+    rho_full = np.asarray(prob.rho, np.float64).reshape(gshape)
+    c = c_full[sl]
+    rho = rho_full[sl]
     N = prob.nrelax
     dt = float(prob.dt) if prob.dt and prob.dt > 0 else cfl_time_step(prob)
     K = rho * c * c
     chi = None
     if prob.nl_mode != "off":
-        beta = np.asarray(prob.beta, np.float64).reshape(gshape)
+        beta = crop(prob.beta)
         kappa0 = 1.0 / K
         if prob.nl_mode == "pressure":
             chi = kappa0 * (1.0 - 2.0 * beta)        # Eq. (general6) factor
@@ -176,32 +190,34 @@ def build(prob, round_to: Optional[str] = None) -> Dict[str, object]:
                               "chi": None if chi is None else chi.ravel()}
     periodic = [prob.bc[q] == "periodic" for q in range(3)]
     axis_of = {0: 2, 1: 1, 2: 0}  # problem axis q -> numpy axis
-    k1 = np.asarray(prob.kappa1, np.float64).reshape(gshape) if N else np.ones(gshape)
-    k2 = np.asarray(prob.kappa2, np.float64).reshape(gshape) if N else np.ones(gshape)
+    k1 = crop(prob.kappa1) if N else np.ones(wg)
+    k2 = crop(prob.kappa2) if N else np.ones(wg)
     LT, LB = int(prob.pml_transition), int(prob.pml_bound)
     L = LT + LB
-    cp = float(prob.pml_cp) if prob.pml_cp and prob.pml_cp > 0 else float(c.max())
+    cp = float(prob.pml_cp) if prob.pml_cp and prob.pml_cp > 0 else float(c_full.max())
     d_target = -(prob.pml_npow + 1.0) * cp * math.log(prob.pml_rc) / (2.0 * L * prob.h) if L > 0 else 0.0
     for q in range(nd):
         ax = axis_of[q]
-        # rho at the +1/2 face: mean of the cell and its +1 neighbour
-        nb = np.roll(rho, -1, axis=ax)
-        if not periodic[q]:
-            last = [slice(None)] * 3
-            last[ax] = slice(shape[q] - 1, shape[q])
-            nb[tuple(last)] = rho[tuple(last)]
+        # rho at the +1/2 face: mean of the cell and its +1 neighbour (global)
+        idx_hi = np.arange(win[q][0], win[q][1]) + 1
+        if periodic[q]:
+            idx_hi = idx_hi % shape[q]
+        else:
+            idx_hi = np.minimum(idx_hi, shape[q] - 1)
+        others = tuple(slice(None) if i == ax else s_ for i, s_ in enumerate(sl))
+        nb = np.take(rho_full[others], idx_hi, axis=ax)
         out[f"buoy{q}"] = (1.0 / (0.5 * (rho + nb))).ravel()
         out[f"ik1{q}"] = (1.0 / k1).ravel()
         out[f"ik2{q}"] = (1.0 / k2).ravel()
         a1 = np.zeros((N, n)); b1 = np.zeros((N, n)); a2 = np.zeros((N, n)); b2 = np.zeros((N, n))
         for stag, (dname, aname, kap, A, B) in ((True, ("d1", "alpha1", k1, a1, b1)),
                                                   (False, ("d2", "alpha2", k2, a2, b2))):
-            depth1 = boundary_depth(shape[q], L, staggered=stag)
-            bshape = [1, 1, 1]; bshape[ax] = shape[q]
-            depth = np.broadcast_to(depth1.reshape(bshape), gshape)
+            depth1 = boundary_depth(shape[q], L, staggered=stag)[win[q][0]:win[q][1]]
+            bshape = [1, 1, 1]; bshape[ax] = wshape[q]
+            depth = np.broadcast_to(depth1.reshape(bshape), wg)
             for nu in range(N):
-                d0 = np.asarray(getattr(prob, dname)[nu], np.float64).reshape(gshape)
-                al0 = np.asarray(getattr(prob, aname)[nu], np.float64).reshape(gshape)
+                d0 = np.asarray(getattr(prob, dname)[nu], np.float64).reshape(gshape)[sl]
+                al0 = np.asarray(getattr(prob, aname)[nu], np.float64).reshape(gshape)[sl]
                 d = boundary_profile(d0, depth, nu + 1, "d", LT, LB, prob.pml_npow, d_target, prob.pml_reading)
                 al = boundary_profile(al0, depth, nu + 1, "alpha", LT, LB, prob.pml_npow, d_target, prob.pml_reading)
                 a, b = relaxation_ab(d, al, kap, dt)

@@ -86,14 +86,24 @@ def make_grid(shape, bc, dt, h, taps, nrelax, centred=True) -> Grid:
 class OracleSim:
     """FP64 simulation of a synth.Problem with the paper's method."""
 
-    def __init__(self, prob, round_to: Optional[str] = None, coefficients: Optional[Dict] = None):
+    def __init__(self, prob, round_to: Optional[str] = None, coefficients: Optional[Dict] = None,
+                 window=None):
+        """`window` = ((x0, x1), (y0, y1)[, (z0, z1)]) simulates only that sub-box
+        of the grid (fields zero outside it); its values are exact at cells
+        farther than 8 cells per step from every cut edge."""
         self.prob = prob
-        self.cf = coefficients if coefficients is not None else coef.build(prob, round_to=round_to)
-        self.dt = self.cf["dt"]
         nd = prob.ndim
-        n = prob.n_pts
+        self.window = [tuple(w) for w in window] if window is not None else [(0, s) for s in prob.shape]
+        self.wshape = tuple(w[1] - w[0] for w in self.window)
+        for q in range(nd):
+            if prob.bc[q] == "periodic" and self.window[q] != (0, prob.shape[q]):
+                raise ValueError("a window cannot cut a periodic axis")
+        self.cf = coefficients if coefficients is not None else coef.build(prob, round_to=round_to,
+                                                                            window=self.window)
+        self.dt = self.cf["dt"]
+        n = int(np.prod(self.wshape))
         N = prob.nrelax
-        self.G = make_grid(prob.shape, prob.bc, self.dt, prob.h, self.cf["taps"], N,
+        self.G = make_grid(self.wshape, prob.bc, self.dt, prob.h, self.cf["taps"], N,
                            centred=(prob.memory_alignment == "centred"))
         self.p = np.zeros(n)
         self.v = [np.zeros(n) for _ in range(nd)]
@@ -116,9 +126,10 @@ class OracleSim:
         kinds, idxs, cols, sigs = [], [], [], []
         col0 = 0
         for s in prob.sources:
-            kinds.append(np.full(s.idx.size, _KIND[s.kind], np.int32))
-            idxs.append(np.asarray(s.idx, np.int64))
-            cols.append(np.asarray(s.group, np.int32) + col0)
+            li, keep = self._localise(s.idx)
+            kinds.append(np.full(li.size, _KIND[s.kind], np.int32))
+            idxs.append(li)
+            cols.append(np.asarray(s.group, np.int32)[keep] + col0)
             sigs.append(np.asarray(s.signal, np.float64))
             col0 += s.signal.shape[1]
         self.src = Sources()
@@ -140,15 +151,38 @@ class OracleSim:
         self.trace = None
         if prob.sensors is not None:
             sn = prob.sensors
-            self._rec_arrays = (np.asarray(sn.idx, np.int64), np.asarray(sn.group, np.int32))
+            li, keep = self._localise(sn.idx)
+            self._rec_arrays = (li, np.ascontiguousarray(np.asarray(sn.group, np.int32)[keep]))
             self.trace = np.zeros((max(prob.n_steps, 1), sn.n_groups))
-            self.rec.n_pts = sn.idx.size
+            self.rec.n_pts = li.size
             self.rec.idx = self._rec_arrays[0].ctypes.data_as(C.POINTER(C.c_int64))
             self.rec.group = self._rec_arrays[1].ctypes.data_as(C.POINTER(C.c_int32))
             self.rec.n_groups = sn.n_groups
             self.rec.trace = _dp(self.trace)
         else:
             self.rec.n_pts = 0
+
+    def _localise(self, idx):
+        """Global flat cell indices -> window-local ones (and the kept mask)."""
+        idx = np.asarray(idx, np.int64)
+        full = list(self.prob.shape) + [1] * (3 - self.prob.ndim)
+        i = idx % full[0]
+        j = (idx // full[0]) % full[1]
+        k = idx // (full[0] * full[1])
+        win = self.window + [(0, 1)] * (3 - len(self.window))
+        keep = ((i >= win[0][0]) & (i < win[0][1]) & (j >= win[1][0]) & (j < win[1][1])
+                & (k >= win[2][0]) & (k < win[2][1]))
+        ws = [w[1] - w[0] for w in win]
+        li = (i - win[0][0]) + ws[0] * ((j - win[1][0]) + ws[1] * (k - win[2][0]))
+        return np.ascontiguousarray(li[keep].astype(np.int64)), keep
+
+    def _crop(self, a):
+        g = self.prob.grid_shape
+        a = np.asarray(a)
+        lead = a.shape[:-len(g)] if a.ndim > len(g) else ()
+        a = a.reshape(lead + g)
+        sl = tuple(slice(w[0], w[1]) for w in reversed(self.window))
+        return a[(Ellipsis,) + sl]
 
     def _bind_state(self):
         self.S.p = _dp(self.p)
@@ -160,12 +194,13 @@ class OracleSim:
     def set_state(self, st: Dict[str, np.ndarray]):
         """Load a state (as from synth.random_state) into the FP64 fields."""
         names = "xyz"
-        self.p[:] = np.asarray(st["p"], np.float64).ravel()
+        N = self.prob.nrelax
+        self.p[:] = self._crop(st["p"]).astype(np.float64).ravel()
         for q in range(len(self.v)):
-            self.v[q][:] = np.asarray(st["v" + names[q]], np.float64).ravel()
-            if self.prob.nrelax:
-                self.psi1[q][:] = np.asarray(st["psi1" + names[q]], np.float64).reshape(self.prob.nrelax, -1)
-                self.psi2[q][:] = np.asarray(st["psi2" + names[q]], np.float64).reshape(self.prob.nrelax, -1)
+            self.v[q][:] = self._crop(st["v" + names[q]]).astype(np.float64).ravel()
+            if N:
+                self.psi1[q][:] = self._crop(np.asarray(st["psi1" + names[q]]).reshape((N,) + self.prob.grid_shape)).reshape(N, -1)
+                self.psi2[q][:] = self._crop(np.asarray(st["psi2" + names[q]]).reshape((N,) + self.prob.grid_shape)).reshape(N, -1)
 
     def run(self, n_steps: int):
         if self.n_signal_rows is not None:
@@ -180,8 +215,8 @@ class OracleSim:
         return self
 
     def field(self, name: str) -> np.ndarray:
-        """A state array reshaped to the grid (numpy order)."""
-        g = self.prob.grid_shape
+        """A state array reshaped to the (window) grid, numpy order."""
+        g = tuple(reversed(self.wshape))
         names = {"p": self.p}
         for q, ch in enumerate("xyz"[: len(self.v)]):
             names["v" + ch] = self.v[q]

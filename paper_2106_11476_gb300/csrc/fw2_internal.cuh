@@ -1,0 +1,97 @@
+// Internal declarations shared by the CUDA translation units of libfw2.
+//
+// Device layout (all arrays in HBM, one allocation per context):
+//   every per-cell array is [nz][ny][pitch] floats (pitch = nx rounded up to
+//   4 so each row starts on a 16-byte boundary for 128-bit accesses; the
+//   padding columns of state arrays stay zero);
+//   memory variables psi1_q / psi2_q are [N][nz][ny][pitch];
+//   coefficient maps use the same cell layout in float or bf16;
+//   boundary strips hold the per-axis a, b of the C-PML region only:
+//     x: [N][nz][ny][2L], y: [N][nz][2L][pitch], z: [N][2L][ny][pitch],
+//   indexed by the strip coordinate (low side 0..L-1, high side L..2L-1).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fw2 {
+
+constexpr int kMaxRelax = 4;
+
+struct StepParams {
+  int nx, ny, nz;        // logical extent
+  int pitch;             // row pitch in elements (multiple of 4)
+  long long plane;       // pitch * ny
+  long long npts_alloc;  // plane * nz
+  int L[3];              // boundary cells per side on each axis (0: no strip)
+  int periodic[3];
+  float dt, two_dt;
+  float gh[4];           // g_i / h
+  float g11h;            // g_{1,1} / h
+  float w_new, w_old;    // memory-term weights: centred (0.5, 0.5), endpoint (1, 0)
+  int nl;                // nonlinear factor present
+  int n_relax;
+  // state (float)
+  float *p;
+  float *v[3];
+  float *psi1[3];        // [N][npts_alloc]
+  float *psi2[3];
+  // maps (float or bf16, see MapT)
+  const void *K;         // rho c^2
+  const void *rho;
+  const void *chi;
+  const void *ik1, *ik2; // 1/kappa1, 1/kappa2
+  const void *a1, *b1, *a2, *b2;          // interior [N][npts_alloc]
+  const void *sa1[3], *sb1[3], *sa2[3], *sb2[3];  // strips
+  long long strip_nu[3]; // elements between mechanisms in a strip array
+};
+
+// ---------------------------------------------------------------- loads ---
+__device__ __forceinline__ float ldmap(const float *p, long long i) { return __ldg(p + i); }
+__device__ __forceinline__ float ldmap(const __nv_bfloat16 *p, long long i) {
+  return __bfloat162float(p[i]);
+}
+__device__ __forceinline__ float4 ldmap4(const float *p, long long i) {
+  return __ldg(reinterpret_cast<const float4 *>(p + i));
+}
+__device__ __forceinline__ float4 ldmap4(const __nv_bfloat16 *p, long long i) {
+  uint2 u = __ldg(reinterpret_cast<const uint2 *>(p + i));
+  __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162 *>(&u.x);
+  __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
+  float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+// streaming state loads/stores: read once, write once per step
+__device__ __forceinline__ float4 ld_state4(const float *p, long long i) {
+  return __ldcs(reinterpret_cast<const float4 *>(p + i));
+}
+__device__ __forceinline__ void st_state4(float *p, long long i, float4 v) {
+  __stcs(reinterpret_cast<float4 *>(p + i), v);
+}
+
+__device__ __forceinline__ float &el(float4 &v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// Strip coordinate along an axis of extent n with L boundary cells per side,
+// or -1 in the interior.
+__device__ __forceinline__ int strip_coord(int i, int n, int L) {
+  if (L <= 0) return -1;
+  if (i < L) return i;
+  if (i >= n - L) return i - (n - 2 * L);
+  return -1;
+}
+
+// ------------------------------------------------------------- launches ---
+// 2D kernels: tile of kTX x kTY cells, block (32, 8), 4 x-cells per thread.
+constexpr int kTX = 128;
+constexpr int kTY = 16;
+constexpr int kBY = 8;
+
+cudaError_t launch_vel2d(const StepParams &P, int map_bf16, cudaStream_t s);
+cudaError_t launch_prs2d(const StepParams &P, int map_bf16, cudaStream_t s);
+cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
+cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
+
+}  // namespace fw2

@@ -1,0 +1,39 @@
+// Parameters of the one-time coefficient preparation and of the auxiliary
+// (source, recording, check) kernels.
+#pragma once
+#include "fw2_internal.cuh"
+
+namespace fw2 {
+
+struct PrepParams {
+  int nx, ny, nz, nd, pitch;
+  long long plane, npts_alloc;
+  int N;
+  double dt;
+  int LT, LB, reading;
+  double npow, d_target;
+  int nl_mode;
+  // raw inputs, dense [n_pts] (relaxation [N][n_pts]), device
+  const float *c, *rho, *beta, *k1, *k2, *d1, *al1, *d2, *al2;
+  // outputs (float or bf16)
+  void *K, *rho_o, *chi, *ik1, *ik2, *a1, *b1, *a2, *b2;
+  void *sa1[3], *sb1[3], *sa2[3], *sb2[3];
+  long long strip_nu[3];
+};
+
+cudaError_t launch_medium_scan(const PrepParams &Q, unsigned long long *maxbits, int *bad,
+                               cudaStream_t s);
+cudaError_t launch_prep(const PrepParams &Q, int map_bf16, cudaStream_t s);
+
+// sources: field[tgt[u]] += sum_{e in [off[u], off[u+1])} row[col[e]]
+cudaError_t launch_inject(float *field, const long long *tgt, const int *off, const int *col,
+                          const float *row, int n_tgt, cudaStream_t s);
+// recording: out[g] = mean over e in [off[g], off[g+1]) of p[cell[e]]
+cudaError_t launch_record(const float *p, const long long *cell, const int *off, int n_groups,
+                          float *out, cudaStream_t s);
+// field scan: max |x| over the cell layout (rows of nx valid values, pitch
+// apart), non-finite values reported as +inf; result in *out_bits (float bits)
+cudaError_t launch_absmax(const float *f, int nx, int pitch, long long rows,
+                          unsigned int *out_bits, cudaStream_t s);
+
+}  // namespace fw2

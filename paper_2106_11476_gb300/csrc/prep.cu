@@ -1,0 +1,210 @@
+// One-time coefficient preparation on the device, in FP64 (Sec. 3.2, 3.3).
+//
+// From the raw per-cell medium (c, rho, beta) and relaxation parameters
+// (kappa1, kappa2, d^nu, alpha^nu for nabla_1 and nabla_2) it writes the maps
+// the step kernels stream:
+//   K = rho c^2, rho, chi (nonlinear factor of Eq. general6),
+//   1/kappa1, 1/kappa2,
+//   interior a, b (Eqs. relaxation_a, relaxation_b) of every cell, and
+//   per-axis a, b inside the boundary strips, where d and alpha follow the
+//   two-stage C-PML ramps of Table 1:  X = (X_target - X_0) g + X_0 with
+//   g = (x/L)^npow (nu = 1, d), x/L (nu = 1, alpha) and
+//   (1 - cos(pi x / L_T)) / 2 over the transition layer (nu >= 2).
+// The profile of a face is evaluated at its exact staggered coordinate; the
+// relaxation parameters of a face are those of its lower-index cell.
+#include "fw2_prep.cuh"
+
+namespace fw2 {
+
+namespace {
+
+__device__ __forceinline__ void store(float *p, long long i, double v) { p[i] = (float)v; }
+__device__ __forceinline__ void store(__nv_bfloat16 *p, long long i, double v) {
+  p[i] = __float2bfloat16_rn((float)v);
+}
+
+// b = exp(-(d/kappa + alpha) dt), a = d (b - 1) / (kappa (d + kappa alpha))
+__device__ __forceinline__ void relax_ab(double d, double alpha, double kappa, double dt, double &a,
+                                         double &b) {
+  b = exp(-(d / kappa + alpha) * dt);
+  const double den = kappa * (d + kappa * alpha);
+  a = (d == 0.0 || den == 0.0) ? 0.0 : d / den * (b - 1.0);
+}
+
+// depth (cells, 0..L) into the boundary region of coordinate x on an axis of
+// n cells whose outer L cells on each side form the region
+__device__ __forceinline__ double depth_of(double x, int n, int L) {
+  if (L <= 0) return 0.0;
+  const double lo = L - 0.5, hi = n - L - 0.5;
+  double d = 0.0;
+  if (x < lo) d = lo - x;
+  else if (x > hi) d = x - hi;
+  return d < (double)L ? d : (double)L;
+}
+
+// C-PML / transition value of parameter X0 at `depth` (Table 1).
+// nu is 0-based here (nu = 0 is the paper's nu = 1); is_d selects d or alpha.
+__device__ double ramp(const PrepParams &Q, double X0, double depth, int nu, bool is_d) {
+  if (depth <= 0.0) return X0;
+  const int LT = Q.LT, LB = Q.LB, L = LT + LB;
+  if (nu == 0) {
+    double s;
+    if (Q.reading == 0) {
+      s = depth / L;
+    } else {
+      if (depth <= LT) return X0;
+      s = (depth - LT) / (LB > 0 ? LB : 1);
+    }
+    if (is_d) return (Q.d_target - X0) * pow(s, Q.npow) + X0;
+    return (0.0 - X0) * s + X0;
+  }
+  double g = 1.0;
+  if (LT > 0 && depth < LT) g = 0.5 * (1.0 - cos(M_PI * depth / LT));
+  return (0.0 - X0) * g + X0;
+}
+
+template <typename MT>
+__global__ void cell_maps_kernel(const PrepParams Q) {
+  const long long n = (long long)Q.nx * Q.ny * Q.nz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % Q.nx);
+    const long long r = t / Q.nx;
+    const int j = (int)(r % Q.ny);
+    const int k = (int)(r / Q.ny);
+    const long long o = (long long)k * Q.plane + (long long)j * Q.pitch + i;
+    const double c = Q.c[t], rho = Q.rho[t];
+    const double K = rho * c * c;
+    store((MT *)Q.K, o, K);
+    store((MT *)Q.rho_o, o, rho);
+    if (Q.nl_mode != 0) {
+      const double beta = Q.beta[t];
+      const double chi = Q.nl_mode == 1 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K;
+      store((MT *)Q.chi, o, chi);
+    }
+    const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
+    store((MT *)Q.ik1, o, 1.0 / k1);
+    store((MT *)Q.ik2, o, 1.0 / k2);
+    for (int nu = 0; nu < Q.N; ++nu) {
+      double a, b;
+      relax_ab(Q.d1[nu * n + t], Q.al1[nu * n + t], k1, Q.dt, a, b);
+      store((MT *)Q.a1, nu * Q.npts_alloc + o, a);
+      store((MT *)Q.b1, nu * Q.npts_alloc + o, b);
+      relax_ab(Q.d2[nu * n + t], Q.al2[nu * n + t], k2, Q.dt, a, b);
+      store((MT *)Q.a2, nu * Q.npts_alloc + o, a);
+      store((MT *)Q.b2, nu * Q.npts_alloc + o, b);
+    }
+  }
+}
+
+// One thread per (strip coordinate, other two coordinates) of axis `axis`.
+template <typename MT>
+__global__ void strip_maps_kernel(const PrepParams Q, int axis) {
+  const int L = Q.LT + Q.LB;
+  const int ext[3] = {Q.nx, Q.ny, Q.nz};
+  // strip extents: the axis has 2L entries, the others their full extent
+  int se[3] = {Q.nx, Q.ny, Q.nz};
+  se[axis] = 2 * L;
+  const long long n = (long long)Q.nx * Q.ny * Q.nz;
+  const long long total = (long long)se[0] * se[1] * se[2];
+  const long long pitch_out = axis == 0 ? 2 * L : Q.pitch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int s[3];
+    s[0] = (int)(t % se[0]);
+    const long long r = t / se[0];
+    s[1] = (int)(r % se[1]);
+    s[2] = (int)(r / se[1]);
+    int cell[3] = {s[0], s[1], s[2]};
+    const int sc = s[axis];
+    cell[axis] = sc < L ? sc : ext[axis] - 2 * L + sc;
+    const long long src = cell[0] + (long long)Q.nx * (cell[1] + (long long)Q.ny * cell[2]);
+    // output index in the strip layout
+    long long out;
+    if (axis == 0) out = ((long long)s[2] * Q.ny + s[1]) * pitch_out + s[0];
+    else if (axis == 1) out = ((long long)s[2] * (2 * L) + s[1]) * pitch_out + s[0];
+    else out = ((long long)s[2] * Q.ny + s[1]) * pitch_out + s[0];
+    const double dface = depth_of(cell[axis] + 0.5, ext[axis], L);
+    const double dcent = depth_of((double)cell[axis], ext[axis], L);
+    const double k1 = Q.k1[src], k2 = Q.k2[src];
+    for (int nu = 0; nu < Q.N; ++nu) {
+      double a, b;
+      const double d1 = ramp(Q, Q.d1[nu * n + src], dface, nu, true);
+      const double al1 = ramp(Q, Q.al1[nu * n + src], dface, nu, false);
+      relax_ab(d1, al1, k1, Q.dt, a, b);
+      store((MT *)Q.sa1[axis], nu * Q.strip_nu[axis] + out, a);
+      store((MT *)Q.sb1[axis], nu * Q.strip_nu[axis] + out, b);
+      const double d2 = ramp(Q, Q.d2[nu * n + src], dcent, nu, true);
+      const double al2 = ramp(Q, Q.al2[nu * n + src], dcent, nu, false);
+      relax_ab(d2, al2, k2, Q.dt, a, b);
+      store((MT *)Q.sa2[axis], nu * Q.strip_nu[axis] + out, a);
+      store((MT *)Q.sb2[axis], nu * Q.strip_nu[axis] + out, b);
+    }
+  }
+}
+
+// Largest c / sqrt(kappa1 kappa2) and largest c (FP64, as ordered bit
+// patterns of positive doubles) and a count of invalid cells.
+__global__ void medium_scan_kernel(const PrepParams Q, unsigned long long *maxbits, int *bad) {
+  const long long n = (long long)Q.nx * Q.ny * Q.nz;
+  double m_eff = 0.0, m_c = 0.0;
+  int nbad = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double c = Q.c[t], rho = Q.rho[t];
+    double k1 = 1.0, k2 = 1.0;
+    if (Q.N) {
+      k1 = Q.k1[t];
+      k2 = Q.k2[t];
+    }
+    const bool ok = isfinite(c) && c > 0.0 && isfinite(rho) && rho > 0.0 && isfinite(k1) && k1 > 0.0 &&
+                    isfinite(k2) && k2 > 0.0 && (Q.nl_mode == 0 || isfinite((double)Q.beta[t]));
+    if (!ok) {
+      ++nbad;
+      continue;
+    }
+    const double ce = c / sqrt(k1 * k2);
+    m_eff = ce > m_eff ? ce : m_eff;
+    m_c = c > m_c ? c : m_c;
+  }
+  if (m_eff > 0.0) atomicMax(&maxbits[0], (unsigned long long)__double_as_longlong(m_eff));
+  if (m_c > 0.0) atomicMax(&maxbits[1], (unsigned long long)__double_as_longlong(m_c));
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_medium_scan(const PrepParams &Q, unsigned long long *maxbits, int *bad,
+                               cudaStream_t s) {
+  const long long n = (long long)Q.nx * Q.ny * Q.nz;
+  medium_scan_kernel<<<grid_for(n), 256, 0, s>>>(Q, maxbits, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const PrepParams &Q, int map_bf16, cudaStream_t s) {
+  const long long n = (long long)Q.nx * Q.ny * Q.nz;
+  if (map_bf16) cell_maps_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, s>>>(Q);
+  else cell_maps_kernel<float><<<grid_for(n), 256, 0, s>>>(Q);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int L = Q.LT + Q.LB;
+  if (L > 0 && Q.N > 0) {
+    for (int axis = 0; axis < Q.nd; ++axis) {
+      long long total = 2LL * L * n / (axis == 0 ? Q.nx : axis == 1 ? Q.ny : Q.nz);
+      if (map_bf16) strip_maps_kernel<__nv_bfloat16><<<grid_for(total), 256, 0, s>>>(Q, axis);
+      else strip_maps_kernel<float><<<grid_for(total), 256, 0, s>>>(Q, axis);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace fw2

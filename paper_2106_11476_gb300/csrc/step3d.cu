@@ -1,0 +1,255 @@
+// 3D fused velocity and pressure half steps (sm_103a).
+//
+// Same arithmetic as the 2D kernels (Sec. 3.1 updates, Eqs. relaxation4,
+// relaxation_psi, general6) with the third axis.  Each block owns a 128 x 8
+// tile of an xy plane and marches through kTZ planes along z; the xy stencil
+// operand of the current plane is staged in shared memory with its halo, the
+// z taps of each cell's own column are read through L2.
+#include "coef.cuh"
+
+namespace fw2 {
+
+namespace {
+
+constexpr int kTY3 = 8;   // tile rows (one per thread row)
+constexpr int kTZ = 8;    // planes per block
+
+struct Win12 {
+  float v[12];
+};
+__device__ __forceinline__ Win12 win12(const float *row, int tx) {
+  Win12 w;
+  const float4 *r4 = reinterpret_cast<const float4 *>(row) + tx;
+  float4 a = r4[0], b = r4[1], c = r4[2];
+  w.v[0] = a.x; w.v[1] = a.y; w.v[2] = a.z; w.v[3] = a.w;
+  w.v[4] = b.x; w.v[5] = b.y; w.v[6] = b.z; w.v[7] = b.w;
+  w.v[8] = c.x; w.v[9] = c.y; w.v[10] = c.z; w.v[11] = c.w;
+  return w;
+}
+
+template <int N, typename MT>
+__global__ void __launch_bounds__(256) vel3d_kernel(const StepParams P) {
+  constexpr int PW = kTX + 8, PH = kTY3 + 7;  // p plane tile: x0-4.., y0-3..
+  constexpr int RW = kTX + 4, RH = kTY3 + 1;  // rho plane tile: x0.., y0..
+  __shared__ __align__(16) float sp[PH][PW];
+  __shared__ __align__(16) float sr[RH][RW];
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY3, z0 = blockIdx.z * kTZ;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const MT *rho = static_cast<const MT *>(P.rho);
+  const MT *ik1 = static_cast<const MT *>(P.ik1);
+  const int i0 = x0 + 4 * tx, j = y0 + ty;
+  const bool active = i0 < P.nx && j < P.ny;
+  const int zend = min(z0 + kTZ, P.nz);
+#pragma unroll 1
+  for (int k = z0; k < zend; ++k) {
+    __syncthreads();
+    for (int t = tid; t < PH * (PW / 4); t += 256) {
+      const int r = t / (PW / 4), c4 = t % (PW / 4);
+      *reinterpret_cast<float4 *>(&sp[r][4 * c4]) = load_chunk(P, P.p, x0 - 4 + 4 * c4, y0 - 3 + r, k);
+    }
+    for (int t = tid; t < RH * RW; t += 256) {
+      const int r = t / RW, cc = t % RW;
+      const int gx = rho_coord(x0 + cc, P.nx, P.periodic[0]);
+      const int gy = rho_coord(y0 + r, P.ny, P.periodic[1]);
+      sr[r][cc] = ldmap(rho, (long long)k * P.plane + (long long)gy * P.pitch + gx);
+    }
+    __syncthreads();
+    if (!active) continue;
+    const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
+    const int sy = ty + 3;
+    const Win12 w = win12(sp[sy], tx);
+    float4 Dx, Dy, Dz;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m] - w.v[4 + e - m + 1], d);
+      el(Dx, e) = d;
+    }
+    {
+      float4 col[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&sp[sy - 3 + m][4 * tx + 4]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float d = 0.f;
+#pragma unroll
+        for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[3 + m], e) - el(col[4 - m], e), d);
+        el(Dy, e) = d;
+      }
+    }
+    {
+      // d/dz at faces k+1/2: sum_m g_m (p[k+m] - p[k-m+1]) on the cell's own column
+      float4 zc[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) zc[m] = load_chunk(P, P.p, i0, j, k - 3 + m);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float d = 0.f;
+#pragma unroll
+        for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(zc[3 + m], e) - el(zc[4 - m], e), d);
+        el(Dz, e) = d;
+      }
+    }
+    float4 bx, by, bz;
+    {
+      const int lx = 4 * tx;
+      const float4 r0 = *reinterpret_cast<const float4 *>(&sr[ty][lx]);
+      const float r4 = sr[ty][lx + 4];
+      const float4 ru = *reinterpret_cast<const float4 *>(&sr[ty + 1][lx]);
+      const int kz = rho_coord(k + 1, P.nz, P.periodic[2]);
+      float4 rz;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = min(i0 + e, P.nx - 1);
+        el(rz, e) = ldmap(rho, (long long)kz * P.plane + (long long)j * P.pitch + x);
+      }
+      bx = make_float4(P.two_dt / (r0.x + r0.y), P.two_dt / (r0.y + r0.z), P.two_dt / (r0.z + r0.w),
+                       P.two_dt / (r0.w + r4));
+      by = make_float4(P.two_dt / (r0.x + ru.x), P.two_dt / (r0.y + ru.y), P.two_dt / (r0.z + ru.z),
+                       P.two_dt / (r0.w + ru.w));
+      bz = make_float4(P.two_dt / (r0.x + rz.x), P.two_dt / (r0.y + rz.y), P.two_dt / (r0.z + rz.z),
+                       P.two_dt / (r0.w + rz.w));
+    }
+    const float4 k1 = ldmap4(ik1, c);
+    {
+      const float4 S = stretch4<0, 1, N, MT>(P, P.psi1[0], Dx, k1, c, i0, j, k);
+      float4 v = ld_state4(P.v[0], c);
+      v.x -= bx.x * S.x; v.y -= bx.y * S.y; v.z -= bx.z * S.z; v.w -= bx.w * S.w;
+      st_state4(P.v[0], c, mask_pad(v, i0, P.nx));
+    }
+    {
+      const float4 S = stretch4<1, 1, N, MT>(P, P.psi1[1], Dy, k1, c, i0, j, k);
+      float4 v = ld_state4(P.v[1], c);
+      v.x -= by.x * S.x; v.y -= by.y * S.y; v.z -= by.z * S.z; v.w -= by.w * S.w;
+      st_state4(P.v[1], c, mask_pad(v, i0, P.nx));
+    }
+    {
+      const float4 S = stretch4<2, 1, N, MT>(P, P.psi1[2], Dz, k1, c, i0, j, k);
+      float4 v = ld_state4(P.v[2], c);
+      v.x -= bz.x * S.x; v.y -= bz.y * S.y; v.z -= bz.z * S.z; v.w -= bz.w * S.w;
+      st_state4(P.v[2], c, mask_pad(v, i0, P.nx));
+    }
+  }
+}
+
+template <int N, typename MT>
+__global__ void __launch_bounds__(256) prs3d_kernel(const StepParams P) {
+  constexpr int W = kTX + 8;
+  constexpr int HX = kTY3;      // v_x rows y0 .. y0+TY-1
+  constexpr int HY = kTY3 + 7;  // v_y rows y0-4 .. y0+TY+2
+  __shared__ __align__(16) float svx[HX][W];
+  __shared__ __align__(16) float svy[HY][W];
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY3, z0 = blockIdx.z * kTZ;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const MT *ik2 = static_cast<const MT *>(P.ik2);
+  const MT *Km = static_cast<const MT *>(P.K);
+  const MT *chim = static_cast<const MT *>(P.chi);
+  const int i0 = x0 + 4 * tx, j = y0 + ty;
+  const bool active = i0 < P.nx && j < P.ny;
+  const int zend = min(z0 + kTZ, P.nz);
+#pragma unroll 1
+  for (int k = z0; k < zend; ++k) {
+    __syncthreads();
+    for (int t = tid; t < HX * (W / 4); t += 256) {
+      const int r = t / (W / 4), c4 = t % (W / 4);
+      *reinterpret_cast<float4 *>(&svx[r][4 * c4]) = load_chunk(P, P.v[0], x0 - 4 + 4 * c4, y0 + r, k);
+    }
+    for (int t = tid; t < HY * (W / 4); t += 256) {
+      const int r = t / (W / 4), c4 = t % (W / 4);
+      *reinterpret_cast<float4 *>(&svy[r][4 * c4]) = load_chunk(P, P.v[1], x0 - 4 + 4 * c4, y0 - 4 + r, k);
+    }
+    __syncthreads();
+    if (!active) continue;
+    const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
+    const Win12 w = win12(svx[ty], tx);
+    float4 Dx, Dy, Dz;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m - 1] - w.v[4 + e - m], d);
+      el(Dx, e) = d;
+    }
+    {
+      float4 col[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&svy[ty + m][4 * tx + 4]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float d = 0.f;
+#pragma unroll
+        for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[4 + m - 1], e) - el(col[4 - m], e), d);
+        el(Dy, e) = d;
+      }
+    }
+    {
+      // d/dz v_z at centres: sum_m g_m (vz[k+m-1] - vz[k-m]); zc[4] is plane k
+      float4 zc[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) zc[m] = load_chunk(P, P.v[2], i0, j, k - 4 + m);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float d = 0.f;
+#pragma unroll
+        for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(zc[4 + m - 1], e) - el(zc[4 - m], e), d);
+        el(Dz, e) = d;
+      }
+    }
+    const float4 k2 = ldmap4(ik2, c);
+    const float4 Sx = stretch4<0, 2, N, MT>(P, P.psi2[0], Dx, k2, c, i0, j, k);
+    const float4 Sy = stretch4<1, 2, N, MT>(P, P.psi2[1], Dy, k2, c, i0, j, k);
+    const float4 Sz = stretch4<2, 2, N, MT>(P, P.psi2[2], Dz, k2, c, i0, j, k);
+    const float4 K = ldmap4(Km, c);
+    float4 p = ld_state4(P.p, c);
+    float4 upd = make_float4(P.dt * K.x * (Sx.x + Sy.x + Sz.x), P.dt * K.y * (Sx.y + Sy.y + Sz.y),
+                             P.dt * K.z * (Sx.z + Sy.z + Sz.z), P.dt * K.w * (Sx.w + Sy.w + Sz.w));
+    if (P.nl) {
+      const float4 ch = ldmap4(chim, c);
+      upd.x /= fmaf(ch.x, p.x, 1.f); upd.y /= fmaf(ch.y, p.y, 1.f);
+      upd.z /= fmaf(ch.z, p.z, 1.f); upd.w /= fmaf(ch.w, p.w, 1.f);
+    }
+    p.x -= upd.x; p.y -= upd.y; p.z -= upd.z; p.w -= upd.w;
+    st_state4(P.p, c, mask_pad(p, i0, P.nx));
+  }
+}
+
+template <typename MT>
+cudaError_t vel3d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
+  switch (P.n_relax) {
+    case 0: vel3d_kernel<0, MT><<<g, b, 0, s>>>(P); break;
+    case 1: vel3d_kernel<1, MT><<<g, b, 0, s>>>(P); break;
+    case 2: vel3d_kernel<2, MT><<<g, b, 0, s>>>(P); break;
+    case 3: vel3d_kernel<3, MT><<<g, b, 0, s>>>(P); break;
+    case 4: vel3d_kernel<4, MT><<<g, b, 0, s>>>(P); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename MT>
+cudaError_t prs3d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
+  switch (P.n_relax) {
+    case 0: prs3d_kernel<0, MT><<<g, b, 0, s>>>(P); break;
+    case 1: prs3d_kernel<1, MT><<<g, b, 0, s>>>(P); break;
+    case 2: prs3d_kernel<2, MT><<<g, b, 0, s>>>(P); break;
+    case 3: prs3d_kernel<3, MT><<<g, b, 0, s>>>(P); break;
+    case 4: prs3d_kernel<4, MT><<<g, b, 0, s>>>(P); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s) {
+  dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kTY3);
+  return map_bf16 ? vel3d_dispatch<__nv_bfloat16>(P, g, b, s) : vel3d_dispatch<float>(P, g, b, s);
+}
+
+cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s) {
+  dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kTY3);
+  return map_bf16 ? prs3d_dispatch<__nv_bfloat16>(P, g, b, s) : prs3d_dispatch<float>(P, g, b, s);
+}
+
+}  // namespace fw2

@@ -1,0 +1,361 @@
+"""ctypes binding of libfw2.so (include/fw2.h): argument marshalling only.
+
+Every function named ``fw2_*`` here forwards to the C entry point of the same
+name; all compute runs in the library's CUDA kernels.  Arrays are numpy
+(host) or torch CUDA tensors (device); torch provides device memory and the
+stream.  Loading fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfw2.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, EUNSTABLE, ETIMEOUT, EUNSUPPORTED = range(8)
+STATUS_NAMES = ["FW2_OK", "FW2_EINVAL", "FW2_ENOMEM", "FW2_ECUDA", "FW2_ESTATE", "FW2_EUNSTABLE",
+                "FW2_ETIMEOUT", "FW2_EUNSUPPORTED"]
+MEM_HOST, MEM_DEVICE = 0, 1
+BC = {"zero": 0, "periodic": 1}
+NL = {"off": 0, "pressure": 1, "westervelt": 2}
+MAP = {"f32": 0, "bf16": 1}
+PML_READING = {"A": 0, "B": 1}
+MEM_ALIGN = {"centred": 0, "endpoint": 1}
+SRC_KIND = {"p": 0, "vx": 1, "vy": 2, "vz": 3}
+FIELD = {"p": 0, "vx": 1, "vy": 2, "vz": 3, "psi1x": 4, "psi1y": 5, "psi1z": 6,
+         "psi2x": 7, "psi2y": 8, "psi2z": 9}
+
+
+class Fw2Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("n_relax", C.c_int32), ("n", C.c_int64 * 3), ("h", C.c_double),
+                ("dt", C.c_double), ("cfl", C.c_double), ("g", C.c_double * 5),
+                ("pml_transition", C.c_int32), ("pml_bound", C.c_int32), ("pml_reading", C.c_int32),
+                ("map_precision", C.c_int32), ("pml_rc", C.c_double), ("pml_npow", C.c_double),
+                ("pml_cp", C.c_double), ("nl_mode", C.c_int32), ("mem_alignment", C.c_int32),
+                ("bc", C.c_int32 * 3), ("reserved_", C.c_int32), ("stream", C.c_void_p)]
+
+
+class RelaxDesc(C.Structure):
+    _fields_ = [("kappa1", C.c_void_p), ("kappa2", C.c_void_p), ("d1", C.c_void_p), ("alpha1", C.c_void_p),
+                ("d2", C.c_void_p), ("alpha2", C.c_void_p), ("mem_space", C.c_int32)]
+
+
+EXPORTS = {
+    "fw2_config_init": (C.c_int, [C.POINTER(Config)]),
+    "fw2_create": (C.c_int, [C.POINTER(Config), C.POINTER(C.c_void_p)]),
+    "fw2_set_medium": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "fw2_set_relaxation": (C.c_int, [C.c_void_p, C.POINTER(RelaxDesc)]),
+    "fw2_add_source": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_int64, C.c_int64, C.c_int32]),
+    "fw2_record": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                             C.c_int64, C.c_int32]),
+    "fw2_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "fw2_destroy": (C.c_int, [C.c_void_p]),
+    "fw2_get_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "fw2_get_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "fw2_set_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "fw2_get_field": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "fw2_set_field": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "fw2_reset": (C.c_int, [C.c_void_p]),
+    "fw2_synchronize": (C.c_int, [C.c_void_p]),
+    "fw2_check_field": (C.c_int, [C.c_void_p, C.c_float, C.POINTER(C.c_float)]),
+    "fw2_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "fw2_kernel_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "fw2_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fw2_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "fw2_last_error": (C.c_char_p, [C.c_void_p]),
+    "fw2_abi_version": (C.c_int32, []),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libfw2.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfw2.so not found at {LIB_PATH}: build it with "
+                               "paper_2106_11476_gb300._build.build() (nvcc, sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, ctx=None):
+    if status != OK:
+        raise Fw2Error(status, fw2_last_error(ctx))
+
+
+def _ptr(a):
+    """(pointer, mem_space, keepalive) of a numpy array or torch tensor (float32/int64/int32)."""
+    if a is None:
+        return None, MEM_HOST, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, MEM_HOST, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        t = a.contiguous()
+        return t.data_ptr(), (MEM_DEVICE if t.is_cuda else MEM_HOST), t
+    raise TypeError(type(a))
+
+
+def _same_space(*arrays):
+    spaces = {_ptr(a)[1] for a in arrays if a is not None}
+    if len(spaces) > 1:
+        raise ValueError("all arrays of one call must live in the same memory space")
+    return spaces.pop() if spaces else MEM_HOST
+
+
+# ---------------------------------------------------------------- C names ---
+
+def fw2_config_init() -> Config:
+    cfg = Config()
+    _check(lib().fw2_config_init(C.byref(cfg)))
+    return cfg
+
+
+def fw2_create(cfg: Config) -> int:
+    h = C.c_void_p()
+    _check(lib().fw2_create(C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def fw2_set_medium(ctx, c, rho, beta=None):
+    space = _same_space(c, rho, beta)
+    pc, _, kc = _ptr(np.asarray(c, np.float32) if isinstance(c, np.ndarray) else c)
+    pr, _, kr = _ptr(np.asarray(rho, np.float32) if isinstance(rho, np.ndarray) else rho)
+    pb, _, kb = _ptr(np.asarray(beta, np.float32) if isinstance(beta, np.ndarray) else beta)
+    _check(lib().fw2_set_medium(ctx, pc, pr, pb, space), ctx)
+
+
+def fw2_set_relaxation(ctx, kappa1, kappa2, d1, alpha1, d2, alpha2):
+    arrs = [np.asarray(x, np.float32) if isinstance(x, np.ndarray) else x
+            for x in (kappa1, kappa2, d1, alpha1, d2, alpha2)]
+    space = _same_space(*arrs)
+    ptrs = [_ptr(a) for a in arrs]
+    desc = RelaxDesc(*[p[0] for p in ptrs], space)
+    _check(lib().fw2_set_relaxation(ctx, C.byref(desc)), ctx)
+
+
+def fw2_add_source(ctx, kind: str, idx, group, signal):
+    idx = np.asarray(idx, np.int64) if isinstance(idx, np.ndarray) else idx
+    group = np.asarray(group, np.int32) if isinstance(group, np.ndarray) else group
+    signal = np.asarray(signal, np.float32) if isinstance(signal, np.ndarray) else signal
+    space = _same_space(idx, group, signal)
+    pi, _, ki = _ptr(idx)
+    pg, _, kg = _ptr(group)
+    ps, _, ks = _ptr(signal)
+    n_steps, n_groups = signal.shape
+    _check(lib().fw2_add_source(ctx, SRC_KIND[kind], int(idx.shape[0]), pi, pg, ps, int(n_groups),
+                                int(n_steps), space), ctx)
+
+
+def fw2_record(ctx, idx, group, n_groups: int, out, n_steps: int):
+    idx = np.asarray(idx, np.int64) if isinstance(idx, np.ndarray) else idx
+    group = np.asarray(group, np.int32) if isinstance(group, np.ndarray) else group
+    space = _same_space(idx, group)
+    pi, _, ki = _ptr(idx)
+    pg, _, kg = _ptr(group)
+    _check(lib().fw2_record(ctx, int(idx.shape[0]), pi, pg, int(n_groups),
+                            C.c_void_p(out.data_ptr() if out is not None else 0), int(n_steps), space), ctx)
+
+
+def fw2_step(ctx, n_steps: int):
+    _check(lib().fw2_step(ctx, int(n_steps)), ctx)
+
+
+def fw2_destroy(ctx):
+    if ctx:
+        lib().fw2_destroy(ctx)
+
+
+def fw2_get_dt(ctx) -> float:
+    v = C.c_double()
+    _check(lib().fw2_get_dt(ctx, C.byref(v)), ctx)
+    return v.value
+
+
+def fw2_get_step(ctx) -> int:
+    v = C.c_int64()
+    _check(lib().fw2_get_step(ctx, C.byref(v)), ctx)
+    return v.value
+
+
+def fw2_set_step(ctx, step: int):
+    _check(lib().fw2_set_step(ctx, int(step)), ctx)
+
+
+def fw2_get_field(ctx, field: str, out):
+    p, space, keep = _ptr(out)
+    _check(lib().fw2_get_field(ctx, FIELD[field], p, space), ctx)
+    return out
+
+
+def fw2_set_field(ctx, field: str, arr):
+    arr = np.asarray(arr, np.float32) if isinstance(arr, np.ndarray) else arr
+    p, space, keep = _ptr(arr)
+    _check(lib().fw2_set_field(ctx, FIELD[field], p, space), ctx)
+
+
+def fw2_reset(ctx):
+    _check(lib().fw2_reset(ctx), ctx)
+
+
+def fw2_synchronize(ctx):
+    _check(lib().fw2_synchronize(ctx), ctx)
+
+
+def fw2_check_field(ctx, bound: float):
+    m = C.c_float()
+    st = lib().fw2_check_field(ctx, C.c_float(bound), C.byref(m))
+    return st, m.value
+
+
+def fw2_device_bytes(ctx) -> int:
+    v = C.c_int64()
+    _check(lib().fw2_device_bytes(ctx, C.byref(v)), ctx)
+    return v.value
+
+
+def fw2_kernel_launches(ctx) -> int:
+    v = C.c_int64()
+    _check(lib().fw2_kernel_launches(ctx, C.byref(v)), ctx)
+    return v.value
+
+
+def fw2_profile(ctx, enable: bool):
+    _check(lib().fw2_profile(ctx, 1 if enable else 0), ctx)
+
+
+def fw2_profile_read(ctx):
+    """(vel_ms, vel_launches, prs_ms, prs_launches) since profiling was enabled."""
+    tv, nv, tp, np_ = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
+    _check(lib().fw2_profile_read(ctx, C.byref(tv), C.byref(nv), C.byref(tp), C.byref(np_)), ctx)
+    return tv.value, nv.value, tp.value, np_.value
+
+
+def fw2_last_error(ctx=None) -> str:
+    r = lib().fw2_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def fw2_abi_version() -> int:
+    return lib().fw2_abi_version()
+
+
+# ------------------------------------------------------------ convenience ---
+
+def config_for(prob, stream: Optional[int] = None, map_precision: str = "f32") -> Config:
+    """A Config for a problem description (any object with the attributes of
+    synth.Problem: shape, h, dt, nrelax, pml_*, nl_mode, memory_alignment, bc, taps)."""
+    cfg = fw2_config_init()
+    nd = len(prob.shape)
+    cfg.ndim = nd
+    cfg.n_relax = int(prob.nrelax)
+    full = list(prob.shape) + [1] * (3 - nd)
+    for q in range(3):
+        cfg.n[q] = int(full[q])
+        cfg.bc[q] = BC[prob.bc[q]] if q < nd else 0
+    cfg.h = float(prob.h)
+    cfg.dt = float(prob.dt) if prob.dt else 0.0
+    if prob.taps is not None:
+        for i in range(5):
+            cfg.g[i] = float(prob.taps[i])
+    cfg.pml_transition = int(prob.pml_transition)
+    cfg.pml_bound = int(prob.pml_bound)
+    cfg.pml_reading = PML_READING[prob.pml_reading]
+    cfg.pml_rc = float(prob.pml_rc)
+    cfg.pml_npow = float(prob.pml_npow)
+    cfg.pml_cp = float(prob.pml_cp)
+    cfg.nl_mode = NL[prob.nl_mode]
+    cfg.mem_alignment = MEM_ALIGN[prob.memory_alignment]
+    cfg.map_precision = MAP[map_precision]
+    cfg.stream = stream
+    return cfg
+
+
+class Simulation:
+    """One fw2 context built from a problem description.
+
+    Traces land in a torch CUDA tensor ``self.trace`` of [n_steps, n_groups].
+    """
+
+    def __init__(self, prob, map_precision: str = "f32", device_inputs: bool = False, stream=None):
+        import torch
+        self.prob = prob
+        self.torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.cfg = config_for(prob, stream=stream.cuda_stream, map_precision=map_precision)
+        self.ctx = fw2_create(self.cfg)
+        try:
+            conv = (lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()) \
+                if device_inputs else (lambda a: a)
+            fw2_set_medium(self.ctx, conv(prob.c), conv(prob.rho), conv(prob.beta) if prob.nl_mode != "off" else None)
+            if prob.nrelax:
+                fw2_set_relaxation(self.ctx, conv(prob.kappa1), conv(prob.kappa2), conv(prob.d1),
+                                   conv(prob.alpha1), conv(prob.d2), conv(prob.alpha2))
+            for s in prob.sources:
+                fw2_add_source(self.ctx, s.kind, conv(s.idx), conv(s.group), conv(s.signal))
+            self.trace = None
+            if prob.sensors is not None and prob.n_steps > 0:
+                sn = prob.sensors
+                self.trace = torch.zeros((prob.n_steps, sn.n_groups), dtype=torch.float32, device="cuda")
+                fw2_record(self.ctx, conv(sn.idx), conv(sn.group), sn.n_groups, self.trace, prob.n_steps)
+            self.dt = fw2_get_dt(self.ctx)
+        except Exception:
+            fw2_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def step(self, n: int):
+        fw2_step(self.ctx, n)
+        return self
+
+    def synchronize(self):
+        fw2_synchronize(self.ctx)
+
+    def field(self, name: str) -> np.ndarray:
+        g = tuple(reversed(self.prob.shape))
+        if name.startswith("psi"):
+            out = np.empty((self.prob.nrelax,) + g, np.float32)
+        else:
+            out = np.empty(g, np.float32)
+        return fw2_get_field(self.ctx, name, out)
+
+    def set_state(self, st: dict):
+        for k, v in st.items():
+            fw2_set_field(self.ctx, k, v)
+
+    @property
+    def launches(self) -> int:
+        return fw2_kernel_launches(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            fw2_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -28,3 +28,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def fw2lib():
+    """libfw2.so, built for sm_103a if missing or stale (nvcc cross-compiles on CPU)."""
+    from paper_2106_11476_gb300 import _build
+    _build.build()
+    from paper_2106_11476_gb300 import fw2
+    return fw2.lib()

@@ -1,0 +1,93 @@
+"""The C ABI library: loads, exports what include/fw2.h declares, validates
+its inputs before touching a device (runs without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2106_11476_gb300 import fw2
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "fw2.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fw2_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary_calls():
+    syms = declared_symbols()
+    for name in ("fw2_create", "fw2_set_medium", "fw2_set_relaxation", "fw2_add_source",
+                 "fw2_step", "fw2_record", "fw2_destroy"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(fw2lib):
+    for name in declared_symbols():
+        assert hasattr(fw2lib, name), name
+    assert set(declared_symbols()) == set(fw2.EXPORTS), "binding and header disagree"
+
+
+def test_struct_layout_matches_header(fw2lib):
+    # fw2_config_init writes the whole struct; the sentinel after it must survive
+    class Guarded(C.Structure):
+        _fields_ = [("cfg", fw2.Config), ("guard", C.c_uint64)]
+    g = Guarded()
+    g.guard = 0xDEADBEEFCAFEF00D
+    assert fw2lib.fw2_config_init(C.byref(g.cfg)) == 0
+    assert g.guard == 0xDEADBEEFCAFEF00D
+    assert g.cfg.ndim == 2 and abs(g.cfg.cfl - 0.4) < 1e-15 and abs(g.cfg.pml_rc - 1e-3) < 1e-18
+    assert g.cfg.pml_npow == 2.0 and g.cfg.mem_alignment == 0
+
+
+def test_abi_version(fw2lib):
+    assert fw2.fw2_abi_version() == 1
+
+
+@pytest.mark.parametrize("patch,status", [
+    ({"ndim": 4}, fw2.EINVAL),
+    ({"n": (4, 64, 1)}, fw2.EINVAL),
+    ({"n_relax": 9}, fw2.EUNSUPPORTED),
+    ({"n_relax": -1}, fw2.EINVAL),
+    ({"h": 0.0}, fw2.EINVAL),
+    ({"pml_transition": 30, "pml_bound": 10, "n_relax": 2}, fw2.EINVAL),   # 2 * 40 > 64
+    ({"pml_transition": 4, "n_relax": 0}, fw2.EINVAL),                     # PML needs N >= 1
+    ({"nl_mode": 7}, fw2.EINVAL),
+    ({"map_precision": 5}, fw2.EINVAL),
+    ({"ndim": 3, "n": (64, 64, 64), "g": (1.0, 0, 0, 0, 0.1)}, fw2.EUNSUPPORTED),
+])
+def test_create_rejects_bad_configs(fw2lib, patch, status):
+    cfg = fw2.fw2_config_init()
+    cfg.n[0], cfg.n[1], cfg.n[2] = 64, 64, 1
+    cfg.h = 1e-4
+    for k, v in patch.items():
+        if k in ("n", "g"):
+            for i, x in enumerate(v):
+                getattr(cfg, k)[i] = x
+        else:
+            setattr(cfg, k, v)
+    h = C.c_void_p()
+    st = fw2lib.fw2_create(C.byref(cfg), C.byref(h))
+    assert st == status, fw2.fw2_last_error(None)
+    assert h.value is None
+    assert len(fw2.fw2_last_error(None)) > 0
+
+
+def test_create_without_device_fails_cleanly(fw2lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    cfg = fw2.fw2_config_init()
+    cfg.n[0], cfg.n[1] = 64, 64
+    cfg.h = 1e-4
+    h = C.c_void_p()
+    assert fw2lib.fw2_create(C.byref(cfg), C.byref(h)) == fw2.ECUDA
+    assert "device" in fw2.fw2_last_error(None)
+
+
+def test_null_context_calls_are_rejected(fw2lib):
+    assert fw2lib.fw2_step(None, 1) == fw2.EINVAL
+    assert fw2lib.fw2_destroy(None) == 0
+    assert fw2.fw2_last_error(None)

@@ -1,0 +1,363 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+The oracle runs on the same float32 inputs with its coefficient maps rounded
+to float32 (the maps the kernels stream), in FP64 arithmetic.  Tolerances
+(the accuracy target of the method's GPU port): relative L2 <= 1e-4 and
+max |error| <= 1e-4 of the peak for fields; sensor traces within -100 dB of
+their peak.
+"""
+import math
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.core import OracleSim
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-4
+MAX_REL = 1e-4
+TRACE_DB = -100.0
+
+
+@pytest.fixture(scope="module")
+def fw2(fw2lib):
+    from paper_2106_11476_gb300 import fw2 as m
+    return m
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def max_rel(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    m = np.max(np.abs(b))
+    return np.max(np.abs(a - b)) / m if m > 0 else np.max(np.abs(a))
+
+
+def trace_db(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    e = np.max(np.abs(a - b)); m = np.max(np.abs(b))
+    return 20 * math.log10(max(e, 1e-300) / m)
+
+
+def assert_field(name, g, o, rel=REL_L2, mx=MAX_REL):
+    r, m = rel_l2(g, o), max_rel(g, o)
+    assert r <= rel and m <= mx, f"{name}: rel L2 {r:.3e}, max/peak {m:.3e}"
+
+
+def state_names(prob):
+    names = ["p"] + ["v" + "xyz"[q] for q in range(prob.ndim)]
+    if prob.nrelax:
+        names += ["psi1" + "xyz"[q] for q in range(prob.ndim)] + ["psi2" + "xyz"[q] for q in range(prob.ndim)]
+    return names
+
+
+def small_2d(nx=200, ny=136, N=2, nl="off", steps=300, seed=0, pml=(12, 4), alignment="centred",
+             reading="A", vel_src=False, hetero=True):
+    key = {2: "N2_y1.0_a0.5", 4: "N4_y1.1_a0.5"}.get(N)
+    rng = np.random.default_rng(seed)
+    f0 = 3e6
+    h = 1540.0 / f0 / 12
+    relax = synth.relaxation_sets()[key] if N else None
+    prob = synth.homogeneous((nx, ny), h, 0.0, relax=relax)
+    g = prob.grid_shape
+    if hetero:
+        prob.c = (1540.0 * (1 + 0.08 * rng.standard_normal(g).clip(-2, 2))).astype(np.float32)
+        prob.rho = (1000.0 * (1 + 0.1 * rng.random(g))).astype(np.float32)
+    prob.dt = 0.4 * h / float(prob.c.max()) * 0.95
+    if nl != "off":
+        prob.beta = rng.uniform(3.0, 8.0, g).astype(np.float32)
+    prob.nl_mode = nl
+    prob.memory_alignment = alignment
+    prob.pml_reading = reading
+    if N:
+        prob.pml_transition, prob.pml_bound = pml
+    L = sum(pml) if N else 0
+    xs = np.arange(L + 2, nx - L - 2)
+    sig = synth.gaussian_pulse(steps, prob.dt, f0, 3.0, 2e6 if nl != "off" else 1e5)
+    prob.sources = [synth.Source("p", synth.flat_index((nx, ny), xs, L + 6), np.zeros(xs.size, np.int32),
+                                 sig[:, None])]
+    if vel_src:
+        ys = np.arange(L + 10, L + 20)
+        sig2 = np.stack([sig * 1e-6, -sig * 2e-6], axis=1).astype(np.float32)
+        prob.sources.append(synth.Source("vx", synth.flat_index((nx, ny), nx // 2, ys),
+                                         (np.arange(ys.size) % 2).astype(np.int32), sig2))
+        prob.sources.append(synth.Source("vy", synth.flat_index((nx, ny), ys, ny // 2),
+                                         np.zeros(ys.size, np.int32), sig2[:, :1].copy()))
+    sens = synth.random_sensors((nx, ny), 30, max(L, 4), rng)
+    # two grouped sensors (element averaging) on top of the point sensors
+    grp_idx = synth.flat_index((nx, ny), np.arange(L + 4, L + 15), ny // 2)
+    sens = synth.Sensors(np.concatenate([sens.idx, grp_idx]),
+                         np.concatenate([sens.group, np.full(grp_idx.size, 30, np.int32)]), 31)
+    prob.sensors = sens
+    prob.n_steps = steps
+    return prob
+
+
+def compare_run(fw2, prob, steps, state=None, check_trace=True, rel=REL_L2, mx=MAX_REL):
+    sim = fw2.Simulation(prob)
+    if state is not None:
+        sim.set_state(state)
+    sim.step(steps)
+    sim.synchronize()
+    orc = OracleSim(prob, round_to="f32")
+    if state is not None:
+        orc.set_state(state)
+    orc.run(steps)
+    for name in state_names(prob):
+        assert_field(name, sim.field(name), orc.field(name), rel, mx)
+    if check_trace and prob.sensors is not None:
+        tg = sim.trace.cpu().numpy()[:steps]
+        to = orc.trace[:steps]
+        db = trace_db(tg, to)
+        assert db <= TRACE_DB, f"trace error {db:.1f} dB"
+    sim.close()
+    return sim, orc
+
+
+CASES_2D = {
+    "base": dict(),
+    "nonlinear-pressure": dict(nl="pressure"),
+    "westervelt-N4": dict(nl="westervelt", N=4),
+    "endpoint-readingB": dict(alignment="endpoint", reading="B"),
+    "ragged-203x77": dict(nx=203, ny=77, pml=(8, 3)),
+    "velocity-sources": dict(vel_src=True, N=4),
+    "tiny-tile": dict(nx=24, ny=20, pml=(3, 1), steps=200),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES_2D))
+def test_parity_2d(fw2, case):
+    kw = dict(CASES_2D[case])
+    steps = kw.get("steps", 300)
+    prob = small_2d(**kw)
+    compare_run(fw2, prob, steps)
+
+
+def test_parity_2d_periodic_lossless_cross_taps(fw2):
+    """N = 0, periodic on both axes, g11 != 0, from a random state (no sources)."""
+    prob = synth.homogeneous((144, 96), 1e-4, 0.0)
+    rng = np.random.default_rng(2)
+    prob.c = (1500 + 200 * rng.random(prob.grid_shape)).astype(np.float32)
+    prob.dt = 0.3 * 1e-4 / float(prob.c.max())
+    prob.bc = ("periodic", "periodic", "zero")
+    taps = [1225 / 1024, -245 / 3072, 49 / 5120, -5 / 7168]
+    prob.taps = (taps[0] * 0.98, taps[1], taps[2], taps[3], 0.005)
+    st = synth.random_state(prob, seed=7)
+    compare_run(fw2, prob, 250, state=st, check_trace=False)
+
+
+def test_parity_2d_random_state_all_fields(fw2):
+    """Non-zero memory variables everywhere from the start (random state)."""
+    prob = small_2d(N=4, nl="pressure", steps=60)
+    st = synth.random_state(prob, seed=11)
+    compare_run(fw2, prob, 60, state=st)
+
+
+def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3):
+    rng = np.random.default_rng(seed)
+    f0 = 1e6
+    h = 1540.0 / f0 / 10
+    relax = synth.relaxation_sets()["N3_y1.2_brain"]
+    prob = synth.homogeneous(n, h, 0.0, relax=relax)
+    g = prob.grid_shape
+    prob.c = (1560.0 * (1 + 0.1 * rng.random(g))).astype(np.float32)
+    prob.rho = (1040.0 * (1 + 0.1 * rng.random(g))).astype(np.float32)
+    prob.dt = 0.4 * h / float(prob.c.max())
+    prob.beta = rng.uniform(3, 6, g).astype(np.float32)
+    prob.nl_mode = nl
+    prob.pml_transition, prob.pml_bound = 6, 2
+    sig = synth.gaussian_pulse(steps, prob.dt, f0, 2.0, 1e6)
+    X, Y = np.meshgrid(np.arange(20, 50), np.arange(12, 28), indexing="xy")
+    idx = synth.flat_index(n, X.ravel(), Y.ravel(), 10)
+    prob.sources = [synth.Source("p", idx, np.zeros(idx.size, np.int32), sig[:, None]),
+                    synth.Source("vz", idx[:40], np.zeros(40, np.int32), (sig * 1e-6)[:, None])]
+    prob.sensors = synth.random_sensors(n, 25, 8, rng)
+    prob.n_steps = steps
+    return prob
+
+
+def test_parity_3d(fw2):
+    prob = small_3d()
+    compare_run(fw2, prob, 80)
+
+
+def test_parity_3d_random_state(fw2):
+    prob = small_3d(n=(36, 44, 40), steps=30)
+    st = synth.random_state(prob, seed=5)
+    compare_run(fw2, prob, 30, state=st)
+
+
+def test_parity_plain_2d_config_full(fw2):
+    """The plain 2D configuration in full: 512 x 512, N = 4, y = 1.1, linear,
+    4-wavelength C-PML, line source, 256 sensors, 1000 steps."""
+    prob = synth.line_source_problem(n=512, n_steps=1000)
+    compare_run(fw2, prob, 1000)
+
+
+def _window_compare(sim, orc, prob, window, steps, rel=REL_L2, mx=MAX_REL):
+    m = 8 * steps
+    sl_g, sl_o = [], []
+    for q in reversed(range(prob.ndim)):
+        lo, hi = window[q]
+        a = lo if lo == 0 else lo + m
+        b = hi if hi == prob.shape[q] else hi - m
+        sl_g.append(slice(a, b))
+        sl_o.append(slice(a - lo, b - lo))
+    for name in state_names(prob):
+        g = sim.field(name)
+        o = orc.field(name)
+        assert_field(name + str(window), g[(Ellipsis,) + tuple(sl_g)], o[(Ellipsis,) + tuple(sl_o)], rel, mx)
+
+
+def test_parity_abdominal_full_size_windows(fw2):
+    """4096 x 4096 heterogeneous nonlinear medium, N = 4, in the launch
+    configuration the benchmark times, from a seeded wavefield: after 4 steps
+    the GPU matches the oracle on windows covering a C-PML corner, the array
+    and the deep interior (sampled outputs the oracle computes exactly)."""
+    prob = synth.abdominal_problem(n=4096, n_steps=8)
+    st = synth.random_state(prob, seed=21)
+    steps = 4
+    sim = fw2.Simulation(prob)
+    sim.set_state(st)
+    sim.step(steps)
+    sim.synchronize()
+    for window in (((0, 160), (0, 160)), ((1900, 2200), (30, 200)), ((3000, 3200), (3900, 4096))):
+        orc = OracleSim(prob, round_to="f32", window=window)
+        orc.set_state(st)
+        orc.run(steps)
+        _window_compare(sim, orc, prob, window, steps)
+    sim.close()
+
+
+def test_deterministic_bitwise(fw2):
+    prob = small_2d(N=4, nl="pressure", steps=120, vel_src=True)
+    out = []
+    for _ in range(2):
+        sim = fw2.Simulation(prob)
+        sim.step(120)
+        out.append((sim.field("p"), sim.trace.cpu().numpy()))
+        sim.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_split_steps_equal_one_call(fw2):
+    """fw2_step(a) + fw2_step(b) == fw2_step(a + b) (source and trace rows follow the step index)."""
+    prob = small_2d(steps=100)
+    s1 = fw2.Simulation(prob); s1.step(100)
+    s2 = fw2.Simulation(prob); s2.step(37); s2.step(0); s2.step(63)
+    np.testing.assert_array_equal(s1.field("p"), s2.field("p"))
+    np.testing.assert_array_equal(s1.trace.cpu().numpy(), s2.trace.cpu().numpy())
+
+
+def test_device_inputs_equal_host_inputs(fw2):
+    prob = small_2d(steps=50, vel_src=True)
+    a = fw2.Simulation(prob); a.step(50)
+    b = fw2.Simulation(prob, device_inputs=True); b.step(50)
+    np.testing.assert_array_equal(a.field("p"), b.field("p"))
+    np.testing.assert_array_equal(a.trace.cpu().numpy(), b.trace.cpu().numpy())
+
+
+def test_steps_past_signal_and_trace_rows(fw2):
+    """Sources fall silent and recording stops past their tables; rows past
+    n_steps of the trace buffer are never written."""
+    import torch
+    prob = small_2d(steps=40)
+    sim = fw2.Simulation(prob)
+    sn = prob.sensors
+    buf = torch.full((50, sn.n_groups), 7.0, device="cuda")
+    fw2.fw2_record(sim.ctx, sn.idx, sn.group, sn.n_groups, buf, 40)
+    sim.step(80)
+    sim.synchronize()
+    assert torch.all(buf[40:] == 7.0)
+    assert not torch.any(buf[:40] == 7.0)
+    orc = OracleSim(replace(synth.with_steps(prob, 80), sensors=None), round_to="f32")
+    orc.run(80)
+    assert_field("p", sim.field("p"), orc.field("p"))
+
+
+def test_checkpoint_restore_is_bitwise(fw2):
+    """Snapshot at step 60 (fields + step counter), restore into a fresh
+    context, continue 40 steps: identical to an uninterrupted 100-step run."""
+    prob = small_2d(N=4, steps=100, vel_src=True)
+    full = fw2.Simulation(prob); full.step(100)
+    a = fw2.Simulation(prob); a.step(60)
+    snap = {n: a.field(n) for n in state_names(prob)}
+    b = fw2.Simulation(prob)
+    b.set_state(snap)
+    fw2.fw2_set_step(b.ctx, fw2.fw2_get_step(a.ctx))
+    b.step(40)
+    for n in state_names(prob):
+        np.testing.assert_array_equal(full.field(n), b.field(n))
+    np.testing.assert_array_equal(full.trace.cpu().numpy()[60:], b.trace.cpu().numpy()[60:])
+
+
+def test_reset_and_field_roundtrip(fw2):
+    prob = small_2d(steps=30)
+    sim = fw2.Simulation(prob)
+    sim.step(30)
+    p = sim.field("p")
+    assert np.abs(p).max() > 0
+    fw2.fw2_reset(sim.ctx)
+    assert np.abs(sim.field("p")).max() == 0 and fw2.fw2_get_step(sim.ctx) == 0
+    sim.set_state({"p": p})
+    np.testing.assert_array_equal(sim.field("p"), p)
+
+
+def test_check_field_flags_nonfinite(fw2):
+    """Failure detection without a GPU fault: a NaN planted from the host."""
+    prob = small_2d(steps=10)
+    sim = fw2.Simulation(prob)
+    sim.step(10)
+    st, m = fw2.fw2_check_field(sim.ctx, 1e9)
+    assert st == fw2.OK and 0 < m < 1e9
+    p = sim.field("p")
+    p[5, 7] = np.nan
+    sim.set_state({"p": p})
+    st, m = fw2.fw2_check_field(sim.ctx, 1e9)
+    assert st == fw2.EUNSTABLE and math.isinf(m)
+    assert "max |p|" in fw2.fw2_last_error(sim.ctx)
+
+
+def test_step_before_medium_is_a_state_error(fw2):
+    prob = small_2d(steps=10)
+    cfg = fw2.config_for(prob)
+    ctx = fw2.fw2_create(cfg)
+    try:
+        with pytest.raises(fw2.Fw2Error) as e:
+            fw2.fw2_step(ctx, 1)
+        assert e.value.status == fw2.ESTATE
+    finally:
+        fw2.fw2_destroy(ctx)
+
+
+def test_unstable_time_step_rejected(fw2):
+    prob = small_2d(steps=10)
+    prob.dt = prob.dt * 2.0
+    with pytest.raises(fw2.Fw2Error) as e:
+        fw2.Simulation(prob)
+    assert e.value.status == fw2.EINVAL and "stability" in str(e.value)
+
+
+def test_bad_medium_rejected(fw2):
+    prob = small_2d(steps=10)
+    prob.c = prob.c.copy()
+    prob.c[3, 3] = -1.0
+    with pytest.raises(fw2.Fw2Error) as e:
+        fw2.Simulation(prob)
+    assert e.value.status == fw2.EINVAL
+
+
+def test_cfl_time_step_matches_oracle_rule(fw2):
+    from oracle import coefficients as cf
+    prob = small_2d(N=4, steps=10)
+    prob.dt = 0.0
+    sim = fw2.Simulation(prob)
+    assert abs(sim.dt / cf.cfl_time_step(prob, 0.4) - 1) < 1e-15
