@@ -57,10 +57,18 @@ enum { FW2_BC_ZERO = 0, FW2_BC_PERIODIC = 1 };
  * Eq. (general6); WESTERVELT: chi = -2 beta kappa0 (kappa0 = 1 / (rho c^2)). */
 enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2 };
 enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1 };
-/* C-PML geometry (Sec. 3.3): A: the nu = 1 ramps span L_T + L_B cells;
- * B: they span only the outer L_B cells.  In both, nu >= 2 parameters fall
- * to zero over the inner L_T cells with the cosine transition. */
-enum { FW2_PML_A = 0, FW2_PML_B = 1 };
+/* C-PML geometry (Sec. 3.3, Table 1).  In every reading the nu >= 2
+ * parameters fall to zero over the inner L_T cells with the cosine transition
+ * and kappa is kept.  A: d^{nu=1} (polynomial) and alpha^{nu=1} (linear) ramp
+ * over all L_T + L_B cells.  B: both ramp over the outer L_B cells only.
+ * C (default): d^{nu=1} as in A; alpha^{nu=1} is blended by the cosine
+ * transition over the inner L_T cells from the tissue's value into the
+ * C-PML profile d_target (1 - x/L) (linear to zero at the outer edge,
+ * d_target of Table 1 acting as the maximum frequency shift), so the
+ * transition layer turns the tissue's first mechanism into the single
+ * C-PML mechanism.  Only C meets the paper's reflection figures in the
+ * Table 2 tissue while staying stable over long runs. */
+enum { FW2_PML_A = 0, FW2_PML_B = 1, FW2_PML_C = 2 };
 /* time alignment of the memory term in Eq. (relaxation_psi): CENTRED uses
  * the mean of the memory variable before and after its update (D^{n-1/2}
  * estimated by (D^n + D^{n-1}) / 2); ENDPOINT uses the updated value. */
@@ -85,7 +93,7 @@ typedef struct {
                             1225/1024, -245/3072, 49/5120, -5/7168, g11 = 0 */
   int32_t pml_transition;/* L_T, cells per side (Sec. 3.3) */
   int32_t pml_bound;     /* L_B, cells per side */
-  int32_t pml_reading;   /* FW2_PML_A (default) or FW2_PML_B */
+  int32_t pml_reading;   /* FW2_PML_C (default), FW2_PML_A or FW2_PML_B */
   int32_t map_precision; /* FW2_MAP_F32 or FW2_MAP_BF16 storage of coefficient maps */
   double pml_rc;         /* reflection target R_c of Table 1 (default 1e-3) */
   double pml_npow;       /* polynomial order of the d ramp (default 2) */
@@ -112,7 +120,7 @@ typedef struct {
 } fw2_relax_desc;
 
 /* Fill *cfg with defaults (2D, N = 0, Taylor taps, CFL 0.4, R_c = 1e-3,
- * npow = 2, reading A, FP32 maps, linear, centred memory term, zero BC). */
+ * npow = 2, reading C, FP32 maps, linear, centred memory term, zero BC). */
 fw2_status fw2_config_init(fw2_config *cfg);
 
 /* Create a context for one grid (Sec. 3.1 staggered layout) and allocate its

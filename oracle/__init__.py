@@ -21,8 +21,12 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
 * attenuating stepper: pinned by the fully discrete dispersion relation of
   the scheme, by the paper's attenuation / phase-velocity claims for its
   Table 2 parameters and by the classical-PML special case.
-* C-PML profiles (Table 1): parity unpinned (reflection pin pending).
-* nonlinear term (Eq. general6): parity unpinned (Burgers pin pending).
+* C-PML profiles (Sec. 3.3, Table 1): pinned by the normal-incidence
+  reflection figures of Sec. 4.2 and by the instability the transition layer
+  removes (the counterfactual planted in the oracle grows, the scheme decays).
+* nonlinear term (Eq. general6): pinned by the first 7 harmonics of the
+  pre-shock Poisson solution of the inviscid Burgers equation (Sec. 4.5),
+  with the effective coefficient of each nonlinear mode.
 * staggered-grid placement of rho, kappa and the PML coordinate (not printed
   in the paper): parity unpinned beyond the readings stated in the design notes.
 """

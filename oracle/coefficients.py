@@ -110,6 +110,12 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
                      the transition layer, 0 beyond it.
     Reading A: the nu = 1 ramps span the whole boundary L_T + L_B.
     Reading B: the nu = 1 ramps span only the outer L_B cells.
+    Reading C: as A for d^{nu=1}; alpha^{nu=1} is blended by the cosine
+    transition over L_T from the tissue's value into the C-PML profile
+    d_target (1 - x/L), which is linear to 0 at the outer edge (d_target
+    plays the role of the maximum frequency shift of a C-PML), so the
+    transition layer turns the tissue's first mechanism into the single
+    C-PML mechanism.
     `nu` is 1-based as in the paper; `which` is "d" or "alpha".
     """
     X0 = np.asarray(X0, np.float64)
@@ -118,8 +124,16 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
     inside = depth > 0
     if not np.any(inside) or L == 0:
         return out
+    if nu == 1 and which == "alpha" and reading.upper() == "C":
+        # the tissue's alpha is blended (cosine over the transition layer)
+        # into the C-PML profile alpha_cfs = d_target (1 - x/L), which falls
+        # linearly to 0 at the outer edge
+        gT = np.where(depth < LT, 0.5 * (1.0 - np.cos(np.pi * depth / max(LT, 1))), 1.0) if LT > 0 \
+            else np.ones_like(depth)
+        a_cfs = d_target * (1.0 - depth / L)
+        return np.where(inside, (1.0 - gT) * X0 + gT * a_cfs, X0)
     if nu == 1:
-        if reading.upper() == "A":
+        if reading.upper() in ("A", "C"):
             s = depth / L
             active = inside
         else:

@@ -46,12 +46,12 @@ class State(C.Structure):
 
 class Sources(C.Structure):
     _fields_ = [("n_pts", C.c_int64), ("kind", C.POINTER(C.c_int32)), ("idx", C.POINTER(C.c_int64)),
-                ("col", C.POINTER(C.c_int32)), ("signal", DP), ("n_cols", C.c_int64)]
+                ("col", C.POINTER(C.c_int32)), ("signal", DP), ("n_cols", C.c_int64), ("n_rows", C.c_int64)]
 
 
 class Record(C.Structure):
     _fields_ = [("n_pts", C.c_int64), ("idx", C.POINTER(C.c_int64)), ("group", C.POINTER(C.c_int32)),
-                ("n_groups", C.c_int64), ("trace", DP)]
+                ("n_groups", C.c_int64), ("trace", DP), ("n_rows", C.c_int64)]
 
 
 def _dp(a: Optional[np.ndarray]):
@@ -143,6 +143,7 @@ class OracleSim:
             self.src.col = c_.ctypes.data_as(C.POINTER(C.c_int32))
             self.src.signal = _dp(sg)
             self.src.n_cols = sg.shape[1]
+            self.src.n_rows = sg.shape[0]
             self.n_signal_rows = sg.shape[0]
         else:
             self.src.n_pts = 0
@@ -159,6 +160,7 @@ class OracleSim:
             self.rec.group = self._rec_arrays[1].ctypes.data_as(C.POINTER(C.c_int32))
             self.rec.n_groups = sn.n_groups
             self.rec.trace = _dp(self.trace)
+            self.rec.n_rows = self.trace.shape[0]
         else:
             self.rec.n_pts = 0
 
@@ -203,10 +205,6 @@ class OracleSim:
                 self.psi2[q][:] = self._crop(np.asarray(st["psi2" + names[q]]).reshape((N,) + self.prob.grid_shape)).reshape(N, -1)
 
     def run(self, n_steps: int):
-        if self.n_signal_rows is not None:
-            assert self.step_index + n_steps <= self.n_signal_rows, "signal table too short"
-        if self.trace is not None:
-            assert self.step_index + n_steps <= self.trace.shape[0], "trace buffer too short"
         lib().orc_run(C.byref(self.G), C.byref(self.C), C.byref(self.S),
                       C.byref(self.src) if self.src.n_pts else None,
                       C.byref(self.rec) if self.rec.n_pts else None,
@@ -222,7 +220,7 @@ class OracleSim:
             names["v" + ch] = self.v[q]
             names["psi1" + ch] = self.psi1[q]
             names["psi2" + ch] = self.psi2[q]
-        a = names[name]
+        a = names[name].copy()
         if a.ndim == 2:
             return a.reshape((a.shape[0],) + g)
         return a.reshape(g)

@@ -70,8 +70,9 @@ typedef struct {
   const int32_t *kind;    /* 0: pressure, 1..3: velocity component x,y,z */
   const int64_t *idx;     /* flat cell index of each entry */
   const int32_t *col;     /* column of the signal table feeding each entry */
-  const double *signal;   /* [n_steps][n_cols] additive source values */
+  const double *signal;   /* [n_rows][n_cols] additive source values */
   int64_t n_cols;
+  int64_t n_rows;         /* steps at or past n_rows inject nothing */
 } orc_sources;
 
 typedef struct {
@@ -79,7 +80,8 @@ typedef struct {
   const int64_t *idx;     /* flat cell index */
   const int32_t *group;   /* sensor (group) of each cell */
   int64_t n_groups;
-  double *trace;          /* [n_steps][n_groups], mean of p over each group */
+  double *trace;          /* [n_rows][n_groups], mean of p over each group */
+  int64_t n_rows;         /* steps at or past n_rows record nothing */
 } orc_record;
 
 static int64_t npts(const orc_grid *G) { return G->n[0] * G->n[1] * G->n[2]; }
@@ -233,7 +235,7 @@ static void pressure_half_step(const orc_grid *G, const orc_coef *C,
 
 static void add_sources(const orc_sources *src, orc_state *S, int64_t step,
                         int want_pressure) {
-  if (!src || src->n_pts == 0) return;
+  if (!src || src->n_pts == 0 || step >= src->n_rows) return;
   for (int64_t e = 0; e < src->n_pts; e++) {
     int kind = src->kind[e];
     if ((kind == 0) != (want_pressure != 0)) continue;
@@ -247,7 +249,7 @@ static void add_sources(const orc_sources *src, orc_state *S, int64_t step,
 }
 
 static void record(const orc_record *rec, const orc_state *S, int64_t step) {
-  if (!rec || rec->n_pts == 0) return;
+  if (!rec || rec->n_pts == 0 || step >= rec->n_rows) return;
   double *row = rec->trace + step * rec->n_groups;
   int64_t *count = (int64_t *)calloc((size_t)rec->n_groups, sizeof(int64_t));
   for (int64_t g = 0; g < rec->n_groups; g++) row[g] = 0.0;

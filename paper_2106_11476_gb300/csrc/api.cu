@@ -398,7 +398,7 @@ fw2_status fw2_config_init(fw2_config *cfg) {
   cfg->cfl = 0.4;
   cfg->pml_rc = 1e-3;
   cfg->pml_npow = 2.0;
-  cfg->pml_reading = FW2_PML_A;
+  cfg->pml_reading = FW2_PML_C;
   cfg->map_precision = FW2_MAP_F32;
   cfg->nl_mode = FW2_NL_OFF;
   cfg->mem_alignment = FW2_MEM_CENTRED;
@@ -432,7 +432,7 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
     if (!(cfg.pml_rc > 0.0 && cfg.pml_rc < 1.0)) return fail(nullptr, FW2_EINVAL, "pml_rc must lie in (0, 1)");
     if (!(cfg.pml_npow >= 0.0)) return fail(nullptr, FW2_EINVAL, "pml_npow must be >= 0");
   }
-  if (cfg.pml_reading != FW2_PML_A && cfg.pml_reading != FW2_PML_B) return fail(nullptr, FW2_EINVAL, "bad pml_reading");
+  if (cfg.pml_reading < FW2_PML_A || cfg.pml_reading > FW2_PML_C) return fail(nullptr, FW2_EINVAL, "bad pml_reading");
   if (cfg.map_precision != FW2_MAP_F32 && cfg.map_precision != FW2_MAP_BF16)
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
   if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_WESTERVELT) return fail(nullptr, FW2_EINVAL, "bad nl_mode");

@@ -73,6 +73,9 @@ __device__ __forceinline__ void st_state4(float *p, long long i, float4 v) {
 __device__ __forceinline__ float &el(float4 &v, int e) {
   return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
+__device__ __forceinline__ float el(const float4 &v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
 
 // Strip coordinate along an axis of extent n with L boundary cells per side,
 // or -1 in the interior.

@@ -9,7 +9,9 @@
 //   per-axis a, b inside the boundary strips, where d and alpha follow the
 //   two-stage C-PML ramps of Table 1:  X = (X_target - X_0) g + X_0 with
 //   g = (x/L)^npow (nu = 1, d), x/L (nu = 1, alpha) and
-//   (1 - cos(pi x / L_T)) / 2 over the transition layer (nu >= 2).
+//   (1 - cos(pi x / L_T)) / 2 over the transition layer (nu >= 2).  In
+//   reading C alpha^{nu=1} is blended by that cosine into the C-PML profile
+//   d_target (1 - x/L).
 // The profile of a face is evaluated at its exact staggered coordinate; the
 // relaxation parameters of a face are those of its lower-index cell.
 #include "fw2_prep.cuh"
@@ -47,9 +49,18 @@ __device__ __forceinline__ double depth_of(double x, int n, int L) {
 __device__ double ramp(const PrepParams &Q, double X0, double depth, int nu, bool is_d) {
   if (depth <= 0.0) return X0;
   const int LT = Q.LT, LB = Q.LB, L = LT + LB;
+  if (nu == 0 && !is_d && Q.reading == 2) {
+    // reading C: the tissue's alpha is blended (cosine over the transition
+    // layer) into the C-PML profile d_target (1 - x/L), linear to 0 at the
+    // outer edge
+    double gT = 1.0;
+    if (LT > 0 && depth < LT) gT = 0.5 * (1.0 - cos(M_PI * depth / LT));
+    const double a_cfs = Q.d_target * (1.0 - depth / L);
+    return (1.0 - gT) * X0 + gT * a_cfs;
+  }
   if (nu == 0) {
     double s;
-    if (Q.reading == 0) {
+    if (Q.reading != 1) {
       s = depth / L;
     } else {
       if (depth <= LT) return X0;

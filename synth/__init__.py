@@ -76,7 +76,7 @@ class Problem:
     pml_rc: float = 1e-3
     pml_npow: float = 2.0
     pml_cp: float = 0.0       # 0: use the largest sound speed of the medium
-    pml_reading: str = "A"
+    pml_reading: str = "C"
     nl_mode: str = "off"      # "off", "pressure" or "westervelt"
     memory_alignment: str = "centred"   # "centred" or "endpoint" time alignment of the memory term
     bc: Tuple[str, ...] = ("zero", "zero", "zero")

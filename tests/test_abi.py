@@ -39,7 +39,7 @@ def test_struct_layout_matches_header(fw2lib):
     assert fw2lib.fw2_config_init(C.byref(g.cfg)) == 0
     assert g.guard == 0xDEADBEEFCAFEF00D
     assert g.cfg.ndim == 2 and abs(g.cfg.cfl - 0.4) < 1e-15 and abs(g.cfg.pml_rc - 1e-3) < 1e-18
-    assert g.cfg.pml_npow == 2.0 and g.cfg.mem_alignment == 0
+    assert g.cfg.pml_npow == 2.0 and g.cfg.mem_alignment == 0 and g.cfg.pml_reading == 2
 
 
 def test_abi_version(fw2lib):
