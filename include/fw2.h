@@ -194,6 +194,26 @@ fw2_status fw2_synchronize(fw2_ctx *ctx);
  * Synchronising.  *max_abs receives max |p| (inf if non-finite); returns
  * FW2_EUNSTABLE when the field fails, FW2_OK otherwise. */
 fw2_status fw2_check_field(fw2_ctx *ctx, float bound, float *max_abs);
+/* Field scan that allocates nothing.  The paper has no counterpart: this is
+ * a service for callers that cannot allocate device memory -- applications
+ * that own every device allocation themselves (a host framework's allocator,
+ * a fixed memory budget that must account for each byte) or latency-critical
+ * loops that cannot afford the device-wide synchronisation cudaMalloc and
+ * cudaFree may cause.  It needs no context.
+ * Computes max |x| over n_rows rows of row_len floats, row_pitch floats
+ * apart, starting at `field` (device memory), and writes it to *out (device
+ * memory); a non-finite value gives +inf.  Asynchronous on `stream` (NULL:
+ * default stream).  Scratch: a file-scope device array of 2^20 floats
+ * (4 MiB), one partial per row, held by every GPU that loads the library
+ * until the process exits; n_rows above 2^20 is rejected with FW2_EINVAL.
+ * The first call on a device resolves that array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  Calls
+ * share the array: calls that overlap on the GPU race; each call overwrites
+ * every row it uses, so nothing carries over.  Calls no cudaMalloc, cudaFree
+ * or other allocating routine.  Errors: FW2_EINVAL (null pointer, bad
+ * sizes), FW2_ECUDA (launch failure); fw2_last_error(NULL) explains. */
+fw2_status fw2_field_absmax_noalloc(const float *field, int64_t row_len, int64_t n_rows,
+                                    int64_t row_pitch, float *out, void *stream);
 /* Bytes of device memory held by the context. */
 fw2_status fw2_device_bytes(fw2_ctx *ctx, int64_t *bytes);
 /* Launches of library kernels since creation (all kinds). */

@@ -14,8 +14,15 @@
 using namespace fw2;
 
 namespace {
-
 thread_local std::string g_create_error = "no error";
+}
+
+namespace fw2 {
+// error text of calls without a context (fw2_last_error(NULL))
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace fw2
+
+namespace {
 
 struct HostSource {
   int kind;

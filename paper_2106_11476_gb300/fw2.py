@@ -74,6 +74,8 @@ EXPORTS = {
     "fw2_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "fw2_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "fw2_field_absmax_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
+                                           C.c_void_p]),
     "fw2_last_error": (C.c_char_p, [C.c_void_p]),
     "fw2_abi_version": (C.c_int32, []),
 }
@@ -249,6 +251,14 @@ def fw2_profile_read(ctx):
     tv, nv, tp, np_ = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
     _check(lib().fw2_profile_read(ctx, C.byref(tv), C.byref(nv), C.byref(tp), C.byref(np_)), ctx)
     return tv.value, nv.value, tp.value, np_.value
+
+
+def fw2_field_absmax_noalloc(field, row_len: int, n_rows: int, row_pitch: int, out, stream=None) -> int:
+    """max |field| over n_rows rows into the one-element device tensor `out`,
+    without allocating (returns the status; see include/fw2.h)."""
+    return lib().fw2_field_absmax_noalloc(C.c_void_p(field.data_ptr()), int(row_len), int(n_rows),
+                                          int(row_pitch), C.c_void_p(out.data_ptr()),
+                                          C.c_void_p(stream if stream else 0))
 
 
 def fw2_last_error(ctx=None) -> str:
