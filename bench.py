@@ -77,6 +77,19 @@ def algorithmic_bytes(shape, N, L, nl, map_bytes=4):
     return vel, prs
 
 
+def algorithmic_bytes_indexed(shape, N, L, nl):
+    """As algorithmic_bytes for the tissue-index form: per cell one uint8 index
+    replaces the interior maps (tables live in shared memory); cells inside a
+    C-PML strip still read that axis' float a, b."""
+    nd = len(shape)
+    classes = strip_cell_counts(shape, L)
+    coef = sum(cnt * len(axes_in) * 2 * N * 4 for axes_in, cnt in classes.items())
+    n = int(np.prod(shape))
+    vel = n * (4 + 1 + nd * 8 + nd * N * 8) + coef
+    prs = n * (nd * 4 + 1 + 8 + nd * N * 8) + coef
+    return vel, prs
+
+
 # --------------------------------------------------------------------------
 # helpers
 # --------------------------------------------------------------------------
@@ -178,10 +191,10 @@ def device_id_for_smi():
         return vis or "0"
 
 
-def oracle_baseline(prob, steps, window):
+def oracle_baseline(prob, steps, window, maps="f32"):
     """The FP64 oracle, as it stands, on a window of the workload (host cores)."""
     from oracle.core import OracleSim
-    orc = OracleSim(prob, round_to="f32", window=window)
+    orc = OracleSim(prob, round_to=maps, window=window)
     orc.run(2)
     t0 = time.perf_counter()
     orc.run(steps)
@@ -189,7 +202,7 @@ def oracle_baseline(prob, steps, window):
     pts = int(np.prod(orc.wshape))
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": pts * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{orc.wshape[0]}x{orc.wshape[1]} window of the workload around the array "
+            "sample": f"{'x'.join(str(w) for w in orc.wshape)} window of the workload around the array "
                       f"(sources inside), {steps} steps, {dt:.1f} s"}
 
 
@@ -205,13 +218,37 @@ def run_fw2(args, rank, world, dist):
     _build.build()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    n = args.n
     total_steps = args.warmup + args.steps
-    prob = synth.abdominal_problem(n=n, n_steps=total_steps, seed=1 + rank)
+    if args.workload == "abdominal-idx":
+        n = args.n
+        prob = synth.indexed_abdominal_problem(nx=n, ny=n, n_steps=total_steps, seed=1 + rank, n_elements=128,
+                                               focus_mm=40.0)
+        maps = args.maps or "idx"
+        mbytes = {"idx": 0, "f32": 4, "bf16": 2}[maps]
+        kv, kp = "vel2d", "prs2d"
+        workload = (f"2D heterogeneous nonlinear abdominal wall in tissue-index form (class x 64 scatterer "
+                    f"levels), {n}x{n} cells at lambda/12 for 3 MHz, N=4, 128-element focused array, "
+                    f"{maps} maps")
+    elif args.workload == "skull":
+        n = args.n if args.n != 4096 else 768
+        prob = synth.skull_problem(n=n, n_steps=total_steps, seed=2 + rank)
+        maps, mbytes, kv, kp = "bf16", 2, "vel3d", "prs3d"
+        workload = (f"3D transcranial-like medium, {n}^3 cells at lambda/10 for 1 MHz, N=3, brain background "
+                    f"with an ellipsoidal skull shell, 16x16 planar array, bf16 maps")
+    else:
+        n = args.n
+        prob = synth.abdominal_problem(n=n, n_steps=total_steps, seed=1 + rank)
+        maps, mbytes, kv, kp = "f32", 4, "vel2d", "prs2d"
+        workload = (f"2D heterogeneous nonlinear abdominal wall, {n}x{n} cells at lambda/12 for 3 MHz, "
+                    f"N=4 mechanisms, beta 4-6, 128-element focused array, element-mean traces, FP32 maps")
     vel_b, prs_b = algorithmic_bytes(prob.shape, prob.nrelax, prob.pml_transition + prob.pml_bound,
-                                     prob.nl_mode != "off")
+                                     prob.nl_mode != "off", map_bytes=mbytes)
+    if maps == "idx":
+        # one uint8 index per cell replaces every interior map; strips stay float
+        vel_b, prs_b = algorithmic_bytes_indexed(prob.shape, prob.nrelax, prob.pml_transition + prob.pml_bound,
+                                                 prob.nl_mode != "off")
     stream = torch.cuda.current_stream()
-    sim = fw2.Simulation(prob, stream=stream)
+    sim = fw2.Simulation(prob, stream=stream, map_precision=maps)
     sim.step(args.warmup)
     sim.synchronize()
     fw2.fw2_profile(sim.ctx, True)
@@ -241,9 +278,9 @@ def run_fw2(args, rank, world, dist):
     value = world * pts * args.steps / (elapsed_max * 1e-3) / 1e9
     # roofline of the dominant kernel
     peaks, peak_kind = measured_peaks()
-    dom = "vel2d" if vel_ms >= prs_ms else "prs2d"
-    dom_ms = (vel_ms / nv) if dom == "vel2d" else (prs_ms / np_)
-    dom_bytes = vel_b if dom == "vel2d" else prs_b
+    dom = kv if vel_ms >= prs_ms else kp
+    dom_ms = (vel_ms / nv) if dom == kv else (prs_ms / np_)
+    dom_bytes = vel_b if dom == kv else prs_b
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
     traffic = committed_traffic(dom)
@@ -268,18 +305,26 @@ def run_fw2(args, rank, world, dist):
             pinned[id(t_)] = t_
             return t_
         import dataclasses
-        hp = dataclasses.replace(prob, c=pin(prob.c), rho=pin(prob.rho), beta=pin(prob.beta),
-                                 kappa1=pin(prob.kappa1), kappa2=pin(prob.kappa2), d1=pin(prob.d1),
-                                 alpha1=pin(prob.alpha1), d2=pin(prob.d2), alpha2=pin(prob.alpha2))
-        h2d = sum(x.numel() * x.element_size() for x in (hp.c, hp.rho, hp.beta, hp.kappa1, hp.kappa2,
-                                                          hp.d1, hp.alpha1, hp.d2, hp.alpha2) if x is not None)
+        if maps == "idx":
+            tabs = {k: pin(v) for k, v in prob.tables.items()}
+            hp = dataclasses.replace(prob, tissue=pin(prob.tissue), tables=tabs)
+            used = [hp.tissue] + [tabs[k] for k in ("c", "rho", "kappa1", "kappa2", "d1", "alpha1", "d2", "alpha2")]
+            if prob.nl_mode != "off":
+                used.append(tabs["beta"])
+        else:
+            hp = dataclasses.replace(prob, c=pin(prob.c), rho=pin(prob.rho), beta=pin(prob.beta),
+                                     kappa1=pin(prob.kappa1), kappa2=pin(prob.kappa2), d1=pin(prob.d1),
+                                     alpha1=pin(prob.alpha1), d2=pin(prob.d2), alpha2=pin(prob.alpha2))
+            used = [x for x in (hp.c, hp.rho, hp.beta, hp.kappa1, hp.kappa2, hp.d1, hp.alpha1, hp.d2, hp.alpha2)
+                    if x is not None]
+        h2d = sum(x.numel() * x.element_size() for x in used)
         h2d += sum(s.idx.nbytes + s.group.nbytes + s.signal.nbytes for s in prob.sources)
         h2d += prob.sensors.idx.nbytes + prob.sensors.group.nbytes
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        s2 = fw2.Simulation(hp, stream=stream)
+        s2 = fw2.Simulation(hp, stream=stream, map_precision=maps)  # tables stay host numpy for idx
         s2.step(args.steps)
         trace_host = s2.trace[: args.steps].cpu()
         t1 = time.perf_counter()
@@ -295,23 +340,198 @@ def run_fw2(args, rank, world, dist):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         c0 = n // 2
-        cpu = oracle_baseline(prob, args.cpu_steps, ((c0 - 256, c0 + 256), (0, 512)))
+        if prob.ndim == 2:
+            win = ((c0 - 256, c0 + 256), (0, 512))
+        else:
+            win = ((c0 - 40, c0 + 40), (c0 - 40, c0 + 40), (36, 116))
+        cpu = oracle_baseline(prob, args.cpu_steps, win, maps)
     if rank != 0:
         return
+    data = ("synthetic (seeded skull-like shell in a brain-like medium; stands in for the micro-CT rat skull)"
+            if prob.ndim == 3 else
+            "synthetic (seeded abdominal-wall-like medium; stands in for the Visible Human phantom)")
     out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(elapsed_max / args.steps, 5),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": "synthetic (seeded abdominal-wall-like medium; stands in for the Visible Human phantom)",
-           "config": {"workload": f"2D heterogeneous nonlinear abdominal wall, {n}x{n} cells at lambda/12 "
-                                  f"for 3 MHz, N=4 mechanisms, beta 4-6, 128-element focused array, "
-                                  f"element-mean traces, FP32 maps",
-                      "grid": [n, n], "n_relax": 4, "nl_mode": prob.nl_mode, "map_precision": "f32",
+           "data": data,
+           "config": {"workload": workload,
+                      "grid": list(prob.shape), "n_relax": prob.nrelax, "nl_mode": prob.nl_mode, "map_precision": maps,
                       "pml_cells": prob.pml_transition + prob.pml_bound,
                       "l2": "state and maps (>2.5 GB) exceed L2; no flush needed",
                       "parallelism": f"replicas x{world} (one transmit event per GPU)"},
            "latency": {"p50_ms_per_step": round(float(np.percentile(per_step, 50)), 5),
                        "p99_ms_per_step": round(float(np.percentile(per_step, 99)), 5)},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+def batch_problems(args, rank):
+    """64 focused transmits over one 2048 x 1024 tissue-index medium (seeded
+    lateral foci) and 16 tissue-index instances with sides in [512, 1536]."""
+    import synth
+    rng = np.random.default_rng(100 + rank)
+    steps = args.warmup + args.steps
+    probs = []
+    for e in range(64):
+        probs.append(synth.indexed_abdominal_problem(nx=2048, ny=1024, n_steps=steps, seed=1 + rank,
+                                                     n_elements=64, focus_mm=float(rng.uniform(15, 35)),
+                                                     focus_x_mm=float(rng.uniform(-10, 10))))
+    for e in range(16):
+        nx, ny = (int(v) for v in rng.integers(512, 1537, 2))
+        probs.append(synth.indexed_abdominal_problem(nx=nx, ny=ny, n_steps=steps, seed=200 + 16 * rank + e,
+                                                     n_elements=16))
+    return probs
+
+
+def run_batch(args, rank, world, dist):
+    """Batched tissue-index form vs the plain form (dense float maps, one
+    context at a time) on the same 80 problems."""
+    import torch
+    from paper_2106_11476_gb300 import _build, fw2
+    _build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    probs = batch_problems(args, rank)
+    cells = sum(p.n_pts for p in probs)
+    sims = [fw2.Simulation(p, map_precision="idx") for p in probs]
+    batch = fw2.fw2_batch_create([s.ctx for s in sims])
+    fw2.fw2_batch_step(batch, max(args.warmup, 4))       # includes the 4 tuning steps
+    fw2.fw2_batch_synchronize(batch)
+    grid, order, l0 = fw2.fw2_batch_info(batch)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(device_id_for_smi()) as clk:
+        t0 = time.perf_counter()
+        fw2.fw2_batch_step(batch, args.steps)
+        fw2.fw2_batch_synchronize(batch)
+        t_batch = time.perf_counter() - t0
+    _, _, l1 = fw2.fw2_batch_info(batch)
+    fw2.fw2_batch_destroy(batch)
+    for s in sims:
+        s.close()
+    del sims
+    torch.cuda.empty_cache()
+    # plain form: the same problems, dense float maps, one after the other
+    plain_steps = min(args.steps, 50)
+    done, t_plain, finish = 0, 0.0, []
+    for p in probs:
+        s = fw2.Simulation(p, map_precision="f32")
+        s.step(3)
+        s.synchronize()
+        t0 = time.perf_counter()
+        s.step(plain_steps)
+        s.synchronize()
+        dt = time.perf_counter() - t0
+        s.close()
+        t_plain += dt * args.steps / plain_steps       # time for the full K steps at this rate
+        finish.append(t_plain)
+        done += p.n_pts * args.steps
+    te = torch.tensor([t_batch], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    value = world * cells * args.steps / float(te.item()) / 1e9
+    if rank != 0:
+        return
+    peaks, _ = measured_peaks()
+    vb = sum(sum(algorithmic_bytes_indexed(p.shape, p.nrelax, p.pml_transition + p.pml_bound, True)) for p in probs)
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_batch / args.steps * 1e3, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded tissue-index abdominal media)",
+           "config": {"workload": "batched: 64 focused transmits over one 2048x1024 tissue-index medium + 16 "
+                                  "instances 512^2..1536^2, one persistent launch per half step, graph-captured "
+                                  "step loop, autotuned launch", "cells_per_step": cells,
+                      "tuned_grid": grid, "tuned_order": order},
+           "roofline": {"bound": "hbm", "kernel": "step (all kernels)", "unit": "GB/s",
+                        "achieved": round(vb * args.steps / t_batch / 1e9, 1), "peak": float(peaks["hbm_gbs"]),
+                        "frac": round(vb * args.steps / t_batch / 1e9 / float(peaks["hbm_gbs"]), 4),
+                        "traffic": None},
+           "plain_form": {"value": round(done / t_plain / 1e9, 4), "unit": UNIT,
+                          "how": "same problems, dense float maps, one context at a time (rate over "
+                                 f"{plain_steps} steps each, scaled to {args.steps})"},
+           "time_to_result_s": {"batched_p50": round(t_batch, 3), "batched_p99": round(t_batch, 3),
+                                "plain_p50": round(float(np.percentile(finish, 50)), 3),
+                                "plain_p99": round(float(np.percentile(finish, 99)), 3)},
+           "gpu_launches": int(l1 - l0), "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+def serve_requests(args, rank):
+    """Poisson arrivals (mean `--rate` per s) of seeded requests: 70 % 2D
+    tissue-index abdominal media, 30 % 3D skull-like media (N = 3, bf16
+    maps).  Sizes and step counts are scaled down from the serving
+    configuration (2D sides 512-4096, 1-4k steps; 3D sides 256-512, 1-2k
+    steps) by --serve-scale so that one bench call stays within minutes."""
+    import synth
+    from paper_2106_11476_gb300.serve import Request
+    rng = np.random.default_rng(500 + rank)
+    sc = args.serve_scale
+    t = 0.0
+    reqs = []
+    for i in range(args.requests):
+        t += rng.exponential(1.0 / args.rate)
+        if rng.random() < 0.7:
+            side = int(rng.integers(512, 4097) * sc) // 4 * 4
+            steps = int(rng.integers(1000, 4001) * sc)
+            p = synth.indexed_abdominal_problem(nx=max(side, 256), ny=max(side, 256), n_steps=steps,
+                                                seed=1000 + i, n_elements=min(64, max(side, 256) // 24))
+            reqs.append(Request(i, t, p, steps, "idx"))
+        else:
+            side = int(rng.integers(256, 513) * sc)
+            steps = int(rng.integers(1000, 2001) * sc)
+            p = synth.skull_problem(n=max(side, 96), n_steps=steps, seed=2000 + i, pml_cells=16, array_elems=4)
+            reqs.append(Request(i, t, p, steps, "bf16"))
+    return reqs
+
+
+def run_serve(args, rank, world, dist):
+    import torch
+    from paper_2106_11476_gb300 import _build, fw2
+    from paper_2106_11476_gb300.serve import Server, latency_stats
+    _build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = serve_requests(args, rank)
+    work = sum(r.cells * r.steps for r in reqs)
+    srv = Server(cap_bytes=160e9, slice_steps=args.slice)
+    with ClockSampler(device_id_for_smi()) as clk:
+        t0 = time.perf_counter()
+        done = srv.run(reqs)
+        makespan = time.perf_counter() - t0
+    served = latency_stats(done)
+    # plain form, one request at a time in arrival order with float maps:
+    # measured rate per request (a short run), then the FIFO schedule
+    t_free, finish = 0.0, []
+    for r in sorted(reqs, key=lambda q: q.arrival):
+        s0 = time.perf_counter()
+        sim = fw2.Simulation(r.problem, map_precision="f32")
+        setup = time.perf_counter() - s0
+        k = min(r.steps, 30)
+        sim.step(2); sim.synchronize()
+        s1 = time.perf_counter()
+        sim.step(k); sim.synchronize()
+        run = (time.perf_counter() - s1) * r.steps / k
+        sim.close()
+        start = max(t_free, r.arrival)
+        t_free = start + setup + run
+        finish.append(t_free - r.arrival)
+    plain_makespan = t_free - min(r.arrival for r in reqs)
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": round(work / makespan / 1e9, 4), "unit": UNIT, "n_gpus": world,
+           "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic (seeded request stream)",
+           "config": {"workload": f"serving: {args.requests} Poisson arrivals at {args.rate}/s, 70 % 2D "
+                                  f"tissue-index / 30 % 3D bf16, sizes and steps scaled by {args.serve_scale}, "
+                                  f"160 GB admission cap, slices of {args.slice} steps",
+                      "makespan_s": round(makespan, 3), "cell_steps": work},
+           "latency": {"p50_time_to_result_s": round(served["p50_s"], 3),
+                       "p99_time_to_result_s": round(served["p99_s"], 3)},
+           "plain_form": {"value": round(work / plain_makespan / 1e9, 4), "unit": UNIT,
+                          "p50_time_to_result_s": round(float(np.percentile(finish, 50)), 3),
+                          "p99_time_to_result_s": round(float(np.percentile(finish, 99)), 3),
+                          "how": "one request at a time in arrival order, float maps; each request's run "
+                                 "time from a 30-step measurement scaled to its steps, plus its measured setup"},
            "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 
@@ -353,6 +573,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fw2", choices=["fw2", "reference"])
     ap.add_argument("--n", type=int, default=4096, help="grid side of the workload")
+    ap.add_argument("--requests", type=int, default=24, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    ap.add_argument("--serve-scale", type=float, default=0.25, help="serving: size and step scale")
+    ap.add_argument("--slice", type=int, default=100, help="serving: steps per slice")
+    ap.add_argument("--workload", default="abdominal",
+                    choices=["abdominal", "abdominal-idx", "skull", "batch", "serve"],
+                    help="abdominal: 2D 4096^2 nonlinear (default); abdominal-idx: the same in tissue-index "
+                         "form; skull: 3D 768^3 with bf16 maps")
+    ap.add_argument("--maps", default=None, choices=["f32", "bf16", "idx"],
+                    help="override the map storage of the workload")
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -372,7 +602,12 @@ def main():
         tdist.init_process_group("nccl")
         dist = tdist
     try:
-        run_fw2(args, rank, world, dist)
+        if args.workload == "batch":
+            run_batch(args, rank, world, dist)
+        elif args.workload == "serve":
+            run_serve(args, rank, world, dist)
+        else:
+            run_fw2(args, rank, world, dist)
     finally:
         if dist:
             dist.destroy_process_group()

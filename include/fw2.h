@@ -56,7 +56,10 @@ enum { FW2_BC_ZERO = 0, FW2_BC_PERIODIC = 1 };
  * OFF: chi = 0; PRESSURE: chi = kappa0 (1 - 2 beta), the factor printed in
  * Eq. (general6); WESTERVELT: chi = -2 beta kappa0 (kappa0 = 1 / (rho c^2)). */
 enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2 };
-enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1 };
+/* storage of the coefficient maps: float, bf16 (b kept as 1 - b), or a
+ * uint8 tissue index per cell into per-tissue float tables (2D only; set the
+ * medium with fw2_set_medium_indexed) */
+enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1, FW2_MAP_IDX_U8 = 2 };
 /* C-PML geometry (Sec. 3.3, Table 1).  In every reading the nu >= 2
  * parameters fall to zero over the inner L_T cells with the cosine transition
  * and kappa is kept.  A: d^{nu=1} (polynomial) and alpha^{nu=1} (linear) ramp
@@ -134,6 +137,18 @@ fw2_status fw2_create(const fw2_config *cfg, fw2_ctx **out);
 fw2_status fw2_set_medium(fw2_ctx *ctx, const float *c, const float *rho,
                           const float *beta, int32_t mem_space);
 
+/* Reduced-storage medium (map_precision FW2_MAP_IDX_U8): every cell holds a
+ * tissue index tissue[n_pts] < n_tissue <= 256, and the material and
+ * relaxation parameters of Eqs. (wave1)-(general6) and Sec. 3.2 are
+ * per-tissue tables: c, rho, beta (nullable when linear) [n_tissue];
+ * relax->kappa1, kappa2 [n_tissue]; relax->d1, alpha1, d2, alpha2
+ * [N][n_tissue].  The result equals fw2_set_medium + fw2_set_relaxation with
+ * the tables gathered per cell; the C-PML still ramps per cell.  Replaces
+ * both calls.  EINVAL on an index >= n_tissue or bad sizes. */
+fw2_status fw2_set_medium_indexed(fw2_ctx *ctx, const uint8_t *tissue, int32_t n_tissue,
+                                  const float *c, const float *rho, const float *beta,
+                                  const fw2_relax_desc *relax, int32_t mem_space);
+
 /* Relaxation parameters (Sec. 3.2, Table 2 shape); required when N > 0.
  * The coefficient maps (b = exp(-(d/kappa + alpha) dt),
  * a = d (b - 1) / (kappa (d + kappa alpha)), Eqs. relaxation_a/b; the C-PML
@@ -169,6 +184,34 @@ fw2_status fw2_step(fw2_ctx *ctx, int64_t n_steps);
 
 /* Release every resource of the context (safe on NULL). */
 fw2_status fw2_destroy(fw2_ctx *ctx);
+
+/* ---- batches ---------------------------------------------------------- */
+
+/* Many 2D contexts advanced together: the transmit events of a full
+ * synthetic aperture sequence (appendix, abdominal wall imaging: one
+ * simulation per transmitting element) or the requests of a serving loop.
+ * Each context computes exactly what fw2_step computes for it alone; the
+ * batch runs one persistent launch per half step over a tile table of all
+ * contexts (grouped by mechanism count and map kind), one launch each for
+ * the sources and recordings of all contexts, and replays chunks of steps
+ * as a captured CUDA graph.  The first four batch steps try four launch
+ * configurations (persistent grid size x tile order) and keep the fastest;
+ * every configuration computes the same result. */
+typedef struct fw2_batch fw2_batch;
+/* Contexts are borrowed (they must outlive the batch), 2D, with medium set;
+ * their coefficient maps and sources are built here.  Re-create the batch
+ * after changing a context's sources or recording.  EUNSUPPORTED for 3D. */
+fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out);
+/* Advance every context by n_steps (each from its own step counter), on the
+ * batch's own stream after the contexts' streams have drained; asynchronous. */
+fw2_status fw2_batch_step(fw2_batch *b, int64_t n_steps);
+fw2_status fw2_batch_synchronize(fw2_batch *b);
+/* Tuned persistent grid (0 before tuning), tile order (0 context-major,
+ * 1 interleaved) and kernel launches (graph replays count their kernels once
+ * at capture). */
+fw2_status fw2_batch_info(fw2_batch *b, int32_t *grid, int32_t *order, int64_t *launches);
+const char *fw2_batch_last_error(const fw2_batch *b);
+fw2_status fw2_batch_destroy(fw2_batch *b);
 
 /* ---- helpers ---------------------------------------------------------- */
 

@@ -155,13 +155,26 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
     return out
 
 
+def to_bf16(x) -> np.ndarray:
+    """Round FP64 values to float32, then to bfloat16 (round to nearest even),
+    returned as FP64: the storage rounding of bf16 coefficient maps."""
+    f = np.ascontiguousarray(np.asarray(x, np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    finite = np.isfinite(f)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    r = np.where(finite, r, u.astype(np.uint32))
+    return r.view(np.float32).astype(np.float64)
+
+
 def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object]:
     """All coefficient arrays of the oracle step, FP64 (flat, x fastest).
 
     Keys: K, chi (or None), buoy[q], ik1[q], a1[q] (N, n), b1[q], ik2[q],
     a2[q], b2[q], dt, taps (g1..g4, g11).
     `round_to` = "f32" rounds every stored coefficient map to float32 first
-    (models coefficient maps kept in single precision).
+    (models coefficient maps kept in single precision); "bf16" rounds them to
+    bfloat16, with b stored as 1 - b (b = 1 - bf16(1 - b)) and the cell
+    density rounded before the face average (models bf16 maps).
     `window` = ((x0, x1), (y0, y1)[, (z0, z1)]) builds the coefficients of that
     sub-box of the grid only, with the boundary profiles and face densities of
     its global position.
@@ -178,11 +191,13 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
     # numpy slices of the window in the global arrays
     sl = tuple(slice(win[q][0], win[q][1]) for q in (2, 1, 0))
     def crop(a):
-        return np.asarray(a, np.float64).reshape(gshape)[sl]
-    c_full = np.asarray(prob.c, np.float64).reshape(gshape)
-    rho_full = np.asarray(prob.rho, np.float64).reshape(gshape)
-    c = c_full[sl]
-    rho = rho_full[sl]
+        return np.asarray(a).reshape(gshape)[sl].astype(np.float64)
+    rho_src = np.asarray(prob.rho).reshape(gshape)
+    c = crop(prob.c)
+    rho = crop(prob.rho)
+    # the face densities use the stored (possibly bf16) cell density; K and
+    # chi are built from the input density and rounded as maps afterwards
+    rho_face_src = to_bf16(rho) if round_to == "bf16" else rho
     N = prob.nrelax
     dt = float(prob.dt) if prob.dt and prob.dt > 0 else cfl_time_step(prob)
     K = rho * c * c
@@ -208,7 +223,7 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
     k2 = crop(prob.kappa2) if N else np.ones(wg)
     LT, LB = int(prob.pml_transition), int(prob.pml_bound)
     L = LT + LB
-    cp = float(prob.pml_cp) if prob.pml_cp and prob.pml_cp > 0 else float(c_full.max())
+    cp = float(prob.pml_cp) if prob.pml_cp and prob.pml_cp > 0 else float(np.asarray(prob.c).max())
     d_target = -(prob.pml_npow + 1.0) * cp * math.log(prob.pml_rc) / (2.0 * L * prob.h) if L > 0 else 0.0
     for q in range(nd):
         ax = axis_of[q]
@@ -219,8 +234,10 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
         else:
             idx_hi = np.minimum(idx_hi, shape[q] - 1)
         others = tuple(slice(None) if i == ax else s_ for i, s_ in enumerate(sl))
-        nb = np.take(rho_full[others], idx_hi, axis=ax)
-        out[f"buoy{q}"] = (1.0 / (0.5 * (rho + nb))).ravel()
+        nb = np.take(rho_src[others], idx_hi, axis=ax).astype(np.float64)
+        if round_to == "bf16":
+            nb = to_bf16(nb)
+        out[f"buoy{q}"] = (1.0 / (0.5 * (rho_face_src + nb))).ravel()
         out[f"ik1{q}"] = (1.0 / k1).ravel()
         out[f"ik2{q}"] = (1.0 / k2).ravel()
         a1 = np.zeros((N, n)); b1 = np.zeros((N, n)); a2 = np.zeros((N, n)); b2 = np.zeros((N, n))
@@ -230,8 +247,8 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
             bshape = [1, 1, 1]; bshape[ax] = wshape[q]
             depth = np.broadcast_to(depth1.reshape(bshape), wg)
             for nu in range(N):
-                d0 = np.asarray(getattr(prob, dname)[nu], np.float64).reshape(gshape)[sl]
-                al0 = np.asarray(getattr(prob, aname)[nu], np.float64).reshape(gshape)[sl]
+                d0 = crop(getattr(prob, dname)[nu])
+                al0 = crop(getattr(prob, aname)[nu])
                 d = boundary_profile(d0, depth, nu + 1, "d", LT, LB, prob.pml_npow, d_target, prob.pml_reading)
                 al = boundary_profile(al0, depth, nu + 1, "alpha", LT, LB, prob.pml_npow, d_target, prob.pml_reading)
                 a, b = relaxation_ab(d, al, kap, dt)
@@ -241,6 +258,16 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
         for k, v in list(out.items()):
             if isinstance(v, np.ndarray):
                 out[k] = v.astype(np.float32).astype(np.float64)
+    elif round_to == "bf16":
+        for k, v in list(out.items()):
+            if not isinstance(v, np.ndarray):
+                continue
+            if k.startswith("buoy"):
+                continue                       # computed in float32 from the rounded density
+            if k.startswith("b1") or k.startswith("b2"):
+                out[k] = 1.0 - to_bf16(1.0 - v)
+            else:
+                out[k] = to_bf16(v)
     elif round_to is not None:
         raise ValueError(round_to)
     return out

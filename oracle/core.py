@@ -200,7 +200,7 @@ class OracleSim:
         self.p[:] = self._crop(st["p"]).astype(np.float64).ravel()
         for q in range(len(self.v)):
             self.v[q][:] = self._crop(st["v" + names[q]]).astype(np.float64).ravel()
-            if N:
+            if N and ("psi1" + names[q]) in st:
                 self.psi1[q][:] = self._crop(np.asarray(st["psi1" + names[q]]).reshape((N,) + self.prob.grid_shape)).reshape(N, -1)
                 self.psi2[q][:] = self._crop(np.asarray(st["psi2" + names[q]]).reshape((N,) + self.prob.grid_shape)).reshape(N, -1)
 

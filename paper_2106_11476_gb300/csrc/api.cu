@@ -8,8 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "fw2.h"
-#include "fw2_prep.cuh"
+#include "ctx.h"
 
 using namespace fw2;
 
@@ -21,73 +20,6 @@ namespace fw2 {
 // error text of calls without a context (fw2_last_error(NULL))
 void set_global_error(const char *msg) { g_create_error = msg; }
 }  // namespace fw2
-
-namespace {
-
-struct HostSource {
-  int kind;
-  std::vector<long long> idx;   // flat dense cell index
-  std::vector<int> group;
-  std::vector<float> signal;    // [n_steps][n_groups]
-  long long n_groups = 0, n_steps = 0;
-};
-
-struct DevSource {
-  long long *tgt = nullptr;
-  int *off = nullptr;
-  int *col = nullptr;
-  int n_tgt = 0;
-};
-
-size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-
-}  // namespace
-
-struct fw2_ctx {
-  fw2_config cfg;
-  int nd = 2, N = 0, nx = 1, ny = 1, nz = 1, pitch = 4;
-  long long plane = 0, npts_alloc = 0, n_pts = 0;
-  cudaStream_t stream = nullptr;
-  std::string err = "no error";
-  // device memory
-  std::vector<void *> allocs;
-  long long dev_bytes = 0;
-  char *state = nullptr;
-  size_t state_bytes = 0;
-  float *p = nullptr, *v[3] = {nullptr, nullptr, nullptr};
-  float *psi1[3] = {nullptr, nullptr, nullptr}, *psi2[3] = {nullptr, nullptr, nullptr};
-  // raw inputs (device, dense)
-  float *raw_c = nullptr, *raw_rho = nullptr, *raw_beta = nullptr;
-  float *raw_k1 = nullptr, *raw_k2 = nullptr, *raw_d1 = nullptr, *raw_al1 = nullptr, *raw_d2 = nullptr,
-        *raw_al2 = nullptr;
-  bool medium_set = false, relax_set = false, finalized = false;
-  // coefficient maps
-  char *maps = nullptr;
-  StepParams P{};
-  int map_bf16 = 0;
-  double dt = 0.0, cmax_eff = 0.0, cmax = 0.0;
-  // sources
-  std::vector<HostSource> sources;
-  bool src_dirty = false;
-  DevSource dsrc[4];
-  float *d_signal = nullptr;
-  long long sig_steps = 0, sig_cols = 0;
-  // recording
-  long long *rec_cell = nullptr;
-  int *rec_off = nullptr;
-  int rec_groups = 0;
-  float *rec_out = nullptr;
-  long long rec_steps = 0;
-  // scratch words for scans
-  unsigned long long *d_scan = nullptr;
-  int *d_bad = nullptr;
-  unsigned int *d_absmax = nullptr;
-  long long step = 0, launches = 0;
-  // optional per-kernel event timing
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_vel, ev_prs;
-};
 
 namespace {
 
@@ -183,6 +115,8 @@ fw2_status finalize(fw2_ctx *c) {
   Q.c = c->raw_c; Q.rho = c->raw_rho; Q.beta = c->raw_beta;
   Q.k1 = c->raw_k1; Q.k2 = c->raw_k2; Q.d1 = c->raw_d1; Q.al1 = c->raw_al1; Q.d2 = c->raw_d2; Q.al2 = c->raw_al2;
   Q.nl_mode = cfg.nl_mode;
+  Q.tissue_in = c->map_kind == FW2_MAP_IDX_U8 ? c->raw_tissue : nullptr;
+  Q.n_tissue = c->n_tissue;
   // medium scan: c_max (high-frequency) and validity
   CK(c, cudaMemsetAsync(c->d_scan, 0, 2 * sizeof(unsigned long long), c->stream));
   CK(c, cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream));
@@ -210,9 +144,11 @@ fw2_status finalize(fw2_ctx *c) {
   Q.LT = cfg.pml_transition; Q.LB = cfg.pml_bound; Q.reading = cfg.pml_reading; Q.npow = cfg.pml_npow;
   const double cp = cfg.pml_cp > 0.0 ? cfg.pml_cp : cm;
   Q.d_target = L > 0 ? -(cfg.pml_npow + 1.0) * cp * std::log(cfg.pml_rc) / (2.0 * L * cfg.h) : 0.0;
-  // map allocation: 5 cell maps + 4N interior + strips
-  const size_t es = c->map_bf16 ? 2 : 4;
-  const size_t cell_bytes = align256(es * (size_t)c->npts_alloc);
+  // map allocation: 5 cell maps + 4N interior + strips (dense forms), or the
+  // per-tissue table + the pitched uint8 index + strips (index form)
+  const bool indexed = c->map_kind == FW2_MAP_IDX_U8;
+  const size_t es = c->map_kind == FW2_MAP_BF16 ? 2 : 4;
+  const size_t cell_bytes = indexed ? 0 : align256(es * (size_t)c->npts_alloc);
   long long strip_nu[3] = {0, 0, 0};
   const bool strips = L > 0 && c->N > 0;
   if (strips) {
@@ -220,7 +156,9 @@ fw2_status finalize(fw2_ctx *c) {
     strip_nu[1] = (long long)c->nz * 2 * L * c->pitch;
     if (c->nd == 3) strip_nu[2] = (long long)2 * L * c->ny * c->pitch;
   }
-  size_t total = 5 * cell_bytes + 4 * (size_t)c->N * cell_bytes;
+  const size_t table_bytes = indexed ? align256(sizeof(float) * kTableFields * kTissues) : 0;
+  const size_t index_bytes = indexed ? align256((size_t)c->npts_alloc) : 0;
+  size_t total = 5 * cell_bytes + 4 * (size_t)c->N * cell_bytes + table_bytes + index_bytes;
   size_t strip_bytes[3];
   for (int q = 0; q < 3; ++q) {
     strip_bytes[q] = align256(es * (size_t)(strip_nu[q] * (c->N ? c->N : 1)));
@@ -237,6 +175,8 @@ fw2_status finalize(fw2_ctx *c) {
   CK(c, cudaMemsetAsync(c->maps, 0, total, c->stream));
   char *cur = c->maps;
   auto take = [&](size_t b) { char *r = cur; cur += b; return (void *)r; };
+  Q.table_out = indexed ? (float *)take(table_bytes) : nullptr;
+  Q.tissue_out = indexed ? (unsigned char *)take(index_bytes) : nullptr;
   Q.K = take(cell_bytes); Q.rho_o = take(cell_bytes); Q.chi = take(cell_bytes);
   Q.ik1 = take(cell_bytes); Q.ik2 = take(cell_bytes);
   const size_t iso = (size_t)c->N * cell_bytes;
@@ -248,8 +188,8 @@ fw2_status finalize(fw2_ctx *c) {
       Q.sa2[q] = take(strip_bytes[q]); Q.sb2[q] = take(strip_bytes[q]);
     }
   }
-  CK(c, launch_prep(Q, c->map_bf16, c->stream));
-  c->launches += 1 + (strips ? c->nd : 0);
+  CK(c, launch_prep(Q, c->map_kind, c->stream));
+  c->launches += (indexed ? 2 : 1) + (strips ? c->nd : 0);
   CK(c, cudaStreamSynchronize(c->stream));
   // raw inputs are no longer needed
   float **raws[] = {&c->raw_c, &c->raw_rho, &c->raw_beta, &c->raw_k1, &c->raw_k2,
@@ -258,6 +198,8 @@ fw2_status finalize(fw2_ctx *c) {
     dfree(c, *r);
     *r = nullptr;
   }
+  dfree(c, c->raw_tissue);
+  c->raw_tissue = nullptr;
   c->medium_set = c->relax_set = false;
   // step parameters
   StepParams &P = c->P;
@@ -281,6 +223,8 @@ fw2_status finalize(fw2_ctx *c) {
   P.p = c->p;
   P.K = Q.K; P.rho = Q.rho_o; P.chi = Q.chi; P.ik1 = Q.ik1; P.ik2 = Q.ik2;
   P.a1 = Q.a1; P.b1 = Q.b1; P.a2 = Q.a2; P.b2 = Q.b2;
+  P.tissue = Q.tissue_out;
+  P.table = Q.table_out;
   c->finalized = true;
   return FW2_OK;
 }
@@ -393,6 +337,15 @@ float *field_ptr(fw2_ctx *c, int field, int *count) {
 
 }  // namespace
 
+namespace fw2 {
+fw2_status ctx_prepare(fw2_ctx *c) {
+  fw2_status st = finalize(c);
+  if (st != FW2_OK) return st;
+  return build_sources(c);
+}
+fw2_status ctx_fail(fw2_ctx *c, fw2_status s, const char *msg) { return fail(c, s, "%s", msg); }
+}  // namespace fw2
+
 extern "C" {
 
 int32_t fw2_abi_version(void) { return 1; }
@@ -440,8 +393,10 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
     if (!(cfg.pml_npow >= 0.0)) return fail(nullptr, FW2_EINVAL, "pml_npow must be >= 0");
   }
   if (cfg.pml_reading < FW2_PML_A || cfg.pml_reading > FW2_PML_C) return fail(nullptr, FW2_EINVAL, "bad pml_reading");
-  if (cfg.map_precision != FW2_MAP_F32 && cfg.map_precision != FW2_MAP_BF16)
+  if (cfg.map_precision < FW2_MAP_F32 || cfg.map_precision > FW2_MAP_IDX_U8)
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
+  if (cfg.map_precision == FW2_MAP_IDX_U8 && cfg.ndim != 2)
+    return fail(nullptr, FW2_EUNSUPPORTED, "tissue-index maps are implemented for 2D grids");
   if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_WESTERVELT) return fail(nullptr, FW2_EINVAL, "bad nl_mode");
   if (cfg.mem_alignment != FW2_MEM_CENTRED && cfg.mem_alignment != FW2_MEM_ENDPOINT)
     return fail(nullptr, FW2_EINVAL, "bad mem_alignment");
@@ -484,7 +439,7 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
   c->npts_alloc = (c->plane * c->nz + 127) / 128 * 128;
   c->n_pts = (long long)c->nx * c->ny * c->nz;
   c->stream = (cudaStream_t)cfg.stream;
-  c->map_bf16 = cfg.map_precision == FW2_MAP_BF16;
+  c->map_kind = cfg.map_precision;
   // state: p, v_q, psi1_q[N], psi2_q[N]
   const size_t arr = align256(sizeof(float) * (size_t)c->npts_alloc);
   const int n_arrays = 1 + c->nd + 2 * c->nd * c->N;
@@ -529,6 +484,7 @@ fw2_status fw2_destroy(fw2_ctx *c) {
 
 fw2_status fw2_set_medium(fw2_ctx *c, const float *cc, const float *rho, const float *beta, int32_t mem_space) {
   if (!c) return FW2_EINVAL;
+  if (c->map_kind == FW2_MAP_IDX_U8) return fail(c, FW2_EINVAL, "tissue-index contexts take fw2_set_medium_indexed");
   if (!cc || !rho) return fail(c, FW2_EINVAL, "c and rho are required");
   if (c->cfg.nl_mode != FW2_NL_OFF && !beta) return fail(c, FW2_EINVAL, "beta is required when nl_mode != OFF");
   if (mem_space != FW2_MEM_HOST && mem_space != FW2_MEM_DEVICE) return fail(c, FW2_EINVAL, "bad mem_space");
@@ -550,6 +506,7 @@ fw2_status fw2_set_medium(fw2_ctx *c, const float *cc, const float *rho, const f
 
 fw2_status fw2_set_relaxation(fw2_ctx *c, const fw2_relax_desc *d) {
   if (!c) return FW2_EINVAL;
+  if (c->map_kind == FW2_MAP_IDX_U8) return fail(c, FW2_EINVAL, "tissue-index contexts take fw2_set_medium_indexed");
   if (!d) return fail(c, FW2_EINVAL, "relaxation descriptor is null");
   if (c->N == 0) return fail(c, FW2_EINVAL, "n_relax is 0: no relaxation parameters to set");
   if (!d->kappa1 || !d->kappa2 || !d->d1 || !d->alpha1 || !d->d2 || !d->alpha2)
@@ -564,6 +521,56 @@ fw2_status fw2_set_relaxation(fw2_ctx *c, const fw2_relax_desc *d) {
     if (!*dst[i]) { if ((st = dalloc(c, sz[i], &m)) != FW2_OK) return st; *dst[i] = (float *)m; }
     if ((st = copy_in(c, *dst[i], src[i], sz[i], d->mem_space)) != FW2_OK) return st;
   }
+  c->relax_set = true;
+  c->finalized = false;
+  return FW2_OK;
+}
+
+fw2_status fw2_set_medium_indexed(fw2_ctx *c, const uint8_t *tissue, int32_t n_tissue, const float *cc,
+                                  const float *rho, const float *beta, const fw2_relax_desc *relax,
+                                  int32_t mem_space) {
+  if (!c) return FW2_EINVAL;
+  if (c->map_kind != FW2_MAP_IDX_U8) return fail(c, FW2_EINVAL, "fw2_set_medium_indexed needs map_precision FW2_MAP_IDX_U8");
+  if (!tissue || !cc || !rho) return fail(c, FW2_EINVAL, "tissue, c and rho are required");
+  if (n_tissue < 1 || n_tissue > kTissues) return fail(c, FW2_EINVAL, "n_tissue = %d outside [1, 256]", n_tissue);
+  if (c->cfg.nl_mode != FW2_NL_OFF && !beta) return fail(c, FW2_EINVAL, "beta is required when nl_mode != OFF");
+  if (c->N > 0 && (!relax || !relax->kappa1 || !relax->kappa2 || !relax->d1 || !relax->alpha1 || !relax->d2 ||
+                   !relax->alpha2))
+    return fail(c, FW2_EINVAL, "every relaxation table is required when n_relax > 0");
+  if (mem_space != FW2_MEM_HOST && mem_space != FW2_MEM_DEVICE) return fail(c, FW2_EINVAL, "bad mem_space");
+  // drop any earlier medium
+  float **raws[] = {&c->raw_c, &c->raw_rho, &c->raw_beta, &c->raw_k1, &c->raw_k2,
+                    &c->raw_d1, &c->raw_al1, &c->raw_d2, &c->raw_al2};
+  for (float **r : raws) {
+    dfree(c, *r);
+    *r = nullptr;
+  }
+  dfree(c, c->raw_tissue);
+  c->raw_tissue = nullptr;
+  void *m;
+  fw2_status st;
+  if ((st = dalloc(c, (size_t)c->n_pts, &m)) != FW2_OK) return st;
+  c->raw_tissue = (unsigned char *)m;
+  if ((st = copy_in(c, c->raw_tissue, tissue, (size_t)c->n_pts, mem_space)) != FW2_OK) return st;
+  const size_t bt = sizeof(float) * (size_t)n_tissue, btN = bt * c->N;
+  struct Item { float **dst; const float *src; size_t bytes; };
+  std::vector<Item> items = {{&c->raw_c, cc, bt}, {&c->raw_rho, rho, bt}};
+  if (c->cfg.nl_mode != FW2_NL_OFF) items.push_back({&c->raw_beta, beta, bt});
+  if (c->N > 0) {
+    items.push_back({&c->raw_k1, relax->kappa1, bt});
+    items.push_back({&c->raw_k2, relax->kappa2, bt});
+    items.push_back({&c->raw_d1, relax->d1, btN});
+    items.push_back({&c->raw_al1, relax->alpha1, btN});
+    items.push_back({&c->raw_d2, relax->d2, btN});
+    items.push_back({&c->raw_al2, relax->alpha2, btN});
+  }
+  for (const Item &it : items) {
+    if ((st = dalloc(c, it.bytes, &m)) != FW2_OK) return st;
+    *it.dst = (float *)m;
+    if ((st = copy_in(c, *it.dst, it.src, it.bytes, mem_space)) != FW2_OK) return st;
+  }
+  c->n_tissue = n_tissue;
+  c->medium_set = true;
   c->relax_set = true;
   c->finalized = false;
   return FW2_OK;
@@ -661,7 +668,7 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
       ev = {take_event(c), take_event(c)};
       CK(c, cudaEventRecord(ev.first, c->stream));
     }
-    CK(c, c->nd == 2 ? launch_vel2d(P, c->map_bf16, c->stream) : launch_vel3d(P, c->map_bf16, c->stream));
+    CK(c, c->nd == 2 ? launch_vel2d(P, c->map_kind, c->stream) : launch_vel3d(P, c->map_kind, c->stream));
     c->launches++;
     if (c->profiling) {
       CK(c, cudaEventRecord(ev.second, c->stream));
@@ -677,7 +684,7 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
       }
     }
     if (c->profiling) CK(c, cudaEventRecord(ev.first, c->stream));
-    CK(c, c->nd == 2 ? launch_prs2d(P, c->map_bf16, c->stream) : launch_prs3d(P, c->map_bf16, c->stream));
+    CK(c, c->nd == 2 ? launch_prs2d(P, c->map_kind, c->stream) : launch_prs3d(P, c->map_kind, c->stream));
     c->launches++;
     if (c->profiling) {
       CK(c, cudaEventRecord(ev.second, c->stream));

@@ -1,0 +1,384 @@
+// Batched stepping of many 2D contexts (transmit events, requests of a
+// serving loop) in persistent launches, with a CUDA-graph-captured step loop.
+//
+// Per time step, for every group of contexts sharing the mechanism count and
+// the map kind: one persistent velocity launch over the group's tile table,
+// one launch injecting the velocity sources of all contexts, one persistent
+// pressure launch, one launch for the pressure sources, one for the
+// recordings, and a tick of the per-context step counters kept on the
+// device.  Since every per-step index comes from those counters, a chunk of
+// steps is captured once as a CUDA graph and replayed.  Each context computes
+// exactly what fw2_step computes for it alone (same tile arithmetic).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace fw2;
+
+namespace {
+
+struct BatchCtx {
+  float *p;
+  float *v[3];
+  const long long *tgt[4];
+  const int *off[4];
+  const int *col[4];
+  const float *signal;
+  long long sig_cols, sig_steps;
+  const long long *rec_cell;
+  const int *rec_off;
+  float *rec_out;
+  long long rec_steps;
+  int rec_groups;
+};
+
+// context of flat work item t, from the per-context prefix offsets
+__device__ __forceinline__ int ctx_of(const int *prefix, int n_ctx, int t) {
+  int lo = 0, hi = n_ctx;  // prefix[lo] <= t < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void batch_inject_kernel(const BatchCtx *C, int n_ctx, const int *prefix, int total, int kind,
+                                    const long long *steps) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int k = ctx_of(prefix, n_ctx, t);
+  const BatchCtx &c = C[k];
+  const long long n = steps[k];
+  if (n >= c.sig_steps) return;
+  const int u = t - prefix[k];
+  const float *row = c.signal + n * c.sig_cols;
+  float s = 0.f;
+  for (int e = c.off[kind][u]; e < c.off[kind][u + 1]; ++e) s += __ldg(row + c.col[kind][e]);
+  float *field = kind == 0 ? c.p : c.v[kind - 1];
+  field[c.tgt[kind][u]] += s;
+}
+
+__global__ void batch_record_kernel(const BatchCtx *C, int n_ctx, const int *prefix, int total,
+                                    const long long *steps) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int k = ctx_of(prefix, n_ctx, t);
+  const BatchCtx &c = C[k];
+  const long long n = steps[k];
+  if (n >= c.rec_steps) return;
+  const int g = t - prefix[k];
+  const int b = c.rec_off[g], e = c.rec_off[g + 1];
+  float s = 0.f;
+  for (int i = b; i < e; ++i) s += c.p[c.rec_cell[i]];
+  c.rec_out[n * c.rec_groups + g] = e > b ? s / (float)(e - b) : 0.f;
+}
+
+__global__ void batch_tick_kernel(long long *steps, int n_ctx) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_ctx) steps[t] += 1;
+}
+
+struct Group {
+  int n_relax, map_kind;
+  std::vector<int> members;
+  StepParams *d_params = nullptr;
+  int4 *d_tiles[2] = {nullptr, nullptr};  // context-major, interleaved
+  int n_tiles = 0;
+};
+
+}  // namespace
+
+struct fw2_batch {
+  std::vector<fw2_ctx *> ctxs;
+  std::vector<Group> groups;
+  cudaStream_t stream = nullptr;
+  BatchCtx *d_ctx = nullptr;
+  long long *d_step = nullptr;
+  int *d_prefix[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // source kinds 0..3, record
+  int total[5] = {0, 0, 0, 0, 0};
+  std::vector<void *> allocs;
+  std::string err = "no error";
+  // launch configuration: persistent grid and tile order, tuned online
+  int grid = 0, order = 0;
+  bool tuned = false;
+  int trial = 0;
+  std::vector<float> trial_ms;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  long long launches = 0;
+};
+
+namespace {
+
+const int kCandidates[4][2] = {{152 * 2, 0}, {152 * 2, 1}, {152, 0}, {152 * 4, 1}};
+
+fw2_status bfail(fw2_batch *b, fw2_status s, const char *what, cudaError_t e = cudaSuccess) {
+  char buf[512];
+  if (e != cudaSuccess) snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  else snprintf(buf, sizeof buf, "%s", what);
+  b->err = buf;
+  return s;
+}
+
+#define BCK(b, call)                                              \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return bfail(b, FW2_ECUDA, #call, e_); \
+  } while (0)
+
+template <typename T>
+fw2_status bupload(fw2_batch *b, const std::vector<T> &v, T **out) {
+  void *m = nullptr;
+  const size_t bytes = std::max<size_t>(sizeof(T) * v.size(), 16);
+  cudaError_t e = cudaMalloc(&m, bytes);
+  if (e != cudaSuccess) return bfail(b, FW2_ENOMEM, "batch allocation", e);
+  b->allocs.push_back(m);
+  if (!v.empty()) {
+    e = cudaMemcpy(m, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bfail(b, FW2_ECUDA, "batch upload", e);
+  }
+  *out = static_cast<T *>(m);
+  return FW2_OK;
+}
+
+// one time step of every context (launch sequence of the file header)
+fw2_status enqueue_step(fw2_batch *b, int grid, int order) {
+  const int n_ctx = (int)b->ctxs.size();
+  for (int half = 0; half < 2; ++half) {
+    const bool vel = half == 0;
+    for (Group &g : b->groups) {
+      BCK(b, launch_batched2d(vel, g.d_params, g.d_tiles[order], g.n_tiles, g.n_relax, g.map_kind, grid, b->stream));
+      b->launches++;
+    }
+    const int kinds[2][2] = {{1, 2}, {0, -1}};
+    for (int kk = 0; kk < 2; ++kk) {
+      const int kind = kinds[half][kk];
+      if (kind < 0 || b->total[kind] == 0) continue;
+      batch_inject_kernel<<<(b->total[kind] + 127) / 128, 128, 0, b->stream>>>(b->d_ctx, n_ctx, b->d_prefix[kind],
+                                                                              b->total[kind], kind, b->d_step);
+      BCK(b, cudaGetLastError());
+      b->launches++;
+    }
+  }
+  if (b->total[4] > 0) {
+    batch_record_kernel<<<(b->total[4] + 127) / 128, 128, 0, b->stream>>>(b->d_ctx, n_ctx, b->d_prefix[4],
+                                                                         b->total[4], b->d_step);
+    BCK(b, cudaGetLastError());
+    b->launches++;
+  }
+  batch_tick_kernel<<<(n_ctx + 127) / 128, 128, 0, b->stream>>>(b->d_step, n_ctx);
+  BCK(b, cudaGetLastError());
+  b->launches++;
+  return FW2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out) {
+  if (!out) return FW2_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n_ctx < 1) return FW2_EINVAL;
+  fw2_batch *b = new (std::nothrow) fw2_batch();
+  if (!b) return FW2_ENOMEM;
+  for (int i = 0; i < n_ctx; ++i) {
+    fw2_ctx *c = ctxs[i];
+    if (!c || c->nd != 2) {
+      fw2_status st = c ? ctx_fail(c, FW2_EUNSUPPORTED, "batches hold 2D contexts") : FW2_EINVAL;
+      delete b;
+      return st;
+    }
+    fw2_status st = ctx_prepare(c);
+    if (st != FW2_OK) {
+      delete b;
+      return st;
+    }
+    b->ctxs.push_back(c);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return FW2_ECUDA;
+  }
+  // groups by (mechanism count, map kind)
+  for (int i = 0; i < n_ctx; ++i) {
+    fw2_ctx *c = b->ctxs[i];
+    auto it = std::find_if(b->groups.begin(), b->groups.end(),
+                           [&](const Group &g) { return g.n_relax == c->N && g.map_kind == c->map_kind; });
+    if (it == b->groups.end()) {
+      b->groups.push_back(Group{c->N, c->map_kind, {}});
+      it = b->groups.end() - 1;
+    }
+    it->members.push_back(i);
+  }
+  fw2_status st = FW2_OK;
+  for (Group &g : b->groups) {
+    std::vector<StepParams> params;
+    std::vector<std::vector<int4>> per;
+    for (int m = 0; m < (int)g.members.size(); ++m) {
+      fw2_ctx *c = b->ctxs[g.members[m]];
+      params.push_back(c->P);
+      std::vector<int4> t;
+      for (int y0 = 0; y0 < c->ny; y0 += kTY)
+        for (int x0 = 0; x0 < c->nx; x0 += kTX) t.push_back(make_int4(m, x0, y0, 0));
+      per.push_back(t);
+    }
+    std::vector<int4> major, inter;
+    for (auto &t : per) major.insert(major.end(), t.begin(), t.end());
+    // interleaved: tiles of the contexts in turn
+    size_t longest = 0;
+    for (auto &t : per) longest = std::max(longest, t.size());
+    for (size_t k = 0; k < longest; ++k)
+      for (auto &t : per)
+        if (k < t.size()) inter.push_back(t[k]);
+    g.n_tiles = (int)major.size();
+    if ((st = bupload(b, params, &g.d_params)) != FW2_OK) break;
+    if ((st = bupload(b, major, &g.d_tiles[0])) != FW2_OK) break;
+    if ((st = bupload(b, inter, &g.d_tiles[1])) != FW2_OK) break;
+  }
+  if (st == FW2_OK) {
+    std::vector<BatchCtx> bc;
+    std::vector<int> prefix[5];
+    for (int k = 0; k < 5; ++k) prefix[k].push_back(0);
+    for (fw2_ctx *c : b->ctxs) {
+      BatchCtx x{};
+      x.p = c->p;
+      for (int q = 0; q < 3; ++q) x.v[q] = c->v[q];
+      for (int k = 0; k < 4; ++k) {
+        x.tgt[k] = c->dsrc[k].tgt;
+        x.off[k] = c->dsrc[k].off;
+        x.col[k] = c->dsrc[k].col;
+        prefix[k].push_back(prefix[k].back() + c->dsrc[k].n_tgt);
+      }
+      x.signal = c->d_signal;
+      x.sig_cols = c->sig_cols;
+      x.sig_steps = c->sig_steps;
+      x.rec_cell = c->rec_cell;
+      x.rec_off = c->rec_off;
+      x.rec_out = c->rec_out;
+      x.rec_steps = c->rec_steps;
+      x.rec_groups = c->rec_groups;
+      prefix[4].push_back(prefix[4].back() + c->rec_groups);
+      bc.push_back(x);
+    }
+    st = bupload(b, bc, &b->d_ctx);
+    for (int k = 0; k < 5 && st == FW2_OK; ++k) {
+      b->total[k] = prefix[k].back();
+      st = bupload(b, prefix[k], &b->d_prefix[k]);
+    }
+    std::vector<long long> steps(b->ctxs.size(), 0);
+    if (st == FW2_OK) st = bupload(b, steps, &b->d_step);
+  }
+  if (st != FW2_OK) {
+    for (void *m : b->allocs) cudaFree(m);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return FW2_OK;
+}
+
+fw2_status fw2_batch_step(fw2_batch *b, int64_t n_steps) {
+  if (!b) return FW2_EINVAL;
+  if (n_steps < 0) return bfail(b, FW2_EINVAL, "negative step count");
+  if (n_steps == 0) return FW2_OK;
+  // work already queued on the contexts' own streams comes first
+  std::vector<long long> steps;
+  for (fw2_ctx *c : b->ctxs) {
+    BCK(b, cudaStreamSynchronize(c->stream));
+    steps.push_back(c->step);
+  }
+  BCK(b, cudaMemcpyAsync(b->d_step, steps.data(), sizeof(long long) * steps.size(), cudaMemcpyHostToDevice,
+                         b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  int64_t done = 0;
+  // online tuning: the first steps try each launch configuration once (every
+  // configuration computes the same result) and keep the fastest
+  while (!b->tuned && done < n_steps) {
+    const int k = b->trial;
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    BCK(b, cudaEventRecord(e0, b->stream));
+    fw2_status st = enqueue_step(b, kCandidates[k][0], kCandidates[k][1]);
+    if (st != FW2_OK) return st;
+    BCK(b, cudaEventRecord(e1, b->stream));
+    BCK(b, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->trial_ms.push_back(ms);
+    ++done;
+    if (++b->trial == 4) {
+      const int best = (int)(std::min_element(b->trial_ms.begin(), b->trial_ms.end()) - b->trial_ms.begin());
+      b->grid = kCandidates[best][0];
+      b->order = kCandidates[best][1];
+      b->tuned = true;
+    }
+  }
+  const int64_t rest = n_steps - done;
+  if (rest > 0) {
+    const int chunk = (int)std::min<int64_t>(rest, 64);
+    if (!b->graph || b->graph_steps != chunk) {
+      if (b->graph) cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+      cudaGraph_t g;
+      BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      fw2_status st = FW2_OK;
+      for (int s = 0; s < chunk && st == FW2_OK; ++s) st = enqueue_step(b, b->grid, b->order);
+      cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+      if (st != FW2_OK) return st;
+      BCK(b, ec);
+      ec = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      BCK(b, ec);
+      b->graph_steps = chunk;
+    }
+    int64_t left = rest;
+    while (left >= chunk) {
+      BCK(b, cudaGraphLaunch(b->graph, b->stream));
+      left -= chunk;
+    }
+    for (int64_t s = 0; s < left; ++s) {
+      fw2_status st = enqueue_step(b, b->grid, b->order);
+      if (st != FW2_OK) return st;
+    }
+  }
+  for (fw2_ctx *c : b->ctxs) c->step += n_steps;
+  return FW2_OK;
+}
+
+fw2_status fw2_batch_synchronize(fw2_batch *b) {
+  if (!b) return FW2_EINVAL;
+  BCK(b, cudaStreamSynchronize(b->stream));
+  return FW2_OK;
+}
+
+fw2_status fw2_batch_info(fw2_batch *b, int32_t *grid, int32_t *order, int64_t *launches) {
+  if (!b) return FW2_EINVAL;
+  if (grid) *grid = b->tuned ? b->grid : 0;
+  if (order) *order = b->tuned ? b->order : -1;
+  if (launches) *launches = b->launches;
+  return FW2_OK;
+}
+
+const char *fw2_batch_last_error(const fw2_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+fw2_status fw2_batch_destroy(fw2_batch *b) {
+  if (!b) return FW2_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void *m : b->allocs) cudaFree(m);
+  cudaStreamDestroy(b->stream);
+  delete b;
+  return FW2_OK;
+}
+
+}  // extern "C"

@@ -23,7 +23,7 @@ __device__ __forceinline__ void coef4(const StepParams &P, int nu, long long c, 
     const bool any = L > 0 && (i0 < L || i0 + 3 >= P.nx - L);
     if (!any) {
       a = ldmap4(ia, iso);
-      b = ldmap4(ib, iso);
+      b = ldb4(ib, iso);
       return;
     }
     const long long row = (long long)nu * P.strip_nu[0] + ((long long)k * P.ny + j) * (2 * L);
@@ -35,10 +35,10 @@ __device__ __forceinline__ void coef4(const StepParams &P, int nu, long long c, 
         const int sc = strip_coord(x, P.nx, L);
         if (sc >= 0) {
           av = ldmap(sa, row + sc);
-          bv = ldmap(sb, row + sc);
+          bv = ldb(sb, row + sc);
         } else {
           av = ldmap(ia, iso + e);
-          bv = ldmap(ib, iso + e);
+          bv = ldb(ib, iso + e);
         }
       }
       el(a, e) = av;
@@ -48,13 +48,13 @@ __device__ __forceinline__ void coef4(const StepParams &P, int nu, long long c, 
     const int sc = Q == 1 ? strip_coord(j, P.ny, L) : strip_coord(k, P.nz, L);
     if (sc < 0) {
       a = ldmap4(ia, iso);
-      b = ldmap4(ib, iso);
+      b = ldb4(ib, iso);
     } else {
       const long long off =
           Q == 1 ? (long long)nu * P.strip_nu[1] + ((long long)k * (2 * L) + sc) * P.pitch + i0
                  : (long long)nu * P.strip_nu[2] + ((long long)sc * P.ny + j) * P.pitch + i0;
       a = ldmap4(sa, off);
-      b = ldmap4(sb, off);
+      b = ldb4(sb, off);
     }
   }
 }

@@ -1,0 +1,88 @@
+// Internal definition of a context (shared by api.cu and batch.cu).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "fw2.h"
+#include "fw2_prep.cuh"
+#include "maps.cuh"
+
+namespace fw2 {
+
+struct HostSource {
+  int kind;
+  std::vector<long long> idx;   // flat dense cell index
+  std::vector<int> group;
+  std::vector<float> signal;    // [n_steps][n_groups]
+  long long n_groups = 0, n_steps = 0;
+};
+
+struct DevSource {
+  long long *tgt = nullptr;
+  int *off = nullptr;
+  int *col = nullptr;
+  int n_tgt = 0;
+};
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace fw2
+
+struct fw2_ctx {
+  using HostSource = fw2::HostSource;
+  using DevSource = fw2::DevSource;
+  using StepParams = fw2::StepParams;
+  fw2_config cfg;
+  int nd = 2, N = 0, nx = 1, ny = 1, nz = 1, pitch = 4;
+  long long plane = 0, npts_alloc = 0, n_pts = 0;
+  cudaStream_t stream = nullptr;
+  std::string err = "no error";
+  // device memory
+  std::vector<void *> allocs;
+  long long dev_bytes = 0;
+  char *state = nullptr;
+  size_t state_bytes = 0;
+  float *p = nullptr, *v[3] = {nullptr, nullptr, nullptr};
+  float *psi1[3] = {nullptr, nullptr, nullptr}, *psi2[3] = {nullptr, nullptr, nullptr};
+  // raw inputs (device, dense)
+  float *raw_c = nullptr, *raw_rho = nullptr, *raw_beta = nullptr;
+  float *raw_k1 = nullptr, *raw_k2 = nullptr, *raw_d1 = nullptr, *raw_al1 = nullptr, *raw_d2 = nullptr,
+        *raw_al2 = nullptr;
+  unsigned char *raw_tissue = nullptr;  // tissue-index form
+  int n_tissue = 0;
+  bool medium_set = false, relax_set = false, finalized = false;
+  // coefficient maps
+  char *maps = nullptr;
+  StepParams P{};
+  int map_kind = 0;  // FW2_MAP_*
+  double dt = 0.0, cmax_eff = 0.0, cmax = 0.0;
+  // sources
+  std::vector<HostSource> sources;
+  bool src_dirty = false;
+  DevSource dsrc[4];
+  float *d_signal = nullptr;
+  long long sig_steps = 0, sig_cols = 0;
+  // recording
+  long long *rec_cell = nullptr;
+  int *rec_off = nullptr;
+  int rec_groups = 0;
+  float *rec_out = nullptr;
+  long long rec_steps = 0;
+  // scratch words for scans
+  unsigned long long *d_scan = nullptr;
+  int *d_bad = nullptr;
+  unsigned int *d_absmax = nullptr;
+  long long step = 0, launches = 0;
+  // optional per-kernel event timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_vel, ev_prs;
+};
+
+
+namespace fw2 {
+// finalize the coefficient maps and upload pending sources (status; the
+// message goes to the context)
+fw2_status ctx_prepare(fw2_ctx *c);
+fw2_status ctx_fail(fw2_ctx *c, fw2_status s, const char *msg);
+}  // namespace fw2

@@ -45,6 +45,10 @@ struct StepParams {
   const void *a1, *b1, *a2, *b2;          // interior [N][npts_alloc]
   const void *sa1[3], *sb1[3], *sa2[3], *sb2[3];  // strips
   long long strip_nu[3]; // elements between mechanisms in a strip array
+  // tissue-index form: uint8 index per cell and per-tissue tables
+  // ([field][256] floats, field order of maps.cuh)
+  const unsigned char *tissue;
+  const float *table;
 };
 
 // ---------------------------------------------------------------- loads ---
@@ -62,6 +66,16 @@ __device__ __forceinline__ float4 ldmap4(const __nv_bfloat16 *p, long long i) {
   float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
   return make_float4(a.x, a.y, b.x, b.y);
 }
+// Decay factors b of the recursion: float maps hold b, bf16 maps hold 1 - b
+// (bf16 cannot resolve b close to 1, e.g. 0.9999 would round to 1.0).
+__device__ __forceinline__ float4 ldb4(const float *p, long long i) { return ldmap4(p, i); }
+__device__ __forceinline__ float4 ldb4(const __nv_bfloat16 *p, long long i) {
+  const float4 v = ldmap4(p, i);
+  return make_float4(1.f - v.x, 1.f - v.y, 1.f - v.z, 1.f - v.w);
+}
+__device__ __forceinline__ float ldb(const float *p, long long i) { return ldmap(p, i); }
+__device__ __forceinline__ float ldb(const __nv_bfloat16 *p, long long i) { return 1.f - ldmap(p, i); }
+
 // streaming state loads/stores: read once, write once per step
 __device__ __forceinline__ float4 ld_state4(const float *p, long long i) {
   return __ldcs(reinterpret_cast<const float4 *>(p + i));
@@ -92,8 +106,13 @@ constexpr int kTX = 128;
 constexpr int kTY = 16;
 constexpr int kBY = 8;
 
-cudaError_t launch_vel2d(const StepParams &P, int map_bf16, cudaStream_t s);
-cudaError_t launch_prs2d(const StepParams &P, int map_bf16, cudaStream_t s);
+// map_kind: 0 float maps, 1 bf16 maps, 2 uint8 tissue index + tables
+cudaError_t launch_vel2d(const StepParams &P, int map_kind, cudaStream_t s);
+cudaError_t launch_prs2d(const StepParams &P, int map_kind, cudaStream_t s);
+// persistent batched 2D half step over a tile table {ctx, x0, y0, -} of
+// several contexts sharing N and the map kind (vel: velocity, else pressure)
+cudaError_t launch_batched2d(bool vel, const StepParams *Ps, const int4 *tiles, int n_tiles, int n_relax,
+                             int map_kind, int grid, cudaStream_t s);
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
 

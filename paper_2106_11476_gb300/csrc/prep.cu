@@ -15,14 +15,28 @@
 // The profile of a face is evaluated at its exact staggered coordinate; the
 // relaxation parameters of a face are those of its lower-index cell.
 #include "fw2_prep.cuh"
+#include "maps.cuh"
 
 namespace fw2 {
 
 namespace {
 
+// raw parameter of cell t (dense inputs) or of its tissue (index form)
+__device__ __forceinline__ long long src_of(const PrepParams &Q, long long t) {
+  return Q.tissue_in ? (long long)Q.tissue_in[t] : t;
+}
+__device__ __forceinline__ long long n_src(const PrepParams &Q) {
+  return Q.tissue_in ? (long long)Q.n_tissue : (long long)Q.nx * Q.ny * Q.nz;
+}
+
 __device__ __forceinline__ void store(float *p, long long i, double v) { p[i] = (float)v; }
 __device__ __forceinline__ void store(__nv_bfloat16 *p, long long i, double v) {
   p[i] = __float2bfloat16_rn((float)v);
+}
+// decay factor b: float maps hold b, bf16 maps hold 1 - b
+__device__ __forceinline__ void store_b(float *p, long long i, double b) { p[i] = (float)b; }
+__device__ __forceinline__ void store_b(__nv_bfloat16 *p, long long i, double b) {
+  p[i] = __float2bfloat16_rn((float)(1.0 - b));
 }
 
 // b = exp(-(d/kappa + alpha) dt), a = d (b - 1) / (kappa (d + kappa alpha))
@@ -100,11 +114,52 @@ __global__ void cell_maps_kernel(const PrepParams Q) {
       double a, b;
       relax_ab(Q.d1[nu * n + t], Q.al1[nu * n + t], k1, Q.dt, a, b);
       store((MT *)Q.a1, nu * Q.npts_alloc + o, a);
-      store((MT *)Q.b1, nu * Q.npts_alloc + o, b);
+      store_b((MT *)Q.b1, nu * Q.npts_alloc + o, b);
       relax_ab(Q.d2[nu * n + t], Q.al2[nu * n + t], k2, Q.dt, a, b);
       store((MT *)Q.a2, nu * Q.npts_alloc + o, a);
-      store((MT *)Q.b2, nu * Q.npts_alloc + o, b);
+      store_b((MT *)Q.b2, nu * Q.npts_alloc + o, b);
     }
+  }
+}
+
+// Tissue-index form: per-tissue coefficient table ([field][256], field order
+// of maps.cuh) with the same arithmetic as the per-cell maps, and the index
+// copied into the pitched cell layout.
+__global__ void table_kernel(const PrepParams Q) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Q.n_tissue) return;
+  float *T = Q.table_out;
+  const double c = Q.c[t], rho = Q.rho[t];
+  const double K = rho * c * c;
+  T[kTabK * kTissues + t] = (float)K;
+  T[kTabRho * kTissues + t] = (float)rho;
+  if (Q.nl_mode != 0) {
+    const double beta = Q.beta[t];
+    T[kTabChi * kTissues + t] = (float)(Q.nl_mode == 1 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K);
+  }
+  const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
+  T[kTabIk1 * kTissues + t] = (float)(1.0 / k1);
+  T[kTabIk2 * kTissues + t] = (float)(1.0 / k2);
+  for (int nu = 0; nu < Q.N; ++nu) {
+    double a, b;
+    relax_ab(Q.d1[nu * Q.n_tissue + t], Q.al1[nu * Q.n_tissue + t], k1, Q.dt, a, b);
+    T[(kTabRelax + nu) * kTissues + t] = (float)a;
+    T[(kTabRelax + kMaxRelax + nu) * kTissues + t] = (float)b;
+    relax_ab(Q.d2[nu * Q.n_tissue + t], Q.al2[nu * Q.n_tissue + t], k2, Q.dt, a, b);
+    T[(kTabRelax + 2 * kMaxRelax + nu) * kTissues + t] = (float)a;
+    T[(kTabRelax + 3 * kMaxRelax + nu) * kTissues + t] = (float)b;
+  }
+}
+
+__global__ void index_copy_kernel(const PrepParams Q) {
+  const long long n = (long long)Q.nx * Q.ny * Q.nz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % Q.nx);
+    const long long r = t / Q.nx;
+    const int j = (int)(r % Q.ny);
+    const int k = (int)(r / Q.ny);
+    Q.tissue_out[(long long)k * Q.plane + (long long)j * Q.pitch + i] = Q.tissue_in[t];
   }
 }
 
@@ -116,7 +171,6 @@ __global__ void strip_maps_kernel(const PrepParams Q, int axis) {
   // strip extents: the axis has 2L entries, the others their full extent
   int se[3] = {Q.nx, Q.ny, Q.nz};
   se[axis] = 2 * L;
-  const long long n = (long long)Q.nx * Q.ny * Q.nz;
   const long long total = (long long)se[0] * se[1] * se[2];
   const long long pitch_out = axis == 0 ? 2 * L : Q.pitch;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -137,19 +191,20 @@ __global__ void strip_maps_kernel(const PrepParams Q, int axis) {
     else out = ((long long)s[2] * Q.ny + s[1]) * pitch_out + s[0];
     const double dface = depth_of(cell[axis] + 0.5, ext[axis], L);
     const double dcent = depth_of((double)cell[axis], ext[axis], L);
-    const double k1 = Q.k1[src], k2 = Q.k2[src];
+    const long long ri = src_of(Q, src), nr = n_src(Q);
+    const double k1 = Q.k1[ri], k2 = Q.k2[ri];
     for (int nu = 0; nu < Q.N; ++nu) {
       double a, b;
-      const double d1 = ramp(Q, Q.d1[nu * n + src], dface, nu, true);
-      const double al1 = ramp(Q, Q.al1[nu * n + src], dface, nu, false);
+      const double d1 = ramp(Q, Q.d1[nu * nr + ri], dface, nu, true);
+      const double al1 = ramp(Q, Q.al1[nu * nr + ri], dface, nu, false);
       relax_ab(d1, al1, k1, Q.dt, a, b);
       store((MT *)Q.sa1[axis], nu * Q.strip_nu[axis] + out, a);
-      store((MT *)Q.sb1[axis], nu * Q.strip_nu[axis] + out, b);
-      const double d2 = ramp(Q, Q.d2[nu * n + src], dcent, nu, true);
-      const double al2 = ramp(Q, Q.al2[nu * n + src], dcent, nu, false);
+      store_b((MT *)Q.sb1[axis], nu * Q.strip_nu[axis] + out, b);
+      const double d2 = ramp(Q, Q.d2[nu * nr + ri], dcent, nu, true);
+      const double al2 = ramp(Q, Q.al2[nu * nr + ri], dcent, nu, false);
       relax_ab(d2, al2, k2, Q.dt, a, b);
       store((MT *)Q.sa2[axis], nu * Q.strip_nu[axis] + out, a);
-      store((MT *)Q.sb2[axis], nu * Q.strip_nu[axis] + out, b);
+      store_b((MT *)Q.sb2[axis], nu * Q.strip_nu[axis] + out, b);
     }
   }
 }
@@ -162,14 +217,19 @@ __global__ void medium_scan_kernel(const PrepParams Q, unsigned long long *maxbi
   int nbad = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    const double c = Q.c[t], rho = Q.rho[t];
+    if (Q.tissue_in && Q.tissue_in[t] >= Q.n_tissue) {
+      ++nbad;
+      continue;
+    }
+    const long long r = src_of(Q, t);
+    const double c = Q.c[r], rho = Q.rho[r];
     double k1 = 1.0, k2 = 1.0;
     if (Q.N) {
-      k1 = Q.k1[t];
-      k2 = Q.k2[t];
+      k1 = Q.k1[r];
+      k2 = Q.k2[r];
     }
     const bool ok = isfinite(c) && c > 0.0 && isfinite(rho) && rho > 0.0 && isfinite(k1) && k1 > 0.0 &&
-                    isfinite(k2) && k2 > 0.0 && (Q.nl_mode == 0 || isfinite((double)Q.beta[t]));
+                    isfinite(k2) && k2 > 0.0 && (Q.nl_mode == 0 || isfinite((double)Q.beta[r]));
     if (!ok) {
       ++nbad;
       continue;
@@ -199,17 +259,23 @@ cudaError_t launch_medium_scan(const PrepParams &Q, unsigned long long *maxbits,
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep(const PrepParams &Q, int map_bf16, cudaStream_t s) {
+cudaError_t launch_prep(const PrepParams &Q, int map_kind, cudaStream_t s) {
   const long long n = (long long)Q.nx * Q.ny * Q.nz;
-  if (map_bf16) cell_maps_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, s>>>(Q);
-  else cell_maps_kernel<float><<<grid_for(n), 256, 0, s>>>(Q);
+  if (map_kind == 2) {
+    table_kernel<<<1, 256, 0, s>>>(Q);
+    index_copy_kernel<<<grid_for(n), 256, 0, s>>>(Q);
+  } else if (map_kind == 1) {
+    cell_maps_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, s>>>(Q);
+  } else {
+    cell_maps_kernel<float><<<grid_for(n), 256, 0, s>>>(Q);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int L = Q.LT + Q.LB;
   if (L > 0 && Q.N > 0) {
     for (int axis = 0; axis < Q.nd; ++axis) {
       long long total = 2LL * L * n / (axis == 0 ? Q.nx : axis == 1 ? Q.ny : Q.nz);
-      if (map_bf16) strip_maps_kernel<__nv_bfloat16><<<grid_for(total), 256, 0, s>>>(Q, axis);
+      if (map_kind == 1) strip_maps_kernel<__nv_bfloat16><<<grid_for(total), 256, 0, s>>>(Q, axis);
       else strip_maps_kernel<float><<<grid_for(total), 256, 0, s>>>(Q, axis);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;

@@ -14,8 +14,12 @@
 // Each block owns a 128 x 16 tile; 256 threads, 4 consecutive x cells per
 // thread (128-bit loads and stores of every streamed array), two rows each.
 // The stencil operand (p, or v_x / v_y) is staged in shared memory with its
-// halo; every other array is read once and written once.
+// halo; every other array is read once and written once.  Interior tiles
+// issue every global load of a row before the first store.  Coefficient maps
+// are read through a policy (maps.cuh): dense float / bf16 maps, or a uint8
+// tissue index into per-tissue tables staged in shared memory.
 #include "coef.cuh"
+#include "maps.cuh"
 
 namespace fw2 {
 
@@ -37,39 +41,6 @@ __device__ __forceinline__ Win12 win12(const float *row, int tx) {
   return w;
 }
 
-
-// x and y derivatives of v_x, v_y at the four centres of a thread (pressure)
-__device__ __forceinline__ void prs_derivs(const StepParams &P, const float (*svx)[kTX + 8],
-                                           const float (*svy)[kTX + 8], int ly, int tx, float4 &Dx, float4 &Dy) {
-  const Win12 w = win12(svx[ly + 1], tx);
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    float d = 0.f;
-#pragma unroll
-    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m - 1] - w.v[4 + e - m], d);
-    el(Dx, e) = d;
-  }
-  float4 col[8];
-#pragma unroll
-  for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&svy[ly + m][4 * tx + 4]);
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    float d = 0.f;
-#pragma unroll
-    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[4 + m - 1], e) - el(col[4 - m], e), d);
-    el(Dy, e) = d;
-  }
-  if (P.g11h != 0.f) {
-    const Win12 up = win12(svx[ly + 2], tx), dn = win12(svx[ly], tx);
-    const Win12 y0w = win12(svy[ly + 4], tx), y1w = win12(svy[ly + 3], tx);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      el(Dx, e) += P.g11h * ((up.v[4 + e] - up.v[3 + e]) + (dn.v[4 + e] - dn.v[3 + e]));
-      el(Dy, e) += P.g11h * ((y0w.v[5 + e] - y1w.v[5 + e]) + (y0w.v[3 + e] - y1w.v[3 + e]));
-    }
-  }
-}
-
 // A tile whose cells, stencil halo and face neighbours all lie inside the
 // grid and outside every C-PML strip: every cell uses the interior maps for
 // both axes, and no boundary rule applies.
@@ -78,8 +49,7 @@ __device__ __forceinline__ bool interior_tile(const StepParams &P, int x0, int y
   return x0 >= Lx && x0 + kTX + Lx <= P.nx && y0 >= Ly && y0 + kTY + Ly <= P.ny;
 }
 
-// x and y derivatives of the staged operand at the four faces of a thread
-// (velocity) -- shared by both paths
+// x and y derivatives of the staged p at the four faces of a thread
 __device__ __forceinline__ void vel_derivs(const StepParams &P, const float (*sp)[kTX + 8], int sy, int tx,
                                            float4 &Dx, float4 &Dy) {
   const Win12 w = win12(sp[sy], tx);
@@ -101,6 +71,8 @@ __device__ __forceinline__ void vel_derivs(const StepParams &P, const float (*sp
     el(Dy, e) = d;
   }
   if (P.g11h != 0.f) {
+    // cross taps of Sec. 3.1: g11 sum_s (p(i+1, j+s) - p(i, j+s)) for x,
+    // g11 sum_s (p(i+s, j+1) - p(i+s, j)) for y
     const Win12 up = win12(sp[sy + 1], tx), dn = win12(sp[sy - 1], tx);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -110,16 +82,119 @@ __device__ __forceinline__ void vel_derivs(const StepParams &P, const float (*sp
   }
 }
 
+// x and y derivatives of v_x, v_y at the four centres of a thread
+__device__ __forceinline__ void prs_derivs(const StepParams &P, const float (*svx)[kTX + 8],
+                                           const float (*svy)[kTX + 8], int ly, int tx, float4 &Dx, float4 &Dy) {
+  const Win12 w = win12(svx[ly + 1], tx);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float d = 0.f;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m - 1] - w.v[4 + e - m], d);
+    el(Dx, e) = d;
+  }
+  float4 col[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&svy[ly + m][4 * tx + 4]);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float d = 0.f;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[4 + m - 1], e) - el(col[4 - m], e), d);
+    el(Dy, e) = d;
+  }
+  if (P.g11h != 0.f) {
+    // g11 sum_s (vx(i, j+s) - vx(i-1, j+s)) and g11 sum_s (vy(i+s, j) - vy(i+s, j-1))
+    const Win12 up = win12(svx[ly + 2], tx), dn = win12(svx[ly], tx);
+    const Win12 y0w = win12(svy[ly + 4], tx), y1w = win12(svy[ly + 3], tx);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el(Dx, e) += P.g11h * ((up.v[4 + e] - up.v[3 + e]) + (dn.v[4 + e] - dn.v[3 + e]));
+      el(Dy, e) += P.g11h * ((y0w.v[5 + e] - y1w.v[5 + e]) + (y0w.v[3 + e] - y1w.v[3 + e]));
+    }
+  }
+}
+
+// a, b of mechanism nu for axis Q at the cells of a group (edge path):
+// from the boundary strip of axis Q inside its C-PML region (Sec. 3.3: each
+// axis' parameters depend on the distance along that axis only), else from
+// the interior maps.
+template <int Q, int OP, typename Maps>
+__device__ __forceinline__ void coef_edge(const StepParams &P, const Maps &M, typename Maps::Cell cell, int nu,
+                                          int i0, int j, float4 &a, float4 &b) {
+  using ST = typename Maps::StripT;
+  const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[Q] : P.sa2[Q]);
+  const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[Q] : P.sb2[Q]);
+  const int L = P.L[Q];
+  if (Q == 0) {
+    const bool any = L > 0 && (i0 < L || i0 + 3 >= P.nx - L);
+    if (!any) {
+      a = M.template a<OP>(cell, nu);
+      b = M.template b<OP>(cell, nu);
+      return;
+    }
+    const long long row = (long long)nu * P.strip_nu[0] + (long long)j * (2 * L);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int x = i0 + e;
+      float av = 0.f, bv = 0.f;
+      if (x < P.nx) {
+        const int sc = strip_coord(x, P.nx, L);
+        if (sc >= 0) {
+          av = ldmap(sa, row + sc);
+          bv = ldb(sb, row + sc);
+        } else {
+          av = M.template a1c<OP>(cell, nu, e);
+          bv = M.template b1c<OP>(cell, nu, e);
+        }
+      }
+      el(a, e) = av;
+      el(b, e) = bv;
+    }
+  } else {
+    const int sc = strip_coord(j, P.ny, L);
+    if (sc < 0) {
+      a = M.template a<OP>(cell, nu);
+      b = M.template b<OP>(cell, nu);
+    } else {
+      const long long off = (long long)nu * P.strip_nu[1] + (long long)sc * P.pitch + i0;
+      a = ldmap4(sa, off);
+      b = ldb4(sb, off);
+    }
+  }
+}
+
+// Stretched derivative of Eq. (relaxation4) for the four cells of a group
+// (edge path): S = D / kappa + sum_nu (w_new psi_new + w_old psi_old),
+// psi_new = b psi_old + a D (Eq. relaxation_psi), psi written back.
+template <int Q, int OP, int N, typename Maps>
+__device__ __forceinline__ float4 stretch_edge(const StepParams &P, const Maps &M, typename Maps::Cell cell,
+                                               float *psi, float4 D, float4 ik, long long c, int i0, int j) {
+  float4 S = make_float4(D.x * ik.x, D.y * ik.y, D.z * ik.z, D.w * ik.w);
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    float4 a, b;
+    coef_edge<Q, OP>(P, M, cell, nu, i0, j, a, b);
+    const long long o = (long long)nu * P.npts_alloc + c;
+    const float4 ps = ld_state4(psi, o);
+    float4 pn;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el(pn, e) = fmaf(el(b, e), el(ps, e), el(a, e) * el(D, e));
+      el(S, e) += fmaf(P.w_new, el(pn, e), P.w_old * el(ps, e));
+    }
+    st_state4(psi, o, mask_pad(pn, i0, P.nx));
+  }
+  return S;
+}
+
 // Interior rows of the velocity half step.  Every global load of a row (both
-// velocity components, 1/kappa1, the shared interior a, b and the memory
-// variables of both axes) is issued before any store, so a row pays one
-// memory latency instead of one per mechanism.
-template <int N, typename MT>
-__device__ __forceinline__ void vel2d_fast_rows(const StepParams &P, const float (*sp)[kTX + 8],
+// velocity components, the maps and the memory variables of both axes) is
+// issued before any store, so a row pays one memory latency instead of one
+// per mechanism.
+template <int N, typename Maps>
+__device__ __forceinline__ void vel2d_fast_rows(const StepParams &P, const Maps &M, const float (*sp)[kTX + 8],
                                                 const float (*sr)[kTX + 4], int x0, int y0, int tx, int ty) {
-  const MT *ik1 = static_cast<const MT *>(P.ik1);
-  const MT *a1 = static_cast<const MT *>(P.a1);
-  const MT *b1 = static_cast<const MT *>(P.b1);
   float *psx = P.psi1[0], *psy = P.psi1[1];
   const long long S = P.npts_alloc;
   const int i0 = x0 + 4 * tx;
@@ -128,15 +203,20 @@ __device__ __forceinline__ void vel2d_fast_rows(const StepParams &P, const float
     const int ly = ty + rr * kBY;
     const int j = y0 + ly;
     const long long c = (long long)j * P.pitch + i0;
+    const typename Maps::Cell cell = M.cell(c);
     float4 vx = ld_state4(P.v[0], c), vy = ld_state4(P.v[1], c);
-    const float4 k1 = ldmap4(ik1, c);
-    float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1], Px[N > 0 ? N : 1], Py[N > 0 ? N : 1];
+    float4 Px[N > 0 ? N : 1], Py[N > 0 ? N : 1];
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      A[nu] = ldmap4(a1, nu * S + c);
-      B[nu] = ldmap4(b1, nu * S + c);
       Px[nu] = ld_state4(psx, nu * S + c);
       Py[nu] = ld_state4(psy, nu * S + c);
+    }
+    const float4 k1 = M.ik1(cell);
+    float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1];
+#pragma unroll
+    for (int nu = 0; nu < N; ++nu) {
+      A[nu] = M.template a<1>(cell, nu);
+      B[nu] = M.template b<1>(cell, nu);
     }
     float4 Dx, Dy;
     vel_derivs(P, sp, ly + 3, tx, Dx, Dy);
@@ -173,14 +253,9 @@ __device__ __forceinline__ void vel2d_fast_rows(const StepParams &P, const float
 }
 
 // Interior rows of the pressure half step (same load-first structure).
-template <int N, typename MT>
-__device__ __forceinline__ void prs2d_fast_rows(const StepParams &P, const float (*svx)[kTX + 8],
+template <int N, typename Maps>
+__device__ __forceinline__ void prs2d_fast_rows(const StepParams &P, const Maps &M, const float (*svx)[kTX + 8],
                                                 const float (*svy)[kTX + 8], int x0, int y0, int tx, int ty) {
-  const MT *ik2 = static_cast<const MT *>(P.ik2);
-  const MT *a2 = static_cast<const MT *>(P.a2);
-  const MT *b2 = static_cast<const MT *>(P.b2);
-  const MT *Km = static_cast<const MT *>(P.K);
-  const MT *chim = static_cast<const MT *>(P.chi);
   float *psx = P.psi2[0], *psy = P.psi2[1];
   const long long S = P.npts_alloc;
   const int i0 = x0 + 4 * tx;
@@ -189,18 +264,23 @@ __device__ __forceinline__ void prs2d_fast_rows(const StepParams &P, const float
     const int ly = ty + rr * kBY;
     const int j = y0 + ly;
     const long long c = (long long)j * P.pitch + i0;
+    const typename Maps::Cell cell = M.cell(c);
     float4 p = ld_state4(P.p, c);
-    const float4 k2 = ldmap4(ik2, c);
-    const float4 K = ldmap4(Km, c);
-    float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (P.nl) ch = ldmap4(chim, c);
-    float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1], Px[N > 0 ? N : 1], Py[N > 0 ? N : 1];
+    float4 Px[N > 0 ? N : 1], Py[N > 0 ? N : 1];
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      A[nu] = ldmap4(a2, nu * S + c);
-      B[nu] = ldmap4(b2, nu * S + c);
       Px[nu] = ld_state4(psx, nu * S + c);
       Py[nu] = ld_state4(psy, nu * S + c);
+    }
+    const float4 k2 = M.ik2(cell);
+    const float4 K = M.Kv(cell);
+    float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (P.nl) ch = M.chiv(cell);
+    float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1];
+#pragma unroll
+    for (int nu = 0; nu < N; ++nu) {
+      A[nu] = M.template a<2>(cell, nu);
+      B[nu] = M.template b<2>(cell, nu);
     }
     float4 Dx, Dy;
     prs_derivs(P, svx, svy, ly, tx, Dx, Dy);
@@ -229,38 +309,40 @@ __device__ __forceinline__ void prs2d_fast_rows(const StepParams &P, const float
   }
 }
 
-template <int N, typename MT>
-__global__ void __launch_bounds__(256, 2) vel2d_kernel(const StepParams P) {
-  constexpr int PW = kTX + 8;  // p tile columns: x0-4 .. x0+TX+3
-  constexpr int PH = kTY + 7;  // p tile rows:    y0-3 .. y0+TY+3
-  constexpr int RW = kTX + 4;  // rho tile columns: x0 .. x0+TX+3
-  constexpr int RH = kTY + 1;  // rho tile rows:    y0 .. y0+TY
-  __shared__ __align__(16) float sp[PH][PW];
-  __shared__ __align__(16) float sr[RH][RW];
+constexpr int kPW = kTX + 8;  // p tile columns: x0-4 .. x0+TX+3
+constexpr int kPH = kTY + 7;  // p tile rows:    y0-3 .. y0+TY+3
+constexpr int kRW = kTX + 4;  // rho tile columns: x0 .. x0+TX+3
+constexpr int kRH = kTY + 1;  // rho tile rows:    y0 .. y0+TY
 
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+// One 128 x 16 tile of the velocity half step.  `stage` false skips copying
+// the maps' shared-memory table (already staged for this context).
+template <int N, typename Maps>
+__device__ __forceinline__ void vel2d_tile(const StepParams &P, int x0, int y0, float (*sp)[kPW],
+                                           float (*sr)[kRW], float *stab, bool stage) {
+  constexpr int PW = kPW, PH = kPH, RW = kRW, RH = kRH;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
-  const MT *rho = static_cast<const MT *>(P.rho);
-
+  Maps M(P);
+  if (stage) M.stage(P, stab, tid);
   for (int t = tid; t < PH * (PW / 4); t += 256) {
     const int r = t / (PW / 4), c4 = t % (PW / 4);
     const float4 v = load_chunk(P, P.p, x0 - 4 + 4 * c4, y0 - 3 + r, 0);
     *reinterpret_cast<float4 *>(&sp[r][4 * c4]) = v;
   }
+  __syncthreads();  // the table must be staged before the rho tile reads it
+  M.bind(stab);
   for (int t = tid; t < RH * RW; t += 256) {
     const int r = t / RW, cc = t % RW;
     const int gx = rho_coord(x0 + cc, P.nx, P.periodic[0]);
     const int gy = rho_coord(y0 + r, P.ny, P.periodic[1]);
-    sr[r][cc] = ldmap(rho, (long long)gy * P.pitch + gx);
+    sr[r][cc] = M.rho_at((long long)gy * P.pitch + gx);
   }
   __syncthreads();
 
   const int i0 = x0 + 4 * tx;
   if (i0 >= P.nx) return;
-  const MT *ik1 = static_cast<const MT *>(P.ik1);
   if (interior_tile(P, x0, y0)) {
-    vel2d_fast_rows<N, MT>(P, sp, sr, x0, y0, tx, ty);
+    vel2d_fast_rows<N>(P, M, sp, sr, x0, y0, tx, ty);
     return;
   }
 #pragma unroll 1
@@ -269,41 +351,9 @@ __global__ void __launch_bounds__(256, 2) vel2d_kernel(const StepParams P) {
     const int j = y0 + ly;
     if (j >= P.ny) break;
     const long long c = (long long)j * P.pitch + i0;
-    const int sy = ly + 3;  // tile row of j
-    // d/dx at faces i+1/2: sum_m g_m (p[i+m] - p[i-m+1]); window col 4 is i0
-    const Win12 w = win12(sp[sy], tx);
+    const typename Maps::Cell cell = M.cell(c);
     float4 Dx, Dy;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      float d = 0.f;
-#pragma unroll
-      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m] - w.v[4 + e - m + 1], d);
-      el(Dx, e) = d;
-    }
-    // d/dy at faces j+1/2: sum_m g_m (p[j+m] - p[j-m+1])
-    {
-      float4 col[8];
-#pragma unroll
-      for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&sp[sy - 3 + m][4 * tx + 4]);
-      // col[3] is row j, col[3 + m] row j+m, col[3 - m + 1] row j-m+1
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        float d = 0.f;
-#pragma unroll
-        for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[3 + m], e) - el(col[4 - m], e), d);
-        el(Dy, e) = d;
-      }
-    }
-    if (P.g11h != 0.f) {
-      // cross taps of Sec. 3.1: g11 sum_s (p(i+1, j+s) - p(i, j+s)) for x,
-      // g11 sum_s (p(i+s, j+1) - p(i+s, j)) for y
-      const Win12 up = win12(sp[sy + 1], tx), dn = win12(sp[sy - 1], tx);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        el(Dx, e) += P.g11h * ((up.v[5 + e] - up.v[4 + e]) + (dn.v[5 + e] - dn.v[4 + e]));
-        el(Dy, e) += P.g11h * ((up.v[5 + e] - w.v[5 + e]) + (up.v[3 + e] - w.v[3 + e]));
-      }
-    }
+    vel_derivs(P, sp, ly + 3, tx, Dx, Dy);
     // dt / rho at the faces: 2 dt / (rho_i + rho_{i+1})
     float4 bx, by;
     {
@@ -316,15 +366,15 @@ __global__ void __launch_bounds__(256, 2) vel2d_kernel(const StepParams P) {
       by = make_float4(P.two_dt / (r0.x + ru.x), P.two_dt / (r0.y + ru.y), P.two_dt / (r0.z + ru.z),
                        P.two_dt / (r0.w + ru.w));
     }
-    const float4 k1 = ldmap4(ik1, c);
+    const float4 k1 = M.ik1(cell);
     {
-      const float4 S = stretch4<0, 1, N, MT>(P, P.psi1[0], Dx, k1, c, i0, j, 0);
+      const float4 S = stretch_edge<0, 1, N>(P, M, cell, P.psi1[0], Dx, k1, c, i0, j);
       float4 v = ld_state4(P.v[0], c);
       v.x -= bx.x * S.x; v.y -= bx.y * S.y; v.z -= bx.z * S.z; v.w -= bx.w * S.w;
       st_state4(P.v[0], c, mask_pad(v, i0, P.nx));
     }
     {
-      const float4 S = stretch4<1, 1, N, MT>(P, P.psi1[1], Dy, k1, c, i0, j, 0);
+      const float4 S = stretch_edge<1, 1, N>(P, M, cell, P.psi1[1], Dy, k1, c, i0, j);
       float4 v = ld_state4(P.v[1], c);
       v.x -= by.x * S.x; v.y -= by.y * S.y; v.z -= by.z * S.z; v.w -= by.w * S.w;
       st_state4(P.v[1], c, mask_pad(v, i0, P.nx));
@@ -332,17 +382,18 @@ __global__ void __launch_bounds__(256, 2) vel2d_kernel(const StepParams P) {
   }
 }
 
-template <int N, typename MT>
-__global__ void __launch_bounds__(256, 2) prs2d_kernel(const StepParams P) {
-  constexpr int W = kTX + 8;   // columns x0-4 .. x0+TX+3
-  constexpr int HX = kTY + 2;  // v_x rows y0-1 .. y0+TY
-  constexpr int HY = kTY + 7;  // v_y rows y0-4 .. y0+TY+2
-  __shared__ __align__(16) float svx[HX][W];
-  __shared__ __align__(16) float svy[HY][W];
+constexpr int kHX = kTY + 2;  // v_x rows y0-1 .. y0+TY
+constexpr int kHY = kTY + 7;  // v_y rows y0-4 .. y0+TY+2
 
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+// One 128 x 16 tile of the pressure half step.
+template <int N, typename Maps>
+__device__ __forceinline__ void prs2d_tile(const StepParams &P, int x0, int y0, float (*svx)[kPW],
+                                           float (*svy)[kPW], float *stab, bool stage) {
+  constexpr int W = kPW, HX = kHX, HY = kHY;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
+  Maps M(P);
+  if (stage) M.stage(P, stab, tid);
   for (int t = tid; t < HX * (W / 4); t += 256) {
     const int r = t / (W / 4), c4 = t % (W / 4);
     *reinterpret_cast<float4 *>(&svx[r][4 * c4]) = load_chunk(P, P.v[0], x0 - 4 + 4 * c4, y0 - 1 + r, 0);
@@ -352,64 +403,32 @@ __global__ void __launch_bounds__(256, 2) prs2d_kernel(const StepParams P) {
     *reinterpret_cast<float4 *>(&svy[r][4 * c4]) = load_chunk(P, P.v[1], x0 - 4 + 4 * c4, y0 - 4 + r, 0);
   }
   __syncthreads();
+  M.bind(stab);
 
   const int i0 = x0 + 4 * tx;
   if (i0 >= P.nx) return;
   if (interior_tile(P, x0, y0)) {
-    prs2d_fast_rows<N, MT>(P, svx, svy, x0, y0, tx, ty);
+    prs2d_fast_rows<N>(P, M, svx, svy, x0, y0, tx, ty);
     return;
   }
-  const MT *ik2 = static_cast<const MT *>(P.ik2);
-  const MT *Km = static_cast<const MT *>(P.K);
-  const MT *chim = static_cast<const MT *>(P.chi);
 #pragma unroll 1
   for (int rr = 0; rr < kRows; ++rr) {
     const int ly = ty + rr * kBY;
     const int j = y0 + ly;
     if (j >= P.ny) break;
     const long long c = (long long)j * P.pitch + i0;
-    // d/dx v_x at centres: sum_m g_m (vx[i+m-1] - vx[i-m]); window col 4 is i0
-    const Win12 w = win12(svx[ly + 1], tx);
+    const typename Maps::Cell cell = M.cell(c);
     float4 Dx, Dy;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      float d = 0.f;
-#pragma unroll
-      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m - 1] - w.v[4 + e - m], d);
-      el(Dx, e) = d;
-    }
-    {
-      // d/dy v_y at centres: sum_m g_m (vy[j+m-1] - vy[j-m]); col[4] is row j
-      float4 col[8];
-#pragma unroll
-      for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&svy[ly + m][4 * tx + 4]);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        float d = 0.f;
-#pragma unroll
-        for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[4 + m - 1], e) - el(col[4 - m], e), d);
-        el(Dy, e) = d;
-      }
-    }
-    if (P.g11h != 0.f) {
-      // g11 sum_s (vx(i, j+s) - vx(i-1, j+s)) and g11 sum_s (vy(i+s, j) - vy(i+s, j-1))
-      const Win12 up = win12(svx[ly + 2], tx), dn = win12(svx[ly], tx);
-      const Win12 y0w = win12(svy[ly + 4], tx), y1w = win12(svy[ly + 3], tx);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        el(Dx, e) += P.g11h * ((up.v[4 + e] - up.v[3 + e]) + (dn.v[4 + e] - dn.v[3 + e]));
-        el(Dy, e) += P.g11h * ((y0w.v[5 + e] - y1w.v[5 + e]) + (y0w.v[3 + e] - y1w.v[3 + e]));
-      }
-    }
-    const float4 k2 = ldmap4(ik2, c);
-    const float4 Sx = stretch4<0, 2, N, MT>(P, P.psi2[0], Dx, k2, c, i0, j, 0);
-    const float4 Sy = stretch4<1, 2, N, MT>(P, P.psi2[1], Dy, k2, c, i0, j, 0);
-    const float4 K = ldmap4(Km, c);
+    prs_derivs(P, svx, svy, ly, tx, Dx, Dy);
+    const float4 k2 = M.ik2(cell);
+    const float4 Sx = stretch_edge<0, 2, N>(P, M, cell, P.psi2[0], Dx, k2, c, i0, j);
+    const float4 Sy = stretch_edge<1, 2, N>(P, M, cell, P.psi2[1], Dy, k2, c, i0, j);
+    const float4 K = M.Kv(cell);
     float4 p = ld_state4(P.p, c);
     float4 upd = make_float4(P.dt * K.x * (Sx.x + Sy.x), P.dt * K.y * (Sx.y + Sy.y),
                              P.dt * K.z * (Sx.z + Sy.z), P.dt * K.w * (Sx.w + Sy.w));
     if (P.nl) {
-      const float4 ch = ldmap4(chim, c);
+      const float4 ch = M.chiv(cell);
       upd.x /= fmaf(ch.x, p.x, 1.f); upd.y /= fmaf(ch.y, p.y, 1.f);
       upd.z /= fmaf(ch.z, p.z, 1.f); upd.w /= fmaf(ch.w, p.w, 1.f);
     }
@@ -418,27 +437,89 @@ __global__ void __launch_bounds__(256, 2) prs2d_kernel(const StepParams P) {
   }
 }
 
-template <typename MT>
+
+template <int N, typename Maps>
+__global__ void __launch_bounds__(256, 2) vel2d_kernel(const StepParams P) {
+  __shared__ __align__(16) float sp[kPH][kPW];
+  __shared__ __align__(16) float sr[kRH][kRW];
+  __shared__ __align__(16) float stab[Maps::kSmemFloats];
+  vel2d_tile<N, Maps>(P, blockIdx.x * kTX, blockIdx.y * kTY, sp, sr, stab, true);
+}
+
+template <int N, typename Maps>
+__global__ void __launch_bounds__(256, 2) prs2d_kernel(const StepParams P) {
+  __shared__ __align__(16) float svx[kHX][kPW];
+  __shared__ __align__(16) float svy[kHY][kPW];
+  __shared__ __align__(16) float stab[Maps::kSmemFloats];
+  prs2d_tile<N, Maps>(P, blockIdx.x * kTX, blockIdx.y * kTY, svx, svy, stab, true);
+}
+
+// Persistent batched half steps: blocks walk the tile table round-robin;
+// entry (ctx, x0, y0).  The context's parameter block is copied to shared
+// memory when the context changes (the table stays staged with it).
+__device__ __forceinline__ bool load_ctx(const StepParams *Ps, int ctx, StepParams *sP, int *cur) {
+  if (*cur == ctx) return false;
+  __syncthreads();
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int *src = reinterpret_cast<const int *>(Ps + ctx);
+  int *dst = reinterpret_cast<int *>(sP);
+  for (int w = tid; w < (int)(sizeof(StepParams) / 4); w += 256) dst[w] = __ldg(src + w);
+  __syncthreads();
+  *cur = ctx;
+  return true;
+}
+
+template <int N, typename Maps>
+__global__ void __launch_bounds__(256, 2) vel2d_batched(const StepParams *Ps, const int4 *tiles, int n_tiles) {
+  __shared__ __align__(16) float sp[kPH][kPW];
+  __shared__ __align__(16) float sr[kRH][kRW];
+  __shared__ __align__(16) float stab[Maps::kSmemFloats];
+  __shared__ __align__(16) StepParams sP;
+  int cur = -1;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int4 e = tiles[t];
+    const bool fresh = load_ctx(Ps, e.x, &sP, &cur);
+    vel2d_tile<N, Maps>(sP, e.y, e.z, sp, sr, stab, fresh);
+    __syncthreads();
+  }
+}
+
+template <int N, typename Maps>
+__global__ void __launch_bounds__(256, 2) prs2d_batched(const StepParams *Ps, const int4 *tiles, int n_tiles) {
+  __shared__ __align__(16) float svx[kHX][kPW];
+  __shared__ __align__(16) float svy[kHY][kPW];
+  __shared__ __align__(16) float stab[Maps::kSmemFloats];
+  __shared__ __align__(16) StepParams sP;
+  int cur = -1;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int4 e = tiles[t];
+    const bool fresh = load_ctx(Ps, e.x, &sP, &cur);
+    prs2d_tile<N, Maps>(sP, e.y, e.z, svx, svy, stab, fresh);
+    __syncthreads();
+  }
+}
+
+template <typename Maps>
 cudaError_t vel2d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
   switch (P.n_relax) {
-    case 0: vel2d_kernel<0, MT><<<g, b, 0, s>>>(P); break;
-    case 1: vel2d_kernel<1, MT><<<g, b, 0, s>>>(P); break;
-    case 2: vel2d_kernel<2, MT><<<g, b, 0, s>>>(P); break;
-    case 3: vel2d_kernel<3, MT><<<g, b, 0, s>>>(P); break;
-    case 4: vel2d_kernel<4, MT><<<g, b, 0, s>>>(P); break;
+    case 0: vel2d_kernel<0, Maps><<<g, b, 0, s>>>(P); break;
+    case 1: vel2d_kernel<1, Maps><<<g, b, 0, s>>>(P); break;
+    case 2: vel2d_kernel<2, Maps><<<g, b, 0, s>>>(P); break;
+    case 3: vel2d_kernel<3, Maps><<<g, b, 0, s>>>(P); break;
+    case 4: vel2d_kernel<4, Maps><<<g, b, 0, s>>>(P); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template <typename MT>
+template <typename Maps>
 cudaError_t prs2d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
   switch (P.n_relax) {
-    case 0: prs2d_kernel<0, MT><<<g, b, 0, s>>>(P); break;
-    case 1: prs2d_kernel<1, MT><<<g, b, 0, s>>>(P); break;
-    case 2: prs2d_kernel<2, MT><<<g, b, 0, s>>>(P); break;
-    case 3: prs2d_kernel<3, MT><<<g, b, 0, s>>>(P); break;
-    case 4: prs2d_kernel<4, MT><<<g, b, 0, s>>>(P); break;
+    case 0: prs2d_kernel<0, Maps><<<g, b, 0, s>>>(P); break;
+    case 1: prs2d_kernel<1, Maps><<<g, b, 0, s>>>(P); break;
+    case 2: prs2d_kernel<2, Maps><<<g, b, 0, s>>>(P); break;
+    case 3: prs2d_kernel<3, Maps><<<g, b, 0, s>>>(P); break;
+    case 4: prs2d_kernel<4, Maps><<<g, b, 0, s>>>(P); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -446,14 +527,51 @@ cudaError_t prs2d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) 
 
 }  // namespace
 
-cudaError_t launch_vel2d(const StepParams &P, int map_bf16, cudaStream_t s) {
+cudaError_t launch_vel2d(const StepParams &P, int map_kind, cudaStream_t s) {
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY), b(32, kBY);
-  return map_bf16 ? vel2d_dispatch<__nv_bfloat16>(P, g, b, s) : vel2d_dispatch<float>(P, g, b, s);
+  if (map_kind == 2) return vel2d_dispatch<IdxMaps>(P, g, b, s);
+  return map_kind ? vel2d_dispatch<DenseMaps<__nv_bfloat16>>(P, g, b, s) : vel2d_dispatch<DenseMaps<float>>(P, g, b, s);
 }
 
-cudaError_t launch_prs2d(const StepParams &P, int map_bf16, cudaStream_t s) {
+cudaError_t launch_prs2d(const StepParams &P, int map_kind, cudaStream_t s) {
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY), b(32, kBY);
-  return map_bf16 ? prs2d_dispatch<__nv_bfloat16>(P, g, b, s) : prs2d_dispatch<float>(P, g, b, s);
+  if (map_kind == 2) return prs2d_dispatch<IdxMaps>(P, g, b, s);
+  return map_kind ? prs2d_dispatch<DenseMaps<__nv_bfloat16>>(P, g, b, s) : prs2d_dispatch<DenseMaps<float>>(P, g, b, s);
+}
+
+}  // namespace fw2
+
+namespace fw2 {
+
+namespace {
+template <typename Maps>
+cudaError_t batched_dispatch(bool vel, const StepParams *Ps, const int4 *tiles, int n_tiles, int n_relax,
+                             int grid, cudaStream_t s) {
+  dim3 b(32, kBY);
+#define FW2_BATCH_CASE(NN)                                                                 \
+  case NN:                                                                                 \
+    if (vel) vel2d_batched<NN, Maps><<<grid, b, 0, s>>>(Ps, tiles, n_tiles);              \
+    else prs2d_batched<NN, Maps><<<grid, b, 0, s>>>(Ps, tiles, n_tiles);                  \
+    break;
+  switch (n_relax) {
+    FW2_BATCH_CASE(0)
+    FW2_BATCH_CASE(1)
+    FW2_BATCH_CASE(2)
+    FW2_BATCH_CASE(3)
+    FW2_BATCH_CASE(4)
+    default: return cudaErrorInvalidValue;
+  }
+#undef FW2_BATCH_CASE
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_batched2d(bool vel, const StepParams *Ps, const int4 *tiles, int n_tiles, int n_relax,
+                             int map_kind, int grid, cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
+  if (map_kind == 2) return batched_dispatch<IdxMaps>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
+  if (map_kind == 1) return batched_dispatch<DenseMaps<__nv_bfloat16>>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
+  return batched_dispatch<DenseMaps<float>>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
 }
 
 }  // namespace fw2

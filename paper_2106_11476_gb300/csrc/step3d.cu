@@ -27,8 +27,210 @@ __device__ __forceinline__ Win12 win12(const float *row, int tx) {
   return w;
 }
 
+
+// xy tile and plane k clear of every C-PML strip and of the outer boundary:
+// all three axes use the interior maps and no boundary rule applies.
+__device__ __forceinline__ bool interior_xy(const StepParams &P, int x0, int y0) {
+  const int Lx = P.L[0] > 4 ? P.L[0] : 4, Ly = P.L[1] > 4 ? P.L[1] : 4;
+  return x0 >= Lx && x0 + kTX + Lx <= P.nx && y0 >= Ly && y0 + kTY3 + Ly <= P.ny;
+}
+__device__ __forceinline__ bool interior_z(const StepParams &P, int k) {
+  const int Lz = P.L[2] > 4 ? P.L[2] : 4;
+  return k >= Lz && k + Lz < P.nz;
+}
+
+// Interior plane of the velocity half step: z taps first (L2), then every
+// streaming load of the plane row before any store.
 template <int N, typename MT>
-__global__ void __launch_bounds__(256) vel3d_kernel(const StepParams P) {
+__device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp)[kTX + 8],
+                                           const float (*sr)[kTX + 4], int i0, int j, int k, int tx, int ty) {
+  const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
+  const long long S = P.npts_alloc;
+  float4 Dz;
+  {
+    float4 zc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+      zc[m] = __ldg(reinterpret_cast<const float4 *>(P.p + c + (long long)(m - 3) * P.plane));
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(zc[3 + m], e) - el(zc[4 - m], e), d);
+      el(Dz, e) = d;
+    }
+  }
+  const MT *ik1 = static_cast<const MT *>(P.ik1);
+  const MT *a1 = static_cast<const MT *>(P.a1);
+  const MT *b1 = static_cast<const MT *>(P.b1);
+  const MT *rho = static_cast<const MT *>(P.rho);
+  float4 v0 = ld_state4(P.v[0], c), v1 = ld_state4(P.v[1], c), v2 = ld_state4(P.v[2], c);
+  const float4 k1 = ldmap4(ik1, c);
+  const float4 rz = ldmap4(rho, c + P.plane);
+  float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1], Q0[N > 0 ? N : 1], Q1[N > 0 ? N : 1], Q2[N > 0 ? N : 1];
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    A[nu] = ldmap4(a1, nu * S + c);
+    B[nu] = ldb4(b1, nu * S + c);
+    Q0[nu] = ld_state4(P.psi1[0], nu * S + c);
+    Q1[nu] = ld_state4(P.psi1[1], nu * S + c);
+    Q2[nu] = ld_state4(P.psi1[2], nu * S + c);
+  }
+  const int sy = ty + 3;
+  const Win12 w = win12(sp[sy], tx);
+  float4 Dx, Dy;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float d = 0.f;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m] - w.v[4 + e - m + 1], d);
+    el(Dx, e) = d;
+  }
+  {
+    float4 col[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&sp[sy - 3 + m][4 * tx + 4]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[3 + m], e) - el(col[4 - m], e), d);
+      el(Dy, e) = d;
+    }
+  }
+  const int lx = 4 * tx;
+  const float4 r0 = *reinterpret_cast<const float4 *>(&sr[ty][lx]);
+  const float r4 = sr[ty][lx + 4];
+  const float4 ru = *reinterpret_cast<const float4 *>(&sr[ty + 1][lx]);
+  float4 S0, S1, S2;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    el(S0, e) = el(Dx, e) * el(k1, e);
+    el(S1, e) = el(Dy, e) * el(k1, e);
+    el(S2, e) = el(Dz, e) * el(k1, e);
+  }
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    float4 n0, n1, n2;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el(n0, e) = fmaf(el(B[nu], e), el(Q0[nu], e), el(A[nu], e) * el(Dx, e));
+      el(n1, e) = fmaf(el(B[nu], e), el(Q1[nu], e), el(A[nu], e) * el(Dy, e));
+      el(n2, e) = fmaf(el(B[nu], e), el(Q2[nu], e), el(A[nu], e) * el(Dz, e));
+      el(S0, e) += fmaf(P.w_new, el(n0, e), P.w_old * el(Q0[nu], e));
+      el(S1, e) += fmaf(P.w_new, el(n1, e), P.w_old * el(Q1[nu], e));
+      el(S2, e) += fmaf(P.w_new, el(n2, e), P.w_old * el(Q2[nu], e));
+    }
+    st_state4(P.psi1[0], nu * S + c, n0);
+    st_state4(P.psi1[1], nu * S + c, n1);
+    st_state4(P.psi1[2], nu * S + c, n2);
+  }
+  const float rr[5] = {r0.x, r0.y, r0.z, r0.w, r4};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    el(v0, e) -= P.two_dt / (rr[e] + rr[e + 1]) * el(S0, e);
+    el(v1, e) -= P.two_dt / (rr[e] + el(ru, e)) * el(S1, e);
+    el(v2, e) -= P.two_dt / (rr[e] + el(rz, e)) * el(S2, e);
+  }
+  st_state4(P.v[0], c, v0);
+  st_state4(P.v[1], c, v1);
+  st_state4(P.v[2], c, v2);
+}
+
+// Interior plane of the pressure half step (same structure).
+template <int N, typename MT>
+__device__ __forceinline__ void prs3d_fast(const StepParams &P, const float (*svx)[kTX + 8],
+                                           const float (*svy)[kTX + 8], int i0, int j, int k, int tx, int ty) {
+  const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
+  const long long S = P.npts_alloc;
+  float4 Dz;
+  {
+    float4 zc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+      zc[m] = __ldg(reinterpret_cast<const float4 *>(P.v[2] + c + (long long)(m - 4) * P.plane));
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(zc[4 + m - 1], e) - el(zc[4 - m], e), d);
+      el(Dz, e) = d;
+    }
+  }
+  const MT *ik2 = static_cast<const MT *>(P.ik2);
+  const MT *a2 = static_cast<const MT *>(P.a2);
+  const MT *b2 = static_cast<const MT *>(P.b2);
+  const MT *Km = static_cast<const MT *>(P.K);
+  const MT *chim = static_cast<const MT *>(P.chi);
+  float4 p = ld_state4(P.p, c);
+  const float4 k2 = ldmap4(ik2, c);
+  const float4 K = ldmap4(Km, c);
+  float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (P.nl) ch = ldmap4(chim, c);
+  float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1], Q0[N > 0 ? N : 1], Q1[N > 0 ? N : 1], Q2[N > 0 ? N : 1];
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    A[nu] = ldmap4(a2, nu * S + c);
+    B[nu] = ldb4(b2, nu * S + c);
+    Q0[nu] = ld_state4(P.psi2[0], nu * S + c);
+    Q1[nu] = ld_state4(P.psi2[1], nu * S + c);
+    Q2[nu] = ld_state4(P.psi2[2], nu * S + c);
+  }
+  const Win12 w = win12(svx[ty], tx);
+  float4 Dx, Dy;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float d = 0.f;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m - 1] - w.v[4 + e - m], d);
+    el(Dx, e) = d;
+  }
+  {
+    float4 col[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&svy[ty + m][4 * tx + 4]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[4 + m - 1], e) - el(col[4 - m], e), d);
+      el(Dy, e) = d;
+    }
+  }
+  float4 S0, S1, S2;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    el(S0, e) = el(Dx, e) * el(k2, e);
+    el(S1, e) = el(Dy, e) * el(k2, e);
+    el(S2, e) = el(Dz, e) * el(k2, e);
+  }
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    float4 n0, n1, n2;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el(n0, e) = fmaf(el(B[nu], e), el(Q0[nu], e), el(A[nu], e) * el(Dx, e));
+      el(n1, e) = fmaf(el(B[nu], e), el(Q1[nu], e), el(A[nu], e) * el(Dy, e));
+      el(n2, e) = fmaf(el(B[nu], e), el(Q2[nu], e), el(A[nu], e) * el(Dz, e));
+      el(S0, e) += fmaf(P.w_new, el(n0, e), P.w_old * el(Q0[nu], e));
+      el(S1, e) += fmaf(P.w_new, el(n1, e), P.w_old * el(Q1[nu], e));
+      el(S2, e) += fmaf(P.w_new, el(n2, e), P.w_old * el(Q2[nu], e));
+    }
+    st_state4(P.psi2[0], nu * S + c, n0);
+    st_state4(P.psi2[1], nu * S + c, n1);
+    st_state4(P.psi2[2], nu * S + c, n2);
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float upd = P.dt * el(K, e) * (el(S0, e) + el(S1, e) + el(S2, e));
+    if (P.nl) upd /= fmaf(el(ch, e), el(p, e), 1.f);
+    el(p, e) -= upd;
+  }
+  st_state4(P.p, c, p);
+}
+
+template <int N, typename MT>
+__global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
   constexpr int PW = kTX + 8, PH = kTY3 + 7;  // p plane tile: x0-4.., y0-3..
   constexpr int RW = kTX + 4, RH = kTY3 + 1;  // rho plane tile: x0.., y0..
   __shared__ __align__(16) float sp[PH][PW];
@@ -39,6 +241,7 @@ __global__ void __launch_bounds__(256) vel3d_kernel(const StepParams P) {
   const MT *ik1 = static_cast<const MT *>(P.ik1);
   const int i0 = x0 + 4 * tx, j = y0 + ty;
   const bool active = i0 < P.nx && j < P.ny;
+  const bool fast_xy = interior_xy(P, x0, y0);
   const int zend = min(z0 + kTZ, P.nz);
 #pragma unroll 1
   for (int k = z0; k < zend; ++k) {
@@ -55,6 +258,10 @@ __global__ void __launch_bounds__(256) vel3d_kernel(const StepParams P) {
     }
     __syncthreads();
     if (!active) continue;
+    if (fast_xy && interior_z(P, k)) {
+      vel3d_fast<N, MT>(P, sp, sr, i0, j, k, tx, ty);
+      continue;
+    }
     const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
     const int sy = ty + 3;
     const Win12 w = win12(sp[sy], tx);
@@ -134,7 +341,7 @@ __global__ void __launch_bounds__(256) vel3d_kernel(const StepParams P) {
 }
 
 template <int N, typename MT>
-__global__ void __launch_bounds__(256) prs3d_kernel(const StepParams P) {
+__global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
   constexpr int W = kTX + 8;
   constexpr int HX = kTY3;      // v_x rows y0 .. y0+TY-1
   constexpr int HY = kTY3 + 7;  // v_y rows y0-4 .. y0+TY+2
@@ -147,6 +354,7 @@ __global__ void __launch_bounds__(256) prs3d_kernel(const StepParams P) {
   const MT *chim = static_cast<const MT *>(P.chi);
   const int i0 = x0 + 4 * tx, j = y0 + ty;
   const bool active = i0 < P.nx && j < P.ny;
+  const bool fast_xy = interior_xy(P, x0, y0);
   const int zend = min(z0 + kTZ, P.nz);
 #pragma unroll 1
   for (int k = z0; k < zend; ++k) {
@@ -161,6 +369,10 @@ __global__ void __launch_bounds__(256) prs3d_kernel(const StepParams P) {
     }
     __syncthreads();
     if (!active) continue;
+    if (fast_xy && interior_z(P, k)) {
+      prs3d_fast<N, MT>(P, svx, svy, i0, j, k, tx, ty);
+      continue;
+    }
     const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
     const Win12 w = win12(svx[ty], tx);
     float4 Dx, Dy, Dz;
@@ -242,7 +454,7 @@ cudaError_t prs3d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) 
 
 }  // namespace
 
-cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s) {
+cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s) {  // map kind 0 or 1
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kTY3);
   return map_bf16 ? vel3d_dispatch<__nv_bfloat16>(P, g, b, s) : vel3d_dispatch<float>(P, g, b, s);
 }

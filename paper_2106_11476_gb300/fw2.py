@@ -22,7 +22,7 @@ STATUS_NAMES = ["FW2_OK", "FW2_EINVAL", "FW2_ENOMEM", "FW2_ECUDA", "FW2_ESTATE",
 MEM_HOST, MEM_DEVICE = 0, 1
 BC = {"zero": 0, "periodic": 1}
 NL = {"off": 0, "pressure": 1, "westervelt": 2}
-MAP = {"f32": 0, "bf16": 1}
+MAP = {"f32": 0, "bf16": 1, "idx": 2}
 PML_READING = {"A": 0, "B": 1, "C": 2}
 MEM_ALIGN = {"centred": 0, "endpoint": 1}
 SRC_KIND = {"p": 0, "vx": 1, "vy": 2, "vz": 3}
@@ -55,6 +55,8 @@ EXPORTS = {
     "fw2_create": (C.c_int, [C.POINTER(Config), C.POINTER(C.c_void_p)]),
     "fw2_set_medium": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "fw2_set_relaxation": (C.c_int, [C.c_void_p, C.POINTER(RelaxDesc)]),
+    "fw2_set_medium_indexed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.POINTER(RelaxDesc), C.c_int32]),
     "fw2_add_source": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_int64, C.c_int64, C.c_int32]),
     "fw2_record": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
@@ -76,6 +78,12 @@ EXPORTS = {
                                    C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "fw2_field_absmax_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                            C.c_void_p]),
+    "fw2_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "fw2_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "fw2_batch_synchronize": (C.c_int, [C.c_void_p]),
+    "fw2_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "fw2_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "fw2_batch_destroy": (C.c_int, [C.c_void_p]),
     "fw2_last_error": (C.c_char_p, [C.c_void_p]),
     "fw2_abi_version": (C.c_int32, []),
 }
@@ -154,6 +162,19 @@ def fw2_set_relaxation(ctx, kappa1, kappa2, d1, alpha1, d2, alpha2):
     ptrs = [_ptr(a) for a in arrs]
     desc = RelaxDesc(*[p[0] for p in ptrs], space)
     _check(lib().fw2_set_relaxation(ctx, C.byref(desc)), ctx)
+
+
+def fw2_set_medium_indexed(ctx, tissue, n_tissue: int, c, rho, beta, kappa1, kappa2, d1, alpha1, d2, alpha2):
+    """Tissue-index medium: uint8 index per cell, per-tissue tables."""
+    tissue = np.asarray(tissue, np.uint8) if isinstance(tissue, np.ndarray) else tissue
+    tabs = [np.asarray(x, np.float32) if isinstance(x, np.ndarray) else x
+            for x in (c, rho, beta, kappa1, kappa2, d1, alpha1, d2, alpha2)]
+    space = _same_space(tissue, *tabs)
+    pt, _, kt = _ptr(tissue)
+    ptrs = [_ptr(a) for a in tabs]
+    desc = RelaxDesc(*[p[0] for p in ptrs[3:]], space)
+    _check(lib().fw2_set_medium_indexed(ctx, pt, int(n_tissue), ptrs[0][0], ptrs[1][0], ptrs[2][0],
+                                        C.byref(desc), space), ctx)
 
 
 def fw2_add_source(ctx, kind: str, idx, group, signal):
@@ -261,6 +282,40 @@ def fw2_field_absmax_noalloc(field, row_len: int, n_rows: int, row_pitch: int, o
                                           C.c_void_p(stream if stream else 0))
 
 
+def _bcheck(status: int, batch):
+    if status != OK:
+        r = lib().fw2_batch_last_error(batch)
+        raise Fw2Error(status, r.decode() if r else "")
+
+
+def fw2_batch_create(ctxs) -> int:
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    h = C.c_void_p()
+    st = lib().fw2_batch_create(arr, len(ctxs), C.byref(h))
+    if st != OK:
+        raise Fw2Error(st, "fw2_batch_create failed")
+    return h.value
+
+
+def fw2_batch_step(batch, n_steps: int):
+    _bcheck(lib().fw2_batch_step(batch, int(n_steps)), batch)
+
+
+def fw2_batch_synchronize(batch):
+    _bcheck(lib().fw2_batch_synchronize(batch), batch)
+
+
+def fw2_batch_info(batch):
+    g, o, n = C.c_int32(), C.c_int32(), C.c_int64()
+    _bcheck(lib().fw2_batch_info(batch, C.byref(g), C.byref(o), C.byref(n)), batch)
+    return g.value, o.value, n.value
+
+
+def fw2_batch_destroy(batch):
+    if batch:
+        lib().fw2_batch_destroy(batch)
+
+
 def fw2_last_error(ctx=None) -> str:
     r = lib().fw2_last_error(ctx)
     return r.decode() if r else ""
@@ -319,10 +374,18 @@ class Simulation:
         try:
             conv = (lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()) \
                 if device_inputs else (lambda a: a)
-            fw2_set_medium(self.ctx, conv(prob.c), conv(prob.rho), conv(prob.beta) if prob.nl_mode != "off" else None)
-            if prob.nrelax:
-                fw2_set_relaxation(self.ctx, conv(prob.kappa1), conv(prob.kappa2), conv(prob.d1),
-                                   conv(prob.alpha1), conv(prob.d2), conv(prob.alpha2))
+            if map_precision == "idx":
+                t = prob.tables
+                fw2_set_medium_indexed(self.ctx, conv(prob.tissue), len(t["c"]), conv(t["c"]), conv(t["rho"]),
+                                       conv(t["beta"]) if prob.nl_mode != "off" else None,
+                                       conv(t["kappa1"]), conv(t["kappa2"]), conv(t["d1"]), conv(t["alpha1"]),
+                                       conv(t["d2"]), conv(t["alpha2"]))
+            else:
+                fw2_set_medium(self.ctx, conv(prob.c), conv(prob.rho),
+                               conv(prob.beta) if prob.nl_mode != "off" else None)
+                if prob.nrelax:
+                    fw2_set_relaxation(self.ctx, conv(prob.kappa1), conv(prob.kappa2), conv(prob.d1),
+                                       conv(prob.alpha1), conv(prob.d2), conv(prob.alpha2))
             for s in prob.sources:
                 fw2_add_source(self.ctx, s.kind, conv(s.idx), conv(s.group), conv(s.signal))
             self.trace = None

@@ -1,0 +1,142 @@
+"""Continuous-batching serving loop over the C ABI.
+
+Simulation requests (2D or 3D problems with a step count) arrive over time.
+The server admits waiting requests in arrival order while their device
+footprint fits under a memory cap, keeps their state resident, and advances
+all active requests in slices: the 2D requests together as one fw2 batch
+(one persistent launch per half step for all of them, rebuilt when the set of
+active requests changes), the 3D requests each on its own stream so that
+their work overlaps on the device.  A request's result is its sensor trace;
+it leaves when its last step is done, freeing memory for waiting requests.
+Every request computes exactly what it would compute alone.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from . import fw2
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float                 # seconds after the start of the run
+    problem: object                # a problem description (synth.Problem shape)
+    steps: int
+    maps: str = "f32"
+    # filled by the server
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    trace: Optional[np.ndarray] = None
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.problem.shape))
+
+
+def footprint_bytes(prob, maps: str) -> int:
+    """Device bytes of a request: state, coefficient maps and C-PML strips."""
+    nd = len(prob.shape)
+    n = int(np.prod(prob.shape))
+    N = prob.nrelax
+    state = (1 + nd + 2 * nd * N) * 4 * n
+    if maps == "idx":
+        mp = n + 21 * 256 * 4
+    else:
+        mp = (5 + 4 * N) * (2 if maps == "bf16" else 4) * n
+    L = prob.pml_transition + prob.pml_bound
+    strips = sum(4 * N * 4 * 2 * L * n // s for s in prob.shape) if L else 0
+    return state + mp + strips
+
+
+class Server:
+    def __init__(self, cap_bytes: float = 160e9, slice_steps: int = 100,
+                 clock: Callable[[], float] = time.perf_counter):
+        self.cap = cap_bytes
+        self.slice = slice_steps
+        self.clock = clock
+        self.launch_log: List[dict] = []
+
+    def run(self, requests: List[Request]) -> List[Request]:
+        import torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        active: List[tuple] = []          # (request, Simulation, remaining, bytes)
+        used = 0.0
+        batch = None
+        batch_members: tuple = ()
+        t0 = self.clock()
+        done: List[Request] = []
+        while pending or active:
+            now = self.clock() - t0
+            # admission by footprint, in arrival order
+            while pending and pending[0].arrival <= now:
+                r = pending[0]
+                fp = footprint_bytes(r.problem, r.maps)
+                if used + fp > self.cap and active:
+                    break
+                pending.pop(0)
+                stream = torch.cuda.Stream() if len(r.problem.shape) == 3 else torch.cuda.current_stream()
+                sim = fw2.Simulation(r.problem, map_precision=r.maps, stream=stream)
+                r.admitted = self.clock() - t0
+                active.append((r, sim, r.steps, fp))
+                used += fp
+            if not active:
+                if pending:
+                    wait = pending[0].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                continue
+            two = [a for a in active if len(a[0].problem.shape) == 2]
+            three = [a for a in active if len(a[0].problem.shape) == 3]
+            n2 = min([a[2] for a in two], default=0)
+            step2 = min(self.slice, n2) if two else 0
+            members = tuple(a[0].rid for a in two)
+            if two and members != batch_members:
+                if batch is not None:
+                    fw2.fw2_batch_destroy(batch)
+                batch = fw2.fw2_batch_create([a[1].ctx for a in two])
+                batch_members = members
+            if two and step2 > 0:
+                fw2.fw2_batch_step(batch, step2)
+            steps3 = []
+            for a in three:
+                k = min(self.slice, a[2])
+                a[1].step(k)
+                steps3.append(k)
+            if two:
+                fw2.fw2_batch_synchronize(batch)
+            for a in three:
+                a[1].synchronize()
+            self.launch_log.append({"t": self.clock() - t0, "n2d": len(two), "n3d": len(three), "steps2d": step2})
+            # bookkeeping
+            new_active = []
+            i3 = 0
+            for a in active:
+                r, sim, rem, fp = a
+                if len(r.problem.shape) == 2:
+                    rem -= step2
+                else:
+                    rem -= steps3[i3]
+                    i3 += 1
+                if rem <= 0:
+                    r.trace = sim.trace.cpu().numpy() if sim.trace is not None else None
+                    r.finished = self.clock() - t0
+                    sim.close()
+                    used -= fp
+                    done.append(r)
+                else:
+                    new_active.append((r, sim, rem, fp))
+            active = new_active
+        if batch is not None:
+            fw2.fw2_batch_destroy(batch)
+        return done
+
+
+def latency_stats(reqs: List[Request]) -> dict:
+    ttr = np.array([r.finished - r.arrival for r in reqs])
+    return {"p50_s": float(np.percentile(ttr, 50)), "p99_s": float(np.percentile(ttr, 99)),
+            "mean_s": float(ttr.mean()), "n": len(reqs)}

@@ -85,6 +85,10 @@ class Problem:
     sensors: Optional[Sensors] = None
     n_steps: int = 0
     name: str = ""
+    # tissue-index form of the same medium (optional): uint8 index per cell
+    # and per-tissue tables; the dense arrays above are these tables gathered
+    tissue: Optional[np.ndarray] = None
+    tables: Optional[dict] = None
 
     @property
     def ndim(self) -> int:
@@ -135,7 +139,7 @@ def random_sensors(shape: Sequence[int], n: int, margin: int, rng: np.random.Gen
 
 def _fill_relaxation(prob: Problem, tissue_of: np.ndarray, sets: List[dict],
                      alpha0_map: Optional[np.ndarray] = None) -> None:
-    """Per-point relaxation parameters from per-tissue parameter sets.
+    """Per-point relaxation parameters from per-tissue parameter sets (float32).
 
     When `alpha0_map` is given, d^{nu=1} of each point is scaled by
     alpha0(x) / alpha0_ref of its tissue set: the paper's modulation rule for
@@ -144,23 +148,25 @@ def _fill_relaxation(prob: Problem, tissue_of: np.ndarray, sets: List[dict],
     """
     N = len(sets[0]["d1"])
     g = tissue_of.shape
-    k1 = np.empty(g, np.float64); k2 = np.empty(g, np.float64)
-    d1 = np.empty((N,) + g, np.float64); a1 = np.empty_like(d1)
+    k1 = np.empty(g, np.float32); k2 = np.empty(g, np.float32)
+    d1 = np.empty((N,) + g, np.float32); a1 = np.empty_like(d1)
     d2 = np.empty_like(d1); a2 = np.empty_like(d1)
-    for t, s in enumerate(sets):
-        m = tissue_of == t
-        k1[m] = s["kappa1"]; k2[m] = s["kappa2"]
-        for nu in range(N):
-            d1[nu][m] = s["d1"][nu]; a1[nu][m] = s["alpha1"][nu]
-            d2[nu][m] = s["d2"][nu]; a2[nu][m] = s["alpha2"][nu]
-        if alpha0_map is not None:
-            scale = alpha0_map[m] / s["alpha0"]
-            d1[0][m] *= scale
-            d2[0][m] *= scale
+    lut = lambda key, nu=None: np.asarray([s[key] if nu is None else s[key][nu] for s in sets], np.float64)
+    flat_t = tissue_of.reshape(-1)
+    def put(dst, values):
+        dst.reshape(-1)[:] = values.astype(np.float32)[flat_t]
+    put(k1, lut("kappa1")); put(k2, lut("kappa2"))
+    for nu in range(N):
+        put(d1[nu], lut("d1", nu)); put(a1[nu], lut("alpha1", nu))
+        put(d2[nu], lut("d2", nu)); put(a2[nu], lut("alpha2", nu))
+    if alpha0_map is not None:
+        ref = lut("alpha0").astype(np.float32)[flat_t].reshape(g)
+        scale = np.asarray(alpha0_map, np.float32) / ref
+        d1[0] *= scale
+        d2[0] *= scale
     prob.nrelax = N
-    prob.kappa1 = k1.astype(np.float32); prob.kappa2 = k2.astype(np.float32)
-    prob.d1 = d1.astype(np.float32); prob.alpha1 = a1.astype(np.float32)
-    prob.d2 = d2.astype(np.float32); prob.alpha2 = a2.astype(np.float32)
+    prob.kappa1, prob.kappa2 = k1, k2
+    prob.d1, prob.alpha1, prob.d2, prob.alpha2 = d1, a1, d2, a2
 
 
 def table2_set() -> dict:
@@ -298,8 +304,9 @@ def abdominal_problem(n: int = 4096, n_steps: int = 8000, seed: int = 1,
     rho[sy[keep], sx[keep]] *= pert[keep]
     sets_all = relaxation_sets()
     sets = [sets_all["N4_y1.1_fat"], sets_all["N4_y1.1_muscle"], sets_all["N4_y1.1_connective"]]
-    c_max = float(c.max())
-    dt = cfl * h / c_max
+    # time step at `cfl` of the fastest high-frequency speed c / sqrt(kappa1 kappa2)
+    kmin = min(s["kappa1"] * s["kappa2"] for s in sets)
+    dt = cfl * h * math.sqrt(kmin) / float(c.max())
     prob = Problem(shape=(nx, ny), h=h, dt=dt, c=c.astype(np.float32), rho=rho.astype(np.float32),
                    beta=beta if nl != "off" else None)
     _fill_relaxation(prob, tissue, sets, alpha0_map=alpha0)
@@ -335,26 +342,26 @@ def abdominal_problem(n: int = 4096, n_steps: int = 8000, seed: int = 1,
 
 
 def _value_noise_3d(shape: Tuple[int, int, int], cell: int, rng: np.random.Generator) -> np.ndarray:
-    """Smooth seeded noise in [0, 1): trilinear interpolation of a random lattice."""
+    """Smooth seeded noise in [0, 1): trilinear interpolation of a random
+    lattice (smoothstep weights), built one z plane at a time in float32."""
     nz, ny, nx = shape
-    lz, ly, lx = nz // cell + 2, ny // cell + 2, nx // cell + 2
-    lat = rng.random((lz, ly, lx))
+    lat = rng.random((nz // cell + 2, ny // cell + 2, nx // cell + 2)).astype(np.float32)
     def coords(n):
         u = np.arange(n) / cell
         i0 = np.floor(u).astype(np.int64)
-        f = u - i0
-        f = f * f * (3 - 2 * f)
-        return i0, f
+        f = (u - i0).astype(np.float32)
+        return i0, f * f * (3 - 2 * f)
     iz, fz = coords(nz); iy, fy = coords(ny); ix, fx = coords(nx)
-    out = np.zeros(shape, np.float32)
-    for dz in (0, 1):
-        wz = (fz if dz else 1 - fz)[:, None, None]
-        for dy in (0, 1):
-            wy = (fy if dy else 1 - fy)[None, :, None]
-            for dx in (0, 1):
-                wx = (fx if dx else 1 - fx)[None, None, :]
-                out += (lat[(iz + dz)[:, None, None], (iy + dy)[None, :, None], (ix + dx)[None, None, :]]
-                        * wz * wy * wx).astype(np.float32)
+    out = np.empty(shape, np.float32)
+    for z in range(nz):
+        acc = np.zeros((ny, nx), np.float32)
+        for dz, wz in ((0, 1 - fz[z]), (1, fz[z])):
+            layer = lat[iz[z] + dz]
+            for dy, wy in ((0, 1 - fy), (1, fy)):
+                rows = layer[iy + dy]                      # (ny, lx)
+                for dx, wx in ((0, 1 - fx), (1, fx)):
+                    acc += (wz * wy[:, None] * wx[None, :]) * rows[:, ix + dx]
+        out[z] = acc
     return out
 
 
@@ -372,14 +379,17 @@ def skull_problem(n: int = 768, n_steps: int = 4000, seed: int = 2, f0: float = 
     rng = np.random.default_rng(seed)
     h = 1540.0 / f0 / ppw
     g = (n, n, n)
-    z, y, x = np.meshgrid(*(np.arange(n, dtype=np.float32) - (n - 1) / 2.0,) * 3, indexing="ij")
     span = (n - 2 * pml_cells) * h * 1e3 * 0.5  # mm radius available
     scale = min(1.0, span / 55.0)
     ax = np.array([50.0, 45.0, 40.0]) * scale
     thick = 1.0 + rng.random() * 1.0
-    r = np.sqrt((x * h * 1e3 / ax[0]) ** 2 + (y * h * 1e3 / ax[1]) ** 2 + (z * h * 1e3 / ax[2]) ** 2)
-    shell = (r >= 1.0) & (r < 1.0 + thick / ax.min())
-    del x, y, z, r
+    coord = (np.arange(n, dtype=np.float32) - (n - 1) / 2.0) * np.float32(h * 1e3)
+    rx2 = (coord / ax[0]) ** 2
+    ry2 = (coord / ax[1]) ** 2
+    shell = np.empty(g, bool)
+    for z in range(n):
+        r = np.sqrt(rx2[None, :] + ry2[:, None] + (coord[z] / ax[2]) ** 2)
+        shell[z] = (r >= 1.0) & (r < 1.0 + thick / ax.min())
     phi = _value_noise_3d(g, max(4, n // 48), rng)
     c = np.full(g, 1560.0, np.float32)
     rho = np.full(g, 1040.0, np.float32)
@@ -387,11 +397,14 @@ def skull_problem(n: int = 768, n_steps: int = 4000, seed: int = 2, f0: float = 
     c[shell] = 2400.0 + 600.0 * phi[shell]
     rho[shell] = 1700.0 + 300.0 * phi[shell]
     alpha0[shell] = 4.0 + 4.0 * phi[shell]
-    tissue = np.zeros(g, np.int32)
-    tissue[shell] = 1
+    del phi
+    tissue = shell.astype(np.uint8)
+    del shell
     sets_all = relaxation_sets()
     sets = [sets_all["N3_y1.2_brain"], sets_all["N3_y1.2_skull"]]
-    dt = cfl * h / float(c.max())
+    # time step at `cfl` of the fastest high-frequency speed c / sqrt(kappa1 kappa2)
+    kmin = min(s["kappa1"] * s["kappa2"] for s in sets)
+    dt = cfl * h * math.sqrt(kmin) / float(c.max())
     prob = Problem(shape=g, h=h, dt=dt, c=c, rho=rho)
     _fill_relaxation(prob, tissue, sets, alpha0_map=alpha0)
     prob.pml_transition = pml_cells * 3 // 4
@@ -425,38 +438,40 @@ def skull_problem(n: int = 768, n_steps: int = 4000, seed: int = 2, f0: float = 
 # states
 # ----------------------------------------------------------------------------
 
-def random_state(prob: Problem, seed: int, amp_p: float = 1.0e5, n_waves: int = 6) -> dict:
-    """Smooth seeded fields for every state array (p, v_q, psi1_q, psi2_q).
+def random_state(prob: Problem, seed: int, amp_p: float = 1.0e5, n_waves: int = 6,
+                 memory: bool = True) -> dict:
+    """Smooth seeded fields for the state arrays (p, v_q and, with `memory`,
+    psi1_q, psi2_q), float32.
 
     Each field is a sum of `n_waves` random plane waves with wavelengths of
     at least 8 cells, so the state looks like a propagating wavefield rather
     than white noise.  Velocities are scaled by 1/(rho c), memory variables by
-    a small random factor.  Returns float32 arrays keyed by state name.
+    a small factor.
     """
     rng = np.random.default_rng(seed)
     g = prob.grid_shape
-    axes = [np.arange(s, dtype=np.float64) for s in g]
-    def field():
-        out = np.zeros(g, np.float64)
+    axes = [np.arange(s, dtype=np.float32) for s in g]
+    def field(scale):
+        out = np.zeros(g, np.float32)
         for _ in range(n_waves):
             kvec = rng.uniform(-1.0, 1.0, len(g)) * (2 * math.pi / 8.0)
             ph = rng.uniform(0, 2 * math.pi)
             a = rng.standard_normal()
-            arg = ph
+            arg = np.float32(ph)
             for d, ax in enumerate(axes):
                 shape = [1] * len(g); shape[d] = g[d]
-                arg = arg + kvec[d] * ax.reshape(shape)
-            out += a * np.sin(arg)
+                arg = arg + (np.float32(kvec[d]) * ax).reshape(shape)
+            out += np.float32(a * scale) * np.sin(arg)
         return out
-    st = {"p": (amp_p * field()).astype(np.float32)}
+    st = {"p": field(amp_p)}
     vscale = amp_p / (1000.0 * 1540.0)
     N = prob.nrelax
     names = "xyz"
     for q in range(prob.ndim):
-        st["v" + names[q]] = (vscale * field()).astype(np.float32)
-        if N:
-            st["psi1" + names[q]] = np.stack([(0.01 * amp_p / prob.h * 1e-3 * field()).astype(np.float32) for _ in range(N)])
-            st["psi2" + names[q]] = np.stack([(0.01 * vscale / prob.h * 1e-3 * field()).astype(np.float32) for _ in range(N)])
+        st["v" + names[q]] = field(vscale)
+        if N and memory:
+            st["psi1" + names[q]] = np.stack([field(0.01 * amp_p / prob.h * 1e-3) for _ in range(N)])
+            st["psi2" + names[q]] = np.stack([field(0.01 * vscale / prob.h * 1e-3) for _ in range(N)])
     return st
 
 
@@ -469,3 +484,121 @@ def with_steps(prob: Problem, n_steps: int) -> Problem:
             sig = np.concatenate([sig, np.zeros((n_steps - sig.shape[0], sig.shape[1]), np.float32)])
         srcs.append(replace(s, signal=np.ascontiguousarray(sig)))
     return replace(prob, sources=srcs, n_steps=n_steps)
+
+
+# Tissue classes of the tissue-index abdominal medium: (name, c, rho, alpha0,
+# beta, relaxation set).  beta is one value per class in this form.
+INDEXED_TISSUES = [
+    ("water", 1540.0, 1000.0, 0.02, 3.5, "N4_y1.1_fat"),
+    ("fat", 1478.0, 950.0, 0.48, 6.0, "N4_y1.1_fat"),
+    ("muscle", 1547.0, 1050.0, 1.09, 4.6, "N4_y1.1_muscle"),
+    ("connective", 1613.0, 1120.0, 1.57, 5.0, "N4_y1.1_connective"),
+]
+LEVELS = 64   # quantised scatterer levels per class; level 0 is unperturbed
+
+
+def indexed_abdominal_problem(nx: int = 2048, ny: int = 1024, n_steps: int = 4000, seed: int = 1,
+                              f0: float = 3e6, ppw: float = 12.0, cfl: float = 0.4,
+                              n_elements: int = 64, focus_mm: float = 30.0, focus_x_mm: float = 0.0,
+                              nl: str = "pressure",
+                              scatterers_per_cell: float = 20.0,
+                              pml_lambda: Tuple[float, float] = (3.0, 1.0), transmit: int = -1) -> Problem:
+    """Abdominal-wall-like medium in tissue-index form (reduced storage).
+
+    Layered fat / muscle / connective tissue under a water coupling layer as
+    in `abdominal_problem`, with one beta per tissue class, and sub-resolution
+    scatterers whose +-2 % c / rho perturbation is quantised to 63 levels: each
+    cell stores index = class * 64 + level into per-entry tables.  The dense
+    per-cell arrays are the tables gathered.  `transmit` >= 0 fires only that
+    element (a full-synthetic-aperture transmit event); -1 fires the focused
+    array, focused at depth `focus_mm` and lateral offset `focus_x_mm` from
+    the array centre.
+    """
+    rng = np.random.default_rng(seed)
+    h = 1540.0 / f0 / ppw
+    lt = int(round(pml_lambda[0] * ppw)); lb = int(round(pml_lambda[1] * ppw))
+    L = lt + lb
+    y_mm = (np.arange(ny) * h) * 1e3
+    x_mm = (np.arange(nx) * h) * 1e3
+    top = (L + 8) * h * 1e3
+    cls = np.zeros((ny, nx), np.uint8)
+    depth = top
+    surface_prev = np.full(nx, top)
+    Y = y_mm[:, None]
+    while depth < y_mm[-1]:
+        kind = int(rng.integers(1, 4))
+        depth += rng.uniform(2.0, 5.0)
+        amp = rng.uniform(0.0, 0.5 / 8, 8); k = rng.uniform(0.2, 2.0, 8); ph = rng.uniform(0, 2 * math.pi, 8)
+        surface = depth + (amp[:, None] * np.sin(k[:, None] * x_mm[None, :] + ph[:, None])).sum(0)
+        m = (Y >= surface_prev[None, :]) & (Y < surface[None, :])
+        cls[m] = kind
+        surface_prev = surface
+    cls[Y >= surface_prev[None, :]] = 1
+    cls[np.broadcast_to(Y < top, (ny, nx))] = 0
+    level = np.zeros((ny, nx), np.uint8)
+    n_sc = int(scatterers_per_cell / (ppw * ppw) * nx * ny)
+    sy = rng.integers(0, ny, n_sc); sx = rng.integers(0, nx, n_sc)
+    pert = np.clip(0.02 * rng.standard_normal(n_sc), -0.0799, 0.0799)
+    lv = (np.round((pert + 0.08) / 0.16 * 62) + 1).astype(np.uint8)      # 1..63
+    keep = cls[sy, sx] != 0
+    level[sy[keep], sx[keep]] = lv[keep]
+    tissue = (cls.astype(np.uint16) * LEVELS + level).astype(np.uint8)
+    sets_all = relaxation_sets()
+    T = len(INDEXED_TISSUES) * LEVELS
+    tab = {k: np.zeros(T, np.float32) for k in ("c", "rho", "beta", "kappa1", "kappa2")}
+    N = len(sets_all["N4_y1.1_fat"]["d1"])
+    for k in ("d1", "alpha1", "d2", "alpha2"):
+        tab[k] = np.zeros((N, T), np.float32)
+    for ci, (name, c0, r0, a0, beta, key) in enumerate(INDEXED_TISSUES):
+        sset = sets_all[key]
+        for lvl in range(LEVELS):
+            e = ci * LEVELS + lvl
+            f = 1.0 if lvl == 0 else 1.0 + (-0.08 + (lvl - 1) / 62 * 0.16)
+            tab["c"][e] = c0 * f; tab["rho"][e] = r0 * f; tab["beta"][e] = beta
+            tab["kappa1"][e] = sset["kappa1"]; tab["kappa2"][e] = sset["kappa2"]
+            for nu in range(N):
+                mod = a0 / sset["alpha0"] if nu == 0 else 1.0
+                tab["d1"][nu, e] = sset["d1"][nu] * mod; tab["alpha1"][nu, e] = sset["alpha1"][nu]
+                tab["d2"][nu, e] = sset["d2"][nu] * mod; tab["alpha2"][nu, e] = sset["alpha2"][nu]
+    used_sets = [sets_all[t[5]] for t in INDEXED_TISSUES]
+    kmin = min(s_["kappa1"] * s_["kappa2"] for s_ in used_sets)
+    dt = cfl * h * math.sqrt(kmin) / float(tab["c"].max())
+    ti = tissue.astype(np.int64)
+    prob = Problem(shape=(nx, ny), h=h, dt=dt, c=tab["c"][ti], rho=tab["rho"][ti],
+                   beta=tab["beta"][ti] if nl != "off" else None)
+    prob.nrelax = N
+    prob.kappa1 = tab["kappa1"][ti]; prob.kappa2 = tab["kappa2"][ti]
+    prob.d1 = tab["d1"][:, ti]; prob.alpha1 = tab["alpha1"][:, ti]
+    prob.d2 = tab["d2"][:, ti]; prob.alpha2 = tab["alpha2"][:, ti]
+    prob.tissue = tissue
+    prob.tables = tab
+    prob.pml_transition, prob.pml_bound = lt, lb
+    prob.nl_mode = nl
+    pitch, width = 12, 11
+    aperture = n_elements * pitch
+    x0 = max(L, (nx - aperture) // 2)
+    row = L + 4
+    el_x0 = x0 + pitch * np.arange(n_elements)
+    idx, grp = [], []
+    for e in range(n_elements):
+        xs = np.arange(el_x0[e], el_x0[e] + width)
+        xs = xs[(xs >= L) & (xs < nx - L)]
+        idx.append(flat_index((nx, ny), xs, row)); grp.append(np.full(xs.size, e, np.int32))
+    idx = np.concatenate(idx); grp = np.concatenate(grp)
+    t = (np.arange(n_steps) + 1.0) * dt
+    tau = 3.0 / (2.0 * f0); t0 = 3.0 / f0
+    if transmit >= 0:
+        delays = np.full(n_elements, np.inf); delays[transmit % n_elements] = 0.0
+    else:
+        centre_mm = (x0 + aperture / 2) * h * 1e3 + focus_x_mm
+        el_mm = (el_x0 + width / 2) * h * 1e3
+        dist = np.sqrt((el_mm - centre_mm) ** 2 + focus_mm ** 2)
+        delays = (dist.max() - dist) / 1540.0 * 1e-3
+    tt = t[:, None] - t0 - np.where(np.isfinite(delays), delays, 0.0)[None, :]
+    sig = 1.0e6 * np.exp(-(tt / tau) ** 2) * np.sin(2 * math.pi * f0 * tt)
+    sig[:, ~np.isfinite(delays)] = 0.0
+    prob.sources = [Source("p", idx, grp, sig.astype(np.float32))]
+    prob.sensors = Sensors(idx=idx.copy(), group=grp.copy(), n_groups=n_elements)
+    prob.n_steps = n_steps
+    prob.name = f"2d-abdominal-indexed-{nx}x{ny}"
+    return prob

@@ -516,3 +516,13 @@ def test_transition_layer_keeps_multiple_relaxation_cpml_stable():
     assert good[-1] < 1e-3 * good[0] and np.all(np.diff(good[2:]) < 0)
     bad = _long_run_peaks(keep_higher=True)
     assert bad[-1] > 10 * bad.min()
+
+
+def test_bf16_storage_rounding_equals_torch():
+    """The oracle's model of bf16 coefficient maps rounds exactly as torch's
+    float32 -> bfloat16 conversion (round to nearest even) does."""
+    import torch
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(200000) * np.exp(rng.uniform(-40, 40, 200000))
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cf.to_bf16(x), ref)
