@@ -2,7 +2,8 @@
 //
 // Same arithmetic as the 2D kernels (Sec. 3.1 updates, Eqs. relaxation4,
 // relaxation_psi, general6) with the third axis.  Each block owns a 128 x 8
-// tile of an xy plane and marches through kTZ planes along z; the xy stencil
+// tile of an xy plane (256 threads, two rows each) and marches through kTZ
+// planes along z; the xy stencil
 // operand of the current plane is staged in shared memory with its halo, the
 // z taps of each cell's own column are read through L2.
 #include "coef.cuh"
@@ -11,7 +12,8 @@ namespace fw2 {
 
 namespace {
 
-constexpr int kTY3 = 8;   // tile rows (one per thread row)
+constexpr int kTY3 = 16;  // tile rows (two per thread row)
+constexpr int kBY3 = 8;   // thread rows
 constexpr int kTZ = 8;    // planes per block
 
 struct Win12 {
@@ -239,8 +241,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const MT *rho = static_cast<const MT *>(P.rho);
   const MT *ik1 = static_cast<const MT *>(P.ik1);
-  const int i0 = x0 + 4 * tx, j = y0 + ty;
-  const bool active = i0 < P.nx && j < P.ny;
+  const int i0 = x0 + 4 * tx;
   const bool fast_xy = interior_xy(P, x0, y0);
   const int zend = min(z0 + kTZ, P.nz);
 #pragma unroll 1
@@ -257,13 +258,16 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
       sr[r][cc] = ldmap(rho, (long long)k * P.plane + (long long)gy * P.pitch + gx);
     }
     __syncthreads();
-    if (!active) continue;
+#pragma unroll 1
+    for (int rr = 0; rr < kTY3 / kBY3; ++rr) {
+    const int ly = ty + rr * kBY3, j = y0 + ly;
+    if (i0 >= P.nx || j >= P.ny) continue;
     if (fast_xy && interior_z(P, k)) {
-      vel3d_fast<N, MT>(P, sp, sr, i0, j, k, tx, ty);
+      vel3d_fast<N, MT>(P, sp, sr, i0, j, k, tx, ly);
       continue;
     }
     const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
-    const int sy = ty + 3;
+    const int sy = ly + 3;
     const Win12 w = win12(sp[sy], tx);
     float4 Dx, Dy, Dz;
 #pragma unroll
@@ -301,9 +305,9 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
     float4 bx, by, bz;
     {
       const int lx = 4 * tx;
-      const float4 r0 = *reinterpret_cast<const float4 *>(&sr[ty][lx]);
-      const float r4 = sr[ty][lx + 4];
-      const float4 ru = *reinterpret_cast<const float4 *>(&sr[ty + 1][lx]);
+      const float4 r0 = *reinterpret_cast<const float4 *>(&sr[ly][lx]);
+      const float r4 = sr[ly][lx + 4];
+      const float4 ru = *reinterpret_cast<const float4 *>(&sr[ly + 1][lx]);
       const int kz = rho_coord(k + 1, P.nz, P.periodic[2]);
       float4 rz;
 #pragma unroll
@@ -337,6 +341,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
       v.x -= bz.x * S.x; v.y -= bz.y * S.y; v.z -= bz.z * S.z; v.w -= bz.w * S.w;
       st_state4(P.v[2], c, mask_pad(v, i0, P.nx));
     }
+    }
   }
 }
 
@@ -352,8 +357,7 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
   const MT *ik2 = static_cast<const MT *>(P.ik2);
   const MT *Km = static_cast<const MT *>(P.K);
   const MT *chim = static_cast<const MT *>(P.chi);
-  const int i0 = x0 + 4 * tx, j = y0 + ty;
-  const bool active = i0 < P.nx && j < P.ny;
+  const int i0 = x0 + 4 * tx;
   const bool fast_xy = interior_xy(P, x0, y0);
   const int zend = min(z0 + kTZ, P.nz);
 #pragma unroll 1
@@ -368,13 +372,16 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
       *reinterpret_cast<float4 *>(&svy[r][4 * c4]) = load_chunk(P, P.v[1], x0 - 4 + 4 * c4, y0 - 4 + r, k);
     }
     __syncthreads();
-    if (!active) continue;
+#pragma unroll 1
+    for (int rr = 0; rr < kTY3 / kBY3; ++rr) {
+    const int ly = ty + rr * kBY3, j = y0 + ly;
+    if (i0 >= P.nx || j >= P.ny) continue;
     if (fast_xy && interior_z(P, k)) {
-      prs3d_fast<N, MT>(P, svx, svy, i0, j, k, tx, ty);
+      prs3d_fast<N, MT>(P, svx, svy, i0, j, k, tx, ly);
       continue;
     }
     const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
-    const Win12 w = win12(svx[ty], tx);
+    const Win12 w = win12(svx[ly], tx);
     float4 Dx, Dy, Dz;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
     {
       float4 col[8];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&svy[ty + m][4 * tx + 4]);
+      for (int m = 0; m < 8; ++m) col[m] = *reinterpret_cast<const float4 *>(&svy[ly + m][4 * tx + 4]);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         float d = 0.f;
@@ -423,6 +430,7 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
     }
     p.x -= upd.x; p.y -= upd.y; p.z -= upd.z; p.w -= upd.w;
     st_state4(P.p, c, mask_pad(p, i0, P.nx));
+    }
   }
 }
 
@@ -455,12 +463,12 @@ cudaError_t prs3d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) 
 }  // namespace
 
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s) {  // map kind 0 or 1
-  dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kTY3);
+  dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kBY3);
   return map_bf16 ? vel3d_dispatch<__nv_bfloat16>(P, g, b, s) : vel3d_dispatch<float>(P, g, b, s);
 }
 
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s) {
-  dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kTY3);
+  dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kBY3);
   return map_bf16 ? prs3d_dispatch<__nv_bfloat16>(P, g, b, s) : prs3d_dispatch<float>(P, g, b, s);
 }
 

@@ -1,0 +1,74 @@
+"""Physics checks of the GPU path against the paper's printed figures
+(the GPU path itself is pinned to the oracle by the parity tests)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+THETAS = (0, 20, 45, 60, 70, 80)
+
+
+@pytest.fixture(scope="module")
+def fw2(fw2lib):
+    from paper_2106_11476_gb300 import fw2 as m
+    return m
+
+
+def _reflection_2d(fw2, reading="C", ppw=16, cfl=0.2, d=24, margin=220, relax=None):
+    """Reflection [dB] of the right boundary for incidence angles THETAS: a
+    point source at distance d from the inner edge of the right C-PML; the
+    reflected wave is |p_test - p_ref| at a sensor at the same depth, offset
+    laterally by 2 d tan(theta); it is normalised by the direct wave of the
+    reference run at the same path length 2 d / cos(theta).  Every other
+    boundary (and every boundary of the reference) is far enough that its
+    reflection arrives after the time window."""
+    relax = relax or synth.TABLE2
+    f0, c0 = 1e6, 1540.0
+    h = c0 / f0 / ppw
+    LT, LB = 3 * ppw, 1 * ppw
+    L = LT + LB
+    keff = math.sqrt(float(np.float32(relax["kappa1"])) * float(np.float32(relax["kappa2"])))
+    dt = cfl * h / (c0 / keff)
+    rmax = max(2 * d / math.cos(math.radians(t)) for t in THETAS)
+    ymax = max(2 * d * math.tan(math.radians(t)) for t in THETAS)
+    window = rmax + 8 * ppw
+    steps = int(window / cfl) + int(3 / f0 / dt)
+    sig = synth.gaussian_pulse(steps, dt, f0, 3.0, 1.0)
+
+    def run(nx, ny, xs, ys):
+        p = synth.homogeneous((nx, ny), h, dt, c=c0, rho=1000.0, relax=relax)
+        p.pml_transition, p.pml_bound, p.pml_reading = LT, LB, reading
+        p.sources = [synth.Source("p", synth.flat_index((nx, ny), [xs], [ys]), np.zeros(1, np.int32),
+                                  sig[:, None])]
+        idx = []
+        for t in THETAS:
+            idx.append(synth.flat_index((nx, ny), [xs], [ys + int(round(2 * d * math.tan(math.radians(t))))])[0])
+            idx.append(synth.flat_index((nx, ny), [xs - int(round(2 * d / math.cos(math.radians(t))))], [ys])[0])
+        p.sensors = synth.Sensors(np.array(idx), np.arange(len(idx), dtype=np.int32), len(idx))
+        p.n_steps = steps
+        s = fw2.Simulation(p)
+        s.step(steps)
+        tr = s.trace.cpu().numpy().astype(np.float64)
+        s.close()
+        return tr
+    nx = L + margin + int(rmax) + d + L
+    ny = L + margin + int(ymax) + margin + L
+    xs, ys = nx - L - d, L + margin
+    test = run(nx, ny, xs, ys)
+    ref = run(nx + 2 * margin, ny + 2 * margin, xs + margin, ys + margin)
+    out = []
+    for i in range(len(THETAS)):
+        out.append(20 * math.log10(np.max(np.abs(test[:, 2 * i] - ref[:, 2 * i])) / np.max(np.abs(ref[:, 2 * i + 1]))))
+    return out
+
+
+def test_cpml_reflection_below_paper_bound_at_all_angles(fw2):
+    """Sec. 4.3: the two-stage C-PML (3 + 1 wavelengths) stays below about
+    -49 dB for incidence from 0 to 80 degrees (16 PPW, CFL 0.2, Table 2 tissue)."""
+    r = _reflection_2d(fw2)
+    print("reflection dB by angle", dict(zip(THETAS, [round(x, 1) for x in r])))
+    assert max(r) < -49.0, r
