@@ -76,6 +76,11 @@ enum { FW2_PML_A = 0, FW2_PML_B = 1, FW2_PML_C = 2 };
  * the mean of the memory variable before and after its update (D^{n-1/2}
  * estimated by (D^n + D^{n-1}) / 2); ENDPOINT uses the updated value. */
 enum { FW2_MEM_CENTRED = 0, FW2_MEM_ENDPOINT = 1 };
+/* kernel path of the 2D half steps (bitwise the same results on every path):
+ * TILE runs one block per 128 x 16 tile; PIPE runs the persistent kernels
+ * that stage the interior through shared memory (float or tissue-index maps;
+ * TILE elsewhere); AUTO picks the faster of the two for the map storage */
+enum { FW2_PATH_AUTO = 0, FW2_PATH_TILE = 1, FW2_PATH_PIPE = 2 };
 enum { FW2_SRC_P = 0, FW2_SRC_VX = 1, FW2_SRC_VY = 2, FW2_SRC_VZ = 3 };
 enum {
   FW2_FIELD_P = 0, FW2_FIELD_VX = 1, FW2_FIELD_VY = 2, FW2_FIELD_VZ = 3,
@@ -104,7 +109,7 @@ typedef struct {
   int32_t nl_mode;       /* FW2_NL_* */
   int32_t mem_alignment; /* FW2_MEM_CENTRED (default) or FW2_MEM_ENDPOINT */
   int32_t bc[3];         /* FW2_BC_* per axis */
-  int32_t reserved_;
+  int32_t kernel_path;   /* FW2_PATH_AUTO (default), FW2_PATH_TILE or FW2_PATH_PIPE */
   void *stream;          /* cudaStream_t, borrowed; NULL = default stream */
 } fw2_config;
 

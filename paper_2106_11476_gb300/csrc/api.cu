@@ -225,6 +225,8 @@ fw2_status finalize(fw2_ctx *c) {
   P.a1 = Q.a1; P.b1 = Q.b1; P.a2 = Q.a2; P.b2 = Q.b2;
   P.tissue = Q.tissue_out;
   P.table = Q.table_out;
+  c->pipe = c->nd == 2 && ((cfg.kernel_path == FW2_PATH_AUTO && pipe2d_preferred(P, c->map_kind)) ||
+                            (cfg.kernel_path == FW2_PATH_PIPE && pipe2d_supported(P, c->map_kind)));
   c->finalized = true;
   return FW2_OK;
 }
@@ -400,6 +402,8 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
   if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_WESTERVELT) return fail(nullptr, FW2_EINVAL, "bad nl_mode");
   if (cfg.mem_alignment != FW2_MEM_CENTRED && cfg.mem_alignment != FW2_MEM_ENDPOINT)
     return fail(nullptr, FW2_EINVAL, "bad mem_alignment");
+  if (cfg.kernel_path != FW2_PATH_AUTO && cfg.kernel_path != FW2_PATH_TILE && cfg.kernel_path != FW2_PATH_PIPE)
+    return fail(nullptr, FW2_EINVAL, "bad kernel_path");
   for (int q = 0; q < 3; ++q)
     if (cfg.bc[q] != FW2_BC_ZERO && cfg.bc[q] != FW2_BC_PERIODIC) return fail(nullptr, FW2_EINVAL, "bad bc[%d]", q);
   bool taps_zero = true;
@@ -440,6 +444,7 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
   c->n_pts = (long long)c->nx * c->ny * c->nz;
   c->stream = (cudaStream_t)cfg.stream;
   c->map_kind = cfg.map_precision;
+  c->n_sm = prop.multiProcessorCount;
   // state: p, v_q, psi1_q[N], psi2_q[N]
   const size_t arr = align256(sizeof(float) * (size_t)c->npts_alloc);
   const int n_arrays = 1 + c->nd + 2 * c->nd * c->N;
@@ -668,7 +673,8 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
       ev = {take_event(c), take_event(c)};
       CK(c, cudaEventRecord(ev.first, c->stream));
     }
-    CK(c, c->nd == 2 ? launch_vel2d(P, c->map_kind, c->stream) : launch_vel3d(P, c->map_kind, c->stream));
+    CK(c, c->pipe ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->stream)
+                  : c->nd == 2 ? launch_vel2d(P, c->map_kind, c->stream) : launch_vel3d(P, c->map_kind, c->stream));
     c->launches++;
     if (c->profiling) {
       CK(c, cudaEventRecord(ev.second, c->stream));
@@ -684,7 +690,8 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
       }
     }
     if (c->profiling) CK(c, cudaEventRecord(ev.first, c->stream));
-    CK(c, c->nd == 2 ? launch_prs2d(P, c->map_kind, c->stream) : launch_prs3d(P, c->map_kind, c->stream));
+    CK(c, c->pipe ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->stream)
+                  : c->nd == 2 ? launch_prs2d(P, c->map_kind, c->stream) : launch_prs3d(P, c->map_kind, c->stream));
     c->launches++;
     if (c->profiling) {
       CK(c, cudaEventRecord(ev.second, c->stream));

@@ -55,6 +55,8 @@ struct fw2_ctx {
   char *maps = nullptr;
   StepParams P{};
   int map_kind = 0;  // FW2_MAP_*
+  int n_sm = 152;    // multiprocessors of the device
+  bool pipe = false; // 2D half steps by the pipelined kernels
   double dt = 0.0, cmax_eff = 0.0, cmax = 0.0;
   // sources
   std::vector<HostSource> sources;

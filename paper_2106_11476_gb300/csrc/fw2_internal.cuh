@@ -113,6 +113,12 @@ cudaError_t launch_prs2d(const StepParams &P, int map_kind, cudaStream_t s);
 // several contexts sharing N and the map kind (vel: velocity, else pressure)
 cudaError_t launch_batched2d(bool vel, const StepParams *Ps, const int4 *tiles, int n_tiles, int n_relax,
                              int map_kind, int grid, cudaStream_t s);
+// persistent pipelined 2D half step (one block per SM: grid = SM count):
+// edge tiles by the tile path, interior half tiles staged by cp.async;
+// float maps (map_kind 0) and the tissue index (2)
+bool pipe2d_supported(const StepParams &P, int map_kind);
+bool pipe2d_preferred(const StepParams &P, int map_kind);
+cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, cudaStream_t s);
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
 

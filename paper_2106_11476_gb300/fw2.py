@@ -42,7 +42,7 @@ class Config(C.Structure):
                 ("pml_transition", C.c_int32), ("pml_bound", C.c_int32), ("pml_reading", C.c_int32),
                 ("map_precision", C.c_int32), ("pml_rc", C.c_double), ("pml_npow", C.c_double),
                 ("pml_cp", C.c_double), ("nl_mode", C.c_int32), ("mem_alignment", C.c_int32),
-                ("bc", C.c_int32 * 3), ("reserved_", C.c_int32), ("stream", C.c_void_p)]
+                ("bc", C.c_int32 * 3), ("kernel_path", C.c_int32), ("stream", C.c_void_p)]
 
 
 class RelaxDesc(C.Structure):
@@ -327,7 +327,10 @@ def fw2_abi_version() -> int:
 
 # ------------------------------------------------------------ convenience ---
 
-def config_for(prob, stream: Optional[int] = None, map_precision: str = "f32") -> Config:
+KERNEL_PATH = {"auto": 0, "tile": 1, "pipe": 2}
+
+
+def config_for(prob, stream: Optional[int] = None, map_precision: str = "f32", kernel_path: str = "auto") -> Config:
     """A Config for a problem description (any object with the attributes of
     synth.Problem: shape, h, dt, nrelax, pml_*, nl_mode, memory_alignment, bc, taps)."""
     cfg = fw2_config_init()
@@ -352,6 +355,7 @@ def config_for(prob, stream: Optional[int] = None, map_precision: str = "f32") -
     cfg.nl_mode = NL[prob.nl_mode]
     cfg.mem_alignment = MEM_ALIGN[prob.memory_alignment]
     cfg.map_precision = MAP[map_precision]
+    cfg.kernel_path = KERNEL_PATH[kernel_path]
     cfg.stream = stream
     return cfg
 
@@ -362,14 +366,16 @@ class Simulation:
     Traces land in a torch CUDA tensor ``self.trace`` of [n_steps, n_groups].
     """
 
-    def __init__(self, prob, map_precision: str = "f32", device_inputs: bool = False, stream=None):
+    def __init__(self, prob, map_precision: str = "f32", device_inputs: bool = False, stream=None,
+                 kernel_path: str = "auto"):
         import torch
         self.prob = prob
         self.torch = torch
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        self.cfg = config_for(prob, stream=stream.cuda_stream, map_precision=map_precision)
+        self.cfg = config_for(prob, stream=stream.cuda_stream, map_precision=map_precision,
+                              kernel_path=kernel_path)
         self.ctx = fw2_create(self.cfg)
         try:
             conv = (lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()) \

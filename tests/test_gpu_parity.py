@@ -93,7 +93,7 @@ def state_names(prob):
 
 def small_2d(nx=200, ny=136, N=2, nl="off", steps=300, seed=0, pml=(12, 4), alignment="centred",
              reading="C", vel_src=False, hetero=True):
-    key = {2: "N2_y1.0_a0.5", 4: "N4_y1.1_a0.5"}.get(N)
+    key = {2: "N2_y1.0_a0.5", 3: "N3_y1.2_brain", 4: "N4_y1.1_a0.5"}.get(N)
     rng = np.random.default_rng(seed)
     f0 = 3e6
     h = 1540.0 / f0 / 12
@@ -133,8 +133,9 @@ def small_2d(nx=200, ny=136, N=2, nl="off", steps=300, seed=0, pml=(12, 4), alig
     return prob
 
 
-def compare_run(fw2, prob, steps, state=None, check_trace=True, rel=REL_L2, mx=MAX_REL, maps="f32"):
-    sim = fw2.Simulation(prob, map_precision=maps)
+def compare_run(fw2, prob, steps, state=None, check_trace=True, rel=REL_L2, mx=MAX_REL, maps="f32",
+                kernel_path="auto"):
+    sim = fw2.Simulation(prob, map_precision=maps, kernel_path=kernel_path)
     if state is not None:
         sim.set_state(state)
     sim.step(steps)
@@ -163,6 +164,9 @@ CASES_2D = {
     "ragged-203x77": dict(nx=203, ny=77, pml=(8, 3)),
     "velocity-sources": dict(vel_src=True, N=4),
     "tiny-tile": dict(nx=24, ny=20, pml=(3, 1), steps=200),
+    # grids with interior tiles: the persistent kernels' staged half tiles
+    "interior-560x200-N4-nl": dict(nx=560, ny=200, N=4, nl="pressure", steps=250),
+    "interior-430x170-N0": dict(nx=430, ny=170, N=0, steps=250),
 }
 
 
@@ -172,6 +176,13 @@ def test_parity_2d(fw2, case):
     steps = kw.get("steps", 300)
     prob = small_2d(**kw)
     compare_run(fw2, prob, steps)
+
+
+@pytest.mark.parametrize("case", ["interior-560x200-N4-nl", "interior-430x170-N0", "ragged-203x77"])
+def test_parity_2d_pipelined_path(fw2, case):
+    kw = dict(CASES_2D[case])
+    steps = kw.get("steps", 300)
+    compare_run(fw2, small_2d(**kw), steps, kernel_path="pipe")
 
 
 @pytest.mark.parametrize("nl,N", [("off", 2), ("pressure", 4)])
@@ -319,6 +330,48 @@ def test_tissue_index_form_equals_dense_form_bitwise(fw2, nl):
     for name in state_names(prob):
         np.testing.assert_array_equal(dense.field(name), idx.field(name), err_msg=name)
     np.testing.assert_array_equal(dense.trace.cpu().numpy(), idx.trace.cpu().numpy())
+
+
+def _pipe_vs_tile(fw2, prob, steps, maps="f32", state=None):
+    out = {}
+    for path in ("tile", "pipe"):
+        sim = fw2.Simulation(prob, map_precision=maps, kernel_path=path)
+        if state is not None:
+            sim.set_state(state)
+        sim.step(steps)
+        out[path] = ({n: sim.field(n) for n in state_names(prob)},
+                     sim.trace.cpu().numpy() if sim.trace is not None else None)
+        sim.close()
+    for n in state_names(prob):
+        np.testing.assert_array_equal(out["pipe"][0][n], out["tile"][0][n], err_msg=n)
+    if out["tile"][1] is not None:
+        np.testing.assert_array_equal(out["pipe"][1], out["tile"][1])
+
+
+@pytest.mark.parametrize("N,nl", [(0, "off"), (2, "westervelt"), (2, "off"), (3, "pressure"), (4, "pressure")])
+def test_pipelined_path_equals_tile_path_bitwise(fw2, N, nl):
+    """The persistent pipelined half steps compute exactly what the one-block-
+    per-tile kernels compute (same arithmetic, staged operands), edge and
+    interior tiles alike, on a ragged grid with many interior tiles."""
+    prob = small_2d(nx=717, ny=333, N=N, nl=nl, steps=120, vel_src=True)
+    _pipe_vs_tile(fw2, prob, 120)
+
+
+def test_pipelined_path_equals_tile_path_periodic_cross_taps(fw2):
+    prob = synth.homogeneous((520, 200), 1e-4, 0.0)
+    rng = np.random.default_rng(5)
+    prob.c = (1500 + 200 * rng.random(prob.grid_shape)).astype(np.float32)
+    prob.dt = 0.3 * 1e-4 / float(prob.c.max())
+    prob.bc = ("periodic", "periodic", "zero")
+    taps = [1225 / 1024, -245 / 3072, 49 / 5120, -5 / 7168]
+    prob.taps = (taps[0] * 0.98, taps[1], taps[2], taps[3], 0.005)
+    _pipe_vs_tile(fw2, prob, 100, state=synth.random_state(prob, seed=3))
+
+
+@pytest.mark.parametrize("nl", ["pressure", "off"])
+def test_pipelined_path_equals_tile_path_tissue_index(fw2, nl):
+    prob = synth.indexed_abdominal_problem(nx=650, ny=300, n_steps=150, n_elements=16, nl=nl)
+    _pipe_vs_tile(fw2, prob, 150, maps="idx")
 
 
 def test_parity_tissue_index_form(fw2):
