@@ -248,7 +248,7 @@ def run_fw2(args, rank, world, dist):
         vel_b, prs_b = algorithmic_bytes_indexed(prob.shape, prob.nrelax, prob.pml_transition + prob.pml_bound,
                                                  prob.nl_mode != "off")
     stream = torch.cuda.current_stream()
-    sim = fw2.Simulation(prob, stream=stream, map_precision=maps)
+    sim = fw2.Simulation(prob, stream=stream, map_precision=maps, kernel_path=args.kernel_path)
     sim.step(args.warmup)
     sim.synchronize()
     fw2.fw2_profile(sim.ctx, True)
@@ -324,7 +324,8 @@ def run_fw2(args, rank, world, dist):
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        s2 = fw2.Simulation(hp, stream=stream, map_precision=maps)  # tables stay host numpy for idx
+        s2 = fw2.Simulation(hp, stream=stream, map_precision=maps,  # tables stay host numpy for idx
+                            kernel_path=args.kernel_path)
         s2.step(args.steps)
         trace_host = s2.trace[: args.steps].cpu()
         t1 = time.perf_counter()
@@ -356,6 +357,7 @@ def run_fw2(args, rank, world, dist):
            "data": data,
            "config": {"workload": workload,
                       "grid": list(prob.shape), "n_relax": prob.nrelax, "nl_mode": prob.nl_mode, "map_precision": maps,
+                      "kernel_path": args.kernel_path,
                       "pml_cells": prob.pml_transition + prob.pml_bound,
                       "l2": "state and maps (>2.5 GB) exceed L2; no flush needed",
                       "parallelism": f"replicas x{world} (one transmit event per GPU)"},
@@ -583,6 +585,8 @@ def main():
                          "form; skull: 3D 768^3 with bf16 maps")
     ap.add_argument("--maps", default=None, choices=["f32", "bf16", "idx"],
                     help="override the map storage of the workload")
+    ap.add_argument("--kernel-path", default="auto", choices=["auto", "tile", "pipe"],
+                    help="2D half-step kernels (bitwise the same results)")
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -262,6 +262,14 @@ fw2_status fw2_check_field(fw2_ctx *ctx, float bound, float *max_abs);
  * sizes), FW2_ECUDA (launch failure); fw2_last_error(NULL) explains. */
 fw2_status fw2_field_absmax_noalloc(const float *field, int64_t row_len, int64_t n_rows,
                                     int64_t row_pitch, float *out, void *stream);
+/* Self-test of the bounded device-side wait that every pipelined kernel uses
+ * on its copy barriers (the paper has no counterpart; it guards against a
+ * hung GPU).  Launches one block that initialises an mbarrier nobody ever
+ * arrives on and waits for it with a limit of limit_ns nanoseconds (1 ..
+ * 10^10); *timed_out (host) becomes 1 when the wait gave up, as it must, and
+ * 0 otherwise.  Synchronous on the default stream; needs no context.  Errors:
+ * FW2_EINVAL (null pointer, limit out of range), FW2_ECUDA. */
+fw2_status fw2_selftest_bounded_wait(int64_t limit_ns, int32_t *timed_out);
 /* Bytes of device memory held by the context. */
 fw2_status fw2_device_bytes(fw2_ctx *ctx, int64_t *bytes);
 /* Launches of library kernels since creation (all kinds). */

@@ -225,8 +225,14 @@ fw2_status finalize(fw2_ctx *c) {
   P.a1 = Q.a1; P.b1 = Q.b1; P.a2 = Q.a2; P.b2 = Q.b2;
   P.tissue = Q.tissue_out;
   P.table = Q.table_out;
+  P.status = c->d_status;
   c->pipe = c->nd == 2 && ((cfg.kernel_path == FW2_PATH_AUTO && pipe2d_preferred(P, c->map_kind)) ||
                             (cfg.kernel_path == FW2_PATH_PIPE && pipe2d_supported(P, c->map_kind)));
+  if (c->pipe) {
+    const char *why = "";
+    if (build_pipe2d_maps(P, c->map_kind, &c->tm_vel, &c->tm_prs, &why) != cudaSuccess)
+      return fail(c, FW2_ECUDA, "tensor maps of the pipelined kernels: %s", why);
+  }
   c->finalized = true;
   return FW2_OK;
 }
@@ -352,6 +358,21 @@ extern "C" {
 
 int32_t fw2_abi_version(void) { return 1; }
 
+fw2_status fw2_selftest_bounded_wait(int64_t limit_ns, int32_t *timed_out) {
+  if (!timed_out || limit_ns < 1 || limit_ns > 10000000000ll)
+    return fail(nullptr, FW2_EINVAL, "timed_out is required and limit_ns must lie in [1, 1e10]");
+  int *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0xff, sizeof(int));
+  if (e == cudaSuccess) e = launch_bounded_wait_selftest((unsigned long long)limit_ns, d);
+  int h = -1;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) return fail(nullptr, FW2_ECUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
+  *timed_out = h;
+  return FW2_OK;
+}
+
 fw2_status fw2_config_init(fw2_config *cfg) {
   if (!cfg) return FW2_EINVAL;
   std::memset(cfg, 0, sizeof *cfg);
@@ -436,7 +457,9 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
   c->nx = (int)cfg.n[0];
   c->ny = (int)cfg.n[1];
   c->nz = cfg.ndim == 3 ? (int)cfg.n[2] : 1;
-  c->pitch = (c->nx + 3) & ~3;
+  // rows start on 64-byte boundaries: 16-byte aligned rows for every element
+  // type (the uint8 tissue index included), as the tensor copies require
+  c->pitch = (c->nx + 15) & ~15;
   c->plane = (long long)c->pitch * c->ny;
   // padded to 128 elements so every per-mechanism array (float or bf16)
   // starts 256-byte aligned at nu * npts_alloc
@@ -461,6 +484,11 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
     if ((st = dalloc(c, 2 * sizeof(unsigned long long), &m)) == FW2_OK) c->d_scan = (unsigned long long *)m;
     if (st == FW2_OK && (st = dalloc(c, sizeof(int), &m)) == FW2_OK) c->d_bad = (int *)m;
     if (st == FW2_OK && (st = dalloc(c, sizeof(unsigned int), &m)) == FW2_OK) c->d_absmax = (unsigned int *)m;
+    if (st == FW2_OK && (st = dalloc(c, sizeof(unsigned int), &m)) == FW2_OK) c->d_status = (unsigned int *)m;
+  }
+  if (st == FW2_OK) {
+    cudaError_t e2 = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream);
+    if (e2 != cudaSuccess) st = cuda_fail(c, e2, "status initialisation");
   }
   if (st == FW2_OK) {
     cudaError_t e2 = cudaMemsetAsync(c->state, 0, c->state_bytes, c->stream);
@@ -673,7 +701,7 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
       ev = {take_event(c), take_event(c)};
       CK(c, cudaEventRecord(ev.first, c->stream));
     }
-    CK(c, c->pipe ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->stream)
+    CK(c, c->pipe ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->tm_vel, c->stream)
                   : c->nd == 2 ? launch_vel2d(P, c->map_kind, c->stream) : launch_vel3d(P, c->map_kind, c->stream));
     c->launches++;
     if (c->profiling) {
@@ -690,7 +718,7 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
       }
     }
     if (c->profiling) CK(c, cudaEventRecord(ev.first, c->stream));
-    CK(c, c->pipe ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->stream)
+    CK(c, c->pipe ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->tm_prs, c->stream)
                   : c->nd == 2 ? launch_prs2d(P, c->map_kind, c->stream) : launch_prs3d(P, c->map_kind, c->stream));
     c->launches++;
     if (c->profiling) {
@@ -763,6 +791,7 @@ fw2_status fw2_set_field(fw2_ctx *c, int32_t field, const float *in, int32_t mem
 fw2_status fw2_reset(fw2_ctx *c) {
   if (!c) return FW2_EINVAL;
   CK(c, cudaMemsetAsync(c->state, 0, c->state_bytes, c->stream));
+  CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->step = 0;
   return FW2_OK;
@@ -770,7 +799,11 @@ fw2_status fw2_reset(fw2_ctx *c) {
 
 fw2_status fw2_synchronize(fw2_ctx *c) {
   if (!c) return FW2_EINVAL;
+  unsigned int status = 0;
+  CK(c, cudaMemcpyAsync(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  if (status & 1u)
+    return fail(c, FW2_ETIMEOUT, "a bounded device-side wait gave up; the state is incomplete (fw2_reset clears it)");
   return FW2_OK;
 }
 

@@ -1,4 +1,6 @@
-// Source injection, sensor recording and the field scan (sm_103a).
+// Source injection, sensor recording, the field scan and the self-test of
+// the bounded wait (sm_103a).
+#include "async.cuh"
 #include "fw2_prep.cuh"
 
 namespace fw2 {
@@ -73,6 +75,21 @@ cudaError_t launch_absmax(const float *f, int nx, int pitch, long long rows, uns
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
   absmax_kernel<<<(int)blocks, 256, 0, s>>>(f, nx, pitch, rows, out_bits);
+  return cudaGetLastError();
+}
+
+namespace {
+// one thread waits on an mbarrier that never completes (count 1, no arrival)
+__global__ void bounded_wait_kernel(unsigned long long limit_ns, int *timed_out) {
+  __shared__ __align__(8) uint64_t bar;
+  mbar_init(&bar, 1);
+  fence_mbarrier_init();
+  *timed_out = mbar_wait_bounded(&bar, 0, limit_ns) ? 0 : 1;
+}
+}  // namespace
+
+cudaError_t launch_bounded_wait_selftest(unsigned long long limit_ns, int *timed_out) {
+  bounded_wait_kernel<<<1, 1>>>(limit_ns, timed_out);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include "fw2.h"
 #include "fw2_prep.cuh"
 #include "maps.cuh"
+#include "tmap.h"
 
 namespace fw2 {
 
@@ -57,6 +58,7 @@ struct fw2_ctx {
   int map_kind = 0;  // FW2_MAP_*
   int n_sm = 152;    // multiprocessors of the device
   bool pipe = false; // 2D half steps by the pipelined kernels
+  fw2::PipeMaps tm_vel{}, tm_prs{};  // their tensor maps
   double dt = 0.0, cmax_eff = 0.0, cmax = 0.0;
   // sources
   std::vector<HostSource> sources;
@@ -74,6 +76,7 @@ struct fw2_ctx {
   unsigned long long *d_scan = nullptr;
   int *d_bad = nullptr;
   unsigned int *d_absmax = nullptr;
+  unsigned int *d_status = nullptr;  // bit 0: a bounded device-side wait gave up
   long long step = 0, launches = 0;
   // optional per-kernel event timing
   bool profiling = false;

@@ -1,9 +1,10 @@
 // Internal declarations shared by the CUDA translation units of libfw2.
 //
 // Device layout (all arrays in HBM, one allocation per context):
-//   every per-cell array is [nz][ny][pitch] floats (pitch = nx rounded up to
-//   4 so each row starts on a 16-byte boundary for 128-bit accesses; the
-//   padding columns of state arrays stay zero);
+//   every per-cell array is [nz][ny][pitch] (pitch = nx rounded up to 16
+//   elements, so each row starts on a 16-byte boundary for 128-bit accesses
+//   and tensor copies of every element type; the padding columns of state
+//   arrays stay zero);
 //   memory variables psi1_q / psi2_q are [N][nz][ny][pitch];
 //   coefficient maps use the same cell layout in float or bf16;
 //   boundary strips hold the per-axis a, b of the C-PML region only:
@@ -21,7 +22,7 @@ constexpr int kMaxRelax = 4;
 
 struct StepParams {
   int nx, ny, nz;        // logical extent
-  int pitch;             // row pitch in elements (multiple of 4)
+  int pitch;             // row pitch in elements (multiple of 16)
   long long plane;       // pitch * ny
   long long npts_alloc;  // plane * nz
   int L[3];              // boundary cells per side on each axis (0: no strip)
@@ -49,6 +50,7 @@ struct StepParams {
   // ([field][256] floats, field order of maps.cuh)
   const unsigned char *tissue;
   const float *table;
+  unsigned int *status;  // device status word: bit 0 set when a bounded wait gave up
 };
 
 // ---------------------------------------------------------------- loads ---
@@ -116,9 +118,14 @@ cudaError_t launch_batched2d(bool vel, const StepParams *Ps, const int4 *tiles, 
 // persistent pipelined 2D half step (one block per SM: grid = SM count):
 // edge tiles by the tile path, interior half tiles staged by cp.async;
 // float maps (map_kind 0) and the tissue index (2)
+struct PipeMaps;
 bool pipe2d_supported(const StepParams &P, int map_kind);
 bool pipe2d_preferred(const StepParams &P, int map_kind);
-cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, cudaStream_t s);
+// encode the tensor maps of both half steps (host); cudaErrorInvalidValue
+// when the driver rejects one (message in *why)
+cudaError_t build_pipe2d_maps(const StepParams &P, int map_kind, PipeMaps *vel, PipeMaps *prs, const char **why);
+cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, const PipeMaps &T,
+                          cudaStream_t s);
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
 

@@ -43,4 +43,8 @@ cudaError_t launch_record(const float *p, const long long *cell, const int *off,
 cudaError_t launch_absmax(const float *f, int nx, int pitch, long long rows,
                           unsigned int *out_bits, cudaStream_t s);
 
+// one block waits on an mbarrier that never completes, with the bounded wait
+// of the pipelined kernels; *timed_out (device) = 1 when it gave up
+cudaError_t launch_bounded_wait_selftest(unsigned long long limit_ns, int *timed_out);
+
 }  // namespace fw2

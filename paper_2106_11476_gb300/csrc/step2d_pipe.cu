@@ -1,17 +1,27 @@
 // Pipelined persistent 2D half steps (sm_103a); same arithmetic as the tile
-// functions of tile2d.cuh, one launch per half step.
+// functions of tile2d.cuh (bitwise the same results), one launch per half
+// step, one block per SM.
 //
-// A grid of one block per SM first runs the edge tiles of the grid (tiles
-// that touch a C-PML strip or the outer boundary) through the general tile
-// path, then walks the interior in half tiles of 128 x 8 cells with a
-// two-stage pipeline: for the next half tile it issues cp.async copies of the
-// stencil operand with its halo, of the density (or tissue-index) tile and of
-// every streamed array of its cells into one shared-memory stage, while it
-// computes the current half tile from the other.  The copies hold no
-// registers, so a block keeps a whole stage (up to ~95 KB) of loads in
-// flight; results go straight from registers to HBM.  Dense float maps and
-// the tissue-index form take this path.
+// The grid is walked in half tiles of 128 x 8 cells through a two-stage
+// pipeline.  For the next half tile one thread issues tiled TMA tensor copies
+// into a shared-memory stage, one box per array: the stencil operand with
+// its halo, the density tile, every streamed array, the N mechanisms of a
+// memory variable or of a relaxation map in one 3D box.  They complete on the
+// stage's mbarrier while all warps compute the current half tile from the
+// other stage, so a whole stage (up to ~95 KB) stays in flight per SM without
+// registers or load instructions of the computing threads; results go
+// straight from registers to HBM.
+//
+// Boundaries: the copies read zero outside the grid (the zero-outside rule of
+// the operand halo); half tiles at the edge of the grid or in a C-PML strip
+// (edge half tiles) also clamp the density tile to the last cell, take the
+// C-PML coefficients of each axis from its strip, and store nothing outside
+// the grid (zeros in the row padding).  With a periodic axis the tiles next
+// to the boundary run the general tile path first and only the rest is staged.
+// Dense float maps and the tissue-index form take this path.
+#include "async.cuh"
 #include "tile2d.cuh"
+#include "tmap.h"
 
 namespace fw2 {
 
@@ -19,20 +29,9 @@ namespace {
 
 constexpr int kHT = 8;              // rows of a half tile
 constexpr int kCW = kTX + 8;        // staged operand columns x0-4 .. x0+TX+3 (= kPW)
-constexpr int kRWp = kTX + 4;       // density / index tile columns x0 .. x0+TX+3 (= kRW)
+constexpr int kRWp = kTX + 4;       // density tile columns x0 .. x0+TX+3 (= kRW)
+constexpr int kIW = kTX + 16;       // staged index bytes per row x0 .. x0+TX+15
 constexpr int kArr = kHT * kTX;     // floats of one streamed array per half tile
-
-__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp4(void *smem, const void *gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
 __device__ __forceinline__ float4 sld4(const float *s) { return *reinterpret_cast<const float4 *>(s); }
 
@@ -45,22 +44,33 @@ struct IsIdx<IdxMaps> {
   static constexpr bool value = true;
 };
 
-constexpr int round4(int n) { return (n + 3) & ~3; }
+// shared-memory regions start on 128-byte boundaries (TMA destinations)
+constexpr int round32(int n) { return (n + 31) & ~31; }
 
-// Tile bookkeeping: the interior region [tx_lo, tx_lo+ntx) x [ty_lo, ty_lo+nty)
-// in 128 x 16 tile units (exactly the tiles interior_tile accepts) and the
-// frame of edge tiles around it in a grid of tnx x tny tiles.
+// Work of one launch.  Staged: the half tiles [tx_lo, tx_lo+ntx) x
+// [hy_lo, hy_lo+nhy) (x in tiles of 128, y in half tiles of 8 rows), x
+// fastest: the whole grid, or with `split` (a periodic axis) the interior
+// tiles [tx_lo, tx_lo+ntx) x [ty_lo, ty_lo+nty) of 128 x 16 (the tiles
+// interior_tile accepts), the frame of tiles around them going through the
+// general tile path.
 struct Region {
-  int tnx, tny, tx_lo, ntx, ty_lo, nty;
-  __device__ __forceinline__ int halves() const { return 2 * ntx * nty; }
+  int nx, ny, Lx, Ly;             // grid, boundary width (at least the halo, 4)
+  int tnx, tny;                   // tiles of 128 x 16
+  int split;
+  int tx_lo, ntx, ty_lo, nty;     // interior tiles (split)
+  int hy_lo, nhy;                 // staged half-tile rows
+  __device__ __forceinline__ int halves() const { return ntx * nhy; }
   __device__ __forceinline__ void half_origin(int h, int &x0, int &y0) const {
-    const int t = h >> 1;
-    x0 = (tx_lo + t % ntx) * kTX;
-    y0 = (ty_lo + t / ntx) * kTY + (h & 1) * kHT;
+    x0 = (tx_lo + h % ntx) * kTX;
+    y0 = (hy_lo + h / ntx) * kHT;
   }
-  __device__ __forceinline__ int edges() const { return tnx * tny - ntx * nty; }
-  // e-th edge tile: the rows below the interior, the side tiles of the
-  // interior rows, then the rows above
+  // a staged half tile clear of the boundary rules and of the C-PML strips
+  __device__ __forceinline__ bool interior(int x0, int y0) const {
+    return x0 >= Lx && x0 + kTX + Lx <= nx && y0 >= Ly && y0 + kHT + Ly <= ny;
+  }
+  __device__ __forceinline__ int edges() const { return split ? tnx * tny - ntx * nty : 0; }
+  // e-th general-path tile (split): the rows below the staged tiles, the
+  // side tiles of their rows, then the rows above
   __device__ __forceinline__ void edge_origin(int e, int &x0, int &y0) const {
     int tx, ty;
     const int low = ty_lo * tnx, side = tnx - ntx;
@@ -91,11 +101,13 @@ struct VelStage {
   // dense: v_x, v_y, psi_x[N], psi_y[N], 1/kappa1, a1[N], b1[N];
   // index: v_x, v_y, psi_x[N], psi_y[N]
   static constexpr int kNs = kIdx ? 2 + 2 * N : 3 + 4 * N;
-  static constexpr int kP = (kHT + 7) * kCW;
-  static constexpr int kR = (kHT + 1) * kRWp;
+  static constexpr int kPb = (kHT + 7) * kCW;    // operand box
+  static constexpr int kRb = (kHT + 1) * kRWp;   // density box
+  static constexpr int kP = round32(kPb);
+  static constexpr int kR = round32(kRb);
   static constexpr int kS = kNs * kArr;
-  static constexpr int kI = kIdx ? (kHT + 1) * kRWp / 4 : 0;  // bytes / 4
-  static constexpr int kFloats = round4(kP + kR + kS + kI);
+  static constexpr int kI = kIdx ? (kHT + 1) * kIW / 4 : 0;  // index bytes / 4
+  static constexpr int kFloats = round32(kP + kR + kS + kI);
   static constexpr int kEdge = kPH * kPW + kRH * kRW;         // general tile
 };
 
@@ -107,81 +119,167 @@ struct PrsStage {
   // dense: p, psi_x[N], psi_y[N], 1/kappa2, K, chi, a2[N], b2[N];
   // index: p, psi_x[N], psi_y[N]
   static constexpr int kNs = kIdx ? 1 + 2 * N : 4 + 4 * N;
-  static constexpr int kX = (kHT + 2) * kCW;
-  static constexpr int kY = (kHT + 7) * kCW;
+  static constexpr int kXb = (kHT + 2) * kCW;
+  static constexpr int kYb = (kHT + 7) * kCW;
+  static constexpr int kX = round32(kXb);
+  static constexpr int kY = round32(kYb);
   static constexpr int kS = kNs * kArr;
   static constexpr int kI = kIdx ? kHT * kTX / 4 : 0;
-  static constexpr int kFloats = round4(kX + kY + kS + kI);
+  static constexpr int kFloats = round32(kX + kY + kS + kI);
   static constexpr int kEdge = kHX * kPW + kHY * kPW;
 };
 
-template <int N, typename Maps>
-__device__ __forceinline__ void vel_prefetch(const StepParams &P, float *st, int x0, int y0, int tid) {
-  using S = VelStage<N, Maps>;
-  float *sp = st, *sr = st + S::kP, *ss = sr + S::kR;
-  for (int t = tid; t < (kHT + 7) * (kCW / 4); t += 256) {
-    const int r = t / (kCW / 4), c4 = t % (kCW / 4);
-    cp16(sp + r * kCW + 4 * c4, P.p + (long long)(y0 - 3 + r) * P.pitch + x0 - 4 + 4 * c4);
+// Bytes one stage receives through the tensor maps (the chi box only with
+// the nonlinear term).
+template <int N, typename Maps, bool VEL>
+__host__ __device__ constexpr unsigned stage_bytes(bool nl) {
+  if (VEL) {
+    using S = VelStage<N, Maps>;
+    return 4u * (S::kPb + (S::kIdx ? 0 : S::kRb) + S::kNs * kArr) + (S::kIdx ? (kHT + 1) * kIW : 0);
+  } else {
+    using S = PrsStage<N, Maps>;
+    return 4u * (S::kXb + S::kYb + S::kNs * kArr) - ((!S::kIdx && !nl) ? 4u * kArr : 0u) +
+           (S::kIdx ? kHT * kTX : 0);
   }
-  const int row = tid >> 5, col = (tid & 31) * 4;
-  const long long c = (long long)(y0 + row) * P.pitch + x0 + col;
-  const long long Sn = P.npts_alloc;
-  float *dst = ss + row * kTX + col;
-  cp16(dst, P.v[0] + c);
-  cp16(dst + kArr, P.v[1] + c);
-#pragma unroll
-  for (int nu = 0; nu < N; ++nu) {
-    cp16(dst + (2 + nu) * kArr, P.psi1[0] + nu * Sn + c);
-    cp16(dst + (2 + N + nu) * kArr, P.psi1[1] + nu * Sn + c);
-  }
-  if constexpr (!S::kIdx) {
-    const float *ik1 = static_cast<const float *>(P.ik1);
-    const float *a1 = static_cast<const float *>(P.a1), *b1 = static_cast<const float *>(P.b1);
-    cp16(dst + (2 + 2 * N) * kArr, ik1 + c);
-#pragma unroll
-    for (int nu = 0; nu < N; ++nu) {
-      cp16(dst + (3 + 2 * N + nu) * kArr, a1 + nu * Sn + c);
-      cp16(dst + (3 + 3 * N + nu) * kArr, b1 + nu * Sn + c);
+}
+
+// Issue the tensor copies of one half tile into a stage (one thread; it
+// first announces the stage's bytes on the stage's mbarrier).  Boxes may
+// reach outside the grid: those cells read as zero.
+template <int N, typename Maps, bool VEL>
+__device__ __forceinline__ void issue_stage(const StepParams &P, const PipeMaps &T, float *st, uint64_t *bar,
+                                            int x0, int y0) {
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, stage_bytes<N, Maps, VEL>(P.nl != 0));
+  if (VEL) {
+    using S = VelStage<N, Maps>;
+    tma_load_2d(st, &T.m[0], x0 - 4, y0 - 3, bar);
+    if (!S::kIdx) tma_load_2d(st + S::kP, &T.m[1], x0, y0, bar);
+    float *ss = st + S::kP + S::kR;
+    tma_load_2d(ss, &T.m[2], x0, y0, bar);
+    tma_load_2d(ss + kArr, &T.m[3], x0, y0, bar);
+    if (N > 0) {
+      tma_load_3d(ss + 2 * kArr, &T.m[4], x0, y0, 0, bar);
+      tma_load_3d(ss + (2 + N) * kArr, &T.m[5], x0, y0, 0, bar);
     }
-    const float *rho = static_cast<const float *>(P.rho);
-    for (int t = tid; t < (kHT + 1) * (kRWp / 4); t += 256) {
-      const int r = t / (kRWp / 4), c4 = t % (kRWp / 4);
-      cp16(sr + r * kRWp + 4 * c4, rho + (long long)(y0 + r) * P.pitch + x0 + 4 * c4);
+    if (!S::kIdx) {
+      tma_load_2d(ss + (2 + 2 * N) * kArr, &T.m[6], x0, y0, bar);
+      if (N > 0) {
+        tma_load_3d(ss + (3 + 2 * N) * kArr, &T.m[7], x0, y0, 0, bar);
+        tma_load_3d(ss + (3 + 3 * N) * kArr, &T.m[8], x0, y0, 0, bar);
+      }
+    } else {
+      tma_load_2d(ss + S::kS, &T.m[1], x0, y0, bar);  // tissue index
     }
   } else {
-    // the uint8 rows start on 4-byte boundaries only
-    unsigned char *si = reinterpret_cast<unsigned char *>(ss + S::kS);
-    for (int t = tid; t < (kHT + 1) * (kRWp / 4); t += 256) {
-      const int r = t / (kRWp / 4), c4 = t % (kRWp / 4);
-      cp4(si + r * kRWp + 4 * c4, P.tissue + (long long)(y0 + r) * P.pitch + x0 + 4 * c4);
+    using S = PrsStage<N, Maps>;
+    tma_load_2d(st, &T.m[0], x0 - 4, y0 - 1, bar);
+    tma_load_2d(st + S::kX, &T.m[1], x0 - 4, y0 - 4, bar);
+    float *ss = st + S::kX + S::kY;
+    tma_load_2d(ss, &T.m[2], x0, y0, bar);
+    if (N > 0) {
+      tma_load_3d(ss + kArr, &T.m[3], x0, y0, 0, bar);
+      tma_load_3d(ss + (1 + N) * kArr, &T.m[4], x0, y0, 0, bar);
+    }
+    if (!S::kIdx) {
+      tma_load_2d(ss + (1 + 2 * N) * kArr, &T.m[5], x0, y0, bar);
+      tma_load_2d(ss + (2 + 2 * N) * kArr, &T.m[6], x0, y0, bar);
+      if (P.nl) tma_load_2d(ss + (3 + 2 * N) * kArr, &T.m[7], x0, y0, bar);
+      if (N > 0) {
+        tma_load_3d(ss + (4 + 2 * N) * kArr, &T.m[8], x0, y0, 0, bar);
+        tma_load_3d(ss + (4 + 3 * N) * kArr, &T.m[9], x0, y0, 0, bar);
+      }
+    } else {
+      tma_load_2d(ss + S::kS, &T.m[5], x0, y0, bar);  // tissue index
     }
   }
 }
 
-template <int N, typename Maps>
+// Density tile rows y0 .. y0+kHT, columns x0 .. x0+kTX+3.  Cells beyond the
+// last one along an axis take that cell's value (rho_coord of the tile path):
+// dense maps fix the staged tile in place (the entries inside the grid are
+// the sources); the index form gathers the tile through the table from the
+// staged index (zero outside the grid, hence the clamp).
+template <typename Maps, bool EDGE>
+__device__ __forceinline__ void density_tile(const StepParams &P, const Maps &M, float *sr,
+                                             const unsigned char *si, int x0, int y0, int tid) {
+  for (int t = tid; t < (kHT + 1) * kRWp; t += 256) {
+    const int r = t / kRWp, cc = t % kRWp;
+    int sxi = cc, syi = r;
+    if (EDGE) {
+      if (x0 + cc >= P.nx) sxi = P.nx - 1 - x0;
+      if (y0 + r >= P.ny) syi = P.ny - 1 - y0;
+    }
+    if constexpr (IsIdx<Maps>::value) {
+      sr[t] = M.tab[kTabRho * kTissues + si[syi * kIW + sxi]];
+    } else {
+      if (sxi != cc || syi != r) sr[t] = sr[syi * kRWp + sxi];
+    }
+  }
+}
+
+// a, b of mechanism nu along x at the four cells of an edge group: from the
+// x strip inside its C-PML region (zero beyond the grid), else the interior
+// values A, B (coef_edge of the tile path)
+template <int OP, typename Maps>
+__device__ __forceinline__ void x_strip_coef(const StepParams &P, int nu, int i0, int j, float4 &a, float4 &b) {
+  using ST = typename Maps::StripT;
+  const int L = P.L[0];
+  if (!(L > 0 && (i0 < L || i0 + 3 >= P.nx - L))) return;
+  const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[0] : P.sa2[0]);
+  const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[0] : P.sb2[0]);
+  const long long row = (long long)nu * P.strip_nu[0] + (long long)j * (2 * L);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int x = i0 + e;
+    if (x >= P.nx) {
+      el(a, e) = 0.f;
+      el(b, e) = 0.f;
+    } else {
+      const int sc = strip_coord(x, P.nx, L);
+      if (sc >= 0) {
+        el(a, e) = ldmap(sa, row + sc);
+        el(b, e) = ldb(sb, row + sc);
+      }
+    }
+  }
+}
+
+// a, b along y at the four cells of an edge group inside the y strip
+template <int OP, typename Maps>
+__device__ __forceinline__ void y_strip_coef(const StepParams &P, int nu, int i0, int sc, float4 &a, float4 &b) {
+  using ST = typename Maps::StripT;
+  const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[1] : P.sa2[1]);
+  const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[1] : P.sb2[1]);
+  const long long off = (long long)nu * P.strip_nu[1] + (long long)sc * P.pitch + i0;
+  a = ldmap4(sa, off);
+  b = ldb4(sb, off);
+}
+
+template <int N, typename Maps, bool EDGE>
 __device__ __forceinline__ void vel_compute(const StepParams &P, const Maps &M, float *st, int x0, int y0,
                                             int tid) {
   using S = VelStage<N, Maps>;
   const float *sp = st;
   float *sr = st + S::kP;
   const float *ss = sr + S::kR;
-  if constexpr (S::kIdx) {
-    // density tile from the staged index and the table
-    const unsigned char *si = reinterpret_cast<const unsigned char *>(ss + S::kS);
-    for (int t = tid; t < (kHT + 1) * kRWp; t += 256) sr[t] = M.tab[kTabRho * kTissues + si[t]];
+  const unsigned char *si = reinterpret_cast<const unsigned char *>(ss + S::kS);
+  if (EDGE || S::kIdx) {
+    density_tile<Maps, EDGE>(P, M, sr, si, x0, y0, tid);
     __syncthreads();
   }
   const int tx = tid & 31, ly = tid >> 5, lx = 4 * tx;
-  const long long c = (long long)(y0 + ly) * P.pitch + x0 + lx;
+  const int i0 = x0 + lx, j = y0 + ly;
+  if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
+  const long long c = (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
   const float *own = ss + ly * kTX + lx;
   float4 Dx, Dy;
   vel_derivs(P, reinterpret_cast<const float(*)[kCW]>(sp), ly + 3, tx, Dx, Dy);
   float4 k1, A[N > 0 ? N : 1], B[N > 0 ? N : 1];
   if constexpr (S::kIdx) {
-    const unsigned char *si = reinterpret_cast<const unsigned char *>(ss + S::kS);
     typename Maps::Cell cell;
-    cell.t = *reinterpret_cast<const uchar4 *>(si + ly * kRWp + lx);
+    cell.t = *reinterpret_cast<const uchar4 *>(si + ly * kIW + lx);
     k1 = M.ik1(cell);
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
@@ -196,19 +294,39 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const Maps &M, 
       B[nu] = sld4(own + (3 + 3 * N + nu) * kArr);
     }
   }
+  // per-axis coefficients; in an edge group the C-PML strips replace them,
+  // every strip value loaded before the first store (one memory latency)
+  float4 AX[N > 0 ? N : 1], BX[N > 0 ? N : 1], AY[N > 0 ? N : 1], BY[N > 0 ? N : 1];
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    AX[nu] = A[nu]; BX[nu] = B[nu]; AY[nu] = A[nu]; BY[nu] = B[nu];
+  }
+  if (EDGE) {
+    const int scy = strip_coord(j, P.ny, P.L[1]);
+#pragma unroll
+    for (int nu = 0; nu < N; ++nu) {
+      x_strip_coef<1, Maps>(P, nu, i0, j, AX[nu], BX[nu]);
+      if (scy >= 0) y_strip_coef<1, Maps>(P, nu, i0, scy, AY[nu], BY[nu]);
+    }
+  }
   float4 vx = sld4(own), vy = sld4(own + kArr);
   float4 Sx = make_float4(Dx.x * k1.x, Dx.y * k1.y, Dx.z * k1.z, Dx.w * k1.w);
   float4 Sy = make_float4(Dy.x * k1.x, Dy.y * k1.y, Dy.z * k1.z, Dy.w * k1.w);
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
     const float4 px = sld4(own + (2 + nu) * kArr), py = sld4(own + (2 + N + nu) * kArr);
+    const float4 ax = AX[nu], bx = BX[nu], ay = AY[nu], by = BY[nu];
     float4 nx_, ny_;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      el(nx_, e) = fmaf(el(B[nu], e), el(px, e), el(A[nu], e) * el(Dx, e));
-      el(ny_, e) = fmaf(el(B[nu], e), el(py, e), el(A[nu], e) * el(Dy, e));
+      el(nx_, e) = fmaf(el(bx, e), el(px, e), el(ax, e) * el(Dx, e));
+      el(ny_, e) = fmaf(el(by, e), el(py, e), el(ay, e) * el(Dy, e));
       el(Sx, e) += fmaf(P.w_new, el(nx_, e), P.w_old * el(px, e));
       el(Sy, e) += fmaf(P.w_new, el(ny_, e), P.w_old * el(py, e));
+    }
+    if (EDGE) {
+      nx_ = mask_pad(nx_, i0, P.nx);
+      ny_ = mask_pad(ny_, i0, P.nx);
     }
     st_state4(P.psi1[0], nu * Sn + c, nx_);
     st_state4(P.psi1[1], nu * Sn + c, ny_);
@@ -224,56 +342,23 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const Maps &M, 
   vy.y -= P.two_dt / (r0.y + ru.y) * Sy.y;
   vy.z -= P.two_dt / (r0.z + ru.z) * Sy.z;
   vy.w -= P.two_dt / (r0.w + ru.w) * Sy.w;
+  if (EDGE) {
+    vx = mask_pad(vx, i0, P.nx);
+    vy = mask_pad(vy, i0, P.nx);
+  }
   st_state4(P.v[0], c, vx);
   st_state4(P.v[1], c, vy);
 }
 
-template <int N, typename Maps>
-__device__ __forceinline__ void prs_prefetch(const StepParams &P, float *st, int x0, int y0, int tid) {
-  using S = PrsStage<N, Maps>;
-  float *sx = st, *sy = st + S::kX, *ss = sy + S::kY;
-  for (int t = tid; t < (kHT + 2) * (kCW / 4); t += 256) {
-    const int r = t / (kCW / 4), c4 = t % (kCW / 4);
-    cp16(sx + r * kCW + 4 * c4, P.v[0] + (long long)(y0 - 1 + r) * P.pitch + x0 - 4 + 4 * c4);
-  }
-  for (int t = tid; t < (kHT + 7) * (kCW / 4); t += 256) {
-    const int r = t / (kCW / 4), c4 = t % (kCW / 4);
-    cp16(sy + r * kCW + 4 * c4, P.v[1] + (long long)(y0 - 4 + r) * P.pitch + x0 - 4 + 4 * c4);
-  }
-  const int row = tid >> 5, col = (tid & 31) * 4;
-  const long long c = (long long)(y0 + row) * P.pitch + x0 + col;
-  const long long Sn = P.npts_alloc;
-  float *dst = ss + row * kTX + col;
-  cp16(dst, P.p + c);
-#pragma unroll
-  for (int nu = 0; nu < N; ++nu) {
-    cp16(dst + (1 + nu) * kArr, P.psi2[0] + nu * Sn + c);
-    cp16(dst + (1 + N + nu) * kArr, P.psi2[1] + nu * Sn + c);
-  }
-  if constexpr (!S::kIdx) {
-    const float *ik2 = static_cast<const float *>(P.ik2), *K = static_cast<const float *>(P.K);
-    const float *a2 = static_cast<const float *>(P.a2), *b2 = static_cast<const float *>(P.b2);
-    cp16(dst + (1 + 2 * N) * kArr, ik2 + c);
-    cp16(dst + (2 + 2 * N) * kArr, K + c);
-    if (P.nl) cp16(dst + (3 + 2 * N) * kArr, static_cast<const float *>(P.chi) + c);
-#pragma unroll
-    for (int nu = 0; nu < N; ++nu) {
-      cp16(dst + (4 + 2 * N + nu) * kArr, a2 + nu * Sn + c);
-      cp16(dst + (4 + 3 * N + nu) * kArr, b2 + nu * Sn + c);
-    }
-  } else {
-    unsigned char *si = reinterpret_cast<unsigned char *>(ss + S::kS);
-    cp4(si + row * kTX + col, P.tissue + c);
-  }
-}
-
-template <int N, typename Maps>
+template <int N, typename Maps, bool EDGE>
 __device__ __forceinline__ void prs_compute(const StepParams &P, const Maps &M, const float *st, int x0, int y0,
                                             int tid) {
   using S = PrsStage<N, Maps>;
   const float *sx = st, *sy = st + S::kX, *ss = sy + S::kY;
   const int tx = tid & 31, ly = tid >> 5, lx = 4 * tx;
-  const long long c = (long long)(y0 + ly) * P.pitch + x0 + lx;
+  const int i0 = x0 + lx, j = y0 + ly;
+  if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
+  const long long c = (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
   const float *own = ss + ly * kTX + lx;
   float4 Dx, Dy;
@@ -281,9 +366,8 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const Maps &M, 
              Dx, Dy);
   float4 k2, K, ch = make_float4(0.f, 0.f, 0.f, 0.f), A[N > 0 ? N : 1], B[N > 0 ? N : 1];
   if constexpr (S::kIdx) {
-    const unsigned char *si = reinterpret_cast<const unsigned char *>(ss + S::kS);
     typename Maps::Cell cell;
-    cell.t = *reinterpret_cast<const uchar4 *>(si + ly * kTX + lx);
+    cell.t = *reinterpret_cast<const uchar4 *>(reinterpret_cast<const unsigned char *>(ss + S::kS) + ly * kTX + lx);
     k2 = M.ik2(cell);
     K = M.Kv(cell);
     if (P.nl) ch = M.chiv(cell);
@@ -302,19 +386,37 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const Maps &M, 
       B[nu] = sld4(own + (4 + 3 * N + nu) * kArr);
     }
   }
+  float4 AX[N > 0 ? N : 1], BX[N > 0 ? N : 1], AY[N > 0 ? N : 1], BY[N > 0 ? N : 1];
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    AX[nu] = A[nu]; BX[nu] = B[nu]; AY[nu] = A[nu]; BY[nu] = B[nu];
+  }
+  if (EDGE) {
+    const int scy = strip_coord(j, P.ny, P.L[1]);
+#pragma unroll
+    for (int nu = 0; nu < N; ++nu) {
+      x_strip_coef<2, Maps>(P, nu, i0, j, AX[nu], BX[nu]);
+      if (scy >= 0) y_strip_coef<2, Maps>(P, nu, i0, scy, AY[nu], BY[nu]);
+    }
+  }
   float4 p = sld4(own);
   float4 Sx = make_float4(Dx.x * k2.x, Dx.y * k2.y, Dx.z * k2.z, Dx.w * k2.w);
   float4 Sy = make_float4(Dy.x * k2.x, Dy.y * k2.y, Dy.z * k2.z, Dy.w * k2.w);
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
     const float4 px = sld4(own + (1 + nu) * kArr), py = sld4(own + (1 + N + nu) * kArr);
+    const float4 ax = AX[nu], bx = BX[nu], ay = AY[nu], by = BY[nu];
     float4 nx_, ny_;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      el(nx_, e) = fmaf(el(B[nu], e), el(px, e), el(A[nu], e) * el(Dx, e));
-      el(ny_, e) = fmaf(el(B[nu], e), el(py, e), el(A[nu], e) * el(Dy, e));
+      el(nx_, e) = fmaf(el(bx, e), el(px, e), el(ax, e) * el(Dx, e));
+      el(ny_, e) = fmaf(el(by, e), el(py, e), el(ay, e) * el(Dy, e));
       el(Sx, e) += fmaf(P.w_new, el(nx_, e), P.w_old * el(px, e));
       el(Sy, e) += fmaf(P.w_new, el(ny_, e), P.w_old * el(py, e));
+    }
+    if (EDGE) {
+      nx_ = mask_pad(nx_, i0, P.nx);
+      ny_ = mask_pad(ny_, i0, P.nx);
     }
     st_state4(P.psi2[0], nu * Sn + c, nx_);
     st_state4(P.psi2[1], nu * Sn + c, ny_);
@@ -325,14 +427,20 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const Maps &M, 
     if (P.nl) upd /= fmaf(el(ch, e), el(p, e), 1.f);
     el(p, e) -= upd;
   }
+  if (EDGE) p = mask_pad(p, i0, P.nx);
   st_state4(P.p, c, p);
 }
 
-// One half step: edge tiles by the general path, then the interior half
-// tiles through the two-stage pipeline.  Block (32, 8).
+// One half step.  Block (32, 8), one per SM.
 template <int N, typename Maps, bool VEL>
-__global__ void __launch_bounds__(256, 1) pipe2d_kernel(const StepParams P, const Region R) {
-  extern __shared__ __align__(16) float smem[];
+__global__ void __launch_bounds__(256, 1)
+    pipe2d_kernel(const StepParams P, const Region R, const __grid_constant__ PipeMaps T) {
+  extern __shared__ __align__(128) float smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int ok;
+  // TMA destinations need 128-byte alignment: round the base up (the launch
+  // adds 128 bytes of slack)
+  float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   using VS = VelStage<N, Maps>;
   using PS = PrsStage<N, Maps>;
   constexpr int kStage = VEL ? VS::kFloats : PS::kFloats;
@@ -342,6 +450,12 @@ __global__ void __launch_bounds__(256, 1) pipe2d_kernel(const StepParams P, cons
   Maps M(P);
   M.stage(P, tab, tid);  // made visible by the first barrier below
   M.bind(tab);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbarrier_init();
+  }
+  // general-path tiles (periodic axes only)
   const int ne = R.edges();
   for (int e = blockIdx.x; e < ne; e += gridDim.x) {
     int x0, y0;
@@ -354,14 +468,14 @@ __global__ void __launch_bounds__(256, 1) pipe2d_kernel(const StepParams P, cons
                           reinterpret_cast<float(*)[kPW]>(smem + kHX * kPW), tab, false);
     __syncthreads();
   }
+  __syncthreads();  // barriers initialised, table staged, general tiles done with the stages
   const int nh = R.halves();
   int h = blockIdx.x;
   if (h >= nh) return;
   int x0, y0;
   R.half_origin(h, x0, y0);
-  if (VEL) vel_prefetch<N, Maps>(P, smem, x0, y0, tid);
-  else prs_prefetch<N, Maps>(P, smem, x0, y0, tid);
-  cp_commit();
+  if (tid == 0) issue_stage<N, Maps, VEL>(P, T, smem, &bar[0], x0, y0);
+  unsigned phase = 0;  // bit s: parity of the next completion of stage s
   int s = 0;
 #pragma unroll 1
   for (; h < nh; h += gridDim.x) {
@@ -369,16 +483,28 @@ __global__ void __launch_bounds__(256, 1) pipe2d_kernel(const StepParams P, cons
     int xn = 0, yn = 0;
     if (hn < nh) {
       R.half_origin(hn, xn, yn);
-      if (VEL) vel_prefetch<N, Maps>(P, smem + (s ^ 1) * kStage, xn, yn, tid);
-      else prs_prefetch<N, Maps>(P, smem + (s ^ 1) * kStage, xn, yn, tid);
-      cp_commit();
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
+      if (tid == 0) issue_stage<N, Maps, VEL>(P, T, smem + (s ^ 1) * kStage, &bar[s ^ 1], xn, yn);
     }
+    if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
     __syncthreads();
-    if (VEL) vel_compute<N, Maps>(P, M, smem + s * kStage, x0, y0, tid);
-    else prs_compute<N, Maps>(P, M, smem + s * kStage, x0, y0, tid);
+    if (!ok) {
+      // a copy never landed: report, let the other stage's copies finish
+      // (bounded), and leave
+      if (tid == 0) {
+        report_status(P.status, kStatusWaitTimeout);
+        if (hn < nh) mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u);
+      }
+      return;
+    }
+    phase ^= 1u << s;
+    float *cur = smem + s * kStage;
+    if (R.interior(x0, y0)) {
+      if (VEL) vel_compute<N, Maps, false>(P, M, cur, x0, y0, tid);
+      else prs_compute<N, Maps, false>(P, M, cur, x0, y0, tid);
+    } else {
+      if (VEL) vel_compute<N, Maps, true>(P, M, cur, x0, y0, tid);
+      else prs_compute<N, Maps, true>(P, M, cur, x0, y0, tid);
+    }
     __syncthreads();
     x0 = xn;
     y0 = yn;
@@ -387,45 +513,61 @@ __global__ void __launch_bounds__(256, 1) pipe2d_kernel(const StepParams P, cons
 }
 
 template <int N, typename Maps, bool VEL>
-cudaError_t pipe_launch(const StepParams &P, const Region &R, int grid, cudaStream_t st) {
+cudaError_t pipe_launch(const StepParams &P, const Region &R, int grid, const PipeMaps &T, cudaStream_t st) {
   constexpr int stage = VEL ? VelStage<N, Maps>::kFloats : PrsStage<N, Maps>::kFloats;
-  constexpr size_t bytes = sizeof(float) * (2 * (size_t)stage + Maps::kSmemFloats);
-  static_assert(bytes <= 227 * 1024, "stages exceed shared memory");
+  constexpr size_t bytes = sizeof(float) * (2 * (size_t)stage + Maps::kSmemFloats) + 128;
+  static_assert(bytes <= 220 * 1024, "stages exceed shared memory");
   cudaError_t e = cudaFuncSetAttribute(pipe2d_kernel<N, Maps, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
-  pipe2d_kernel<N, Maps, VEL><<<grid, dim3(32, kBY), bytes, st>>>(P, R);
+  pipe2d_kernel<N, Maps, VEL><<<grid, dim3(32, kBY), bytes, st>>>(P, R, T);
   return cudaGetLastError();
 }
 
 template <typename Maps, bool VEL>
-cudaError_t pipe_dispatch(const StepParams &P, const Region &R, int grid, cudaStream_t st) {
+cudaError_t pipe_dispatch(const StepParams &P, const Region &R, int grid, const PipeMaps &T, cudaStream_t st) {
   switch (P.n_relax) {
-    case 0: return pipe_launch<0, Maps, VEL>(P, R, grid, st);
-    case 1: return pipe_launch<1, Maps, VEL>(P, R, grid, st);
-    case 2: return pipe_launch<2, Maps, VEL>(P, R, grid, st);
-    case 3: return pipe_launch<3, Maps, VEL>(P, R, grid, st);
-    case 4: return pipe_launch<4, Maps, VEL>(P, R, grid, st);
+    case 0: return pipe_launch<0, Maps, VEL>(P, R, grid, T, st);
+    case 1: return pipe_launch<1, Maps, VEL>(P, R, grid, T, st);
+    case 2: return pipe_launch<2, Maps, VEL>(P, R, grid, T, st);
+    case 3: return pipe_launch<3, Maps, VEL>(P, R, grid, T, st);
+    case 4: return pipe_launch<4, Maps, VEL>(P, R, grid, T, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-// interior tiles as interior_tile defines them: x0 >= Lx, x0 + kTX + Lx <= nx
 Region region_of(const StepParams &P) {
   Region R;
-  const int Lx = P.L[0] > 4 ? P.L[0] : 4, Ly = P.L[1] > 4 ? P.L[1] : 4;
+  R.nx = P.nx;
+  R.ny = P.ny;
+  R.Lx = P.L[0] > 4 ? P.L[0] : 4;
+  R.Ly = P.L[1] > 4 ? P.L[1] : 4;
   R.tnx = (P.nx + kTX - 1) / kTX;
   R.tny = (P.ny + kTY - 1) / kTY;
-  R.tx_lo = (Lx + kTX - 1) / kTX;
-  R.ty_lo = (Ly + kTY - 1) / kTY;
-  R.ntx = (P.nx - Lx) / kTX - R.tx_lo;
-  R.nty = (P.ny - Ly) / kTY - R.ty_lo;
+  R.split = P.periodic[0] || P.periodic[1];
+  if (!R.split) {
+    // every half tile of the grid is staged
+    R.tx_lo = 0;
+    R.ntx = R.tnx;
+    R.ty_lo = 0;
+    R.nty = 0;
+    R.hy_lo = 0;
+    R.nhy = (P.ny + kHT - 1) / kHT;
+    return R;
+  }
+  // interior tiles as interior_tile defines them: x0 >= Lx, x0 + kTX + Lx <= nx
+  R.tx_lo = (R.Lx + kTX - 1) / kTX;
+  R.ty_lo = (R.Ly + kTY - 1) / kTY;
+  R.ntx = (P.nx - R.Lx) / kTX - R.tx_lo;
+  R.nty = (P.ny - R.Ly) / kTY - R.ty_lo;
   if (R.ntx <= 0 || R.nty <= 0) {
     R.ntx = 0;
     R.nty = 0;
     R.tx_lo = 0;
     R.ty_lo = 0;
   }
+  R.hy_lo = 2 * R.ty_lo;
+  R.nhy = 2 * R.nty;
   return R;
 }
 
@@ -435,21 +577,108 @@ bool pipe2d_supported(const StepParams &P, int map_kind) {
   return P.nz == 1 && (map_kind == 0 || map_kind == 2) && P.n_relax >= 0 && P.n_relax <= kMaxRelax;
 }
 
-bool pipe2d_preferred(const StepParams &P, int map_kind) {
-  // measured on a 4096^2 N = 4 grid: faster than the tile kernels for the
-  // tissue index (the tile kernels' table lookups stall them), slower for
-  // dense float maps
-  return pipe2d_supported(P, map_kind) && map_kind == 2;
-}
+bool pipe2d_preferred(const StepParams &P, int map_kind) { return pipe2d_supported(P, map_kind); }
 
-cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, cudaStream_t st) {
+cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, const PipeMaps &T,
+                          cudaStream_t st) {
   const Region R = region_of(P);
   if (map_kind == 2)
-    return vel ? pipe_dispatch<IdxMaps, true>(P, R, grid, st) : pipe_dispatch<IdxMaps, false>(P, R, grid, st);
+    return vel ? pipe_dispatch<IdxMaps, true>(P, R, grid, T, st) : pipe_dispatch<IdxMaps, false>(P, R, grid, T, st);
   if (map_kind == 0)
-    return vel ? pipe_dispatch<DenseMaps<float>, true>(P, R, grid, st)
-               : pipe_dispatch<DenseMaps<float>, false>(P, R, grid, st);
+    return vel ? pipe_dispatch<DenseMaps<float>, true>(P, R, grid, T, st)
+               : pipe_dispatch<DenseMaps<float>, false>(P, R, grid, T, st);
   return cudaErrorInvalidValue;
+}
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiled>(f);
+  }();
+  return fn;
+}
+
+// float (or uint8) tensor map over [ny][nx] (rank 2, row stride pitch) or
+// [n3][ny][nx] (rank 3, plane stride s3 elements) with a box of bx x by
+// (x bz); cells outside the tensor read as zero
+bool encode(CUtensorMap *m, const void *base, const StepParams &P, int rank, int n3, long long s3, int bx, int by,
+            int bz, bool u8 = false) {
+  EncodeTiled fn = encoder();
+  if (!fn || !base) return false;
+  const cuuint64_t es = u8 ? 1 : 4;
+  cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)n3};
+  cuuint64_t strides[2] = {(cuuint64_t)P.pitch * es, (cuuint64_t)s3 * es};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+            const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t build_pipe2d_maps(const StepParams &P, int map_kind, PipeMaps *vel, PipeMaps *prs, const char **why) {
+  *vel = PipeMaps{};
+  *prs = PipeMaps{};
+  if (!encoder()) {
+    *why = "cuTensorMapEncodeTiled is not available from the driver";
+    return cudaErrorInvalidValue;
+  }
+  const int N = P.n_relax;
+  const long long S = P.npts_alloc;
+  const bool dense = map_kind == 0;
+  bool ok = true;
+  // velocity half step
+  ok = ok && encode(&vel->m[0], P.p, P, 2, 1, S, kCW, kHT + 7, 1);
+  if (dense) ok = ok && encode(&vel->m[1], P.rho, P, 2, 1, S, kRWp, kHT + 1, 1);
+  else ok = ok && encode(&vel->m[1], P.tissue, P, 2, 1, S, kIW, kHT + 1, 1, true);
+  ok = ok && encode(&vel->m[2], P.v[0], P, 2, 1, S, kTX, kHT, 1);
+  ok = ok && encode(&vel->m[3], P.v[1], P, 2, 1, S, kTX, kHT, 1);
+  if (N > 0) {
+    ok = ok && encode(&vel->m[4], P.psi1[0], P, 3, N, S, kTX, kHT, N);
+    ok = ok && encode(&vel->m[5], P.psi1[1], P, 3, N, S, kTX, kHT, N);
+  }
+  if (dense) {
+    ok = ok && encode(&vel->m[6], P.ik1, P, 2, 1, S, kTX, kHT, 1);
+    if (N > 0) {
+      ok = ok && encode(&vel->m[7], P.a1, P, 3, N, S, kTX, kHT, N);
+      ok = ok && encode(&vel->m[8], P.b1, P, 3, N, S, kTX, kHT, N);
+    }
+  }
+  // pressure half step
+  ok = ok && encode(&prs->m[0], P.v[0], P, 2, 1, S, kCW, kHT + 2, 1);
+  ok = ok && encode(&prs->m[1], P.v[1], P, 2, 1, S, kCW, kHT + 7, 1);
+  ok = ok && encode(&prs->m[2], P.p, P, 2, 1, S, kTX, kHT, 1);
+  if (N > 0) {
+    ok = ok && encode(&prs->m[3], P.psi2[0], P, 3, N, S, kTX, kHT, N);
+    ok = ok && encode(&prs->m[4], P.psi2[1], P, 3, N, S, kTX, kHT, N);
+  }
+  if (!dense) ok = ok && encode(&prs->m[5], P.tissue, P, 2, 1, S, kTX, kHT, 1, true);
+  if (dense) {
+    ok = ok && encode(&prs->m[5], P.ik2, P, 2, 1, S, kTX, kHT, 1);
+    ok = ok && encode(&prs->m[6], P.K, P, 2, 1, S, kTX, kHT, 1);
+    if (P.nl) ok = ok && encode(&prs->m[7], P.chi, P, 2, 1, S, kTX, kHT, 1);
+    if (N > 0) {
+      ok = ok && encode(&prs->m[8], P.a2, P, 3, N, S, kTX, kHT, N);
+      ok = ok && encode(&prs->m[9], P.b2, P, 3, N, S, kTX, kHT, N);
+    }
+  }
+  if (!ok) {
+    *why = "cuTensorMapEncodeTiled rejected a map";
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace fw2

@@ -78,6 +78,7 @@ EXPORTS = {
                                    C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "fw2_field_absmax_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                            C.c_void_p]),
+    "fw2_selftest_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
     "fw2_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "fw2_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "fw2_batch_synchronize": (C.c_int, [C.c_void_p]),
@@ -272,6 +273,13 @@ def fw2_profile_read(ctx):
     tv, nv, tp, np_ = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
     _check(lib().fw2_profile_read(ctx, C.byref(tv), C.byref(nv), C.byref(tp), C.byref(np_)), ctx)
     return tv.value, nv.value, tp.value, np_.value
+
+
+def fw2_selftest_bounded_wait(limit_ns: int) -> bool:
+    """True when a wait on a barrier nobody arrives on gave up after limit_ns."""
+    t = C.c_int32(-1)
+    _check(lib().fw2_selftest_bounded_wait(int(limit_ns), C.byref(t)))
+    return bool(t.value)
 
 
 def fw2_field_absmax_noalloc(field, row_len: int, n_rows: int, row_pitch: int, out, stream=None) -> int:
