@@ -229,6 +229,18 @@ __device__ __forceinline__ void x_strip_coef(const StepParams &P, int nu, int i0
   const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[0] : P.sa2[0]);
   const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[0] : P.sb2[0]);
   const long long row = (long long)nu * P.strip_nu[0] + (long long)j * (2 * L);
+  // a group wholly inside one side of the strip reads 16 aligned bytes when
+  // the strip rows (2L values) and the high side's offset keep that alignment
+  if ((L & 1) == 0) {
+    int sc0 = -1;
+    if (i0 + 3 < L) sc0 = i0;
+    else if ((P.nx & 3) == 0 && i0 >= P.nx - L && i0 + 3 < P.nx) sc0 = i0 - (P.nx - 2 * L);
+    if (sc0 >= 0) {
+      a = ldmap4(sa, row + sc0);
+      b = ldb4(sb, row + sc0);
+      return;
+    }
+  }
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int x = i0 + e;
