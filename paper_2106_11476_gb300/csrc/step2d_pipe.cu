@@ -2,15 +2,15 @@
 // functions of tile2d.cuh (bitwise the same results), one launch per half
 // step, one block per SM.
 //
-// The grid is walked in half tiles of 128 x 8 cells through a two-stage
-// pipeline.  For the next half tile one thread issues tiled TMA tensor copies
-// into a shared-memory stage, one box per array: the stencil operand with
-// its halo, the density tile, every streamed array, the N mechanisms of a
-// memory variable or of a relaxation map in one 3D box.  They complete on the
-// stage's mbarrier while all warps compute the current half tile from the
-// other stage, so a whole stage (up to ~95 KB) stays in flight per SM without
-// registers or load instructions of the computing threads; results go
-// straight from registers to HBM.
+// The grid is walked in half tiles of 128 x 8 cells through a ring of two to
+// four shared-memory stages (as many as fit).  For a coming half tile one
+// thread issues tiled TMA tensor copies into a free stage, one box per array:
+// the stencil operand with its halo, the density tile (or the uint8 tissue
+// index), every streamed array, the N mechanisms of a memory variable or of a
+// relaxation map in one 3D box.  They complete on the stage's mbarrier while
+// all warps compute the current half tile from another stage, so up to
+// ~190 KB stay in flight per SM without registers or load instructions of the
+// computing threads; results go straight from registers to HBM.
 //
 // Boundaries: the copies read zero outside the grid (the zero-outside rule of
 // the operand halo); half tiles at the edge of the grid or in a C-PML strip
@@ -443,28 +443,38 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const Maps &M, 
   st_state4(P.p, c, p);
 }
 
+// Ring of stages: as many as fit next to the maps' table (2 .. 4).
+template <int N, typename Maps, bool VEL>
+struct Ring {
+  static constexpr int kStage = VEL ? VelStage<N, Maps>::kFloats : PrsStage<N, Maps>::kFloats;
+  static constexpr int kEdge = VEL ? VelStage<N, Maps>::kEdge : PrsStage<N, Maps>::kEdge;
+  static constexpr int kBudget = (220 * 1024 - 128) / 4 - Maps::kSmemFloats;  // floats
+  static constexpr int kFit = kBudget / kStage;
+  static constexpr int kStages = kFit > 4 ? 4 : kFit;
+  static constexpr size_t kBytes = sizeof(float) * ((size_t)kStages * kStage + Maps::kSmemFloats) + 128;
+  static_assert(kStages >= 2, "two stages must fit in shared memory");
+  static_assert(kEdge <= kStages * kStage, "a general tile must fit in the stages");
+};
+
 // One half step.  Block (32, 8), one per SM.
 template <int N, typename Maps, bool VEL>
 __global__ void __launch_bounds__(256, 1)
     pipe2d_kernel(const StepParams P, const Region R, const __grid_constant__ PipeMaps T) {
+  using G = Ring<N, Maps, VEL>;
+  constexpr int kS = G::kStages, kStage = G::kStage;
   extern __shared__ __align__(128) float smem_raw[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[kS];
   __shared__ int ok;
   // TMA destinations need 128-byte alignment: round the base up (the launch
   // adds 128 bytes of slack)
   float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  using VS = VelStage<N, Maps>;
-  using PS = PrsStage<N, Maps>;
-  constexpr int kStage = VEL ? VS::kFloats : PS::kFloats;
-  static_assert((VEL ? VS::kEdge : PS::kEdge) <= 2 * kStage, "edge tile must fit in the stages");
-  float *tab = smem + 2 * kStage;
+  float *tab = smem + kS * kStage;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   Maps M(P);
   M.stage(P, tab, tid);  // made visible by the first barrier below
   M.bind(tab);
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int q = 0; q < kS; ++q) mbar_init(&bar[q], 1);
     fence_mbarrier_init();
   }
   // general-path tiles (periodic axes only)
@@ -484,31 +494,49 @@ __global__ void __launch_bounds__(256, 1)
   const int nh = R.halves();
   int h = blockIdx.x;
   if (h >= nh) return;
-  int x0, y0;
-  R.half_origin(h, x0, y0);
-  if (tid == 0) issue_stage<N, Maps, VEL>(P, T, smem, &bar[0], x0, y0);
-  unsigned phase = 0;  // bit s: parity of the next completion of stage s
+  // this block's half tiles are h, h + grid, ...; the first kS - 1 go out now,
+  // then each iteration issues one more into the stage freed last
+  unsigned phase = 0;    // bit q: parity of the next completion of stage q
+  unsigned pending = 0;  // bit q: copies issued into stage q, not consumed
+  int hs = h;            // next half tile to issue
+  for (int q = 0; q < kS - 1; ++q, hs += gridDim.x) {
+    if (hs >= nh) break;
+    if (tid == 0) {
+      int xq, yq;
+      R.half_origin(hs, xq, yq);
+      issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
+    }
+    pending |= 1u << q;
+  }
   int s = 0;
 #pragma unroll 1
   for (; h < nh; h += gridDim.x) {
-    const int hn = h + gridDim.x;
-    int xn = 0, yn = 0;
-    if (hn < nh) {
-      R.half_origin(hn, xn, yn);
-      if (tid == 0) issue_stage<N, Maps, VEL>(P, T, smem + (s ^ 1) * kStage, &bar[s ^ 1], xn, yn);
+    if (hs < nh) {
+      const int q = (s + kS - 1) % kS;  // computed in the previous iteration
+      if (tid == 0) {
+        int xq, yq;
+        R.half_origin(hs, xq, yq);
+        issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
+      }
+      pending |= 1u << q;
+      hs += gridDim.x;
     }
     if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
     __syncthreads();
     if (!ok) {
-      // a copy never landed: report, let the other stage's copies finish
+      // a copy never landed: report, let the other stages' copies finish
       // (bounded), and leave
       if (tid == 0) {
         report_status(P.status, kStatusWaitTimeout);
-        if (hn < nh) mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u);
+        for (int q = 0; q < kS; ++q)
+          if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
       }
       return;
     }
     phase ^= 1u << s;
+    pending &= ~(1u << s);
+    int x0, y0;
+    R.half_origin(h, x0, y0);
     float *cur = smem + s * kStage;
     if (R.interior(x0, y0)) {
       if (VEL) vel_compute<N, Maps, false>(P, M, cur, x0, y0, tid);
@@ -518,17 +546,13 @@ __global__ void __launch_bounds__(256, 1)
       else prs_compute<N, Maps, true>(P, M, cur, x0, y0, tid);
     }
     __syncthreads();
-    x0 = xn;
-    y0 = yn;
-    s ^= 1;
+    s = (s + 1) % kS;
   }
 }
 
 template <int N, typename Maps, bool VEL>
 cudaError_t pipe_launch(const StepParams &P, const Region &R, int grid, const PipeMaps &T, cudaStream_t st) {
-  constexpr int stage = VEL ? VelStage<N, Maps>::kFloats : PrsStage<N, Maps>::kFloats;
-  constexpr size_t bytes = sizeof(float) * (2 * (size_t)stage + Maps::kSmemFloats) + 128;
-  static_assert(bytes <= 220 * 1024, "stages exceed shared memory");
+  constexpr size_t bytes = Ring<N, Maps, VEL>::kBytes;
   cudaError_t e = cudaFuncSetAttribute(pipe2d_kernel<N, Maps, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
