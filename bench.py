@@ -104,7 +104,8 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("step2d.cu", "step3d.cu", "coef.cuh", "fw2_internal.cuh"):
+    for f in ("step2d.cu", "step2d_pipe.cu", "tile2d.cuh", "async.cuh", "maps.cuh", "tmap.h", "step3d.cu",
+              "coef.cuh", "fw2_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2106_11476_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -270,6 +271,8 @@ def run_fw2(args, rank, world, dist):
     elapsed_ms = float(events[0].elapsed_time(events[-1]))
     vel_ms, nv, prs_ms, np_ = fw2.fw2_profile_read(sim.ctx)
     fw2.fw2_profile(sim.ctx, False)
+    if fw2.fw2_kernel_path(sim.ctx) == "pipe":
+        kv, kp = "pipe2d_vel", "pipe2d_prs"
     t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -283,7 +286,7 @@ def run_fw2(args, rank, world, dist):
     dom_bytes = vel_b if dom == kv else prs_b
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    traffic = committed_traffic(dom)
+    traffic = committed_traffic(f"{args.workload}:{maps}:{n}:{dom}")
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": round(dom_ms, 5),

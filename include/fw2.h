@@ -270,6 +270,10 @@ fw2_status fw2_field_absmax_noalloc(const float *field, int64_t row_len, int64_t
  * 0 otherwise.  Synchronous on the default stream; needs no context.  Errors:
  * FW2_EINVAL (null pointer, limit out of range), FW2_ECUDA. */
 fw2_status fw2_selftest_bounded_wait(int64_t limit_ns, int32_t *timed_out);
+/* Kernel path the context's half steps take, resolved once the coefficients
+ * are built (first fw2_step): FW2_PATH_TILE or FW2_PATH_PIPE (3D contexts and
+ * bf16 maps: FW2_PATH_TILE); FW2_PATH_AUTO before the first step. */
+fw2_status fw2_kernel_path(fw2_ctx *ctx, int32_t *path);
 /* Bytes of device memory held by the context. */
 fw2_status fw2_device_bytes(fw2_ctx *ctx, int64_t *bytes);
 /* Launches of library kernels since creation (all kinds). */

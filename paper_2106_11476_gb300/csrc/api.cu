@@ -358,6 +358,12 @@ extern "C" {
 
 int32_t fw2_abi_version(void) { return 1; }
 
+fw2_status fw2_kernel_path(fw2_ctx *c, int32_t *path) {
+  if (!c || !path) return FW2_EINVAL;
+  *path = !c->finalized ? FW2_PATH_AUTO : (c->pipe ? FW2_PATH_PIPE : FW2_PATH_TILE);
+  return FW2_OK;
+}
+
 fw2_status fw2_selftest_bounded_wait(int64_t limit_ns, int32_t *timed_out) {
   if (!timed_out || limit_ns < 1 || limit_ns > 10000000000ll)
     return fail(nullptr, FW2_EINVAL, "timed_out is required and limit_ns must lie in [1, 1e10]");

@@ -79,6 +79,7 @@ EXPORTS = {
     "fw2_field_absmax_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                            C.c_void_p]),
     "fw2_selftest_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
+    "fw2_kernel_path": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "fw2_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "fw2_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "fw2_batch_synchronize": (C.c_int, [C.c_void_p]),
@@ -273,6 +274,13 @@ def fw2_profile_read(ctx):
     tv, nv, tp, np_ = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
     _check(lib().fw2_profile_read(ctx, C.byref(tv), C.byref(nv), C.byref(tp), C.byref(np_)), ctx)
     return tv.value, nv.value, tp.value, np_.value
+
+
+def fw2_kernel_path(ctx) -> str:
+    """'tile' or 'pipe' once the context has stepped ('auto' before)."""
+    v = C.c_int32(0)
+    _check(lib().fw2_kernel_path(ctx, C.byref(v)), ctx)
+    return {0: "auto", 1: "tile", 2: "pipe"}[v.value]
 
 
 def fw2_selftest_bounded_wait(limit_ns: int) -> bool:
