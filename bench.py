@@ -272,7 +272,7 @@ def run_fw2(args, rank, world, dist):
     vel_ms, nv, prs_ms, np_ = fw2.fw2_profile_read(sim.ctx)
     fw2.fw2_profile(sim.ctx, False)
     if fw2.fw2_kernel_path(sim.ctx) == "pipe":
-        kv, kp = "pipe2d_vel", "pipe2d_prs"
+        kv, kp = ("pipe2d_vel", "pipe2d_prs") if len(prob.shape) == 2 else ("pipe3d_vel", "pipe3d_prs")
     t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfw2.so")
-SOURCES = ["api.cu", "prep.cu", "aux.cu", "step2d.cu", "step2d_pipe.cu", "step3d.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "prep.cu", "aux.cu", "step2d.cu", "step2d_pipe.cu", "step3d.cu", "step3d_pipe.cu", "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

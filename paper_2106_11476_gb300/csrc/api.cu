@@ -226,12 +226,16 @@ fw2_status finalize(fw2_ctx *c) {
   P.tissue = Q.tissue_out;
   P.table = Q.table_out;
   P.status = c->d_status;
-  c->pipe = c->nd == 2 && ((cfg.kernel_path == FW2_PATH_AUTO && pipe2d_preferred(P, c->map_kind)) ||
-                            (cfg.kernel_path == FW2_PATH_PIPE && pipe2d_supported(P, c->map_kind)));
+  if (c->nd == 2)
+    c->pipe = (cfg.kernel_path == FW2_PATH_AUTO && pipe2d_preferred(P, c->map_kind)) ||
+              (cfg.kernel_path == FW2_PATH_PIPE && pipe2d_supported(P, c->map_kind));
+  else
+    c->pipe = cfg.kernel_path != FW2_PATH_TILE && pipe3d_supported(P, c->map_kind);
   if (c->pipe) {
     const char *why = "";
-    if (build_pipe2d_maps(P, c->map_kind, &c->tm_vel, &c->tm_prs, &why) != cudaSuccess)
-      return fail(c, FW2_ECUDA, "tensor maps of the pipelined kernels: %s", why);
+    const cudaError_t e = c->nd == 2 ? build_pipe2d_maps(P, c->map_kind, &c->tm_vel, &c->tm_prs, &why)
+                                     : build_pipe3d_maps(P, &c->tm_vel, &c->tm_prs, &why);
+    if (e != cudaSuccess) return fail(c, FW2_ECUDA, "tensor maps of the pipelined kernels: %s", why);
   }
   c->finalized = true;
   return FW2_OK;
@@ -707,7 +711,8 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
       ev = {take_event(c), take_event(c)};
       CK(c, cudaEventRecord(ev.first, c->stream));
     }
-    CK(c, c->pipe ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->tm_vel, c->stream)
+    CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->tm_vel, c->stream)
+                                : launch_pipe3d(true, P, c->n_sm, c->tm_vel, c->stream))
                   : c->nd == 2 ? launch_vel2d(P, c->map_kind, c->stream) : launch_vel3d(P, c->map_kind, c->stream));
     c->launches++;
     if (c->profiling) {
@@ -724,7 +729,8 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
       }
     }
     if (c->profiling) CK(c, cudaEventRecord(ev.first, c->stream));
-    CK(c, c->pipe ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->tm_prs, c->stream)
+    CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->tm_prs, c->stream)
+                                : launch_pipe3d(false, P, c->n_sm, c->tm_prs, c->stream))
                   : c->nd == 2 ? launch_prs2d(P, c->map_kind, c->stream) : launch_prs3d(P, c->map_kind, c->stream));
     c->launches++;
     if (c->profiling) {

@@ -126,6 +126,10 @@ bool pipe2d_preferred(const StepParams &P, int map_kind);
 cudaError_t build_pipe2d_maps(const StepParams &P, int map_kind, PipeMaps *vel, PipeMaps *prs, const char **why);
 cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, const PipeMaps &T,
                           cudaStream_t s);
+// persistent pipelined 3D half step (bf16 maps, N <= 3, no periodic axis)
+bool pipe3d_supported(const StepParams &P, int map_kind);
+cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why);
+cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t s);
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
 

@@ -646,23 +646,37 @@ EncodeTiled encoder() {
 
 // float (or uint8) tensor map over [ny][nx] (rank 2, row stride pitch) or
 // [n3][ny][nx] (rank 3, plane stride s3 elements) with a box of bx x by
-// (x bz); cells outside the tensor read as zero
+// (x bz)
 bool encode(CUtensorMap *m, const void *base, const StepParams &P, int rank, int n3, long long s3, int bx, int by,
             int bz, bool u8 = false) {
-  EncodeTiled fn = encoder();
-  if (!fn || !base) return false;
-  const cuuint64_t es = u8 ? 1 : 4;
-  cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)n3};
-  cuuint64_t strides[2] = {(cuuint64_t)P.pitch * es, (cuuint64_t)s3 * es};
-  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
-  cuuint32_t estr[3] = {1, 1, 1};
-  return fn(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
-            const_cast<void *>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  const unsigned long long es = u8 ? 1 : 4;
+  const unsigned long long dims[3] = {(unsigned long long)P.nx, (unsigned long long)P.ny, (unsigned long long)n3};
+  const unsigned long long strides[2] = {(unsigned long long)P.pitch * es, (unsigned long long)s3 * es};
+  const unsigned box[3] = {(unsigned)bx, (unsigned)by, (unsigned)bz};
+  return encode_tensor_map(m, base, (int)es, rank, dims, strides, box);
 }
 
 }  // namespace
+
+bool encode_tensor_map(CUtensorMap *m, const void *base, int elem_bytes, int rank, const unsigned long long *dims,
+                       const unsigned long long *strides_bytes, const unsigned *box) {
+  EncodeTiled fn = encoder();
+  if (!fn || !base || rank < 2 || rank > 5) return false;
+  cuuint64_t d[5], st[4];
+  cuuint32_t b[5], e[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    e[i] = 1;
+  }
+  for (int i = 0; i + 1 < rank; ++i) st[i] = strides_bytes[i];
+  const CUtensorMapDataType t = elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                : elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(m, t, (cuuint32_t)rank, const_cast<void *>(base), d, st, b, e, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
 
 cudaError_t build_pipe2d_maps(const StepParams &P, int map_kind, PipeMaps *vel, PipeMaps *prs, const char **why) {
   *vel = PipeMaps{};

@@ -1,0 +1,609 @@
+// Pipelined persistent 3D half steps (sm_103a) for bf16 coefficient maps;
+// same arithmetic as step3d.cu (bitwise the same results), one launch per
+// half step, one block of 256 threads per SM.
+//
+// Work unit: a 128 x 8 half tile of one z plane, x fastest, then y, then z.
+// For a coming unit one thread issues tiled TMA tensor copies into a free
+// stage of a two-stage ring (one box per array): the xy operand plane with
+// its halo, the operand's own 8-plane z column (x and y taps from the halo
+// plane, z taps from the column; the column's planes are the neighbouring
+// units' planes, so their re-reads come from L2), the density of the plane
+// and of the next one, the velocity (or pressure) of the unit, all 3N memory
+// variables of the half step in one 4D box, and the bf16 maps (a and b of the
+// N mechanisms in one 4D box each).  Copies complete on the stage's mbarrier
+// while all threads compute the current unit from the other stage; no
+// computing thread issues a global load outside the C-PML strips.
+//
+// Boundaries as in the 2D pipeline: the copies read zero outside the grid;
+// units at the grid's edge or in a C-PML strip clamp the density to the last
+// cell, take each axis' C-PML coefficients from its strip (all mechanisms
+// loaded before the first store) and store nothing outside the grid.
+// Periodic axes are not taken by this path (the tile kernels run them).
+#include "async.cuh"
+#include "coef.cuh"
+#include "tmap.h"
+
+namespace fw2 {
+
+namespace {
+
+constexpr int kHT = 8;            // rows of a unit
+constexpr int kCW = kTX + 8;      // operand halo columns x0-4 .. x0+TX+3
+constexpr int kRWb = kTX + 8;     // staged bf16 density columns x0 .. x0+TX+7 (16-byte rows)
+constexpr int kRWf = kTX + 4;     // float density tile columns x0 .. x0+TX+3
+constexpr int kArr = kHT * kTX;   // elements of one array per unit
+
+using bf16 = __nv_bfloat16;
+
+constexpr int round32(int n) { return (n + 31) & ~31; }  // floats: 128-byte regions
+constexpr int fl(int bytes) { return (bytes + 3) / 4; }
+
+__device__ __forceinline__ float4 sld4(const float *s) { return *reinterpret_cast<const float4 *>(s); }
+__device__ __forceinline__ float4 sldh4(const bf16 *s) {
+  const uint2 u = *reinterpret_cast<const uint2 *>(s);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+// decay factors: bf16 maps hold 1 - b
+__device__ __forceinline__ float4 sldb4(const bf16 *s) {
+  const float4 v = sldh4(s);
+  return make_float4(1.f - v.x, 1.f - v.y, 1.f - v.z, 1.f - v.w);
+}
+
+// ------------------------------------------------------------- stages ---
+// velocity: p halo plane [15][136] (rows y0-3 .. y0+11), p column [8][8][128]
+// (planes k-3 .. k+4), density bf16 [2][9][136] (planes k, k+1), v [3][8][128],
+// psi1 [3N][8][128], 1/kappa1 bf16 [8][128], a1, b1 bf16 [N][8][128]
+template <int N>
+struct Vel3 {
+  static constexpr int kHalo = round32((kHT + 7) * kCW);
+  static constexpr int kCol = 8 * kArr;
+  static constexpr int kRho = round32(fl(2 * (kHT + 1) * kRWb * 2));
+  static constexpr int kV = 3 * kArr;
+  static constexpr int kPsi = 3 * N * kArr;
+  static constexpr int kK = round32(fl(kArr * 2));
+  static constexpr int kAB = round32(fl(N * kArr * 2));
+  static constexpr int oHalo = 0, oCol = oHalo + kHalo, oRho = oCol + kCol, oV = oRho + kRho, oPsi = oV + kV,
+                       oK = oPsi + kPsi, oA = oK + kK, oB = oA + kAB;
+  static constexpr int kFloats = round32(oB + kAB);
+  static constexpr unsigned kBytes =
+      4u * ((kHT + 7) * kCW + kCol + kV + kPsi) + 2u * (2 * (kHT + 1) * kRWb + kArr + 2 * N * kArr);
+};
+
+// pressure: v_x plane [8][136] (x halo), v_y plane [15][128] (rows y0-4 ..),
+// v_z column [8][8][128] (planes k-4 .. k+3), p [8][128], psi2 [3N][8][128],
+// 1/kappa2, K, chi bf16 [8][128], a2, b2 bf16 [N][8][128]
+template <int N>
+struct Prs3 {
+  static constexpr int kVx = round32(kHT * kCW);
+  static constexpr int kVy = round32((kHT + 7) * kTX);
+  static constexpr int kCol = 8 * kArr;
+  static constexpr int kP = kArr;
+  static constexpr int kPsi = 3 * N * kArr;
+  static constexpr int kK = round32(fl(kArr * 2));
+  static constexpr int kAB = round32(fl(N * kArr * 2));
+  static constexpr int oVx = 0, oVy = oVx + kVx, oCol = oVy + kVy, oP = oCol + kCol, oPsi = oP + kP,
+                       oIk = oPsi + kPsi, oKm = oIk + kK, oChi = oKm + kK, oA = oChi + kK, oB = oA + kAB;
+  static constexpr int kFloats = round32(oB + kAB);
+  static constexpr unsigned kBytesNoChi =
+      4u * (kHT * kCW + (kHT + 7) * kTX + kCol + kP + kPsi) + 2u * (2 * kArr + 2 * N * kArr);
+};
+
+// density tile (float) built from the staged bf16 planes: [2][9][132]
+constexpr int kRhoTile = 2 * (kHT + 1) * kRWf;
+
+template <int N, bool VEL>
+struct Ring3 {
+  static constexpr int kStage = VEL ? Vel3<N>::kFloats : Prs3<N>::kFloats;
+  static constexpr int kExtra = VEL ? kRhoTile : 0;
+  static constexpr size_t kBytes = sizeof(float) * (2 * (size_t)kStage + kExtra) + 128;
+};
+
+// Work: units of 128 x 8 cells per plane, x fastest.
+struct Region3 {
+  int nx, ny, nz, Lx, Ly, Lz;
+  int tnx, nhy;  // x tiles, half-tile rows per plane
+  __device__ __forceinline__ long long units() const { return (long long)tnx * nhy * nz; }
+  __device__ __forceinline__ void origin(long long u, int &x0, int &y0, int &k) const {
+    const int per = tnx * nhy;
+    k = (int)(u / per);
+    const int r = (int)(u - (long long)k * per);
+    x0 = (r % tnx) * kTX;
+    y0 = (r / tnx) * kHT;
+  }
+  __device__ __forceinline__ bool interior(int x0, int y0, int k) const {
+    return x0 >= Lx && x0 + kTX + Lx <= nx && y0 >= Ly && y0 + kHT + Ly <= ny && k >= Lz && k + Lz < nz;
+  }
+};
+
+template <int N, bool VEL>
+__device__ __forceinline__ void issue3(const PipeMaps &T, float *st, uint64_t *bar, int x0, int y0, int k,
+                                       bool nl) {
+  fence_proxy_async_smem();
+  if (VEL) {
+    using S = Vel3<N>;
+    mbar_arrive_expect_tx(bar, S::kBytes);
+    tma_load_3d(st + S::oHalo, &T.m[0], x0 - 4, y0 - 3, k, bar);
+    tma_load_3d(st + S::oCol, &T.m[1], x0, y0, k - 3, bar);
+    tma_load_3d(st + S::oRho, &T.m[2], x0, y0, k, bar);
+    tma_load_4d(st + S::oV, &T.m[3], x0, y0, k, 0, bar);
+    if (N > 0) tma_load_4d(st + S::oPsi, &T.m[4], x0, y0, k, 0, bar);
+    tma_load_3d(st + S::oK, &T.m[5], x0, y0, k, bar);
+    if (N > 0) {
+      tma_load_4d(st + S::oA, &T.m[6], x0, y0, k, 0, bar);
+      tma_load_4d(st + S::oB, &T.m[7], x0, y0, k, 0, bar);
+    }
+  } else {
+    using S = Prs3<N>;
+    mbar_arrive_expect_tx(bar, S::kBytesNoChi + (nl ? 2u * kArr : 0u));
+    tma_load_3d(st + S::oVx, &T.m[0], x0 - 4, y0, k, bar);
+    tma_load_3d(st + S::oVy, &T.m[1], x0, y0 - 4, k, bar);
+    tma_load_3d(st + S::oCol, &T.m[2], x0, y0, k - 4, bar);
+    tma_load_3d(st + S::oP, &T.m[3], x0, y0, k, bar);
+    if (N > 0) tma_load_4d(st + S::oPsi, &T.m[4], x0, y0, k, 0, bar);
+    tma_load_3d(st + S::oIk, &T.m[5], x0, y0, k, bar);
+    tma_load_3d(st + S::oKm, &T.m[6], x0, y0, k, bar);
+    if (nl) tma_load_3d(st + S::oChi, &T.m[7], x0, y0, k, bar);
+    if (N > 0) {
+      tma_load_4d(st + S::oA, &T.m[8], x0, y0, k, 0, bar);
+      tma_load_4d(st + S::oB, &T.m[9], x0, y0, k, 0, bar);
+    }
+  }
+}
+
+// a, b along axis Q (OP: 1 faces, 2 centres) of mechanism nu at the four
+// cells of an edge group, from that axis' C-PML strip where the cells lie in
+// it (coef4 of the tile path); unchanged elsewhere
+template <int Q, int OP>
+__device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int j, int k, float4 &a, float4 &b) {
+  const bf16 *sa = static_cast<const bf16 *>(OP == 1 ? P.sa1[Q] : P.sa2[Q]);
+  const bf16 *sb = static_cast<const bf16 *>(OP == 1 ? P.sb1[Q] : P.sb2[Q]);
+  const int L = P.L[Q];
+  if (L <= 0) return;
+  if (Q == 0) {
+    if (!(i0 < L || i0 + 3 >= P.nx - L)) return;
+    const long long row = (long long)nu * P.strip_nu[0] + ((long long)k * P.ny + j) * (2 * L);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int x = i0 + e;
+      if (x >= P.nx) {
+        el(a, e) = 0.f;
+        el(b, e) = 0.f;
+      } else {
+        const int sc = strip_coord(x, P.nx, L);
+        if (sc >= 0) {
+          el(a, e) = ldmap(sa, row + sc);
+          el(b, e) = ldb(sb, row + sc);
+        }
+      }
+    }
+  } else {
+    const int sc = Q == 1 ? strip_coord(j, P.ny, L) : strip_coord(k, P.nz, L);
+    if (sc < 0) return;
+    const long long off = Q == 1 ? (long long)nu * P.strip_nu[1] + ((long long)k * (2 * L) + sc) * P.pitch + i0
+                                 : (long long)nu * P.strip_nu[2] + ((long long)sc * P.ny + j) * P.pitch + i0;
+    a = ldmap4(sa, off);
+    b = ldb4(sb, off);
+  }
+}
+
+// float density tile [2][9][132] of planes k, k+1 from the staged bf16 box;
+// cells beyond the last one along an axis take that cell's value
+template <bool EDGE>
+__device__ __forceinline__ void density3(const StepParams &P, const bf16 *rb, float *rt, int x0, int y0, int k,
+                                         int tid) {
+  for (int t = tid; t < kRhoTile; t += 256) {
+    const int pz = t / ((kHT + 1) * kRWf), rem = t % ((kHT + 1) * kRWf);
+    const int r = rem / kRWf, cc = rem % kRWf;
+    int sx = cc, sy = r, sz = pz;
+    if (EDGE) {
+      if (x0 + cc >= P.nx) sx = P.nx - 1 - x0;
+      if (y0 + r >= P.ny) sy = P.ny - 1 - y0;
+      if (k + pz >= P.nz) sz = P.nz - 1 - k;
+    }
+    rt[t] = __bfloat162float(rb[(sz * (kHT + 1) + sy) * kRWb + sx]);
+  }
+}
+
+template <int N, bool EDGE>
+__device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, float *rt, int x0, int y0, int k,
+                                             int tid) {
+  using S = Vel3<N>;
+  density3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), rt, x0, y0, k, tid);
+  __syncthreads();
+  const int tx = tid & 31, ly = tid >> 5, lx = 4 * tx;
+  const int i0 = x0 + lx, j = y0 + ly;
+  if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
+  const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
+  const long long Sn = P.npts_alloc;
+  const int o = ly * kTX + lx;
+  // derivatives: x, y from the halo plane, z from the column
+  const float *sp = st + S::oHalo;
+  const int sy = ly + 3;
+  float4 Dx, Dy, Dz;
+  {
+    const float4 *r4 = reinterpret_cast<const float4 *>(sp + sy * kCW) + tx;
+    const float4 a = r4[0], b = r4[1], cc = r4[2];
+    const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w[4 + e + m] - w[4 + e - m + 1], d);
+      el(Dx, e) = d;
+    }
+  }
+  {
+    float4 col[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) col[m] = sld4(sp + (sy - 3 + m) * kCW + lx + 4);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[3 + m], e) - el(col[4 - m], e), d);
+      el(Dy, e) = d;
+    }
+  }
+  {
+    float4 zc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) zc[m] = sld4(st + S::oCol + m * kArr + o);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(zc[3 + m], e) - el(zc[4 - m], e), d);
+      el(Dz, e) = d;
+    }
+  }
+  const float4 k1 = sldh4(reinterpret_cast<const bf16 *>(st + S::oK) + o);
+  float4 A[3][N > 0 ? N : 1], B[3][N > 0 ? N : 1];
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    const float4 a = sldh4(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
+    const float4 b = sldb4(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      A[q][nu] = a;
+      B[q][nu] = b;
+    }
+  }
+  if (EDGE) {
+#pragma unroll
+    for (int nu = 0; nu < N; ++nu) {
+      strip3<0, 1>(P, nu, i0, j, k, A[0][nu], B[0][nu]);
+      strip3<1, 1>(P, nu, i0, j, k, A[1][nu], B[1][nu]);
+      strip3<2, 1>(P, nu, i0, j, k, A[2][nu], B[2][nu]);
+    }
+  }
+  float4 v0 = sld4(st + S::oV + o), v1 = sld4(st + S::oV + kArr + o), v2 = sld4(st + S::oV + 2 * kArr + o);
+  float4 S0, S1, S2;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    el(S0, e) = el(Dx, e) * el(k1, e);
+    el(S1, e) = el(Dy, e) * el(k1, e);
+    el(S2, e) = el(Dz, e) * el(k1, e);
+  }
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    const float4 q0 = sld4(st + S::oPsi + nu * kArr + o);
+    const float4 q1 = sld4(st + S::oPsi + (N + nu) * kArr + o);
+    const float4 q2 = sld4(st + S::oPsi + (2 * N + nu) * kArr + o);
+    float4 n0, n1, n2;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el(n0, e) = fmaf(el(B[0][nu], e), el(q0, e), el(A[0][nu], e) * el(Dx, e));
+      el(n1, e) = fmaf(el(B[1][nu], e), el(q1, e), el(A[1][nu], e) * el(Dy, e));
+      el(n2, e) = fmaf(el(B[2][nu], e), el(q2, e), el(A[2][nu], e) * el(Dz, e));
+      el(S0, e) += fmaf(P.w_new, el(n0, e), P.w_old * el(q0, e));
+      el(S1, e) += fmaf(P.w_new, el(n1, e), P.w_old * el(q1, e));
+      el(S2, e) += fmaf(P.w_new, el(n2, e), P.w_old * el(q2, e));
+    }
+    if (EDGE) {
+      n0 = mask_pad(n0, i0, P.nx);
+      n1 = mask_pad(n1, i0, P.nx);
+      n2 = mask_pad(n2, i0, P.nx);
+    }
+    st_state4(P.psi1[0], nu * Sn + c, n0);
+    st_state4(P.psi1[1], nu * Sn + c, n1);
+    st_state4(P.psi1[2], nu * Sn + c, n2);
+  }
+  const float *r = rt + ly * kRWf + lx;
+  const float4 r0 = sld4(r);
+  const float r4 = r[4];
+  const float4 ru = sld4(r + kRWf);
+  const float4 rz = sld4(r + (kHT + 1) * kRWf);
+  const float rr[5] = {r0.x, r0.y, r0.z, r0.w, r4};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    el(v0, e) -= P.two_dt / (rr[e] + rr[e + 1]) * el(S0, e);
+    el(v1, e) -= P.two_dt / (rr[e] + el(ru, e)) * el(S1, e);
+    el(v2, e) -= P.two_dt / (rr[e] + el(rz, e)) * el(S2, e);
+  }
+  if (EDGE) {
+    v0 = mask_pad(v0, i0, P.nx);
+    v1 = mask_pad(v1, i0, P.nx);
+    v2 = mask_pad(v2, i0, P.nx);
+  }
+  st_state4(P.v[0], c, v0);
+  st_state4(P.v[1], c, v1);
+  st_state4(P.v[2], c, v2);
+}
+
+template <int N, bool EDGE>
+__device__ __forceinline__ void prs3_compute(const StepParams &P, const float *st, int x0, int y0, int k,
+                                             int tid) {
+  using S = Prs3<N>;
+  const int tx = tid & 31, ly = tid >> 5, lx = 4 * tx;
+  const int i0 = x0 + lx, j = y0 + ly;
+  if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
+  const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
+  const long long Sn = P.npts_alloc;
+  const int o = ly * kTX + lx;
+  float4 Dx, Dy, Dz;
+  {
+    const float4 *r4 = reinterpret_cast<const float4 *>(st + S::oVx + ly * kCW) + tx;
+    const float4 a = r4[0], b = r4[1], cc = r4[2];
+    const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w[4 + e + m - 1] - w[4 + e - m], d);
+      el(Dx, e) = d;
+    }
+  }
+  {
+    float4 col[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) col[m] = sld4(st + S::oVy + (ly + m) * kTX + lx);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[4 + m - 1], e) - el(col[4 - m], e), d);
+      el(Dy, e) = d;
+    }
+  }
+  {
+    float4 zc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) zc[m] = sld4(st + S::oCol + m * kArr + o);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(zc[4 + m - 1], e) - el(zc[4 - m], e), d);
+      el(Dz, e) = d;
+    }
+  }
+  const float4 k2 = sldh4(reinterpret_cast<const bf16 *>(st + S::oIk) + o);
+  const float4 K = sldh4(reinterpret_cast<const bf16 *>(st + S::oKm) + o);
+  float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (P.nl) ch = sldh4(reinterpret_cast<const bf16 *>(st + S::oChi) + o);
+  float4 A[3][N > 0 ? N : 1], B[3][N > 0 ? N : 1];
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    const float4 a = sldh4(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
+    const float4 b = sldb4(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      A[q][nu] = a;
+      B[q][nu] = b;
+    }
+  }
+  if (EDGE) {
+#pragma unroll
+    for (int nu = 0; nu < N; ++nu) {
+      strip3<0, 2>(P, nu, i0, j, k, A[0][nu], B[0][nu]);
+      strip3<1, 2>(P, nu, i0, j, k, A[1][nu], B[1][nu]);
+      strip3<2, 2>(P, nu, i0, j, k, A[2][nu], B[2][nu]);
+    }
+  }
+  float4 p = sld4(st + S::oP + o);
+  float4 S0, S1, S2;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    el(S0, e) = el(Dx, e) * el(k2, e);
+    el(S1, e) = el(Dy, e) * el(k2, e);
+    el(S2, e) = el(Dz, e) * el(k2, e);
+  }
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    const float4 q0 = sld4(st + S::oPsi + nu * kArr + o);
+    const float4 q1 = sld4(st + S::oPsi + (N + nu) * kArr + o);
+    const float4 q2 = sld4(st + S::oPsi + (2 * N + nu) * kArr + o);
+    float4 n0, n1, n2;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el(n0, e) = fmaf(el(B[0][nu], e), el(q0, e), el(A[0][nu], e) * el(Dx, e));
+      el(n1, e) = fmaf(el(B[1][nu], e), el(q1, e), el(A[1][nu], e) * el(Dy, e));
+      el(n2, e) = fmaf(el(B[2][nu], e), el(q2, e), el(A[2][nu], e) * el(Dz, e));
+      el(S0, e) += fmaf(P.w_new, el(n0, e), P.w_old * el(q0, e));
+      el(S1, e) += fmaf(P.w_new, el(n1, e), P.w_old * el(q1, e));
+      el(S2, e) += fmaf(P.w_new, el(n2, e), P.w_old * el(q2, e));
+    }
+    if (EDGE) {
+      n0 = mask_pad(n0, i0, P.nx);
+      n1 = mask_pad(n1, i0, P.nx);
+      n2 = mask_pad(n2, i0, P.nx);
+    }
+    st_state4(P.psi2[0], nu * Sn + c, n0);
+    st_state4(P.psi2[1], nu * Sn + c, n1);
+    st_state4(P.psi2[2], nu * Sn + c, n2);
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float upd = P.dt * el(K, e) * (el(S0, e) + el(S1, e) + el(S2, e));
+    if (P.nl) upd /= fmaf(el(ch, e), el(p, e), 1.f);
+    el(p, e) -= upd;
+  }
+  if (EDGE) p = mask_pad(p, i0, P.nx);
+  st_state4(P.p, c, p);
+}
+
+template <int N, bool VEL>
+__global__ void __launch_bounds__(256, 1)
+    pipe3d_kernel(const StepParams P, const Region3 R, const __grid_constant__ PipeMaps T) {
+  using G = Ring3<N, VEL>;
+  constexpr int kStage = G::kStage;
+  extern __shared__ __align__(128) float smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int ok;
+  float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float *rt = smem + 2 * kStage;  // float density tile (velocity)
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbarrier_init();
+  }
+  __syncthreads();
+  const long long nu_ = R.units();
+  long long u = blockIdx.x;
+  if (u >= nu_) return;
+  unsigned phase = 0, pending = 0;
+  long long us = u;  // next unit to issue
+  if (tid == 0) {
+    int x, y, z;
+    R.origin(us, x, y, z);
+    issue3<N, VEL>(T, smem, &bar[0], x, y, z, P.nl != 0);
+  }
+  pending |= 1u;
+  us += gridDim.x;
+  int s = 0;
+#pragma unroll 1
+  for (; u < nu_; u += gridDim.x) {
+    if (us < nu_) {
+      const int q = s ^ 1;
+      if (tid == 0) {
+        int x, y, z;
+        R.origin(us, x, y, z);
+        issue3<N, VEL>(T, smem + q * kStage, &bar[q], x, y, z, P.nl != 0);
+      }
+      pending |= 1u << q;
+      us += gridDim.x;
+    }
+    if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    __syncthreads();
+    if (!ok) {
+      if (tid == 0) {
+        report_status(P.status, kStatusWaitTimeout);
+        if ((pending >> (s ^ 1)) & 1u) mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u);
+      }
+      return;
+    }
+    phase ^= 1u << s;
+    pending &= ~(1u << s);
+    int x0, y0, k;
+    R.origin(u, x0, y0, k);
+    float *cur = smem + s * kStage;
+    if (R.interior(x0, y0, k)) {
+      if (VEL) vel3_compute<N, false>(P, cur, rt, x0, y0, k, tid);
+      else prs3_compute<N, false>(P, cur, x0, y0, k, tid);
+    } else {
+      if (VEL) vel3_compute<N, true>(P, cur, rt, x0, y0, k, tid);
+      else prs3_compute<N, true>(P, cur, x0, y0, k, tid);
+    }
+    __syncthreads();
+    s ^= 1;
+  }
+}
+
+template <int N, bool VEL>
+cudaError_t pipe3_launch(const StepParams &P, const Region3 &R, int grid, const PipeMaps &T, cudaStream_t st) {
+  constexpr size_t bytes = Ring3<N, VEL>::kBytes;
+  static_assert(bytes <= 227 * 1024, "stages exceed shared memory");
+  cudaError_t e =
+      cudaFuncSetAttribute(pipe3d_kernel<N, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  pipe3d_kernel<N, VEL><<<grid, dim3(32, kBY), bytes, st>>>(P, R, T);
+  return cudaGetLastError();
+}
+
+template <bool VEL>
+cudaError_t pipe3_dispatch(const StepParams &P, const Region3 &R, int grid, const PipeMaps &T, cudaStream_t st) {
+  switch (P.n_relax) {
+    case 0: return pipe3_launch<0, VEL>(P, R, grid, T, st);
+    case 1: return pipe3_launch<1, VEL>(P, R, grid, T, st);
+    case 2: return pipe3_launch<2, VEL>(P, R, grid, T, st);
+    case 3: return pipe3_launch<3, VEL>(P, R, grid, T, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+Region3 region3_of(const StepParams &P) {
+  Region3 R;
+  R.nx = P.nx;
+  R.ny = P.ny;
+  R.nz = P.nz;
+  R.Lx = P.L[0] > 4 ? P.L[0] : 4;
+  R.Ly = P.L[1] > 4 ? P.L[1] : 4;
+  R.Lz = P.L[2] > 4 ? P.L[2] : 4;
+  R.tnx = (P.nx + kTX - 1) / kTX;
+  R.nhy = (P.ny + kHT - 1) / kHT;
+  return R;
+}
+
+}  // namespace
+
+bool pipe3d_supported(const StepParams &P, int map_kind) {
+  // bf16 maps (two stages of ~107 KB fit); N <= 3 keeps the 4D boxes and
+  // the stage within shared memory; no periodic axis
+  return P.nz > 1 && map_kind == 1 && P.n_relax >= 0 && P.n_relax <= 3 && !P.periodic[0] && !P.periodic[1] &&
+         !P.periodic[2];
+}
+
+cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why) {
+  *vel = PipeMaps{};
+  *prs = PipeMaps{};
+  const int N = P.n_relax;
+  using ull = unsigned long long;
+  const ull nx = P.nx, ny = P.ny, nz = P.nz, S = P.npts_alloc;
+  const ull f3[2] = {(ull)P.pitch * 4, (ull)P.plane * 4}, h3[2] = {(ull)P.pitch * 2, (ull)P.plane * 2};
+  const ull f4[3] = {(ull)P.pitch * 4, (ull)P.plane * 4, S * 4}, h4[3] = {(ull)P.pitch * 2, (ull)P.plane * 2, S * 2};
+  const ull d3[3] = {nx, ny, nz};
+  const ull dv[4] = {nx, ny, nz, 3}, dpsi[4] = {nx, ny, nz, (ull)(3 * N)}, dab[4] = {nx, ny, nz, (ull)N};
+  const unsigned halo[3] = {kCW, kHT + 7, 1}, col[3] = {kTX, kHT, 8}, rho[3] = {kRWb, kHT + 1, 2},
+                 one[3] = {kTX, kHT, 1}, v4[4] = {kTX, kHT, 1, 3}, psi4[4] = {kTX, kHT, 1, (unsigned)(3 * N)},
+                 ab4[4] = {kTX, kHT, 1, (unsigned)N}, vx[3] = {kCW, kHT, 1}, vy[3] = {kTX, kHT + 7, 1};
+  bool ok = true;
+  // velocity half step
+  ok = ok && encode_tensor_map(&vel->m[0], P.p, 4, 3, d3, f3, halo);
+  ok = ok && encode_tensor_map(&vel->m[1], P.p, 4, 3, d3, f3, col);
+  ok = ok && encode_tensor_map(&vel->m[2], P.rho, 2, 3, d3, h3, rho);
+  ok = ok && encode_tensor_map(&vel->m[3], P.v[0], 4, 4, dv, f4, v4);
+  if (N > 0) ok = ok && encode_tensor_map(&vel->m[4], P.psi1[0], 4, 4, dpsi, f4, psi4);
+  ok = ok && encode_tensor_map(&vel->m[5], P.ik1, 2, 3, d3, h3, one);
+  if (N > 0) {
+    ok = ok && encode_tensor_map(&vel->m[6], P.a1, 2, 4, dab, h4, ab4);
+    ok = ok && encode_tensor_map(&vel->m[7], P.b1, 2, 4, dab, h4, ab4);
+  }
+  // pressure half step
+  ok = ok && encode_tensor_map(&prs->m[0], P.v[0], 4, 3, d3, f3, vx);
+  ok = ok && encode_tensor_map(&prs->m[1], P.v[1], 4, 3, d3, f3, vy);
+  ok = ok && encode_tensor_map(&prs->m[2], P.v[2], 4, 3, d3, f3, col);
+  ok = ok && encode_tensor_map(&prs->m[3], P.p, 4, 3, d3, f3, one);
+  if (N > 0) ok = ok && encode_tensor_map(&prs->m[4], P.psi2[0], 4, 4, dpsi, f4, psi4);
+  ok = ok && encode_tensor_map(&prs->m[5], P.ik2, 2, 3, d3, h3, one);
+  ok = ok && encode_tensor_map(&prs->m[6], P.K, 2, 3, d3, h3, one);
+  if (P.nl) ok = ok && encode_tensor_map(&prs->m[7], P.chi, 2, 3, d3, h3, one);
+  if (N > 0) {
+    ok = ok && encode_tensor_map(&prs->m[8], P.a2, 2, 4, dab, h4, ab4);
+    ok = ok && encode_tensor_map(&prs->m[9], P.b2, 2, 4, dab, h4, ab4);
+  }
+  if (!ok) {
+    *why = "cuTensorMapEncodeTiled rejected a 3D map (or the driver entry point is missing)";
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t st) {
+  const Region3 R = region3_of(P);
+  return vel ? pipe3_dispatch<true>(P, R, grid, T, st) : pipe3_dispatch<false>(P, R, grid, T, st);
+}
+
+}  // namespace fw2

@@ -18,4 +18,19 @@ struct PipeMaps {
   CUtensorMap m[kPipeMaps];
 };
 
+// 3D pipelined half steps (bf16 maps):
+// velocity: 0 p halo plane (136 x 15 x 1), 1 p column (128 x 8 x 8), 2 rho
+//   bf16 (136 x 9 x 2), 3 v (128 x 8 x 1 x 3), 4 psi1 (128 x 8 x 1 x 3N),
+//   5 1/kappa1 bf16, 6 a1 bf16 (128 x 8 x 1 x N), 7 b1 bf16
+// pressure: 0 v_x (136 x 8 x 1), 1 v_y (128 x 15 x 1), 2 v_z column
+//   (128 x 8 x 8), 3 p, 4 psi2 (128 x 8 x 1 x 3N), 5 1/kappa2, 6 K, 7 chi,
+//   8 a2, 9 b2 (bf16)
+
+// Encode a tiled tensor map (host): element size 1, 2 or 4 bytes (uint8,
+// bf16, float), rank 2..4, dims[0] innermost, strides in bytes of dims 1..;
+// cells outside the tensor read as zero.  False when the driver entry point
+// is missing or rejects the map.
+bool encode_tensor_map(CUtensorMap *m, const void *base, int elem_bytes, int rank, const unsigned long long *dims,
+                       const unsigned long long *strides_bytes, const unsigned *box);
+
 }  // namespace fw2

@@ -216,7 +216,8 @@ def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3):
     rng = np.random.default_rng(seed)
     f0 = 1e6
     h = 1540.0 / f0 / 10
-    relax = synth.relaxation_sets()["N3_y1.2_brain"]
+    key = {2: "N2_y1.0_a0.5", 3: "N3_y1.2_brain"}.get(N)
+    relax = synth.relaxation_sets()[key] if N else None
     prob = synth.homogeneous(n, h, 0.0, relax=relax)
     g = prob.grid_shape
     prob.c = (1560.0 * (1 + 0.1 * rng.random(g))).astype(np.float32)
@@ -224,7 +225,7 @@ def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3):
     prob.dt = 0.4 * h / float(prob.c.max())
     prob.beta = rng.uniform(3, 6, g).astype(np.float32)
     prob.nl_mode = nl
-    prob.pml_transition, prob.pml_bound = 6, 2
+    prob.pml_transition, prob.pml_bound = (6, 2) if N else (0, 0)
     sig = synth.gaussian_pulse(steps, prob.dt, f0, 2.0, 1e6)
     X, Y = np.meshgrid(np.arange(20, 50), np.arange(12, 28), indexing="xy")
     idx = synth.flat_index(n, X.ravel(), Y.ravel(), 10)
@@ -249,6 +250,20 @@ def test_parity_3d_random_state(fw2):
     prob = small_3d(n=(36, 44, 40), steps=30)
     st = synth.random_state(prob, seed=5)
     compare_run(fw2, prob, 30, state=st)
+
+
+@pytest.mark.parametrize("N,nl", [(0, "off"), (2, "pressure"), (3, "westervelt"), (3, "off")])
+def test_pipelined_3d_equals_tile_path_bitwise(fw2, N, nl):
+    """The persistent TMA-staged 3D half steps (bf16 maps) compute exactly what
+    the tile kernels compute: interior and edge units, ragged x and y, C-PML
+    strips on every axis."""
+    prob = small_3d(n=(300, 70, 45), N=N, nl=nl, steps=40)
+    _pipe_vs_tile(fw2, prob, 40, maps="bf16")
+
+
+def test_parity_3d_pipelined_path(fw2):
+    prob = small_3d(n=(300, 70, 45), steps=60)
+    compare_run(fw2, prob, 60, maps="bf16", kernel_path="pipe")
 
 
 def test_parity_plain_2d_config_full(fw2):
