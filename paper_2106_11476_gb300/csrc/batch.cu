@@ -88,6 +88,12 @@ struct Group {
   StepParams *d_params = nullptr;
   int4 *d_tiles[2] = {nullptr, nullptr};  // context-major, interleaved
   int n_tiles = 0;
+  // pipelined form (float or index maps, no periodic axis): units of
+  // 128 x 8 cells {ctx, x0, y0, interior}, tensor maps per context
+  bool pipe = false;
+  int4 *d_units = nullptr;
+  int n_units = 0;
+  PipeMaps *d_maps[2] = {nullptr, nullptr};  // velocity, pressure
 };
 
 }  // namespace
@@ -104,6 +110,7 @@ struct fw2_batch {
   std::string err = "no error";
   // launch configuration: persistent grid and tile order, tuned online
   int grid = 0, order = 0;
+  int n_sm = 152;
   bool tuned = false;
   int trial = 0;
   std::vector<float> trial_ms;
@@ -151,7 +158,12 @@ fw2_status enqueue_step(fw2_batch *b, int grid, int order) {
   for (int half = 0; half < 2; ++half) {
     const bool vel = half == 0;
     for (Group &g : b->groups) {
-      BCK(b, launch_batched2d(vel, g.d_params, g.d_tiles[order], g.n_tiles, g.n_relax, g.map_kind, grid, b->stream));
+      if (g.pipe)
+        BCK(b, launch_pipe2d_batched(vel, g.d_params, g.d_maps[vel ? 0 : 1], g.d_units, g.n_units, g.n_relax,
+                                     g.map_kind, b->n_sm, b->stream));
+      else
+        BCK(b, launch_batched2d(vel, g.d_params, g.d_tiles[order], g.n_tiles, g.n_relax, g.map_kind, grid,
+                                b->stream));
       b->launches++;
     }
     const int kinds[2][2] = {{1, 2}, {0, -1}};
@@ -200,6 +212,7 @@ fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out
     }
     b->ctxs.push_back(c);
   }
+  b->n_sm = b->ctxs[0]->n_sm;
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     delete b;
@@ -240,6 +253,28 @@ fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out
     if ((st = bupload(b, params, &g.d_params)) != FW2_OK) break;
     if ((st = bupload(b, major, &g.d_tiles[0])) != FW2_OK) break;
     if ((st = bupload(b, inter, &g.d_tiles[1])) != FW2_OK) break;
+    // the pipelined form when every member allows it
+    g.pipe = true;
+    for (const StepParams &P : params)
+      if (!pipe2d_supported(P, g.map_kind) || P.periodic[0] || P.periodic[1]) g.pipe = false;
+    if (g.pipe) {
+      std::vector<PipeMaps> mv(params.size()), mp(params.size());
+      std::vector<int4> units;
+      for (int m = 0; m < (int)params.size() && g.pipe; ++m) {
+        const StepParams &P = params[m];
+        const char *why = "";
+        if (build_pipe2d_maps(P, g.map_kind, &mv[m], &mp[m], &why) != cudaSuccess) g.pipe = false;
+        for (int y0 = 0; y0 < P.ny; y0 += kPipeHalf)
+          for (int x0 = 0; x0 < P.nx; x0 += kTX)
+            units.push_back(make_int4(m, x0, y0, pipe2d_interior_half(P, x0, y0) ? 1 : 0));
+      }
+      if (g.pipe) {
+        g.n_units = (int)units.size();
+        if ((st = bupload(b, units, &g.d_units)) != FW2_OK) break;
+        if ((st = bupload(b, mv, &g.d_maps[0])) != FW2_OK) break;
+        if ((st = bupload(b, mp, &g.d_maps[1])) != FW2_OK) break;
+      }
+    }
   }
   if (st == FW2_OK) {
     std::vector<BatchCtx> bc;

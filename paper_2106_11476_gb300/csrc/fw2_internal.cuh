@@ -126,6 +126,12 @@ bool pipe2d_preferred(const StepParams &P, int map_kind);
 cudaError_t build_pipe2d_maps(const StepParams &P, int map_kind, PipeMaps *vel, PipeMaps *prs, const char **why);
 cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, const PipeMaps &T,
                           cudaStream_t s);
+// batched form over a unit table {ctx, x0, y0, interior} of 128 x 8 half
+// tiles (no periodic context); Ps and Ts in device memory, one per context
+constexpr int kPipeHalf = 8;  // rows of a pipelined half tile
+bool pipe2d_interior_half(const StepParams &P, int x0, int y0);
+cudaError_t launch_pipe2d_batched(bool vel, const StepParams *Ps, const PipeMaps *Ts, const int4 *units,
+                                  int n_units, int n_relax, int map_kind, int grid, cudaStream_t s);
 // persistent pipelined 3D half step (bf16 maps, N <= 3, no periodic axis)
 bool pipe3d_supported(const StepParams &P, int map_kind);
 cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why);

@@ -550,6 +550,117 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
+// Batched half step over a unit table of several contexts (one group: same
+// N and map kind, no periodic axis): entry (ctx, x0, y0, interior).  The
+// contexts' step parameters and tensor maps sit in device memory (TMA reads
+// the maps from there); a block copies a context's parameters to shared
+// memory, and stages its tissue-index table, when the context changes.
+template <int N, typename Maps, bool VEL>
+__global__ void __launch_bounds__(256, 1)
+    pipe2d_batched_kernel(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, int n_units) {
+  using G = Ring<N, Maps, VEL>;
+  constexpr int kS = G::kStages, kStage = G::kStage;
+  extern __shared__ __align__(128) float smem_raw[];
+  __shared__ __align__(8) uint64_t bar[kS];
+  __shared__ __align__(16) StepParams sP;
+  __shared__ int ok;
+  float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float *tab = smem + kS * kStage;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid == 0) {
+    for (int q = 0; q < kS; ++q) mbar_init(&bar[q], 1);
+    fence_mbarrier_init();
+  }
+  __syncthreads();
+  // a contiguous run of units per block: consecutive units share a context
+  // (one parameter and table load per context) and halo rows (L2)
+  const int h_end = (int)(((long long)n_units * (blockIdx.x + 1)) / gridDim.x);
+  int h = (int)(((long long)n_units * blockIdx.x) / gridDim.x);
+  if (h >= h_end) return;
+  unsigned phase = 0, pending = 0;
+  int hs = h;
+  for (int q = 0; q < kS - 1; ++q, ++hs) {
+    if (hs >= h_end) break;
+    if (tid == 0) {
+      const int4 e = units[hs];
+      issue_stage<N, Maps, VEL>(Ps[e.x], Ts[e.x], smem + q * kStage, &bar[q], e.y, e.z);
+    }
+    pending |= 1u << q;
+  }
+  int s = 0, cur = -1;
+#pragma unroll 1
+  for (; h < h_end; ++h) {
+    if (hs < h_end) {
+      const int q = (s + kS - 1) % kS;
+      if (tid == 0) {
+        const int4 e = units[hs];
+        issue_stage<N, Maps, VEL>(Ps[e.x], Ts[e.x], smem + q * kStage, &bar[q], e.y, e.z);
+      }
+      pending |= 1u << q;
+      ++hs;
+    }
+    const int4 e = units[h];
+    if (e.x != cur) {
+      // new context: parameters (and index table) into shared memory; the
+      // previous unit's compute finished at the last barrier
+      const int *src = reinterpret_cast<const int *>(Ps + e.x);
+      int *dst = reinterpret_cast<int *>(&sP);
+      for (int w = tid; w < (int)(sizeof(StepParams) / 4); w += 256) dst[w] = __ldg(src + w);
+      __syncthreads();
+      Maps(sP).stage(sP, tab, tid);
+      cur = e.x;
+    }
+    if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    __syncthreads();
+    if (!ok) {
+      if (tid == 0) {
+        report_status(sP.status, kStatusWaitTimeout);
+        for (int q = 0; q < kS; ++q)
+          if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
+      }
+      return;
+    }
+    phase ^= 1u << s;
+    pending &= ~(1u << s);
+    Maps M(sP);
+    M.bind(tab);
+    float *stp = smem + s * kStage;
+    if (e.w) {
+      if (VEL) vel_compute<N, Maps, false>(sP, M, stp, e.y, e.z, tid);
+      else prs_compute<N, Maps, false>(sP, M, stp, e.y, e.z, tid);
+    } else {
+      if (VEL) vel_compute<N, Maps, true>(sP, M, stp, e.y, e.z, tid);
+      else prs_compute<N, Maps, true>(sP, M, stp, e.y, e.z, tid);
+    }
+    __syncthreads();
+    s = (s + 1) % kS;
+  }
+}
+
+template <int N, typename Maps, bool VEL>
+cudaError_t pipe_batched_launch(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, int n_units, int grid,
+                                cudaStream_t st) {
+  constexpr size_t bytes = Ring<N, Maps, VEL>::kBytes;
+  cudaError_t e = cudaFuncSetAttribute(pipe2d_batched_kernel<N, Maps, VEL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  pipe2d_batched_kernel<N, Maps, VEL><<<grid, dim3(32, kBY), bytes, st>>>(Ps, Ts, units, n_units);
+  return cudaGetLastError();
+}
+
+template <typename Maps, bool VEL>
+cudaError_t pipe_batched_dispatch(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, int n_units,
+                                  int n_relax, int grid, cudaStream_t st) {
+  switch (n_relax) {
+    case 0: return pipe_batched_launch<0, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
+    case 1: return pipe_batched_launch<1, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
+    case 2: return pipe_batched_launch<2, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
+    case 3: return pipe_batched_launch<3, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
+    case 4: return pipe_batched_launch<4, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int N, typename Maps, bool VEL>
 cudaError_t pipe_launch(const StepParams &P, const Region &R, int grid, const PipeMaps &T, cudaStream_t st) {
   constexpr size_t bytes = Ring<N, Maps, VEL>::kBytes;
@@ -614,6 +725,23 @@ bool pipe2d_supported(const StepParams &P, int map_kind) {
 }
 
 bool pipe2d_preferred(const StepParams &P, int map_kind) { return pipe2d_supported(P, map_kind); }
+
+bool pipe2d_interior_half(const StepParams &P, int x0, int y0) {
+  const int Lx = P.L[0] > 4 ? P.L[0] : 4, Ly = P.L[1] > 4 ? P.L[1] : 4;
+  return x0 >= Lx && x0 + kTX + Lx <= P.nx && y0 >= Ly && y0 + kHT + Ly <= P.ny;
+}
+
+cudaError_t launch_pipe2d_batched(bool vel, const StepParams *Ps, const PipeMaps *Ts, const int4 *units,
+                                  int n_units, int n_relax, int map_kind, int grid, cudaStream_t st) {
+  if (n_units <= 0) return cudaSuccess;
+  if (map_kind == 2)
+    return vel ? pipe_batched_dispatch<IdxMaps, true>(Ps, Ts, units, n_units, n_relax, grid, st)
+               : pipe_batched_dispatch<IdxMaps, false>(Ps, Ts, units, n_units, n_relax, grid, st);
+  if (map_kind == 0)
+    return vel ? pipe_batched_dispatch<DenseMaps<float>, true>(Ps, Ts, units, n_units, n_relax, grid, st)
+               : pipe_batched_dispatch<DenseMaps<float>, false>(Ps, Ts, units, n_units, n_relax, grid, st);
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, const PipeMaps &T,
                           cudaStream_t st) {
