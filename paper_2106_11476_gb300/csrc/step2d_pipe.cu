@@ -1,6 +1,6 @@
-// Pipelined persistent 2D half steps (sm_103a); same arithmetic as the tile
-// functions of tile2d.cuh (bitwise the same results), one launch per half
-// step, one block per SM.
+// Pipelined persistent 2D half steps (sm_103a); the arithmetic of the tile
+// kernels (tile2d.cuh) cell for cell, so the results are bitwise the same;
+// one launch per half step, one block of 512 threads per SM.
 //
 // The grid is walked in half tiles of 128 x 8 cells through a ring of two to
 // four shared-memory stages (as many as fit).  For a coming half tile one
@@ -8,19 +8,20 @@
 // the stencil operand with its halo, the density tile (or the uint8 tissue
 // index), every streamed array, the N mechanisms of a memory variable or of a
 // relaxation map in one 3D box.  They complete on the stage's mbarrier while
-// all warps compute the current half tile from another stage, so up to
-// ~190 KB stay in flight per SM without registers or load instructions of the
-// computing threads; results go straight from registers to HBM.
+// all threads compute the current half tile from another stage, two cells
+// each, so up to ~190 KB stay in flight per SM without registers or load
+// instructions of the computing threads; results go straight from registers
+// to HBM.
 //
 // Boundaries: the copies read zero outside the grid (the zero-outside rule of
 // the operand halo); half tiles at the edge of the grid or in a C-PML strip
 // (edge half tiles) also clamp the density tile to the last cell, take the
 // C-PML coefficients of each axis from its strip, and store nothing outside
-// the grid (zeros in the row padding).  With a periodic axis the tiles next
-// to the boundary run the general tile path first and only the rest is staged.
+// the grid (zeros in the row padding).  Periodic grids take the tile kernels.
 // Dense float maps and the tissue-index form take this path.
 #include "async.cuh"
-#include "tile2d.cuh"
+#include "coef.cuh"
+#include "maps.cuh"
 #include "tmap.h"
 
 namespace fw2 {
@@ -47,48 +48,19 @@ struct IsIdx<IdxMaps> {
 // shared-memory regions start on 128-byte boundaries (TMA destinations)
 constexpr int round32(int n) { return (n + 31) & ~31; }
 
-// Work of one launch.  Staged: the half tiles [tx_lo, tx_lo+ntx) x
-// [hy_lo, hy_lo+nhy) (x in tiles of 128, y in half tiles of 8 rows), x
-// fastest: the whole grid, or with `split` (a periodic axis) the interior
-// tiles [tx_lo, tx_lo+ntx) x [ty_lo, ty_lo+nty) of 128 x 16 (the tiles
-// interior_tile accepts), the frame of tiles around them going through the
-// general tile path.
+// Work of one launch: the half tiles of the grid (tiles of 128 x 8 cells,
+// x fastest).
 struct Region {
-  int nx, ny, Lx, Ly;             // grid, boundary width (at least the halo, 4)
-  int tnx, tny;                   // tiles of 128 x 16
-  int split;
-  int tx_lo, ntx, ty_lo, nty;     // interior tiles (split)
-  int hy_lo, nhy;                 // staged half-tile rows
+  int nx, ny, Lx, Ly;  // grid, boundary width (at least the halo, 4)
+  int ntx, nhy;        // tiles along x, half-tile rows
   __device__ __forceinline__ int halves() const { return ntx * nhy; }
   __device__ __forceinline__ void half_origin(int h, int &x0, int &y0) const {
-    x0 = (tx_lo + h % ntx) * kTX;
-    y0 = (hy_lo + h / ntx) * kHT;
+    x0 = (h % ntx) * kTX;
+    y0 = (h / ntx) * kHT;
   }
-  // a staged half tile clear of the boundary rules and of the C-PML strips
+  // a half tile clear of the boundary rules and of the C-PML strips
   __device__ __forceinline__ bool interior(int x0, int y0) const {
     return x0 >= Lx && x0 + kTX + Lx <= nx && y0 >= Ly && y0 + kHT + Ly <= ny;
-  }
-  __device__ __forceinline__ int edges() const { return split ? tnx * tny - ntx * nty : 0; }
-  // e-th general-path tile (split): the rows below the staged tiles, the
-  // side tiles of their rows, then the rows above
-  __device__ __forceinline__ void edge_origin(int e, int &x0, int &y0) const {
-    int tx, ty;
-    const int low = ty_lo * tnx, side = tnx - ntx;
-    if (e < low) {
-      ty = e / tnx;
-      tx = e % tnx;
-    } else if (e - low < nty * side) {
-      const int k = e - low;
-      ty = ty_lo + k / side;
-      const int s = k % side;
-      tx = s < tx_lo ? s : s + ntx;
-    } else {
-      const int k = e - low - nty * side;
-      ty = ty_lo + nty + k / tnx;
-      tx = k % tnx;
-    }
-    x0 = tx * kTX;
-    y0 = ty * kTY;
   }
 };
 
@@ -108,7 +80,6 @@ struct VelStage {
   static constexpr int kS = kNs * kArr;
   static constexpr int kI = kIdx ? (kHT + 1) * kIW / 4 : 0;  // index bytes / 4
   static constexpr int kFloats = round32(kP + kR + kS + kI);
-  static constexpr int kEdge = kPH * kPW + kRH * kRW;         // general tile
 };
 
 // pressure: v_x rows y0-1 .. y0+kHT, v_y rows y0-4 .. y0+kHT+2; streamed
@@ -126,7 +97,6 @@ struct PrsStage {
   static constexpr int kS = kNs * kArr;
   static constexpr int kI = kIdx ? kHT * kTX / 4 : 0;
   static constexpr int kFloats = round32(kX + kY + kS + kI);
-  static constexpr int kEdge = kHX * kPW + kHY * kPW;
 };
 
 // Bytes one stage receives through the tensor maps (the chi box only with
@@ -195,15 +165,131 @@ __device__ __forceinline__ void issue_stage(const StepParams &P, const PipeMaps 
   }
 }
 
+// ------------------------------------------------------------ compute ---
+// 512 threads per block, two consecutive x cells each: thread t of row ly
+// (64 threads per row) owns cells x0 + 2t, x0 + 2t + 1.  Every cell sees the
+// operations of the tile path in the same order, so results are bitwise the
+// same.
+constexpr int kThreads = 512;
+
+__device__ __forceinline__ float2 sld2(const float *s) { return *reinterpret_cast<const float2 *>(s); }
+__device__ __forceinline__ void st_state2(float *p, long long i, float2 v) {
+  __stcs(reinterpret_cast<float2 *>(p + i), v);
+}
+__device__ __forceinline__ float &el2(float2 &v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ float el2(const float2 &v, int e) { return e == 0 ? v.x : v.y; }
+// zero the cells of a pair that fall in the row padding (x >= nx)
+__device__ __forceinline__ float2 mask_pad2(float2 v, int i0, int nx) {
+  if (i0 + 1 >= nx) v.y = 0.f;
+  if (i0 >= nx) v.x = 0.f;
+  return v;
+}
+
+// ten consecutive shared-memory values from column c of a row (c even)
+struct Win10 {
+  float v[10];
+};
+__device__ __forceinline__ Win10 win10(const float *row, int c) {
+  Win10 w;
+  const float2 *r2 = reinterpret_cast<const float2 *>(row + c);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float2 t = r2[i];
+    w.v[2 * i] = t.x;
+    w.v[2 * i + 1] = t.y;
+  }
+  return w;
+}
+
+// x and y derivatives of the staged p at the faces of cells x0+lx, x0+lx+1
+// (operand rows y0-3.., columns x0-4..; cell e sits at column lx + 4 + e)
+__device__ __forceinline__ void vel_derivs2(const StepParams &P, const float *sp, int sy, int lx, float2 &Dx,
+                                            float2 &Dy) {
+  const Win10 w = win10(sp + sy * kCW, lx);  // columns lx .. lx+9
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    float d = 0.f;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m] - w.v[4 + e - m + 1], d);
+    el2(Dx, e) = d;
+  }
+  float2 col[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) col[m] = sld2(sp + (sy - 3 + m) * kCW + lx + 4);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    float d = 0.f;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(col[3 + m], e) - el2(col[4 - m], e), d);
+    el2(Dy, e) = d;
+  }
+  if (P.g11h != 0.f) {
+    const Win10 up = win10(sp + (sy + 1) * kCW, lx), dn = win10(sp + (sy - 1) * kCW, lx);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      el2(Dx, e) += P.g11h * ((up.v[5 + e] - up.v[4 + e]) + (dn.v[5 + e] - dn.v[4 + e]));
+      el2(Dy, e) += P.g11h * ((up.v[5 + e] - w.v[5 + e]) + (up.v[3 + e] - w.v[3 + e]));
+    }
+  }
+}
+
+// x and y derivatives of v_x (rows y0-1..), v_y (rows y0-4..) at the centres
+__device__ __forceinline__ void prs_derivs2(const StepParams &P, const float *svx, const float *svy, int ly,
+                                            int lx, float2 &Dx, float2 &Dy) {
+  const Win10 w = win10(svx + (ly + 1) * kCW, lx);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    float d = 0.f;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m - 1] - w.v[4 + e - m], d);
+    el2(Dx, e) = d;
+  }
+  float2 col[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) col[m] = sld2(svy + (ly + m) * kCW + lx + 4);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    float d = 0.f;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(col[4 + m - 1], e) - el2(col[4 - m], e), d);
+    el2(Dy, e) = d;
+  }
+  if (P.g11h != 0.f) {
+    const Win10 up = win10(svx + (ly + 2) * kCW, lx), dn = win10(svx + ly * kCW, lx);
+    const Win10 y0w = win10(svy + (ly + 4) * kCW, lx), y1w = win10(svy + (ly + 3) * kCW, lx);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      el2(Dx, e) += P.g11h * ((up.v[4 + e] - up.v[3 + e]) + (dn.v[4 + e] - dn.v[3 + e]));
+      el2(Dy, e) += P.g11h * ((y0w.v[5 + e] - y1w.v[5 + e]) + (y0w.v[3 + e] - y1w.v[3 + e]));
+    }
+  }
+}
+
+// per-tissue table of the index form into shared memory (all threads)
+template <typename Maps>
+__device__ __forceinline__ void stage_table(const StepParams &P, float *tab, int tid) {
+  if constexpr (IsIdx<Maps>::value) {
+    const float4 *src = reinterpret_cast<const float4 *>(P.table);
+    float4 *dst = reinterpret_cast<float4 *>(tab);
+    for (int t = tid; t < kTableFields * kTissues / 4; t += kThreads) dst[t] = __ldg(src + t);
+  }
+}
+
+// coefficient of field f at the two cells of a pair (index form)
+__device__ __forceinline__ float2 look2(const float *tab, int f, uchar2 t) {
+  const float *r = tab + f * kTissues;
+  return make_float2(r[t.x], r[t.y]);
+}
+
 // Density tile rows y0 .. y0+kHT, columns x0 .. x0+kTX+3.  Cells beyond the
 // last one along an axis take that cell's value (rho_coord of the tile path):
 // dense maps fix the staged tile in place (the entries inside the grid are
 // the sources); the index form gathers the tile through the table from the
 // staged index (zero outside the grid, hence the clamp).
 template <typename Maps, bool EDGE>
-__device__ __forceinline__ void density_tile(const StepParams &P, const Maps &M, float *sr,
+__device__ __forceinline__ void density_tile(const StepParams &P, const float *tab, float *sr,
                                              const unsigned char *si, int x0, int y0, int tid) {
-  for (int t = tid; t < (kHT + 1) * kRWp; t += 256) {
+  for (int t = tid; t < (kHT + 1) * kRWp; t += kThreads) {
     const int r = t / kRWp, cc = t % kRWp;
     int sxi = cc, syi = r;
     if (EDGE) {
@@ -211,65 +297,53 @@ __device__ __forceinline__ void density_tile(const StepParams &P, const Maps &M,
       if (y0 + r >= P.ny) syi = P.ny - 1 - y0;
     }
     if constexpr (IsIdx<Maps>::value) {
-      sr[t] = M.tab[kTabRho * kTissues + si[syi * kIW + sxi]];
+      sr[t] = tab[kTabRho * kTissues + si[syi * kIW + sxi]];
     } else {
       if (sxi != cc || syi != r) sr[t] = sr[syi * kRWp + sxi];
     }
   }
 }
 
-// a, b of mechanism nu along x at the four cells of an edge group: from the
-// x strip inside its C-PML region (zero beyond the grid), else the interior
-// values A, B (coef_edge of the tile path)
+// a, b of mechanism nu along x at the two cells of an edge pair: from the x
+// strip inside its C-PML region, else unchanged (coef_edge of the tile path;
+// its zero beyond the grid only reaches cells that are masked)
 template <int OP, typename Maps>
-__device__ __forceinline__ void x_strip_coef(const StepParams &P, int nu, int i0, int j, float4 &a, float4 &b) {
+__device__ __forceinline__ void x_strip_coef2(const StepParams &P, int nu, int i0, int j, float2 &a, float2 &b) {
   using ST = typename Maps::StripT;
   const int L = P.L[0];
-  if (!(L > 0 && (i0 < L || i0 + 3 >= P.nx - L))) return;
+  if (!(L > 0 && (i0 < L || i0 + 1 >= P.nx - L))) return;
   const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[0] : P.sa2[0]);
   const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[0] : P.sb2[0]);
   const long long row = (long long)nu * P.strip_nu[0] + (long long)j * (2 * L);
-  // a group wholly inside one side of the strip reads 16 aligned bytes when
-  // the strip rows (2L values) and the high side's offset keep that alignment
-  if ((L & 1) == 0) {
-    int sc0 = -1;
-    if (i0 + 3 < L) sc0 = i0;
-    else if ((P.nx & 3) == 0 && i0 >= P.nx - L && i0 + 3 < P.nx) sc0 = i0 - (P.nx - 2 * L);
-    if (sc0 >= 0) {
-      a = ldmap4(sa, row + sc0);
-      b = ldb4(sb, row + sc0);
-      return;
-    }
-  }
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
+  for (int e = 0; e < 2; ++e) {
     const int x = i0 + e;
     if (x >= P.nx) {
-      el(a, e) = 0.f;
-      el(b, e) = 0.f;
+      el2(a, e) = 0.f;
+      el2(b, e) = 0.f;
     } else {
       const int sc = strip_coord(x, P.nx, L);
       if (sc >= 0) {
-        el(a, e) = ldmap(sa, row + sc);
-        el(b, e) = ldb(sb, row + sc);
+        el2(a, e) = ldmap(sa, row + sc);
+        el2(b, e) = ldb(sb, row + sc);
       }
     }
   }
 }
 
-// a, b along y at the four cells of an edge group inside the y strip
+// a, b along y at the two cells of an edge pair inside the y strip
 template <int OP, typename Maps>
-__device__ __forceinline__ void y_strip_coef(const StepParams &P, int nu, int i0, int sc, float4 &a, float4 &b) {
+__device__ __forceinline__ void y_strip_coef2(const StepParams &P, int nu, int i0, int sc, float2 &a, float2 &b) {
   using ST = typename Maps::StripT;
   const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[1] : P.sa2[1]);
   const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[1] : P.sb2[1]);
   const long long off = (long long)nu * P.strip_nu[1] + (long long)sc * P.pitch + i0;
-  a = ldmap4(sa, off);
-  b = ldb4(sb, off);
+  a = make_float2(ldmap(sa, off), ldmap(sa, off + 1));
+  b = make_float2(ldb(sb, off), ldb(sb, off + 1));
 }
 
 template <int N, typename Maps, bool EDGE>
-__device__ __forceinline__ void vel_compute(const StepParams &P, const Maps &M, float *st, int x0, int y0,
+__device__ __forceinline__ void vel_compute(const StepParams &P, const float *tab, float *st, int x0, int y0,
                                             int tid) {
   using S = VelStage<N, Maps>;
   const float *sp = st;
@@ -277,38 +351,37 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const Maps &M, 
   const float *ss = sr + S::kR;
   const unsigned char *si = reinterpret_cast<const unsigned char *>(ss + S::kS);
   if (EDGE || S::kIdx) {
-    density_tile<Maps, EDGE>(P, M, sr, si, x0, y0, tid);
+    density_tile<Maps, EDGE>(P, tab, sr, si, x0, y0, tid);
     __syncthreads();
   }
-  const int tx = tid & 31, ly = tid >> 5, lx = 4 * tx;
+  const int t2 = tid & 63, ly = tid >> 6, lx = 2 * t2;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
   const long long c = (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
   const float *own = ss + ly * kTX + lx;
-  float4 Dx, Dy;
-  vel_derivs(P, reinterpret_cast<const float(*)[kCW]>(sp), ly + 3, tx, Dx, Dy);
-  float4 k1, A[N > 0 ? N : 1], B[N > 0 ? N : 1];
+  float2 Dx, Dy;
+  vel_derivs2(P, sp, ly + 3, lx, Dx, Dy);
+  float2 k1, A[N > 0 ? N : 1], B[N > 0 ? N : 1];
   if constexpr (S::kIdx) {
-    typename Maps::Cell cell;
-    cell.t = *reinterpret_cast<const uchar4 *>(si + ly * kIW + lx);
-    k1 = M.ik1(cell);
+    const uchar2 cell = *reinterpret_cast<const uchar2 *>(si + ly * kIW + lx);
+    k1 = look2(tab, kTabIk1, cell);
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      A[nu] = M.template a<1>(cell, nu);
-      B[nu] = M.template b<1>(cell, nu);
+      A[nu] = look2(tab, kTabRelax + nu, cell);
+      B[nu] = look2(tab, kTabRelax + kMaxRelax + nu, cell);
     }
   } else {
-    k1 = sld4(own + (2 + 2 * N) * kArr);
+    k1 = sld2(own + (2 + 2 * N) * kArr);
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      A[nu] = sld4(own + (3 + 2 * N + nu) * kArr);
-      B[nu] = sld4(own + (3 + 3 * N + nu) * kArr);
+      A[nu] = sld2(own + (3 + 2 * N + nu) * kArr);
+      B[nu] = sld2(own + (3 + 3 * N + nu) * kArr);
     }
   }
-  // per-axis coefficients; in an edge group the C-PML strips replace them,
+  // per-axis coefficients; in an edge pair the C-PML strips replace them,
   // every strip value loaded before the first store (one memory latency)
-  float4 AX[N > 0 ? N : 1], BX[N > 0 ? N : 1], AY[N > 0 ? N : 1], BY[N > 0 ? N : 1];
+  float2 AX[N > 0 ? N : 1], BX[N > 0 ? N : 1], AY[N > 0 ? N : 1], BY[N > 0 ? N : 1];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
     AX[nu] = A[nu]; BX[nu] = B[nu]; AY[nu] = A[nu]; BY[nu] = B[nu];
@@ -317,88 +390,83 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const Maps &M, 
     const int scy = strip_coord(j, P.ny, P.L[1]);
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      x_strip_coef<1, Maps>(P, nu, i0, j, AX[nu], BX[nu]);
-      if (scy >= 0) y_strip_coef<1, Maps>(P, nu, i0, scy, AY[nu], BY[nu]);
+      x_strip_coef2<1, Maps>(P, nu, i0, j, AX[nu], BX[nu]);
+      if (scy >= 0) y_strip_coef2<1, Maps>(P, nu, i0, scy, AY[nu], BY[nu]);
     }
   }
-  float4 vx = sld4(own), vy = sld4(own + kArr);
-  float4 Sx = make_float4(Dx.x * k1.x, Dx.y * k1.y, Dx.z * k1.z, Dx.w * k1.w);
-  float4 Sy = make_float4(Dy.x * k1.x, Dy.y * k1.y, Dy.z * k1.z, Dy.w * k1.w);
+  float2 vx = sld2(own), vy = sld2(own + kArr);
+  float2 Sx = make_float2(Dx.x * k1.x, Dx.y * k1.y);
+  float2 Sy = make_float2(Dy.x * k1.x, Dy.y * k1.y);
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    const float4 px = sld4(own + (2 + nu) * kArr), py = sld4(own + (2 + N + nu) * kArr);
-    const float4 ax = AX[nu], bx = BX[nu], ay = AY[nu], by = BY[nu];
-    float4 nx_, ny_;
+    const float2 px = sld2(own + (2 + nu) * kArr), py = sld2(own + (2 + N + nu) * kArr);
+    float2 nx_, ny_;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      el(nx_, e) = fmaf(el(bx, e), el(px, e), el(ax, e) * el(Dx, e));
-      el(ny_, e) = fmaf(el(by, e), el(py, e), el(ay, e) * el(Dy, e));
-      el(Sx, e) += fmaf(P.w_new, el(nx_, e), P.w_old * el(px, e));
-      el(Sy, e) += fmaf(P.w_new, el(ny_, e), P.w_old * el(py, e));
+    for (int e = 0; e < 2; ++e) {
+      el2(nx_, e) = fmaf(el2(BX[nu], e), el2(px, e), el2(AX[nu], e) * el2(Dx, e));
+      el2(ny_, e) = fmaf(el2(BY[nu], e), el2(py, e), el2(AY[nu], e) * el2(Dy, e));
+      el2(Sx, e) += fmaf(P.w_new, el2(nx_, e), P.w_old * el2(px, e));
+      el2(Sy, e) += fmaf(P.w_new, el2(ny_, e), P.w_old * el2(py, e));
     }
     if (EDGE) {
-      nx_ = mask_pad(nx_, i0, P.nx);
-      ny_ = mask_pad(ny_, i0, P.nx);
+      nx_ = mask_pad2(nx_, i0, P.nx);
+      ny_ = mask_pad2(ny_, i0, P.nx);
     }
-    st_state4(P.psi1[0], nu * Sn + c, nx_);
-    st_state4(P.psi1[1], nu * Sn + c, ny_);
+    st_state2(P.psi1[0], nu * Sn + c, nx_);
+    st_state2(P.psi1[1], nu * Sn + c, ny_);
   }
-  const float4 r0 = sld4(sr + ly * kRWp + lx);
-  const float r4 = sr[ly * kRWp + lx + 4];
-  const float4 ru = sld4(sr + (ly + 1) * kRWp + lx);
+  const float *r = sr + ly * kRWp + lx;
+  const float2 r0 = sld2(r);
+  const float r2 = r[2];
+  const float2 ru = sld2(r + kRWp);
   vx.x -= P.two_dt / (r0.x + r0.y) * Sx.x;
-  vx.y -= P.two_dt / (r0.y + r0.z) * Sx.y;
-  vx.z -= P.two_dt / (r0.z + r0.w) * Sx.z;
-  vx.w -= P.two_dt / (r0.w + r4) * Sx.w;
+  vx.y -= P.two_dt / (r0.y + r2) * Sx.y;
   vy.x -= P.two_dt / (r0.x + ru.x) * Sy.x;
   vy.y -= P.two_dt / (r0.y + ru.y) * Sy.y;
-  vy.z -= P.two_dt / (r0.z + ru.z) * Sy.z;
-  vy.w -= P.two_dt / (r0.w + ru.w) * Sy.w;
   if (EDGE) {
-    vx = mask_pad(vx, i0, P.nx);
-    vy = mask_pad(vy, i0, P.nx);
+    vx = mask_pad2(vx, i0, P.nx);
+    vy = mask_pad2(vy, i0, P.nx);
   }
-  st_state4(P.v[0], c, vx);
-  st_state4(P.v[1], c, vy);
+  st_state2(P.v[0], c, vx);
+  st_state2(P.v[1], c, vy);
 }
 
 template <int N, typename Maps, bool EDGE>
-__device__ __forceinline__ void prs_compute(const StepParams &P, const Maps &M, const float *st, int x0, int y0,
+__device__ __forceinline__ void prs_compute(const StepParams &P, const float *tab, const float *st, int x0, int y0,
                                             int tid) {
   using S = PrsStage<N, Maps>;
   const float *sx = st, *sy = st + S::kX, *ss = sy + S::kY;
-  const int tx = tid & 31, ly = tid >> 5, lx = 4 * tx;
+  const int t2 = tid & 63, ly = tid >> 6, lx = 2 * t2;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
   const long long c = (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
   const float *own = ss + ly * kTX + lx;
-  float4 Dx, Dy;
-  prs_derivs(P, reinterpret_cast<const float(*)[kCW]>(sx), reinterpret_cast<const float(*)[kCW]>(sy), ly, tx,
-             Dx, Dy);
-  float4 k2, K, ch = make_float4(0.f, 0.f, 0.f, 0.f), A[N > 0 ? N : 1], B[N > 0 ? N : 1];
+  float2 Dx, Dy;
+  prs_derivs2(P, sx, sy, ly, lx, Dx, Dy);
+  float2 k2, K, ch = make_float2(0.f, 0.f), A[N > 0 ? N : 1], B[N > 0 ? N : 1];
   if constexpr (S::kIdx) {
-    typename Maps::Cell cell;
-    cell.t = *reinterpret_cast<const uchar4 *>(reinterpret_cast<const unsigned char *>(ss + S::kS) + ly * kTX + lx);
-    k2 = M.ik2(cell);
-    K = M.Kv(cell);
-    if (P.nl) ch = M.chiv(cell);
+    const uchar2 cell =
+        *reinterpret_cast<const uchar2 *>(reinterpret_cast<const unsigned char *>(ss + S::kS) + ly * kTX + lx);
+    k2 = look2(tab, kTabIk2, cell);
+    K = look2(tab, kTabK, cell);
+    if (P.nl) ch = look2(tab, kTabChi, cell);
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      A[nu] = M.template a<2>(cell, nu);
-      B[nu] = M.template b<2>(cell, nu);
+      A[nu] = look2(tab, kTabRelax + 2 * kMaxRelax + nu, cell);
+      B[nu] = look2(tab, kTabRelax + 3 * kMaxRelax + nu, cell);
     }
   } else {
-    k2 = sld4(own + (1 + 2 * N) * kArr);
-    K = sld4(own + (2 + 2 * N) * kArr);
-    if (P.nl) ch = sld4(own + (3 + 2 * N) * kArr);
+    k2 = sld2(own + (1 + 2 * N) * kArr);
+    K = sld2(own + (2 + 2 * N) * kArr);
+    if (P.nl) ch = sld2(own + (3 + 2 * N) * kArr);
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      A[nu] = sld4(own + (4 + 2 * N + nu) * kArr);
-      B[nu] = sld4(own + (4 + 3 * N + nu) * kArr);
+      A[nu] = sld2(own + (4 + 2 * N + nu) * kArr);
+      B[nu] = sld2(own + (4 + 3 * N + nu) * kArr);
     }
   }
-  float4 AX[N > 0 ? N : 1], BX[N > 0 ? N : 1], AY[N > 0 ? N : 1], BY[N > 0 ? N : 1];
+  float2 AX[N > 0 ? N : 1], BX[N > 0 ? N : 1], AY[N > 0 ? N : 1], BY[N > 0 ? N : 1];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
     AX[nu] = A[nu]; BX[nu] = B[nu]; AY[nu] = A[nu]; BY[nu] = B[nu];
@@ -407,58 +475,55 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const Maps &M, 
     const int scy = strip_coord(j, P.ny, P.L[1]);
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      x_strip_coef<2, Maps>(P, nu, i0, j, AX[nu], BX[nu]);
-      if (scy >= 0) y_strip_coef<2, Maps>(P, nu, i0, scy, AY[nu], BY[nu]);
+      x_strip_coef2<2, Maps>(P, nu, i0, j, AX[nu], BX[nu]);
+      if (scy >= 0) y_strip_coef2<2, Maps>(P, nu, i0, scy, AY[nu], BY[nu]);
     }
   }
-  float4 p = sld4(own);
-  float4 Sx = make_float4(Dx.x * k2.x, Dx.y * k2.y, Dx.z * k2.z, Dx.w * k2.w);
-  float4 Sy = make_float4(Dy.x * k2.x, Dy.y * k2.y, Dy.z * k2.z, Dy.w * k2.w);
+  float2 p = sld2(own);
+  float2 Sx = make_float2(Dx.x * k2.x, Dx.y * k2.y);
+  float2 Sy = make_float2(Dy.x * k2.x, Dy.y * k2.y);
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    const float4 px = sld4(own + (1 + nu) * kArr), py = sld4(own + (1 + N + nu) * kArr);
-    const float4 ax = AX[nu], bx = BX[nu], ay = AY[nu], by = BY[nu];
-    float4 nx_, ny_;
+    const float2 px = sld2(own + (1 + nu) * kArr), py = sld2(own + (1 + N + nu) * kArr);
+    float2 nx_, ny_;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      el(nx_, e) = fmaf(el(bx, e), el(px, e), el(ax, e) * el(Dx, e));
-      el(ny_, e) = fmaf(el(by, e), el(py, e), el(ay, e) * el(Dy, e));
-      el(Sx, e) += fmaf(P.w_new, el(nx_, e), P.w_old * el(px, e));
-      el(Sy, e) += fmaf(P.w_new, el(ny_, e), P.w_old * el(py, e));
+    for (int e = 0; e < 2; ++e) {
+      el2(nx_, e) = fmaf(el2(BX[nu], e), el2(px, e), el2(AX[nu], e) * el2(Dx, e));
+      el2(ny_, e) = fmaf(el2(BY[nu], e), el2(py, e), el2(AY[nu], e) * el2(Dy, e));
+      el2(Sx, e) += fmaf(P.w_new, el2(nx_, e), P.w_old * el2(px, e));
+      el2(Sy, e) += fmaf(P.w_new, el2(ny_, e), P.w_old * el2(py, e));
     }
     if (EDGE) {
-      nx_ = mask_pad(nx_, i0, P.nx);
-      ny_ = mask_pad(ny_, i0, P.nx);
+      nx_ = mask_pad2(nx_, i0, P.nx);
+      ny_ = mask_pad2(ny_, i0, P.nx);
     }
-    st_state4(P.psi2[0], nu * Sn + c, nx_);
-    st_state4(P.psi2[1], nu * Sn + c, ny_);
+    st_state2(P.psi2[0], nu * Sn + c, nx_);
+    st_state2(P.psi2[1], nu * Sn + c, ny_);
   }
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    float upd = P.dt * el(K, e) * (el(Sx, e) + el(Sy, e));
-    if (P.nl) upd /= fmaf(el(ch, e), el(p, e), 1.f);
-    el(p, e) -= upd;
+  for (int e = 0; e < 2; ++e) {
+    float upd = P.dt * el2(K, e) * (el2(Sx, e) + el2(Sy, e));
+    if (P.nl) upd /= fmaf(el2(ch, e), el2(p, e), 1.f);
+    el2(p, e) -= upd;
   }
-  if (EDGE) p = mask_pad(p, i0, P.nx);
-  st_state4(P.p, c, p);
+  if (EDGE) p = mask_pad2(p, i0, P.nx);
+  st_state2(P.p, c, p);
 }
 
 // Ring of stages: as many as fit next to the maps' table (2 .. 4).
 template <int N, typename Maps, bool VEL>
 struct Ring {
   static constexpr int kStage = VEL ? VelStage<N, Maps>::kFloats : PrsStage<N, Maps>::kFloats;
-  static constexpr int kEdge = VEL ? VelStage<N, Maps>::kEdge : PrsStage<N, Maps>::kEdge;
   static constexpr int kBudget = (220 * 1024 - 128) / 4 - Maps::kSmemFloats;  // floats
   static constexpr int kFit = kBudget / kStage;
   static constexpr int kStages = kFit > 4 ? 4 : kFit;
   static constexpr size_t kBytes = sizeof(float) * ((size_t)kStages * kStage + Maps::kSmemFloats) + 128;
   static_assert(kStages >= 2, "two stages must fit in shared memory");
-  static_assert(kEdge <= kStages * kStage, "a general tile must fit in the stages");
 };
 
-// One half step.  Block (32, 8), one per SM.
+// One half step.  Block (32, 16), one per SM.
 template <int N, typename Maps, bool VEL>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     pipe2d_kernel(const StepParams P, const Region R, const __grid_constant__ PipeMaps T) {
   using G = Ring<N, Maps, VEL>;
   constexpr int kS = G::kStages, kStage = G::kStage;
@@ -470,27 +535,12 @@ __global__ void __launch_bounds__(256, 1)
   float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float *tab = smem + kS * kStage;
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  Maps M(P);
-  M.stage(P, tab, tid);  // made visible by the first barrier below
-  M.bind(tab);
+  stage_table<Maps>(P, tab, tid);  // made visible by the barrier below
   if (tid == 0) {
     for (int q = 0; q < kS; ++q) mbar_init(&bar[q], 1);
     fence_mbarrier_init();
   }
-  // general-path tiles (periodic axes only)
-  const int ne = R.edges();
-  for (int e = blockIdx.x; e < ne; e += gridDim.x) {
-    int x0, y0;
-    R.edge_origin(e, x0, y0);
-    if (VEL)
-      vel2d_tile<N, Maps>(P, x0, y0, reinterpret_cast<float(*)[kPW]>(smem),
-                          reinterpret_cast<float(*)[kRW]>(smem + kPH * kPW), tab, false);
-    else
-      prs2d_tile<N, Maps>(P, x0, y0, reinterpret_cast<float(*)[kPW]>(smem),
-                          reinterpret_cast<float(*)[kPW]>(smem + kHX * kPW), tab, false);
-    __syncthreads();
-  }
-  __syncthreads();  // barriers initialised, table staged, general tiles done with the stages
+  __syncthreads();
   const int nh = R.halves();
   int h = blockIdx.x;
   if (h >= nh) return;
@@ -539,11 +589,11 @@ __global__ void __launch_bounds__(256, 1)
     R.half_origin(h, x0, y0);
     float *cur = smem + s * kStage;
     if (R.interior(x0, y0)) {
-      if (VEL) vel_compute<N, Maps, false>(P, M, cur, x0, y0, tid);
-      else prs_compute<N, Maps, false>(P, M, cur, x0, y0, tid);
+      if (VEL) vel_compute<N, Maps, false>(P, tab, cur, x0, y0, tid);
+      else prs_compute<N, Maps, false>(P, tab, cur, x0, y0, tid);
     } else {
-      if (VEL) vel_compute<N, Maps, true>(P, M, cur, x0, y0, tid);
-      else prs_compute<N, Maps, true>(P, M, cur, x0, y0, tid);
+      if (VEL) vel_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
+      else prs_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
     }
     __syncthreads();
     s = (s + 1) % kS;
@@ -556,7 +606,7 @@ __global__ void __launch_bounds__(256, 1)
 // the maps from there); a block copies a context's parameters to shared
 // memory, and stages its tissue-index table, when the context changes.
 template <int N, typename Maps, bool VEL>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     pipe2d_batched_kernel(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, int n_units) {
   using G = Ring<N, Maps, VEL>;
   constexpr int kS = G::kStages, kStage = G::kStage;
@@ -605,9 +655,9 @@ __global__ void __launch_bounds__(256, 1)
       // previous unit's compute finished at the last barrier
       const int *src = reinterpret_cast<const int *>(Ps + e.x);
       int *dst = reinterpret_cast<int *>(&sP);
-      for (int w = tid; w < (int)(sizeof(StepParams) / 4); w += 256) dst[w] = __ldg(src + w);
+      for (int w = tid; w < (int)(sizeof(StepParams) / 4); w += kThreads) dst[w] = __ldg(src + w);
       __syncthreads();
-      Maps(sP).stage(sP, tab, tid);
+      stage_table<Maps>(sP, tab, tid);
       cur = e.x;
     }
     if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
@@ -622,15 +672,13 @@ __global__ void __launch_bounds__(256, 1)
     }
     phase ^= 1u << s;
     pending &= ~(1u << s);
-    Maps M(sP);
-    M.bind(tab);
     float *stp = smem + s * kStage;
     if (e.w) {
-      if (VEL) vel_compute<N, Maps, false>(sP, M, stp, e.y, e.z, tid);
-      else prs_compute<N, Maps, false>(sP, M, stp, e.y, e.z, tid);
+      if (VEL) vel_compute<N, Maps, false>(sP, tab, stp, e.y, e.z, tid);
+      else prs_compute<N, Maps, false>(sP, tab, stp, e.y, e.z, tid);
     } else {
-      if (VEL) vel_compute<N, Maps, true>(sP, M, stp, e.y, e.z, tid);
-      else prs_compute<N, Maps, true>(sP, M, stp, e.y, e.z, tid);
+      if (VEL) vel_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
+      else prs_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
     }
     __syncthreads();
     s = (s + 1) % kS;
@@ -644,7 +692,7 @@ cudaError_t pipe_batched_launch(const StepParams *Ps, const PipeMaps *Ts, const 
   cudaError_t e = cudaFuncSetAttribute(pipe2d_batched_kernel<N, Maps, VEL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pipe2d_batched_kernel<N, Maps, VEL><<<grid, dim3(32, kBY), bytes, st>>>(Ps, Ts, units, n_units);
+  pipe2d_batched_kernel<N, Maps, VEL><<<grid, dim3(32, kThreads / 32), bytes, st>>>(Ps, Ts, units, n_units);
   return cudaGetLastError();
 }
 
@@ -667,7 +715,7 @@ cudaError_t pipe_launch(const StepParams &P, const Region &R, int grid, const Pi
   cudaError_t e = cudaFuncSetAttribute(pipe2d_kernel<N, Maps, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bytes);
   if (e != cudaSuccess) return e;
-  pipe2d_kernel<N, Maps, VEL><<<grid, dim3(32, kBY), bytes, st>>>(P, R, T);
+  pipe2d_kernel<N, Maps, VEL><<<grid, dim3(32, kThreads / 32), bytes, st>>>(P, R, T);
   return cudaGetLastError();
 }
 
@@ -689,39 +737,17 @@ Region region_of(const StepParams &P) {
   R.ny = P.ny;
   R.Lx = P.L[0] > 4 ? P.L[0] : 4;
   R.Ly = P.L[1] > 4 ? P.L[1] : 4;
-  R.tnx = (P.nx + kTX - 1) / kTX;
-  R.tny = (P.ny + kTY - 1) / kTY;
-  R.split = P.periodic[0] || P.periodic[1];
-  if (!R.split) {
-    // every half tile of the grid is staged
-    R.tx_lo = 0;
-    R.ntx = R.tnx;
-    R.ty_lo = 0;
-    R.nty = 0;
-    R.hy_lo = 0;
-    R.nhy = (P.ny + kHT - 1) / kHT;
-    return R;
-  }
-  // interior tiles as interior_tile defines them: x0 >= Lx, x0 + kTX + Lx <= nx
-  R.tx_lo = (R.Lx + kTX - 1) / kTX;
-  R.ty_lo = (R.Ly + kTY - 1) / kTY;
-  R.ntx = (P.nx - R.Lx) / kTX - R.tx_lo;
-  R.nty = (P.ny - R.Ly) / kTY - R.ty_lo;
-  if (R.ntx <= 0 || R.nty <= 0) {
-    R.ntx = 0;
-    R.nty = 0;
-    R.tx_lo = 0;
-    R.ty_lo = 0;
-  }
-  R.hy_lo = 2 * R.ty_lo;
-  R.nhy = 2 * R.nty;
+  R.ntx = (P.nx + kTX - 1) / kTX;
+  R.nhy = (P.ny + kHT - 1) / kHT;
   return R;
 }
 
 }  // namespace
 
 bool pipe2d_supported(const StepParams &P, int map_kind) {
-  return P.nz == 1 && (map_kind == 0 || map_kind == 2) && P.n_relax >= 0 && P.n_relax <= kMaxRelax;
+  // the copies read zero outside the grid: the zero-outside boundary only
+  return P.nz == 1 && (map_kind == 0 || map_kind == 2) && P.n_relax >= 0 && P.n_relax <= kMaxRelax &&
+         !P.periodic[0] && !P.periodic[1];
 }
 
 bool pipe2d_preferred(const StepParams &P, int map_kind) { return pipe2d_supported(P, map_kind); }

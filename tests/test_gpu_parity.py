@@ -372,15 +372,25 @@ def test_pipelined_path_equals_tile_path_bitwise(fw2, N, nl):
     _pipe_vs_tile(fw2, prob, 120)
 
 
-def test_pipelined_path_equals_tile_path_periodic_cross_taps(fw2):
+def test_pipelined_path_equals_tile_path_cross_taps(fw2):
+    """g11 cross taps (Sec. 3.1) on a zero-outside grid from a random state."""
     prob = synth.homogeneous((520, 200), 1e-4, 0.0)
     rng = np.random.default_rng(5)
     prob.c = (1500 + 200 * rng.random(prob.grid_shape)).astype(np.float32)
     prob.dt = 0.3 * 1e-4 / float(prob.c.max())
-    prob.bc = ("periodic", "periodic", "zero")
     taps = [1225 / 1024, -245 / 3072, 49 / 5120, -5 / 7168]
     prob.taps = (taps[0] * 0.98, taps[1], taps[2], taps[3], 0.005)
     _pipe_vs_tile(fw2, prob, 100, state=synth.random_state(prob, seed=3))
+
+
+def test_periodic_grids_take_the_tile_kernels(fw2):
+    prob = synth.homogeneous((144, 96), 1e-4, 0.0)
+    prob.dt = 0.3 * 1e-4 / 1540.0
+    prob.bc = ("periodic", "zero", "zero")
+    sim = fw2.Simulation(prob, kernel_path="pipe")
+    sim.step(1)
+    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    sim.close()
 
 
 @pytest.mark.parametrize("nl", ["pressure", "off"])
