@@ -1,6 +1,6 @@
 // Pipelined persistent 3D half steps (sm_103a) for bf16 coefficient maps;
 // same arithmetic as step3d.cu (bitwise the same results), one launch per
-// half step, one block of 256 threads per SM.
+// half step, one block of 512 threads per SM (two x cells per thread).
 //
 // Work unit: a 128 x 8 half tile of one z plane, x fastest, then y, then z.
 // For a coming unit one thread issues tiled TMA tensor copies into a free
@@ -37,19 +37,6 @@ using bf16 = __nv_bfloat16;
 
 constexpr int round32(int n) { return (n + 31) & ~31; }  // floats: 128-byte regions
 constexpr int fl(int bytes) { return (bytes + 3) / 4; }
-
-__device__ __forceinline__ float4 sld4(const float *s) { return *reinterpret_cast<const float4 *>(s); }
-__device__ __forceinline__ float4 sldh4(const bf16 *s) {
-  const uint2 u = *reinterpret_cast<const uint2 *>(s);
-  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
-  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
-  return make_float4(a.x, a.y, b.x, b.y);
-}
-// decay factors: bf16 maps hold 1 - b
-__device__ __forceinline__ float4 sldb4(const bf16 *s) {
-  const float4 v = sldh4(s);
-  return make_float4(1.f - v.x, 1.f - v.y, 1.f - v.z, 1.f - v.w);
-}
 
 // ------------------------------------------------------------- stages ---
 // velocity: p halo plane [15][136] (rows y0-3 .. y0+11), p column [8][8][128]
@@ -152,29 +139,65 @@ __device__ __forceinline__ void issue3(const PipeMaps &T, float *st, uint64_t *b
   }
 }
 
-// a, b along axis Q (OP: 1 faces, 2 centres) of mechanism nu at the four
-// cells of an edge group, from that axis' C-PML strip where the cells lie in
-// it (coef4 of the tile path); unchanged elsewhere
+// ------------------------------------------------------------ compute ---
+// 512 threads, two consecutive x cells each (64 threads per row); every cell
+// sees the operations of the tile kernels in the same order.
+constexpr int kThreads = 512;
+
+__device__ __forceinline__ float2 sld2(const float *s) { return *reinterpret_cast<const float2 *>(s); }
+__device__ __forceinline__ float2 sldh2(const bf16 *s) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(s));
+}
+__device__ __forceinline__ float2 sldb2(const bf16 *s) {  // bf16 maps hold 1 - b
+  const float2 v = sldh2(s);
+  return make_float2(1.f - v.x, 1.f - v.y);
+}
+__device__ __forceinline__ void st_state2(float *p, long long i, float2 v) {
+  __stcs(reinterpret_cast<float2 *>(p + i), v);
+}
+__device__ __forceinline__ float &el2(float2 &v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ float el2(const float2 &v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ float2 mask_pad2(float2 v, int i0, int nx) {
+  if (i0 + 1 >= nx) v.y = 0.f;
+  if (i0 >= nx) v.x = 0.f;
+  return v;
+}
+struct Win10 {
+  float v[10];
+};
+__device__ __forceinline__ Win10 win10(const float *row, int c) {
+  Win10 w;
+  const float2 *r2 = reinterpret_cast<const float2 *>(row + c);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float2 t = r2[i];
+    w.v[2 * i] = t.x;
+    w.v[2 * i + 1] = t.y;
+  }
+  return w;
+}
+
+// a, b along axis Q (OP: 1 faces, 2 centres) of mechanism nu at the two
+// cells of an edge pair, from that axis' C-PML strip where the cells lie in
+// it (coef4 of the tile kernels; its zero beyond the grid only reaches
+// masked cells); unchanged elsewhere
 template <int Q, int OP>
-__device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int j, int k, float4 &a, float4 &b) {
+__device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int j, int k, float2 &a, float2 &b) {
   const bf16 *sa = static_cast<const bf16 *>(OP == 1 ? P.sa1[Q] : P.sa2[Q]);
   const bf16 *sb = static_cast<const bf16 *>(OP == 1 ? P.sb1[Q] : P.sb2[Q]);
   const int L = P.L[Q];
   if (L <= 0) return;
   if (Q == 0) {
-    if (!(i0 < L || i0 + 3 >= P.nx - L)) return;
+    if (!(i0 < L || i0 + 1 >= P.nx - L)) return;
     const long long row = (long long)nu * P.strip_nu[0] + ((long long)k * P.ny + j) * (2 * L);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
       const int x = i0 + e;
-      if (x >= P.nx) {
-        el(a, e) = 0.f;
-        el(b, e) = 0.f;
-      } else {
+      if (x < P.nx) {
         const int sc = strip_coord(x, P.nx, L);
         if (sc >= 0) {
-          el(a, e) = ldmap(sa, row + sc);
-          el(b, e) = ldb(sb, row + sc);
+          el2(a, e) = ldmap(sa, row + sc);
+          el2(b, e) = ldb(sb, row + sc);
         }
       }
     }
@@ -183,8 +206,8 @@ __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int 
     if (sc < 0) return;
     const long long off = Q == 1 ? (long long)nu * P.strip_nu[1] + ((long long)k * (2 * L) + sc) * P.pitch + i0
                                  : (long long)nu * P.strip_nu[2] + ((long long)sc * P.ny + j) * P.pitch + i0;
-    a = ldmap4(sa, off);
-    b = ldb4(sb, off);
+    a = make_float2(ldmap(sa, off), ldmap(sa, off + 1));
+    b = make_float2(ldb(sb, off), ldb(sb, off + 1));
   }
 }
 
@@ -193,7 +216,7 @@ __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int 
 template <bool EDGE>
 __device__ __forceinline__ void density3(const StepParams &P, const bf16 *rb, float *rt, int x0, int y0, int k,
                                          int tid) {
-  for (int t = tid; t < kRhoTile; t += 256) {
+  for (int t = tid; t < kRhoTile; t += kThreads) {
     const int pz = t / ((kHT + 1) * kRWf), rem = t % ((kHT + 1) * kRWf);
     const int r = rem / kRWf, cc = rem % kRWf;
     int sx = cc, sy = r, sz = pz;
@@ -212,58 +235,57 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, flo
   using S = Vel3<N>;
   density3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), rt, x0, y0, k, tid);
   __syncthreads();
-  const int tx = tid & 31, ly = tid >> 5, lx = 4 * tx;
+  const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
   const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
   const int o = ly * kTX + lx;
-  // derivatives: x, y from the halo plane, z from the column
+  // derivatives: x, y from the halo plane (cell e at column lx + 4 + e), z
+  // from the column
   const float *sp = st + S::oHalo;
   const int sy = ly + 3;
-  float4 Dx, Dy, Dz;
+  float2 Dx, Dy, Dz;
   {
-    const float4 *r4 = reinterpret_cast<const float4 *>(sp + sy * kCW) + tx;
-    const float4 a = r4[0], b = r4[1], cc = r4[2];
-    const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, cc.x, cc.y, cc.z, cc.w};
+    const Win10 w = win10(sp + sy * kCW, lx);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
-      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w[4 + e + m] - w[4 + e - m + 1], d);
-      el(Dx, e) = d;
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m] - w.v[4 + e - m + 1], d);
+      el2(Dx, e) = d;
     }
   }
   {
-    float4 col[8];
+    float2 col[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) col[m] = sld4(sp + (sy - 3 + m) * kCW + lx + 4);
+    for (int m = 0; m < 8; ++m) col[m] = sld2(sp + (sy - 3 + m) * kCW + lx + 4);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
-      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[3 + m], e) - el(col[4 - m], e), d);
-      el(Dy, e) = d;
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(col[3 + m], e) - el2(col[4 - m], e), d);
+      el2(Dy, e) = d;
     }
   }
   {
-    float4 zc[8];
+    float2 zc[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) zc[m] = sld4(st + S::oCol + m * kArr + o);
+    for (int m = 0; m < 8; ++m) zc[m] = sld2(st + S::oCol + m * kArr + o);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
-      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(zc[3 + m], e) - el(zc[4 - m], e), d);
-      el(Dz, e) = d;
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(zc[3 + m], e) - el2(zc[4 - m], e), d);
+      el2(Dz, e) = d;
     }
   }
-  const float4 k1 = sldh4(reinterpret_cast<const bf16 *>(st + S::oK) + o);
-  float4 A[3][N > 0 ? N : 1], B[3][N > 0 ? N : 1];
+  const float2 k1 = sldh2(reinterpret_cast<const bf16 *>(st + S::oK) + o);
+  float2 A[3][N > 0 ? N : 1], B[3][N > 0 ? N : 1];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    const float4 a = sldh4(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
-    const float4 b = sldb4(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
+    const float2 a = sldh2(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
+    const float2 b = sldb2(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       A[q][nu] = a;
@@ -278,116 +300,114 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, flo
       strip3<2, 1>(P, nu, i0, j, k, A[2][nu], B[2][nu]);
     }
   }
-  float4 v0 = sld4(st + S::oV + o), v1 = sld4(st + S::oV + kArr + o), v2 = sld4(st + S::oV + 2 * kArr + o);
-  float4 S0, S1, S2;
+  float2 v0 = sld2(st + S::oV + o), v1 = sld2(st + S::oV + kArr + o), v2 = sld2(st + S::oV + 2 * kArr + o);
+  float2 S0, S1, S2;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    el(S0, e) = el(Dx, e) * el(k1, e);
-    el(S1, e) = el(Dy, e) * el(k1, e);
-    el(S2, e) = el(Dz, e) * el(k1, e);
+  for (int e = 0; e < 2; ++e) {
+    el2(S0, e) = el2(Dx, e) * el2(k1, e);
+    el2(S1, e) = el2(Dy, e) * el2(k1, e);
+    el2(S2, e) = el2(Dz, e) * el2(k1, e);
   }
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    const float4 q0 = sld4(st + S::oPsi + nu * kArr + o);
-    const float4 q1 = sld4(st + S::oPsi + (N + nu) * kArr + o);
-    const float4 q2 = sld4(st + S::oPsi + (2 * N + nu) * kArr + o);
-    float4 n0, n1, n2;
+    const float2 q0 = sld2(st + S::oPsi + nu * kArr + o);
+    const float2 q1 = sld2(st + S::oPsi + (N + nu) * kArr + o);
+    const float2 q2 = sld2(st + S::oPsi + (2 * N + nu) * kArr + o);
+    float2 n0, n1, n2;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      el(n0, e) = fmaf(el(B[0][nu], e), el(q0, e), el(A[0][nu], e) * el(Dx, e));
-      el(n1, e) = fmaf(el(B[1][nu], e), el(q1, e), el(A[1][nu], e) * el(Dy, e));
-      el(n2, e) = fmaf(el(B[2][nu], e), el(q2, e), el(A[2][nu], e) * el(Dz, e));
-      el(S0, e) += fmaf(P.w_new, el(n0, e), P.w_old * el(q0, e));
-      el(S1, e) += fmaf(P.w_new, el(n1, e), P.w_old * el(q1, e));
-      el(S2, e) += fmaf(P.w_new, el(n2, e), P.w_old * el(q2, e));
+    for (int e = 0; e < 2; ++e) {
+      el2(n0, e) = fmaf(el2(B[0][nu], e), el2(q0, e), el2(A[0][nu], e) * el2(Dx, e));
+      el2(n1, e) = fmaf(el2(B[1][nu], e), el2(q1, e), el2(A[1][nu], e) * el2(Dy, e));
+      el2(n2, e) = fmaf(el2(B[2][nu], e), el2(q2, e), el2(A[2][nu], e) * el2(Dz, e));
+      el2(S0, e) += fmaf(P.w_new, el2(n0, e), P.w_old * el2(q0, e));
+      el2(S1, e) += fmaf(P.w_new, el2(n1, e), P.w_old * el2(q1, e));
+      el2(S2, e) += fmaf(P.w_new, el2(n2, e), P.w_old * el2(q2, e));
     }
     if (EDGE) {
-      n0 = mask_pad(n0, i0, P.nx);
-      n1 = mask_pad(n1, i0, P.nx);
-      n2 = mask_pad(n2, i0, P.nx);
+      n0 = mask_pad2(n0, i0, P.nx);
+      n1 = mask_pad2(n1, i0, P.nx);
+      n2 = mask_pad2(n2, i0, P.nx);
     }
-    st_state4(P.psi1[0], nu * Sn + c, n0);
-    st_state4(P.psi1[1], nu * Sn + c, n1);
-    st_state4(P.psi1[2], nu * Sn + c, n2);
+    st_state2(P.psi1[0], nu * Sn + c, n0);
+    st_state2(P.psi1[1], nu * Sn + c, n1);
+    st_state2(P.psi1[2], nu * Sn + c, n2);
   }
   const float *r = rt + ly * kRWf + lx;
-  const float4 r0 = sld4(r);
-  const float r4 = r[4];
-  const float4 ru = sld4(r + kRWf);
-  const float4 rz = sld4(r + (kHT + 1) * kRWf);
-  const float rr[5] = {r0.x, r0.y, r0.z, r0.w, r4};
+  const float2 r0 = sld2(r);
+  const float r2 = r[2];
+  const float2 ru = sld2(r + kRWf);
+  const float2 rz = sld2(r + (kHT + 1) * kRWf);
+  const float rr[3] = {r0.x, r0.y, r2};
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    el(v0, e) -= P.two_dt / (rr[e] + rr[e + 1]) * el(S0, e);
-    el(v1, e) -= P.two_dt / (rr[e] + el(ru, e)) * el(S1, e);
-    el(v2, e) -= P.two_dt / (rr[e] + el(rz, e)) * el(S2, e);
+  for (int e = 0; e < 2; ++e) {
+    el2(v0, e) -= P.two_dt / (rr[e] + rr[e + 1]) * el2(S0, e);
+    el2(v1, e) -= P.two_dt / (rr[e] + el2(ru, e)) * el2(S1, e);
+    el2(v2, e) -= P.two_dt / (rr[e] + el2(rz, e)) * el2(S2, e);
   }
   if (EDGE) {
-    v0 = mask_pad(v0, i0, P.nx);
-    v1 = mask_pad(v1, i0, P.nx);
-    v2 = mask_pad(v2, i0, P.nx);
+    v0 = mask_pad2(v0, i0, P.nx);
+    v1 = mask_pad2(v1, i0, P.nx);
+    v2 = mask_pad2(v2, i0, P.nx);
   }
-  st_state4(P.v[0], c, v0);
-  st_state4(P.v[1], c, v1);
-  st_state4(P.v[2], c, v2);
+  st_state2(P.v[0], c, v0);
+  st_state2(P.v[1], c, v1);
+  st_state2(P.v[2], c, v2);
 }
 
 template <int N, bool EDGE>
 __device__ __forceinline__ void prs3_compute(const StepParams &P, const float *st, int x0, int y0, int k,
                                              int tid) {
   using S = Prs3<N>;
-  const int tx = tid & 31, ly = tid >> 5, lx = 4 * tx;
+  const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
   const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
   const int o = ly * kTX + lx;
-  float4 Dx, Dy, Dz;
+  float2 Dx, Dy, Dz;
   {
-    const float4 *r4 = reinterpret_cast<const float4 *>(st + S::oVx + ly * kCW) + tx;
-    const float4 a = r4[0], b = r4[1], cc = r4[2];
-    const float w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, cc.x, cc.y, cc.z, cc.w};
+    const Win10 w = win10(st + S::oVx + ly * kCW, lx);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
-      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w[4 + e + m - 1] - w[4 + e - m], d);
-      el(Dx, e) = d;
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m - 1] - w.v[4 + e - m], d);
+      el2(Dx, e) = d;
     }
   }
   {
-    float4 col[8];
+    float2 col[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) col[m] = sld4(st + S::oVy + (ly + m) * kTX + lx);
+    for (int m = 0; m < 8; ++m) col[m] = sld2(st + S::oVy + (ly + m) * kTX + lx);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
-      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(col[4 + m - 1], e) - el(col[4 - m], e), d);
-      el(Dy, e) = d;
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(col[4 + m - 1], e) - el2(col[4 - m], e), d);
+      el2(Dy, e) = d;
     }
   }
   {
-    float4 zc[8];
+    float2 zc[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) zc[m] = sld4(st + S::oCol + m * kArr + o);
+    for (int m = 0; m < 8; ++m) zc[m] = sld2(st + S::oCol + m * kArr + o);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
-      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el(zc[4 + m - 1], e) - el(zc[4 - m], e), d);
-      el(Dz, e) = d;
+      for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(zc[4 + m - 1], e) - el2(zc[4 - m], e), d);
+      el2(Dz, e) = d;
     }
   }
-  const float4 k2 = sldh4(reinterpret_cast<const bf16 *>(st + S::oIk) + o);
-  const float4 K = sldh4(reinterpret_cast<const bf16 *>(st + S::oKm) + o);
-  float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (P.nl) ch = sldh4(reinterpret_cast<const bf16 *>(st + S::oChi) + o);
-  float4 A[3][N > 0 ? N : 1], B[3][N > 0 ? N : 1];
+  const float2 k2 = sldh2(reinterpret_cast<const bf16 *>(st + S::oIk) + o);
+  const float2 K = sldh2(reinterpret_cast<const bf16 *>(st + S::oKm) + o);
+  float2 ch = make_float2(0.f, 0.f);
+  if (P.nl) ch = sldh2(reinterpret_cast<const bf16 *>(st + S::oChi) + o);
+  float2 A[3][N > 0 ? N : 1], B[3][N > 0 ? N : 1];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    const float4 a = sldh4(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
-    const float4 b = sldb4(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
+    const float2 a = sldh2(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
+    const float2 b = sldb2(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       A[q][nu] = a;
@@ -402,50 +422,50 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const float *s
       strip3<2, 2>(P, nu, i0, j, k, A[2][nu], B[2][nu]);
     }
   }
-  float4 p = sld4(st + S::oP + o);
-  float4 S0, S1, S2;
+  float2 p = sld2(st + S::oP + o);
+  float2 S0, S1, S2;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    el(S0, e) = el(Dx, e) * el(k2, e);
-    el(S1, e) = el(Dy, e) * el(k2, e);
-    el(S2, e) = el(Dz, e) * el(k2, e);
+  for (int e = 0; e < 2; ++e) {
+    el2(S0, e) = el2(Dx, e) * el2(k2, e);
+    el2(S1, e) = el2(Dy, e) * el2(k2, e);
+    el2(S2, e) = el2(Dz, e) * el2(k2, e);
   }
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    const float4 q0 = sld4(st + S::oPsi + nu * kArr + o);
-    const float4 q1 = sld4(st + S::oPsi + (N + nu) * kArr + o);
-    const float4 q2 = sld4(st + S::oPsi + (2 * N + nu) * kArr + o);
-    float4 n0, n1, n2;
+    const float2 q0 = sld2(st + S::oPsi + nu * kArr + o);
+    const float2 q1 = sld2(st + S::oPsi + (N + nu) * kArr + o);
+    const float2 q2 = sld2(st + S::oPsi + (2 * N + nu) * kArr + o);
+    float2 n0, n1, n2;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      el(n0, e) = fmaf(el(B[0][nu], e), el(q0, e), el(A[0][nu], e) * el(Dx, e));
-      el(n1, e) = fmaf(el(B[1][nu], e), el(q1, e), el(A[1][nu], e) * el(Dy, e));
-      el(n2, e) = fmaf(el(B[2][nu], e), el(q2, e), el(A[2][nu], e) * el(Dz, e));
-      el(S0, e) += fmaf(P.w_new, el(n0, e), P.w_old * el(q0, e));
-      el(S1, e) += fmaf(P.w_new, el(n1, e), P.w_old * el(q1, e));
-      el(S2, e) += fmaf(P.w_new, el(n2, e), P.w_old * el(q2, e));
+    for (int e = 0; e < 2; ++e) {
+      el2(n0, e) = fmaf(el2(B[0][nu], e), el2(q0, e), el2(A[0][nu], e) * el2(Dx, e));
+      el2(n1, e) = fmaf(el2(B[1][nu], e), el2(q1, e), el2(A[1][nu], e) * el2(Dy, e));
+      el2(n2, e) = fmaf(el2(B[2][nu], e), el2(q2, e), el2(A[2][nu], e) * el2(Dz, e));
+      el2(S0, e) += fmaf(P.w_new, el2(n0, e), P.w_old * el2(q0, e));
+      el2(S1, e) += fmaf(P.w_new, el2(n1, e), P.w_old * el2(q1, e));
+      el2(S2, e) += fmaf(P.w_new, el2(n2, e), P.w_old * el2(q2, e));
     }
     if (EDGE) {
-      n0 = mask_pad(n0, i0, P.nx);
-      n1 = mask_pad(n1, i0, P.nx);
-      n2 = mask_pad(n2, i0, P.nx);
+      n0 = mask_pad2(n0, i0, P.nx);
+      n1 = mask_pad2(n1, i0, P.nx);
+      n2 = mask_pad2(n2, i0, P.nx);
     }
-    st_state4(P.psi2[0], nu * Sn + c, n0);
-    st_state4(P.psi2[1], nu * Sn + c, n1);
-    st_state4(P.psi2[2], nu * Sn + c, n2);
+    st_state2(P.psi2[0], nu * Sn + c, n0);
+    st_state2(P.psi2[1], nu * Sn + c, n1);
+    st_state2(P.psi2[2], nu * Sn + c, n2);
   }
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    float upd = P.dt * el(K, e) * (el(S0, e) + el(S1, e) + el(S2, e));
-    if (P.nl) upd /= fmaf(el(ch, e), el(p, e), 1.f);
-    el(p, e) -= upd;
+  for (int e = 0; e < 2; ++e) {
+    float upd = P.dt * el2(K, e) * (el2(S0, e) + el2(S1, e) + el2(S2, e));
+    if (P.nl) upd /= fmaf(el2(ch, e), el2(p, e), 1.f);
+    el2(p, e) -= upd;
   }
-  if (EDGE) p = mask_pad(p, i0, P.nx);
-  st_state4(P.p, c, p);
+  if (EDGE) p = mask_pad2(p, i0, P.nx);
+  st_state2(P.p, c, p);
 }
 
 template <int N, bool VEL>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     pipe3d_kernel(const StepParams P, const Region3 R, const __grid_constant__ PipeMaps T) {
   using G = Ring3<N, VEL>;
   constexpr int kStage = G::kStage;
@@ -519,7 +539,7 @@ cudaError_t pipe3_launch(const StepParams &P, const Region3 &R, int grid, const 
   cudaError_t e =
       cudaFuncSetAttribute(pipe3d_kernel<N, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pipe3d_kernel<N, VEL><<<grid, dim3(32, kBY), bytes, st>>>(P, R, T);
+  pipe3d_kernel<N, VEL><<<grid, dim3(32, kThreads / 32), bytes, st>>>(P, R, T);
   return cudaGetLastError();
 }
 
