@@ -10,8 +10,9 @@
 // relaxation map in one 3D box.  They complete on the stage's mbarrier while
 // all threads compute the current half tile from another stage, two cells
 // each, so up to ~190 KB stay in flight per SM without registers or load
-// instructions of the computing threads; results go straight from registers
-// to HBM.
+// instructions of the computing threads.  With float maps the updated arrays
+// are written back into the stage and leave for HBM as TMA tensor stores;
+// with the index form every thread stores its own results.
 //
 // Boundaries: the copies read zero outside the grid (the zero-outside rule of
 // the operand halo); half tiles at the edge of the grid or in a C-PML strip
@@ -34,7 +35,6 @@ constexpr int kRWp = kTX + 4;       // density tile columns x0 .. x0+TX+3 (= kRW
 constexpr int kIW = kTX + 16;       // staged index bytes per row x0 .. x0+TX+15
 constexpr int kArr = kHT * kTX;     // floats of one streamed array per half tile
 
-__device__ __forceinline__ float4 sld4(const float *s) { return *reinterpret_cast<const float4 *>(s); }
 
 template <typename Maps>
 struct IsIdx {
@@ -165,6 +165,32 @@ __device__ __forceinline__ void issue_stage(const StepParams &P, const PipeMaps 
   }
 }
 
+// Store the updated arrays of a half tile from its stage (one thread, after
+// every thread's fence and a barrier): velocity v_x, v_y, psi1_x, psi1_y;
+// pressure p, psi2_x, psi2_y.  The copies write nothing outside the grid.
+template <int N, typename Maps, bool VEL>
+__device__ __forceinline__ void store_stage(const PipeMaps &T, const float *st, int x0, int y0) {
+  if (VEL) {
+    using S = VelStage<N, Maps>;
+    const float *ss = st + S::kP + S::kR;
+    tma_store_2d(&T.m[2], x0, y0, ss);
+    tma_store_2d(&T.m[3], x0, y0, ss + kArr);
+    if (N > 0) {
+      tma_store_3d(&T.m[4], x0, y0, 0, ss + 2 * kArr);
+      tma_store_3d(&T.m[5], x0, y0, 0, ss + (2 + N) * kArr);
+    }
+  } else {
+    using S = PrsStage<N, Maps>;
+    const float *ss = st + S::kX + S::kY;
+    tma_store_2d(&T.m[2], x0, y0, ss);
+    if (N > 0) {
+      tma_store_3d(&T.m[3], x0, y0, 0, ss + kArr);
+      tma_store_3d(&T.m[4], x0, y0, 0, ss + (1 + N) * kArr);
+    }
+  }
+  bulk_commit();
+}
+
 // ------------------------------------------------------------ compute ---
 // 512 threads per block, two consecutive x cells each: thread t of row ly
 // (64 threads per row) owns cells x0 + 2t, x0 + 2t + 1.  Every cell sees the
@@ -176,15 +202,30 @@ __device__ __forceinline__ float2 sld2(const float *s) { return *reinterpret_cas
 __device__ __forceinline__ void st_state2(float *p, long long i, float2 v) {
   __stcs(reinterpret_cast<float2 *>(p + i), v);
 }
-__device__ __forceinline__ float &el2(float2 &v, int e) { return e == 0 ? v.x : v.y; }
-__device__ __forceinline__ float el2(const float2 &v, int e) { return e == 0 ? v.x : v.y; }
 // zero the cells of a pair that fall in the row padding (x >= nx)
 __device__ __forceinline__ float2 mask_pad2(float2 v, int i0, int nx) {
   if (i0 + 1 >= nx) v.y = 0.f;
   if (i0 >= nx) v.x = 0.f;
   return v;
 }
-
+// Results leave through the stage and TMA tensor stores with float maps (the
+// memory-bound form, where fewer store instructions pay); with the index
+// form (bound by its compute phase) each thread stores its own results.
+template <typename Maps>
+struct TmaStore {
+  static constexpr bool value = !IsIdx<Maps>::value;
+};
+// one result pair of array `a` (stage offset in arrays) of cell c
+template <typename Maps, bool EDGE>
+__device__ __forceinline__ void put2(float *own, int a, float *g, long long gi, float2 v, int i0, int nx) {
+  if constexpr (TmaStore<Maps>::value) {
+    *reinterpret_cast<float2 *>(own + a * kArr) = v;
+  } else {
+    st_state2(g, gi, EDGE ? mask_pad2(v, i0, nx) : v);
+  }
+}
+__device__ __forceinline__ float &el2(float2 &v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ float el2(const float2 &v, int e) { return e == 0 ? v.x : v.y; }
 // ten consecutive shared-memory values from column c of a row (c even)
 struct Win10 {
   float v[10];
@@ -357,9 +398,9 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
   const int t2 = tid & 63, ly = tid >> 6, lx = 2 * t2;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
+  float *own = const_cast<float *>(ss) + ly * kTX + lx;
   const long long c = (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
-  const float *own = ss + ly * kTX + lx;
   float2 Dx, Dy;
   vel_derivs2(P, sp, ly + 3, lx, Dx, Dy);
   float2 k1, A[N > 0 ? N : 1], B[N > 0 ? N : 1];
@@ -408,12 +449,8 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
       el2(Sx, e) += fmaf(P.w_new, el2(nx_, e), P.w_old * el2(px, e));
       el2(Sy, e) += fmaf(P.w_new, el2(ny_, e), P.w_old * el2(py, e));
     }
-    if (EDGE) {
-      nx_ = mask_pad2(nx_, i0, P.nx);
-      ny_ = mask_pad2(ny_, i0, P.nx);
-    }
-    st_state2(P.psi1[0], nu * Sn + c, nx_);
-    st_state2(P.psi1[1], nu * Sn + c, ny_);
+    put2<Maps, EDGE>(own, 2 + nu, P.psi1[0], nu * Sn + c, nx_, i0, P.nx);
+    put2<Maps, EDGE>(own, 2 + N + nu, P.psi1[1], nu * Sn + c, ny_, i0, P.nx);
   }
   const float *r = sr + ly * kRWp + lx;
   const float2 r0 = sld2(r);
@@ -423,25 +460,22 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
   vx.y -= P.two_dt / (r0.y + r2) * Sx.y;
   vy.x -= P.two_dt / (r0.x + ru.x) * Sy.x;
   vy.y -= P.two_dt / (r0.y + ru.y) * Sy.y;
-  if (EDGE) {
-    vx = mask_pad2(vx, i0, P.nx);
-    vy = mask_pad2(vy, i0, P.nx);
-  }
-  st_state2(P.v[0], c, vx);
-  st_state2(P.v[1], c, vy);
+  put2<Maps, EDGE>(own, 0, P.v[0], c, vx, i0, P.nx);
+  put2<Maps, EDGE>(own, 1, P.v[1], c, vy, i0, P.nx);
 }
 
 template <int N, typename Maps, bool EDGE>
-__device__ __forceinline__ void prs_compute(const StepParams &P, const float *tab, const float *st, int x0, int y0,
+__device__ __forceinline__ void prs_compute(const StepParams &P, const float *tab, float *st, int x0, int y0,
                                             int tid) {
   using S = PrsStage<N, Maps>;
-  const float *sx = st, *sy = st + S::kX, *ss = sy + S::kY;
+  const float *sx = st, *sy = st + S::kX;
+  float *ss = st + S::kX + S::kY;
   const int t2 = tid & 63, ly = tid >> 6, lx = 2 * t2;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
+  float *own = ss + ly * kTX + lx;
   const long long c = (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
-  const float *own = ss + ly * kTX + lx;
   float2 Dx, Dy;
   prs_derivs2(P, sx, sy, ly, lx, Dx, Dy);
   float2 k2, K, ch = make_float2(0.f, 0.f), A[N > 0 ? N : 1], B[N > 0 ? N : 1];
@@ -493,12 +527,8 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const float *ta
       el2(Sx, e) += fmaf(P.w_new, el2(nx_, e), P.w_old * el2(px, e));
       el2(Sy, e) += fmaf(P.w_new, el2(ny_, e), P.w_old * el2(py, e));
     }
-    if (EDGE) {
-      nx_ = mask_pad2(nx_, i0, P.nx);
-      ny_ = mask_pad2(ny_, i0, P.nx);
-    }
-    st_state2(P.psi2[0], nu * Sn + c, nx_);
-    st_state2(P.psi2[1], nu * Sn + c, ny_);
+    put2<Maps, EDGE>(own, 1 + nu, P.psi2[0], nu * Sn + c, nx_, i0, P.nx);
+    put2<Maps, EDGE>(own, 1 + N + nu, P.psi2[1], nu * Sn + c, ny_, i0, P.nx);
   }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -506,8 +536,7 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const float *ta
     if (P.nl) upd /= fmaf(el2(ch, e), el2(p, e), 1.f);
     el2(p, e) -= upd;
   }
-  if (EDGE) p = mask_pad2(p, i0, P.nx);
-  st_state2(P.p, c, p);
+  put2<Maps, EDGE>(own, 0, P.p, c, p, i0, P.nx);
 }
 
 // Ring of stages: as many as fit next to the maps' table (2 .. 4).
@@ -566,6 +595,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (tid == 0) {
         int xq, yq;
         R.half_origin(hs, xq, yq);
+        bulk_wait_read<0>();  // its results have left for HBM
         issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
       }
       pending |= 1u << q;
@@ -580,6 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         report_status(P.status, kStatusWaitTimeout);
         for (int q = 0; q < kS; ++q)
           if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
+        bulk_wait_all();
       }
       return;
     }
@@ -595,9 +626,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (VEL) vel_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
       else prs_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
     }
-    __syncthreads();
+    if constexpr (TmaStore<Maps>::value) {
+      fence_proxy_async_smem();  // this thread's results, visible to the store
+      __syncthreads();
+      if (tid == 0) store_stage<N, Maps, VEL>(T, cur, x0, y0);
+    } else {
+      __syncthreads();
+    }
     s = (s + 1) % kS;
   }
+  if (tid == 0) bulk_wait_all();
 }
 
 // Batched half step over a unit table of several contexts (one group: same
@@ -644,6 +682,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int q = (s + kS - 1) % kS;
       if (tid == 0) {
         const int4 e = units[hs];
+        bulk_wait_read<0>();
         issue_stage<N, Maps, VEL>(Ps[e.x], Ts[e.x], smem + q * kStage, &bar[q], e.y, e.z);
       }
       pending |= 1u << q;
@@ -667,6 +706,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         report_status(sP.status, kStatusWaitTimeout);
         for (int q = 0; q < kS; ++q)
           if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
+        bulk_wait_all();
       }
       return;
     }
@@ -680,9 +720,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (VEL) vel_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
       else prs_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
     }
-    __syncthreads();
+    if constexpr (TmaStore<Maps>::value) {
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) store_stage<N, Maps, VEL>(Ts[e.x], stp, e.y, e.z);
+    } else {
+      __syncthreads();
+    }
     s = (s + 1) % kS;
   }
+  if (tid == 0) bulk_wait_all();
 }
 
 template <int N, typename Maps, bool VEL>
