@@ -195,7 +195,8 @@ def device_id_for_smi():
 def oracle_baseline(prob, steps, window, maps="f32"):
     """The FP64 oracle, as it stands, on a window of the workload (host cores)."""
     from oracle.core import OracleSim
-    orc = OracleSim(prob, round_to=maps, window=window)
+    # the index form's coefficients are the float maps gathered from its tables
+    orc = OracleSim(prob, round_to="f32" if maps == "idx" else maps, window=window)
     orc.run(2)
     t0 = time.perf_counter()
     orc.run(steps)
