@@ -212,6 +212,22 @@ def oracle_baseline(prob, steps, window, maps="f32"):
 # arms
 # --------------------------------------------------------------------------
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Whole-job GPts/s: every rank updates `cells` points `steps` times in the
+    slowest rank's `seconds` (weak scaling)."""
+    return world * cells * steps / seconds / 1e9
+
+
 def run_fw2(args, rank, world, dist):
     import torch
     import synth
@@ -274,12 +290,9 @@ def run_fw2(args, rank, world, dist):
     fw2.fw2_profile(sim.ctx, False)
     if fw2.fw2_kernel_path(sim.ctx) == "pipe":
         kv, kp = ("pipe2d_vel", "pipe2d_prs") if len(prob.shape) == 2 else ("pipe3d_vel", "pipe3d_prs")
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_max = float(t.item())
+    elapsed_max = max_over_ranks(elapsed_ms, dist)
     pts = prob.n_pts
-    value = world * pts * args.steps / (elapsed_max * 1e-3) / 1e9
+    value = job_rate(world, pts, args.steps, elapsed_max * 1e-3)
     # roofline of the dominant kernel
     peaks, peak_kind = measured_peaks()
     dom = kv if vel_ms >= prs_ms else kp
@@ -335,10 +348,7 @@ def run_fw2(args, rank, world, dist):
         t1 = time.perf_counter()
         d2h = trace_host.numel() * 4
         s2.close()
-        te = torch.tensor([t1 - t0], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * pts * args.steps / float(te.item()) / 1e9, "unit": UNIT,
+        e2e = {"value": job_rate(world, pts, args.steps, max_over_ranks(t1 - t0, dist)), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps),
                "scope": "whole job through the C ABI from pinned host buffers: set_medium, set_relaxation, "
                         "add_source, record, coefficient build, K steps, trace read-back"}
@@ -433,10 +443,8 @@ def run_batch(args, rank, world, dist):
         t_plain += dt * args.steps / plain_steps       # time for the full K steps at this rate
         finish.append(t_plain)
         done += p.n_pts * args.steps
-    te = torch.tensor([t_batch], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    value = world * cells * args.steps / float(te.item()) / 1e9
+    t_batch = max_over_ranks(t_batch, dist)
+    value = job_rate(world, cells, args.steps, t_batch)
     if rank != 0:
         return
     peaks, _ = measured_peaks()
