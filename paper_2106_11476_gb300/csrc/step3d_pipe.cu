@@ -211,6 +211,58 @@ __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int 
   }
 }
 
+// Prefetch into L2 the C-PML strip rows an edge unit will read (warp 0, one
+// unit ahead): its C-PML coefficients are otherwise read straight from DRAM
+// while the unit computes.  OP: 1 velocity (a1, b1), 2 pressure (a2, b2).
+__device__ __forceinline__ void l2_line(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+template <int N, int OP>
+__device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int y0, int k, int lane) {
+  if (N == 0) return;
+  const bf16 *sa[3], *sb[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    sa[q] = static_cast<const bf16 *>(OP == 1 ? P.sa1[q] : P.sa2[q]);
+    sb[q] = static_cast<const bf16 *>(OP == 1 ? P.sb1[q] : P.sb2[q]);
+  }
+  // x strip: rows (k, y) of 2L values, for units reaching into it
+  const int Lx = P.L[0];
+  if (Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
+    for (int t = lane; t < kHT * N * 2; t += 32) {
+      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+      const int y = y0 + r;
+      if (y >= P.ny) continue;
+      const bf16 *b = (ab ? sb[0] : sa[0]) + nu * P.strip_nu[0] + ((long long)k * P.ny + y) * (2 * Lx);
+      for (int o = 0; o < 2 * Lx; o += 64) l2_line(b + o);  // 128-byte lines
+    }
+  }
+  // y strip: rows (k, sc) of the unit's 128 columns
+  const int Ly = P.L[1];
+  if (Ly > 0) {
+    for (int t = lane; t < kHT * N * 2; t += 32) {
+      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+      const int y = y0 + r;
+      const int sc = y < P.ny ? strip_coord(y, P.ny, Ly) : -1;
+      if (sc < 0) continue;
+      const bf16 *b = (ab ? sb[1] : sa[1]) + nu * P.strip_nu[1] + ((long long)k * (2 * Ly) + sc) * P.pitch + x0;
+      l2_line(b);
+      if (x0 + 64 < P.nx) l2_line(b + 64);
+    }
+  }
+  // z strip: plane sc, rows y of the unit
+  const int Lz = P.L[2];
+  const int scz = Lz > 0 ? strip_coord(k, P.nz, Lz) : -1;
+  if (scz >= 0) {
+    for (int t = lane; t < kHT * N * 2; t += 32) {
+      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+      const int y = y0 + r;
+      if (y >= P.ny) continue;
+      const bf16 *b = (ab ? sb[2] : sa[2]) + nu * P.strip_nu[2] + ((long long)scz * P.ny + y) * P.pitch + x0;
+      l2_line(b);
+      if (x0 + 64 < P.nx) l2_line(b + 64);
+    }
+  }
+}
+
 // float density tile [2][9][132] of planes k, k+1 from the staged bf16 box;
 // cells beyond the last one along an axis take that cell's value
 template <bool EDGE>
@@ -498,10 +550,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (; u < nu_; u += gridDim.x) {
     if (us < nu_) {
       const int q = s ^ 1;
-      if (tid == 0) {
+      if (tid < 32) {
         int x, y, z;
         R.origin(us, x, y, z);
-        issue3<N, VEL>(T, smem + q * kStage, &bar[q], x, y, z, P.nl != 0);
+        if (tid == 0) issue3<N, VEL>(T, smem + q * kStage, &bar[q], x, y, z, P.nl != 0);
+        if (!R.interior(x, y, z)) prefetch_strips<N, VEL ? 1 : 2>(P, x, y, z, tid);
       }
       pending |= 1u << q;
       us += gridDim.x;
