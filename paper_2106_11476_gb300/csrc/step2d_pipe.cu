@@ -351,11 +351,22 @@ __device__ __forceinline__ void density_tile(const StepParams &P, const float *t
 template <int OP, typename Maps>
 __device__ __forceinline__ void x_strip_coef2(const StepParams &P, int nu, int i0, int j, float2 &a, float2 &b) {
   using ST = typename Maps::StripT;
+  static_assert(sizeof(ST) == 4, "the pipelined 2D kernels read float strips");
   const int L = P.L[0];
   if (!(L > 0 && (i0 < L || i0 + 1 >= P.nx - L))) return;
-  const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[0] : P.sa2[0]);
-  const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[0] : P.sb2[0]);
+  const float *sa = static_cast<const float *>(OP == 1 ? P.sa1[0] : P.sa2[0]);
+  const float *sb = static_cast<const float *>(OP == 1 ? P.sb1[0] : P.sb2[0]);
   const long long row = (long long)nu * P.strip_nu[0] + (long long)j * (2 * L);
+  // both cells on one side of the strip: one aligned pair (i0 and the high
+  // side's offset nx - 2L are even)
+  int sc0 = -1;
+  if (i0 + 1 < L) sc0 = i0;
+  else if (i0 >= P.nx - L && i0 + 1 < P.nx && ((P.nx - 2 * L) & 1) == 0) sc0 = i0 - (P.nx - 2 * L);
+  if (sc0 >= 0) {
+    a = __ldg(reinterpret_cast<const float2 *>(sa + row + sc0));
+    b = __ldg(reinterpret_cast<const float2 *>(sb + row + sc0));
+    return;
+  }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     const int x = i0 + e;
@@ -372,15 +383,51 @@ __device__ __forceinline__ void x_strip_coef2(const StepParams &P, int nu, int i
   }
 }
 
-// a, b along y at the two cells of an edge pair inside the y strip
+// a, b along y at the two cells of an edge pair inside the y strip (an
+// aligned pair: i0 even, pitch a multiple of 16)
 template <int OP, typename Maps>
 __device__ __forceinline__ void y_strip_coef2(const StepParams &P, int nu, int i0, int sc, float2 &a, float2 &b) {
-  using ST = typename Maps::StripT;
-  const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[1] : P.sa2[1]);
-  const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[1] : P.sb2[1]);
+  const float *sa = static_cast<const float *>(OP == 1 ? P.sa1[1] : P.sa2[1]);
+  const float *sb = static_cast<const float *>(OP == 1 ? P.sb1[1] : P.sb2[1]);
   const long long off = (long long)nu * P.strip_nu[1] + (long long)sc * P.pitch + i0;
-  a = make_float2(ldmap(sa, off), ldmap(sa, off + 1));
-  b = make_float2(ldb(sb, off), ldb(sb, off + 1));
+  a = __ldg(reinterpret_cast<const float2 *>(sa + off));
+  b = __ldg(reinterpret_cast<const float2 *>(sb + off));
+}
+
+// Prefetch into L2 the C-PML strip rows an edge half tile will read (warp 0,
+// when its copies are issued): otherwise they come straight from DRAM while
+// the half tile computes.  OP: 1 velocity (a1, b1), 2 pressure (a2, b2).
+__device__ __forceinline__ void l2_line(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+template <int N, int OP>
+__device__ __forceinline__ void prefetch_strips2(const StepParams &P, int x0, int y0, int lane) {
+  if (N == 0) return;
+  const float *sa[2], *sb[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    sa[q] = static_cast<const float *>(OP == 1 ? P.sa1[q] : P.sa2[q]);
+    sb[q] = static_cast<const float *>(OP == 1 ? P.sb1[q] : P.sb2[q]);
+  }
+  const int Lx = P.L[0];
+  if (Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
+    for (int t = lane; t < kHT * N * 2; t += 32) {
+      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+      const int y = y0 + r;
+      if (y >= P.ny) continue;
+      const float *b = (ab ? sb[0] : sa[0]) + nu * P.strip_nu[0] + (long long)y * (2 * Lx);
+      for (int o = 0; o < 2 * Lx; o += 32) l2_line(b + o);  // 128-byte lines
+    }
+  }
+  const int Ly = P.L[1];
+  if (Ly > 0) {
+    for (int t = lane; t < kHT * N * 2; t += 32) {
+      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+      const int y = y0 + r;
+      const int sc = y < P.ny ? strip_coord(y, P.ny, Ly) : -1;
+      if (sc < 0) continue;
+      const float *b = (ab ? sb[1] : sa[1]) + nu * P.strip_nu[1] + (long long)sc * P.pitch + x0;
+      for (int o = 0; o < kTX && x0 + o < P.nx; o += 32) l2_line(b + o);
+    }
+  }
 }
 
 template <int N, typename Maps, bool EDGE>
@@ -592,11 +639,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (; h < nh; h += gridDim.x) {
     if (hs < nh) {
       const int q = (s + kS - 1) % kS;  // computed in the previous iteration
-      if (tid == 0) {
+      if (tid < 32) {
         int xq, yq;
         R.half_origin(hs, xq, yq);
-        bulk_wait_read<0>();  // its results have left for HBM
-        issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
+        if (tid == 0) {
+          bulk_wait_read<0>();  // its results have left for HBM
+          issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
+        }
+        if (!R.interior(xq, yq)) prefetch_strips2<N, VEL ? 1 : 2>(P, xq, yq, tid);
       }
       pending |= 1u << q;
       hs += gridDim.x;
@@ -680,10 +730,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (; h < h_end; ++h) {
     if (hs < h_end) {
       const int q = (s + kS - 1) % kS;
-      if (tid == 0) {
+      if (tid < 32) {
         const int4 e = units[hs];
-        bulk_wait_read<0>();
-        issue_stage<N, Maps, VEL>(Ps[e.x], Ts[e.x], smem + q * kStage, &bar[q], e.y, e.z);
+        if (tid == 0) {
+          bulk_wait_read<0>();
+          issue_stage<N, Maps, VEL>(Ps[e.x], Ts[e.x], smem + q * kStage, &bar[q], e.y, e.z);
+        }
+        // (the parameters of the context being computed are in shared memory)
+        if (!e.w && e.x == cur) prefetch_strips2<N, VEL ? 1 : 2>(sP, e.y, e.z, tid);
       }
       pending |= 1u << q;
       ++hs;

@@ -190,6 +190,18 @@ __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int 
   if (Q == 0) {
     if (!(i0 < L || i0 + 1 >= P.nx - L)) return;
     const long long row = (long long)nu * P.strip_nu[0] + ((long long)k * P.ny + j) * (2 * L);
+    // both cells on one side of the strip: one aligned bf16 pair (i0 and
+    // the high side's offset nx - 2L are even)
+    int sc0 = -1;
+    if (i0 + 1 < L) sc0 = i0;
+    else if (i0 >= P.nx - L && i0 + 1 < P.nx && ((P.nx - 2 * L) & 1) == 0) sc0 = i0 - (P.nx - 2 * L);
+    if (sc0 >= 0) {
+      const float2 va = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(sa + row + sc0));
+      const float2 vb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(sb + row + sc0));
+      a = va;
+      b = make_float2(1.f - vb.x, 1.f - vb.y);
+      return;
+    }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int x = i0 + e;
@@ -206,8 +218,11 @@ __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int 
     if (sc < 0) return;
     const long long off = Q == 1 ? (long long)nu * P.strip_nu[1] + ((long long)k * (2 * L) + sc) * P.pitch + i0
                                  : (long long)nu * P.strip_nu[2] + ((long long)sc * P.ny + j) * P.pitch + i0;
-    a = make_float2(ldmap(sa, off), ldmap(sa, off + 1));
-    b = make_float2(ldb(sb, off), ldb(sb, off + 1));
+    // i0 even, pitch a multiple of 16: an aligned bf16 pair
+    const float2 va = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(sa + off));
+    const float2 vb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(sb + off));
+    a = va;
+    b = make_float2(1.f - vb.x, 1.f - vb.y);
   }
 }
 
