@@ -322,27 +322,31 @@ __device__ __forceinline__ float2 look2(const float *tab, int f, uchar2 t) {
   return make_float2(r[t.x], r[t.y]);
 }
 
-// Density tile rows y0 .. y0+kHT, columns x0 .. x0+kTX+3.  Cells beyond the
-// last one along an axis take that cell's value (rho_coord of the tile path):
-// dense maps fix the staged tile in place (the entries inside the grid are
-// the sources); the index form gathers the tile through the table from the
-// staged index (zero outside the grid, hence the clamp).
+// Densities at the faces of a pair, read where the thread needs them: cells
+// (lx, ly), (lx + 1, ly), (lx + 2, ly), (lx, ly + 1), (lx + 1, ly + 1) of the
+// half tile.  Cells beyond the last one along an axis take that cell's value
+// (rho_coord of the tile path).  Dense maps read the staged density box; the
+// index form looks the staged index up in the table.
+struct FaceRho {
+  float r0, r1, r2, u0, u1;  // row ly: lx .. lx+2; row ly+1: lx, lx+1
+};
 template <typename Maps, bool EDGE>
-__device__ __forceinline__ void density_tile(const StepParams &P, const float *tab, float *sr,
-                                             const unsigned char *si, int x0, int y0, int tid) {
-  for (int t = tid; t < (kHT + 1) * kRWp; t += kThreads) {
-    const int r = t / kRWp, cc = t % kRWp;
-    int sxi = cc, syi = r;
-    if (EDGE) {
-      if (x0 + cc >= P.nx) sxi = P.nx - 1 - x0;
-      if (y0 + r >= P.ny) syi = P.ny - 1 - y0;
-    }
-    if constexpr (IsIdx<Maps>::value) {
-      sr[t] = tab[kTabRho * kTissues + si[syi * kIW + sxi]];
-    } else {
-      if (sxi != cc || syi != r) sr[t] = sr[syi * kRWp + sxi];
-    }
+__device__ __forceinline__ FaceRho face_rho(const StepParams &P, const float *tab, const float *sr,
+                                            const unsigned char *si, int x0, int y0, int lx, int ly) {
+  int c0 = lx, c1 = lx + 1, c2 = lx + 2, r0 = ly, r1 = ly + 1;
+  if (EDGE) {
+    const int mx = P.nx - 1 - x0, my = P.ny - 1 - y0;  // last cell inside, tile coordinates
+    c0 = min(c0, mx);
+    c1 = min(c1, mx);
+    c2 = min(c2, mx);
+    r0 = min(r0, my);
+    r1 = min(r1, my);
   }
+  auto at = [&](int r, int cc) -> float {
+    if constexpr (IsIdx<Maps>::value) return tab[kTabRho * kTissues + si[r * kIW + cc]];
+    else return sr[r * kRWp + cc];
+  };
+  return FaceRho{at(r0, c0), at(r0, c1), at(r0, c2), at(r1, c0), at(r1, c1)};
 }
 
 // a, b of mechanism nu along x at the two cells of an edge pair: from the x
@@ -400,32 +404,33 @@ __device__ __forceinline__ void y_strip_coef2(const StepParams &P, int nu, int i
 __device__ __forceinline__ void l2_line(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 template <int N, int OP>
 __device__ __forceinline__ void prefetch_strips2(const StepParams &P, int x0, int y0, int lane) {
-  if (N == 0) return;
-  const float *sa[2], *sb[2];
+  if constexpr (N > 0) {
+    const float *sa[2], *sb[2];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    sa[q] = static_cast<const float *>(OP == 1 ? P.sa1[q] : P.sa2[q]);
-    sb[q] = static_cast<const float *>(OP == 1 ? P.sb1[q] : P.sb2[q]);
-  }
-  const int Lx = P.L[0];
-  if (Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
-    for (int t = lane; t < kHT * N * 2; t += 32) {
-      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
-      const int y = y0 + r;
-      if (y >= P.ny) continue;
-      const float *b = (ab ? sb[0] : sa[0]) + nu * P.strip_nu[0] + (long long)y * (2 * Lx);
-      for (int o = 0; o < 2 * Lx; o += 32) l2_line(b + o);  // 128-byte lines
+    for (int q = 0; q < 2; ++q) {
+      sa[q] = static_cast<const float *>(OP == 1 ? P.sa1[q] : P.sa2[q]);
+      sb[q] = static_cast<const float *>(OP == 1 ? P.sb1[q] : P.sb2[q]);
     }
-  }
-  const int Ly = P.L[1];
-  if (Ly > 0) {
-    for (int t = lane; t < kHT * N * 2; t += 32) {
-      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
-      const int y = y0 + r;
-      const int sc = y < P.ny ? strip_coord(y, P.ny, Ly) : -1;
-      if (sc < 0) continue;
-      const float *b = (ab ? sb[1] : sa[1]) + nu * P.strip_nu[1] + (long long)sc * P.pitch + x0;
-      for (int o = 0; o < kTX && x0 + o < P.nx; o += 32) l2_line(b + o);
+    const int Lx = P.L[0];
+    if (Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
+      for (int t = lane; t < kHT * N * 2; t += 32) {
+        const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+        const int y = y0 + r;
+        if (y >= P.ny) continue;
+        const float *b = (ab ? sb[0] : sa[0]) + nu * P.strip_nu[0] + (long long)y * (2 * Lx);
+        for (int o = 0; o < 2 * Lx; o += 32) l2_line(b + o);  // 128-byte lines
+      }
+    }
+    const int Ly = P.L[1];
+    if (Ly > 0) {
+      for (int t = lane; t < kHT * N * 2; t += 32) {
+        const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+        const int y = y0 + r;
+        const int sc = y < P.ny ? strip_coord(y, P.ny, Ly) : -1;
+        if (sc < 0) continue;
+        const float *b = (ab ? sb[1] : sa[1]) + nu * P.strip_nu[1] + (long long)sc * P.pitch + x0;
+        for (int o = 0; o < kTX && x0 + o < P.nx; o += 32) l2_line(b + o);
+      }
     }
   }
 }
@@ -435,13 +440,9 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
                                             int tid) {
   using S = VelStage<N, Maps>;
   const float *sp = st;
-  float *sr = st + S::kP;
+  const float *sr = st + S::kP;
   const float *ss = sr + S::kR;
   const unsigned char *si = reinterpret_cast<const unsigned char *>(ss + S::kS);
-  if (EDGE || S::kIdx) {
-    density_tile<Maps, EDGE>(P, tab, sr, si, x0, y0, tid);
-    __syncthreads();
-  }
   const int t2 = tid & 63, ly = tid >> 6, lx = 2 * t2;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
@@ -499,14 +500,11 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
     put2<Maps, EDGE>(own, 2 + nu, P.psi1[0], nu * Sn + c, nx_, i0, P.nx);
     put2<Maps, EDGE>(own, 2 + N + nu, P.psi1[1], nu * Sn + c, ny_, i0, P.nx);
   }
-  const float *r = sr + ly * kRWp + lx;
-  const float2 r0 = sld2(r);
-  const float r2 = r[2];
-  const float2 ru = sld2(r + kRWp);
-  vx.x -= P.two_dt / (r0.x + r0.y) * Sx.x;
-  vx.y -= P.two_dt / (r0.y + r2) * Sx.y;
-  vy.x -= P.two_dt / (r0.x + ru.x) * Sy.x;
-  vy.y -= P.two_dt / (r0.y + ru.y) * Sy.y;
+  const FaceRho fr = face_rho<Maps, EDGE>(P, tab, sr, si, x0, y0, lx, ly);
+  vx.x -= P.two_dt / (fr.r0 + fr.r1) * Sx.x;
+  vx.y -= P.two_dt / (fr.r1 + fr.r2) * Sx.y;
+  vy.x -= P.two_dt / (fr.r0 + fr.u0) * Sy.x;
+  vy.y -= P.two_dt / (fr.r1 + fr.u1) * Sy.y;
   put2<Maps, EDGE>(own, 0, P.v[0], c, vx, i0, P.nx);
   put2<Maps, EDGE>(own, 1, P.v[1], c, vy, i0, P.nx);
 }

@@ -30,7 +30,6 @@ namespace {
 constexpr int kHT = 8;            // rows of a unit
 constexpr int kCW = kTX + 8;      // operand halo columns x0-4 .. x0+TX+3
 constexpr int kRWb = kTX + 8;     // staged bf16 density columns x0 .. x0+TX+7 (16-byte rows)
-constexpr int kRWf = kTX + 4;     // float density tile columns x0 .. x0+TX+3
 constexpr int kArr = kHT * kTX;   // elements of one array per unit
 
 using bf16 = __nv_bfloat16;
@@ -77,14 +76,11 @@ struct Prs3 {
       4u * (kHT * kCW + (kHT + 7) * kTX + kCol + kP + kPsi) + 2u * (2 * kArr + 2 * N * kArr);
 };
 
-// density tile (float) built from the staged bf16 planes: [2][9][132]
-constexpr int kRhoTile = 2 * (kHT + 1) * kRWf;
 
 template <int N, bool VEL>
 struct Ring3 {
   static constexpr int kStage = VEL ? Vel3<N>::kFloats : Prs3<N>::kFloats;
-  static constexpr int kExtra = VEL ? kRhoTile : 0;
-  static constexpr size_t kBytes = sizeof(float) * (2 * (size_t)kStage + kExtra) + 128;
+  static constexpr size_t kBytes = sizeof(float) * (2 * (size_t)kStage) + 128;
 };
 
 // Work: units of 128 x 8 cells per plane, x fastest.
@@ -232,76 +228,81 @@ __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int 
 __device__ __forceinline__ void l2_line(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 template <int N, int OP>
 __device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int y0, int k, int lane) {
-  if (N == 0) return;
-  const bf16 *sa[3], *sb[3];
+  if constexpr (N > 0) {
+    const bf16 *sa[3], *sb[3];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    sa[q] = static_cast<const bf16 *>(OP == 1 ? P.sa1[q] : P.sa2[q]);
-    sb[q] = static_cast<const bf16 *>(OP == 1 ? P.sb1[q] : P.sb2[q]);
-  }
-  // x strip: rows (k, y) of 2L values, for units reaching into it
-  const int Lx = P.L[0];
-  if (Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
-    for (int t = lane; t < kHT * N * 2; t += 32) {
-      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
-      const int y = y0 + r;
-      if (y >= P.ny) continue;
-      const bf16 *b = (ab ? sb[0] : sa[0]) + nu * P.strip_nu[0] + ((long long)k * P.ny + y) * (2 * Lx);
-      for (int o = 0; o < 2 * Lx; o += 64) l2_line(b + o);  // 128-byte lines
+    for (int q = 0; q < 3; ++q) {
+      sa[q] = static_cast<const bf16 *>(OP == 1 ? P.sa1[q] : P.sa2[q]);
+      sb[q] = static_cast<const bf16 *>(OP == 1 ? P.sb1[q] : P.sb2[q]);
     }
-  }
-  // y strip: rows (k, sc) of the unit's 128 columns
-  const int Ly = P.L[1];
-  if (Ly > 0) {
-    for (int t = lane; t < kHT * N * 2; t += 32) {
-      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
-      const int y = y0 + r;
-      const int sc = y < P.ny ? strip_coord(y, P.ny, Ly) : -1;
-      if (sc < 0) continue;
-      const bf16 *b = (ab ? sb[1] : sa[1]) + nu * P.strip_nu[1] + ((long long)k * (2 * Ly) + sc) * P.pitch + x0;
-      l2_line(b);
-      if (x0 + 64 < P.nx) l2_line(b + 64);
+    // x strip: rows (k, y) of 2L values, for units reaching into it
+    const int Lx = P.L[0];
+    if (Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
+      for (int t = lane; t < kHT * N * 2; t += 32) {
+        const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+        const int y = y0 + r;
+        if (y >= P.ny) continue;
+        const bf16 *b = (ab ? sb[0] : sa[0]) + nu * P.strip_nu[0] + ((long long)k * P.ny + y) * (2 * Lx);
+        for (int o = 0; o < 2 * Lx; o += 64) l2_line(b + o);  // 128-byte lines
+      }
     }
-  }
-  // z strip: plane sc, rows y of the unit
-  const int Lz = P.L[2];
-  const int scz = Lz > 0 ? strip_coord(k, P.nz, Lz) : -1;
-  if (scz >= 0) {
-    for (int t = lane; t < kHT * N * 2; t += 32) {
-      const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
-      const int y = y0 + r;
-      if (y >= P.ny) continue;
-      const bf16 *b = (ab ? sb[2] : sa[2]) + nu * P.strip_nu[2] + ((long long)scz * P.ny + y) * P.pitch + x0;
-      l2_line(b);
-      if (x0 + 64 < P.nx) l2_line(b + 64);
+    // y strip: rows (k, sc) of the unit's 128 columns
+    const int Ly = P.L[1];
+    if (Ly > 0) {
+      for (int t = lane; t < kHT * N * 2; t += 32) {
+        const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+        const int y = y0 + r;
+        const int sc = y < P.ny ? strip_coord(y, P.ny, Ly) : -1;
+        if (sc < 0) continue;
+        const bf16 *b = (ab ? sb[1] : sa[1]) + nu * P.strip_nu[1] + ((long long)k * (2 * Ly) + sc) * P.pitch + x0;
+        l2_line(b);
+        if (x0 + 64 < P.nx) l2_line(b + 64);
+      }
+    }
+    // z strip: plane sc, rows y of the unit
+    const int Lz = P.L[2];
+    const int scz = Lz > 0 ? strip_coord(k, P.nz, Lz) : -1;
+    if (scz >= 0) {
+      for (int t = lane; t < kHT * N * 2; t += 32) {
+        const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
+        const int y = y0 + r;
+        if (y >= P.ny) continue;
+        const bf16 *b = (ab ? sb[2] : sa[2]) + nu * P.strip_nu[2] + ((long long)scz * P.ny + y) * P.pitch + x0;
+        l2_line(b);
+        if (x0 + 64 < P.nx) l2_line(b + 64);
+      }
     }
   }
 }
 
-// float density tile [2][9][132] of planes k, k+1 from the staged bf16 box;
-// cells beyond the last one along an axis take that cell's value
+// Densities at the faces of a pair, read from the staged bf16 box [2][9][136]
+// (planes k, k + 1) where the thread needs them: plane k row ly at lx .. lx+2,
+// row ly+1 at lx, lx+1; plane k+1 row ly at lx, lx+1.  Cells beyond the last
+// one along an axis take that cell's value (rho_coord of the tile kernels).
+struct FaceRho3 {
+  float r0, r1, r2, u0, u1, z0, z1;
+};
 template <bool EDGE>
-__device__ __forceinline__ void density3(const StepParams &P, const bf16 *rb, float *rt, int x0, int y0, int k,
-                                         int tid) {
-  for (int t = tid; t < kRhoTile; t += kThreads) {
-    const int pz = t / ((kHT + 1) * kRWf), rem = t % ((kHT + 1) * kRWf);
-    const int r = rem / kRWf, cc = rem % kRWf;
-    int sx = cc, sy = r, sz = pz;
-    if (EDGE) {
-      if (x0 + cc >= P.nx) sx = P.nx - 1 - x0;
-      if (y0 + r >= P.ny) sy = P.ny - 1 - y0;
-      if (k + pz >= P.nz) sz = P.nz - 1 - k;
-    }
-    rt[t] = __bfloat162float(rb[(sz * (kHT + 1) + sy) * kRWb + sx]);
+__device__ __forceinline__ FaceRho3 face_rho3(const StepParams &P, const bf16 *rb, int x0, int y0, int k, int lx,
+                                              int ly) {
+  int c0 = lx, c1 = lx + 1, c2 = lx + 2, r0 = ly, r1 = ly + 1, pz = 1;
+  if (EDGE) {
+    const int mx = P.nx - 1 - x0, my = P.ny - 1 - y0;
+    c0 = min(c0, mx);
+    c1 = min(c1, mx);
+    c2 = min(c2, mx);
+    r0 = min(r0, my);
+    r1 = min(r1, my);
+    if (k + 1 >= P.nz) pz = 0;
   }
+  auto at = [&](int z, int r, int cc) { return __bfloat162float(rb[(z * (kHT + 1) + r) * kRWb + cc]); };
+  return FaceRho3{at(0, r0, c0), at(0, r0, c1), at(0, r0, c2), at(0, r1, c0), at(0, r1, c1),
+                  at(pz, r0, c0), at(pz, r0, c1)};
 }
 
 template <int N, bool EDGE>
-__device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, float *rt, int x0, int y0, int k,
-                                             int tid) {
+__device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, int x0, int y0, int k, int tid) {
   using S = Vel3<N>;
-  density3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), rt, x0, y0, k, tid);
-  __syncthreads();
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
@@ -399,17 +400,13 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, flo
     st_state2(P.psi1[1], nu * Sn + c, n1);
     st_state2(P.psi1[2], nu * Sn + c, n2);
   }
-  const float *r = rt + ly * kRWf + lx;
-  const float2 r0 = sld2(r);
-  const float r2 = r[2];
-  const float2 ru = sld2(r + kRWf);
-  const float2 rz = sld2(r + (kHT + 1) * kRWf);
-  const float rr[3] = {r0.x, r0.y, r2};
+  const FaceRho3 f = face_rho3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), x0, y0, k, lx, ly);
+  const float rr[3] = {f.r0, f.r1, f.r2}, ru[2] = {f.u0, f.u1}, rz[2] = {f.z0, f.z1};
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     el2(v0, e) -= P.two_dt / (rr[e] + rr[e + 1]) * el2(S0, e);
-    el2(v1, e) -= P.two_dt / (rr[e] + el2(ru, e)) * el2(S1, e);
-    el2(v2, e) -= P.two_dt / (rr[e] + el2(rz, e)) * el2(S2, e);
+    el2(v1, e) -= P.two_dt / (rr[e] + ru[e]) * el2(S1, e);
+    el2(v2, e) -= P.two_dt / (rr[e] + rz[e]) * el2(S2, e);
   }
   if (EDGE) {
     v0 = mask_pad2(v0, i0, P.nx);
@@ -540,7 +537,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int ok;
   float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  float *rt = smem + 2 * kStage;  // float density tile (velocity)
   const int tid = threadIdx.y * 32 + threadIdx.x;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -589,10 +585,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     R.origin(u, x0, y0, k);
     float *cur = smem + s * kStage;
     if (R.interior(x0, y0, k)) {
-      if (VEL) vel3_compute<N, false>(P, cur, rt, x0, y0, k, tid);
+      if (VEL) vel3_compute<N, false>(P, cur, x0, y0, k, tid);
       else prs3_compute<N, false>(P, cur, x0, y0, k, tid);
     } else {
-      if (VEL) vel3_compute<N, true>(P, cur, rt, x0, y0, k, tid);
+      if (VEL) vel3_compute<N, true>(P, cur, x0, y0, k, tid);
       else prs3_compute<N, true>(P, cur, x0, y0, k, tid);
     }
     __syncthreads();
