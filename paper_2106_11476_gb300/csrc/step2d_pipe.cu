@@ -633,113 +633,60 @@ __global__ void __launch_bounds__(kThreads, 1)
     pending |= 1u << q;
   }
   int s = 0;
-  if constexpr (kS >= 3) {
-    // One barrier per half tile: after the wait for stage s it also marks
-    // the previous half tile computed, so its stage is refilled (and, with
-    // TMA stores, its results sent) right after it.
-    int xp = -1, yp = -1;  // previous half tile of this block
+  // One barrier per half tile: after the wait for stage s it also marks
+  // the previous half tile computed, so its stage is refilled (and, with
+  // TMA stores, its results sent) right after it.
+  int xp = -1, yp = -1;  // previous half tile of this block
 #pragma unroll 1
-    for (; h < nh; h += gridDim.x) {
-      if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
-      __syncthreads();
-      if (!ok) {
-        if (tid == 0) {
-          report_status(P.status, kStatusWaitTimeout);
-          for (int q = 0; q < kS; ++q)
-            if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
-          bulk_wait_all();
-        }
-        return;
+  for (; h < nh; h += gridDim.x) {
+    if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    __syncthreads();
+    if (!ok) {
+      if (tid == 0) {
+        report_status(P.status, kStatusWaitTimeout);
+        for (int q = 0; q < kS; ++q)
+          if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
+        bulk_wait_all();
       }
-      phase ^= 1u << s;
-      pending &= ~(1u << s);
-      const int q = (s + kS - 1) % kS;  // the previous half tile's stage, free now
-      if constexpr (TmaStore<Maps>::value) {
-        if (tid == 0 && xp >= 0) store_stage<N, Maps, VEL>(T, smem + q * kStage, xp, yp);
-      }
-      if (hs < nh) {
-        if (tid < 32) {
-          int xq, yq;
-          R.half_origin(hs, xq, yq);
-          if (tid == 0) {
-            bulk_wait_read<0>();
-            issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
-          }
-          if (!R.interior(xq, yq)) prefetch_strips2<N, VEL ? 1 : 2>(P, xq, yq, tid);
-        }
-        pending |= 1u << q;
-        hs += gridDim.x;
-      }
-      int x0, y0;
-      R.half_origin(h, x0, y0);
-      float *cur = smem + s * kStage;
-      if (R.interior(x0, y0)) {
-        if (VEL) vel_compute<N, Maps, false>(P, tab, cur, x0, y0, tid);
-        else prs_compute<N, Maps, false>(P, tab, cur, x0, y0, tid);
-      } else {
-        if (VEL) vel_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
-        else prs_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
-      }
-      if constexpr (TmaStore<Maps>::value) fence_proxy_async_smem();
-      xp = x0;
-      yp = y0;
-      s = (s + 1) % kS;
+      return;
     }
+    phase ^= 1u << s;
+    pending &= ~(1u << s);
+    const int q = (s + kS - 1) % kS;  // the previous half tile's stage, free now
     if constexpr (TmaStore<Maps>::value) {
-      __syncthreads();
-      if (tid == 0 && xp >= 0) store_stage<N, Maps, VEL>(T, smem + ((s + kS - 1) % kS) * kStage, xp, yp);
+      if (tid == 0 && xp >= 0) store_stage<N, Maps, VEL>(T, smem + q * kStage, xp, yp);
     }
-  } else {
-#pragma unroll 1
-    for (; h < nh; h += gridDim.x) {
-      if (hs < nh) {
-        const int q = (s + kS - 1) % kS;  // computed in the previous iteration
-        if (tid < 32) {
-          int xq, yq;
-          R.half_origin(hs, xq, yq);
-          if (tid == 0) {
-            bulk_wait_read<0>();  // its results have left for HBM
-            issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
-          }
-          if (!R.interior(xq, yq)) prefetch_strips2<N, VEL ? 1 : 2>(P, xq, yq, tid);
-        }
-        pending |= 1u << q;
-        hs += gridDim.x;
-      }
-      if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
-      __syncthreads();
-      if (!ok) {
-        // a copy never landed: report, let the other stages' copies finish
-        // (bounded), and leave
+    if (hs < nh) {
+      if (tid < 32) {
+        int xq, yq;
+        R.half_origin(hs, xq, yq);
         if (tid == 0) {
-          report_status(P.status, kStatusWaitTimeout);
-          for (int q = 0; q < kS; ++q)
-            if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
-          bulk_wait_all();
+          bulk_wait_read<0>();
+          issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
         }
-        return;
+        if (!R.interior(xq, yq)) prefetch_strips2<N, VEL ? 1 : 2>(P, xq, yq, tid);
       }
-      phase ^= 1u << s;
-      pending &= ~(1u << s);
-      int x0, y0;
-      R.half_origin(h, x0, y0);
-      float *cur = smem + s * kStage;
-      if (R.interior(x0, y0)) {
-        if (VEL) vel_compute<N, Maps, false>(P, tab, cur, x0, y0, tid);
-        else prs_compute<N, Maps, false>(P, tab, cur, x0, y0, tid);
-      } else {
-        if (VEL) vel_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
-        else prs_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
-      }
-      if constexpr (TmaStore<Maps>::value) {
-        fence_proxy_async_smem();  // this thread's results, visible to the store
-        __syncthreads();
-        if (tid == 0) store_stage<N, Maps, VEL>(T, cur, x0, y0);
-      } else {
-        __syncthreads();
-      }
-      s = (s + 1) % kS;
+      pending |= 1u << q;
+      hs += gridDim.x;
     }
+    int x0, y0;
+    R.half_origin(h, x0, y0);
+    float *cur = smem + s * kStage;
+    if (R.interior(x0, y0)) {
+      if (VEL) vel_compute<N, Maps, false>(P, tab, cur, x0, y0, tid);
+      else prs_compute<N, Maps, false>(P, tab, cur, x0, y0, tid);
+    } else {
+      if (VEL) vel_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
+      else prs_compute<N, Maps, true>(P, tab, cur, x0, y0, tid);
+    }
+    if constexpr (TmaStore<Maps>::value) fence_proxy_async_smem();
+    xp = x0;
+    yp = y0;
+    s = (s + 1) % kS;
+  }
+  if constexpr (TmaStore<Maps>::value) {
+    __syncthreads();
+    if (tid == 0 && xp >= 0) store_stage<N, Maps, VEL>(T, smem + ((s + kS - 1) % kS) * kStage, xp, yp);
   }
   if (tid == 0) bulk_wait_all();
 }
@@ -782,126 +729,66 @@ __global__ void __launch_bounds__(kThreads, 1)
     pending |= 1u << q;
   }
   int s = 0, cur = -1;
-  if constexpr (kS >= 3) {
-    // one barrier per unit (see pipe2d_kernel); a context change adds one
-    int4 prev = make_int4(-1, 0, 0, 0);
+  // one barrier per unit (see pipe2d_kernel); a context change adds one
+  int4 prev = make_int4(-1, 0, 0, 0);
 #pragma unroll 1
-    for (; h < h_end; ++h) {
-      if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
-      __syncthreads();
-      if (!ok) {
-        if (tid == 0) {
-          report_status(Ps[units[h].x].status, kStatusWaitTimeout);
-          for (int q = 0; q < kS; ++q)
-            if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
-          bulk_wait_all();
-        }
-        return;
+  for (; h < h_end; ++h) {
+    if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    __syncthreads();
+    if (!ok) {
+      if (tid == 0) {
+        report_status(Ps[units[h].x].status, kStatusWaitTimeout);
+        for (int q = 0; q < kS; ++q)
+          if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
+        bulk_wait_all();
       }
-      phase ^= 1u << s;
-      pending &= ~(1u << s);
-      const int q = (s + kS - 1) % kS;  // the previous unit's stage, free now
-      if constexpr (TmaStore<Maps>::value) {
-        if (tid == 0 && prev.x >= 0) store_stage<N, Maps, VEL>(Ts[prev.x], smem + q * kStage, prev.y, prev.z);
-      }
-      const int4 e = units[h];
-      if (e.x != cur) {
-        // new context: parameters (and index table) into shared memory
-        const int *src = reinterpret_cast<const int *>(Ps + e.x);
-        int *dst = reinterpret_cast<int *>(&sP);
-        for (int w = tid; w < (int)(sizeof(StepParams) / 4); w += kThreads) dst[w] = __ldg(src + w);
-        __syncthreads();
-        stage_table<Maps>(sP, tab, tid);
-        __syncthreads();
-        cur = e.x;
-      }
-      if (hs < h_end) {
-        if (tid < 32) {
-          const int4 en = units[hs];
-          if (tid == 0) {
-            bulk_wait_read<0>();
-            issue_stage<N, Maps, VEL>(Ps[en.x], Ts[en.x], smem + q * kStage, &bar[q], en.y, en.z);
-          }
-          if (!en.w && en.x == cur) prefetch_strips2<N, VEL ? 1 : 2>(sP, en.y, en.z, tid);
-        }
-        pending |= 1u << q;
-        ++hs;
-      }
-      float *stp = smem + s * kStage;
-      if (e.w) {
-        if (VEL) vel_compute<N, Maps, false>(sP, tab, stp, e.y, e.z, tid);
-        else prs_compute<N, Maps, false>(sP, tab, stp, e.y, e.z, tid);
-      } else {
-        if (VEL) vel_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
-        else prs_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
-      }
-      if constexpr (TmaStore<Maps>::value) fence_proxy_async_smem();
-      prev = e;
-      s = (s + 1) % kS;
+      return;
     }
+    phase ^= 1u << s;
+    pending &= ~(1u << s);
+    const int q = (s + kS - 1) % kS;  // the previous unit's stage, free now
     if constexpr (TmaStore<Maps>::value) {
-      __syncthreads();
-      if (tid == 0 && prev.x >= 0)
-        store_stage<N, Maps, VEL>(Ts[prev.x], smem + ((s + kS - 1) % kS) * kStage, prev.y, prev.z);
+      if (tid == 0 && prev.x >= 0) store_stage<N, Maps, VEL>(Ts[prev.x], smem + q * kStage, prev.y, prev.z);
     }
-  } else {
-#pragma unroll 1
-    for (; h < h_end; ++h) {
-      if (hs < h_end) {
-        const int q = (s + kS - 1) % kS;
-        if (tid < 32) {
-          const int4 e = units[hs];
-          if (tid == 0) {
-            bulk_wait_read<0>();
-            issue_stage<N, Maps, VEL>(Ps[e.x], Ts[e.x], smem + q * kStage, &bar[q], e.y, e.z);
-          }
-          // (the parameters of the context being computed are in shared memory)
-          if (!e.w && e.x == cur) prefetch_strips2<N, VEL ? 1 : 2>(sP, e.y, e.z, tid);
-        }
-        pending |= 1u << q;
-        ++hs;
-      }
-      const int4 e = units[h];
-      if (e.x != cur) {
-        // new context: parameters (and index table) into shared memory; the
-        // previous unit's compute finished at the last barrier
-        const int *src = reinterpret_cast<const int *>(Ps + e.x);
-        int *dst = reinterpret_cast<int *>(&sP);
-        for (int w = tid; w < (int)(sizeof(StepParams) / 4); w += kThreads) dst[w] = __ldg(src + w);
-        __syncthreads();
-        stage_table<Maps>(sP, tab, tid);
-        cur = e.x;
-      }
-      if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    const int4 e = units[h];
+    if (e.x != cur) {
+      // new context: parameters (and index table) into shared memory
+      const int *src = reinterpret_cast<const int *>(Ps + e.x);
+      int *dst = reinterpret_cast<int *>(&sP);
+      for (int w = tid; w < (int)(sizeof(StepParams) / 4); w += kThreads) dst[w] = __ldg(src + w);
       __syncthreads();
-      if (!ok) {
+      stage_table<Maps>(sP, tab, tid);
+      __syncthreads();
+      cur = e.x;
+    }
+    if (hs < h_end) {
+      if (tid < 32) {
+        const int4 en = units[hs];
         if (tid == 0) {
-          report_status(sP.status, kStatusWaitTimeout);
-          for (int q = 0; q < kS; ++q)
-            if (q != s && ((pending >> q) & 1u)) mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
-          bulk_wait_all();
+          bulk_wait_read<0>();
+          issue_stage<N, Maps, VEL>(Ps[en.x], Ts[en.x], smem + q * kStage, &bar[q], en.y, en.z);
         }
-        return;
+        if (!en.w && en.x == cur) prefetch_strips2<N, VEL ? 1 : 2>(sP, en.y, en.z, tid);
       }
-      phase ^= 1u << s;
-      pending &= ~(1u << s);
-      float *stp = smem + s * kStage;
-      if (e.w) {
-        if (VEL) vel_compute<N, Maps, false>(sP, tab, stp, e.y, e.z, tid);
-        else prs_compute<N, Maps, false>(sP, tab, stp, e.y, e.z, tid);
-      } else {
-        if (VEL) vel_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
-        else prs_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
-      }
-      if constexpr (TmaStore<Maps>::value) {
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) store_stage<N, Maps, VEL>(Ts[e.x], stp, e.y, e.z);
-      } else {
-        __syncthreads();
-      }
-      s = (s + 1) % kS;
+      pending |= 1u << q;
+      ++hs;
     }
+    float *stp = smem + s * kStage;
+    if (e.w) {
+      if (VEL) vel_compute<N, Maps, false>(sP, tab, stp, e.y, e.z, tid);
+      else prs_compute<N, Maps, false>(sP, tab, stp, e.y, e.z, tid);
+    } else {
+      if (VEL) vel_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
+      else prs_compute<N, Maps, true>(sP, tab, stp, e.y, e.z, tid);
+    }
+    if constexpr (TmaStore<Maps>::value) fence_proxy_async_smem();
+    prev = e;
+    s = (s + 1) % kS;
+  }
+  if constexpr (TmaStore<Maps>::value) {
+    __syncthreads();
+    if (tid == 0 && prev.x >= 0)
+      store_stage<N, Maps, VEL>(Ts[prev.x], smem + ((s + kS - 1) % kS) * kStage, prev.y, prev.z);
   }
   if (tid == 0) bulk_wait_all();
 }

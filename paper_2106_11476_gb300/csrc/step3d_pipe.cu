@@ -559,17 +559,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   int s = 0;
 #pragma unroll 1
   for (; u < nu_; u += gridDim.x) {
-    if (us < nu_) {
-      const int q = s ^ 1;
-      if (tid < 32) {
-        int x, y, z;
-        R.origin(us, x, y, z);
-        if (tid == 0) issue3<N, VEL>(T, smem + q * kStage, &bar[q], x, y, z, P.nl != 0);
-        if (!R.interior(x, y, z)) prefetch_strips<N, VEL ? 1 : 2>(P, x, y, z, tid);
-      }
-      pending |= 1u << q;
-      us += gridDim.x;
-    }
     if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
     __syncthreads();
     if (!ok) {
@@ -581,6 +570,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     phase ^= 1u << s;
     pending &= ~(1u << s);
+    if (us < nu_) {
+      const int q = s ^ 1;
+      if (tid < 32) {
+        int x, y, z;
+        R.origin(us, x, y, z);
+        if (tid == 0) issue3<N, VEL>(T, smem + q * kStage, &bar[q], x, y, z, P.nl != 0);
+        if (!R.interior(x, y, z)) prefetch_strips<N, VEL ? 1 : 2>(P, x, y, z, tid);
+      }
+      pending |= 1u << q;
+      us += gridDim.x;
+    }
     int x0, y0, k;
     R.origin(u, x0, y0, k);
     float *cur = smem + s * kStage;
@@ -591,7 +591,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (VEL) vel3_compute<N, true>(P, cur, x0, y0, k, tid);
       else prs3_compute<N, true>(P, cur, x0, y0, k, tid);
     }
-    __syncthreads();
     s ^= 1;
   }
 }
