@@ -76,10 +76,11 @@ enum { FW2_PML_A = 0, FW2_PML_B = 1, FW2_PML_C = 2 };
  * the mean of the memory variable before and after its update (D^{n-1/2}
  * estimated by (D^n + D^{n-1}) / 2); ENDPOINT uses the updated value. */
 enum { FW2_MEM_CENTRED = 0, FW2_MEM_ENDPOINT = 1 };
-/* kernel path of the 2D half steps (bitwise the same results on every path):
- * TILE runs one block per 128 x 16 tile; PIPE runs the persistent kernels
- * that stage the interior through shared memory (float or tissue-index maps;
- * TILE elsewhere); AUTO picks the faster of the two for the map storage */
+/* kernel path of the half steps (bitwise the same results on every path):
+ * TILE runs one block per tile; PIPE runs the persistent kernels that stage
+ * every tile through shared memory with TMA copies, where they apply (2D
+ * float or tissue-index maps, 3D bf16 maps with N <= 3, no periodic axis),
+ * and TILE elsewhere; AUTO (default) is PIPE */
 enum { FW2_PATH_AUTO = 0, FW2_PATH_TILE = 1, FW2_PATH_PIPE = 2 };
 enum { FW2_SRC_P = 0, FW2_SRC_VX = 1, FW2_SRC_VY = 2, FW2_SRC_VZ = 3 };
 enum {
@@ -271,8 +272,8 @@ fw2_status fw2_field_absmax_noalloc(const float *field, int64_t row_len, int64_t
  * FW2_EINVAL (null pointer, limit out of range), FW2_ECUDA. */
 fw2_status fw2_selftest_bounded_wait(int64_t limit_ns, int32_t *timed_out);
 /* Kernel path the context's half steps take, resolved once the coefficients
- * are built (first fw2_step): FW2_PATH_TILE or FW2_PATH_PIPE (3D contexts and
- * bf16 maps: FW2_PATH_TILE); FW2_PATH_AUTO before the first step. */
+ * are built (first fw2_step): FW2_PATH_TILE or FW2_PATH_PIPE; FW2_PATH_AUTO
+ * before the first step. */
 fw2_status fw2_kernel_path(fw2_ctx *ctx, int32_t *path);
 /* Bytes of device memory held by the context. */
 fw2_status fw2_device_bytes(fw2_ctx *ctx, int64_t *bytes);
