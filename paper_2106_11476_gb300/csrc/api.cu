@@ -368,6 +368,34 @@ fw2_status fw2_kernel_path(fw2_ctx *c, int32_t *path) {
   return FW2_OK;
 }
 
+fw2_status fw2_taps_time_space(double r, double *g) {
+  if (!g || !(r >= 0.0 && r < 1.0)) return fail(nullptr, FW2_EINVAL, "g is required and r must lie in [0, 1)");
+  // g_11 from the direction-dependent part of the (k h)^4 term; g_1..g_4
+  // from the odd powers p = 1, 3, 5, 7 of the axial relation
+  //   sum_m g_m b_m^p + 2 g_11 2^-p = r^(p-1) 2^-p,  b_m = (2m - 1) / 2
+  const double g11 = r * r / 24.0;
+  double A[4][5];
+  for (int row = 0; row < 4; ++row) {
+    const int p = 2 * row + 1;
+    for (int m = 0; m < 4; ++m) A[row][m] = std::pow((2.0 * m + 1.0) / 2.0, p);
+    A[row][4] = (std::pow(r, p - 1) - 2.0 * g11) / std::pow(2.0, p);
+  }
+  for (int col = 0; col < 4; ++col) {  // Gaussian elimination, partial pivoting
+    int piv = col;
+    for (int row = col + 1; row < 4; ++row)
+      if (std::fabs(A[row][col]) > std::fabs(A[piv][col])) piv = row;
+    for (int k = 0; k < 5; ++k) std::swap(A[col][k], A[piv][k]);
+    for (int row = 0; row < 4; ++row) {
+      if (row == col) continue;
+      const double f = A[row][col] / A[col][col];
+      for (int k = col; k < 5; ++k) A[row][k] -= f * A[col][k];
+    }
+  }
+  for (int m = 0; m < 4; ++m) g[m] = A[m][4] / A[m][m];
+  g[4] = g11;
+  return FW2_OK;
+}
+
 fw2_status fw2_selftest_bounded_wait(int64_t limit_ns, int32_t *timed_out) {
   if (!timed_out || limit_ns < 1 || limit_ns > 10000000000ll)
     return fail(nullptr, FW2_EINVAL, "timed_out is required and limit_ns must lie in [1, 1e10]");

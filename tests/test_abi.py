@@ -93,3 +93,20 @@ def test_null_context_calls_are_rejected(fw2lib):
     assert fw2lib.fw2_step(None, 1) == fw2.EINVAL
     assert fw2lib.fw2_destroy(None) == 0
     assert fw2.fw2_last_error(None)
+
+
+@pytest.mark.parametrize("r", [0.0, 0.1, 0.35, 0.4, 0.7])
+def test_time_space_taps_match_the_oracle(fw2lib, r):
+    """The library's time-space optimised taps (a host computation) equal the
+    oracle's independent derivation."""
+    import numpy as np
+    from oracle import coefficients as cf
+    got = np.array(fw2.fw2_taps_time_space(r))
+    want = np.array(cf.time_space_taps(r))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("r", [-0.1, 1.0, float("nan")])
+def test_time_space_taps_reject_bad_courant_numbers(fw2lib, r):
+    with pytest.raises(fw2.Fw2Error):
+        fw2.fw2_taps_time_space(r)

@@ -383,6 +383,18 @@ def test_pipelined_path_equals_tile_path_cross_taps(fw2):
     _pipe_vs_tile(fw2, prob, 100, state=synth.random_state(prob, seed=3))
 
 
+def test_parity_2d_time_space_taps(fw2):
+    """The time-space optimised operator of Sec. 3.1 (library taps at the
+    problem's Courant number, g11 != 0) against the oracle with the same taps;
+    the pipelined path equals the tile path bitwise with them."""
+    prob = small_2d(nx=560, ny=200, N=4, nl="pressure", steps=200)
+    r = float(np.max(prob.c)) * prob.dt / prob.h
+    prob.taps = tuple(fw2.fw2_taps_time_space(r))
+    assert prob.taps[4] > 0
+    compare_run(fw2, prob, 200)
+    _pipe_vs_tile(fw2, prob, 120)
+
+
 def test_periodic_grids_take_the_tile_kernels(fw2):
     prob = synth.homogeneous((144, 96), 1e-4, 0.0)
     prob.dt = 0.3 * 1e-4 / 1540.0

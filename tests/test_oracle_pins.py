@@ -242,6 +242,69 @@ def test_discrete_dispersion_periodic(shape, m, g11):
         np.testing.assert_allclose(ratio, math.cos(w * dt), rtol=0, atol=1e-11)
 
 
+def test_time_space_taps_reduce_to_taylor_at_zero_courant():
+    ts = cf.time_space_taps(0.0)
+    np.testing.assert_allclose(ts[:4], [float(x) for x in TAPS[:4]], rtol=0, atol=1e-14)
+    assert ts[4] == 0.0
+
+
+@pytest.mark.parametrize("r", [0.2, 0.4])
+def test_time_space_taps_dispersion_orders(r):
+    """Sec. 3.1 time-space optimised operator (our derivation): the relative
+    phase-velocity error of the full leapfrog scheme falls as (k h)^4 in every
+    direction (4th order in time and space off the axes) and as (k h)^8 along
+    the axes, where the Taylor taps fall as (k h)^2 (the 2nd-order time
+    error).  A wrong cross tap or time term leaves the off-axis error at
+    second order."""
+    h, c0 = 1.0, 1.0
+    dt = r * h / c0
+    ts = cf.time_space_taps(r)
+    tay = [float(x) for x in TAPS[:4]] + [0.0]
+
+    def err(taps, a, th):
+        k = [a * math.cos(th), a * math.sin(th)]
+        return an.discrete_omega(k, c0, dt, h, taps) / (c0 * a) - 1.0
+
+    for th in (math.pi / 8, math.pi / 4, 3 * math.pi / 8):
+        ratio = err(ts, 0.2, th) / err(ts, 0.1, th)
+        assert 14.0 < ratio < 18.0, (th, ratio)             # slope 4
+        assert 3.5 < err(tay, 0.2, th) / err(tay, 0.1, th) < 4.5
+        assert abs(err(ts, 0.2, th)) < abs(err(tay, 0.2, th)) / 100
+    ratio_axis = err(ts, 0.4, 0.0) / err(ts, 0.2, 0.0)
+    assert 200.0 < ratio_axis < 300.0                       # slope 8
+
+
+def test_time_space_taps_through_the_stepper():
+    """The oracle stepper with the time-space taps advances a periodic oblique
+    plane wave (|k| h = 0.91) at the closed-form rate, whose error against
+    c |k| is a twentieth of the Taylor taps' or less."""
+    h = 1e-4
+    c0, rho0 = 1540.0, 1000.0
+    r = 0.4
+    dt = r * h / c0
+    shape, m = (48, 40), (5, -4)
+    taps = tuple(cf.time_space_taps(r))
+    prob = synth.homogeneous(shape, h, dt, c=c0, rho=rho0)
+    prob.bc = ("periodic",) * 3
+    prob.taps = taps
+    sim = OracleSim(prob)
+    kh = [2 * math.pi * mq / nq for mq, nq in zip(m, shape)]
+    X, Y = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), indexing="ij")
+    sim.p[:] = np.cos(kh[0] * X + kh[1] * Y).T.ravel()
+    ps = [sim.p.copy()]
+    for _ in range(4):
+        sim.run(1)
+        ps.append(sim.p.copy())
+    w = an.discrete_omega(kh, c0, dt, h, taps)
+    for n in range(1, 4):
+        sel = np.abs(ps[n]) > 0.3
+        ratio = (ps[n + 1][sel] + ps[n - 1][sel]) / (2 * ps[n][sel])
+        np.testing.assert_allclose(ratio, math.cos(w * dt), rtol=0, atol=1e-11)
+    w_exact = c0 * math.hypot(*kh) / h
+    w_taylor = an.discrete_omega(kh, c0, dt, h, TAPS)
+    assert abs(w / w_exact - 1) < abs(w_taylor / w_exact - 1) / 20
+
+
 # --------------------------------------------------------------------------
 # attenuating stepper vs the paper's claims (Sec. 4.1, Table 2)
 # --------------------------------------------------------------------------
