@@ -589,3 +589,43 @@ def test_bf16_storage_rounding_equals_torch():
     x = rng.standard_normal(200000) * np.exp(rng.uniform(-40, 40, 200000))
     ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(cf.to_bf16(x), ref)
+
+
+# --------------------------------------------------------------------------
+# relaxation fitter: the paper's coarse-to-fine grid search (Sec. 4.1)
+# --------------------------------------------------------------------------
+
+def test_batched_curves_equal_the_dispersion_relation():
+    from oracle import fit_relaxation as fr
+    rng = np.random.default_rng(3)
+    f = np.linspace(1e6, 20e6, 31)
+    B, N = 7, 2
+    k1, k2 = rng.uniform(0.8, 1.2, B), rng.uniform(0.8, 1.2, B)
+    d1, d2 = 10 ** rng.uniform(3, 8, (N, B)), 10 ** rng.uniform(3, 8, (N, B))
+    a1, a2 = 10 ** rng.uniform(5, 10, (N, B)), 10 ** rng.uniform(5, 10, (N, B))
+    att, cph = fr.curves_batch(f, 1540.0, k1, k2, d1, a1, d2, a2)
+    for b in range(B):
+        p = {"kappa1": k1[b], "kappa2": k2[b], "d1": d1[:, b], "alpha1": a1[:, b], "d2": d2[:, b],
+             "alpha2": a2[:, b]}
+        att1, c1 = an.model_curves(f, 1540.0, p)
+        np.testing.assert_allclose(att[b], att1, rtol=1e-12)
+        np.testing.assert_allclose(cph[b], c1, rtol=1e-12)
+
+
+def test_grid_search_refines_monotonically():
+    """Each finer grid is centred on the previous best with an odd number of
+    points, so the best cost never rises from one level to the next; on a
+    target made by a known single mechanism it drops by orders of magnitude
+    and stays inside the paper's bounds."""
+    from oracle import fit_relaxation as fr
+    f = np.linspace(1e6, 20e6, 77)
+    truth = {"kappa1": 0.9, "kappa2": 1.1, "d1": [3e5], "alpha1": [2e7], "d2": [5e4], "alpha2": [4e6]}
+    target = an.model_curves(f, 1540.0, truth)
+    p = fr.fit_grid(0, 0, 1, target=target, points=5, refinements=6)
+    lv = p["J_levels"]
+    assert all(b <= a for a, b in zip(lv, lv[1:]))
+    assert lv[-1] < 0.02 * lv[0]
+    b = fr.PAPER_BOUNDS
+    assert b["kappa"][0] <= p["kappa1"] <= b["kappa"][1]
+    for key, lim in (("d1", "log_d"), ("d2", "log_d"), ("alpha1", "log_alpha"), ("alpha2", "log_alpha")):
+        assert all(10 ** b[lim][0] <= v <= 10 ** b[lim][1] for v in p[key])
