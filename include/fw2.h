@@ -54,8 +54,13 @@ enum { FW2_MEM_HOST = 0, FW2_MEM_DEVICE = 1 };
 enum { FW2_BC_ZERO = 0, FW2_BC_PERIODIC = 1 };
 /* nonlinear factor chi of the pressure update p -= dt K div / (1 + chi p):
  * OFF: chi = 0; PRESSURE: chi = kappa0 (1 - 2 beta), the factor printed in
- * Eq. (general6); WESTERVELT: chi = -2 beta kappa0 (kappa0 = 1 / (rho c^2)). */
-enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2 };
+ * Eq. (general6); WESTERVELT: chi = -2 beta kappa0 (kappa0 = 1 / (rho c^2)).
+ * LITERAL: the system as printed, Eqs. (general5) and (general6): the
+ * PRESSURE factor, and the velocity update divided by 1 + kappa0 p at the face
+ * (kappa0 the mean of the two cells' 1/K, p the mean of their p^n), which
+ * propagates with speed c0 + (beta - 1) v.  LITERAL runs the tile kernels in
+ * 3D. */
+enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2, FW2_NL_LITERAL = 3 };
 /* storage of the coefficient maps: float, bf16 (b kept as 1 - b), or a
  * uint8 tissue index per cell into per-tissue float tables (2D only; set the
  * medium with fw2_set_medium_indexed) */

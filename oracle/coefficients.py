@@ -233,7 +233,7 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
     if prob.nl_mode != "off":
         beta = crop(prob.beta)
         kappa0 = 1.0 / K
-        if prob.nl_mode == "pressure":
+        if prob.nl_mode in ("pressure", "literal"):
             chi = kappa0 * (1.0 - 2.0 * beta)        # Eq. (general6) factor
         elif prob.nl_mode == "westervelt":
             chi = -2.0 * beta * kappa0
@@ -266,6 +266,18 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
         if round_to == "bf16":
             nb = to_bf16(nb)
         out[f"buoy{q}"] = (1.0 / (0.5 * (rho_face_src + nb))).ravel()
+        if prob.nl_mode == "literal":
+            # kappa_0 at the face of the momentum factor rho_0 (1 + kappa_0 p)
+            # (Eq. general5): mean of the two cells' 1/K, from K as stored
+            # (same neighbour rule as the density)
+            Kw = (to_bf16(K) if round_to == "bf16" else
+                  K.astype(np.float32).astype(np.float64) if round_to == "f32" else K)
+            c_src, r_src = np.asarray(prob.c).reshape(gshape), rho_src
+            K_src = r_src.astype(np.float64) * c_src.astype(np.float64) ** 2
+            Knb = np.take(K_src[others], idx_hi, axis=ax)
+            Knb = (to_bf16(Knb) if round_to == "bf16" else
+                   Knb.astype(np.float32).astype(np.float64) if round_to == "f32" else Knb)
+            out[f"k0f{q}"] = (0.5 * (1.0 / Kw + 1.0 / Knb)).ravel()
         out[f"ik1{q}"] = (1.0 / k1).ravel()
         out[f"ik2{q}"] = (1.0 / k2).ravel()
         a1 = np.zeros((N, n)); b1 = np.zeros((N, n)); a2 = np.zeros((N, n)); b2 = np.zeros((N, n))
@@ -284,14 +296,14 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
         out[f"a1{q}"], out[f"b1{q}"], out[f"a2{q}"], out[f"b2{q}"] = a1, b1, a2, b2
     if round_to == "f32":
         for k, v in list(out.items()):
-            if isinstance(v, np.ndarray):
+            if isinstance(v, np.ndarray) and not k.startswith("k0f"):
                 out[k] = v.astype(np.float32).astype(np.float64)
     elif round_to == "bf16":
         for k, v in list(out.items()):
             if not isinstance(v, np.ndarray):
                 continue
-            if k.startswith("buoy"):
-                continue                       # computed in float32 from the rounded density
+            if k.startswith("buoy") or k.startswith("k0f"):
+                continue                       # computed from the rounded cell values
             if k.startswith("b1") or k.startswith("b2"):
                 out[k] = 1.0 - to_bf16(1.0 - v)
             else:

@@ -37,7 +37,7 @@ class Grid(C.Structure):
 
 class Coef(C.Structure):
     _fields_ = [("K", DP), ("chi", DP), ("buoy", DP * 3), ("ik1", DP * 3), ("a1", DP * 3),
-                ("b1", DP * 3), ("ik2", DP * 3), ("a2", DP * 3), ("b2", DP * 3)]
+                ("b1", DP * 3), ("ik2", DP * 3), ("a2", DP * 3), ("b2", DP * 3), ("k0f", DP * 3)]
 
 
 class State(C.Structure):
@@ -116,7 +116,9 @@ class OracleSim:
         self.C.K = _dp(cf["K"])
         self.C.chi = _dp(cf["chi"])
         for q in range(nd):
-            for name in ("buoy", "ik1", "ik2", "a1", "b1", "a2", "b2"):
+            for name in ("buoy", "ik1", "ik2", "a1", "b1", "a2", "b2", "k0f"):
+                if f"{name}{q}" not in cf:
+                    continue                   # k0f: only with the momentum factor
                 arr = np.ascontiguousarray(cf[f"{name}{q}"], np.float64)
                 self._keep.append(arr)
                 getattr(self.C, name)[q] = _dp(arr)

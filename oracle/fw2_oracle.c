@@ -56,6 +56,9 @@ typedef struct {
   const double *ik2[3];     /* [n] 1/kappa_2 at cell centres, axis q */
   const double *a2[3];      /* [N][n] */
   const double *b2[3];      /* [N][n] */
+  const double *k0f[3];     /* [n] kappa_0 = 1/K at the +1/2 face of axis q (mean of
+                               the two cells); NULL: no nonlinear factor in the
+                               momentum equation */
 } orc_coef;
 
 typedef struct {
@@ -171,7 +174,10 @@ static double d_centre(const orc_grid *G, const double *v, int q, int64_t i,
  *   psi_nu = b psi_nu + a D                     (nu = 1..N)
  *   S      = D / kappa_1 + sum_nu psi_nu        (or the mean of old and new
  *                                                psi_nu when centred)
- *   v_q   -= dt * (1/rho_face) * S               (Eq. general5, linear in rho) */
+ *   v_q   -= dt * (1/rho_face) * S               (Eq. general5, linear in rho)
+ * With the momentum equation's nonlinear factor (k0f given, Eq. general5 as
+ * printed: rho_0 (1 + kappa_0 p)) the update is divided by
+ * 1 + kappa_0,face p_face, p_face the mean of p^n at the face's two cells. */
 static void velocity_half_step(const orc_grid *G, const orc_coef *C,
                                orc_state *S) {
   const int64_t n = npts(G);
@@ -191,7 +197,14 @@ static void velocity_half_step(const orc_grid *G, const orc_coef *C,
                    C->a1[q][(int64_t)nu * n + c] * D;
             stretched += G->centred ? 0.5 * (old + *psi) : *psi;
           }
-          S->v[q][c] -= G->dt * C->buoy[q][c] * stretched;
+          double upd = G->dt * C->buoy[q][c] * stretched;
+          if (C->k0f[q]) {
+            int64_t e[3] = {0, 0, 0};
+            e[q] = 1;
+            const double pf = 0.5 * (S->p[c] + fetch(G, S->p, i + e[0], j + e[1], k + e[2]));
+            upd /= 1.0 + C->k0f[q][c] * pf;
+          }
+          S->v[q][c] -= upd;
         }
       }
     }

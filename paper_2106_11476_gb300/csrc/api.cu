@@ -219,6 +219,7 @@ fw2_status finalize(fw2_ctx *c) {
   if (cfg.mem_alignment == FW2_MEM_CENTRED) { P.w_new = 0.5f; P.w_old = 0.5f; }
   else { P.w_new = 1.0f; P.w_old = 0.0f; }
   P.nl = cfg.nl_mode != FW2_NL_OFF;
+  P.nl_vel = cfg.nl_mode == FW2_NL_LITERAL;
   P.n_relax = c->N;
   P.p = c->p;
   P.K = Q.K; P.rho = Q.rho_o; P.chi = Q.chi; P.ik1 = Q.ik1; P.ik2 = Q.ik2;
@@ -458,7 +459,7 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
   if (cfg.map_precision == FW2_MAP_IDX_U8 && cfg.ndim != 2)
     return fail(nullptr, FW2_EUNSUPPORTED, "tissue-index maps are implemented for 2D grids");
-  if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_WESTERVELT) return fail(nullptr, FW2_EINVAL, "bad nl_mode");
+  if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_LITERAL) return fail(nullptr, FW2_EINVAL, "bad nl_mode");
   if (cfg.mem_alignment != FW2_MEM_CENTRED && cfg.mem_alignment != FW2_MEM_ENDPOINT)
     return fail(nullptr, FW2_EINVAL, "bad mem_alignment");
   if (cfg.kernel_path != FW2_PATH_AUTO && cfg.kernel_path != FW2_PATH_TILE && cfg.kernel_path != FW2_PATH_PIPE)

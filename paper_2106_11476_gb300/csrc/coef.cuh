@@ -124,6 +124,20 @@ __device__ __forceinline__ float4 load_chunk(const StepParams &P, const float *f
   return v;
 }
 
+// Momentum factor of the literal nonlinear system (Eq. general5,
+// rho_0 (1 + kappa_0 p)) at the face between cells a and b: 1 + kappa0_face
+// p_face, both the mean of the two cells (kappa0 = 1 / K).
+__device__ __forceinline__ float mom_factor(float Ka, float Kb, float pa, float pb) {
+  return fmaf(0.5f * (1.f / Ka + 1.f / Kb), 0.5f * (pa + pb), 1.f);
+}
+
+// The velocity update v - b S (Eq. general5, b = 2 dt / (rho_a + rho_b)),
+// and with the literal system's momentum factor f, v - b (S / f).  One fused
+// multiply-add each, written out so that every kernel of the half step
+// rounds alike whatever the compiler's contraction choices.
+__device__ __forceinline__ float vel_upd(float v, float b, float S) { return fmaf(-b, S, v); }
+__device__ __forceinline__ float vel_upd(float v, float b, float S, float f) { return fmaf(-b, S / f, v); }
+
 // Density used for the face average: cells beyond the last one along an
 // axis take the last cell's value (zero-outside boundary) or wrap (periodic).
 __device__ __forceinline__ int rho_coord(int x, int n, int periodic) {

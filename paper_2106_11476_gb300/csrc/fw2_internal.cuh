@@ -32,6 +32,7 @@ struct StepParams {
   float g11h;            // g_{1,1} / h
   float w_new, w_old;    // memory-term weights: centred (0.5, 0.5), endpoint (1, 0)
   int nl;                // nonlinear factor present
+  int nl_vel;            // momentum factor 1 + kappa0 p at the faces (literal system)
   int n_relax;
   // state (float)
   float *p;

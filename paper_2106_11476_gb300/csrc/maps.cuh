@@ -34,6 +34,7 @@ struct DenseMaps {
   __device__ __forceinline__ void bind(const float *) {}
   __device__ __forceinline__ Cell cell(long long c) const { return {c}; }
   __device__ __forceinline__ float rho_at(long long gidx) const { return ldmap(rho, gidx); }
+  __device__ __forceinline__ float K_at(long long gidx) const { return ldmap(K, gidx); }
   __device__ __forceinline__ float4 Kv(Cell x) const { return ldmap4(K, x.c); }
   __device__ __forceinline__ float4 chiv(Cell x) const { return ldmap4(chi, x.c); }
   __device__ __forceinline__ float4 ik1(Cell x) const { return ldmap4(ik1_, x.c); }
@@ -84,6 +85,7 @@ struct IdxMaps {
   __device__ __forceinline__ float rho_at(long long gidx) const {
     return tab[kTabRho * kTissues + __ldg(idx + gidx)];
   }
+  __device__ __forceinline__ float K_at(long long gidx) const { return tab[kTabK * kTissues + __ldg(idx + gidx)]; }
   __device__ __forceinline__ float4 Kv(Cell x) const { return look(kTabK, x); }
   __device__ __forceinline__ float4 chiv(Cell x) const { return look(kTabChi, x); }
   __device__ __forceinline__ float4 ik1(Cell x) const { return look(kTabIk1, x); }

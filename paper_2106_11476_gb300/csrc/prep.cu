@@ -104,7 +104,7 @@ __global__ void cell_maps_kernel(const PrepParams Q) {
     store((MT *)Q.rho_o, o, rho);
     if (Q.nl_mode != 0) {
       const double beta = Q.beta[t];
-      const double chi = Q.nl_mode == 1 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K;
+      const double chi = Q.nl_mode != 2 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K;  // 1, 3: Eq. general6
       store((MT *)Q.chi, o, chi);
     }
     const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
@@ -135,7 +135,7 @@ __global__ void table_kernel(const PrepParams Q) {
   T[kTabRho * kTissues + t] = (float)rho;
   if (Q.nl_mode != 0) {
     const double beta = Q.beta[t];
-    T[kTabChi * kTissues + t] = (float)(Q.nl_mode == 1 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K);
+    T[kTabChi * kTissues + t] = (float)(Q.nl_mode != 2 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K);
   }
   const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
   T[kTabIk1 * kTissues + t] = (float)(1.0 / k1);

@@ -349,6 +349,30 @@ __device__ __forceinline__ FaceRho face_rho(const StepParams &P, const float *ta
   return FaceRho{at(r0, c0), at(r0, c1), at(r0, c2), at(r1, c0), at(r1, c1)};
 }
 
+// Momentum factors of the literal nonlinear system (Eq. general5) at the x
+// and y faces of the pair: p from the staged operand (cell e at column
+// lx + 4 + e of row sy; zero beyond the grid), K from the map (float maps) or
+// the staged index (index form), neighbours clamped to the last cell.
+template <typename Maps, bool EDGE>
+__device__ __forceinline__ void mom_factors2(const StepParams &P, const float *tab, const unsigned char *si,
+                                             const float *sp, int sy, int lx, int ly, int x0, int y0, float2 &fx,
+                                             float2 &fy) {
+  const float *row = sp + sy * kCW + lx + 4, *up = sp + (sy + 1) * kCW + lx + 4;
+  const int mx = P.nx - 1 - x0, my = P.ny - 1 - y0;
+  const int r1 = EDGE ? min(ly + 1, my) : ly + 1;
+  auto K = [&](int r, int cc) -> float {
+    if constexpr (IsIdx<Maps>::value) return tab[kTabK * kTissues + si[r * kIW + cc]];
+    else return ldmap(static_cast<const float *>(P.K), (long long)(y0 + r) * P.pitch + x0 + cc);
+  };
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int c0 = EDGE ? min(lx + e, mx) : lx + e, c1 = EDGE ? min(lx + e + 1, mx) : lx + e + 1;
+    const float Kc = K(ly, c0), Kx = K(ly, c1), Ky = K(r1, c0);
+    el2(fx, e) = mom_factor(Kc, Kx, row[e], row[e + 1]);
+    el2(fy, e) = mom_factor(Kc, Ky, row[e], up[e]);
+  }
+}
+
 // a, b of mechanism nu along x at the two cells of an edge pair: from the x
 // strip inside its C-PML region, else unchanged (coef_edge of the tile path;
 // its zero beyond the grid only reaches cells that are masked)
@@ -501,10 +525,19 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
     put2<Maps, EDGE>(own, 2 + N + nu, P.psi1[1], nu * Sn + c, ny_, i0, P.nx);
   }
   const FaceRho fr = face_rho<Maps, EDGE>(P, tab, sr, si, x0, y0, lx, ly);
-  vx.x -= P.two_dt / (fr.r0 + fr.r1) * Sx.x;
-  vx.y -= P.two_dt / (fr.r1 + fr.r2) * Sx.y;
-  vy.x -= P.two_dt / (fr.r0 + fr.u0) * Sy.x;
-  vy.y -= P.two_dt / (fr.r1 + fr.u1) * Sy.y;
+  if (P.nl_vel) {
+    float2 fx, fy;
+    mom_factors2<Maps, EDGE>(P, tab, si, sp, ly + 3, lx, ly, x0, y0, fx, fy);
+    vx.x = vel_upd(vx.x, P.two_dt / (fr.r0 + fr.r1), Sx.x, fx.x);
+    vx.y = vel_upd(vx.y, P.two_dt / (fr.r1 + fr.r2), Sx.y, fx.y);
+    vy.x = vel_upd(vy.x, P.two_dt / (fr.r0 + fr.u0), Sy.x, fy.x);
+    vy.y = vel_upd(vy.y, P.two_dt / (fr.r1 + fr.u1), Sy.y, fy.y);
+  } else {
+    vx.x = vel_upd(vx.x, P.two_dt / (fr.r0 + fr.r1), Sx.x);
+    vx.y = vel_upd(vx.y, P.two_dt / (fr.r1 + fr.r2), Sx.y);
+    vy.x = vel_upd(vy.x, P.two_dt / (fr.r0 + fr.u0), Sy.x);
+    vy.y = vel_upd(vy.y, P.two_dt / (fr.r1 + fr.u1), Sy.y);
+  }
   put2<Maps, EDGE>(own, 0, P.v[0], c, vx, i0, P.nx);
   put2<Maps, EDGE>(own, 1, P.v[1], c, vy, i0, P.nx);
 }

@@ -41,6 +41,30 @@ __device__ __forceinline__ bool interior_z(const StepParams &P, int k) {
   return k >= Lz && k + Lz < P.nz;
 }
 
+// Momentum factors of the literal nonlinear system (Eq. general5) at the x, y
+// and z faces of the four cells i0..i0+3 of row (j, k): p from the staged
+// plane (row sy of sp) and the z column (pz1 = p at k+1), K from the map with
+// the density's neighbour rule; cells past nx are clamped (masked later).
+template <typename MT>
+__device__ __forceinline__ void mom_factors3(const StepParams &P, const float (*sp)[kTX + 8], int sy, int tx, int i0,
+                                             int j, int k, const float4 &pz1, float4 &fx, float4 &fy, float4 &fz) {
+  const MT *Km = static_cast<const MT *>(P.K);
+  const Win12 w = win12(sp[sy], tx), up = win12(sp[sy + 1], tx);
+  const int jn = rho_coord(j + 1, P.ny, P.periodic[1]), kn = rho_coord(k + 1, P.nz, P.periodic[2]);
+  const long long row = (long long)k * P.plane + (long long)j * P.pitch;
+  const long long rowy = (long long)k * P.plane + (long long)jn * P.pitch;
+  const long long rowz = (long long)kn * P.plane + (long long)j * P.pitch;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int x = min(i0 + e, P.nx - 1);
+    const int xn = rho_coord(min(i0 + e + 1, P.nx), P.nx, P.periodic[0]);
+    const float Kc = ldmap(Km, row + x);
+    el(fx, e) = mom_factor(Kc, ldmap(Km, row + xn), w.v[4 + e], w.v[5 + e]);
+    el(fy, e) = mom_factor(Kc, ldmap(Km, rowy + x), w.v[4 + e], up.v[4 + e]);
+    el(fz, e) = mom_factor(Kc, ldmap(Km, rowz + x), w.v[4 + e], el(pz1, e));
+  }
+}
+
 // Interior plane of the velocity half step: z taps first (L2), then every
 // streaming load of the plane row before any store.
 template <int N, typename MT>
@@ -48,12 +72,13 @@ __device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp
                                            const float (*sr)[kTX + 4], int i0, int j, int k, int tx, int ty) {
   const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
   const long long S = P.npts_alloc;
-  float4 Dz;
+  float4 Dz, pz1;
   {
     float4 zc[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m)
       zc[m] = __ldg(reinterpret_cast<const float4 *>(P.p + c + (long long)(m - 3) * P.plane));
+    pz1 = zc[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       float d = 0.f;
@@ -128,11 +153,22 @@ __device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp
     st_state4(P.psi1[2], nu * S + c, n2);
   }
   const float rr[5] = {r0.x, r0.y, r0.z, r0.w, r4};
+  if (P.nl_vel) {
+    float4 fx, fy, fz;
+    mom_factors3<MT>(P, sp, sy, tx, i0, j, k, pz1, fx, fy, fz);
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    el(v0, e) -= P.two_dt / (rr[e] + rr[e + 1]) * el(S0, e);
-    el(v1, e) -= P.two_dt / (rr[e] + el(ru, e)) * el(S1, e);
-    el(v2, e) -= P.two_dt / (rr[e] + el(rz, e)) * el(S2, e);
+    for (int e = 0; e < 4; ++e) {
+      el(v0, e) = vel_upd(el(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el(S0, e), el(fx, e));
+      el(v1, e) = vel_upd(el(v1, e), P.two_dt / (rr[e] + el(ru, e)), el(S1, e), el(fy, e));
+      el(v2, e) = vel_upd(el(v2, e), P.two_dt / (rr[e] + el(rz, e)), el(S2, e), el(fz, e));
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el(v0, e) = vel_upd(el(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el(S0, e));
+      el(v1, e) = vel_upd(el(v1, e), P.two_dt / (rr[e] + el(ru, e)), el(S1, e));
+      el(v2, e) = vel_upd(el(v2, e), P.two_dt / (rr[e] + el(rz, e)), el(S2, e));
+    }
   }
   st_state4(P.v[0], c, v0);
   st_state4(P.v[1], c, v1);
@@ -289,11 +325,13 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
         el(Dy, e) = d;
       }
     }
+    float4 pz1;
     {
       // d/dz at faces k+1/2: sum_m g_m (p[k+m] - p[k-m+1]) on the cell's own column
       float4 zc[8];
 #pragma unroll
       for (int m = 0; m < 8; ++m) zc[m] = load_chunk(P, P.p, i0, j, k - 3 + m);
+      pz1 = zc[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         float d = 0.f;
@@ -323,23 +361,23 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
                        P.two_dt / (r0.w + rz.w));
     }
     const float4 k1 = ldmap4(ik1, c);
-    {
-      const float4 S = stretch4<0, 1, N, MT>(P, P.psi1[0], Dx, k1, c, i0, j, k);
-      float4 v = ld_state4(P.v[0], c);
-      v.x -= bx.x * S.x; v.y -= bx.y * S.y; v.z -= bx.z * S.z; v.w -= bx.w * S.w;
-      st_state4(P.v[0], c, mask_pad(v, i0, P.nx));
-    }
-    {
-      const float4 S = stretch4<1, 1, N, MT>(P, P.psi1[1], Dy, k1, c, i0, j, k);
-      float4 v = ld_state4(P.v[1], c);
-      v.x -= by.x * S.x; v.y -= by.y * S.y; v.z -= by.z * S.z; v.w -= by.w * S.w;
-      st_state4(P.v[1], c, mask_pad(v, i0, P.nx));
-    }
-    {
-      const float4 S = stretch4<2, 1, N, MT>(P, P.psi1[2], Dz, k1, c, i0, j, k);
-      float4 v = ld_state4(P.v[2], c);
-      v.x -= bz.x * S.x; v.y -= bz.y * S.y; v.z -= bz.z * S.z; v.w -= bz.w * S.w;
-      st_state4(P.v[2], c, mask_pad(v, i0, P.nx));
+    float4 fx = make_float4(1.f, 1.f, 1.f, 1.f), fy = fx, fz = fx;
+    if (P.nl_vel) mom_factors3<MT>(P, sp, ly + 3, tx, i0, j, k, pz1, fx, fy, fz);
+    const float4 bb[3] = {bx, by, bz}, ff[3] = {fx, fy, fz};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 S = q == 0 ? stretch4<0, 1, N, MT>(P, P.psi1[0], Dx, k1, c, i0, j, k)
+                     : q == 1 ? stretch4<1, 1, N, MT>(P, P.psi1[1], Dy, k1, c, i0, j, k)
+                              : stretch4<2, 1, N, MT>(P, P.psi1[2], Dz, k1, c, i0, j, k);
+      float4 v = ld_state4(P.v[q], c);
+      if (P.nl_vel) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) el(v, e) = vel_upd(el(v, e), el(bb[q], e), el(S, e), el(ff[q], e));
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) el(v, e) = vel_upd(el(v, e), el(bb[q], e), el(S, e));
+      }
+      st_state4(P.v[q], c, mask_pad(v, i0, P.nx));
     }
     }
   }

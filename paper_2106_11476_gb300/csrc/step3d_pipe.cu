@@ -404,9 +404,9 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, int
   const float rr[3] = {f.r0, f.r1, f.r2}, ru[2] = {f.u0, f.u1}, rz[2] = {f.z0, f.z1};
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    el2(v0, e) -= P.two_dt / (rr[e] + rr[e + 1]) * el2(S0, e);
-    el2(v1, e) -= P.two_dt / (rr[e] + ru[e]) * el2(S1, e);
-    el2(v2, e) -= P.two_dt / (rr[e] + rz[e]) * el2(S2, e);
+    el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(S0, e));
+    el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(S1, e));
+    el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(S2, e));
   }
   if (EDGE) {
     v0 = mask_pad2(v0, i0, P.nx);
@@ -634,9 +634,10 @@ Region3 region3_of(const StepParams &P) {
 
 bool pipe3d_supported(const StepParams &P, int map_kind) {
   // bf16 maps (two stages of ~107 KB fit); N <= 3 keeps the 4D boxes and
-  // the stage within shared memory; no periodic axis
+  // the stage within shared memory; no periodic axis; the momentum
+  // equation's nonlinear factor is left to the tile kernels
   return P.nz > 1 && map_kind == 1 && P.n_relax >= 0 && P.n_relax <= 3 && !P.periodic[0] && !P.periodic[1] &&
-         !P.periodic[2];
+         !P.periodic[2] && !P.nl_vel;
 }
 
 cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why) {

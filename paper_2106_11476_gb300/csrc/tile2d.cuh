@@ -189,6 +189,27 @@ __device__ __forceinline__ float4 stretch_edge(const StepParams &P, const Maps &
   return S;
 }
 
+// Momentum factors of the literal nonlinear system (Eq. general5) at the x
+// and y faces of the four cells i0..i0+3 of row j: p from the staged operand
+// (row sy of sp; zero or wrapped beyond the grid), K through the maps with
+// the density's neighbour rule.  Cells past nx are clamped (their results are
+// masked).
+template <typename Maps>
+__device__ __forceinline__ void mom_factors(const StepParams &P, const Maps &M, const float (*sp)[kTX + 8], int sy,
+                                            int tx, int i0, int j, float4 &fx, float4 &fy) {
+  const Win12 w = win12(sp[sy], tx), up = win12(sp[sy + 1], tx);
+  const int jn = rho_coord(j + 1, P.ny, P.periodic[1]);
+  const long long row = (long long)j * P.pitch, rown = (long long)jn * P.pitch;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int x = min(i0 + e, P.nx - 1);
+    const int xn = rho_coord(min(i0 + e + 1, P.nx), P.nx, P.periodic[0]);
+    const float Kc = M.K_at(row + x), Kx = M.K_at(row + xn), Ky = M.K_at(rown + x);
+    el(fx, e) = mom_factor(Kc, Kx, w.v[4 + e], w.v[5 + e]);
+    el(fy, e) = mom_factor(Kc, Ky, w.v[4 + e], up.v[4 + e]);
+  }
+}
+
 // Interior rows of the velocity half step.  Every global load of a row (both
 // velocity components, the maps and the memory variables of both axes) is
 // issued before any store, so a row pays one memory latency instead of one
@@ -240,14 +261,27 @@ __device__ __forceinline__ void vel2d_fast_rows(const StepParams &P, const Maps 
       st_state4(psx, nu * S + c, nx_);
       st_state4(psy, nu * S + c, ny_);
     }
-    vx.x -= P.two_dt / (r0.x + r0.y) * Sx.x;
-    vx.y -= P.two_dt / (r0.y + r0.z) * Sx.y;
-    vx.z -= P.two_dt / (r0.z + r0.w) * Sx.z;
-    vx.w -= P.two_dt / (r0.w + r4) * Sx.w;
-    vy.x -= P.two_dt / (r0.x + ru.x) * Sy.x;
-    vy.y -= P.two_dt / (r0.y + ru.y) * Sy.y;
-    vy.z -= P.two_dt / (r0.z + ru.z) * Sy.z;
-    vy.w -= P.two_dt / (r0.w + ru.w) * Sy.w;
+    if (P.nl_vel) {
+      float4 fx, fy;
+      mom_factors(P, M, sp, ly + 3, tx, i0, j, fx, fy);
+      vx.x = vel_upd(vx.x, P.two_dt / (r0.x + r0.y), Sx.x, fx.x);
+      vx.y = vel_upd(vx.y, P.two_dt / (r0.y + r0.z), Sx.y, fx.y);
+      vx.z = vel_upd(vx.z, P.two_dt / (r0.z + r0.w), Sx.z, fx.z);
+      vx.w = vel_upd(vx.w, P.two_dt / (r0.w + r4), Sx.w, fx.w);
+      vy.x = vel_upd(vy.x, P.two_dt / (r0.x + ru.x), Sy.x, fy.x);
+      vy.y = vel_upd(vy.y, P.two_dt / (r0.y + ru.y), Sy.y, fy.y);
+      vy.z = vel_upd(vy.z, P.two_dt / (r0.z + ru.z), Sy.z, fy.z);
+      vy.w = vel_upd(vy.w, P.two_dt / (r0.w + ru.w), Sy.w, fy.w);
+    } else {
+      vx.x = vel_upd(vx.x, P.two_dt / (r0.x + r0.y), Sx.x);
+      vx.y = vel_upd(vx.y, P.two_dt / (r0.y + r0.z), Sx.y);
+      vx.z = vel_upd(vx.z, P.two_dt / (r0.z + r0.w), Sx.z);
+      vx.w = vel_upd(vx.w, P.two_dt / (r0.w + r4), Sx.w);
+      vy.x = vel_upd(vy.x, P.two_dt / (r0.x + ru.x), Sy.x);
+      vy.y = vel_upd(vy.y, P.two_dt / (r0.y + ru.y), Sy.y);
+      vy.z = vel_upd(vy.z, P.two_dt / (r0.z + ru.z), Sy.z);
+      vy.w = vel_upd(vy.w, P.two_dt / (r0.w + ru.w), Sy.w);
+    }
     st_state4(P.v[0], c, vx);
     st_state4(P.v[1], c, vy);
   }
@@ -368,16 +402,30 @@ __device__ __forceinline__ void vel2d_tile(const StepParams &P, int x0, int y0, 
                        P.two_dt / (r0.w + ru.w));
     }
     const float4 k1 = M.ik1(cell);
+    float4 fx = make_float4(1.f, 1.f, 1.f, 1.f), fy = fx;
+    if (P.nl_vel) mom_factors(P, M, sp, ly + 3, tx, i0, j, fx, fy);
     {
       const float4 S = stretch_edge<0, 1, N>(P, M, cell, P.psi1[0], Dx, k1, c, i0, j);
       float4 v = ld_state4(P.v[0], c);
-      v.x -= bx.x * S.x; v.y -= bx.y * S.y; v.z -= bx.z * S.z; v.w -= bx.w * S.w;
+      if (P.nl_vel) {
+        v.x = vel_upd(v.x, bx.x, S.x, fx.x); v.y = vel_upd(v.y, bx.y, S.y, fx.y);
+        v.z = vel_upd(v.z, bx.z, S.z, fx.z); v.w = vel_upd(v.w, bx.w, S.w, fx.w);
+      } else {
+        v.x = vel_upd(v.x, bx.x, S.x); v.y = vel_upd(v.y, bx.y, S.y);
+        v.z = vel_upd(v.z, bx.z, S.z); v.w = vel_upd(v.w, bx.w, S.w);
+      }
       st_state4(P.v[0], c, mask_pad(v, i0, P.nx));
     }
     {
       const float4 S = stretch_edge<1, 1, N>(P, M, cell, P.psi1[1], Dy, k1, c, i0, j);
       float4 v = ld_state4(P.v[1], c);
-      v.x -= by.x * S.x; v.y -= by.y * S.y; v.z -= by.z * S.z; v.w -= by.w * S.w;
+      if (P.nl_vel) {
+        v.x = vel_upd(v.x, by.x, S.x, fy.x); v.y = vel_upd(v.y, by.y, S.y, fy.y);
+        v.z = vel_upd(v.z, by.z, S.z, fy.z); v.w = vel_upd(v.w, by.w, S.w, fy.w);
+      } else {
+        v.x = vel_upd(v.x, by.x, S.x); v.y = vel_upd(v.y, by.y, S.y);
+        v.z = vel_upd(v.z, by.z, S.z); v.w = vel_upd(v.w, by.w, S.w);
+      }
       st_state4(P.v[1], c, mask_pad(v, i0, P.nx));
     }
   }

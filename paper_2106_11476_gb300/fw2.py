@@ -21,7 +21,7 @@ STATUS_NAMES = ["FW2_OK", "FW2_EINVAL", "FW2_ENOMEM", "FW2_ECUDA", "FW2_ESTATE",
                 "FW2_ETIMEOUT", "FW2_EUNSUPPORTED"]
 MEM_HOST, MEM_DEVICE = 0, 1
 BC = {"zero": 0, "periodic": 1}
-NL = {"off": 0, "pressure": 1, "westervelt": 2}
+NL = {"off": 0, "pressure": 1, "westervelt": 2, "literal": 3}
 MAP = {"f32": 0, "bf16": 1, "idx": 2}
 PML_READING = {"A": 0, "B": 1, "C": 2}
 MEM_ALIGN = {"centred": 0, "endpoint": 1}

@@ -77,7 +77,7 @@ class Problem:
     pml_npow: float = 2.0
     pml_cp: float = 0.0       # 0: use the largest sound speed of the medium
     pml_reading: str = "C"
-    nl_mode: str = "off"      # "off", "pressure" or "westervelt"
+    nl_mode: str = "off"      # "off", "pressure", "westervelt" or "literal"
     memory_alignment: str = "centred"   # "centred" or "endpoint" time alignment of the memory term
     bc: Tuple[str, ...] = ("zero", "zero", "zero")
     taps: Optional[Tuple[float, ...]] = None   # (g1, g2, g3, g4, g11); None: 8th-order Taylor

@@ -25,6 +25,8 @@ def _problems():
     probs.append(("f32", small_2d(nx=200, ny=136, N=2, steps=90)))
     probs.append(("f32", small_2d(nx=150, ny=60, N=4, nl="pressure", steps=90, pml=(6, 2), vel_src=True)))
     probs.append(("bf16", small_2d(nx=96, ny=96, N=4, steps=90, pml=(6, 2))))
+    # both nonlinear factors, grouped with the linear N = 2 context above
+    probs.append(("f32", small_2d(nx=180, ny=100, N=2, nl="literal", steps=90, amp=2e7)))
     return probs
 
 

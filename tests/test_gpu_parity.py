@@ -92,7 +92,7 @@ def state_names(prob):
 
 
 def small_2d(nx=200, ny=136, N=2, nl="off", steps=300, seed=0, pml=(12, 4), alignment="centred",
-             reading="C", vel_src=False, hetero=True):
+             reading="C", vel_src=False, hetero=True, amp=None):
     key = {2: "N2_y1.0_a0.5", 3: "N3_y1.2_brain", 4: "N4_y1.1_a0.5"}.get(N)
     rng = np.random.default_rng(seed)
     f0 = 3e6
@@ -113,7 +113,7 @@ def small_2d(nx=200, ny=136, N=2, nl="off", steps=300, seed=0, pml=(12, 4), alig
         prob.pml_transition, prob.pml_bound = pml
     L = sum(pml) if N else 0
     xs = np.arange(L + 2, nx - L - 2)
-    sig = synth.gaussian_pulse(steps, prob.dt, f0, 3.0, 2e6 if nl != "off" else 1e5)
+    sig = synth.gaussian_pulse(steps, prob.dt, f0, 3.0, amp or (2e6 if nl != "off" else 1e5))
     prob.sources = [synth.Source("p", synth.flat_index((nx, ny), xs, L + 6), np.zeros(xs.size, np.int32),
                                  sig[:, None])]
     if vel_src:
@@ -167,6 +167,10 @@ CASES_2D = {
     # grids with interior tiles: the persistent kernels' staged half tiles
     "interior-560x200-N4-nl": dict(nx=560, ny=200, N=4, nl="pressure", steps=250),
     "interior-430x170-N0": dict(nx=430, ny=170, N=0, steps=250),
+    # both nonlinear factors (Eqs. general5-general6) at 2e7 Pa, where the
+    # momentum factor moves the fields by ~1e-2, a hundred times the bound
+    "literal-N4": dict(nl="literal", N=4, vel_src=True, amp=2e7),
+    "literal-interior-560x200-N2": dict(nx=560, ny=200, N=2, nl="literal", steps=250, amp=2e7),
 }
 
 
@@ -178,11 +182,31 @@ def test_parity_2d(fw2, case):
     compare_run(fw2, prob, steps)
 
 
-@pytest.mark.parametrize("case", ["interior-560x200-N4-nl", "interior-430x170-N0", "ragged-203x77"])
+@pytest.mark.parametrize("case", ["interior-560x200-N4-nl", "interior-430x170-N0", "ragged-203x77",
+                                  "literal-interior-560x200-N2"])
 def test_parity_2d_pipelined_path(fw2, case):
     kw = dict(CASES_2D[case])
     steps = kw.get("steps", 300)
     compare_run(fw2, small_2d(**kw), steps, kernel_path="pipe")
+
+
+@pytest.mark.parametrize("path", ["tile", "pipe"])
+def test_parity_2d_literal_tile_and_pipe(fw2, path):
+    kw = dict(CASES_2D["literal-interior-560x200-N2"])
+    compare_run(fw2, small_2d(**kw), kw["steps"], kernel_path=path)
+
+
+def test_literal_momentum_factor_acts(fw2):
+    """The literal system differs from the pressure-only factor with the same
+    beta_eff by far more than the parity bound: the momentum factor runs."""
+    out = {}
+    for nl in ("pressure", "literal"):
+        prob = small_2d(nx=300, ny=200, N=2, nl=nl, steps=250, amp=2e7)
+        sim = fw2.Simulation(prob)
+        sim.step(250)
+        out[nl] = sim.field("p")
+        sim.close()
+    assert rel_l2(out["literal"], out["pressure"]) > 30 * REL_L2
 
 
 @pytest.mark.parametrize("nl,N", [("off", 2), ("pressure", 4)])
@@ -239,6 +263,21 @@ def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3):
 def test_parity_3d(fw2):
     prob = small_3d()
     compare_run(fw2, prob, 80)
+
+
+@pytest.mark.parametrize("maps", ["f32", "bf16"])
+def test_parity_3d_literal(fw2, maps):
+    """Both nonlinear factors in 3D (tile kernels; the pipelined 3D half
+    steps leave this mode to them)."""
+    prob = small_3d(nl="literal", steps=80)
+    for s in prob.sources:
+        if s.kind == "p":
+            s.signal = s.signal * 20
+    compare_run(fw2, prob, 80, maps=maps, kernel_path="pipe" if maps == "bf16" else "auto")
+    sim = fw2.Simulation(prob, map_precision="bf16", kernel_path="pipe")
+    sim.step(1)
+    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    sim.close()
 
 
 def test_parity_3d_bf16_maps(fw2):
@@ -334,7 +373,7 @@ def test_parity_skull_full_size_windows(fw2):
     sim.close()
 
 
-@pytest.mark.parametrize("nl", ["pressure", "off"])
+@pytest.mark.parametrize("nl", ["pressure", "off", "literal"])
 def test_tissue_index_form_equals_dense_form_bitwise(fw2, nl):
     """uint8 tissue index + per-tissue tables give bitwise the same fields and
     traces as the dense float maps of the same medium (ragged 203 x 150 grid)."""
@@ -363,7 +402,8 @@ def _pipe_vs_tile(fw2, prob, steps, maps="f32", state=None):
         np.testing.assert_array_equal(out["pipe"][1], out["tile"][1])
 
 
-@pytest.mark.parametrize("N,nl", [(0, "off"), (2, "westervelt"), (2, "off"), (3, "pressure"), (4, "pressure")])
+@pytest.mark.parametrize("N,nl", [(0, "off"), (2, "westervelt"), (2, "off"), (3, "pressure"), (4, "pressure"),
+                                  (0, "literal"), (4, "literal")])
 def test_pipelined_path_equals_tile_path_bitwise(fw2, N, nl):
     """The persistent pipelined half steps compute exactly what the one-block-
     per-tile kernels compute (same arithmetic, staged operands), edge and
@@ -405,7 +445,7 @@ def test_periodic_grids_take_the_tile_kernels(fw2):
     sim.close()
 
 
-@pytest.mark.parametrize("nl", ["pressure", "off"])
+@pytest.mark.parametrize("nl", ["pressure", "off", "literal"])
 def test_pipelined_path_equals_tile_path_tissue_index(fw2, nl):
     prob = synth.indexed_abdominal_problem(nx=650, ny=300, n_steps=150, n_elements=16, nl=nl)
     _pipe_vs_tile(fw2, prob, 150, maps="idx")
