@@ -26,30 +26,36 @@ from typing import Dict, Optional
 import numpy as np
 
 
-def time_space_taps(r: float, M: int = 4):
-    """Taps g_1..g_M and the cross tap g_11 of the 2D staggered operator
-    optimised for the leapfrog step at Courant number r = c dt / h (Sec. 3.1
-    cites a time-space-domain optimised set without printing it; this is our
-    derivation from that principle).
+def time_space_taps(r: float, M: int = 4, D: int = 2):
+    """Taps g_1..g_M and the cross tap g_11 of the D-dimensional staggered
+    operator optimised for the leapfrog step at Courant number r = c dt / h
+    (Sec. 3.1 cites a time-space-domain optimised set without printing it;
+    this is our derivation from that principle), D = 2 or 3.
 
-    With b_m = (2m-1)/2 and a = |k| h at angle theta, the scheme's dispersion
-    relation is sin^2(r a / 2) / r^2 = G_x^2 + G_y^2, where
-    G_x = sum_m g_m sin(b_m a cos) + 2 g_11 sin(a cos / 2) cos(a sin).  The taps
-    make it hold
-      - to order a^4 in every direction: consistency at a^2; at a^4 the
-        direction-independent part (the time error r^2 a^4 / 48) and the
-        cos^2 sin^2 part, which asks g_11 = r^2 / 24;
-      - along the axes to order a^(2M): the odd powers a^p, p = 1, 3, ..., 2M-1,
-        of G_x(a, 0) equal those of sin(r a / 2) / r, i.e.
-        sum_m g_m b_m^p + 2 g_11 (1/2)^p = r^(p-1) / 2^p.
-    At r = 0 this is the Taylor set with g_11 = 0.  Returns [g_1..g_M, g_11].
+    With b_m = (2m-1)/2 and a_q = k_q h, the scheme's dispersion relation is
+    sin^2(r |a| / 2) / r^2 = sum_q G_q^2, where
+    G_q = sum_m g_m sin(b_m a_q) + 2 g_11 sin(a_q / 2) sum_{t != q} cos(a_t).
+    Expanding, sum_q G_q^2 = A^2 |a|^2 - A g_11 |a|^4 + (A g_11 - 2 A B) sum_q a_q^4
+    + O(a^6), with A the a_q coefficient and B the a_q^3 one of G_q along an
+    axis.  The taps make the relation hold
+      - to order a^4 in every direction: A = 1/2; the |a|^4 term is the time
+        error r^2 |a|^4 / 48, which asks g_11 = r^2 / 24 in any D; the
+        direction-dependent sum_q a_q^4 term vanishes, g_11 = 2 B;
+      - along the axes to order a^(2M): the odd powers a^p, p = 1, 3, ...,
+        2M-1, of G_q along an axis (where it has D - 1 cross pairs) equal
+        those of sin(r a / 2) / r, i.e.
+        sum_m g_m b_m^p + 2 g_11 (D - 1) (1/2)^p = r^(p-1) / 2^p
+      (the p = 3 condition is g_11 = 2 B again).  At r = 0 this is the Taylor
+    set with g_11 = 0.  Returns [g_1..g_M, g_11].
     """
+    if D not in (2, 3):
+        raise ValueError("D must be 2 or 3")
     r = float(r)
     b = np.array([(2 * m - 1) / 2.0 for m in range(1, M + 1)])
     g11 = r * r / 24.0
     ps = [2 * n + 1 for n in range(M)]
     A = np.array([[bm ** p for bm in b] for p in ps])
-    rhs = np.array([r ** (p - 1) / 2.0 ** p - 2.0 * g11 * 0.5 ** p for p in ps])
+    rhs = np.array([r ** (p - 1) / 2.0 ** p - 2.0 * g11 * (D - 1) * 0.5 ** p for p in ps])
     g = np.linalg.solve(A, rhs)
     return [float(x) for x in g] + [g11]
 

@@ -248,8 +248,14 @@ def test_time_space_taps_reduce_to_taylor_at_zero_courant():
     assert ts[4] == 0.0
 
 
+def _unit(*v):
+    n = math.sqrt(sum(x * x for x in v))
+    return [x / n for x in v]
+
+
 @pytest.mark.parametrize("r", [0.2, 0.4])
-def test_time_space_taps_dispersion_orders(r):
+@pytest.mark.parametrize("D", [2, 3])
+def test_time_space_taps_dispersion_orders(r, D):
     """Sec. 3.1 time-space optimised operator (our derivation): the relative
     phase-velocity error of the full leapfrog scheme falls as (k h)^4 in every
     direction (4th order in time and space off the axes) and as (k h)^8 along
@@ -258,39 +264,60 @@ def test_time_space_taps_dispersion_orders(r):
     second order."""
     h, c0 = 1.0, 1.0
     dt = r * h / c0
-    ts = cf.time_space_taps(r)
+    ts = cf.time_space_taps(r, D=D)
     tay = [float(x) for x in TAPS[:4]] + [0.0]
 
-    def err(taps, a, th):
-        k = [a * math.cos(th), a * math.sin(th)]
-        return an.discrete_omega(k, c0, dt, h, taps) / (c0 * a) - 1.0
+    def err(taps, a, u):
+        return an.discrete_omega([a * x for x in u], c0, dt, h, taps) / (c0 * a) - 1.0
 
-    for th in (math.pi / 8, math.pi / 4, 3 * math.pi / 8):
-        ratio = err(ts, 0.2, th) / err(ts, 0.1, th)
-        assert 14.0 < ratio < 18.0, (th, ratio)             # slope 4
-        assert 3.5 < err(tay, 0.2, th) / err(tay, 0.1, th) < 4.5
-        assert abs(err(ts, 0.2, th)) < abs(err(tay, 0.2, th)) / 100
-    ratio_axis = err(ts, 0.4, 0.0) / err(ts, 0.2, 0.0)
+    if D == 2:
+        dirs = [_unit(math.cos(t), math.sin(t)) for t in (math.pi / 8, math.pi / 4, 3 * math.pi / 8)]
+    else:
+        dirs = [_unit(1, 1, 1), _unit(1, 2, 0), _unit(1, 1, 2), _unit(3, -1, 2)]
+    for u in dirs:
+        ratio = err(ts, 0.2, u) / err(ts, 0.1, u)
+        assert 14.0 < ratio < 18.0, (u, ratio)              # slope 4
+        assert 3.5 < err(tay, 0.2, u) / err(tay, 0.1, u) < 4.5
+        assert abs(err(ts, 0.2, u)) < abs(err(tay, 0.2, u)) / 100
+    axis = [1.0] + [0.0] * (D - 1)
+    ratio_axis = err(ts, 0.4, axis) / err(ts, 0.2, axis)
     assert 200.0 < ratio_axis < 300.0                       # slope 8
 
 
-def test_time_space_taps_through_the_stepper():
-    """The oracle stepper with the time-space taps advances a periodic oblique
-    plane wave (|k| h = 0.91) at the closed-form rate, whose error against
-    c |k| is a twentieth of the Taylor taps' or less."""
+def test_time_space_taps_depend_on_the_dimension():
+    """Along an axis of a 3D grid the cross tap has two transverse pairs, not
+    one: the 2D set there misses the consistency condition (a wave-speed
+    error of order g_11 that does not fall with k h), the 3D set does not."""
+    r = 0.4
+    t2, t3 = cf.time_space_taps(r, D=2), cf.time_space_taps(r, D=3)
+    np.testing.assert_allclose(t2[1:], t3[1:], rtol=0, atol=1e-15)   # only g_1 absorbs it
+    assert abs(t2[0] - t3[0] - 2 * t3[4]) < 1e-15
+    for a in (0.05, 0.1):
+        e2 = an.discrete_omega([a, 0, 0], 1.0, r, 1.0, t2) / a - 1.0
+        e3 = an.discrete_omega([a, 0, 0], 1.0, r, 1.0, t3) / a - 1.0
+        assert abs(e2) > 0.01 and abs(e3) < 1e-9
+
+
+@pytest.mark.parametrize("shape,m", [((48, 40), (5, -4)), ((32, 24, 20), (3, -2, 2))])
+def test_time_space_taps_through_the_stepper(shape, m):
+    """The oracle stepper with the time-space taps of its dimension advances a
+    periodic oblique plane wave at the closed-form rate, whose error against
+    c |k| is a twentieth of the Taylor taps' or less (2D: |k| h = 0.91; 3D:
+    |k| h = 1.01, the cross taps over both transverse axes)."""
     h = 1e-4
     c0, rho0 = 1540.0, 1000.0
     r = 0.4
     dt = r * h / c0
-    shape, m = (48, 40), (5, -4)
-    taps = tuple(cf.time_space_taps(r))
+    D = len(shape)
+    taps = tuple(cf.time_space_taps(r, D=D))
     prob = synth.homogeneous(shape, h, dt, c=c0, rho=rho0)
     prob.bc = ("periodic",) * 3
     prob.taps = taps
     sim = OracleSim(prob)
     kh = [2 * math.pi * mq / nq for mq, nq in zip(m, shape)]
-    X, Y = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), indexing="ij")
-    sim.p[:] = np.cos(kh[0] * X + kh[1] * Y).T.ravel()
+    grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")     # x, y, (z)
+    phase = sum(k * X for k, X in zip(kh, grids))
+    sim.p[:] = np.transpose(np.cos(phase)).ravel()
     ps = [sim.p.copy()]
     for _ in range(4):
         sim.run(1)
@@ -300,7 +327,7 @@ def test_time_space_taps_through_the_stepper():
         sel = np.abs(ps[n]) > 0.3
         ratio = (ps[n + 1][sel] + ps[n - 1][sel]) / (2 * ps[n][sel])
         np.testing.assert_allclose(ratio, math.cos(w * dt), rtol=0, atol=1e-11)
-    w_exact = c0 * math.hypot(*kh) / h
+    w_exact = c0 * math.sqrt(sum(k * k for k in kh)) / h
     w_taylor = an.discrete_omega(kh, c0, dt, h, TAPS)
     assert abs(w / w_exact - 1) < abs(w_taylor / w_exact - 1) / 20
 
