@@ -268,15 +268,18 @@ fw2_status fw2_check_field(fw2_ctx *ctx, float bound, float *max_abs);
  * sizes), FW2_ECUDA (launch failure); fw2_last_error(NULL) explains. */
 fw2_status fw2_field_absmax_noalloc(const float *field, int64_t row_len, int64_t n_rows,
                                     int64_t row_pitch, float *out, void *stream);
-/* Time-space optimised taps of the 2D staggered operator for Courant number
- * r = c dt / h (Sec. 3.1 cites such a set, after Tan and Huang, without
- * printing it; this is the library's derivation from that principle).  Writes
- * g[0..3] = g_{1,0}..g_{4,0} and g[4] = g_{1,1} for fw2_config.g: with them the
- * leapfrog dispersion relation sin^2(w dt/2) = r^2 (G_x^2 + G_y^2) holds to
- * order (k h)^4 in every direction (4th order in time) and to (k h)^8 along the
- * axes; at r = 0 they are the Taylor set.  Pure host computation, no device
- * needed.  Errors: FW2_EINVAL (g NULL, r outside [0, 1)). */
-fw2_status fw2_taps_time_space(double r, double *g);
+/* Time-space optimised taps of the staggered operator of an ndim-dimensional
+ * grid (2 or 3) for Courant number r = c dt / h (Sec. 3.1 cites such a set,
+ * after Tan and Huang, without printing it; this is the library's derivation
+ * from that principle).  Writes g[0..3] = g_{1,0}..g_{4,0} and g[4] = g_{1,1}
+ * for fw2_config.g: with them the leapfrog dispersion relation
+ * sin^2(w dt/2) = r^2 sum_q G_q^2 holds to order (k h)^4 in every direction
+ * (4th order in time) and to (k h)^8 along the axes; at r = 0 they are the
+ * Taylor set.  g_{1,1} = r^2 / 24 in both dimensions; g_{1,0} differs, since
+ * along an axis of a 3D grid the cross tap has two transverse pairs.  Pure
+ * host computation, no device needed.  Errors: FW2_EINVAL (g NULL, r outside
+ * [0, 1), ndim not 2 or 3). */
+fw2_status fw2_taps_time_space(double r, int32_t ndim, double *g);
 /* Self-test of the bounded device-side wait that every pipelined kernel uses
  * on its copy barriers (the paper has no counterpart; it guards against a
  * hung GPU).  Launches one block that initialises an mbarrier nobody ever

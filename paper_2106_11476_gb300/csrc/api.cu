@@ -369,17 +369,19 @@ fw2_status fw2_kernel_path(fw2_ctx *c, int32_t *path) {
   return FW2_OK;
 }
 
-fw2_status fw2_taps_time_space(double r, double *g) {
+fw2_status fw2_taps_time_space(double r, int32_t ndim, double *g) {
   if (!g || !(r >= 0.0 && r < 1.0)) return fail(nullptr, FW2_EINVAL, "g is required and r must lie in [0, 1)");
-  // g_11 from the direction-dependent part of the (k h)^4 term; g_1..g_4
-  // from the odd powers p = 1, 3, 5, 7 of the axial relation
-  //   sum_m g_m b_m^p + 2 g_11 2^-p = r^(p-1) 2^-p,  b_m = (2m - 1) / 2
+  if (ndim != 2 && ndim != 3) return fail(nullptr, FW2_EINVAL, "ndim must be 2 or 3");
+  // g_11 from the |k h|^4 term (the time error; the direction-dependent part
+  // then vanishes); g_1..g_4 from the odd powers p = 1, 3, 5, 7 of the axial
+  // relation, where the cross tap has ndim - 1 transverse pairs:
+  //   sum_m g_m b_m^p + 2 g_11 (ndim - 1) 2^-p = r^(p-1) 2^-p,  b_m = (2m - 1) / 2
   const double g11 = r * r / 24.0;
   double A[4][5];
   for (int row = 0; row < 4; ++row) {
     const int p = 2 * row + 1;
     for (int m = 0; m < 4; ++m) A[row][m] = std::pow((2.0 * m + 1.0) / 2.0, p);
-    A[row][4] = (std::pow(r, p - 1) - 2.0 * g11) / std::pow(2.0, p);
+    A[row][4] = (std::pow(r, p - 1) - 2.0 * g11 * (ndim - 1)) / std::pow(2.0, p);
   }
   for (int col = 0; col < 4; ++col) {  // Gaussian elimination, partial pivoting
     int piv = col;
@@ -475,8 +477,6 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
     cfg.g[3] = -5.0 / 7168.0;
     cfg.g[4] = 0.0;
   }
-  if (cfg.ndim == 3 && cfg.g[4] != 0.0)
-    return fail(nullptr, FW2_EUNSUPPORTED, "the g11 cross term is implemented for 2D grids only");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev < 1)

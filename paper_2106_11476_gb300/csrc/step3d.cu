@@ -41,6 +41,71 @@ __device__ __forceinline__ bool interior_z(const StepParams &P, int k) {
   return k >= Lz && k + Lz < P.nz;
 }
 
+// Twelve values x = i0-4 .. i0+7 of row (j, k) of a cell-indexed field read
+// from global memory under the outer boundary rule (v[4 + e] is x = i0 + e);
+// the cross taps' rows in planes the tile does not stage.
+__device__ __forceinline__ Win12 win12_g(const StepParams &P, const float *f, int i0, int j, int k) {
+  const float4 a = load_chunk(P, f, i0 - 4, j, k), b = load_chunk(P, f, i0, j, k), c = load_chunk(P, f, i0 + 4, j, k);
+  Win12 w;
+  w.v[0] = a.x; w.v[1] = a.y; w.v[2] = a.z; w.v[3] = a.w;
+  w.v[4] = b.x; w.v[5] = b.y; w.v[6] = b.z; w.v[7] = b.w;
+  w.v[8] = c.x; w.v[9] = c.y; w.v[10] = c.z; w.v[11] = c.w;
+  return w;
+}
+
+// Cross taps of Sec. 3.1 over both transverse axes at the faces of the four
+// cells i0..i0+3 of row (j, k): for the face of axis q,
+// g11 sum_{t != q} sum_{s = +-1} (p(c + e_q + s e_t) - p(c + s e_t)).
+// sp row sy is row j of plane k (rows sy +- 1 are j +- 1).
+__device__ __forceinline__ void vel3_cross(const StepParams &P, const float (*sp)[kTX + 8], int sy, int tx, int i0,
+                                           int j, int k, float4 &Dx, float4 &Dy, float4 &Dz) {
+  const Win12 w = win12(sp[sy], tx), up = win12(sp[sy + 1], tx), dn = win12(sp[sy - 1], tx);
+  const Win12 zp = win12_g(P, P.p, i0, j, k + 1), zm = win12_g(P, P.p, i0, j, k - 1);
+  const Win12 zp_up = win12_g(P, P.p, i0, j + 1, k + 1), zm_up = win12_g(P, P.p, i0, j + 1, k - 1);
+  const Win12 zp_dn = win12_g(P, P.p, i0, j - 1, k + 1);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    el(Dx, e) += P.g11h * (((up.v[5 + e] - up.v[4 + e]) + (dn.v[5 + e] - dn.v[4 + e])) +
+                           ((zp.v[5 + e] - zp.v[4 + e]) + (zm.v[5 + e] - zm.v[4 + e])));
+    el(Dy, e) += P.g11h * (((up.v[5 + e] - w.v[5 + e]) + (up.v[3 + e] - w.v[3 + e])) +
+                           ((zp_up.v[4 + e] - zp.v[4 + e]) + (zm_up.v[4 + e] - zm.v[4 + e])));
+    el(Dz, e) += P.g11h * (((zp.v[5 + e] - w.v[5 + e]) + (zp.v[3 + e] - w.v[3 + e])) +
+                           ((zp_up.v[4 + e] - up.v[4 + e]) + (zp_dn.v[4 + e] - dn.v[4 + e])));
+  }
+}
+
+// The same at the cell centres of the pressure half step, for axis q:
+// g11 sum_{t != q} sum_{s = +-1} (v_q(c + s e_t) - v_q(c - e_q + s e_t)).
+__device__ __forceinline__ void prs3_cross(const StepParams &P, int i0, int j, int k, float4 &Dx, float4 &Dy,
+                                           float4 &Dz) {
+  {
+    const Win12 a = win12_g(P, P.v[0], i0, j + 1, k), b = win12_g(P, P.v[0], i0, j - 1, k);
+    const Win12 c = win12_g(P, P.v[0], i0, j, k + 1), d = win12_g(P, P.v[0], i0, j, k - 1);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      el(Dx, e) += P.g11h * (((a.v[4 + e] - a.v[3 + e]) + (b.v[4 + e] - b.v[3 + e])) +
+                             ((c.v[4 + e] - c.v[3 + e]) + (d.v[4 + e] - d.v[3 + e])));
+  }
+  {
+    const Win12 y0 = win12_g(P, P.v[1], i0, j, k), y1 = win12_g(P, P.v[1], i0, j - 1, k);
+    const Win12 zp0 = win12_g(P, P.v[1], i0, j, k + 1), zp1 = win12_g(P, P.v[1], i0, j - 1, k + 1);
+    const Win12 zm0 = win12_g(P, P.v[1], i0, j, k - 1), zm1 = win12_g(P, P.v[1], i0, j - 1, k - 1);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      el(Dy, e) += P.g11h * (((y0.v[5 + e] - y1.v[5 + e]) + (y0.v[3 + e] - y1.v[3 + e])) +
+                             ((zp0.v[4 + e] - zp1.v[4 + e]) + (zm0.v[4 + e] - zm1.v[4 + e])));
+  }
+  {
+    const Win12 z0 = win12_g(P, P.v[2], i0, j, k), z1 = win12_g(P, P.v[2], i0, j, k - 1);
+    const Win12 u0 = win12_g(P, P.v[2], i0, j + 1, k), u1 = win12_g(P, P.v[2], i0, j + 1, k - 1);
+    const Win12 d0 = win12_g(P, P.v[2], i0, j - 1, k), d1 = win12_g(P, P.v[2], i0, j - 1, k - 1);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      el(Dz, e) += P.g11h * (((z0.v[5 + e] - z1.v[5 + e]) + (z0.v[3 + e] - z1.v[3 + e])) +
+                             ((u0.v[4 + e] - u1.v[4 + e]) + (d0.v[4 + e] - d1.v[4 + e])));
+  }
+}
+
 // Momentum factors of the literal nonlinear system (Eq. general5) at the x, y
 // and z faces of the four cells i0..i0+3 of row (j, k): p from the staged
 // plane (row sy of sp) and the z column (pz1 = p at k+1), K from the map with
@@ -278,7 +343,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
   const MT *rho = static_cast<const MT *>(P.rho);
   const MT *ik1 = static_cast<const MT *>(P.ik1);
   const int i0 = x0 + 4 * tx;
-  const bool fast_xy = interior_xy(P, x0, y0);
+  const bool fast_xy = interior_xy(P, x0, y0) && P.g11h == 0.f;  // cross taps: general path
   const int zend = min(z0 + kTZ, P.nz);
 #pragma unroll 1
   for (int k = z0; k < zend; ++k) {
@@ -340,6 +405,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
         el(Dz, e) = d;
       }
     }
+    if (P.g11h != 0.f) vel3_cross(P, sp, sy, tx, i0, j, k, Dx, Dy, Dz);
     float4 bx, by, bz;
     {
       const int lx = 4 * tx;
@@ -396,7 +462,7 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
   const MT *Km = static_cast<const MT *>(P.K);
   const MT *chim = static_cast<const MT *>(P.chi);
   const int i0 = x0 + 4 * tx;
-  const bool fast_xy = interior_xy(P, x0, y0);
+  const bool fast_xy = interior_xy(P, x0, y0) && P.g11h == 0.f;  // cross taps: general path
   const int zend = min(z0 + kTZ, P.nz);
 #pragma unroll 1
   for (int k = z0; k < zend; ++k) {
@@ -453,6 +519,7 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
         el(Dz, e) = d;
       }
     }
+    if (P.g11h != 0.f) prs3_cross(P, i0, j, k, Dx, Dy, Dz);
     const float4 k2 = ldmap4(ik2, c);
     const float4 Sx = stretch4<0, 2, N, MT>(P, P.psi2[0], Dx, k2, c, i0, j, k);
     const float4 Sy = stretch4<1, 2, N, MT>(P, P.psi2[1], Dy, k2, c, i0, j, k);

@@ -635,9 +635,10 @@ Region3 region3_of(const StepParams &P) {
 bool pipe3d_supported(const StepParams &P, int map_kind) {
   // bf16 maps (two stages of ~107 KB fit); N <= 3 keeps the 4D boxes and
   // the stage within shared memory; no periodic axis; the momentum
-  // equation's nonlinear factor is left to the tile kernels
+  // equation's nonlinear factor and the cross taps are left to the tile
+  // kernels
   return P.nz > 1 && map_kind == 1 && P.n_relax >= 0 && P.n_relax <= 3 && !P.periodic[0] && !P.periodic[1] &&
-         !P.periodic[2] && !P.nl_vel;
+         !P.periodic[2] && !P.nl_vel && P.g11h == 0.f;
 }
 
 cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why) {

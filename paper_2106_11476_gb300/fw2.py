@@ -80,7 +80,7 @@ EXPORTS = {
                                            C.c_void_p]),
     "fw2_selftest_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
     "fw2_kernel_path": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
-    "fw2_taps_time_space": (C.c_int, [C.c_double, C.POINTER(C.c_double)]),
+    "fw2_taps_time_space": (C.c_int, [C.c_double, C.c_int32, C.POINTER(C.c_double)]),
     "fw2_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "fw2_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "fw2_batch_synchronize": (C.c_int, [C.c_void_p]),
@@ -277,10 +277,11 @@ def fw2_profile_read(ctx):
     return tv.value, nv.value, tp.value, np_.value
 
 
-def fw2_taps_time_space(r: float) -> tuple:
-    """(g_1..g_4, g_11) of the time-space optimised 2D operator at Courant number r."""
+def fw2_taps_time_space(r: float, ndim: int = 2) -> tuple:
+    """(g_1..g_4, g_11) of the time-space optimised operator of an ndim-D grid
+    at Courant number r."""
     g = (C.c_double * 5)()
-    _check(lib().fw2_taps_time_space(float(r), g))
+    _check(lib().fw2_taps_time_space(float(r), int(ndim), g))
     return tuple(g)
 
 

@@ -266,6 +266,35 @@ def test_parity_3d(fw2):
 
 
 @pytest.mark.parametrize("maps", ["f32", "bf16"])
+def test_parity_3d_time_space_taps(fw2, maps):
+    """The 3D time-space optimised operator (Sec. 3.1; cross taps over both
+    transverse axes, library taps for a 3D grid at the problem's Courant
+    number) against the oracle with the same taps; the pipelined 3D half
+    steps leave the cross taps to the tile kernels."""
+    prob = small_3d(n=(70, 40, 36), steps=80)
+    r = float(np.max(prob.c)) * prob.dt / prob.h
+    prob.taps = tuple(fw2.fw2_taps_time_space(r, 3))
+    assert prob.taps[4] > 0
+    compare_run(fw2, prob, 80, maps=maps, kernel_path="pipe" if maps == "bf16" else "auto")
+    sim = fw2.Simulation(prob, map_precision="bf16", kernel_path="pipe")
+    sim.step(1)
+    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    sim.close()
+
+
+def test_parity_3d_periodic_lossless_cross_taps(fw2):
+    """N = 0, periodic on all three axes, g11 != 0, from a random state: the
+    cross taps wrap across every face of the grid."""
+    prob = synth.homogeneous((52, 36, 28), 1e-4, 0.0)
+    rng = np.random.default_rng(4)
+    prob.c = (1500 + 200 * rng.random(prob.grid_shape)).astype(np.float32)
+    prob.dt = 0.3 * 1e-4 / float(prob.c.max())
+    prob.bc = ("periodic",) * 3
+    prob.taps = tuple(fw2.fw2_taps_time_space(0.3, 3))
+    compare_run(fw2, prob, 40, state=synth.random_state(prob, seed=8))
+
+
+@pytest.mark.parametrize("maps", ["f32", "bf16"])
 def test_parity_3d_literal(fw2, maps):
     """Both nonlinear factors in 3D (tile kernels; the pipelined 3D half
     steps leave this mode to them)."""
