@@ -57,13 +57,15 @@ def strip_cell_counts(shape, L):
     return out
 
 
-def algorithmic_bytes(shape, N, L, nl, map_bytes=4):
+def algorithmic_bytes(shape, N, L, nl, map_bytes=4, nl_vel=False):
     """Compulsory DRAM bytes of one launch of the velocity and of the pressure kernel.
 
     Every streamed array is read once and every updated array written once;
     the stencil operand (p, or v_q) is read once.  Coefficient a, b pairs of
     an axis come from its boundary strip inside the C-PML region, otherwise
     from the interior maps (read once per cell when any axis needs them).
+    The literal nonlinear system's momentum factor adds the K map to the
+    velocity half step (nl_vel).
     """
     nd = len(shape)
     classes = strip_cell_counts(shape, L)
@@ -72,7 +74,7 @@ def algorithmic_bytes(shape, N, L, nl, map_bytes=4):
         sets = len(axes_in) + (1 if len(axes_in) < nd else 0)
         coef += cnt * sets * 2 * N * map_bytes
     n = int(np.prod(shape))
-    vel = n * (4 + map_bytes + map_bytes + nd * 8 + nd * N * 8) + coef
+    vel = n * (4 + map_bytes + map_bytes + (map_bytes if nl_vel else 0) + nd * 8 + nd * N * 8) + coef
     prs = n * (nd * 4 + map_bytes + (map_bytes if nl else 0) + map_bytes + 8 + nd * N * 8) + coef
     return vel, prs
 
@@ -104,7 +106,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("step2d.cu", "step2d_pipe.cu", "tile2d.cuh", "async.cuh", "maps.cuh", "tmap.h", "step3d.cu",
+    for f in ("step2d.cu", "step2d_pipe.cu", "tile2d.cuh", "async.cuh", "maps.cuh", "tmap.h", "step3d.cu", "step3d_pipe.cu",
               "coef.cuh", "fw2_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2106_11476_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
@@ -259,8 +261,18 @@ def run_fw2(args, rank, world, dist):
         maps, mbytes, kv, kp = "f32", 4, "vel2d", "prs2d"
         workload = (f"2D heterogeneous nonlinear abdominal wall, {n}x{n} cells at lambda/12 for 3 MHz, "
                     f"N=4 mechanisms, beta 4-6, 128-element focused array, element-mean traces, FP32 maps")
+    if args.nl:
+        prob.nl_mode = args.nl
+        workload += f", nonlinear mode {args.nl}"
+        if args.nl != "off" and prob.beta is None:
+            prob.beta = np.full(prob.grid_shape, 4.0, np.float32)
+            workload += " (beta = 4 everywhere)"
+    if args.taps == "time-space":
+        r = float(np.max(prob.c)) * prob.dt / prob.h
+        prob.taps = tuple(fw2.fw2_taps_time_space(r, prob.ndim))
+        workload += f", time-space optimised taps at r = {r:.3f}"
     vel_b, prs_b = algorithmic_bytes(prob.shape, prob.nrelax, prob.pml_transition + prob.pml_bound,
-                                     prob.nl_mode != "off", map_bytes=mbytes)
+                                     prob.nl_mode != "off", map_bytes=mbytes, nl_vel=prob.nl_mode == "literal")
     if maps == "idx":
         # one uint8 index per cell replaces every interior map; strips stay float
         vel_b, prs_b = algorithmic_bytes_indexed(prob.shape, prob.nrelax, prob.pml_transition + prob.pml_bound,
@@ -300,7 +312,8 @@ def run_fw2(args, rank, world, dist):
     dom_bytes = vel_b if dom == kv else prs_b
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    traffic = committed_traffic(f"{args.workload}:{maps}:{n}:{dom}")
+    variant = ("" if args.taps == "taylor" else f":{args.taps}") + (f":{args.nl}" if args.nl else "")
+    traffic = committed_traffic(f"{args.workload}:{maps}:{n}:{dom}{variant}")
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": round(dom_ms, 5),
@@ -371,7 +384,7 @@ def run_fw2(args, rank, world, dist):
            "data": data,
            "config": {"workload": workload,
                       "grid": list(prob.shape), "n_relax": prob.nrelax, "nl_mode": prob.nl_mode, "map_precision": maps,
-                      "kernel_path": args.kernel_path,
+                      "kernel_path": args.kernel_path, "taps": args.taps,
                       "pml_cells": prob.pml_transition + prob.pml_bound,
                       "l2": "state and maps (>2.5 GB) exceed L2; no flush needed",
                       "parallelism": f"replicas x{world} (one transmit event per GPU)"},
@@ -599,6 +612,10 @@ def main():
                     help="override the map storage of the workload")
     ap.add_argument("--kernel-path", default="auto", choices=["auto", "tile", "pipe"],
                     help="2D half-step kernels (bitwise the same results)")
+    ap.add_argument("--taps", default="taylor", choices=["taylor", "time-space"],
+                    help="staggered taps: 8th-order Taylor, or the time-space optimised set with cross taps")
+    ap.add_argument("--nl", default=None, choices=["off", "pressure", "westervelt", "literal"],
+                    help="override the workload's nonlinear mode")
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
