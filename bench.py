@@ -106,8 +106,8 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("step2d.cu", "step2d_pipe.cu", "tile2d.cuh", "async.cuh", "maps.cuh", "tmap.h", "step3d.cu", "step3d_pipe.cu",
-              "coef.cuh", "fw2_internal.cuh"):
+    for f in ("step2d.cu", "step2d_pipe.cu", "tile2d.cuh", "async.cuh", "maps.cuh", "tmap.h", "step3d.cu",
+              "step3d_pipe.cu", "coef.cuh", "fw2_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2106_11476_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

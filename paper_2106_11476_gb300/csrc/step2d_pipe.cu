@@ -79,7 +79,9 @@ struct VelStage {
   static constexpr int kR = round32(kRb);
   static constexpr int kS = kNs * kArr;
   static constexpr int kI = kIdx ? (kHT + 1) * kIW / 4 : 0;  // index bytes / 4
-  static constexpr int kFloats = round32(kP + kR + kS + kI);
+  // dense, literal nonlinear system: K box of the density box's shape
+  static constexpr int kK = kIdx ? 0 : kR;
+  static constexpr int kFloats = round32(kP + kR + kS + kI + kK);
 };
 
 // pressure: v_x rows y0-1 .. y0+kHT, v_y rows y0-4 .. y0+kHT+2; streamed
@@ -100,12 +102,13 @@ struct PrsStage {
 };
 
 // Bytes one stage receives through the tensor maps (the chi box only with
-// the nonlinear term).
+// the nonlinear term, the velocity's K box only with the literal system).
 template <int N, typename Maps, bool VEL>
-__host__ __device__ constexpr unsigned stage_bytes(bool nl) {
+__host__ __device__ constexpr unsigned stage_bytes(bool nl, bool nl_vel) {
   if (VEL) {
     using S = VelStage<N, Maps>;
-    return 4u * (S::kPb + (S::kIdx ? 0 : S::kRb) + S::kNs * kArr) + (S::kIdx ? (kHT + 1) * kIW : 0);
+    return 4u * (S::kPb + (S::kIdx ? 0 : S::kRb) + S::kNs * kArr) + (S::kIdx ? (kHT + 1) * kIW : 0) +
+           ((!S::kIdx && nl_vel) ? 4u * S::kRb : 0u);
   } else {
     using S = PrsStage<N, Maps>;
     return 4u * (S::kXb + S::kYb + S::kNs * kArr) - ((!S::kIdx && !nl) ? 4u * kArr : 0u) +
@@ -120,7 +123,7 @@ template <int N, typename Maps, bool VEL>
 __device__ __forceinline__ void issue_stage(const StepParams &P, const PipeMaps &T, float *st, uint64_t *bar,
                                             int x0, int y0) {
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(bar, stage_bytes<N, Maps, VEL>(P.nl != 0));
+  mbar_arrive_expect_tx(bar, stage_bytes<N, Maps, VEL>(P.nl != 0, P.nl_vel != 0));
   if (VEL) {
     using S = VelStage<N, Maps>;
     tma_load_2d(st, &T.m[0], x0 - 4, y0 - 3, bar);
@@ -138,6 +141,7 @@ __device__ __forceinline__ void issue_stage(const StepParams &P, const PipeMaps 
         tma_load_3d(ss + (3 + 2 * N) * kArr, &T.m[7], x0, y0, 0, bar);
         tma_load_3d(ss + (3 + 3 * N) * kArr, &T.m[8], x0, y0, 0, bar);
       }
+      if (P.nl_vel) tma_load_2d(ss + S::kS, &T.m[9], x0, y0, bar);  // K, density-box shape
     } else {
       tma_load_2d(ss + S::kS, &T.m[1], x0, y0, bar);  // tissue index
     }
@@ -351,18 +355,19 @@ __device__ __forceinline__ FaceRho face_rho(const StepParams &P, const float *ta
 
 // Momentum factors of the literal nonlinear system (Eq. general5) at the x
 // and y faces of the pair: p from the staged operand (cell e at column
-// lx + 4 + e of row sy; zero beyond the grid), K from the map (float maps) or
-// the staged index (index form), neighbours clamped to the last cell.
+// lx + 4 + e of row sy; zero beyond the grid), K from the staged K box (float
+// maps; the density box's shape) or the staged index (index form),
+// neighbours clamped to the last cell.
 template <typename Maps, bool EDGE>
 __device__ __forceinline__ void mom_factors2(const StepParams &P, const float *tab, const unsigned char *si,
-                                             const float *sp, int sy, int lx, int ly, int x0, int y0, float2 &fx,
-                                             float2 &fy) {
+                                             const float *sk, const float *sp, int sy, int lx, int ly, int x0,
+                                             int y0, float2 &fx, float2 &fy) {
   const float *row = sp + sy * kCW + lx + 4, *up = sp + (sy + 1) * kCW + lx + 4;
   const int mx = P.nx - 1 - x0, my = P.ny - 1 - y0;
   const int r1 = EDGE ? min(ly + 1, my) : ly + 1;
   auto K = [&](int r, int cc) -> float {
     if constexpr (IsIdx<Maps>::value) return tab[kTabK * kTissues + si[r * kIW + cc]];
-    else return ldmap(static_cast<const float *>(P.K), (long long)(y0 + r) * P.pitch + x0 + cc);
+    else return sk[r * kRWp + cc];
   };
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -527,7 +532,7 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
   const FaceRho fr = face_rho<Maps, EDGE>(P, tab, sr, si, x0, y0, lx, ly);
   if (P.nl_vel) {
     float2 fx, fy;
-    mom_factors2<Maps, EDGE>(P, tab, si, sp, ly + 3, lx, ly, x0, y0, fx, fy);
+    mom_factors2<Maps, EDGE>(P, tab, si, ss + S::kS, sp, ly + 3, lx, ly, x0, y0, fx, fy);
     vx.x = vel_upd(vx.x, P.two_dt / (fr.r0 + fr.r1), Sx.x, fx.x);
     vx.y = vel_upd(vx.y, P.two_dt / (fr.r1 + fr.r2), Sx.y, fx.y);
     vy.x = vel_upd(vy.x, P.two_dt / (fr.r0 + fr.u0), Sy.x, fy.x);
@@ -988,6 +993,7 @@ cudaError_t build_pipe2d_maps(const StepParams &P, int map_kind, PipeMaps *vel, 
   ok = ok && encode(&vel->m[0], P.p, P, 2, 1, S, kCW, kHT + 7, 1);
   if (dense) ok = ok && encode(&vel->m[1], P.rho, P, 2, 1, S, kRWp, kHT + 1, 1);
   else ok = ok && encode(&vel->m[1], P.tissue, P, 2, 1, S, kIW, kHT + 1, 1, true);
+  if (dense && P.nl_vel) ok = ok && encode(&vel->m[9], P.K, P, 2, 1, S, kRWp, kHT + 1, 1);
   ok = ok && encode(&vel->m[2], P.v[0], P, 2, 1, S, kTX, kHT, 1);
   ok = ok && encode(&vel->m[3], P.v[1], P, 2, 1, S, kTX, kHT, 1);
   if (N > 0) {

@@ -9,7 +9,8 @@ constexpr int kPipeMaps = 10;
 
 // velocity: 0 p (136 x 15 halo box), 1 rho (132 x 9; tissue-index form: the
 //   uint8 index, 144 x 9), 2 v_x, 3 v_y, 4 psi1_x (128 x 8 x N), 5 psi1_y,
-//   6 1/kappa1, 7 a1 (128 x 8 x N), 8 b1
+//   6 1/kappa1, 7 a1 (128 x 8 x N), 8 b1, 9 K (132 x 9, float maps with the
+//   literal nonlinear system)
 // pressure: 0 v_x (136 x 10 halo box), 1 v_y (136 x 15), 2 p, 3 psi2_x,
 //   4 psi2_y, 5 1/kappa2 (tissue-index form: the uint8 index), 6 K, 7 chi,
 //   8 a2, 9 b2
