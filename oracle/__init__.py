@@ -28,5 +28,7 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   pre-shock Poisson solution of the inviscid Burgers equation (Sec. 4.5),
   with the effective coefficient of each nonlinear mode.
 * staggered-grid placement of rho, kappa and the PML coordinate (not printed
-  in the paper): parity unpinned beyond the readings stated in the design notes.
+  in the paper): parity unpinned beyond the discrete energy conservation,
+  which fixes the pairing of K with the cell centres and of the face density
+  (mean of the two cells) with the faces.
 """

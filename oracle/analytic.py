@@ -3,11 +3,12 @@
 * continuous dispersion relation of the multiple-relaxation model,
   Eq. (dispersion_relations) with Eq. (gamma1), Sec. 3.2 / appendix A;
 * power-law attenuation target and its Kramers-Kronig phase velocity
-  (Sec. 4.1; nearly-local form, see the design notes' reading R1);
+  (Sec. 4.1; nearly-local form 1/c = 1/c0 + alpha0' tan(pi y / 2)
+  (omega^(y-1) - omega_ref^(y-1)), and its y = 1 limit);
 * the closed-form numerical dispersion relation of the lossless staggered
   leapfrog scheme of Sec. 3.1;
-* the pre-shock (Poisson) solution of the inviscid Burgers equation used as
-  the nonlinear reference of Sec. 4.5.
+* the pre-shock (Poisson) solution of the inviscid Burgers equation and a
+  Rusanov finite-volume solution of it, the nonlinear references of Sec. 4.5.
 """
 from __future__ import annotations
 
@@ -112,6 +113,46 @@ def burgers_poisson(p_in, t, x, beta_eff, rho0, c0, iters: int = 200):
     for _ in range(iters):
         p = p_in(tau + coef * p)
     return p
+
+
+def burgers_rusanov(p_in, dtau, x, beta_eff, rho0, c0, cfl: float = 0.4):
+    """The inviscid Burgers equation of a progressive wave, solved numerically
+    with a Rusanov (local Lax-Friedrichs) finite-volume scheme, the reference
+    solver of Sec. 4.5.
+
+    In retarded time tau = t - x/c0 the wave obeys dp/dx = b p dp/dtau with
+    b = beta_eff / (rho0 c0^3), a conservation law in the marching variable x:
+    dp/dx + dF(p)/dtau = 0, F(p) = -b p^2 / 2.  `p_in` holds p at x = 0 on a
+    uniform tau grid of spacing `dtau` (the pulse well inside it; p = 0 held at
+    both ends).  Cell interfaces take piecewise-linear states with minmod
+    slopes (second order away from extrema) and the Rusanov flux
+    F* = (F(pL) + F(pR))/2 - a (pR - pL)/2, a = |b| max(|pL|, |pR|); the march
+    in x is the two-stage strong-stability-preserving Runge-Kutta scheme with
+    steps dx = cfl dtau / (|b| max |p|).  Returns p at distance x on the same
+    tau grid.
+    """
+    u = np.array(p_in, np.float64)
+    b = beta_eff / (rho0 * c0 ** 3)
+
+    def rhs(v):
+        w = np.concatenate([[0.0, 0.0], v, [0.0, 0.0]])
+        d1, d2 = w[1:-1] - w[:-2], w[2:] - w[1:-1]
+        slope = np.where(d1 * d2 > 0, np.sign(d1) * np.minimum(np.abs(d1), np.abs(d2)), 0.0)
+        c = w[1:-1]
+        pl = c[:-1] + 0.5 * slope[:-1]   # left state at interface i+1/2
+        pr = c[1:] - 0.5 * slope[1:]     # right state
+        a = abs(b) * np.maximum(np.abs(pl), np.abs(pr))
+        flux = 0.5 * (-0.5 * b * pl ** 2 - 0.5 * b * pr ** 2) - 0.5 * a * (pr - pl)
+        return -(flux[1:] - flux[:-1]) / dtau
+
+    done = 0.0
+    while done < x:
+        amax = abs(b) * max(float(np.max(np.abs(u))), 1e-300)
+        dx = min(cfl * dtau / amax, x - done)
+        u1 = u + dx * rhs(u)
+        u = 0.5 * (u + u1 + dx * rhs(u1))
+        done += dx
+    return u
 
 
 def discrete_wavenumber_1d(freqs_hz, c, h, dt, p, taps, centred=True):

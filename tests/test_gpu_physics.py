@@ -85,3 +85,60 @@ def test_cpml_reflection_by_incidence_angle(fw2):
             assert db < r0_db * math.cos(math.radians(theta)), (theta, r)
     # rising toward grazing incidence beyond 45 degrees
     assert r[THETAS.index(80)] > r[THETAS.index(70)] > r[THETAS.index(60)] > r[THETAS.index(45)]
+
+
+def _harmonics(sig, dt, f0, n=7):
+    F = np.fft.rfft(sig, 1 << 17)
+    f = np.fft.rfftfreq(1 << 17, dt)
+    return np.array([abs(F[int(np.argmin(np.abs(f - k * f0)))]) for k in range(1, n + 1)])
+
+
+@pytest.mark.parametrize("mode,beta,sigma", [("literal", 11.0, 0.7), ("pressure", 10.5, 0.9)])
+def test_nonlinear_plane_wave_against_rusanov(fw2, mode, beta, sigma):
+    """Sec. 4.5 on the GPU path: a plane wave (a 2D grid periodic across the
+    beam, one source row) of a 1 MHz, 4-cycle, 1 MPa pulse, 40 points per
+    period, CFL 0.1.  The harmonics 1-7 at the far sensor that carry energy
+    (1 % of the fundamental or more) match the Rusanov solution of the
+    inviscid Burgers equation driven by the near-sensor waveform within
+    0.3 dB, with the effective coefficient of the mode (both factors of
+    Eqs. general5-general6: beta - 1; pressure factor only: beta - 1/2)."""
+    from scipy.interpolate import CubicSpline
+    from oracle import analytic as an
+    c0, rho0, f0, p0, ppw, cfl = 1500.0, 1000.0, 1e6, 1e6, 40, 0.1
+    h = c0 / f0 / ppw
+    dt = cfl * h / c0
+    beff = beta - (1.0 if mode == "literal" else 0.5)
+    gap = int(round(sigma / (beff * p0 / (rho0 * c0 ** 2) * 2 * math.pi * f0 / c0) / h))
+    s0, s1 = 2000, 2100      # the wave reflected at x = 0 arrives after the record ends
+    s2 = s1 + gap
+    nx, ny = s2 + 400, 16
+    steps = int((s2 - s0 + 300) / cfl + 8 / f0 / dt)
+    sig = synth.gaussian_pulse(steps, dt, f0, 4.0, 1.0)
+
+    def run(nl, amp):
+        prob = synth.homogeneous((nx, ny), h, dt, c=c0, rho=rho0, beta=beta)
+        prob.nl_mode = nl
+        prob.bc = ("zero", "periodic", "zero")
+        prob.sources = [synth.Source("p", synth.flat_index((nx, ny), s0, np.arange(ny)),
+                                     np.zeros(ny, np.int32), (sig * amp)[:, None].astype(np.float32))]
+        prob.sensors = synth.Sensors(synth.flat_index((nx, ny), [s1, s2], ny // 2), np.arange(2, dtype=np.int32), 2)
+        prob.n_steps = steps
+        s = fw2.Simulation(prob)
+        s.step(steps)
+        tr = s.trace.cpu().numpy().astype(np.float64)
+        s.close()
+        return tr
+
+    lin = run("off", 1.0)
+    tr = run(mode, p0 / np.max(np.abs(lin[:, 0])))
+    t = (np.arange(steps) + 1) * dt
+    spline = CubicSpline(t, tr[:, 0])
+    tp = t[int(np.argmax(np.abs(tr[:, 0])))]
+    fine = np.arange(tp - 10 / f0, tp + 10 / f0, 1 / f0 / 300)
+    ru = an.burgers_rusanov(spline(fine), 1 / f0 / 300, gap * h, beff, rho0, c0)
+    pred = np.interp(t - gap * h / c0, fine, ru, left=0.0, right=0.0)
+    mg, mp = _harmonics(tr[:, 1], dt, f0), _harmonics(pred, dt, f0)
+    keep = mp >= 0.01 * mp[0]
+    d = 20 * np.log10(mg / mp)[keep]
+    assert keep.sum() >= 5
+    assert np.max(np.abs(d)) < 0.3, d
