@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kS = G::kStages, kStage = G::kStage;
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t bar[kS];
-  __shared__ int ok;
+  __shared__ int ok[kS];  // per stage: thread 0 never rewrites a flag a thread has yet to read
   // TMA destinations need 128-byte alignment: round the base up (the launch
   // adds 128 bytes of slack)
   float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -677,9 +677,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   int xp = -1, yp = -1;  // previous half tile of this block
 #pragma unroll 1
   for (; h < nh; h += gridDim.x) {
-    if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    if (tid == 0) ok[s] = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
     __syncthreads();
-    if (!ok) {
+    if (!ok[s]) {
       if (tid == 0) {
         report_status(P.status, kStatusWaitTimeout);
         for (int q = 0; q < kS; ++q)
@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t bar[kS];
   __shared__ __align__(16) StepParams sP;
-  __shared__ int ok;
+  __shared__ int ok[kS];  // per stage: thread 0 never rewrites a flag a thread has yet to read
   float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float *tab = smem + kS * kStage;
   const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -771,9 +771,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   int4 prev = make_int4(-1, 0, 0, 0);
 #pragma unroll 1
   for (; h < h_end; ++h) {
-    if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    if (tid == 0) ok[s] = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
     __syncthreads();
-    if (!ok) {
+    if (!ok[s]) {
       if (tid == 0) {
         report_status(Ps[units[h].x].status, kStatusWaitTimeout);
         for (int q = 0; q < kS; ++q)

@@ -2,17 +2,23 @@
 // same arithmetic as step3d.cu (bitwise the same results), one launch per
 // half step, one block of 512 threads per SM (two x cells per thread).
 //
-// Work unit: a 128 x 8 half tile of one z plane, x fastest, then y, then z.
-// For a coming unit one thread issues tiled TMA tensor copies into a free
-// stage of a two-stage ring (one box per array): the xy operand plane with
-// its halo, the operand's own 8-plane z column (x and y taps from the halo
-// plane, z taps from the column; the column's planes are the neighbouring
-// units' planes, so their re-reads come from L2), the density of the plane
-// and of the next one, the velocity (or pressure) of the unit, all 3N memory
-// variables of the half step in one 4D box, and the bf16 maps (a and b of the
-// N mechanisms in one 4D box each).  Copies complete on the stage's mbarrier
-// while all threads compute the current unit from the other stage; no
-// computing thread issues a global load outside the C-PML strips.
+// Work unit: a 128 x 8 half tile of one z plane.  A block marches a column
+// of units through z (a work item: one xy position and a range of planes;
+// items are numbered xy position first, so the blocks running at one time
+// hold neighbouring columns at about the same depth and share the halo rows
+// in L2).  The operand planes a unit's z taps need stay in a ring of nine
+// plane slots in shared memory (velocity: p planes k-3 .. k+4 with their xy
+// halo, which also give the x and y taps; pressure: v_z planes k-4 .. k+3), so
+// each unit adds one plane.  For a coming unit one thread issues tiled TMA
+// tensor copies, one box per array, into a free stage of a two-stage ring:
+// the operand plane the unit adds (into the plane ring), the density of the
+// plane and of the next one, the velocity (or pressure) of the unit, all 3N
+// memory variables of the half step in one 4D box, and the bf16 maps (a and b
+// of the N mechanisms in one 4D box each).  The first unit of an item loads
+// its eight planes after the previous unit's compute.  Copies complete on
+// the stage's mbarrier while all threads compute the current unit from the
+// other stage; no computing thread issues a global load outside the C-PML
+// strips.
 //
 // Boundaries as in the 2D pipeline: the copies read zero outside the grid;
 // units at the grid's edge or in a C-PML strip clamp the density to the last
@@ -38,77 +44,92 @@ constexpr int round32(int n) { return (n + 31) & ~31; }  // floats: 128-byte reg
 constexpr int fl(int bytes) { return (bytes + 3) / 4; }
 
 // ------------------------------------------------------------- stages ---
-// velocity: p halo plane [15][136] (rows y0-3 .. y0+11), p column [8][8][128]
-// (planes k-3 .. k+4), density bf16 [2][9][136] (planes k, k+1), v [3][8][128],
-// psi1 [3N][8][128], 1/kappa1 bf16 [8][128], a1, b1 bf16 [N][8][128]
+constexpr int kSlots = 9;  // plane ring: the eight planes of a unit and the one the next unit adds
+
+__host__ __device__ constexpr int ring_slot(int k) { return ((k % kSlots) + kSlots) % kSlots; }
+
+// velocity stage: density bf16 [2][9][136] (planes k, k+1), v [3][8][128],
+// psi1 [3N][8][128], 1/kappa1 bf16 [8][128], a1, b1 bf16 [N][8][128];
+// plane ring: p planes [15][136] (rows y0-3 .. y0+11, columns x0-4 ..)
 template <int N>
 struct Vel3 {
-  static constexpr int kHalo = round32((kHT + 7) * kCW);
-  static constexpr int kCol = 8 * kArr;
   static constexpr int kRho = round32(fl(2 * (kHT + 1) * kRWb * 2));
   static constexpr int kV = 3 * kArr;
   static constexpr int kPsi = 3 * N * kArr;
   static constexpr int kK = round32(fl(kArr * 2));
   static constexpr int kAB = round32(fl(N * kArr * 2));
-  static constexpr int oHalo = 0, oCol = oHalo + kHalo, oRho = oCol + kCol, oV = oRho + kRho, oPsi = oV + kV,
-                       oK = oPsi + kPsi, oA = oK + kK, oB = oA + kAB;
+  static constexpr int oRho = 0, oV = oRho + kRho, oPsi = oV + kV, oK = oPsi + kPsi, oA = oK + kK, oB = oA + kAB;
   static constexpr int kFloats = round32(oB + kAB);
-  static constexpr unsigned kBytes =
-      4u * ((kHT + 7) * kCW + kCol + kV + kPsi) + 2u * (2 * (kHT + 1) * kRWb + kArr + 2 * N * kArr);
+  static constexpr unsigned kBytes = 4u * (kV + kPsi) + 2u * (2 * (kHT + 1) * kRWb + kArr + 2 * N * kArr);
+  static constexpr int kPlane = round32((kHT + 7) * kCW);
+  static constexpr unsigned kPlaneBytes = 4u * (kHT + 7) * kCW;
 };
 
-// pressure: v_x plane [8][136] (x halo), v_y plane [15][128] (rows y0-4 ..),
-// v_z column [8][8][128] (planes k-4 .. k+3), p [8][128], psi2 [3N][8][128],
-// 1/kappa2, K, chi bf16 [8][128], a2, b2 bf16 [N][8][128]
+// pressure stage: v_x plane [8][136] (x halo), v_y plane [15][128] (rows
+// y0-4 ..), p [8][128], psi2 [3N][8][128], 1/kappa2, K, chi bf16 [8][128],
+// a2, b2 bf16 [N][8][128]; plane ring: v_z planes [8][128]
 template <int N>
 struct Prs3 {
   static constexpr int kVx = round32(kHT * kCW);
   static constexpr int kVy = round32((kHT + 7) * kTX);
-  static constexpr int kCol = 8 * kArr;
   static constexpr int kP = kArr;
   static constexpr int kPsi = 3 * N * kArr;
   static constexpr int kK = round32(fl(kArr * 2));
   static constexpr int kAB = round32(fl(N * kArr * 2));
-  static constexpr int oVx = 0, oVy = oVx + kVx, oCol = oVy + kVy, oP = oCol + kCol, oPsi = oP + kP,
-                       oIk = oPsi + kPsi, oKm = oIk + kK, oChi = oKm + kK, oA = oChi + kK, oB = oA + kAB;
+  static constexpr int oVx = 0, oVy = oVx + kVx, oP = oVy + kVy, oPsi = oP + kP, oIk = oPsi + kPsi,
+                       oKm = oIk + kK, oChi = oKm + kK, oA = oChi + kK, oB = oA + kAB;
   static constexpr int kFloats = round32(oB + kAB);
   static constexpr unsigned kBytesNoChi =
-      4u * (kHT * kCW + (kHT + 7) * kTX + kCol + kP + kPsi) + 2u * (2 * kArr + 2 * N * kArr);
+      4u * (kHT * kCW + (kHT + 7) * kTX + kP + kPsi) + 2u * (2 * kArr + 2 * N * kArr);
+  static constexpr int kPlane = kArr;
+  static constexpr unsigned kPlaneBytes = 4u * kArr;
 };
-
 
 template <int N, bool VEL>
 struct Ring3 {
   static constexpr int kStage = VEL ? Vel3<N>::kFloats : Prs3<N>::kFloats;
-  static constexpr size_t kBytes = sizeof(float) * (2 * (size_t)kStage) + 128;
+  static constexpr int kPlane = VEL ? Vel3<N>::kPlane : Prs3<N>::kPlane;
+  static constexpr unsigned kPlaneBytes = VEL ? Vel3<N>::kPlaneBytes : Prs3<N>::kPlaneBytes;
+  static constexpr size_t kBytes = sizeof(float) * (2 * (size_t)kStage + (size_t)kSlots * kPlane) + 128;
 };
 
-// Work: units of 128 x 8 cells per plane, x fastest.
+// Work items: a column of units (xy position, x fastest) and a range of
+// planes; item it covers column it % ncols, planes seg * seglen ..
 struct Region3 {
   int nx, ny, nz, Lx, Ly, Lz;
-  int tnx, nhy;  // x tiles, half-tile rows per plane
-  __device__ __forceinline__ long long units() const { return (long long)tnx * nhy * nz; }
-  __device__ __forceinline__ void origin(long long u, int &x0, int &y0, int &k) const {
-    const int per = tnx * nhy;
-    k = (int)(u / per);
-    const int r = (int)(u - (long long)k * per);
-    x0 = (r % tnx) * kTX;
-    y0 = (r / tnx) * kHT;
+  int tnx, nhy;      // x tiles, half-tile rows per plane
+  int seglen, nseg;  // planes per item, items per column
+  __device__ __forceinline__ long long items() const { return (long long)tnx * nhy * nseg; }
+  __device__ __forceinline__ void item(long long it, int &x0, int &y0, int &k0, int &k1) const {
+    const int ncols = tnx * nhy;
+    const int col = (int)(it % ncols), seg = (int)(it / ncols);
+    x0 = (col % tnx) * kTX;
+    y0 = (col / tnx) * kHT;
+    k0 = seg * seglen;
+    k1 = min(nz, k0 + seglen);
   }
   __device__ __forceinline__ bool interior(int x0, int y0, int k) const {
     return x0 >= Lx && x0 + kTX + Lx <= nx && y0 >= Ly && y0 + kHT + Ly <= ny && k >= Lz && k + Lz < nz;
   }
 };
 
+// first plane of the operand ring a unit at plane k reads (8 planes)
+template <bool VEL>
+__host__ __device__ constexpr int ring_first(int k) { return VEL ? k - 3 : k - 4; }
+
+// Issue the copies of a unit at (x0, y0, k): its stage and the operand
+// planes k_lo .. k_hi of the plane ring (one plane, or eight for the first
+// unit of an item), all completing on the stage's mbarrier.
 template <int N, bool VEL>
-__device__ __forceinline__ void issue3(const PipeMaps &T, float *st, uint64_t *bar, int x0, int y0, int k,
-                                       bool nl) {
+__device__ __forceinline__ void issue3(const PipeMaps &T, float *st, float *ring, uint64_t *bar, int x0, int y0,
+                                       int k, int k_lo, int k_hi, bool nl) {
+  using G = Ring3<N, VEL>;
   fence_proxy_async_smem();
+  const unsigned planes = G::kPlaneBytes * (unsigned)(k_hi - k_lo + 1);
   if (VEL) {
     using S = Vel3<N>;
-    mbar_arrive_expect_tx(bar, S::kBytes);
-    tma_load_3d(st + S::oHalo, &T.m[0], x0 - 4, y0 - 3, k, bar);
-    tma_load_3d(st + S::oCol, &T.m[1], x0, y0, k - 3, bar);
+    mbar_arrive_expect_tx(bar, S::kBytes + planes);
+    for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[0], x0 - 4, y0 - 3, kp, bar);
     tma_load_3d(st + S::oRho, &T.m[2], x0, y0, k, bar);
     tma_load_4d(st + S::oV, &T.m[3], x0, y0, k, 0, bar);
     if (N > 0) tma_load_4d(st + S::oPsi, &T.m[4], x0, y0, k, 0, bar);
@@ -119,10 +140,10 @@ __device__ __forceinline__ void issue3(const PipeMaps &T, float *st, uint64_t *b
     }
   } else {
     using S = Prs3<N>;
-    mbar_arrive_expect_tx(bar, S::kBytesNoChi + (nl ? 2u * kArr : 0u));
+    mbar_arrive_expect_tx(bar, S::kBytesNoChi + (nl ? 2u * kArr : 0u) + planes);
+    for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[2], x0, y0, kp, bar);
     tma_load_3d(st + S::oVx, &T.m[0], x0 - 4, y0, k, bar);
     tma_load_3d(st + S::oVy, &T.m[1], x0, y0 - 4, k, bar);
-    tma_load_3d(st + S::oCol, &T.m[2], x0, y0, k - 4, bar);
     tma_load_3d(st + S::oP, &T.m[3], x0, y0, k, bar);
     if (N > 0) tma_load_4d(st + S::oPsi, &T.m[4], x0, y0, k, 0, bar);
     tma_load_3d(st + S::oIk, &T.m[5], x0, y0, k, bar);
@@ -301,7 +322,8 @@ __device__ __forceinline__ FaceRho3 face_rho3(const StepParams &P, const bf16 *r
 }
 
 template <int N, bool EDGE>
-__device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, int x0, int y0, int k, int tid) {
+__device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, const float *ring, int x0, int y0, int k,
+                                             int tid) {
   using S = Vel3<N>;
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
@@ -309,9 +331,10 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, int
   const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
   const int o = ly * kTX + lx;
-  // derivatives: x, y from the halo plane (cell e at column lx + 4 + e), z
-  // from the column
-  const float *sp = st + S::oHalo;
+  // derivatives: x, y from the halo plane of k (cell e at column lx + 4 + e),
+  // z from the same cell of planes k-3 .. k+4 in the ring
+  constexpr int kPl = Vel3<N>::kPlane;
+  const float *sp = ring + ring_slot(k) * kPl;
   const int sy = ly + 3;
   float2 Dx, Dy, Dz;
   {
@@ -339,7 +362,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, int
   {
     float2 zc[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) zc[m] = sld2(st + S::oCol + m * kArr + o);
+    for (int m = 0; m < 8; ++m) zc[m] = sld2(ring + ring_slot(k - 3 + m) * kPl + sy * kCW + lx + 4);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       float d = 0.f;
@@ -419,8 +442,8 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, int
 }
 
 template <int N, bool EDGE>
-__device__ __forceinline__ void prs3_compute(const StepParams &P, const float *st, int x0, int y0, int k,
-                                             int tid) {
+__device__ __forceinline__ void prs3_compute(const StepParams &P, const float *st, const float *ring, int x0, int y0,
+                                             int k, int tid) {
   using S = Prs3<N>;
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
@@ -454,7 +477,7 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const float *s
   {
     float2 zc[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) zc[m] = sld2(st + S::oCol + m * kArr + o);
+    for (int m = 0; m < 8; ++m) zc[m] = sld2(ring + ring_slot(k - 4 + m) * kArr + o);  // v_z planes k-4 ..
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       float d = 0.f;
@@ -528,6 +551,8 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const float *s
   st_state2(P.p, c, p);
 }
 
+// One half step.  Block (32, 16), one per SM; items blockIdx.x,
+// blockIdx.x + gridDim.x, ...; within an item the units k0 .. k1-1 in order.
 template <int N, bool VEL>
 __global__ void __launch_bounds__(kThreads, 1)
     pipe3d_kernel(const StepParams P, const Region3 R, const __grid_constant__ PipeMaps T) {
@@ -535,8 +560,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kStage = G::kStage;
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int ok;
+  __shared__ int ok[2];  // per stage: thread 0 never rewrites a flag a thread has yet to read
   float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float *ring = smem + 2 * kStage;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -544,24 +570,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_mbarrier_init();
   }
   __syncthreads();
-  const long long nu_ = R.units();
-  long long u = blockIdx.x;
-  if (u >= nu_) return;
+  const long long n_items = R.items();
+  long long it = blockIdx.x;
+  if (it >= n_items) return;
+  int x0, y0, k0, k1;
+  R.item(it, x0, y0, k0, k1);
+  int k = k0;
   unsigned phase = 0, pending = 0;
-  long long us = u;  // next unit to issue
-  if (tid == 0) {
-    int x, y, z;
-    R.origin(us, x, y, z);
-    issue3<N, VEL>(T, smem, &bar[0], x, y, z, P.nl != 0);
-  }
+  if (tid == 0)
+    issue3<N, VEL>(T, smem, ring, &bar[0], x0, y0, k, ring_first<VEL>(k), ring_first<VEL>(k) + 7, P.nl != 0);
   pending |= 1u;
-  us += gridDim.x;
   int s = 0;
 #pragma unroll 1
-  for (; u < nu_; u += gridDim.x) {
-    if (tid == 0) ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+  while (true) {
+    if (tid == 0) ok[s] = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
     __syncthreads();
-    if (!ok) {
+    if (!ok[s]) {
       if (tid == 0) {
         report_status(P.status, kStatusWaitTimeout);
         if ((pending >> (s ^ 1)) & 1u) mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u);
@@ -570,28 +594,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     phase ^= 1u << s;
     pending &= ~(1u << s);
-    if (us < nu_) {
-      const int q = s ^ 1;
+    // the next unit: the next plane of this item, or the first of the next
+    long long nit = it;
+    int nx0 = x0, ny0 = y0, nk0 = k0, nk1 = k1, nk = k + 1;
+    if (nk >= k1) {
+      nit = it + gridDim.x;
+      if (nit < n_items) R.item(nit, nx0, ny0, nk0, nk1);
+      nk = nk0;
+    }
+    const bool more = nit < n_items, fresh = nit != it;
+    const int q = s ^ 1;
+    if (more && !fresh) {  // one new ring plane, into the slot no unit of this item reads any more
       if (tid < 32) {
-        int x, y, z;
-        R.origin(us, x, y, z);
-        if (tid == 0) issue3<N, VEL>(T, smem + q * kStage, &bar[q], x, y, z, P.nl != 0);
-        if (!R.interior(x, y, z)) prefetch_strips<N, VEL ? 1 : 2>(P, x, y, z, tid);
+        const int kp = ring_first<VEL>(nk) + 7;
+        if (tid == 0) issue3<N, VEL>(T, smem + q * kStage, ring, &bar[q], nx0, ny0, nk, kp, kp, P.nl != 0);
+        if (!R.interior(nx0, ny0, nk)) prefetch_strips<N, VEL ? 1 : 2>(P, nx0, ny0, nk, tid);
       }
       pending |= 1u << q;
-      us += gridDim.x;
     }
-    int x0, y0, k;
-    R.origin(u, x0, y0, k);
     float *cur = smem + s * kStage;
     if (R.interior(x0, y0, k)) {
-      if (VEL) vel3_compute<N, false>(P, cur, x0, y0, k, tid);
-      else prs3_compute<N, false>(P, cur, x0, y0, k, tid);
+      if (VEL) vel3_compute<N, false>(P, cur, ring, x0, y0, k, tid);
+      else prs3_compute<N, false>(P, cur, ring, x0, y0, k, tid);
     } else {
-      if (VEL) vel3_compute<N, true>(P, cur, x0, y0, k, tid);
-      else prs3_compute<N, true>(P, cur, x0, y0, k, tid);
+      if (VEL) vel3_compute<N, true>(P, cur, ring, x0, y0, k, tid);
+      else prs3_compute<N, true>(P, cur, ring, x0, y0, k, tid);
     }
-    s ^= 1;
+    if (!more) break;
+    if (fresh) {  // a new column: all eight ring planes, once every thread is done with the ring
+      __syncthreads();
+      if (tid == 0)
+        issue3<N, VEL>(T, smem + q * kStage, ring, &bar[q], nx0, ny0, nk, ring_first<VEL>(nk),
+                       ring_first<VEL>(nk) + 7, P.nl != 0);
+      pending |= 1u << q;
+    }
+    it = nit;
+    x0 = nx0; y0 = ny0; k0 = nk0; k1 = nk1; k = nk;
+    s = q;
   }
 }
 
@@ -617,7 +656,10 @@ cudaError_t pipe3_dispatch(const StepParams &P, const Region3 &R, int grid, cons
   }
 }
 
-Region3 region3_of(const StepParams &P) {
+// Planes per item: the split of each column into items that minimises the
+// busiest block's work, counting each item's start (eight ring planes and
+// one exposed copy latency) as about 1.5 units.
+Region3 region3_of(const StepParams &P, int grid) {
   Region3 R;
   R.nx = P.nx;
   R.ny = P.ny;
@@ -627,6 +669,22 @@ Region3 region3_of(const StepParams &P) {
   R.Lz = P.L[2] > 4 ? P.L[2] : 4;
   R.tnx = (P.nx + kTX - 1) / kTX;
   R.nhy = (P.ny + kHT - 1) / kHT;
+  const long long ncols = (long long)R.tnx * R.nhy;
+  double best = 1e300;
+  R.seglen = P.nz;
+  R.nseg = 1;
+  for (int nseg = 1; nseg <= P.nz && nseg <= 64; ++nseg) {
+    const int seglen = (P.nz + nseg - 1) / nseg;
+    const int used = (P.nz + seglen - 1) / seglen;
+    const long long items = ncols * used;
+    const long long rounds = (items + grid - 1) / grid;
+    const double cost = (double)rounds * (seglen + 1.5);
+    if (cost < best - 1e-9) {
+      best = cost;
+      R.seglen = seglen;
+      R.nseg = used;
+    }
+  }
   return R;
 }
 
@@ -651,13 +709,12 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
   const ull f4[3] = {(ull)P.pitch * 4, (ull)P.plane * 4, S * 4}, h4[3] = {(ull)P.pitch * 2, (ull)P.plane * 2, S * 2};
   const ull d3[3] = {nx, ny, nz};
   const ull dv[4] = {nx, ny, nz, 3}, dpsi[4] = {nx, ny, nz, (ull)(3 * N)}, dab[4] = {nx, ny, nz, (ull)N};
-  const unsigned halo[3] = {kCW, kHT + 7, 1}, col[3] = {kTX, kHT, 8}, rho[3] = {kRWb, kHT + 1, 2},
+  const unsigned halo[3] = {kCW, kHT + 7, 1}, rho[3] = {kRWb, kHT + 1, 2},
                  one[3] = {kTX, kHT, 1}, v4[4] = {kTX, kHT, 1, 3}, psi4[4] = {kTX, kHT, 1, (unsigned)(3 * N)},
                  ab4[4] = {kTX, kHT, 1, (unsigned)N}, vx[3] = {kCW, kHT, 1}, vy[3] = {kTX, kHT + 7, 1};
   bool ok = true;
   // velocity half step
   ok = ok && encode_tensor_map(&vel->m[0], P.p, 4, 3, d3, f3, halo);
-  ok = ok && encode_tensor_map(&vel->m[1], P.p, 4, 3, d3, f3, col);
   ok = ok && encode_tensor_map(&vel->m[2], P.rho, 2, 3, d3, h3, rho);
   ok = ok && encode_tensor_map(&vel->m[3], P.v[0], 4, 4, dv, f4, v4);
   if (N > 0) ok = ok && encode_tensor_map(&vel->m[4], P.psi1[0], 4, 4, dpsi, f4, psi4);
@@ -669,7 +726,7 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
   // pressure half step
   ok = ok && encode_tensor_map(&prs->m[0], P.v[0], 4, 3, d3, f3, vx);
   ok = ok && encode_tensor_map(&prs->m[1], P.v[1], 4, 3, d3, f3, vy);
-  ok = ok && encode_tensor_map(&prs->m[2], P.v[2], 4, 3, d3, f3, col);
+  ok = ok && encode_tensor_map(&prs->m[2], P.v[2], 4, 3, d3, f3, one);
   ok = ok && encode_tensor_map(&prs->m[3], P.p, 4, 3, d3, f3, one);
   if (N > 0) ok = ok && encode_tensor_map(&prs->m[4], P.psi2[0], 4, 4, dpsi, f4, psi4);
   ok = ok && encode_tensor_map(&prs->m[5], P.ik2, 2, 3, d3, h3, one);
@@ -687,7 +744,7 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
 }
 
 cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t st) {
-  const Region3 R = region3_of(P);
+  const Region3 R = region3_of(P, grid);
   return vel ? pipe3_dispatch<true>(P, R, grid, T, st) : pipe3_dispatch<false>(P, R, grid, T, st);
 }
 

@@ -329,6 +329,13 @@ def test_pipelined_3d_equals_tile_path_bitwise(fw2, N, nl):
     _pipe_vs_tile(fw2, prob, 40, maps="bf16")
 
 
+def test_pipelined_3d_many_columns_equals_tile_path_bitwise(fw2):
+    """More columns of units than blocks: each block marches several items
+    (columns and plane ranges), reloading its plane ring at each new one."""
+    prob = small_3d(n=(300, 600, 20), N=3, nl="westervelt", steps=30)
+    _pipe_vs_tile(fw2, prob, 30, maps="bf16")
+
+
 def test_parity_3d_pipelined_path(fw2):
     prob = small_3d(n=(300, 70, 45), steps=60)
     compare_run(fw2, prob, 60, maps="bf16", kernel_path="pipe")
