@@ -45,6 +45,14 @@ constexpr int fl(int bytes) { return (bytes + 3) / 4; }
 
 // ------------------------------------------------------------- stages ---
 constexpr int kSlots = 9;  // plane ring: the eight planes of a unit and the one the next unit adds
+constexpr int kXsMax = 64; // widest x C-PML strip (cells per side) staged by TMA
+
+// x-strip region of a stage: a then b, each [N][8][L] bf16 (L <= kXsMax)
+template <int N>
+struct XStrip {
+  static constexpr int kHalf = N * kHT * kXsMax / 2;  // floats of a (or b); 128-byte multiple
+  static constexpr int kFloats = 2 * kHalf;
+};
 
 __host__ __device__ constexpr int ring_slot(int k) { return ((k % kSlots) + kSlots) % kSlots; }
 
@@ -58,8 +66,9 @@ struct Vel3 {
   static constexpr int kPsi = 3 * N * kArr;
   static constexpr int kK = round32(fl(kArr * 2));
   static constexpr int kAB = round32(fl(N * kArr * 2));
-  static constexpr int oRho = 0, oV = oRho + kRho, oPsi = oV + kV, oK = oPsi + kPsi, oA = oK + kK, oB = oA + kAB;
-  static constexpr int kFloats = round32(oB + kAB);
+  static constexpr int oRho = 0, oV = oRho + kRho, oPsi = oV + kV, oK = oPsi + kPsi, oA = oK + kK, oB = oA + kAB,
+                       oXs = oB + kAB;
+  static constexpr int kFloats = round32(oXs + XStrip<N>::kFloats);
   static constexpr unsigned kBytes = 4u * (kV + kPsi) + 2u * (2 * (kHT + 1) * kRWb + kArr + 2 * N * kArr);
   static constexpr int kPlane = round32((kHT + 7) * kCW);
   static constexpr unsigned kPlaneBytes = 4u * (kHT + 7) * kCW;
@@ -77,8 +86,8 @@ struct Prs3 {
   static constexpr int kK = round32(fl(kArr * 2));
   static constexpr int kAB = round32(fl(N * kArr * 2));
   static constexpr int oVx = 0, oVy = oVx + kVx, oP = oVy + kVy, oPsi = oP + kP, oIk = oPsi + kPsi,
-                       oKm = oIk + kK, oChi = oKm + kK, oA = oChi + kK, oB = oA + kAB;
-  static constexpr int kFloats = round32(oB + kAB);
+                       oKm = oIk + kK, oChi = oKm + kK, oA = oChi + kK, oB = oA + kAB, oXs = oB + kAB;
+  static constexpr int kFloats = round32(oXs + XStrip<N>::kFloats);
   static constexpr unsigned kBytesNoChi =
       4u * (kHT * kCW + (kHT + 7) * kTX + kP + kPsi) + 2u * (2 * kArr + 2 * N * kArr);
   static constexpr int kPlane = kArr;
@@ -99,6 +108,13 @@ struct Region3 {
   int nx, ny, nz, Lx, Ly, Lz;
   int tnx, nhy;      // x tiles, half-tile rows per plane
   int seglen, nseg;  // planes per item, items per column
+  int xsL;           // x C-PML strip cells per side when its coefficients come by TMA, else 0
+  // the side of the x strip a unit at x0 reaches: 0 low, 1 high, -1 none
+  // (with xsL set no unit reaches both)
+  __device__ __forceinline__ int xs_side(int x0) const {
+    if (xsL == 0) return -1;
+    return x0 < xsL ? 0 : (x0 + kTX > nx - xsL ? 1 : -1);
+  }
   __device__ __forceinline__ long long items() const { return (long long)tnx * nhy * nseg; }
   __device__ __forceinline__ void item(long long it, int &x0, int &y0, int &k0, int &k1) const {
     const int ncols = tnx * nhy;
@@ -122,13 +138,24 @@ __host__ __device__ constexpr int ring_first(int k) { return VEL ? k - 3 : k - 4
 // unit of an item), all completing on the stage's mbarrier.
 template <int N, bool VEL>
 __device__ __forceinline__ void issue3(const PipeMaps &T, float *st, float *ring, uint64_t *bar, int x0, int y0,
-                                       int k, int k_lo, int k_hi, bool nl) {
+                                       int k, int k_lo, int k_hi, bool nl, int xs_side, int xsL) {
   using G = Ring3<N, VEL>;
   fence_proxy_async_smem();
   const unsigned planes = G::kPlaneBytes * (unsigned)(k_hi - k_lo + 1);
+  // the x strip's coefficients of the unit's rows: one box of a and one of b
+  // (L values of the side the unit reaches, all mechanisms)
+  const unsigned xs = (N > 0 && xs_side >= 0) ? 2u * 2u * (unsigned)(N * kHT * xsL) : 0u;
+  auto load_xs = [&] {
+    if (xs) {
+      float *d = st + (VEL ? Vel3<N>::oXs : Prs3<N>::oXs);
+      tma_load_4d(d, &T.m[10], xs_side * xsL, y0, k, 0, bar);
+      tma_load_4d(d + XStrip<N>::kHalf, &T.m[11], xs_side * xsL, y0, k, 0, bar);
+    }
+  };
   if (VEL) {
     using S = Vel3<N>;
-    mbar_arrive_expect_tx(bar, S::kBytes + planes);
+    mbar_arrive_expect_tx(bar, S::kBytes + planes + xs);
+    load_xs();
     for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[0], x0 - 4, y0 - 3, kp, bar);
     tma_load_3d(st + S::oRho, &T.m[2], x0, y0, k, bar);
     tma_load_4d(st + S::oV, &T.m[3], x0, y0, k, 0, bar);
@@ -140,7 +167,8 @@ __device__ __forceinline__ void issue3(const PipeMaps &T, float *st, float *ring
     }
   } else {
     using S = Prs3<N>;
-    mbar_arrive_expect_tx(bar, S::kBytesNoChi + (nl ? 2u * kArr : 0u) + planes);
+    mbar_arrive_expect_tx(bar, S::kBytesNoChi + (nl ? 2u * kArr : 0u) + planes + xs);
+    load_xs();
     for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[2], x0, y0, kp, bar);
     tma_load_3d(st + S::oVx, &T.m[0], x0 - 4, y0, k, bar);
     tma_load_3d(st + S::oVy, &T.m[1], x0, y0 - 4, k, bar);
@@ -243,12 +271,32 @@ __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int 
   }
 }
 
+// a, b of the x strip at the two cells of an edge pair from the staged boxes
+// (a then b, each [N][8][L] bf16, the side the unit reaches): the values
+// strip3<0> reads from global memory, for the cells in the strip
+__device__ __forceinline__ void strip3x_staged(const StepParams &P, const bf16 *xa, const bf16 *xb, int xsL, int nu,
+                                               int i0, int ly, float2 &a, float2 &b) {
+  const int L = P.L[0];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int x = i0 + e;
+    if (x < P.nx) {
+      const int sc = strip_coord(x, P.nx, L);
+      if (sc >= 0) {
+        const int i = (nu * kHT + ly) * xsL + (sc >= L ? sc - L : sc);
+        el2(a, e) = __bfloat162float(xa[i]);
+        el2(b, e) = 1.f - __bfloat162float(xb[i]);
+      }
+    }
+  }
+}
+
 // Prefetch into L2 the C-PML strip rows an edge unit will read (warp 0, one
 // unit ahead): its C-PML coefficients are otherwise read straight from DRAM
 // while the unit computes.  OP: 1 velocity (a1, b1), 2 pressure (a2, b2).
 __device__ __forceinline__ void l2_line(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 template <int N, int OP>
-__device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int y0, int k, int lane) {
+__device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int y0, int k, int lane, bool xs_staged) {
   if constexpr (N > 0) {
     const bf16 *sa[3], *sb[3];
 #pragma unroll
@@ -258,7 +306,7 @@ __device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int
     }
     // x strip: rows (k, y) of 2L values, for units reaching into it
     const int Lx = P.L[0];
-    if (Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
+    if (!xs_staged && Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
       for (int t = lane; t < kHT * N * 2; t += 32) {
         const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
         const int y = y0 + r;
@@ -323,7 +371,7 @@ __device__ __forceinline__ FaceRho3 face_rho3(const StepParams &P, const bf16 *r
 
 template <int N, bool EDGE>
 __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, const float *ring, int x0, int y0, int k,
-                                             int tid) {
+                                             int tid, int xs_side, int xsL) {
   using S = Vel3<N>;
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
@@ -386,7 +434,12 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, con
   if (EDGE) {
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      strip3<0, 1>(P, nu, i0, j, k, A[0][nu], B[0][nu]);
+      if (xs_side >= 0)
+        strip3x_staged(P, reinterpret_cast<const bf16 *>(st + S::oXs),
+                       reinterpret_cast<const bf16 *>(st + S::oXs + XStrip<N>::kHalf), xsL, nu, i0, ly, A[0][nu],
+                       B[0][nu]);
+      else
+        strip3<0, 1>(P, nu, i0, j, k, A[0][nu], B[0][nu]);
       strip3<1, 1>(P, nu, i0, j, k, A[1][nu], B[1][nu]);
       strip3<2, 1>(P, nu, i0, j, k, A[2][nu], B[2][nu]);
     }
@@ -443,7 +496,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, con
 
 template <int N, bool EDGE>
 __device__ __forceinline__ void prs3_compute(const StepParams &P, const float *st, const float *ring, int x0, int y0,
-                                             int k, int tid) {
+                                             int k, int tid, int xs_side, int xsL) {
   using S = Prs3<N>;
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
@@ -504,7 +557,12 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const float *s
   if (EDGE) {
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      strip3<0, 2>(P, nu, i0, j, k, A[0][nu], B[0][nu]);
+      if (xs_side >= 0)
+        strip3x_staged(P, reinterpret_cast<const bf16 *>(st + S::oXs),
+                       reinterpret_cast<const bf16 *>(st + S::oXs + XStrip<N>::kHalf), xsL, nu, i0, ly, A[0][nu],
+                       B[0][nu]);
+      else
+        strip3<0, 2>(P, nu, i0, j, k, A[0][nu], B[0][nu]);
       strip3<1, 2>(P, nu, i0, j, k, A[1][nu], B[1][nu]);
       strip3<2, 2>(P, nu, i0, j, k, A[2][nu], B[2][nu]);
     }
@@ -578,7 +636,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   int k = k0;
   unsigned phase = 0, pending = 0;
   if (tid == 0)
-    issue3<N, VEL>(T, smem, ring, &bar[0], x0, y0, k, ring_first<VEL>(k), ring_first<VEL>(k) + 7, P.nl != 0);
+    issue3<N, VEL>(T, smem, ring, &bar[0], x0, y0, k, ring_first<VEL>(k), ring_first<VEL>(k) + 7, P.nl != 0,
+                   R.xs_side(x0), R.xsL);
   pending |= 1u;
   int s = 0;
 #pragma unroll 1
@@ -607,25 +666,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (more && !fresh) {  // one new ring plane, into the slot no unit of this item reads any more
       if (tid < 32) {
         const int kp = ring_first<VEL>(nk) + 7;
-        if (tid == 0) issue3<N, VEL>(T, smem + q * kStage, ring, &bar[q], nx0, ny0, nk, kp, kp, P.nl != 0);
-        if (!R.interior(nx0, ny0, nk)) prefetch_strips<N, VEL ? 1 : 2>(P, nx0, ny0, nk, tid);
+        if (tid == 0)
+          issue3<N, VEL>(T, smem + q * kStage, ring, &bar[q], nx0, ny0, nk, kp, kp, P.nl != 0, R.xs_side(nx0),
+                         R.xsL);
+        if (!R.interior(nx0, ny0, nk)) prefetch_strips<N, VEL ? 1 : 2>(P, nx0, ny0, nk, tid, R.xsL > 0);
       }
       pending |= 1u << q;
     }
     float *cur = smem + s * kStage;
     if (R.interior(x0, y0, k)) {
-      if (VEL) vel3_compute<N, false>(P, cur, ring, x0, y0, k, tid);
-      else prs3_compute<N, false>(P, cur, ring, x0, y0, k, tid);
+      if (VEL) vel3_compute<N, false>(P, cur, ring, x0, y0, k, tid, -1, 0);
+      else prs3_compute<N, false>(P, cur, ring, x0, y0, k, tid, -1, 0);
     } else {
-      if (VEL) vel3_compute<N, true>(P, cur, ring, x0, y0, k, tid);
-      else prs3_compute<N, true>(P, cur, ring, x0, y0, k, tid);
+      const int xside = R.xs_side(x0);
+      if (VEL) vel3_compute<N, true>(P, cur, ring, x0, y0, k, tid, xside, R.xsL);
+      else prs3_compute<N, true>(P, cur, ring, x0, y0, k, tid, xside, R.xsL);
     }
     if (!more) break;
     if (fresh) {  // a new column: all eight ring planes, once every thread is done with the ring
       __syncthreads();
       if (tid == 0)
         issue3<N, VEL>(T, smem + q * kStage, ring, &bar[q], nx0, ny0, nk, ring_first<VEL>(nk),
-                       ring_first<VEL>(nk) + 7, P.nl != 0);
+                       ring_first<VEL>(nk) + 7, P.nl != 0, R.xs_side(nx0), R.xsL);
       pending |= 1u << q;
     }
     it = nit;
@@ -656,6 +718,14 @@ cudaError_t pipe3_dispatch(const StepParams &P, const Region3 &R, int grid, cons
   }
 }
 
+// The x strip's coefficients come by TMA when a box of L values per row
+// starts on a 16-byte boundary and fits the stage (L a multiple of 8, at
+// most kXsMax), and no unit reaches both sides (nx >= 128 + L).
+bool x_strip_staged(const StepParams &P) {
+  const int L = P.L[0];
+  return P.n_relax > 0 && L > 0 && L % 8 == 0 && L <= kXsMax && P.nx >= kTX + L && P.sa1[0] != nullptr;
+}
+
 // Planes per item: the split of each column into items that minimises the
 // busiest block's work, counting each item's start (eight ring planes and
 // one exposed copy latency) as about 1.5 units.
@@ -669,6 +739,7 @@ Region3 region3_of(const StepParams &P, int grid) {
   R.Lz = P.L[2] > 4 ? P.L[2] : 4;
   R.tnx = (P.nx + kTX - 1) / kTX;
   R.nhy = (P.ny + kHT - 1) / kHT;
+  R.xsL = x_strip_staged(P) ? P.L[0] : 0;
   const long long ncols = (long long)R.tnx * R.nhy;
   double best = 1e300;
   R.seglen = P.nz;
@@ -735,6 +806,15 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
   if (N > 0) {
     ok = ok && encode_tensor_map(&prs->m[8], P.a2, 2, 4, dab, h4, ab4);
     ok = ok && encode_tensor_map(&prs->m[9], P.b2, 2, 4, dab, h4, ab4);
+  }
+  if (x_strip_staged(P)) {  // x strips [N][z][y][2L] bf16, boxes L x 8 x 1 x N
+    const ull L = (ull)P.L[0];
+    const ull dxs[4] = {2 * L, ny, nz, (ull)N}, sxs[3] = {2 * L * 2, ny * 2 * L * 2, (ull)P.strip_nu[0] * 2};
+    const unsigned bxs[4] = {(unsigned)L, kHT, 1, (unsigned)N};
+    ok = ok && encode_tensor_map(&vel->m[10], P.sa1[0], 2, 4, dxs, sxs, bxs);
+    ok = ok && encode_tensor_map(&vel->m[11], P.sb1[0], 2, 4, dxs, sxs, bxs);
+    ok = ok && encode_tensor_map(&prs->m[10], P.sa2[0], 2, 4, dxs, sxs, bxs);
+    ok = ok && encode_tensor_map(&prs->m[11], P.sb2[0], 2, 4, dxs, sxs, bxs);
   }
   if (!ok) {
     *why = "cuTensorMapEncodeTiled rejected a 3D map (or the driver entry point is missing)";

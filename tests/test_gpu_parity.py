@@ -236,7 +236,7 @@ def test_parity_2d_random_state_all_fields(fw2):
     compare_run(fw2, prob, 60, state=st)
 
 
-def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3):
+def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3, pml=(6, 2)):
     rng = np.random.default_rng(seed)
     f0 = 1e6
     h = 1540.0 / f0 / 10
@@ -249,7 +249,7 @@ def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3):
     prob.dt = 0.4 * h / float(prob.c.max())
     prob.beta = rng.uniform(3, 6, g).astype(np.float32)
     prob.nl_mode = nl
-    prob.pml_transition, prob.pml_bound = (6, 2) if N else (0, 0)
+    prob.pml_transition, prob.pml_bound = pml if N else (0, 0)
     sig = synth.gaussian_pulse(steps, prob.dt, f0, 2.0, 1e6)
     X, Y = np.meshgrid(np.arange(20, 50), np.arange(12, 28), indexing="xy")
     idx = synth.flat_index(n, X.ravel(), Y.ravel(), 10)
@@ -326,6 +326,13 @@ def test_pipelined_3d_equals_tile_path_bitwise(fw2, N, nl):
     the tile kernels compute: interior and edge units, ragged x and y, C-PML
     strips on every axis."""
     prob = small_3d(n=(300, 70, 45), N=N, nl=nl, steps=40)
+    _pipe_vs_tile(fw2, prob, 40, maps="bf16")
+
+
+def test_pipelined_3d_x_strip_loaded_per_cell_equals_tile_path_bitwise(fw2):
+    """A C-PML of 7 cells: the x strip's coefficient rows are not 16-byte
+    multiples, so edge units read them per cell instead of by TMA."""
+    prob = small_3d(n=(300, 70, 45), N=3, nl="pressure", steps=40, pml=(5, 2))
     _pipe_vs_tile(fw2, prob, 40, maps="bf16")
 
 
