@@ -76,7 +76,7 @@ struct VelStage {
   static constexpr int kPb = (kHT + 7) * kCW;    // operand box
   static constexpr int kRb = (kHT + 1) * kRWp;   // density box
   static constexpr int kP = round32(kPb);
-  static constexpr int kR = round32(kRb);
+  static constexpr int kR = kIdx ? 0 : round32(kRb);  // the index form looks the density up
   static constexpr int kS = kNs * kArr;
   static constexpr int kI = kIdx ? (kHT + 1) * kIW / 4 : 0;  // index bytes / 4
   // dense, literal nonlinear system: K box of the density box's shape
@@ -212,12 +212,12 @@ __device__ __forceinline__ float2 mask_pad2(float2 v, int i0, int nx) {
   if (i0 >= nx) v.x = 0.f;
   return v;
 }
-// Results leave through the stage and TMA tensor stores with float maps (the
-// memory-bound form, where fewer store instructions pay); with the index
-// form (bound by its compute phase) each thread stores its own results.
+// Results leave through the stage and TMA tensor stores (fewer store
+// instructions than per-thread stores; the store of a unit overlaps the
+// compute of the next).
 template <typename Maps>
 struct TmaStore {
-  static constexpr bool value = !IsIdx<Maps>::value;
+  static constexpr bool value = true;
 };
 // one result pair of array `a` (stage offset in arrays) of cell c
 template <typename Maps, bool EDGE>
@@ -626,11 +626,18 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const float *ta
 template <int N, typename Maps, bool VEL>
 struct Ring {
   static constexpr int kStage = VEL ? VelStage<N, Maps>::kFloats : PrsStage<N, Maps>::kFloats;
-  static constexpr int kBudget = (220 * 1024 - 128) / 4 - Maps::kSmemFloats;  // floats
+  static constexpr int kBudget = (224 * 1024 - 128) / 4 - Maps::kSmemFloats;  // floats
   static constexpr int kFit = kBudget / kStage;
   static constexpr int kStages = kFit > 4 ? 4 : kFit;
+  // With four stages a stage is refilled one unit after its results were
+  // stored (the store has read it by then: no wait on it), two units ahead
+  // of its compute; with two or three, right after its store, kStages - 1
+  // units ahead.
+  static constexpr int kLag = (TmaStore<Maps>::value && kStages >= 4) ? 1 : 0;
+  static constexpr int kAhead = kStages - 1 - kLag;
   static constexpr size_t kBytes = sizeof(float) * ((size_t)kStages * kStage + Maps::kSmemFloats) + 128;
   static_assert(kStages >= 2, "two stages must fit in shared memory");
+  static_assert(kBytes + 1024 <= 227 * 1024, "stages and table leave 1 KB for static shared memory");
 };
 
 // One half step.  Block (32, 16), one per SM.
@@ -661,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned phase = 0;    // bit q: parity of the next completion of stage q
   unsigned pending = 0;  // bit q: copies issued into stage q, not consumed
   int hs = h;            // next half tile to issue
-  for (int q = 0; q < kS - 1; ++q, hs += gridDim.x) {
+  for (int q = 0; q < G::kAhead; ++q, hs += gridDim.x) {
     if (hs >= nh) break;
     if (tid == 0) {
       int xq, yq;
@@ -690,16 +697,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     phase ^= 1u << s;
     pending &= ~(1u << s);
-    const int q = (s + kS - 1) % kS;  // the previous half tile's stage, free now
+    const int sp = (s + kS - 1) % kS;       // the previous half tile's stage
+    const int q = (s + G::kAhead) % kS;     // the stage refilled now
     if constexpr (TmaStore<Maps>::value) {
-      if (tid == 0 && xp >= 0) store_stage<N, Maps, VEL>(T, smem + q * kStage, xp, yp);
+      if (tid == 0 && xp >= 0) store_stage<N, Maps, VEL>(T, smem + sp * kStage, xp, yp);
     }
     if (hs < nh) {
       if (tid < 32) {
         int xq, yq;
         R.half_origin(hs, xq, yq);
         if (tid == 0) {
-          bulk_wait_read<0>();
+          bulk_wait_read<G::kLag>();
           issue_stage<N, Maps, VEL>(P, T, smem + q * kStage, &bar[q], xq, yq);
         }
         if (!R.interior(xq, yq)) prefetch_strips2<N, VEL ? 1 : 2>(P, xq, yq, tid);
@@ -758,7 +766,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (h >= h_end) return;
   unsigned phase = 0, pending = 0;
   int hs = h;
-  for (int q = 0; q < kS - 1; ++q, ++hs) {
+  for (int q = 0; q < G::kAhead; ++q, ++hs) {
     if (hs >= h_end) break;
     if (tid == 0) {
       const int4 e = units[hs];
@@ -784,9 +792,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     phase ^= 1u << s;
     pending &= ~(1u << s);
-    const int q = (s + kS - 1) % kS;  // the previous unit's stage, free now
+    const int sp = (s + kS - 1) % kS;       // the previous unit's stage
+    const int q = (s + G::kAhead) % kS;     // the stage refilled now
     if constexpr (TmaStore<Maps>::value) {
-      if (tid == 0 && prev.x >= 0) store_stage<N, Maps, VEL>(Ts[prev.x], smem + q * kStage, prev.y, prev.z);
+      if (tid == 0 && prev.x >= 0) store_stage<N, Maps, VEL>(Ts[prev.x], smem + sp * kStage, prev.y, prev.z);
     }
     const int4 e = units[h];
     if (e.x != cur) {
@@ -803,7 +812,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (tid < 32) {
         const int4 en = units[hs];
         if (tid == 0) {
-          bulk_wait_read<0>();
+          bulk_wait_read<G::kLag>();
           issue_stage<N, Maps, VEL>(Ps[en.x], Ts[en.x], smem + q * kStage, &bar[q], en.y, en.z);
         }
         if (!en.w && en.x == cur) prefetch_strips2<N, VEL ? 1 : 2>(sP, en.y, en.z, tid);
