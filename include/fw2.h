@@ -84,8 +84,9 @@ enum { FW2_MEM_CENTRED = 0, FW2_MEM_ENDPOINT = 1 };
 /* kernel path of the half steps (bitwise the same results on every path):
  * TILE runs one block per tile; PIPE runs the persistent kernels that stage
  * every tile through shared memory with TMA copies, where they apply (2D
- * float or tissue-index maps, 3D bf16 maps with N <= 3, no periodic axis),
- * and TILE elsewhere; AUTO (default) is PIPE */
+ * float or tissue-index maps; 3D bf16 maps with N <= 3, no g_{1,1} cross
+ * taps and no LITERAL momentum factor; no periodic axis), and TILE
+ * elsewhere; AUTO (default) is PIPE */
 enum { FW2_PATH_AUTO = 0, FW2_PATH_TILE = 1, FW2_PATH_PIPE = 2 };
 enum { FW2_SRC_P = 0, FW2_SRC_VX = 1, FW2_SRC_VY = 2, FW2_SRC_VZ = 3 };
 enum {
