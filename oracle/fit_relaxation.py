@@ -140,7 +140,9 @@ def fit_grid(alpha0, y, N, c0=1540.0, f_ref=3e6, points=5, refinements=4, shrink
     """The paper's coarse-to-fine grid search (Sec. 4.1): `points` values per
     dimension spanning the current range (first the bounds), the best of the
     whole grid becomes the centre of the next search, whose range in every
-    dimension is (1 - shrink) of the previous one (kept inside the bounds);
+    dimension is (1 - shrink) of the previous one; grid values beyond the
+    bounds are moved onto them, so with an odd `points` the previous best is
+    a point of every finer grid and the best cost never rises.
     1 + refinements searches in all.  target: optional (att, c) curves to fit
     instead of the power law; workers > 1 splits each grid over a process
     pool.  Returns the parameter dict, each level's best cost in `J_levels`."""
@@ -161,9 +163,11 @@ def fit_grid(alpha0, y, N, c0=1540.0, f_ref=3e6, points=5, refinements=4, shrink
         import multiprocessing as mp
         pool = mp.get_context("spawn").Pool(workers)
     best_theta, best_j, levels = None, np.inf, []
+    centre, width = (lo + hi) / 2.0, hi - lo
     try:
         for level in range(refinements + 1):
-            axes = [np.linspace(lo[i], hi[i], points) for i in range(D)]
+            axes = [np.clip(np.linspace(centre[i] - width[i] / 2, centre[i] + width[i] / 2, points), blo[i], bhi[i])
+                    for i in range(D)]
             cuts = np.linspace(0, total, (workers if pool else 1) + 1).astype(np.int64)
             jobs = [(int(cuts[i]), int(cuts[i + 1]), axes, N, f, c0, att_t, c_t, chunk)
                     for i in range(len(cuts) - 1)]
@@ -172,9 +176,7 @@ def fit_grid(alpha0, y, N, c0=1540.0, f_ref=3e6, points=5, refinements=4, shrink
             levels.append(level_best[0])
             if level_best[0] < best_j:
                 best_j, best_theta = level_best
-            half = (hi - lo) * (1.0 - shrink) / 2.0
-            lo = np.maximum(best_theta - half, blo)
-            hi = np.minimum(best_theta + half, bhi)
+            centre, width = best_theta, width * (1.0 - shrink)
     finally:
         if pool:
             pool.close()
