@@ -336,6 +336,24 @@ def test_pipelined_3d_x_strip_loaded_per_cell_equals_tile_path_bitwise(fw2):
     _pipe_vs_tile(fw2, prob, 40, maps="bf16")
 
 
+@pytest.mark.parametrize("shape,pml", [((100, 40, 20), (6, 2)), ((264, 30, 18), (6, 2)), ((200, 24, 17), (3, 1)),
+                                       ((300, 36, 8), (1, 1))])
+def test_pipelined_3d_small_grids_equal_tile_path_bitwise(fw2, shape, pml):
+    """Grids at the limits of the 3D pipeline from a random state: one x tile
+    reaching both x strips (nx < 128 + L: the strip read per cell), a ragged
+    last x tile holding the whole high strip (staged), a strip that is not a
+    16-byte row (per cell), and the fewest planes a grid may have, eight
+    (most ring planes outside the grid)."""
+    rng = np.random.default_rng(11)
+    h = 1e-4
+    prob = synth.homogeneous(shape, h, 0.0, relax=synth.relaxation_sets()["N2_y1.0_a0.5"])
+    prob.c = (1540.0 * (1 + 0.05 * rng.random(prob.grid_shape))).astype(np.float32)
+    prob.rho = (1000.0 * (1 + 0.1 * rng.random(prob.grid_shape))).astype(np.float32)
+    prob.dt = 0.3 * h / float(prob.c.max())
+    prob.pml_transition, prob.pml_bound = pml
+    _pipe_vs_tile(fw2, prob, 20, maps="bf16", state=synth.random_state(prob, seed=12))
+
+
 def test_pipelined_3d_many_columns_equals_tile_path_bitwise(fw2):
     """More columns of units than blocks: each block marches several items
     (columns and plane ranges), reloading its plane ring at each new one."""
