@@ -1,0 +1,69 @@
+"""Host logic of bench.py: the algorithmic bytes behind the roofline fraction
+(counted by hand from the arrays each half step must read and write once)
+and the committed DRAM traffic lookup."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_algorithmic_bytes_2d_by_hand():
+    """2D, N = 4, nonlinear, float maps, no C-PML: the velocity half step reads
+    p, rho, 1/kappa1 and a, b of 4 mechanisms and reads and writes v_x, v_y and
+    8 memory variables: 4 + 4 + 4 + 32 + 16 + 64 = 124 B per cell; the
+    pressure half step 8 (v) + 4 (K) + 4 (chi) + 4 + 32 + 8 (p) + 64 = 124."""
+    n = 1000 * 700
+    vel, prs = bench.algorithmic_bytes((1000, 700), 4, 0, True, map_bytes=4)
+    assert vel == 124 * n and prs == 124 * n
+    vel, prs = bench.algorithmic_bytes((1000, 700), 4, 0, False, map_bytes=4)
+    assert prs == 120 * n                                  # no chi
+    vel, _ = bench.algorithmic_bytes((1000, 700), 4, 0, True, map_bytes=4, nl_vel=True)
+    assert vel == 128 * n                                  # K in the velocity half step
+
+
+def test_algorithmic_bytes_3d_bf16_by_hand():
+    """3D, N = 3, linear, bf16 maps, no C-PML: velocity 4 (p) + 2 + 2 + 12
+    (a, b) + 24 (v) + 72 (psi) = 116 B; pressure 12 (v) + 2 (K) + 2 + 12 + 8
+    (p) + 72 = 108 B per cell."""
+    n = 64 * 48 * 40
+    vel, prs = bench.algorithmic_bytes((64, 48, 40), 3, 0, False, map_bytes=2)
+    assert vel == 116 * n and prs == 108 * n
+
+
+def test_strip_bytes_count_each_axis_inside_its_strip():
+    """A cell inside the C-PML of k axes reads k strip sets of a, b (one per
+    axis) plus the interior set when some axis is outside its strip."""
+    shape, N, L = (40, 30), 2, 5
+    vel0, _ = bench.algorithmic_bytes(shape, N, 0, False)
+    vel, _ = bench.algorithmic_bytes(shape, N, L, False)
+    per_set = 2 * N * 4
+    nx, ny = shape
+    corner = (2 * L) * (2 * L)                           # both axes in a strip: 2 sets
+    edge = (2 * L) * (ny - 2 * L) + (nx - 2 * L) * (2 * L)  # one axis: strip + interior
+    assert vel - vel0 == (corner * 1 + edge * 1) * per_set
+
+
+def test_index_form_bytes():
+    n = 512 * 256
+    vel, prs = bench.algorithmic_bytes_indexed((512, 256), 4, 0, True)
+    assert vel == n * (4 + 1 + 16 + 64) and prs == n * (8 + 1 + 8 + 64)
+
+
+def test_committed_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The committed traffic is used only while its source hash matches."""
+    real = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    key = next(k for k in real if not k.startswith("_"))
+    if real[key]["source_hash"] == bench.kernel_source_hash():
+        assert bench.committed_traffic(key) == real[key]["dram_bytes_per_launch"]
+    root = tmp_path
+    (root / "profiles").mkdir()
+    (root / "profiles" / "traffic.json").write_text(json.dumps({
+        "old": {"dram_bytes_per_launch": 5, "source_hash": "stale"},
+        "new": {"dram_bytes_per_launch": 7, "source_hash": "current"}}))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "current")
+    assert bench.committed_traffic("new") == 7
+    assert bench.committed_traffic("old") is None
+    assert bench.committed_traffic("missing") is None
