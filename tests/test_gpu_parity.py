@@ -411,6 +411,27 @@ def test_parity_abdominal_full_size_windows(fw2):
     sim.close()
 
 
+def test_parity_abdominal_tissue_index_full_size_windows(fw2):
+    """The tissue-index workload the benchmark times (4096 x 4096, uint8
+    index, 128-element focused array) from a seeded wavefield: after 4 steps
+    the GPU matches the oracle (the gathered float tables) on windows covering
+    a C-PML corner, the array and the deep interior."""
+    prob = synth.indexed_abdominal_problem(nx=4096, ny=4096, n_steps=8, seed=1, n_elements=128, focus_mm=40.0)
+    st = synth.random_state(prob, seed=22)
+    steps = 4
+    sim = fw2.Simulation(prob, map_precision="idx")
+    sim.set_state(st)
+    sim.step(steps)
+    sim.synchronize()
+    assert fw2.fw2_kernel_path(sim.ctx) == "pipe"
+    for window in (((0, 160), (0, 160)), ((1900, 2200), (30, 200)), ((3000, 3200), (3900, 4096))):
+        orc = OracleSim(prob, round_to="f32", window=window)
+        orc.set_state(st)
+        orc.run(steps)
+        _window_compare(sim, orc, prob, window, steps)
+    sim.close()
+
+
 def test_parity_skull_full_size_windows(fw2):
     """768^3 transcranial-like medium with bf16 maps, N = 3, in the launch
     configuration the 3D benchmark times, from a seeded wavefield: after 2
