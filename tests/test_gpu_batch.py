@@ -72,3 +72,32 @@ def test_batch_rejects_3d(fw2):
     with pytest.raises(fw2.Fw2Error):
         fw2.fw2_batch_create([s.ctx])
     s.close()
+
+
+def test_batch_full_size_equals_each_context_alone(fw2):
+    """The benchmark's batch (64 focused transmits over one 2048 x 1024
+    tissue-index medium and 16 uneven instances, 151 M cells) after the four
+    autotuning steps and four more: sampled contexts hold bitwise what they
+    hold when stepped alone."""
+    import types
+    import bench
+    probs = bench.batch_problems(types.SimpleNamespace(warmup=4, steps=4), 0)
+    steps = 8
+    sims = [fw2.Simulation(p, map_precision="idx") for p in probs]
+    batch = fw2.fw2_batch_create([s.ctx for s in sims])
+    try:
+        fw2.fw2_batch_step(batch, steps)
+        fw2.fw2_batch_synchronize(batch)
+        picked = [0, 31, 63, 64, 71, 79]
+        got = {i: (sims[i].field("p"), sims[i].field("vy"), sims[i].trace.cpu().numpy()[:steps]) for i in picked}
+    finally:
+        fw2.fw2_batch_destroy(batch)
+        for s in sims:
+            s.close()
+    for i in picked:
+        s = fw2.Simulation(probs[i], map_precision="idx")
+        s.step(steps)
+        np.testing.assert_array_equal(got[i][0], s.field("p"))
+        np.testing.assert_array_equal(got[i][1], s.field("vy"))
+        np.testing.assert_array_equal(got[i][2], s.trace.cpu().numpy()[:steps])
+        s.close()
