@@ -371,7 +371,7 @@ def run_fw2(args, rank, world, dist):
         if prob.ndim == 2:
             win = ((c0 - 256, c0 + 256), (0, 512))
         else:
-            win = ((c0 - 40, c0 + 40), (c0 - 40, c0 + 40), (36, 116))
+            win = ((c0 - 64, c0 + 64), (c0 - 64, c0 + 64), (36, 164))
         cpu = oracle_baseline(prob, args.cpu_steps, win, maps)
     if rank != 0:
         return
@@ -616,7 +616,8 @@ def main():
                     help="staggered taps: 8th-order Taylor, or the time-space optimised set with cross taps")
     ap.add_argument("--nl", default=None, choices=["off", "pressure", "westervelt", "literal"],
                     help="override the workload's nonlinear mode")
-    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--cpu-steps", type=int, default=300,
+                    help="oracle steps of the cpu_baseline sample (about 10 s on 16 host cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
