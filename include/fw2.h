@@ -58,8 +58,7 @@ enum { FW2_BC_ZERO = 0, FW2_BC_PERIODIC = 1 };
  * LITERAL: the system as printed, Eqs. (general5) and (general6): the
  * PRESSURE factor, and the velocity update divided by 1 + kappa0 p at the face
  * (kappa0 the mean of the two cells' 1/K, p the mean of their p^n), which
- * propagates with speed c0 + (beta - 1) v.  LITERAL runs the tile kernels in
- * 3D. */
+ * propagates with speed c0 + (beta - 1) v. */
 enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2, FW2_NL_LITERAL = 3 };
 /* storage of the coefficient maps: float, bf16 (b kept as 1 - b), or a
  * uint8 tissue index per cell into per-tissue float tables (2D only; set the
@@ -84,9 +83,8 @@ enum { FW2_MEM_CENTRED = 0, FW2_MEM_ENDPOINT = 1 };
 /* kernel path of the half steps (bitwise the same results on every path):
  * TILE runs one block per tile; PIPE runs the persistent kernels that stage
  * every tile through shared memory with TMA copies, where they apply (2D
- * float or tissue-index maps; 3D bf16 maps with N <= 3, no g_{1,1} cross
- * taps and no LITERAL momentum factor; no periodic axis), and TILE
- * elsewhere; AUTO (default) is PIPE */
+ * float or tissue-index maps; 3D bf16 maps with N <= 3 and no g_{1,1} cross
+ * taps; no periodic axis), and TILE elsewhere; AUTO (default) is PIPE */
 enum { FW2_PATH_AUTO = 0, FW2_PATH_TILE = 1, FW2_PATH_PIPE = 2 };
 enum { FW2_SRC_P = 0, FW2_SRC_VX = 1, FW2_SRC_VY = 2, FW2_SRC_VZ = 3 };
 enum {

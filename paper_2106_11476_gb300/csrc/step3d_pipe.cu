@@ -478,11 +478,35 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, con
   }
   const FaceRho3 f = face_rho3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), x0, y0, k, lx, ly);
   const float rr[3] = {f.r0, f.r1, f.r2}, ru[2] = {f.u0, f.u1}, rz[2] = {f.z0, f.z1};
+  if (P.nl_vel) {
+    // momentum factors of the literal system (Eq. general5) at the x, y, z
+    // faces: p from the staged planes (zero beyond the grid), K of the cell
+    // and of its +1 neighbours from the map, clamped to the last cell
+    const bf16 *Km = static_cast<const bf16 *>(P.K);
+    const int jn = min(j + 1, P.ny - 1), kn = min(k + 1, P.nz - 1);
+    const long long row = (long long)k * P.plane + (long long)j * P.pitch;
+    const long long rowy = (long long)k * P.plane + (long long)jn * P.pitch;
+    const long long rowz = (long long)kn * P.plane + (long long)j * P.pitch;
+    const float *pr = sp + sy * kCW + lx + 4, *pu = sp + (sy + 1) * kCW + lx + 4;
+    const float *pz = ring + ring_slot(k + 1) * kPl + sy * kCW + lx + 4;
 #pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(S0, e));
-    el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(S1, e));
-    el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(S2, e));
+    for (int e = 0; e < 2; ++e) {
+      const int x = min(i0 + e, P.nx - 1), xn = min(i0 + e + 1, P.nx - 1);
+      const float Kc = ldmap(Km, row + x);
+      const float fx = mom_factor(Kc, ldmap(Km, row + xn), pr[e], pr[e + 1]);
+      const float fy = mom_factor(Kc, ldmap(Km, rowy + x), pr[e], pu[e]);
+      const float fz = mom_factor(Kc, ldmap(Km, rowz + x), pr[e], pz[e]);
+      el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(S0, e), fx);
+      el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(S1, e), fy);
+      el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(S2, e), fz);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(S0, e));
+      el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(S1, e));
+      el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(S2, e));
+    }
   }
   if (EDGE) {
     v0 = mask_pad2(v0, i0, P.nx);
@@ -763,11 +787,10 @@ Region3 region3_of(const StepParams &P, int grid) {
 
 bool pipe3d_supported(const StepParams &P, int map_kind) {
   // bf16 maps (two stages of ~107 KB fit); N <= 3 keeps the 4D boxes and
-  // the stage within shared memory; no periodic axis; the momentum
-  // equation's nonlinear factor and the cross taps are left to the tile
-  // kernels
+  // the stage within shared memory; no periodic axis; the cross taps are
+  // left to the tile kernels
   return P.nz > 1 && map_kind == 1 && P.n_relax >= 0 && P.n_relax <= 3 && !P.periodic[0] && !P.periodic[1] &&
-         !P.periodic[2] && !P.nl_vel && P.g11h == 0.f;
+         !P.periodic[2] && P.g11h == 0.f;
 }
 
 cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why) {

@@ -296,8 +296,8 @@ def test_parity_3d_periodic_lossless_cross_taps(fw2):
 
 @pytest.mark.parametrize("maps", ["f32", "bf16"])
 def test_parity_3d_literal(fw2, maps):
-    """Both nonlinear factors in 3D (tile kernels; the pipelined 3D half
-    steps leave this mode to them)."""
+    """Both nonlinear factors in 3D: float maps on the tile kernels, bf16 maps
+    on the pipelined half steps."""
     prob = small_3d(nl="literal", steps=80)
     for s in prob.sources:
         if s.kind == "p":
@@ -305,7 +305,7 @@ def test_parity_3d_literal(fw2, maps):
     compare_run(fw2, prob, 80, maps=maps, kernel_path="pipe" if maps == "bf16" else "auto")
     sim = fw2.Simulation(prob, map_precision="bf16", kernel_path="pipe")
     sim.step(1)
-    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    assert fw2.fw2_kernel_path(sim.ctx) == "pipe"
     sim.close()
 
 
@@ -320,7 +320,7 @@ def test_parity_3d_random_state(fw2):
     compare_run(fw2, prob, 30, state=st)
 
 
-@pytest.mark.parametrize("N,nl", [(0, "off"), (2, "pressure"), (3, "westervelt"), (3, "off")])
+@pytest.mark.parametrize("N,nl", [(0, "off"), (2, "pressure"), (3, "westervelt"), (3, "off"), (3, "literal")])
 def test_pipelined_3d_equals_tile_path_bitwise(fw2, N, nl):
     """The persistent TMA-staged 3D half steps (bf16 maps) compute exactly what
     the tile kernels compute: interior and edge units, ragged x and y, C-PML
