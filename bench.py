@@ -104,17 +104,24 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_source_hash():
+# sources of each kernel family: a committed traffic figure stays valid while
+# the sources of its own family are unchanged
+_COMMON_SOURCES = ("async.cuh", "maps.cuh", "tmap.h", "coef.cuh", "fw2_internal.cuh")
+_FAMILY_SOURCES = {"pipe2d": ("step2d.cu", "step2d_pipe.cu", "tile2d.cuh"),
+                   "pipe3d": ("step3d.cu", "step3d_pipe.cu", "tile2d.cuh")}
+
+
+def kernel_source_hash(family="pipe2d"):
     h = hashlib.sha256()
-    for f in ("step2d.cu", "step2d_pipe.cu", "tile2d.cuh", "async.cuh", "maps.cuh", "tmap.h", "step3d.cu",
-              "step3d_pipe.cu", "coef.cuh", "fw2_internal.cuh"):
+    for f in _FAMILY_SOURCES[family] + _COMMON_SOURCES:
         with open(os.path.join(ROOT, "paper_2106_11476_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def committed_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    """DRAM bytes per launch from the committed ncu summary, if it matches the
+    current sources of the kernel's family (pipe2d or pipe3d, from the key)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -122,7 +129,8 @@ def committed_traffic(kernel):
     except Exception:
         return None
     entry = t.get(kernel)
-    if not entry or entry.get("source_hash") != kernel_source_hash():
+    family = "pipe3d" if ":pipe3d" in kernel else "pipe2d"
+    if not entry or entry.get("source_hash") != kernel_source_hash(family):
         return None
     return entry.get("dram_bytes_per_launch")
 

@@ -52,18 +52,24 @@ def test_index_form_bytes():
 
 
 def test_committed_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
-    """The committed traffic is used only while its source hash matches."""
+    """The committed traffic is used only while the sources of its kernel
+    family (2D or 3D pipeline) are the ones it was captured with."""
     real = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
-    key = next(k for k in real if not k.startswith("_"))
-    if real[key]["source_hash"] == bench.kernel_source_hash():
-        assert bench.committed_traffic(key) == real[key]["dram_bytes_per_launch"]
+    for key in (k for k in real if not k.startswith("_")):
+        family = "pipe3d" if ":pipe3d" in key else "pipe2d"
+        if real[key]["source_hash"] == bench.kernel_source_hash(family):
+            assert bench.committed_traffic(key) == real[key]["dram_bytes_per_launch"]
+        else:
+            assert bench.committed_traffic(key) is None
     root = tmp_path
     (root / "profiles").mkdir()
     (root / "profiles" / "traffic.json").write_text(json.dumps({
-        "old": {"dram_bytes_per_launch": 5, "source_hash": "stale"},
-        "new": {"dram_bytes_per_launch": 7, "source_hash": "current"}}))
+        "w:f32:1:pipe2d_vel": {"dram_bytes_per_launch": 5, "source_hash": "stale"},
+        "w:f32:1:pipe2d_prs": {"dram_bytes_per_launch": 7, "source_hash": "current2d"},
+        "w:bf16:1:pipe3d_vel": {"dram_bytes_per_launch": 9, "source_hash": "current2d"}}))
     monkeypatch.setattr(bench, "ROOT", str(root))
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "current")
-    assert bench.committed_traffic("new") == 7
-    assert bench.committed_traffic("old") is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda family="pipe2d": "current" + family[-2:])
+    assert bench.committed_traffic("w:f32:1:pipe2d_prs") == 7
+    assert bench.committed_traffic("w:f32:1:pipe2d_vel") is None
+    assert bench.committed_traffic("w:bf16:1:pipe3d_vel") is None   # another family's sources
     assert bench.committed_traffic("missing") is None
