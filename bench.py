@@ -10,6 +10,8 @@ recording.  The state (19 float32 arrays, 1.3 GB) plus the coefficient maps
 exceed L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fw2|reference]
+                  [--workload abdominal|abdominal-idx|skull|batch|serve]
+                  [--taps taylor|time-space] [--nl off|pressure|westervelt|literal]
 
 Under torchrun each rank simulates its own transmit event (independent
 problems: weak scaling, no data-path collective); the barrier and the max
