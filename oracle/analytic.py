@@ -38,16 +38,20 @@ def wavenumber(omega, c, kappa1, kappa2, d1, alpha1, d2, alpha2):
 
 
 def attenuation_db_cm(k):
-    """Amplitude attenuation -Im(k) in dB/cm (k in 1/m)."""
+    """Amplitude attenuation -Im(k) in dB/cm (k in 1/m), the attenuation of
+    Eq. (dispersion_relations) in the units of Sec. 4.1."""
     return -np.imag(k) / NP_PER_DB / 100.0
 
 
 def phase_velocity(omega, k):
+    """Phase velocity omega / Re(k) of Eq. (dispersion_relations) (Sec. 4.1)."""
     return np.asarray(omega) / np.real(k)
 
 
 def model_curves(freqs_hz, c, p):
-    """(attenuation dB/cm, phase velocity m/s) of a parameter set dict at freqs."""
+    """(attenuation dB/cm, phase velocity m/s) of a parameter set dict at
+    freqs: alpha_model and c_model of Eq. (relaxation_parameter_optimization),
+    from Eq. (dispersion_relations)."""
     w = 2 * math.pi * np.asarray(freqs_hz, np.float64)
     k = wavenumber(w, c, p["kappa1"], p["kappa2"], np.asarray(p["d1"]), np.asarray(p["alpha1"]),
                    np.asarray(p["d2"]), np.asarray(p["alpha2"]))
@@ -55,12 +59,14 @@ def model_curves(freqs_hz, c, p):
 
 
 def power_law_db_cm(freqs_hz, alpha0, y):
-    """alpha(f) = alpha0 f^y, f in MHz, result in dB/cm."""
+    """alpha(f) = alpha0 f^y, f in MHz, result in dB/cm: the target attenuation
+    law of Sec. 4.1."""
     return alpha0 * (np.asarray(freqs_hz) / 1e6) ** y
 
 
 def kk_phase_velocity(freqs_hz, alpha0, y, c0, f_ref):
-    """Kramers-Kronig phase velocity of a power law (nearly-local form).
+    """Kramers-Kronig phase velocity of a power law (nearly-local form), the
+    target phase velocity of Sec. 4.1 (its form is not printed there).
 
     alpha(omega) = a0 |omega|^y in Np/m with a0 from alpha0 [dB/cm/MHz^y];
     y != 1: 1/c = 1/c0 + a0 tan(pi y / 2) (omega^(y-1) - omega_ref^(y-1))
@@ -77,13 +83,15 @@ def kk_phase_velocity(freqs_hz, alpha0, y, c0, f_ref):
 
 
 def staggered_symbol(kh, taps):
-    """sum_i g_i sin((2i-1) k h / 2): h/2 times the symbol of the staggered derivative."""
+    """sum_i g_i sin((2i-1) k h / 2): h/2 times the symbol of the staggered
+    derivative D^{2M,4} of Sec. 3.1 without its cross tap."""
     kh = np.asarray(kh, np.float64)
     return sum(taps[i] * np.sin((2 * i + 1) * kh / 2.0) for i in range(4))
 
 
 def discrete_omega(kvec_h, c, dt, h, taps):
-    """omega of a plane wave exp(i(k.x - omega t)) under the lossless leapfrog scheme.
+    """omega of a plane wave exp(i(k.x - omega t)) under the lossless leapfrog
+    scheme of Sec. 3.1 (the staggered updates with the operator D^{2M,4}).
 
     sin(omega dt / 2) = (c dt / h) sqrt(sum_q G_q^2),
     G_q = sum_i g_i sin((2i-1) k_q h / 2) + 2 g11 sin(k_q h / 2) sum_{t != q} cos(k_t h).
@@ -100,7 +108,8 @@ def discrete_omega(kvec_h, c, dt, h, taps):
 
 
 def burgers_poisson(p_in, t, x, beta_eff, rho0, c0, iters: int = 200):
-    """Pre-shock solution of the inviscid Burgers equation for a progressive wave.
+    """Pre-shock solution of the inviscid Burgers equation for a progressive
+    wave, the reference of the nonlinearity evaluation of Sec. 4.5.
 
     p(x, tau) = p_in(tau + beta_eff x p / (rho0 c0^3)), tau = t - x/c0 the
     retarded time (the implicit Poisson / Earnshaw form, valid before shock
@@ -156,7 +165,9 @@ def burgers_rusanov(p_in, dtau, x, beta_eff, rho0, c0, cfl: float = 0.4):
 
 
 def discrete_wavenumber_1d(freqs_hz, c, h, dt, p, taps, centred=True):
-    """Complex k of the fully discrete 1D scheme with memory variables.
+    """Complex k of the fully discrete 1D scheme with memory variables
+    (Sec. 3.1 updates; recursion of Eqs. relaxation_a, relaxation_b,
+    relaxation_psi).
 
     For a mode exp(i(omega t - k x)) the stored recursion
     chi^n = b chi^{n-1} + a D^n gives chi = a D / (1 - b e^{-i omega dt}); the

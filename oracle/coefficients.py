@@ -116,7 +116,8 @@ def cfl_time_step(prob, cfl: float = 0.4) -> float:
 
 
 def boundary_depth(n: int, L: int, staggered: bool) -> np.ndarray:
-    """Depth into the boundary region (in cells, 0..L) of each point on one axis.
+    """Depth into the boundary region (in cells, 0..L) of each point on one
+    axis: the coordinate of the C-PML profiles of Sec. 3.3 and Table 1.
 
     Cell centres sit at x = i, faces at x = i + 1/2.  The region occupies the
     outer L cells of each side: on the low side its inner edge is x = L - 1/2
@@ -201,7 +202,11 @@ def to_bf16(x) -> np.ndarray:
 
 
 def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object]:
-    """All coefficient arrays of the oracle step, FP64 (flat, x fastest).
+    """All coefficient arrays of the oracle step, FP64 (flat, x fastest):
+    Eqs. (relaxation_a), (relaxation_b) per mechanism and axis, the C-PML
+    profiles of Sec. 3.3 / Table 1, K = rho c^2 and the nonlinear factor of
+    Eq. (general6) (with Eq. (general5)'s kappa0 at the faces in the literal
+    mode).
 
     Keys: K, chi (or None), buoy[q], ik1[q], a1[q] (N, n), b1[q], ik2[q],
     a2[q], b2[q], dt, taps (g1..g4, g11).

@@ -31,6 +31,7 @@ BOUNDS_LOG_ALPHA = (5.0, 12.0)
 
 
 def nmse(x, y):
+    """NMSE of Sec. 4.1: mean squared error over the variance of the target."""
     return float(np.mean((x - y) ** 2) / np.var(y))
 
 
@@ -44,6 +45,7 @@ def unpack(theta, N):
 
 
 def cost(theta, N, f, c0, att_t, c_t):
+    """J of Eq. (relaxation_parameter_optimization), w_alpha = 0.1 (Sec. 4.1)."""
     p = unpack(theta, N)
     att, cph = an.model_curves(f, c0, p)
     if not np.all(np.isfinite(att)) or not np.all(np.isfinite(cph)):
@@ -52,6 +54,9 @@ def cost(theta, N, f, c0, att_t, c_t):
 
 
 def fit(alpha0, y, N, c0=1540.0, f_ref=3e6, n_starts=24, seed=0):
+    """Minimise J (Sec. 4.1) over N mechanisms inside the Table 2 bounds by a
+    multi-start bounded quasi-Newton search polished by Nelder-Mead; returns
+    the parameter dict with its cost and the attenuation / phase errors."""
     f = np.linspace(1e6, 20e6, 77)
     att_t = an.power_law_db_cm(f, alpha0, y)
     c_t = an.kk_phase_velocity(f, alpha0, y, c0, f_ref)
@@ -106,7 +111,8 @@ def curves_batch(freqs_hz, c0, k1, k2, d1, a1, d2, a2):
 
 
 def grid_cost(theta, N, f, c0, att_t, c_t):
-    """Cost J of B parameter vectors theta (B, 2 + 4N) in the layout of unpack."""
+    """Cost J (Eq. relaxation_parameter_optimization) of B parameter vectors
+    theta (B, 2 + 4N) in the layout of unpack."""
     k1, k2 = theta[:, 0], theta[:, 1]
     d1 = 10.0 ** theta[:, 2:2 + N].T
     d2 = 10.0 ** theta[:, 2 + N:2 + 2 * N].T
