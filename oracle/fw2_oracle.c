@@ -246,6 +246,9 @@ static void pressure_half_step(const orc_grid *G, const orc_coef *C,
   }
 }
 
+/* Additive sources (reading N2: the paper drives its transducers with the
+ * pulse of Sec. 4.5 without stating the coupling): signal row `step` added
+ * to p or to one velocity component at the source cells. */
 static void add_sources(const orc_sources *src, orc_state *S, int64_t step,
                         int want_pressure) {
   if (!src || src->n_pts == 0 || step >= src->n_rows) return;
@@ -261,6 +264,9 @@ static void add_sources(const orc_sources *src, orc_state *S, int64_t step,
   }
 }
 
+/* Sensor traces (the recorded pressure of Secs. 4.2-4.5): trace row `step`
+ * holds p^{n+1} averaged over the cells of each sensor group (array
+ * elements record the mean over their cells). */
 static void record(const orc_record *rec, const orc_state *S, int64_t step) {
   if (!rec || rec->n_pts == 0 || step >= rec->n_rows) return;
   double *row = rec->trace + step * rec->n_groups;
