@@ -246,9 +246,10 @@ static void pressure_half_step(const orc_grid *G, const orc_coef *C,
   }
 }
 
-/* Additive sources (reading N2: the paper drives its transducers with the
- * pulse of Sec. 4.5 without stating the coupling): signal row `step` added
- * to p or to one velocity component at the source cells. */
+/* Additive sources (the paper drives its transducers with the pulse of
+ * Sec. 4.5 without stating how they couple to the field; adding the signal
+ * is the plain reading): signal row `step` added to p or to one velocity
+ * component at the source cells. */
 static void add_sources(const orc_sources *src, orc_state *S, int64_t step,
                         int want_pressure) {
   if (!src || src->n_pts == 0 || step >= src->n_rows) return;
