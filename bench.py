@@ -269,8 +269,7 @@ def run_fw2(args, rank, world, dist):
         n = args.n
         prob = synth.abdominal_problem(n=n, n_steps=total_steps, seed=1 + rank)
         maps, mbytes, kv, kp = "f32", 4, "vel2d", "prs2d"
-        workload = (f"2D heterogeneous nonlinear abdominal wall, {n}x{n} cells at lambda/12 for 3 MHz, "
-                    f"N=4 mechanisms, beta 4-6, 128-element focused array, element-mean traces, FP32 maps")
+        workload = abdominal_workload(n)
     if args.nl:
         prob.nl_mode = args.nl
         workload += f", nonlinear mode {args.nl}"
@@ -573,6 +572,11 @@ def run_serve(args, rank, world, dist):
     print(json.dumps(out), flush=True)
 
 
+def abdominal_workload(n):
+    return (f"2D heterogeneous nonlinear abdominal wall, {n}x{n} cells at lambda/12 for 3 MHz, "
+            f"N=4 mechanisms, beta 4-6, 128-element focused array, element-mean traces, FP32 maps")
+
+
 def run_reference(args, rank, world):
     """The FP64 oracle on the host cores, on a bounded window of the same workload."""
     if rank != 0:
@@ -596,8 +600,10 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded abdominal-wall-like medium)",
-           "config": {"workload": f"2D heterogeneous nonlinear abdominal wall, {n}x{n} cells, N=4 "
-                                  f"(oracle on a 256x256 window)"},
+           "config": {"workload": abdominal_workload(n), "grid": [n, n], "n_relax": prob.nrelax,
+                      "nl_mode": prob.nl_mode, "map_precision": "f32", "taps": "taylor",
+                      "pml_cells": prob.pml_transition + prob.pml_bound,
+                      "parallelism": f"replicas x{world} (rank 0 runs the oracle)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
