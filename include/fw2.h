@@ -107,7 +107,7 @@ typedef struct {
   int32_t pml_transition;/* L_T, cells per side (Sec. 3.3) */
   int32_t pml_bound;     /* L_B, cells per side */
   int32_t pml_reading;   /* FW2_PML_C (default), FW2_PML_A or FW2_PML_B */
-  int32_t map_precision; /* FW2_MAP_F32 or FW2_MAP_BF16 storage of coefficient maps */
+  int32_t map_precision; /* FW2_MAP_F32, FW2_MAP_BF16 or FW2_MAP_IDX_U8 (2D) storage of the maps */
   double pml_rc;         /* reflection target R_c of Table 1 (default 1e-3) */
   double pml_npow;       /* polynomial order of the d ramp (default 2) */
   double pml_cp;         /* c_p of Table 1 [m/s]; <= 0: largest c of the medium */
