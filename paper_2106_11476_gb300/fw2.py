@@ -139,18 +139,21 @@ def _same_space(*arrays):
 # ---------------------------------------------------------------- C names ---
 
 def fw2_config_init() -> Config:
+    """Defaults of fw2_config (fw2_config_init in include/fw2.h)."""
     cfg = Config()
     _check(lib().fw2_config_init(C.byref(cfg)))
     return cfg
 
 
 def fw2_create(cfg: Config) -> int:
+    """Create a context for one grid (fw2_create); returns the handle."""
     h = C.c_void_p()
     _check(lib().fw2_create(C.byref(cfg), C.byref(h)))
     return h.value
 
 
 def fw2_set_medium(ctx, c, rho, beta=None):
+    """c, rho and beta of every cell, host or device arrays (fw2_set_medium)."""
     space = _same_space(c, rho, beta)
     pc, _, kc = _ptr(np.asarray(c, np.float32) if isinstance(c, np.ndarray) else c)
     pr, _, kr = _ptr(np.asarray(rho, np.float32) if isinstance(rho, np.ndarray) else rho)
@@ -159,6 +162,7 @@ def fw2_set_medium(ctx, c, rho, beta=None):
 
 
 def fw2_set_relaxation(ctx, kappa1, kappa2, d1, alpha1, d2, alpha2):
+    """Interior relaxation parameters of every cell (fw2_set_relaxation)."""
     arrs = [np.asarray(x, np.float32) if isinstance(x, np.ndarray) else x
             for x in (kappa1, kappa2, d1, alpha1, d2, alpha2)]
     space = _same_space(*arrs)
@@ -181,6 +185,7 @@ def fw2_set_medium_indexed(ctx, tissue, n_tissue: int, c, rho, beta, kappa1, kap
 
 
 def fw2_add_source(ctx, kind: str, idx, group, signal):
+    """Add an additive source of kind FW2_SRC_* (fw2_add_source)."""
     idx = np.asarray(idx, np.int64) if isinstance(idx, np.ndarray) else idx
     group = np.asarray(group, np.int32) if isinstance(group, np.ndarray) else group
     signal = np.asarray(signal, np.float32) if isinstance(signal, np.ndarray) else signal
@@ -194,6 +199,7 @@ def fw2_add_source(ctx, kind: str, idx, group, signal):
 
 
 def fw2_record(ctx, idx, group, n_groups: int, out, n_steps: int):
+    """Record p after every step into a caller-owned device buffer (fw2_record)."""
     idx = np.asarray(idx, np.int64) if isinstance(idx, np.ndarray) else idx
     group = np.asarray(group, np.int32) if isinstance(group, np.ndarray) else group
     space = _same_space(idx, group)
@@ -204,69 +210,82 @@ def fw2_record(ctx, idx, group, n_groups: int, out, n_steps: int):
 
 
 def fw2_step(ctx, n_steps: int):
+    """Advance n_steps time steps, asynchronously on the context stream (fw2_step)."""
     _check(lib().fw2_step(ctx, int(n_steps)), ctx)
 
 
 def fw2_destroy(ctx):
+    """Release the context (fw2_destroy)."""
     if ctx:
         lib().fw2_destroy(ctx)
 
 
 def fw2_get_dt(ctx) -> float:
+    """The time step in use; builds the coefficient maps if needed (fw2_get_dt)."""
     v = C.c_double()
     _check(lib().fw2_get_dt(ctx, C.byref(v)), ctx)
     return v.value
 
 
 def fw2_get_step(ctx) -> int:
+    """Index of the next time step (fw2_get_step)."""
     v = C.c_int64()
     _check(lib().fw2_get_step(ctx, C.byref(v)), ctx)
     return v.value
 
 
 def fw2_set_step(ctx, step: int):
+    """Set the index of the next time step, for restore (fw2_set_step)."""
     _check(lib().fw2_set_step(ctx, int(step)), ctx)
 
 
 def fw2_get_field(ctx, field: str, out):
+    """Copy a state array out (fw2_get_field)."""
     p, space, keep = _ptr(out)
     _check(lib().fw2_get_field(ctx, FIELD[field], p, space), ctx)
     return out
 
 
 def fw2_set_field(ctx, field: str, arr):
+    """Copy a state array in (fw2_set_field)."""
     arr = np.asarray(arr, np.float32) if isinstance(arr, np.ndarray) else arr
     p, space, keep = _ptr(arr)
     _check(lib().fw2_set_field(ctx, FIELD[field], p, space), ctx)
 
 
 def fw2_reset(ctx):
+    """Zero the state and the step counter (fw2_reset)."""
     _check(lib().fw2_reset(ctx), ctx)
 
 
 def fw2_synchronize(ctx):
+    """Wait for the context stream; raises on a device-side wait that gave up (fw2_synchronize)."""
     _check(lib().fw2_synchronize(ctx), ctx)
 
 
 def fw2_check_field(ctx, bound: float):
+    """Scan p for non-finite values or a bound (fw2_check_field)."""
     m = C.c_float()
     st = lib().fw2_check_field(ctx, C.c_float(bound), C.byref(m))
     return st, m.value
 
 
 def fw2_device_bytes(ctx) -> int:
+    """Device bytes the context holds (fw2_device_bytes)."""
     v = C.c_int64()
     _check(lib().fw2_device_bytes(ctx, C.byref(v)), ctx)
     return v.value
 
 
 def fw2_kernel_launches(ctx) -> int:
+    """Kernels the context has launched (fw2_kernel_launches)."""
     v = C.c_int64()
     _check(lib().fw2_kernel_launches(ctx, C.byref(v)), ctx)
     return v.value
 
 
 def fw2_profile(ctx, enable: bool):
+    """Switch per-kernel event timing on or off (fw2_profile)."""
     _check(lib().fw2_profile(ctx, 1 if enable else 0), ctx)
 
 
@@ -314,6 +333,7 @@ def _bcheck(status: int, batch):
 
 
 def fw2_batch_create(ctxs) -> int:
+    """One batch over several 2D contexts (fw2_batch_create); returns the handle."""
     arr = (C.c_void_p * len(ctxs))(*ctxs)
     h = C.c_void_p()
     st = lib().fw2_batch_create(arr, len(ctxs), C.byref(h))
@@ -323,30 +343,36 @@ def fw2_batch_create(ctxs) -> int:
 
 
 def fw2_batch_step(batch, n_steps: int):
+    """Advance every context of the batch n_steps (fw2_batch_step)."""
     _bcheck(lib().fw2_batch_step(batch, int(n_steps)), batch)
 
 
 def fw2_batch_synchronize(batch):
+    """Wait for the batch (fw2_batch_synchronize)."""
     _bcheck(lib().fw2_batch_synchronize(batch), batch)
 
 
 def fw2_batch_info(batch):
+    """(grid, order, launches) chosen by the batch autotuner (fw2_batch_info)."""
     g, o, n = C.c_int32(), C.c_int32(), C.c_int64()
     _bcheck(lib().fw2_batch_info(batch, C.byref(g), C.byref(o), C.byref(n)), batch)
     return g.value, o.value, n.value
 
 
 def fw2_batch_destroy(batch):
+    """Release the batch (fw2_batch_destroy); the contexts remain."""
     if batch:
         lib().fw2_batch_destroy(batch)
 
 
 def fw2_last_error(ctx=None) -> str:
+    """Text of the last error of a context (or of the library with None)."""
     r = lib().fw2_last_error(ctx)
     return r.decode() if r else ""
 
 
 def fw2_abi_version() -> int:
+    """Version of the C ABI."""
     return lib().fw2_abi_version()
 
 
