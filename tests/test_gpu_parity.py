@@ -585,6 +585,27 @@ def test_steps_past_signal_and_trace_rows(fw2):
     assert_field("p", sim.field("p"), orc.field("p"))
 
 
+@pytest.mark.parametrize("dims", [2, 3])
+def test_empty_inputs(fw2, dims):
+    """No sources, no sensors, zero steps: a zero state stays exactly zero on
+    every path (the memory variables and the C-PML included), and zero steps
+    change nothing."""
+    shape = (200, 72) if dims == 2 else (140, 40, 24)
+    prob = synth.homogeneous(shape, 1e-4, 0.0, relax=synth.relaxation_sets()["N2_y1.0_a0.5"])
+    prob.dt = 0.3e-4 / 1540.0
+    prob.pml_transition, prob.pml_bound = 6, 2
+    for maps in ("f32", "bf16"):
+        sim = fw2.Simulation(prob, map_precision=maps)
+        sim.step(0)
+        assert fw2.fw2_get_step(sim.ctx) == 0
+        sim.step(7)
+        sim.synchronize()
+        assert fw2.fw2_get_step(sim.ctx) == 7
+        for name in state_names(prob):
+            assert not np.any(sim.field(name)), name
+        sim.close()
+
+
 def test_checkpoint_restore_is_bitwise(fw2):
     """Snapshot at step 60 (fields + step counter), restore into a fresh
     context, continue 40 steps: identical to an uninterrupted 100-step run."""
