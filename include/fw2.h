@@ -259,12 +259,14 @@ fw2_status fw2_check_field(fw2_ctx *ctx, float bound, float *max_abs);
  * default stream).  Scratch: a file-scope device array of 2^20 floats
  * (4 MiB), one partial per row, held by every GPU that loads the library
  * until the process exits; n_rows above 2^20 is rejected with FW2_EINVAL.
- * The first call on a device resolves that array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture.  Calls
- * share the array: calls that overlap on the GPU race; each call overwrites
- * every row it uses, so nothing carries over.  Calls no cudaMalloc, cudaFree
- * or other allocating routine.  Errors: FW2_EINVAL (null pointer, bad
- * sizes), FW2_ECUDA (launch failure); fw2_last_error(NULL) explains. */
+ * Every call looks up that array's device address in the current context
+ * (cudaGetSymbolAddress); the first call on a device may load the library's
+ * device code, so it should come before any stream capture.  Calls share
+ * the array: calls that overlap on the GPU race; each call overwrites every
+ * row it uses, so nothing carries over.  Calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Errors: FW2_EINVAL (null pointer, a pointer
+ * that is not device or managed memory of the current device, bad sizes),
+ * FW2_ECUDA (launch failure); fw2_last_error(NULL) explains. */
 fw2_status fw2_field_absmax_noalloc(const float *field, int64_t row_len, int64_t n_rows,
                                     int64_t row_pitch, float *out, void *stream);
 /* Time-space optimised taps of the staggered operator of an ndim-dimensional

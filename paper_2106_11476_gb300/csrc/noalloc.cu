@@ -7,8 +7,6 @@
 // a latency-critical loop that cannot afford the device-wide synchronisation
 // cudaMalloc / cudaFree may cause.  Its scratch is the file-scope device
 // array below, held by every GPU that loads the library until exit.
-#include <mutex>
-
 #include "fw2.h"
 #include "fw2_internal.cuh"
 
@@ -21,10 +19,6 @@ namespace {
 // Capacity of the scratch: one partial maximum per field row (4 MiB).
 constexpr long long kScratchRows = 1LL << 20;
 __device__ __align__(256) float g_row_absmax[kScratchRows];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-float *g_scratch[kMaxDevices] = {nullptr};
 
 // One warp per row: max |x| over the row's row_len values, +inf if any is
 // non-finite; every row r < n_rows of the scratch is overwritten.
@@ -59,22 +53,30 @@ __global__ void rows_fold_kernel(const float *rowmax, long long n_rows, float *o
   if (threadIdx.x == 0) *out = red[0];
 }
 
-// Device address of the scratch on the current device, resolved once per
-// device (host code may not use the array's name as a device address).
+// Device address of the scratch in the current device's context.  Host code
+// may not use the array's name as a device address, so it is looked up on
+// every call: a lookup is cheap once the module is loaded, and nothing is
+// cached that a device reset (a new primary context) would leave stale.
 cudaError_t scratch_for_current_device(float **ptr) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_row_absmax);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_row_absmax);
-    if (e != cudaSuccess) return e;
-    g_scratch[dev] = static_cast<float *>(p);
-  }
-  *ptr = g_scratch[dev];
+  *ptr = static_cast<float *>(p);
   return cudaSuccess;
+}
+
+// True when p is device (or managed) memory that the current device owns;
+// host memory, pinned or not, and memory of another device are refused
+// before any kernel could dereference them.  Queries only, no allocation.
+bool on_current_device(const void *p) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error so the next runtime call does not report it
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -83,6 +85,11 @@ extern "C" fw2_status fw2_field_absmax_noalloc(const float *field, int64_t row_l
                                                int64_t row_pitch, float *out, void *stream) {
   if (!field || !out) {
     fw2::set_global_error("fw2_field_absmax_noalloc: field and out must be device pointers");
+    return FW2_EINVAL;
+  }
+  if (!on_current_device(field) || !on_current_device(out)) {
+    fw2::set_global_error(
+        "fw2_field_absmax_noalloc: field and out must be device memory of the current device");
     return FW2_EINVAL;
   }
   if (row_len < 1 || n_rows < 1 || row_pitch < row_len) {

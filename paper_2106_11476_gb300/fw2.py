@@ -320,10 +320,31 @@ def fw2_selftest_bounded_wait(limit_ns: int) -> bool:
 
 def fw2_field_absmax_noalloc(field, row_len: int, n_rows: int, row_pitch: int, out, stream=None) -> int:
     """max |field| over n_rows rows into the one-element device tensor `out`,
-    without allocating (returns the status; see include/fw2.h)."""
-    return lib().fw2_field_absmax_noalloc(C.c_void_p(field.data_ptr()), int(row_len), int(n_rows),
-                                          int(row_pitch), C.c_void_p(out.data_ptr()),
-                                          C.c_void_p(stream if stream else 0))
+    without allocating (fw2_field_absmax_noalloc; returns the status).
+
+    `field` and `out` must be float32 CUDA tensors of one device, `field`
+    contiguous and holding every row that the call reads.  The call is
+    enqueued on `stream` (a cudaStream_t handle), by default on torch's
+    current stream of the field's device, so that it follows the work that
+    produced the field.  Arguments that would make the kernel reach outside
+    the tensors raise ValueError before any call."""
+    import torch
+    for name, t in (("field", field), ("out", out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+            raise ValueError(f"{name} must be a float32 CUDA tensor")
+    if out.device != field.device:
+        raise ValueError("field and out must be on the same device")
+    if out.numel() < 1:
+        raise ValueError("out needs one element")
+    if not field.is_contiguous():
+        raise ValueError("field must be contiguous")
+    row_len, n_rows, row_pitch = int(row_len), int(n_rows), int(row_pitch)
+    if row_len >= 1 and n_rows >= 1 and (n_rows - 1) * row_pitch + row_len > field.numel():
+        raise ValueError("rows reach past the field's storage")
+    if stream is None:
+        stream = torch.cuda.current_stream(field.device).cuda_stream
+    return lib().fw2_field_absmax_noalloc(C.c_void_p(field.data_ptr()), row_len, n_rows, row_pitch,
+                                          C.c_void_p(out.data_ptr()), C.c_void_p(stream if stream else 0))
 
 
 def _bcheck(status: int, batch):
