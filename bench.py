@@ -433,7 +433,7 @@ def run_batch(args, rank, world, dist):
     cells = sum(p.n_pts for p in probs)
     sims = [fw2.Simulation(p, map_precision="idx") for p in probs]
     batch = fw2.fw2_batch_create([s.ctx for s in sims])
-    fw2.fw2_batch_step(batch, max(args.warmup, 4))       # includes the 4 tuning steps
+    fw2.fw2_batch_step(batch, max(args.warmup, 13))      # includes the 13 tuning steps
     fw2.fw2_batch_synchronize(batch)
     grid, order, l0 = fw2.fw2_batch_info(batch)
     if dist:

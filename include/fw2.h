@@ -204,9 +204,10 @@ fw2_status fw2_destroy(fw2_ctx *ctx);
  * batch runs one persistent launch per half step over a tile table of all
  * contexts (grouped by mechanism count and map kind), one launch each for
  * the sources and recordings of all contexts, and replays chunks of steps
- * as a captured CUDA graph.  The first four batch steps try four launch
- * configurations (persistent grid size x tile order) and keep the fastest;
- * every configuration computes the same result. */
+ * as a captured CUDA graph.  The first batch step warms up; the next twelve
+ * time four launch configurations (persistent grid size x tile order),
+ * three steps each, and the one with the fastest median is kept; every
+ * configuration computes the same result. */
 typedef struct fw2_batch fw2_batch;
 /* Contexts are borrowed (they must outlive the batch), 2D, with medium set;
  * their coefficient maps and sources are built here.  Re-create the batch

@@ -17,21 +17,21 @@ def fw2(fw2lib):
 def _problems():
     probs = []
     for t in range(3):   # full-synthetic-aperture style: one element fires per event
-        probs.append(("idx", synth.indexed_abdominal_problem(nx=260, ny=170, n_steps=90, n_elements=8,
+        probs.append(("idx", synth.indexed_abdominal_problem(nx=260, ny=170, n_steps=95, n_elements=8,
                                                             transmit=t, pml_lambda=(1.0, 0.5))))
-    probs.append(("idx", synth.indexed_abdominal_problem(nx=131, ny=97, n_steps=90, n_elements=4,
+    probs.append(("idx", synth.indexed_abdominal_problem(nx=131, ny=97, n_steps=95, n_elements=4,
                                                         pml_lambda=(1.0, 0.5), seed=7)))
     from tests.test_gpu_parity import small_2d
-    probs.append(("f32", small_2d(nx=200, ny=136, N=2, steps=90)))
-    probs.append(("f32", small_2d(nx=150, ny=60, N=4, nl="pressure", steps=90, pml=(6, 2), vel_src=True)))
-    probs.append(("bf16", small_2d(nx=96, ny=96, N=4, steps=90, pml=(6, 2))))
+    probs.append(("f32", small_2d(nx=200, ny=136, N=2, steps=95)))
+    probs.append(("f32", small_2d(nx=150, ny=60, N=4, nl="pressure", steps=95, pml=(6, 2), vel_src=True)))
+    probs.append(("bf16", small_2d(nx=96, ny=96, N=4, steps=95, pml=(6, 2))))
     # both nonlinear factors, grouped with the linear N = 2 context above
-    probs.append(("f32", small_2d(nx=180, ny=100, N=2, nl="literal", steps=90, amp=2e7)))
+    probs.append(("f32", small_2d(nx=180, ny=100, N=2, nl="literal", steps=95, amp=2e7)))
     return probs
 
 
 def test_batch_equals_each_context_alone(fw2):
-    steps = 75                     # 4 tuning steps, one 64-step graph, 7 plain
+    steps = 90                     # 13 tuning steps, one 64-step graph, 13 plain
     probs = _problems()
     alone = []
     for maps, p in probs:
@@ -76,13 +76,13 @@ def test_batch_rejects_3d(fw2):
 
 def test_batch_full_size_equals_each_context_alone(fw2):
     """The benchmark's batch (64 focused transmits over one 2048 x 1024
-    tissue-index medium and 16 uneven instances, 151 M cells) after the four
-    autotuning steps and four more: sampled contexts hold bitwise what they
-    hold when stepped alone."""
+    tissue-index medium and 16 uneven instances, 151 M cells) after the
+    thirteen autotuning steps and three more: sampled contexts hold bitwise
+    what they hold when stepped alone."""
     import types
     import bench
-    probs = bench.batch_problems(types.SimpleNamespace(warmup=4, steps=4), 0)
-    steps = 8
+    probs = bench.batch_problems(types.SimpleNamespace(warmup=8, steps=8), 0)
+    steps = 16
     sims = [fw2.Simulation(p, map_precision="idx") for p in probs]
     batch = fw2.fw2_batch_create([s.ctx for s in sims])
     try:
