@@ -64,18 +64,25 @@ enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2, FW2_NL_LITERA
  * uint8 tissue index per cell into per-tissue float tables (2D only; set the
  * medium with fw2_set_medium_indexed) */
 enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1, FW2_MAP_IDX_U8 = 2 };
-/* C-PML geometry (Sec. 3.3, Table 1).  In every reading the nu >= 2
+/* C-PML geometry (Sec. 3.3, Table 1).  In both readings the nu >= 2
  * parameters fall to zero over the inner L_T cells with the cosine transition
- * and kappa is kept.  A: d^{nu=1} (polynomial) and alpha^{nu=1} (linear) ramp
- * over all L_T + L_B cells.  B: both ramp over the outer L_B cells only.
- * C (default): d^{nu=1} as in A; alpha^{nu=1} is blended by the cosine
- * transition over the inner L_T cells from the tissue's value into the
- * C-PML profile d_target (1 - x/L) (linear to zero at the outer edge,
- * d_target of Table 1 acting as the maximum frequency shift), so the
- * transition layer turns the tissue's first mechanism into the single
- * C-PML mechanism.  Only C meets the paper's reflection figures in the
- * Table 2 tissue while staying stable over long runs. */
-enum { FW2_PML_A = 0, FW2_PML_B = 1, FW2_PML_C = 2 };
+ * and kappa is kept, and d^{nu=1} ramps as a polynomial over all L_T + L_B
+ * cells toward Table 1's d_target.
+ * A: Table 1 as printed: alpha^{nu=1} falls linearly from the tissue's value
+ * to zero over all L_T + L_B cells.
+ * C (default): NOT Table 1's alpha^{nu=1} profile.  alpha^{nu=1} is blended
+ * by the cosine transition over the inner L_T cells from the tissue's value
+ * into the C-PML profile d_target (1 - x/L), which falls linearly to zero at
+ * the outer edge (d_target acting as the maximum frequency shift of a
+ * C-PML), so the transition layer turns the tissue's first mechanism into
+ * the single C-PML mechanism.  Why: with Table 2's alpha^{nu=1} = 2.8e8 1/s,
+ * far above the C-PML damping, reading A's first mechanism absorbs only in
+ * the outermost cells and the boundary reflects at about -28 dB in that
+ * tissue (3 + 1 wavelengths); C reflects at -53 dB there and stays stable.
+ * In a non-attenuating medium both reach about -60 dB.  The value 1 (an
+ * earlier reading that ramped the first mechanism over the outer L_B cells
+ * only, reflecting at about -9 dB) is rejected with FW2_EINVAL. */
+enum { FW2_PML_A = 0, FW2_PML_C = 2 };
 /* time alignment of the memory term in Eq. (relaxation_psi): CENTRED uses
  * the mean of the memory variable before and after its update (D^{n-1/2}
  * estimated by (D^n + D^{n-1}) / 2); ENDPOINT uses the updated value. */
@@ -106,7 +113,7 @@ typedef struct {
                             1225/1024, -245/3072, 49/5120, -5/7168, g11 = 0 */
   int32_t pml_transition;/* L_T, cells per side (Sec. 3.3) */
   int32_t pml_bound;     /* L_B, cells per side */
-  int32_t pml_reading;   /* FW2_PML_C (default), FW2_PML_A or FW2_PML_B */
+  int32_t pml_reading;   /* FW2_PML_C (default) or FW2_PML_A */
   int32_t map_precision; /* FW2_MAP_F32, FW2_MAP_BF16 or FW2_MAP_IDX_U8 (2D) storage of the maps */
   double pml_rc;         /* reflection target R_c of Table 1 (default 1e-3) */
   double pml_npow;       /* polynomial order of the d ramp (default 2) */

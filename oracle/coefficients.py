@@ -144,7 +144,6 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
       nu >= 2      : cosine     g = (1 - cos(pi x / L_T)) / 2 toward 0 over
                      the transition layer, 0 beyond it.
     Reading A: the nu = 1 ramps span the whole boundary L_T + L_B.
-    Reading B: the nu = 1 ramps span only the outer L_B cells.
     Reading C: as A for d^{nu=1}; alpha^{nu=1} is blended by the cosine
     transition over L_T from the tissue's value into the C-PML profile
     d_target (1 - x/L), which is linear to 0 at the outer edge (d_target
@@ -153,6 +152,8 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
     C-PML mechanism.
     `nu` is 1-based as in the paper; `which` is "d" or "alpha".
     """
+    if reading.upper() not in ("A", "C"):
+        raise ValueError(f"C-PML reading {reading!r}: A or C")
     X0 = np.asarray(X0, np.float64)
     L = LT + LB
     out = X0.copy()
@@ -168,12 +169,8 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
         a_cfs = d_target * (1.0 - depth / L)
         return np.where(inside, (1.0 - gT) * X0 + gT * a_cfs, X0)
     if nu == 1:
-        if reading.upper() in ("A", "C"):
-            s = depth / L
-            active = inside
-        else:
-            s = np.where(depth > LT, (depth - LT) / max(LB, 1), 0.0)
-            active = depth > LT
+        s = depth / L
+        active = inside
         if which == "d":
             g = s ** npow
             tgt = d_target

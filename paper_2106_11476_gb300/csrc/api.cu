@@ -456,7 +456,8 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
     if (!(cfg.pml_rc > 0.0 && cfg.pml_rc < 1.0)) return fail(nullptr, FW2_EINVAL, "pml_rc must lie in (0, 1)");
     if (!(cfg.pml_npow >= 0.0)) return fail(nullptr, FW2_EINVAL, "pml_npow must be >= 0");
   }
-  if (cfg.pml_reading < FW2_PML_A || cfg.pml_reading > FW2_PML_C) return fail(nullptr, FW2_EINVAL, "bad pml_reading");
+  if (cfg.pml_reading != FW2_PML_A && cfg.pml_reading != FW2_PML_C)
+    return fail(nullptr, FW2_EINVAL, "bad pml_reading (FW2_PML_A = 0 or FW2_PML_C = 2)");
   if (cfg.map_precision < FW2_MAP_F32 || cfg.map_precision > FW2_MAP_IDX_U8)
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
   if (cfg.map_precision == FW2_MAP_IDX_U8 && cfg.ndim != 2)

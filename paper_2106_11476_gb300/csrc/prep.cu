@@ -73,13 +73,7 @@ __device__ double ramp(const PrepParams &Q, double X0, double depth, int nu, boo
     return (1.0 - gT) * X0 + gT * a_cfs;
   }
   if (nu == 0) {
-    double s;
-    if (Q.reading != 1) {
-      s = depth / L;
-    } else {
-      if (depth <= LT) return X0;
-      s = (depth - LT) / (LB > 0 ? LB : 1);
-    }
+    const double s = depth / L;
     if (is_d) return (Q.d_target - X0) * pow(s, Q.npow) + X0;
     return (0.0 - X0) * s + X0;
   }

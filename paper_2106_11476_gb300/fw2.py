@@ -23,7 +23,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 BC = {"zero": 0, "periodic": 1}
 NL = {"off": 0, "pressure": 1, "westervelt": 2, "literal": 3}
 MAP = {"f32": 0, "bf16": 1, "idx": 2}
-PML_READING = {"A": 0, "B": 1, "C": 2}
+PML_READING = {"A": 0, "C": 2}
 MEM_ALIGN = {"centred": 0, "endpoint": 1}
 SRC_KIND = {"p": 0, "vx": 1, "vy": 2, "vz": 3}
 FIELD = {"p": 0, "vx": 1, "vy": 2, "vz": 3, "psi1x": 4, "psi1y": 5, "psi1z": 6,

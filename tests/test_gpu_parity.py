@@ -159,7 +159,7 @@ CASES_2D = {
     "base": dict(),
     "nonlinear-pressure": dict(nl="pressure"),
     "westervelt-N4": dict(nl="westervelt", N=4),
-    "endpoint-readingB": dict(alignment="endpoint", reading="B"),
+    "endpoint-readingA": dict(alignment="endpoint", reading="A"),
     "readingA": dict(reading="A", N=4),
     "ragged-203x77": dict(nx=203, ny=77, pml=(8, 3)),
     "velocity-sources": dict(vel_src=True, N=4),
