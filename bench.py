@@ -9,8 +9,17 @@ step is one full time step: velocity half step, sources, pressure half step,
 recording.  The state (19 float32 arrays, 1.3 GB) plus the coefficient maps
 exceed L2, so no flush is needed between steps.
 
+The line carries the roofline of the dominant kernel (compulsory bytes of
+the step, charged to the half step that updates each array), the parity of
+the reached state against the FP64 oracle on a window, the end-to-end rate
+through the C ABI from host buffers, the oracle's own rate on host cores,
+and, under `other_configs`, the plain 512^2 method (1000 steps), the 768^3
+transcranial medium and the batch of 80 transmit events, each measured the
+same way in the same run.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fw2|reference]
-                  [--workload abdominal|abdominal-idx|skull|batch|serve]
+                  [--workload abdominal|abdominal-idx|skull|plain|batch|serve]
+                  [--configs all|none|plain,skull,batch] [--no-parity]
                   [--taps taylor|time-space] [--nl off|pressure|westervelt|literal]
 
 Under torchrun each rank simulates its own transmit event (independent
@@ -59,39 +68,59 @@ def strip_cell_counts(shape, L):
     return out
 
 
-def algorithmic_bytes(shape, N, L, nl, map_bytes=4, nl_vel=False):
-    """Compulsory DRAM bytes of one launch of the velocity and of the pressure kernel.
-
-    Every streamed array is read once and every updated array written once;
-    the stencil operand (p, or v_q) is read once.  Coefficient a, b pairs of
-    an axis come from its boundary strip inside the C-PML region, otherwise
-    from the interior maps (read once per cell when any axis needs them).
-    The literal nonlinear system's momentum factor adds the K map to the
-    velocity half step (nl_vel).
-    """
+def _strip_bytes(shape, N, L, map_bytes):
+    """Bytes of the a, b pairs one half step reads for every cell: inside the
+    C-PML strip of an axis that axis' set, the interior set when some axis
+    is outside its strip."""
     nd = len(shape)
-    classes = strip_cell_counts(shape, L)
     coef = 0
-    for axes_in, cnt in classes.items():
+    for axes_in, cnt in strip_cell_counts(shape, L).items():
         sets = len(axes_in) + (1 if len(axes_in) < nd else 0)
         coef += cnt * sets * 2 * N * map_bytes
+    return coef
+
+
+def algorithmic_bytes(shape, N, L, nl, map_bytes=4, nl_vel=False):
+    """Compulsory DRAM bytes of one time step, split into the velocity and the
+    pressure half step.
+
+    The minimum for the whole step: every state array (p, v_q, psi1_q^nu,
+    psi2_q^nu) read once and written once, every coefficient map read once,
+    a, b pairs of an axis from its C-PML strip inside the boundary region.
+    Each state array is charged to the half step that updates it: v_q and
+    psi1 to the velocity half step (with rho, 1/kappa1, a1, b1 and, for the
+    literal nonlinear system's momentum factor, K), p and psi2 to the
+    pressure half step (with K, chi, 1/kappa2, a2, b2).  Reading p in the
+    velocity half step and v_q in the pressure half step again, as stencil
+    operands, is the cost of splitting the step into two launches:
+    split_overhead_bytes."""
+    nd = len(shape)
+    coef = _strip_bytes(shape, N, L, map_bytes)
     n = int(np.prod(shape))
-    vel = n * (4 + map_bytes + map_bytes + (map_bytes if nl_vel else 0) + nd * 8 + nd * N * 8) + coef
-    prs = n * (nd * 4 + map_bytes + (map_bytes if nl else 0) + map_bytes + 8 + nd * N * 8) + coef
+    vel = n * (nd * 8 + nd * N * 8 + map_bytes + map_bytes + (map_bytes if nl_vel else 0)) + coef
+    prs = n * (8 + nd * N * 8 + map_bytes + (map_bytes if nl else 0) + map_bytes) + coef
     return vel, prs
 
 
 def algorithmic_bytes_indexed(shape, N, L, nl):
-    """As algorithmic_bytes for the tissue-index form: per cell one uint8 index
-    replaces the interior maps (tables live in shared memory); cells inside a
-    C-PML strip still read that axis' float a, b."""
+    """As algorithmic_bytes for the tissue-index form: one uint8 index per
+    cell replaces the interior maps (the tables live in shared memory) and is
+    charged to the velocity half step; cells inside a C-PML strip still read
+    that axis' float a, b."""
     nd = len(shape)
-    classes = strip_cell_counts(shape, L)
-    coef = sum(cnt * len(axes_in) * 2 * N * 4 for axes_in, cnt in classes.items())
+    coef = sum(cnt * len(axes_in) * 2 * N * 4 for axes_in, cnt in strip_cell_counts(shape, L).items())
     n = int(np.prod(shape))
-    vel = n * (4 + 1 + nd * 8 + nd * N * 8) + coef
-    prs = n * (nd * 4 + 1 + 8 + nd * N * 8) + coef
+    vel = n * (1 + nd * 8 + nd * N * 8) + coef
+    prs = n * (8 + nd * N * 8) + coef
     return vel, prs
+
+
+def split_overhead_bytes(shape, indexed=False):
+    """Bytes per launch that the two-launch split reads beyond the step's
+    minimum: p again in the velocity half step, v_q again in the pressure
+    half step (and the tissue index again there)."""
+    n = int(np.prod(shape))
+    return 4 * n, 4 * len(shape) * n + (n if indexed else 0)
 
 
 # --------------------------------------------------------------------------
@@ -204,20 +233,118 @@ def device_id_for_smi():
         return vis or "0"
 
 
-def oracle_baseline(prob, steps, window, maps="f32"):
-    """The FP64 oracle, as it stands, on a window of the workload (host cores)."""
+def _round_of(maps):
+    """The oracle's model of the maps the kernels stream (the index form's
+    coefficients are the float maps gathered from its tables)."""
+    return "f32" if maps == "idx" else maps
+
+
+def oracle_baseline(prob, steps, window, maps="f32", media=True):
+    """The FP64 oracle, as it stands, on a window of the workload (host
+    cores).  With `media`, the same window is also run on the unrounded
+    inputs: how far the stored (float32 or bf16) medium moves the result, a
+    property of the input rather than of the kernels."""
     from oracle.core import OracleSim
-    # the index form's coefficients are the float maps gathered from its tables
-    orc = OracleSim(prob, round_to="f32" if maps == "idx" else maps, window=window)
+    orc = OracleSim(prob, round_to=_round_of(maps), window=window)
     orc.run(2)
     t0 = time.perf_counter()
     orc.run(steps)
     dt = time.perf_counter() - t0
     pts = int(np.prod(orc.wshape))
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": pts * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{'x'.join(str(w) for w in orc.wshape)} window of the workload around the array "
-                      f"(sources inside), {steps} steps, {dt:.1f} s"}
+    out = {"value": pts * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{'x'.join(str(w) for w in orc.wshape)} window of the workload around the array "
+                     f"(sources inside), {steps} steps, {dt:.1f} s"}
+    if media:
+        exact = OracleSim(prob, round_to=None, window=window)
+        exact.run(2 + steps)
+        p0, p1 = exact.field("p"), orc.field("p")
+        dev = {"rel_l2": float(np.linalg.norm(p1 - p0) / max(np.linalg.norm(p0), 1e-300)),
+               "max_over_peak": float(np.max(np.abs(p1 - p0)) / max(np.max(np.abs(p0)), 1e-300))}
+        if orc.trace is not None and orc.trace.size:
+            rows = slice(0, 2 + steps)
+            e = np.max(np.abs(orc.trace[rows] - exact.trace[rows]))
+            dev["trace_db"] = float(20 * math.log10(max(e, 1e-300) / max(np.max(np.abs(exact.trace[rows])), 1e-300)))
+        dev["how"] = (f"oracle on the {maps} maps the kernels stream vs the oracle on the unrounded inputs, "
+                      f"same window, {2 + steps} steps from rest")
+        out["media_deviation"] = dev
+    return out
+
+
+def exact_region(window, shape, margin):
+    """Slices (numpy order) of the part of a window at least `margin` cells
+    from every edge where the window cuts the grid (edges on the grid's own
+    boundary need no margin)."""
+    sl = []
+    for (w0, w1), n in zip(window, shape):
+        lo = w0 + (margin if w0 > 0 else 0)
+        hi = w1 - (margin if w1 < n else 0)
+        sl.append(slice(lo - w0, max(hi, lo) - w0))
+    return tuple(reversed(sl)), [(w0 + s.start, w0 + s.stop) for (w0, _), s in zip(window, sl)]
+
+
+def parity_after_run(sim, prob, maps, window, extra=4):
+    """Parity of the timed run: the state the kernels reached is cut to
+    `window`; the kernels then take `extra` more steps on the whole grid,
+    and the FP64 oracle takes them on the window from the same state.
+    Compared where the window is exact (8 cells per step from its cut
+    edges): rel L2 and max |error| / peak of p and v_q, and the trace error
+    [dB] of the sensor groups that lie entirely in that region."""
+    from oracle.core import OracleSim
+    from paper_2106_11476_gb300 import fw2
+    names = ["p"] + ["v" + "xyz"[q] for q in range(prob.ndim)]
+    if prob.nrelax:
+        names += [f"psi{o}{'xyz'[q]}" for o in (1, 2) for q in range(prob.ndim)]
+    sim.synchronize()
+    n0 = fw2.fw2_get_step(sim.ctx)
+    state = {nm: sim.field_window(nm, window) for nm in names}
+    sim.step(extra)
+    sim.synchronize()
+    orc = OracleSim(prob, round_to=_round_of(maps), window=window)
+    orc.set_state(state, step=n0)
+    orc.run(extra)
+    sl, region = exact_region(window, prob.shape, 8 * extra)
+    err2 = ref2 = 0.0
+    emax = peak = 0.0
+    for nm in names[:1 + prob.ndim]:
+        g = sim.field_window(nm, window)[sl].astype(np.float64)
+        o = orc.field(nm)[sl]
+        err2 += float(np.sum((g - o) ** 2))
+        ref2 += float(np.sum(o ** 2))
+        emax = max(emax, float(np.max(np.abs(g - o))) / max(float(np.max(np.abs(o))), 1e-300))
+    out = {"rel_l2": math.sqrt(err2 / max(ref2, 1e-300)), "max_over_peak": emax, "trace_db": None,
+           "steps_compared": extra, "window": [list(w) for w in window],
+           "region": [list(r) for r in region]}
+    sn = prob.sensors
+    if sn is not None and sim.trace is not None and n0 + extra <= sim.trace.shape[0]:
+        full = list(prob.shape) + [1] * (3 - prob.ndim)
+        i = sn.idx % full[0]
+        j = (sn.idx // full[0]) % full[1]
+        k = sn.idx // (full[0] * full[1])
+        rr = region + [(0, 1)] * (3 - prob.ndim)
+        inside = ((i >= rr[0][0]) & (i < rr[0][1]) & (j >= rr[1][0]) & (j < rr[1][1])
+                  & (k >= rr[2][0]) & (k < rr[2][1]))
+        groups = [gi for gi in range(sn.n_groups) if np.all(inside[sn.group == gi]) and np.any(sn.group == gi)]
+        if groups:
+            tg = sim.trace[n0:n0 + extra].cpu().numpy()[:, groups].astype(np.float64)
+            to = orc.trace[n0:n0 + extra][:, groups]
+            e = float(np.max(np.abs(tg - to)))
+            out["trace_db"] = 20 * math.log10(max(e, 1e-300) / max(float(np.max(np.abs(to))), 1e-300))
+            out["trace_groups"] = len(groups)
+    out["how"] = (f"state after the timed run cut to the window; {extra} further steps by the kernels on the "
+                  f"whole grid and by the FP64 oracle on the window; compared {8 * extra} cells from its cut edges")
+    return out
+
+
+def parity_window(prob):
+    """The window of the cpu_baseline sample and of the parity check: 512 x 512
+    cells around the array (2D) or the 128^3 box around the array's centre
+    from the grid's z = 0 face (3D)."""
+    n = prob.shape[0]
+    c0 = n // 2
+    if prob.ndim == 2:
+        return ((max(c0 - 256, 0), min(c0 + 256, n)), (0, min(512, prob.shape[1])))
+    return ((max(c0 - 64, 0), min(c0 + 64, n)), (max(c0 - 64, 0), min(c0 + 64, n)), (0, min(128, prob.shape[2])))
 
 
 # --------------------------------------------------------------------------
@@ -240,64 +367,63 @@ def job_rate(world: int, cells: int, steps: int, seconds: float) -> float:
     return world * cells * steps / seconds / 1e9
 
 
-def run_fw2(args, rank, world, dist):
-    import torch
+def workload_problem(args, name, n, total_steps, rank):
+    """(problem, maps, description) of a single-grid workload."""
     import synth
-    from paper_2106_11476_gb300 import _build, fw2
-
-    _build.build()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    total_steps = args.warmup + args.steps
-    if args.workload == "abdominal-idx":
-        n = args.n
+    if name == "abdominal-idx":
         prob = synth.indexed_abdominal_problem(nx=n, ny=n, n_steps=total_steps, seed=1 + rank, n_elements=128,
                                                focus_mm=40.0)
         maps = args.maps or "idx"
-        mbytes = {"idx": 0, "f32": 4, "bf16": 2}[maps]
-        kv, kp = "vel2d", "prs2d"
-        workload = (f"2D heterogeneous nonlinear abdominal wall in tissue-index form (class x 64 scatterer "
-                    f"levels), {n}x{n} cells at lambda/12 for 3 MHz, N=4, 128-element focused array, "
-                    f"{maps} maps")
-    elif args.workload == "skull":
-        n = args.n if args.n != 4096 else 768
+        desc = (f"2D heterogeneous nonlinear abdominal wall in tissue-index form (class x 64 scatterer "
+                f"levels), {n}x{n} cells at lambda/12 for 3 MHz, N=4, 128-element focused array, {maps} maps")
+    elif name == "skull":
         prob = synth.skull_problem(n=n, n_steps=total_steps, seed=2 + rank)
-        maps, mbytes, kv, kp = "bf16", 2, "vel3d", "prs3d"
-        workload = (f"3D transcranial-like medium, {n}^3 cells at lambda/10 for 1 MHz, N=3, brain background "
-                    f"with an ellipsoidal skull shell, 16x16 planar array, bf16 maps")
+        maps = "bf16"
+        desc = (f"3D transcranial-like medium, {n}^3 cells at lambda/10 for 1 MHz, N=3, brain background "
+                f"with an ellipsoidal skull shell, 16x16 planar array, bf16 maps")
+    elif name == "plain":
+        prob = synth.line_source_problem(n=n, n_steps=total_steps, seed=rank)
+        maps = args.maps or "f32"
+        desc = (f"2D plain method: homogeneous attenuating tissue (N=4, alpha0 0.5, y 1.1), {n}x{n} cells at "
+                f"lambda/12 for 3 MHz, linear, line source, 256 point sensors, {maps} maps")
     else:
-        n = args.n
         prob = synth.abdominal_problem(n=n, n_steps=total_steps, seed=1 + rank)
-        maps, mbytes, kv, kp = "f32", 4, "vel2d", "prs2d"
-        workload = abdominal_workload(n)
-    if args.nl:
-        prob.nl_mode = args.nl
-        workload += f", nonlinear mode {args.nl}"
-        if args.nl != "off" and prob.beta is None:
-            prob.beta = np.full(prob.grid_shape, 4.0, np.float32)
-            workload += " (beta = 4 everywhere)"
-    if args.taps == "time-space":
-        r = float(np.max(prob.c)) * prob.dt / prob.h
-        prob.taps = tuple(fw2.fw2_taps_time_space(r, prob.ndim))
-        workload += f", time-space optimised taps at r = {r:.3f}"
-    vel_b, prs_b = algorithmic_bytes(prob.shape, prob.nrelax, prob.pml_transition + prob.pml_bound,
-                                     prob.nl_mode != "off", map_bytes=mbytes, nl_vel=prob.nl_mode == "literal")
+        maps = args.maps or "f32"
+        desc = abdominal_workload(n)
+    return prob, maps, desc
+
+
+def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=True, want_cpu=True,
+            want_parity=True, parity_steps=4, name=None):
+    """One single-grid workload: warm-up, K timed steps (CUDA events on the
+    library's stream, max over ranks), per-kernel event timing for the
+    roofline, the parity of the reached state against the oracle, the end
+    to end run through the C ABI from pinned host buffers, and the oracle
+    baseline.  Returns the fields of a bench line (rank 0) or None."""
+    import torch
+    import synth
+    from paper_2106_11476_gb300 import fw2
+    total_steps = warmup + steps
+    prob = synth.with_steps(prob, total_steps + (parity_steps if want_parity else 0))
+    L = prob.pml_transition + prob.pml_bound
     if maps == "idx":
-        # one uint8 index per cell replaces every interior map; strips stay float
-        vel_b, prs_b = algorithmic_bytes_indexed(prob.shape, prob.nrelax, prob.pml_transition + prob.pml_bound,
-                                                 prob.nl_mode != "off")
+        vel_b, prs_b = algorithmic_bytes_indexed(prob.shape, prob.nrelax, L, prob.nl_mode != "off")
+    else:
+        vel_b, prs_b = algorithmic_bytes(prob.shape, prob.nrelax, L, prob.nl_mode != "off",
+                                         map_bytes={"f32": 4, "bf16": 2}[maps], nl_vel=prob.nl_mode == "literal")
+    vel_o, prs_o = split_overhead_bytes(prob.shape, indexed=maps == "idx")
     stream = torch.cuda.current_stream()
     sim = fw2.Simulation(prob, stream=stream, map_precision=maps, kernel_path=args.kernel_path)
-    sim.step(args.warmup)
+    sim.step(warmup)
     sim.synchronize()
     fw2.fw2_profile(sim.ctx, True)
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = sim.launches
     with ClockSampler(device_id_for_smi()) as clk:
-        for i in range(args.steps):
+        for i in range(steps):
             events[i].record(stream)
             sim.step(1)
         events[-1].record(stream)
@@ -305,103 +431,185 @@ def run_fw2(args, rank, world, dist):
     launches = sim.launches - launches0
     if dist:
         dist.barrier()
-    per_step = np.array([events[i].elapsed_time(events[i + 1]) for i in range(args.steps)])
+    per_step = np.array([events[i].elapsed_time(events[i + 1]) for i in range(steps)])
     elapsed_ms = float(events[0].elapsed_time(events[-1]))
     vel_ms, nv, prs_ms, np_ = fw2.fw2_profile_read(sim.ctx)
     fw2.fw2_profile(sim.ctx, False)
+    nd = prob.ndim
     if fw2.fw2_kernel_path(sim.ctx) == "pipe":
-        kv, kp = ("pipe2d_vel", "pipe2d_prs") if len(prob.shape) == 2 else ("pipe3d_vel", "pipe3d_prs")
+        kv, kp = (f"pipe{nd}d_vel", f"pipe{nd}d_prs")
+    else:
+        kv, kp = (f"vel{nd}d", f"prs{nd}d")
     elapsed_max = max_over_ranks(elapsed_ms, dist)
-    pts = prob.n_pts
-    value = job_rate(world, pts, args.steps, elapsed_max * 1e-3)
-    # roofline of the dominant kernel
+    value = job_rate(world, prob.n_pts, steps, elapsed_max * 1e-3)
     peaks, peak_kind = measured_peaks()
-    dom = kv if vel_ms >= prs_ms else kp
-    dom_ms = (vel_ms / nv) if dom == kv else (prs_ms / np_)
-    dom_bytes = vel_b if dom == kv else prs_b
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
+    dom = kv if vel_ms / nv >= prs_ms / np_ else kp
+    dom_ms = (vel_ms / nv) if dom == kv else (prs_ms / np_)
+    dom_bytes, dom_over = (vel_b, vel_o) if dom == kv else (prs_b, prs_o)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     variant = ("" if args.taps == "taylor" else f":{args.taps}") + (f":{args.nl}" if args.nl else "")
-    traffic = committed_traffic(f"{args.workload}:{maps}:{n}:{dom}{variant}")
+    traffic = committed_traffic(f"{name or args.workload}:{maps}:{prob.shape[0]}:{dom}{variant}")
+    step_b = vel_b + prs_b
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
-            "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": round(dom_ms, 5),
+            "algorithmic_bytes_per_launch": int(dom_bytes), "split_overhead_bytes_per_launch": int(dom_over),
+            "bytes_basis": "compulsory bytes of the fused step (each state array read and written once, each "
+                           "map read once, C-PML strips inside the boundary), charged to the half step that "
+                           "updates each array; the second read of the stencil operand that the two-launch "
+                           "split makes is split_overhead_bytes_per_launch, not counted",
+            "algorithmic_bytes_per_cell_step": round(step_b / prob.n_pts, 2),
+            "avg_launch_ms": round(dom_ms, 5),
             "peak_source": f"{peak_kind} copy bandwidth hbm_gbs",
-            "step_roofline_frac": round((vel_b + prs_b) / ((vel_ms / nv + prs_ms / np_) * 1e-3) / 1e9 / peak, 4),
+            "step_frac": round(step_b / ((vel_ms / nv + prs_ms / np_) * 1e-3) / 1e9 / peak, 4),
+            "step_frac_of_ms_per_step": round(step_b * steps / (elapsed_max * 1e-3) / 1e9 / peak, 4),
             "vel_ms": round(vel_ms / nv, 5), "prs_ms": round(prs_ms / np_, 5)}
+    win = parity_window(prob)
+    parity = None
+    if want_parity and rank == 0:
+        parity = parity_after_run(sim, prob, maps, win, extra=parity_steps)
     sim.close()
     del sim
     torch.cuda.empty_cache()
-    # end to end through the C ABI with host buffers: medium, relaxation and
-    # sources copied in from pinned host memory, K steps, traces copied out
     e2e = None
-    if not args.no_e2e:
-        pinned = {}
-        def pin(a):
-            if a is None:
-                return None
-            t_ = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-            pinned[id(t_)] = t_
-            return t_
-        import dataclasses
-        if maps == "idx":
-            tabs = {k: pin(v) for k, v in prob.tables.items()}
-            hp = dataclasses.replace(prob, tissue=pin(prob.tissue), tables=tabs)
-            used = [hp.tissue] + [tabs[k] for k in ("c", "rho", "kappa1", "kappa2", "d1", "alpha1", "d2", "alpha2")]
-            if prob.nl_mode != "off":
-                used.append(tabs["beta"])
-        else:
-            hp = dataclasses.replace(prob, c=pin(prob.c), rho=pin(prob.rho), beta=pin(prob.beta),
-                                     kappa1=pin(prob.kappa1), kappa2=pin(prob.kappa2), d1=pin(prob.d1),
-                                     alpha1=pin(prob.alpha1), d2=pin(prob.d2), alpha2=pin(prob.alpha2))
-            used = [x for x in (hp.c, hp.rho, hp.beta, hp.kappa1, hp.kappa2, hp.d1, hp.alpha1, hp.d2, hp.alpha2)
-                    if x is not None]
-        h2d = sum(x.numel() * x.element_size() for x in used)
-        h2d += sum(s.idx.nbytes + s.group.nbytes + s.signal.nbytes for s in prob.sources)
-        h2d += prob.sensors.idx.nbytes + prob.sensors.group.nbytes
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        t0 = time.perf_counter()
-        s2 = fw2.Simulation(hp, stream=stream, map_precision=maps,  # tables stay host numpy for idx
-                            kernel_path=args.kernel_path)
-        s2.step(args.steps)
-        trace_host = s2.trace[: args.steps].cpu()
-        t1 = time.perf_counter()
-        d2h = trace_host.numel() * 4
-        s2.close()
-        e2e = {"value": job_rate(world, pts, args.steps, max_over_ranks(t1 - t0, dist)), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps),
-               "scope": "whole job through the C ABI from pinned host buffers: set_medium, set_relaxation, "
-                        "add_source, record, coefficient build, K steps, trace read-back"}
+    if want_e2e:
+        e2e = end_to_end(args, prob, maps, steps, world, dist, stream)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        c0 = n // 2
-        if prob.ndim == 2:
-            win = ((c0 - 256, c0 + 256), (0, 512))
-        else:
-            win = ((c0 - 64, c0 + 64), (c0 - 64, c0 + 64), (36, 164))
+    if want_cpu and rank == 0 and world == 1:
         cpu = oracle_baseline(prob, args.cpu_steps, win, maps)
+    if rank != 0:
+        return None
+    return {"value": round(value, 4), "ms_per_step": round(elapsed_max / steps, 5),
+            "config": {"workload": desc, "grid": list(prob.shape), "n_relax": prob.nrelax,
+                       "nl_mode": prob.nl_mode, "map_precision": maps, "kernel_path": args.kernel_path,
+                       "taps": args.taps, "pml_cells": L},
+            "latency": {"p50_ms_per_step": round(float(np.percentile(per_step, 50)), 5),
+                        "p99_ms_per_step": round(float(np.percentile(per_step, 99)), 5)},
+            "roofline": roof, "parity": parity, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+
+
+def end_to_end(args, prob, maps, steps, world, dist, stream):
+    """The whole job through the C ABI with host buffers: medium, relaxation
+    and sources copied in from pinned host memory, K steps, traces copied
+    out, all inside the timed region."""
+    import dataclasses
+    import torch
+    from paper_2106_11476_gb300 import fw2
+    pinned = {}
+
+    def pin(a):
+        if a is None:
+            return None
+        t_ = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        pinned[id(t_)] = t_
+        return t_
+    if maps == "idx":
+        tabs = {k: pin(v) for k, v in prob.tables.items()}
+        hp = dataclasses.replace(prob, tissue=pin(prob.tissue), tables=tabs)
+        used = [hp.tissue] + [tabs[k] for k in ("c", "rho", "kappa1", "kappa2", "d1", "alpha1", "d2", "alpha2")]
+        if prob.nl_mode != "off":
+            used.append(tabs["beta"])
+    else:
+        hp = dataclasses.replace(prob, c=pin(prob.c), rho=pin(prob.rho), beta=pin(prob.beta),
+                                 kappa1=pin(prob.kappa1), kappa2=pin(prob.kappa2), d1=pin(prob.d1),
+                                 alpha1=pin(prob.alpha1), d2=pin(prob.d2), alpha2=pin(prob.alpha2))
+        used = [x for x in (hp.c, hp.rho, hp.beta, hp.kappa1, hp.kappa2, hp.d1, hp.alpha1, hp.d2, hp.alpha2)
+                if x is not None]
+    h2d = sum(x.numel() * x.element_size() for x in used)
+    h2d += sum(s.idx.nbytes + s.group.nbytes + s.signal.nbytes for s in prob.sources)
+    if prob.sensors is not None:
+        h2d += prob.sensors.idx.nbytes + prob.sensors.group.nbytes
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    s2 = fw2.Simulation(hp, stream=stream, map_precision=maps, kernel_path=args.kernel_path)
+    t_setup = time.perf_counter()
+    s2.step(steps)
+    trace_host = s2.trace[:steps].cpu() if s2.trace is not None else None
+    t1 = time.perf_counter()
+    d2h = trace_host.numel() * 4 if trace_host is not None else 0
+    s2.close()
+    return {"value": job_rate(world, prob.n_pts, steps, max_over_ranks(t1 - t0, dist)), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d // steps), "d2h_bytes_per_step": int(d2h // steps),
+            "setup_s": round(t_setup - t0, 3), "steps_and_readback_s": round(t1 - t_setup, 3),
+            "scope": "whole job through the C ABI from pinned host buffers: create, set_medium, set_relaxation, "
+                     "add_source, record, coefficient build, K steps, trace read-back"}
+
+
+def run_fw2(args, rank, world, dist):
+    import torch
+    from paper_2106_11476_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = args.n if not (args.workload == "skull" and args.n == 4096) else 768
+    if args.workload == "plain" and args.n == 4096:
+        n = 512
+    prob, maps, desc = workload_problem(args, args.workload, n, args.warmup + args.steps, rank)
+    if args.nl:
+        prob.nl_mode = args.nl
+        desc += f", nonlinear mode {args.nl}"
+        if args.nl != "off" and prob.beta is None:
+            prob.beta = np.full(prob.grid_shape, 4.0, np.float32)
+            desc += " (beta = 4 everywhere)"
+    if args.taps == "time-space":
+        from paper_2106_11476_gb300 import fw2
+        r = float(np.max(prob.c)) * prob.dt / prob.h
+        prob.taps = tuple(fw2.fw2_taps_time_space(r, prob.ndim))
+        desc += f", time-space optimised taps at r = {r:.3f}"
+    res = measure(args, prob, maps, desc, args.steps, args.warmup, rank, world, dist,
+                  want_e2e=not args.no_e2e, want_cpu=not args.no_cpu_baseline, want_parity=not args.no_parity)
+    del prob
+    extras = None
+    if args.workload == "abdominal" and args.configs != "none" and world == 1:
+        extras = other_configs(args, rank)
     if rank != 0:
         return
     data = ("synthetic (seeded skull-like shell in a brain-like medium; stands in for the micro-CT rat skull)"
-            if prob.ndim == 3 else
+            if args.workload == "skull" else
+            "synthetic (seeded homogeneous attenuating medium, line source)" if args.workload == "plain" else
             "synthetic (seeded abdominal-wall-like medium; stands in for the Visible Human phantom)")
-    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(elapsed_max / args.steps, 5),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": data,
-           "config": {"workload": workload,
-                      "grid": list(prob.shape), "n_relax": prob.nrelax, "nl_mode": prob.nl_mode, "map_precision": maps,
-                      "kernel_path": args.kernel_path, "taps": args.taps,
-                      "pml_cells": prob.pml_transition + prob.pml_bound,
-                      "l2": "state and maps (>2.5 GB) exceed L2; no flush needed",
-                      "parallelism": f"replicas x{world} (one transmit event per GPU)"},
-           "latency": {"p50_ms_per_step": round(float(np.percentile(per_step, 50)), 5),
-                       "p99_ms_per_step": round(float(np.percentile(per_step, 99)), 5)},
-           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-           "clocks": clk.summary()}
+    res["config"]["l2"] = ("working set within L2 (the HBM roofline is L2-distorted)"
+                           if args.workload == "plain" and n <= 1024 else
+                           "state and maps exceed L2 (129 MB); no flush needed")
+    res["config"]["parallelism"] = f"replicas x{world} (one transmit event per GPU)"
+    out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": data}
+    for k in ("config", "latency", "roofline", "parity", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+        out[k] = res[k]
+    if extras is not None:
+        out["other_configs"] = extras
     print(json.dumps(out), flush=True)
+
+
+def other_configs(args, rank):
+    """The other configurations of the workload family, measured in the same
+    run (rank 0 of a single-GPU run): the plain 512^2 method for its full
+    1000 steps, the 768^3 transcranial medium for K steps, and the batch of
+    80 transmit events / uneven instances for K steps."""
+    import torch
+    out = {}
+    sel = args.configs.split(",") if args.configs != "all" else ["plain", "skull", "batch"]
+    if "plain" in sel:
+        prob, maps, desc = workload_problem(args, "plain", 512, 1000, rank)
+        r = measure(args, prob, maps, desc, 1000 - 20, 20, rank, 1, None, want_e2e=True, want_cpu=False,
+                    name="plain")
+        r["config"]["l2"] = "working set (about 70 MB) within L2: the HBM roofline is L2-distorted"
+        out["plain_512"] = r
+        torch.cuda.empty_cache()
+    if "skull" in sel:
+        prob, maps, desc = workload_problem(args, "skull", 768, args.steps + args.warmup, rank)
+        r = measure(args, prob, maps, desc, args.steps, args.warmup, rank, 1, None, want_e2e=False,
+                    want_cpu=True, name="skull")
+        out["skull_768"] = r
+        del prob
+        torch.cuda.empty_cache()
+    if "batch" in sel:
+        out["batch"] = batch_measurement(args, rank, 1, None)
+        torch.cuda.empty_cache()
+    return out
 
 
 def batch_problems(args, rank):
@@ -422,13 +630,11 @@ def batch_problems(args, rank):
     return probs
 
 
-def run_batch(args, rank, world, dist):
+def batch_measurement(args, rank, world, dist):
     """Batched tissue-index form vs the plain form (dense float maps, one
-    context at a time) on the same 80 problems."""
+    context at a time) on the same 80 problems, both for K steps."""
     import torch
-    from paper_2106_11476_gb300 import _build, fw2
-    _build.build()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2106_11476_gb300 import fw2
     probs = batch_problems(args, rank)
     cells = sum(p.n_pts for p in probs)
     sims = [fw2.Simulation(p, map_precision="idx") for p in probs]
@@ -450,46 +656,59 @@ def run_batch(args, rank, world, dist):
         s.close()
     del sims
     torch.cuda.empty_cache()
-    # plain form: the same problems, dense float maps, one after the other
-    plain_steps = min(args.steps, 50)
-    done, t_plain, finish = 0, 0.0, []
+    # plain form: the same problems, dense float maps, one after the other,
+    # each for the same K steps after a short warm-up
+    t_plain, finish, done = 0.0, [], 0
     for p in probs:
         s = fw2.Simulation(p, map_precision="f32")
         s.step(3)
         s.synchronize()
         t0 = time.perf_counter()
-        s.step(plain_steps)
+        s.step(args.steps)
         s.synchronize()
-        dt = time.perf_counter() - t0
+        t_plain += time.perf_counter() - t0
         s.close()
-        t_plain += dt * args.steps / plain_steps       # time for the full K steps at this rate
         finish.append(t_plain)
         done += p.n_pts * args.steps
     t_batch = max_over_ranks(t_batch, dist)
     value = job_rate(world, cells, args.steps, t_batch)
     if rank != 0:
-        return
+        return None
     peaks, _ = measured_peaks()
     vb = sum(sum(algorithmic_bytes_indexed(p.shape, p.nrelax, p.pml_transition + p.pml_bound, True)) for p in probs)
-    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(t_batch / args.steps * 1e3, 4),
+    return {"value": round(value, 4), "unit": UNIT, "steps": args.steps,
+            "ms_per_step": round(t_batch / args.steps * 1e3, 4),
+            "config": {"workload": "batched: 64 focused transmits over one 2048x1024 tissue-index medium + 16 "
+                                   "instances 512^2..1536^2, one persistent launch per half step, graph-captured "
+                                   "step loop, autotuned launch", "cells_per_step": cells,
+                       "tuned_grid": grid, "tuned_order": order},
+            "roofline": {"bound": "hbm", "kernel": "step (all kernels)", "unit": "GB/s",
+                         "achieved": round(vb * args.steps / t_batch / 1e9, 1), "peak": float(peaks["hbm_gbs"]),
+                         "frac": round(vb * args.steps / t_batch / 1e9 / float(peaks["hbm_gbs"]), 4),
+                         "traffic": None},
+            "plain_form": {"value": round(done / t_plain / 1e9, 4), "unit": UNIT,
+                           "how": "same problems, dense float maps, one context at a time, each measured "
+                                  f"over the same {args.steps} steps"},
+            "time_to_result_s": {"batched_p50": round(t_batch, 3), "batched_p99": round(t_batch, 3),
+                                 "plain_p50": round(float(np.percentile(finish, 50)), 3),
+                                 "plain_p99": round(float(np.percentile(finish, 99)), 3)},
+            "gpu_launches": int(l1 - l0), "clocks": clk.summary()}
+
+
+def run_batch(args, rank, world, dist):
+    import torch
+    from paper_2106_11476_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    r = batch_measurement(args, rank, world, dist)
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": "synthetic (seeded tissue-index abdominal media)",
-           "config": {"workload": "batched: 64 focused transmits over one 2048x1024 tissue-index medium + 16 "
-                                  "instances 512^2..1536^2, one persistent launch per half step, graph-captured "
-                                  "step loop, autotuned launch", "cells_per_step": cells,
-                      "tuned_grid": grid, "tuned_order": order},
-           "roofline": {"bound": "hbm", "kernel": "step (all kernels)", "unit": "GB/s",
-                        "achieved": round(vb * args.steps / t_batch / 1e9, 1), "peak": float(peaks["hbm_gbs"]),
-                        "frac": round(vb * args.steps / t_batch / 1e9 / float(peaks["hbm_gbs"]), 4),
-                        "traffic": None},
-           "plain_form": {"value": round(done / t_plain / 1e9, 4), "unit": UNIT,
-                          "how": "same problems, dense float maps, one context at a time (rate over "
-                                 f"{plain_steps} steps each, scaled to {args.steps})"},
-           "time_to_result_s": {"batched_p50": round(t_batch, 3), "batched_p99": round(t_batch, 3),
-                                "plain_p50": round(float(np.percentile(finish, 50)), 3),
-                                "plain_p99": round(float(np.percentile(finish, 99)), 3)},
-           "gpu_launches": int(l1 - l0), "clocks": clk.summary()}
+           "data": "synthetic (seeded tissue-index abdominal media)"}
+    for k in ("config", "roofline", "plain_form", "time_to_result_s", "gpu_launches", "clocks"):
+        out[k] = r[k]
     print(json.dumps(out), flush=True)
 
 
@@ -621,9 +840,9 @@ def main():
     ap.add_argument("--serve-scale", type=float, default=0.25, help="serving: size and step scale")
     ap.add_argument("--slice", type=int, default=100, help="serving: steps per slice")
     ap.add_argument("--workload", default="abdominal",
-                    choices=["abdominal", "abdominal-idx", "skull", "batch", "serve"],
+                    choices=["abdominal", "abdominal-idx", "skull", "plain", "batch", "serve"],
                     help="abdominal: 2D 4096^2 nonlinear (default); abdominal-idx: the same in tissue-index "
-                         "form; skull: 3D 768^3 with bf16 maps")
+                         "form; skull: 3D 768^3 with bf16 maps; plain: 2D 512^2 homogeneous line source")
     ap.add_argument("--maps", default=None, choices=["f32", "bf16", "idx"],
                     help="override the map storage of the workload")
     ap.add_argument("--kernel-path", default="auto", choices=["auto", "tile", "pipe"],
@@ -636,6 +855,10 @@ def main():
                     help="oracle steps of the cpu_baseline sample (about 10 s on 16 host cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--configs", default="all",
+                    help="other configurations measured after the default workload: all, none, or a comma list "
+                         "of plain, skull, batch")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

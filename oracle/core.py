@@ -195,16 +195,28 @@ class OracleSim:
             self.S.psi1[q] = _dp(self.psi1[q])
             self.S.psi2[q] = _dp(self.psi2[q])
 
-    def set_state(self, st: Dict[str, np.ndarray]):
-        """Load a state (as from synth.random_state) into the FP64 fields."""
+    def set_state(self, st: Dict[str, np.ndarray], step: Optional[int] = None):
+        """Load a state (as from synth.random_state) into the FP64 fields.
+        Arrays shaped like the whole grid are cut to the window; arrays
+        already shaped like the window are taken as they are.  `step` sets
+        the index of the next time step (source and trace row)."""
         names = "xyz"
         N = self.prob.nrelax
-        self.p[:] = self._crop(st["p"]).astype(np.float64).ravel()
+        wg = tuple(reversed(self.wshape))
+
+        def cut(a, lead=()):
+            a = np.asarray(a)
+            if a.shape == lead + wg and self.wshape != tuple(self.prob.shape):
+                return a
+            return self._crop(a.reshape(lead + self.prob.grid_shape))
+        self.p[:] = cut(st["p"]).astype(np.float64).ravel()
         for q in range(len(self.v)):
-            self.v[q][:] = self._crop(st["v" + names[q]]).astype(np.float64).ravel()
+            self.v[q][:] = cut(st["v" + names[q]]).astype(np.float64).ravel()
             if N and ("psi1" + names[q]) in st:
-                self.psi1[q][:] = self._crop(np.asarray(st["psi1" + names[q]]).reshape((N,) + self.prob.grid_shape)).reshape(N, -1)
-                self.psi2[q][:] = self._crop(np.asarray(st["psi2" + names[q]]).reshape((N,) + self.prob.grid_shape)).reshape(N, -1)
+                self.psi1[q][:] = cut(st["psi1" + names[q]], (N,)).reshape(N, -1)
+                self.psi2[q][:] = cut(st["psi2" + names[q]], (N,)).reshape(N, -1)
+        if step is not None:
+            self.step_index = int(step)
 
     def run(self, n_steps: int):
         lib().orc_run(C.byref(self.G), C.byref(self.C), C.byref(self.S),

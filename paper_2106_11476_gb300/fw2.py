@@ -492,6 +492,20 @@ class Simulation:
             out = np.empty(g, np.float32)
         return fw2_get_field(self.ctx, name, out)
 
+    def field_window(self, name: str, window) -> np.ndarray:
+        """A state array cut to `window` ((x0, x1), (y0, y1)[, (z0, z1)]):
+        copied out into device memory, cut there, and only the window copied
+        to the host (numpy order, memory variables [N, ...])."""
+        torch = self.torch
+        g = tuple(reversed(self.prob.shape))
+        shape = ((self.prob.nrelax,) + g) if name.startswith("psi") else g
+        buf = torch.empty(shape, dtype=torch.float32, device="cuda")
+        fw2_get_field(self.ctx, name, buf)
+        sl = tuple(slice(int(w[0]), int(w[1])) for w in reversed(list(window)))
+        out = buf[(Ellipsis,) + sl].cpu().numpy()
+        del buf
+        return out
+
     def set_state(self, st: dict):
         for k, v in st.items():
             fw2_set_field(self.ctx, k, v)

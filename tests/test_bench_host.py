@@ -10,26 +10,39 @@ import bench
 
 
 def test_algorithmic_bytes_2d_by_hand():
-    """2D, N = 4, nonlinear, float maps, no C-PML: the velocity half step reads
-    p, rho, 1/kappa1 and a, b of 4 mechanisms and reads and writes v_x, v_y and
-    8 memory variables: 4 + 4 + 4 + 32 + 16 + 64 = 124 B per cell; the
-    pressure half step 8 (v) + 4 (K) + 4 (chi) + 4 + 32 + 8 (p) + 64 = 124."""
+    """2D, N = 4, nonlinear, float maps, no C-PML: the compulsory bytes of a
+    step (each state array read and written once, each map read once) split
+    by the array each half step updates.  Velocity: v_x, v_y and 8 memory
+    variables read and written, rho, 1/kappa1 and a, b of 4 mechanisms:
+    16 + 64 + 4 + 4 + 32 = 120 B per cell; pressure: p and 8 memory
+    variables read and written, K, chi, 1/kappa2, a, b: 8 + 64 + 4 + 4 + 4
+    + 32 = 116 B (236 B per cell-step)."""
     n = 1000 * 700
     vel, prs = bench.algorithmic_bytes((1000, 700), 4, 0, True, map_bytes=4)
-    assert vel == 124 * n and prs == 124 * n
+    assert vel == 120 * n and prs == 116 * n
     vel, prs = bench.algorithmic_bytes((1000, 700), 4, 0, False, map_bytes=4)
-    assert prs == 120 * n                                  # no chi
+    assert prs == 112 * n                                  # no chi
     vel, _ = bench.algorithmic_bytes((1000, 700), 4, 0, True, map_bytes=4, nl_vel=True)
-    assert vel == 128 * n                                  # K in the velocity half step
+    assert vel == 124 * n                                  # K in the velocity half step
+
+
+def test_split_overhead_is_the_second_operand_read():
+    """The two-launch split reads p again in the velocity half step and v_q
+    again in the pressure half step: 4 and 4 D bytes per cell (and the
+    tissue index again in the index form)."""
+    n = 64 * 48
+    assert bench.split_overhead_bytes((64, 48)) == (4 * n, 8 * n)
+    assert bench.split_overhead_bytes((64, 48), indexed=True) == (4 * n, 9 * n)
+    assert bench.split_overhead_bytes((8, 8, 8)) == (4 * 512, 12 * 512)
 
 
 def test_algorithmic_bytes_3d_bf16_by_hand():
-    """3D, N = 3, linear, bf16 maps, no C-PML: velocity 4 (p) + 2 + 2 + 12
-    (a, b) + 24 (v) + 72 (psi) = 116 B; pressure 12 (v) + 2 (K) + 2 + 12 + 8
-    (p) + 72 = 108 B per cell."""
+    """3D, N = 3, linear, bf16 maps, no C-PML: velocity 24 (v) + 72 (psi) + 2
+    (rho) + 2 (1/kappa1) + 12 (a, b) = 112 B; pressure 8 (p) + 72 + 2 (K) + 2
+    + 12 = 96 B per cell."""
     n = 64 * 48 * 40
     vel, prs = bench.algorithmic_bytes((64, 48, 40), 3, 0, False, map_bytes=2)
-    assert vel == 116 * n and prs == 108 * n
+    assert vel == 112 * n and prs == 96 * n
 
 
 def test_strip_bytes_count_each_axis_inside_its_strip():
@@ -46,9 +59,21 @@ def test_strip_bytes_count_each_axis_inside_its_strip():
 
 
 def test_index_form_bytes():
+    """8 bytes per state array and one index byte per cell-step: 153 B."""
     n = 512 * 256
     vel, prs = bench.algorithmic_bytes_indexed((512, 256), 4, 0, True)
-    assert vel == n * (4 + 1 + 16 + 64) and prs == n * (8 + 1 + 8 + 64)
+    assert vel == n * (1 + 16 + 64) and prs == n * (8 + 64)
+    assert vel + prs == n * (8 * 19 + 1)
+
+
+def test_exact_region_keeps_margins_only_at_cut_edges():
+    """The parity region stays `margin` cells away from the window's edges
+    inside the grid, but reaches the grid's own boundary."""
+    sl, reg = bench.exact_region(((100, 612), (0, 512)), (4096, 4096), 32)
+    assert reg == [(132, 580), (0, 480)]
+    assert sl == (slice(0, 480), slice(32, 480))
+    sl, reg = bench.exact_region(((0, 512), (0, 512)), (512, 512), 32)
+    assert reg == [(0, 512), (0, 512)]
 
 
 def test_committed_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
