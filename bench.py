@@ -338,18 +338,34 @@ def parity_after_run(sim, prob, maps, window, extra=4):
 
 def parity_window(prob):
     """The window of the cpu_baseline sample and of the parity check: 512 x 512
-    cells around the array (2D) or the 128^3 box around the array's centre
-    from the grid's z = 0 face (3D)."""
-    n = prob.shape[0]
-    c0 = n // 2
+    cells from the grid's y = 0 edge (2D), or the 128^3 box from its z = 0
+    face (3D), centred in x (and y) on the source cell that fires first, so
+    that the window holds a wavefield however few steps the run takes."""
+    n = prob.shape
+    x_c, y_c = n[0] // 2, n[1] // 2 if prob.ndim == 3 else 0
+    first = None
+    for s in prob.sources:
+        sig = np.abs(np.asarray(s.signal))
+        if sig.size == 0 or sig.max() == 0:
+            continue
+        on = sig >= 1e-3 * sig.max()
+        t_on = np.where(on.any(axis=0), on.argmax(axis=0), sig.shape[0])   # first significant row per column
+        col = int(np.argmin(t_on))
+        cell = int(np.asarray(s.idx)[np.asarray(s.group) == col][0])
+        if first is None or t_on[col] < first[0]:
+            first = (int(t_on[col]), cell)
+    if first is not None:
+        x_c = first[1] % n[0]
+        if prob.ndim == 3:
+            y_c = (first[1] // n[0]) % n[1]
+
+    def span(c, half, size):
+        lo = min(max(c - half, 0), max(size - 2 * half, 0))
+        return (lo, min(lo + 2 * half, size))
     if prob.ndim == 2:
-        return ((max(c0 - 256, 0), min(c0 + 256, n)), (0, min(512, prob.shape[1])))
-    return ((max(c0 - 64, 0), min(c0 + 64, n)), (max(c0 - 64, 0), min(c0 + 64, n)), (0, min(128, prob.shape[2])))
+        return (span(x_c, 256, n[0]), (0, min(512, n[1])))
+    return (span(x_c, 64, n[0]), span(y_c, 64, n[1]), (0, min(128, n[2])))
 
-
-# --------------------------------------------------------------------------
-# arms
-# --------------------------------------------------------------------------
 
 def max_over_ranks(x: float, dist=None, device="cuda") -> float:
     """The largest value of x over all ranks (x itself without a process group)."""

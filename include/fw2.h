@@ -79,10 +79,17 @@ enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1, FW2_MAP_IDX_U8 = 2 };
  * far above the C-PML damping, reading A's first mechanism absorbs only in
  * the outermost cells and the boundary reflects at about -28 dB in that
  * tissue (3 + 1 wavelengths); C reflects at -53 dB there and stays stable.
- * In a non-attenuating medium both reach about -60 dB.  The value 1 (an
- * earlier reading that ramped the first mechanism over the outer L_B cells
- * only, reflecting at about -9 dB) is rejected with FW2_EINVAL. */
-enum { FW2_PML_A = 0, FW2_PML_C = 2 };
+ * In a non-attenuating medium both reach about -60 dB.
+ * NO_TRANSITION: reading C for the first mechanism, but the nu >= 2
+ * parameters keep their interior values inside the boundary: the
+ * multi-mechanism C-PML without a transition layer that Sec. 3.3 reports
+ * unstable (the field grows by about x1.5 every 5000 steps in Table 2
+ * tissue).  It is offered to reproduce that result and to exercise the
+ * blow-up detection of fw2_set_watch; do not use it for simulations.
+ * The value 1 (an earlier reading that ramped the first mechanism over the
+ * outer L_B cells only, reflecting at about -9 dB) is rejected with
+ * FW2_EINVAL. */
+enum { FW2_PML_A = 0, FW2_PML_C = 2, FW2_PML_NO_TRANSITION = 3 };
 /* time alignment of the memory term in Eq. (relaxation_psi): CENTRED uses
  * the mean of the memory variable before and after its update (D^{n-1/2}
  * estimated by (D^n + D^{n-1}) / 2); ENDPOINT uses the updated value. */
@@ -90,8 +97,9 @@ enum { FW2_MEM_CENTRED = 0, FW2_MEM_ENDPOINT = 1 };
 /* kernel path of the half steps (bitwise the same results on every path):
  * TILE runs one block per tile; PIPE runs the persistent kernels that stage
  * every tile through shared memory with TMA copies, where they apply (2D
- * float or tissue-index maps; 3D bf16 maps with N <= 3 and no g_{1,1} cross
- * taps; no periodic axis), and TILE elsewhere; AUTO (default) is PIPE */
+ * float or tissue-index maps; 3D bf16 maps with N <= 3, g_{1,1} cross taps
+ * and the literal system included; no periodic axis), and TILE elsewhere;
+ * AUTO (default) is PIPE */
 enum { FW2_PATH_AUTO = 0, FW2_PATH_TILE = 1, FW2_PATH_PIPE = 2 };
 enum { FW2_SRC_P = 0, FW2_SRC_VX = 1, FW2_SRC_VY = 2, FW2_SRC_VZ = 3 };
 enum {
@@ -113,7 +121,7 @@ typedef struct {
                             1225/1024, -245/3072, 49/5120, -5/7168, g11 = 0 */
   int32_t pml_transition;/* L_T, cells per side (Sec. 3.3) */
   int32_t pml_bound;     /* L_B, cells per side */
-  int32_t pml_reading;   /* FW2_PML_C (default) or FW2_PML_A */
+  int32_t pml_reading;   /* FW2_PML_C (default), FW2_PML_A or FW2_PML_NO_TRANSITION */
   int32_t map_precision; /* FW2_MAP_F32, FW2_MAP_BF16 or FW2_MAP_IDX_U8 (2D) storage of the maps */
   double pml_rc;         /* reflection target R_c of Table 1 (default 1e-3) */
   double pml_npow;       /* polynomial order of the d ramp (default 2) */
@@ -202,6 +210,16 @@ fw2_status fw2_step(fw2_ctx *ctx, int64_t n_steps);
 /* Release every resource of the context (safe on NULL). */
 fw2_status fw2_destroy(fw2_ctx *ctx);
 
+/* In-loop blow-up detection (a numerical failure such as the C-PML
+ * instability with N >= 2 and no transition layer, Sec. 3.3).  With
+ * every > 0, fw2_step scans p after each step whose count is a multiple of
+ * `every` and stops with FW2_EUNSTABLE when a value is not finite or
+ * |p| > bound (fw2_last_error names the step and the value); the steps up to
+ * the failing scan are taken and counted (fw2_get_step).  Each scan
+ * synchronises the context stream once.  every = 0 (the default) switches
+ * it off.  EINVAL for every < 0, or bound <= 0 with every > 0. */
+fw2_status fw2_set_watch(fw2_ctx *ctx, int64_t every, float bound);
+
 /* ---- batches ---------------------------------------------------------- */
 
 /* Many 2D contexts advanced together: the transmit events of a full
@@ -229,6 +247,14 @@ fw2_status fw2_batch_synchronize(fw2_batch *b);
  * at capture). */
 fw2_status fw2_batch_info(fw2_batch *b, int32_t *grid, int32_t *order, int64_t *launches);
 const char *fw2_batch_last_error(const fw2_batch *b);
+/* Blow-up detection for the batch (as fw2_set_watch): with every > 0, after
+ * each batch step whose count (steps since the batch's first) is a multiple
+ * of `every`, p of every context is scanned and fw2_batch_step stops with
+ * FW2_EUNSTABLE when one holds a non-finite value or |p| > bound
+ * (fw2_batch_last_error names the context); the steps up to that scan are
+ * taken and counted on every context.  Synchronises the batch stream once
+ * per scan.  EINVAL for every < 0, or bound <= 0 with every > 0. */
+fw2_status fw2_batch_set_watch(fw2_batch *b, int64_t every, float bound);
 fw2_status fw2_batch_destroy(fw2_batch *b);
 
 /* ---- helpers ---------------------------------------------------------- */

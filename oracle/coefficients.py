@@ -144,6 +144,9 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
       nu >= 2      : cosine     g = (1 - cos(pi x / L_T)) / 2 toward 0 over
                      the transition layer, 0 beyond it.
     Reading A: the nu = 1 ramps span the whole boundary L_T + L_B.
+    Reading K: as C for nu = 1, but the nu >= 2 parameters keep their
+    interior values (no transition layer: the unstable configuration of
+    Sec. 3.3).
     Reading C: as A for d^{nu=1}; alpha^{nu=1} is blended by the cosine
     transition over L_T from the tissue's value into the C-PML profile
     d_target (1 - x/L), which is linear to 0 at the outer edge (d_target
@@ -152,8 +155,12 @@ def boundary_profile(X0: np.ndarray, depth: np.ndarray, nu: int, which: str,
     C-PML mechanism.
     `nu` is 1-based as in the paper; `which` is "d" or "alpha".
     """
-    if reading.upper() not in ("A", "C"):
-        raise ValueError(f"C-PML reading {reading!r}: A or C")
+    if reading.upper() not in ("A", "C", "K"):
+        raise ValueError(f"C-PML reading {reading!r}: A, C or K")
+    if reading.upper() == "K":
+        if nu >= 2:
+            return np.asarray(X0, np.float64).copy()
+        reading = "C"
     X0 = np.asarray(X0, np.float64)
     L = LT + LB
     out = X0.copy()

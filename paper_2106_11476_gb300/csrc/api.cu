@@ -357,6 +357,67 @@ fw2_status ctx_prepare(fw2_ctx *c) {
   return build_sources(c);
 }
 fw2_status ctx_fail(fw2_ctx *c, fw2_status s, const char *msg) { return fail(c, s, "%s", msg); }
+
+// Enqueue every launch of time step n (Sec. 3.1 order): velocity half step,
+// velocity sources, pressure half step, pressure sources, recording.
+fw2_status enqueue_step(fw2_ctx *c, long long n) {
+  const StepParams &P = c->P;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (c->profiling) {
+    ev = {take_event(c), take_event(c)};
+    CK(c, cudaEventRecord(ev.first, c->stream));
+  }
+  CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->tm_vel, c->stream)
+                              : launch_pipe3d(true, P, c->n_sm, c->tm_vel, c->stream))
+                : c->nd == 2 ? launch_vel2d(P, c->map_kind, c->stream) : launch_vel3d(P, c->map_kind, c->stream));
+  c->launches++;
+  if (c->profiling) {
+    CK(c, cudaEventRecord(ev.second, c->stream));
+    c->ev_vel.push_back(ev);
+    ev = {take_event(c), take_event(c)};
+  }
+  if (n < c->sig_steps) {
+    for (int kind = 1; kind <= c->nd; ++kind) {
+      const DevSource &d = c->dsrc[kind];
+      if (d.n_tgt == 0) continue;
+      CK(c, launch_inject(c->v[kind - 1], d.tgt, d.off, d.col, c->d_signal + n * c->sig_cols, d.n_tgt, c->stream));
+      c->launches++;
+    }
+  }
+  if (c->profiling) CK(c, cudaEventRecord(ev.first, c->stream));
+  CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->tm_prs, c->stream)
+                              : launch_pipe3d(false, P, c->n_sm, c->tm_prs, c->stream))
+                : c->nd == 2 ? launch_prs2d(P, c->map_kind, c->stream) : launch_prs3d(P, c->map_kind, c->stream));
+  c->launches++;
+  if (c->profiling) {
+    CK(c, cudaEventRecord(ev.second, c->stream));
+    c->ev_prs.push_back(ev);
+  }
+  if (n < c->sig_steps && c->dsrc[0].n_tgt > 0) {
+    const DevSource &d = c->dsrc[0];
+    CK(c, launch_inject(c->p, d.tgt, d.off, d.col, c->d_signal + n * c->sig_cols, d.n_tgt, c->stream));
+    c->launches++;
+  }
+  if (c->rec_groups > 0 && n < c->rec_steps) {
+    CK(c, launch_record(c->p, c->rec_cell, c->rec_off, c->rec_groups, c->rec_out + n * c->rec_groups, c->stream));
+    c->launches++;
+  }
+  return FW2_OK;
+}
+
+// max |p| of the context (+inf when a value is not finite); synchronises the
+// context stream.
+fw2_status scan_p(fw2_ctx *c, float *max_abs) {
+  CK(c, cudaMemsetAsync(c->d_absmax, 0, sizeof(unsigned int), c->stream));
+  CK(c, launch_absmax(c->p, c->nx, c->pitch, (long long)c->ny * c->nz, c->d_absmax, c->stream));
+  c->launches++;
+  unsigned int bits = 0;
+  CK(c, cudaMemcpyAsync(&bits, c->d_absmax, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  std::memcpy(max_abs, &bits, 4);
+  return FW2_OK;
+}
+
 }  // namespace fw2
 
 extern "C" {
@@ -456,8 +517,8 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
     if (!(cfg.pml_rc > 0.0 && cfg.pml_rc < 1.0)) return fail(nullptr, FW2_EINVAL, "pml_rc must lie in (0, 1)");
     if (!(cfg.pml_npow >= 0.0)) return fail(nullptr, FW2_EINVAL, "pml_npow must be >= 0");
   }
-  if (cfg.pml_reading != FW2_PML_A && cfg.pml_reading != FW2_PML_C)
-    return fail(nullptr, FW2_EINVAL, "bad pml_reading (FW2_PML_A = 0 or FW2_PML_C = 2)");
+  if (cfg.pml_reading != FW2_PML_A && cfg.pml_reading != FW2_PML_C && cfg.pml_reading != FW2_PML_NO_TRANSITION)
+    return fail(nullptr, FW2_EINVAL, "bad pml_reading (FW2_PML_A = 0, FW2_PML_C = 2 or FW2_PML_NO_TRANSITION = 3)");
   if (cfg.map_precision < FW2_MAP_F32 || cfg.map_precision > FW2_MAP_IDX_U8)
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
   if (cfg.map_precision == FW2_MAP_IDX_U8 && cfg.ndim != 2)
@@ -733,51 +794,26 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
   fw2_status st;
   if ((st = finalize(c)) != FW2_OK) return st;
   if ((st = build_sources(c)) != FW2_OK) return st;
-  const StepParams &P = c->P;
   for (int64_t s = 0; s < n_steps; ++s) {
-    const long long n = c->step + s;
-    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-    if (c->profiling) {
-      ev = {take_event(c), take_event(c)};
-      CK(c, cudaEventRecord(ev.first, c->stream));
-    }
-    CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->tm_vel, c->stream)
-                                : launch_pipe3d(true, P, c->n_sm, c->tm_vel, c->stream))
-                  : c->nd == 2 ? launch_vel2d(P, c->map_kind, c->stream) : launch_vel3d(P, c->map_kind, c->stream));
-    c->launches++;
-    if (c->profiling) {
-      CK(c, cudaEventRecord(ev.second, c->stream));
-      c->ev_vel.push_back(ev);
-      ev = {take_event(c), take_event(c)};
-    }
-    if (n < c->sig_steps) {
-      for (int kind = 1; kind <= c->nd; ++kind) {
-        const DevSource &d = c->dsrc[kind];
-        if (d.n_tgt == 0) continue;
-        CK(c, launch_inject(c->v[kind - 1], d.tgt, d.off, d.col, c->d_signal + n * c->sig_cols, d.n_tgt, c->stream));
-        c->launches++;
-      }
-    }
-    if (c->profiling) CK(c, cudaEventRecord(ev.first, c->stream));
-    CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->tm_prs, c->stream)
-                                : launch_pipe3d(false, P, c->n_sm, c->tm_prs, c->stream))
-                  : c->nd == 2 ? launch_prs2d(P, c->map_kind, c->stream) : launch_prs3d(P, c->map_kind, c->stream));
-    c->launches++;
-    if (c->profiling) {
-      CK(c, cudaEventRecord(ev.second, c->stream));
-      c->ev_prs.push_back(ev);
-    }
-    if (n < c->sig_steps && c->dsrc[0].n_tgt > 0) {
-      const DevSource &d = c->dsrc[0];
-      CK(c, launch_inject(c->p, d.tgt, d.off, d.col, c->d_signal + n * c->sig_cols, d.n_tgt, c->stream));
-      c->launches++;
-    }
-    if (c->rec_groups > 0 && n < c->rec_steps) {
-      CK(c, launch_record(c->p, c->rec_cell, c->rec_off, c->rec_groups, c->rec_out + n * c->rec_groups, c->stream));
-      c->launches++;
+    if ((st = enqueue_step(c, c->step)) != FW2_OK) return st;
+    c->step += 1;  // every launch of the step is enqueued; it counts even if a later one fails
+    if (c->watch_every > 0 && c->step % c->watch_every == 0) {
+      float m = 0.f;
+      if ((st = scan_p(c, &m)) != FW2_OK) return st;
+      if (!(m <= c->watch_bound))
+        return fail(c, FW2_EUNSTABLE, "field blew up by step %lld: max |p| = %g exceeds the watch bound %g",
+                    (long long)c->step, m, c->watch_bound);
     }
   }
-  c->step += n_steps;
+  return FW2_OK;
+}
+
+fw2_status fw2_set_watch(fw2_ctx *c, int64_t every, float bound) {
+  if (!c) return FW2_EINVAL;
+  if (every < 0) return fail(c, FW2_EINVAL, "negative watch interval");
+  if (every > 0 && !(bound > 0.f)) return fail(c, FW2_EINVAL, "the watch bound must be positive");
+  c->watch_every = every;
+  c->watch_bound = bound;
   return FW2_OK;
 }
 
@@ -851,14 +887,9 @@ fw2_status fw2_synchronize(fw2_ctx *c) {
 
 fw2_status fw2_check_field(fw2_ctx *c, float bound, float *max_abs) {
   if (!c) return FW2_EINVAL;
-  CK(c, cudaMemsetAsync(c->d_absmax, 0, sizeof(unsigned int), c->stream));
-  CK(c, launch_absmax(c->p, c->nx, c->pitch, (long long)c->ny * c->nz, c->d_absmax, c->stream));
-  c->launches++;
-  unsigned int bits = 0;
-  CK(c, cudaMemcpyAsync(&bits, c->d_absmax, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
-  float m;
-  std::memcpy(&m, &bits, 4);
+  float m = 0.f;
+  const fw2_status st = scan_p(c, &m);
+  if (st != FW2_OK) return st;
   if (max_abs) *max_abs = m;
   if (!(m <= bound)) return fail(c, FW2_EUNSTABLE, "field check failed: max |p| = %g exceeds %g", m, bound);
   return FW2_OK;

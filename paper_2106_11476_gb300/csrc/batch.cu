@@ -116,6 +116,10 @@ struct fw2_batch {
   std::vector<float> trial_ms[4];
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  long long steps_done = 0;  // batch steps since creation
+  // blow-up detection: scan every context's p every watch_every steps (0: off)
+  long long watch_every = 0;
+  float watch_bound = 0.f;
   long long launches = 0;
 };
 
@@ -341,8 +345,16 @@ float median_of(std::vector<float> v) {
 }
 
 // Enqueue n_steps batch steps; *done counts the steps enqueued (they run
-// even when a later enqueue fails).
-fw2_status batch_advance(fw2_batch *b, int64_t n_steps, int64_t *done) {
+// even when a later enqueue fails), b->steps_done follows it.
+fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
+  const int64_t start = *done;
+  struct Count {  // keeps b->steps_done in step with *done on every return
+    fw2_batch *b;
+    const int64_t *done;
+    int64_t start;
+    ~Count() { b->steps_done += *done - start; }
+  } count{b, done, start};
+  n_steps += start;
   // online tuning: one warm-up step (it pays the first launch's cold start),
   // then each launch configuration for kTrialReps steps (every
   // configuration computes the same result); the fastest median wins
@@ -408,6 +420,46 @@ fw2_status batch_advance(fw2_batch *b, int64_t n_steps, int64_t *done) {
   return FW2_OK;
 }
 
+// max |p| of every context, scanned on the batch stream; FW2_EUNSTABLE names
+// the first context that holds a non-finite value or exceeds the bound.
+fw2_status batch_scan(fw2_batch *b) {
+  std::vector<unsigned int> bits(b->ctxs.size(), 0u);
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    fw2_ctx *c = b->ctxs[i];
+    BCK(b, cudaMemsetAsync(c->d_absmax, 0, sizeof(unsigned int), b->stream));
+    BCK(b, launch_absmax(c->p, c->nx, c->pitch, (long long)c->ny * c->nz, c->d_absmax, b->stream));
+    ++b->launches;
+    BCK(b, cudaMemcpyAsync(&bits[i], c->d_absmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream));
+  }
+  BCK(b, cudaStreamSynchronize(b->stream));
+  for (size_t i = 0; i < bits.size(); ++i) {
+    float m;
+    std::memcpy(&m, &bits[i], 4);
+    if (!(m <= b->watch_bound)) {
+      char msg[200];
+      std::snprintf(msg, sizeof msg, "context %zu blew up by batch step %lld: max |p| = %g exceeds the watch bound %g",
+                    i, b->steps_done, (double)m, (double)b->watch_bound);
+      return bfail(b, FW2_EUNSTABLE, msg);
+    }
+  }
+  return FW2_OK;
+}
+
+// batch_run in segments that end where a blow-up scan is due.
+fw2_status batch_advance(fw2_batch *b, int64_t n_steps, int64_t *done) {
+  while (*done < n_steps) {
+    int64_t seg = n_steps - *done;
+    if (b->watch_every > 0) seg = std::min<int64_t>(seg, b->watch_every - b->steps_done % b->watch_every);
+    const fw2_status st = batch_run(b, seg, done);
+    if (st != FW2_OK) return st;
+    if (b->watch_every > 0 && b->steps_done % b->watch_every == 0) {
+      const fw2_status sc = batch_scan(b);
+      if (sc != FW2_OK) return sc;
+    }
+  }
+  return FW2_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -430,6 +482,15 @@ fw2_status fw2_batch_step(fw2_batch *b, int64_t n_steps) {
   // the steps enqueued before a failure still advance the contexts
   for (fw2_ctx *c : b->ctxs) c->step += done;
   return st;
+}
+
+fw2_status fw2_batch_set_watch(fw2_batch *b, int64_t every, float bound) {
+  if (!b) return FW2_EINVAL;
+  if (every < 0) return bfail(b, FW2_EINVAL, "negative watch interval");
+  if (every > 0 && !(bound > 0.f)) return bfail(b, FW2_EINVAL, "the watch bound must be positive");
+  b->watch_every = every;
+  b->watch_bound = bound;
+  return FW2_OK;
 }
 
 fw2_status fw2_batch_synchronize(fw2_batch *b) {

@@ -80,6 +80,9 @@ struct fw2_ctx {
   long long step = 0, launches = 0;
   // optional per-kernel event timing
   bool profiling = false;
+  // in-loop blow-up detection: scan p every watch_every steps (0: off)
+  long long watch_every = 0;
+  float watch_bound = 0.f;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_vel, ev_prs;
 };

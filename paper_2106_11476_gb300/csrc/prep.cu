@@ -63,7 +63,7 @@ __device__ __forceinline__ double depth_of(double x, int n, int L) {
 __device__ double ramp(const PrepParams &Q, double X0, double depth, int nu, bool is_d) {
   if (depth <= 0.0) return X0;
   const int LT = Q.LT, LB = Q.LB, L = LT + LB;
-  if (nu == 0 && !is_d && Q.reading == 2) {
+  if (nu == 0 && !is_d && (Q.reading == 2 || Q.reading == 3)) {
     // reading C: the tissue's alpha is blended (cosine over the transition
     // layer) into the C-PML profile d_target (1 - x/L), linear to 0 at the
     // outer edge
@@ -77,6 +77,7 @@ __device__ double ramp(const PrepParams &Q, double X0, double depth, int nu, boo
     if (is_d) return (Q.d_target - X0) * pow(s, Q.npow) + X0;
     return (0.0 - X0) * s + X0;
   }
+  if (Q.reading == 3) return X0;  // no transition layer: nu >= 2 kept (unstable, Sec. 3.3)
   double g = 1.0;
   if (LT > 0 && depth < LT) g = 0.5 * (1.0 - cos(M_PI * depth / LT));
   return (0.0 - X0) * g + X0;

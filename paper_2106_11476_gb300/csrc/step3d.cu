@@ -65,12 +65,12 @@ __device__ __forceinline__ void vel3_cross(const StepParams &P, const float (*sp
   const Win12 zp_dn = win12_g(P, P.p, i0, j - 1, k + 1);
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    el(Dx, e) += P.g11h * (((up.v[5 + e] - up.v[4 + e]) + (dn.v[5 + e] - dn.v[4 + e])) +
-                           ((zp.v[5 + e] - zp.v[4 + e]) + (zm.v[5 + e] - zm.v[4 + e])));
-    el(Dy, e) += P.g11h * (((up.v[5 + e] - w.v[5 + e]) + (up.v[3 + e] - w.v[3 + e])) +
-                           ((zp_up.v[4 + e] - zp.v[4 + e]) + (zm_up.v[4 + e] - zm.v[4 + e])));
-    el(Dz, e) += P.g11h * (((zp.v[5 + e] - w.v[5 + e]) + (zp.v[3 + e] - w.v[3 + e])) +
-                           ((zp_up.v[4 + e] - up.v[4 + e]) + (zp_dn.v[4 + e] - dn.v[4 + e])));
+    el(Dx, e) = fmaf(P.g11h, (((up.v[5 + e] - up.v[4 + e]) + (dn.v[5 + e] - dn.v[4 + e])) +
+                           ((zp.v[5 + e] - zp.v[4 + e]) + (zm.v[5 + e] - zm.v[4 + e]))), el(Dx, e));
+    el(Dy, e) = fmaf(P.g11h, (((up.v[5 + e] - w.v[5 + e]) + (up.v[3 + e] - w.v[3 + e])) +
+                           ((zp_up.v[4 + e] - zp.v[4 + e]) + (zm_up.v[4 + e] - zm.v[4 + e]))), el(Dy, e));
+    el(Dz, e) = fmaf(P.g11h, (((zp.v[5 + e] - w.v[5 + e]) + (zp.v[3 + e] - w.v[3 + e])) +
+                           ((zp_up.v[4 + e] - up.v[4 + e]) + (zp_dn.v[4 + e] - dn.v[4 + e]))), el(Dz, e));
   }
 }
 
@@ -83,8 +83,8 @@ __device__ __forceinline__ void prs3_cross(const StepParams &P, int i0, int j, i
     const Win12 c = win12_g(P, P.v[0], i0, j, k + 1), d = win12_g(P, P.v[0], i0, j, k - 1);
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      el(Dx, e) += P.g11h * (((a.v[4 + e] - a.v[3 + e]) + (b.v[4 + e] - b.v[3 + e])) +
-                             ((c.v[4 + e] - c.v[3 + e]) + (d.v[4 + e] - d.v[3 + e])));
+      el(Dx, e) = fmaf(P.g11h, (((a.v[4 + e] - a.v[3 + e]) + (b.v[4 + e] - b.v[3 + e])) +
+                             ((c.v[4 + e] - c.v[3 + e]) + (d.v[4 + e] - d.v[3 + e]))), el(Dx, e));
   }
   {
     const Win12 y0 = win12_g(P, P.v[1], i0, j, k), y1 = win12_g(P, P.v[1], i0, j - 1, k);
@@ -92,8 +92,8 @@ __device__ __forceinline__ void prs3_cross(const StepParams &P, int i0, int j, i
     const Win12 zm0 = win12_g(P, P.v[1], i0, j, k - 1), zm1 = win12_g(P, P.v[1], i0, j - 1, k - 1);
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      el(Dy, e) += P.g11h * (((y0.v[5 + e] - y1.v[5 + e]) + (y0.v[3 + e] - y1.v[3 + e])) +
-                             ((zp0.v[4 + e] - zp1.v[4 + e]) + (zm0.v[4 + e] - zm1.v[4 + e])));
+      el(Dy, e) = fmaf(P.g11h, (((y0.v[5 + e] - y1.v[5 + e]) + (y0.v[3 + e] - y1.v[3 + e])) +
+                             ((zp0.v[4 + e] - zp1.v[4 + e]) + (zm0.v[4 + e] - zm1.v[4 + e]))), el(Dy, e));
   }
   {
     const Win12 z0 = win12_g(P, P.v[2], i0, j, k), z1 = win12_g(P, P.v[2], i0, j, k - 1);
@@ -101,8 +101,8 @@ __device__ __forceinline__ void prs3_cross(const StepParams &P, int i0, int j, i
     const Win12 d0 = win12_g(P, P.v[2], i0, j - 1, k), d1 = win12_g(P, P.v[2], i0, j - 1, k - 1);
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      el(Dz, e) += P.g11h * (((z0.v[5 + e] - z1.v[5 + e]) + (z0.v[3 + e] - z1.v[3 + e])) +
-                             ((u0.v[4 + e] - u1.v[4 + e]) + (d0.v[4 + e] - d1.v[4 + e])));
+      el(Dz, e) = fmaf(P.g11h, (((z0.v[5 + e] - z1.v[5 + e]) + (z0.v[3 + e] - z1.v[3 + e])) +
+                             ((u0.v[4 + e] - u1.v[4 + e]) + (d0.v[4 + e] - d1.v[4 + e]))), el(Dz, e));
   }
 }
 

@@ -8,23 +8,31 @@
 // hold neighbouring columns at about the same depth and share the halo rows
 // in L2).  The operand planes a unit's z taps need stay in a ring of nine
 // plane slots in shared memory (velocity: p planes k-3 .. k+4 with their xy
-// halo, which also give the x and y taps; pressure: v_z planes k-4 .. k+3), so
-// each unit adds one plane.  For a coming unit one thread issues tiled TMA
-// tensor copies, one box per array, into a free stage of a two-stage ring:
-// the operand plane the unit adds (into the plane ring), the density of the
-// plane and of the next one, the velocity (or pressure) of the unit, all 3N
-// memory variables of the half step in one 4D box, and the bf16 maps (a and b
-// of the N mechanisms in one 4D box each).  The first unit of an item loads
-// its eight planes after the previous unit's compute.  Copies complete on
-// the stage's mbarrier while all threads compute the current unit from the
-// other stage; no computing thread issues a global load outside the C-PML
-// strips.
+// halo, which also give the x and y taps and the g_{1,1} cross taps of
+// planes k-1 .. k+1; pressure: v_z planes k-4 .. k+3), so each unit adds one
+// plane.  With cross taps the pressure half step also keeps v_x and v_y
+// planes k-1 .. k+1 (with a one-cell halo) in rings of four slots, and its
+// v_z slots carry the same halo.  For a coming unit one thread issues tiled
+// TMA tensor copies, one box per array, into a free stage of a two-stage
+// ring: the operand planes the unit adds, the density of the plane and of
+// the next one, the velocity (or pressure) of the unit, the bf16 maps (a and
+// b of the N mechanisms in one 4D box each), K of planes k and k + 1 for the
+// literal system's momentum factor, and in edge units the C-PML strip
+// coefficients of each axis the unit reaches.  The memory variables, read
+// once and written once by the thread that owns the cell, bypass shared
+// memory: every thread loads the next unit's into registers while it
+// computes the current one.  Copies complete on the stage's mbarrier while
+// all threads compute the current unit from the other stage.
 //
 // Boundaries as in the 2D pipeline: the copies read zero outside the grid;
 // units at the grid's edge or in a C-PML strip clamp the density to the last
-// cell, take each axis' C-PML coefficients from its strip (all mechanisms
-// loaded before the first store) and store nothing outside the grid.
-// Periodic axes are not taken by this path (the tile kernels run them).
+// cell, take each axis' C-PML coefficients from its strip (staged, or read
+// per cell where a box cannot serve: a strip wider than 64 cells or not a
+// multiple of 8 along x, a grid too small for a unit to reach one side only
+// along y) and store nothing outside the grid.  Periodic axes are not taken
+// by this path (the tile kernels run them).
+#include <climits>
+
 #include "async.cuh"
 #include "coef.cuh"
 #include "tmap.h"
@@ -34,8 +42,8 @@ namespace fw2 {
 namespace {
 
 constexpr int kHT = 8;            // rows of a unit
-constexpr int kCW = kTX + 8;      // operand halo columns x0-4 .. x0+TX+3
-constexpr int kRWb = kTX + 8;     // staged bf16 density columns x0 .. x0+TX+7 (16-byte rows)
+constexpr int kCW = kTX + 8;      // halo columns x0-4 .. x0+TX+3
+constexpr int kRWb = kTX + 8;     // staged bf16 density / K columns x0 .. x0+TX+7 (16-byte rows)
 constexpr int kArr = kHT * kTX;   // elements of one array per unit
 
 using bf16 = __nv_bfloat16;
@@ -43,63 +51,77 @@ using bf16 = __nv_bfloat16;
 constexpr int round32(int n) { return (n + 31) & ~31; }  // floats: 128-byte regions
 constexpr int fl(int bytes) { return (bytes + 3) / 4; }
 
-// ------------------------------------------------------------- stages ---
-constexpr int kSlots = 9;  // plane ring: the eight planes of a unit and the one the next unit adds
+constexpr int kSlots = 9;  // operand ring: the eight planes of a unit and the one the next unit adds
+constexpr int kSub = 4;    // cross-tap rings of v_x, v_y: planes k-1 .. k+1 and the one the next unit adds
 constexpr int kXsMax = 64; // widest x C-PML strip (cells per side) staged by TMA
 
-// x-strip region of a stage: a then b, each [N][8][L] bf16 (L <= kXsMax)
+__host__ __device__ constexpr int ring_slot(int k) { return ((k % kSlots) + kSlots) % kSlots; }
+__host__ __device__ constexpr int sub_slot(int k) { return ((k % kSub) + kSub) % kSub; }
+
+// C-PML strip coefficients of a stage (bf16): x strip a then b, each
+// [N][8][L] (L <= kXsMax); y strip a, b and z strip a, b, each [N][8][128]
 template <int N>
-struct XStrip {
-  static constexpr int kHalf = N * kHT * kXsMax / 2;  // floats of a (or b); 128-byte multiple
-  static constexpr int kFloats = 2 * kHalf;
+struct Strips {
+  static constexpr int kX = N * kHT * kXsMax / 2;  // floats of the x strip's a (or b)
+  static constexpr int kYZ = N * kArr / 2;         // floats of a y or z strip's a (or b)
+  static constexpr int oXa = 0, oXb = kX, oYa = 2 * kX, oYb = oYa + kYZ, oZa = oYb + kYZ, oZb = oZa + kYZ;
+  static constexpr int kFloats = oZb + kYZ;
 };
 
-__host__ __device__ constexpr int ring_slot(int k) { return ((k % kSlots) + kSlots) % kSlots; }
-
 // velocity stage: density bf16 [2][9][136] (planes k, k+1), v [3][8][128],
-// psi1 [3N][8][128], 1/kappa1 bf16 [8][128], a1, b1 bf16 [N][8][128];
-// plane ring: p planes [15][136] (rows y0-3 .. y0+11, columns x0-4 ..)
+// 1/kappa1 bf16 [8][128], a1, b1 bf16 [N][8][128], K bf16 [2][9][136]
+// (literal system), strips; plane ring: p planes [15][136] (rows y0-3 ..
+// y0+11, columns x0-4 ..)
 template <int N>
 struct Vel3 {
   static constexpr int kRho = round32(fl(2 * (kHT + 1) * kRWb * 2));
   static constexpr int kV = 3 * kArr;
-  static constexpr int kPsi = 3 * N * kArr;
   static constexpr int kK = round32(fl(kArr * 2));
   static constexpr int kAB = round32(fl(N * kArr * 2));
-  static constexpr int oRho = 0, oV = oRho + kRho, oPsi = oV + kV, oK = oPsi + kPsi, oA = oK + kK, oB = oA + kAB,
-                       oXs = oB + kAB;
-  static constexpr int kFloats = round32(oXs + XStrip<N>::kFloats);
-  static constexpr unsigned kBytes = 4u * (kV + kPsi) + 2u * (2 * (kHT + 1) * kRWb + kArr + 2 * N * kArr);
+  static constexpr int oRho = 0, oV = oRho + kRho, oK = oV + kV, oA = oK + kK, oB = oA + kAB, oKm = oB + kAB,
+                       oS = oKm + kRho;
+  static constexpr int kFloats = round32(oS + Strips<N>::kFloats);
+  static constexpr unsigned kBytes = 4u * kV + 2u * (2 * (kHT + 1) * kRWb + kArr + 2 * N * kArr);
+  static constexpr unsigned kKmBytes = 2u * 2 * (kHT + 1) * kRWb;
   static constexpr int kPlane = round32((kHT + 7) * kCW);
   static constexpr unsigned kPlaneBytes = 4u * (kHT + 7) * kCW;
 };
 
-// pressure stage: v_x plane [8][136] (x halo), v_y plane [15][128] (rows
-// y0-4 ..), p [8][128], psi2 [3N][8][128], 1/kappa2, K, chi bf16 [8][128],
-// a2, b2 bf16 [N][8][128]; plane ring: v_z planes [8][128]
-template <int N>
+// pressure stage: p [8][128], 1/kappa2, K, chi bf16 [8][128], a2, b2 bf16
+// [N][8][128], strips; without cross taps also v_x [8][136] (x halo) and v_y
+// [15][128] (rows y0-4 ..), with the plane ring of v_z [8][128]; with cross
+// taps the rings hold v_z [10][136] (rows y0-1 .., columns x0-4 ..), v_x
+// [10][136] (rows y0-1 ..) and v_y [15][136] (rows y0-4 ..)
+template <int N, bool CROSS>
 struct Prs3 {
-  static constexpr int kVx = round32(kHT * kCW);
-  static constexpr int kVy = round32((kHT + 7) * kTX);
+  static constexpr int kVx = CROSS ? 0 : round32(kHT * kCW);
+  static constexpr int kVy = CROSS ? 0 : round32((kHT + 7) * kTX);
   static constexpr int kP = kArr;
-  static constexpr int kPsi = 3 * N * kArr;
   static constexpr int kK = round32(fl(kArr * 2));
   static constexpr int kAB = round32(fl(N * kArr * 2));
-  static constexpr int oVx = 0, oVy = oVx + kVx, oP = oVy + kVy, oPsi = oP + kP, oIk = oPsi + kPsi,
-                       oKm = oIk + kK, oChi = oKm + kK, oA = oChi + kK, oB = oA + kAB, oXs = oB + kAB;
-  static constexpr int kFloats = round32(oXs + XStrip<N>::kFloats);
+  static constexpr int oVx = 0, oVy = oVx + kVx, oP = oVy + kVy, oIk = oP + kP, oKm = oIk + kK, oChi = oKm + kK,
+                       oA = oChi + kK, oB = oA + kAB, oS = oB + kAB;
+  static constexpr int kFloats = round32(oS + Strips<N>::kFloats);
   static constexpr unsigned kBytesNoChi =
-      4u * (kHT * kCW + (kHT + 7) * kTX + kP + kPsi) + 2u * (2 * kArr + 2 * N * kArr);
-  static constexpr int kPlane = kArr;
-  static constexpr unsigned kPlaneBytes = 4u * kArr;
+      4u * (CROSS ? kP : kHT * kCW + (kHT + 7) * kTX + kP) + 2u * (2 * kArr + 2 * N * kArr);
+  // v_z ring slot; with cross taps also the v_x and v_y ring slots
+  static constexpr int kPlane = CROSS ? round32((kHT + 2) * kCW) : kArr;
+  static constexpr unsigned kPlaneBytes = 4u * (CROSS ? (kHT + 2) * kCW : kArr);
+  static constexpr int kXPlane = round32((kHT + 2) * kCW);
+  static constexpr unsigned kXPlaneBytes = 4u * (kHT + 2) * kCW;
+  static constexpr int kYPlane = round32((kHT + 7) * kCW);
+  static constexpr unsigned kYPlaneBytes = 4u * (kHT + 7) * kCW;
 };
 
-template <int N, bool VEL>
+template <int N, bool VEL, bool CROSS>
 struct Ring3 {
-  static constexpr int kStage = VEL ? Vel3<N>::kFloats : Prs3<N>::kFloats;
-  static constexpr int kPlane = VEL ? Vel3<N>::kPlane : Prs3<N>::kPlane;
-  static constexpr unsigned kPlaneBytes = VEL ? Vel3<N>::kPlaneBytes : Prs3<N>::kPlaneBytes;
-  static constexpr size_t kBytes = sizeof(float) * (2 * (size_t)kStage + (size_t)kSlots * kPlane) + 128;
+  static constexpr int kStage = VEL ? Vel3<N>::kFloats : Prs3<N, CROSS>::kFloats;
+  static constexpr int kPlane = VEL ? Vel3<N>::kPlane : Prs3<N, CROSS>::kPlane;
+  static constexpr unsigned kPlaneBytes = VEL ? Vel3<N>::kPlaneBytes : Prs3<N, CROSS>::kPlaneBytes;
+  static constexpr int kSubFloats =
+      (!VEL && CROSS) ? kSub * (Prs3<N, CROSS>::kXPlane + Prs3<N, CROSS>::kYPlane) : 0;
+  static constexpr size_t kBytes =
+      sizeof(float) * (2 * (size_t)kStage + (size_t)kSlots * kPlane + (size_t)kSubFloats) + 128;
 };
 
 // Work items: a column of units (xy position, x fastest) and a range of
@@ -109,11 +131,23 @@ struct Region3 {
   int tnx, nhy;      // x tiles, half-tile rows per plane
   int seglen, nseg;  // planes per item, items per column
   int xsL;           // x C-PML strip cells per side when its coefficients come by TMA, else 0
+  int ysL, zsL;      // the same for the y and z strips
   // the side of the x strip a unit at x0 reaches: 0 low, 1 high, -1 none
   // (with xsL set no unit reaches both)
   __device__ __forceinline__ int xs_side(int x0) const {
     if (xsL == 0) return -1;
     return x0 < xsL ? 0 : (x0 + kTX > nx - xsL ? 1 : -1);
+  }
+  // first strip row of the y box of a unit at y0 (INT_MIN: none)
+  __device__ __forceinline__ int ys_row(int y0) const {
+    if (ysL == 0) return INT_MIN;
+    if (y0 < ysL) return y0;
+    if (y0 + kHT > ny - ysL) return y0 - (ny - 2 * ysL);
+    return INT_MIN;
+  }
+  __device__ __forceinline__ int zs_plane(int k) const {
+    if (zsL == 0) return -1;
+    return strip_coord(k, nz, zsL);
   }
   __device__ __forceinline__ long long items() const { return (long long)tnx * nhy * nseg; }
   __device__ __forceinline__ void item(long long it, int &x0, int &y0, int &k0, int &k1) const {
@@ -133,47 +167,70 @@ struct Region3 {
 template <bool VEL>
 __host__ __device__ constexpr int ring_first(int k) { return VEL ? k - 3 : k - 4; }
 
-// Issue the copies of a unit at (x0, y0, k): its stage and the operand
-// planes k_lo .. k_hi of the plane ring (one plane, or eight for the first
-// unit of an item), all completing on the stage's mbarrier.
-template <int N, bool VEL>
-__device__ __forceinline__ void issue3(const PipeMaps &T, float *st, float *ring, uint64_t *bar, int x0, int y0,
-                                       int k, int k_lo, int k_hi, bool nl, int xs_side, int xsL) {
-  using G = Ring3<N, VEL>;
+// Issue the copies of a unit at (x0, y0, k): its stage, the operand planes
+// k_lo .. k_hi of the plane ring (one plane, or eight for the first unit of
+// an item) and, with cross taps in the pressure half step, the v_x and v_y
+// planes s_lo .. s_hi of their rings, all completing on the stage's mbarrier.
+template <int N, bool VEL, bool CROSS>
+__device__ __forceinline__ void issue3(const PipeMaps &T, const Region3 &R, float *st, float *ring, float *sub,
+                                       uint64_t *bar, int x0, int y0, int k, int k_lo, int k_hi, int s_lo, int s_hi,
+                                       bool nl, bool nl_vel) {
+  using G = Ring3<N, VEL, CROSS>;
+  using SS = Strips<N>;
   fence_proxy_async_smem();
   const unsigned planes = G::kPlaneBytes * (unsigned)(k_hi - k_lo + 1);
-  // the x strip's coefficients of the unit's rows: one box of a and one of b
-  // (L values of the side the unit reaches, all mechanisms)
-  const unsigned xs = (N > 0 && xs_side >= 0) ? 2u * 2u * (unsigned)(N * kHT * xsL) : 0u;
-  auto load_xs = [&] {
-    if (xs) {
-      float *d = st + (VEL ? Vel3<N>::oXs : Prs3<N>::oXs);
-      tma_load_4d(d, &T.m[10], xs_side * xsL, y0, k, 0, bar);
-      tma_load_4d(d + XStrip<N>::kHalf, &T.m[11], xs_side * xsL, y0, k, 0, bar);
+  // C-PML strip boxes of the axes the unit reaches (all mechanisms)
+  const int xside = N > 0 ? R.xs_side(x0) : -1;
+  const int yrow = N > 0 ? R.ys_row(y0) : INT_MIN;
+  const int zpl = N > 0 ? R.zs_plane(k) : -1;
+  const unsigned xs = xside >= 0 ? 2u * 2u * (unsigned)(N * kHT * R.xsL) : 0u;
+  const unsigned yz = (yrow != INT_MIN ? 2u * 2u * N * kArr : 0u) + (zpl >= 0 ? 2u * 2u * N * kArr : 0u);
+  float *ss = st + (VEL ? Vel3<N>::oS : Prs3<N, CROSS>::oS);
+  auto load_strips = [&] {
+    if (xside >= 0) {
+      tma_load_4d(ss + SS::oXa, &T.m[10], xside * R.xsL, y0, k, 0, bar);
+      tma_load_4d(ss + SS::oXb, &T.m[11], xside * R.xsL, y0, k, 0, bar);
+    }
+    if (yrow != INT_MIN) {
+      tma_load_4d(ss + SS::oYa, &T.m[13], x0, yrow, k, 0, bar);
+      tma_load_4d(ss + SS::oYb, &T.m[14], x0, yrow, k, 0, bar);
+    }
+    if (zpl >= 0) {
+      tma_load_4d(ss + SS::oZa, &T.m[15], x0, y0, zpl, 0, bar);
+      tma_load_4d(ss + SS::oZb, &T.m[16], x0, y0, zpl, 0, bar);
     }
   };
   if (VEL) {
     using S = Vel3<N>;
-    mbar_arrive_expect_tx(bar, S::kBytes + planes + xs);
-    load_xs();
+    mbar_arrive_expect_tx(bar, S::kBytes + (nl_vel ? S::kKmBytes : 0u) + planes + xs + yz);
+    load_strips();
     for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[0], x0 - 4, y0 - 3, kp, bar);
     tma_load_3d(st + S::oRho, &T.m[2], x0, y0, k, bar);
     tma_load_4d(st + S::oV, &T.m[3], x0, y0, k, 0, bar);
-    if (N > 0) tma_load_4d(st + S::oPsi, &T.m[4], x0, y0, k, 0, bar);
     tma_load_3d(st + S::oK, &T.m[5], x0, y0, k, bar);
     if (N > 0) {
       tma_load_4d(st + S::oA, &T.m[6], x0, y0, k, 0, bar);
       tma_load_4d(st + S::oB, &T.m[7], x0, y0, k, 0, bar);
     }
+    if (nl_vel) tma_load_3d(st + S::oKm, &T.m[12], x0, y0, k, bar);
   } else {
-    using S = Prs3<N>;
-    mbar_arrive_expect_tx(bar, S::kBytesNoChi + (nl ? 2u * kArr : 0u) + planes + xs);
-    load_xs();
-    for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[2], x0, y0, kp, bar);
-    tma_load_3d(st + S::oVx, &T.m[0], x0 - 4, y0, k, bar);
-    tma_load_3d(st + S::oVy, &T.m[1], x0, y0 - 4, k, bar);
+    using S = Prs3<N, CROSS>;
+    const unsigned subs = CROSS ? (S::kXPlaneBytes + S::kYPlaneBytes) * (unsigned)(s_hi - s_lo + 1) : 0u;
+    mbar_arrive_expect_tx(bar, S::kBytesNoChi + (nl ? 2u * kArr : 0u) + planes + subs + xs + yz);
+    load_strips();
+    if (CROSS) {
+      for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[2], x0 - 4, y0 - 1, kp, bar);
+      float *sx = sub, *sy = sub + kSub * S::kXPlane;
+      for (int kp = s_lo; kp <= s_hi; ++kp) {
+        tma_load_3d(sx + sub_slot(kp) * S::kXPlane, &T.m[0], x0 - 4, y0 - 1, kp, bar);
+        tma_load_3d(sy + sub_slot(kp) * S::kYPlane, &T.m[1], x0 - 4, y0 - 4, kp, bar);
+      }
+    } else {
+      for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[2], x0, y0, kp, bar);
+      tma_load_3d(st + S::oVx, &T.m[0], x0 - 4, y0, k, bar);
+      tma_load_3d(st + S::oVy, &T.m[1], x0, y0 - 4, k, bar);
+    }
     tma_load_3d(st + S::oP, &T.m[3], x0, y0, k, bar);
-    if (N > 0) tma_load_4d(st + S::oPsi, &T.m[4], x0, y0, k, 0, bar);
     tma_load_3d(st + S::oIk, &T.m[5], x0, y0, k, bar);
     tma_load_3d(st + S::oKm, &T.m[6], x0, y0, k, bar);
     if (nl) tma_load_3d(st + S::oChi, &T.m[7], x0, y0, k, bar);
@@ -221,11 +278,39 @@ __device__ __forceinline__ Win10 win10(const float *row, int c) {
   }
   return w;
 }
+// columns c+2 .. c+7 of a halo row (v[2 + e] is the cell e of a pair at c+4)
+struct Win6 {
+  float v[6];
+};
+__device__ __forceinline__ Win6 win6(const float *row, int c) {
+  Win6 w;
+  const float2 *r2 = reinterpret_cast<const float2 *>(row + c + 2);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float2 t = r2[i];
+    w.v[2 * i] = t.x;
+    w.v[2 * i + 1] = t.y;
+  }
+  return w;
+}
+
+// Memory variables of a thread's two cells: q[axis][nu], loaded one unit
+// ahead (zero for a pair outside the grid, like the padding it would read).
+template <int N>
+using Psi = float2[3][N > 0 ? N : 1];
+template <int N>
+__device__ __forceinline__ void load_psi(float *const *psi, long long Sn, long long c, bool ok, Psi<N> &q) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int nu = 0; nu < N; ++nu)
+      q[a][nu] = ok ? __ldcs(reinterpret_cast<const float2 *>(psi[a] + nu * Sn + c)) : make_float2(0.f, 0.f);
+}
 
 // a, b along axis Q (OP: 1 faces, 2 centres) of mechanism nu at the two
-// cells of an edge pair, from that axis' C-PML strip where the cells lie in
-// it (coef4 of the tile kernels; its zero beyond the grid only reaches
-// masked cells); unchanged elsewhere
+// cells of an edge pair, from that axis' C-PML strip in global memory where
+// the cells lie in it (coef4 of the tile kernels; its zero beyond the grid
+// only reaches masked cells); unchanged elsewhere
 template <int Q, int OP>
 __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int j, int k, float2 &a, float2 &b) {
   const bf16 *sa = static_cast<const bf16 *>(OP == 1 ? P.sa1[Q] : P.sa2[Q]);
@@ -272,8 +357,8 @@ __device__ __forceinline__ void strip3(const StepParams &P, int nu, int i0, int 
 }
 
 // a, b of the x strip at the two cells of an edge pair from the staged boxes
-// (a then b, each [N][8][L] bf16, the side the unit reaches): the values
-// strip3<0> reads from global memory, for the cells in the strip
+// (each [N][8][L] bf16, the side the unit reaches): the values strip3<0>
+// reads from global memory, for the cells in the strip
 __device__ __forceinline__ void strip3x_staged(const StepParams &P, const bf16 *xa, const bf16 *xb, int xsL, int nu,
                                                int i0, int ly, float2 &a, float2 &b) {
   const int L = P.L[0];
@@ -291,12 +376,43 @@ __device__ __forceinline__ void strip3x_staged(const StepParams &P, const bf16 *
   }
 }
 
-// Prefetch into L2 the C-PML strip rows an edge unit will read (warp 0, one
-// unit ahead): its C-PML coefficients are otherwise read straight from DRAM
-// while the unit computes.  OP: 1 velocity (a1, b1), 2 pressure (a2, b2).
+// All C-PML coefficient overrides of an edge pair for mechanism nu (axes x,
+// y, z), from the staged boxes where the unit has them, else global memory.
+template <int N, int OP>
+__device__ __forceinline__ void strips_of(const StepParams &P, const Region3 &R, const float *ss, int xside, bool ys,
+                                          bool zs, int nu, int i0, int j, int k, int ly, int lx, float2 (&A)[3],
+                                          float2 (&B)[3]) {
+  using SS = Strips<N>;
+  if (xside >= 0)
+    strip3x_staged(P, reinterpret_cast<const bf16 *>(ss + SS::oXa), reinterpret_cast<const bf16 *>(ss + SS::oXb),
+                   R.xsL, nu, i0, ly, A[0], B[0]);
+  else
+    strip3<0, OP>(P, nu, i0, j, k, A[0], B[0]);
+  if (ys) {
+    if (strip_coord(j, P.ny, P.L[1]) >= 0) {
+      const int o = nu * kArr + ly * kTX + lx;
+      A[1] = sldh2(reinterpret_cast<const bf16 *>(ss + SS::oYa) + o);
+      B[1] = sldb2(reinterpret_cast<const bf16 *>(ss + SS::oYb) + o);
+    }
+  } else {
+    strip3<1, OP>(P, nu, i0, j, k, A[1], B[1]);
+  }
+  if (zs) {
+    const int o = nu * kArr + ly * kTX + lx;
+    A[2] = sldh2(reinterpret_cast<const bf16 *>(ss + SS::oZa) + o);
+    B[2] = sldb2(reinterpret_cast<const bf16 *>(ss + SS::oZb) + o);
+  } else {
+    strip3<2, OP>(P, nu, i0, j, k, A[2], B[2]);
+  }
+}
+
+// Prefetch into L2 the C-PML strip rows an edge unit will read per cell from
+// global memory (warp 0, one unit ahead): only strips without a staged box.
+// OP: 1 velocity (a1, b1), 2 pressure (a2, b2).
 __device__ __forceinline__ void l2_line(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 template <int N, int OP>
-__device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int y0, int k, int lane, bool xs_staged) {
+__device__ __forceinline__ void prefetch_strips(const StepParams &P, const Region3 &R, int x0, int y0, int k,
+                                                int lane) {
   if constexpr (N > 0) {
     const bf16 *sa[3], *sb[3];
 #pragma unroll
@@ -306,7 +422,7 @@ __device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int
     }
     // x strip: rows (k, y) of 2L values, for units reaching into it
     const int Lx = P.L[0];
-    if (!xs_staged && Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
+    if (R.xsL == 0 && Lx > 0 && (x0 < Lx || x0 + kTX > P.nx - Lx)) {
       for (int t = lane; t < kHT * N * 2; t += 32) {
         const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
         const int y = y0 + r;
@@ -317,7 +433,7 @@ __device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int
     }
     // y strip: rows (k, sc) of the unit's 128 columns
     const int Ly = P.L[1];
-    if (Ly > 0) {
+    if (R.ysL == 0 && Ly > 0) {
       for (int t = lane; t < kHT * N * 2; t += 32) {
         const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
         const int y = y0 + r;
@@ -330,7 +446,7 @@ __device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int
     }
     // z strip: plane sc, rows y of the unit
     const int Lz = P.L[2];
-    const int scz = Lz > 0 ? strip_coord(k, P.nz, Lz) : -1;
+    const int scz = (R.zsL == 0 && Lz > 0) ? strip_coord(k, P.nz, Lz) : -1;
     if (scz >= 0) {
       for (int t = lane; t < kHT * N * 2; t += 32) {
         const int r = t % kHT, nu = (t / kHT) % N, ab = t / (kHT * N);
@@ -344,16 +460,15 @@ __device__ __forceinline__ void prefetch_strips(const StepParams &P, int x0, int
   }
 }
 
-// Densities at the faces of a pair, read from the staged bf16 box [2][9][136]
-// (planes k, k + 1) where the thread needs them: plane k row ly at lx .. lx+2,
-// row ly+1 at lx, lx+1; plane k+1 row ly at lx, lx+1.  Cells beyond the last
-// one along an axis take that cell's value (rho_coord of the tile kernels).
-struct FaceRho3 {
+// Values at the faces of a pair read from a staged bf16 box [2][9][136]
+// (planes k, k + 1: the density, or K): plane k row ly at lx .. lx+2, row
+// ly+1 at lx, lx+1; plane k+1 row ly at lx, lx+1.  Cells beyond the last one
+// along an axis take that cell's value (rho_coord of the tile kernels).
+struct Face3 {
   float r0, r1, r2, u0, u1, z0, z1;
 };
 template <bool EDGE>
-__device__ __forceinline__ FaceRho3 face_rho3(const StepParams &P, const bf16 *rb, int x0, int y0, int k, int lx,
-                                              int ly) {
+__device__ __forceinline__ Face3 face3(const StepParams &P, const bf16 *rb, int x0, int y0, int k, int lx, int ly) {
   int c0 = lx, c1 = lx + 1, c2 = lx + 2, r0 = ly, r1 = ly + 1, pz = 1;
   if (EDGE) {
     const int mx = P.nx - 1 - x0, my = P.ny - 1 - y0;
@@ -365,13 +480,34 @@ __device__ __forceinline__ FaceRho3 face_rho3(const StepParams &P, const bf16 *r
     if (k + 1 >= P.nz) pz = 0;
   }
   auto at = [&](int z, int r, int cc) { return __bfloat162float(rb[(z * (kHT + 1) + r) * kRWb + cc]); };
-  return FaceRho3{at(0, r0, c0), at(0, r0, c1), at(0, r0, c2), at(0, r1, c0), at(0, r1, c1),
-                  at(pz, r0, c0), at(pz, r0, c1)};
+  return Face3{at(0, r0, c0), at(0, r0, c1), at(0, r0, c2), at(0, r1, c0), at(0, r1, c1),
+               at(pz, r0, c0), at(pz, r0, c1)};
 }
 
-template <int N, bool EDGE>
-__device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, const float *ring, int x0, int y0, int k,
-                                             int tid, int xs_side, int xsL) {
+// The memory-variable update of mechanism nu on the three axes and its
+// contribution to the stretched derivatives (Eqs. relaxation4,
+// relaxation_psi), writing psi back; A[a], B[a] are the coefficients of
+// axis a, q the memory variables before the update.
+template <int N>
+__device__ __forceinline__ void relax3(const StepParams &P, float *const *psi, long long o, int i0, bool edge,
+                                       const Psi<N> &q, int nu, const float2 (&A)[3], const float2 (&B)[3],
+                                       const float2 (&D)[3], float2 (&S)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 n;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      el2(n, e) = fmaf(el2(B[a], e), el2(q[a][nu], e), el2(A[a], e) * el2(D[a], e));
+      el2(S[a], e) += fmaf(P.w_new, el2(n, e), P.w_old * el2(q[a][nu], e));
+    }
+    if (edge) n = mask_pad2(n, i0, P.nx);
+    st_state2(psi[a], o, n);
+  }
+}
+
+template <int N, bool EDGE, bool CROSS>
+__device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 &R, float *st, const float *ring,
+                                             int x0, int y0, int k, int tid, const Psi<N> &q) {
   using S = Vel3<N>;
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
@@ -384,7 +520,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, con
   constexpr int kPl = Vel3<N>::kPlane;
   const float *sp = ring + ring_slot(k) * kPl;
   const int sy = ly + 3;
-  float2 Dx, Dy, Dz;
+  float2 D[3];
   {
     const Win10 w = win10(sp + sy * kCW, lx);
 #pragma unroll
@@ -392,7 +528,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, con
       float d = 0.f;
 #pragma unroll
       for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m] - w.v[4 + e - m + 1], d);
-      el2(Dx, e) = d;
+      el2(D[0], e) = d;
     }
   }
   {
@@ -404,7 +540,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, con
       float d = 0.f;
 #pragma unroll
       for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(col[3 + m], e) - el2(col[4 - m], e), d);
-      el2(Dy, e) = d;
+      el2(D[1], e) = d;
     }
   }
   {
@@ -416,96 +552,70 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, con
       float d = 0.f;
 #pragma unroll
       for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(zc[3 + m], e) - el2(zc[4 - m], e), d);
-      el2(Dz, e) = d;
+      el2(D[2], e) = d;
+    }
+  }
+  if (CROSS) {
+    // cross taps (Sec. 3.1) over both transverse axes, in the order of the
+    // tile kernels: w row j, up / dn rows j +- 1 of plane k; zp, zm row j of
+    // planes k +- 1; zp_up, zm_up row j+1, zp_dn row j-1 of those planes
+    const float *pp = ring + ring_slot(k + 1) * kPl, *pm = ring + ring_slot(k - 1) * kPl;
+    const Win6 w = win6(sp + sy * kCW, lx), up = win6(sp + (sy + 1) * kCW, lx), dn = win6(sp + (sy - 1) * kCW, lx);
+    const Win6 zp = win6(pp + sy * kCW, lx), zm = win6(pm + sy * kCW, lx);
+    const Win6 zp_up = win6(pp + (sy + 1) * kCW, lx), zm_up = win6(pm + (sy + 1) * kCW, lx);
+    const Win6 zp_dn = win6(pp + (sy - 1) * kCW, lx);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      el2(D[0], e) = fmaf(P.g11h, (((up.v[3 + e] - up.v[2 + e]) + (dn.v[3 + e] - dn.v[2 + e])) +
+                                ((zp.v[3 + e] - zp.v[2 + e]) + (zm.v[3 + e] - zm.v[2 + e]))), el2(D[0], e));
+      el2(D[1], e) = fmaf(P.g11h, (((up.v[3 + e] - w.v[3 + e]) + (up.v[1 + e] - w.v[1 + e])) +
+                                ((zp_up.v[2 + e] - zp.v[2 + e]) + (zm_up.v[2 + e] - zm.v[2 + e]))), el2(D[1], e));
+      el2(D[2], e) = fmaf(P.g11h, (((zp.v[3 + e] - w.v[3 + e]) + (zp.v[1 + e] - w.v[1 + e])) +
+                                ((zp_up.v[2 + e] - up.v[2 + e]) + (zp_dn.v[2 + e] - dn.v[2 + e]))), el2(D[2], e));
     }
   }
   const float2 k1 = sldh2(reinterpret_cast<const bf16 *>(st + S::oK) + o);
-  float2 A[3][N > 0 ? N : 1], B[3][N > 0 ? N : 1];
+  float2 v0 = sld2(st + S::oV + o), v1 = sld2(st + S::oV + kArr + o), v2 = sld2(st + S::oV + 2 * kArr + o);
+  float2 Sd[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) el2(Sd[a], e) = el2(D[a], e) * el2(k1, e);
+  const int xside = EDGE ? R.xs_side(x0) : -1;
+  const bool ys = EDGE && R.ys_row(y0) != INT_MIN, zs = EDGE && R.zs_plane(k) >= 0;
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
     const float2 a = sldh2(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
     const float2 b = sldb2(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      A[q][nu] = a;
-      B[q][nu] = b;
-    }
+    float2 A[3] = {a, a, a}, B[3] = {b, b, b};
+    if (EDGE) strips_of<N, 1>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A, B);
+    relax3<N>(P, P.psi1, nu * Sn + c, i0, EDGE, q, nu, A, B, D, Sd);
   }
-  if (EDGE) {
-#pragma unroll
-    for (int nu = 0; nu < N; ++nu) {
-      if (xs_side >= 0)
-        strip3x_staged(P, reinterpret_cast<const bf16 *>(st + S::oXs),
-                       reinterpret_cast<const bf16 *>(st + S::oXs + XStrip<N>::kHalf), xsL, nu, i0, ly, A[0][nu],
-                       B[0][nu]);
-      else
-        strip3<0, 1>(P, nu, i0, j, k, A[0][nu], B[0][nu]);
-      strip3<1, 1>(P, nu, i0, j, k, A[1][nu], B[1][nu]);
-      strip3<2, 1>(P, nu, i0, j, k, A[2][nu], B[2][nu]);
-    }
-  }
-  float2 v0 = sld2(st + S::oV + o), v1 = sld2(st + S::oV + kArr + o), v2 = sld2(st + S::oV + 2 * kArr + o);
-  float2 S0, S1, S2;
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    el2(S0, e) = el2(Dx, e) * el2(k1, e);
-    el2(S1, e) = el2(Dy, e) * el2(k1, e);
-    el2(S2, e) = el2(Dz, e) * el2(k1, e);
-  }
-#pragma unroll
-  for (int nu = 0; nu < N; ++nu) {
-    const float2 q0 = sld2(st + S::oPsi + nu * kArr + o);
-    const float2 q1 = sld2(st + S::oPsi + (N + nu) * kArr + o);
-    const float2 q2 = sld2(st + S::oPsi + (2 * N + nu) * kArr + o);
-    float2 n0, n1, n2;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      el2(n0, e) = fmaf(el2(B[0][nu], e), el2(q0, e), el2(A[0][nu], e) * el2(Dx, e));
-      el2(n1, e) = fmaf(el2(B[1][nu], e), el2(q1, e), el2(A[1][nu], e) * el2(Dy, e));
-      el2(n2, e) = fmaf(el2(B[2][nu], e), el2(q2, e), el2(A[2][nu], e) * el2(Dz, e));
-      el2(S0, e) += fmaf(P.w_new, el2(n0, e), P.w_old * el2(q0, e));
-      el2(S1, e) += fmaf(P.w_new, el2(n1, e), P.w_old * el2(q1, e));
-      el2(S2, e) += fmaf(P.w_new, el2(n2, e), P.w_old * el2(q2, e));
-    }
-    if (EDGE) {
-      n0 = mask_pad2(n0, i0, P.nx);
-      n1 = mask_pad2(n1, i0, P.nx);
-      n2 = mask_pad2(n2, i0, P.nx);
-    }
-    st_state2(P.psi1[0], nu * Sn + c, n0);
-    st_state2(P.psi1[1], nu * Sn + c, n1);
-    st_state2(P.psi1[2], nu * Sn + c, n2);
-  }
-  const FaceRho3 f = face_rho3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), x0, y0, k, lx, ly);
+  const Face3 f = face3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), x0, y0, k, lx, ly);
   const float rr[3] = {f.r0, f.r1, f.r2}, ru[2] = {f.u0, f.u1}, rz[2] = {f.z0, f.z1};
   if (P.nl_vel) {
     // momentum factors of the literal system (Eq. general5) at the x, y, z
     // faces: p from the staged planes (zero beyond the grid), K of the cell
-    // and of its +1 neighbours from the map, clamped to the last cell
-    const bf16 *Km = static_cast<const bf16 *>(P.K);
-    const int jn = min(j + 1, P.ny - 1), kn = min(k + 1, P.nz - 1);
-    const long long row = (long long)k * P.plane + (long long)j * P.pitch;
-    const long long rowy = (long long)k * P.plane + (long long)jn * P.pitch;
-    const long long rowz = (long long)kn * P.plane + (long long)j * P.pitch;
+    // and of its +1 neighbours from the staged K box, clamped to the last cell
+    const Face3 g = face3<true>(P, reinterpret_cast<const bf16 *>(st + S::oKm), x0, y0, k, lx, ly);
+    const float Kr[3] = {g.r0, g.r1, g.r2}, Ku[2] = {g.u0, g.u1}, Kz[2] = {g.z0, g.z1};
     const float *pr = sp + sy * kCW + lx + 4, *pu = sp + (sy + 1) * kCW + lx + 4;
     const float *pz = ring + ring_slot(k + 1) * kPl + sy * kCW + lx + 4;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      const int x = min(i0 + e, P.nx - 1), xn = min(i0 + e + 1, P.nx - 1);
-      const float Kc = ldmap(Km, row + x);
-      const float fx = mom_factor(Kc, ldmap(Km, row + xn), pr[e], pr[e + 1]);
-      const float fy = mom_factor(Kc, ldmap(Km, rowy + x), pr[e], pu[e]);
-      const float fz = mom_factor(Kc, ldmap(Km, rowz + x), pr[e], pz[e]);
-      el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(S0, e), fx);
-      el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(S1, e), fy);
-      el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(S2, e), fz);
+      const float fx = mom_factor(Kr[e], Kr[e + 1], pr[e], pr[e + 1]);
+      const float fy = mom_factor(Kr[e], Ku[e], pr[e], pu[e]);
+      const float fz = mom_factor(Kr[e], Kz[e], pr[e], pz[e]);
+      el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(Sd[0], e), fx);
+      el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(Sd[1], e), fy);
+      el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(Sd[2], e), fz);
     }
   } else {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(S0, e));
-      el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(S1, e));
-      el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(S2, e));
+      el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(Sd[0], e));
+      el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(Sd[1], e));
+      el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(Sd[2], e));
     }
   }
   if (EDGE) {
@@ -518,114 +628,119 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, float *st, con
   st_state2(P.v[2], c, v2);
 }
 
-template <int N, bool EDGE>
-__device__ __forceinline__ void prs3_compute(const StepParams &P, const float *st, const float *ring, int x0, int y0,
-                                             int k, int tid, int xs_side, int xsL) {
-  using S = Prs3<N>;
+template <int N, bool EDGE, bool CROSS>
+__device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 &R, const float *st, const float *ring,
+                                             const float *sub, int x0, int y0, int k, int tid, const Psi<N> &q) {
+  using S = Prs3<N, CROSS>;
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
   const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
   const long long Sn = P.npts_alloc;
   const int o = ly * kTX + lx;
-  float2 Dx, Dy, Dz;
+  constexpr int kPl = S::kPlane;
+  const float *subx = sub, *suby = sub + kSub * S::kXPlane;
+  float2 D[3];
   {
-    const Win10 w = win10(st + S::oVx + ly * kCW, lx);
+    // v_x row j of plane k (stage rows y0 .., or ring rows y0-1 ..), columns x0-4 ..
+    const float *row = CROSS ? subx + sub_slot(k) * S::kXPlane + (ly + 1) * kCW : st + S::oVx + ly * kCW;
+    const Win10 w = win10(row, lx);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
       for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], w.v[4 + e + m - 1] - w.v[4 + e - m], d);
-      el2(Dx, e) = d;
+      el2(D[0], e) = d;
     }
   }
   {
+    // v_y rows j-4 .. j+3 of plane k
     float2 col[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) col[m] = sld2(st + S::oVy + (ly + m) * kTX + lx);
+    for (int m = 0; m < 8; ++m)
+      col[m] = CROSS ? sld2(suby + sub_slot(k) * S::kYPlane + (ly + m) * kCW + lx + 4)
+                     : sld2(st + S::oVy + (ly + m) * kTX + lx);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
       for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(col[4 + m - 1], e) - el2(col[4 - m], e), d);
-      el2(Dy, e) = d;
+      el2(D[1], e) = d;
     }
   }
   {
+    // v_z planes k-4 .. k+3 of the ring
     float2 zc[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) zc[m] = sld2(ring + ring_slot(k - 4 + m) * kArr + o);  // v_z planes k-4 ..
+    for (int m = 0; m < 8; ++m)
+      zc[m] = CROSS ? sld2(ring + ring_slot(k - 4 + m) * kPl + (ly + 1) * kCW + lx + 4)
+                    : sld2(ring + ring_slot(k - 4 + m) * kPl + o);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       float d = 0.f;
 #pragma unroll
       for (int m = 1; m <= 4; ++m) d = fmaf(P.gh[m - 1], el2(zc[4 + m - 1], e) - el2(zc[4 - m], e), d);
-      el2(Dz, e) = d;
+      el2(D[2], e) = d;
+    }
+  }
+  if (CROSS) {
+    // cross taps (Sec. 3.1) at the centres, in the order of the tile
+    // kernels: g11 sum_{t != q} sum_{s = +-1} (v_q(c + s e_t) - v_q(c - e_q + s e_t))
+    {
+      const float *xk = subx + sub_slot(k) * S::kXPlane, *xp = subx + sub_slot(k + 1) * S::kXPlane,
+                  *xm = subx + sub_slot(k - 1) * S::kXPlane;
+      const Win6 a = win6(xk + (ly + 2) * kCW, lx), b = win6(xk + ly * kCW, lx);
+      const Win6 cc = win6(xp + (ly + 1) * kCW, lx), dd = win6(xm + (ly + 1) * kCW, lx);
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+        el2(D[0], e) = fmaf(P.g11h, (((a.v[2 + e] - a.v[1 + e]) + (b.v[2 + e] - b.v[1 + e])) +
+                                  ((cc.v[2 + e] - cc.v[1 + e]) + (dd.v[2 + e] - dd.v[1 + e]))), el2(D[0], e));
+    }
+    {
+      const float *yk = suby + sub_slot(k) * S::kYPlane, *yp = suby + sub_slot(k + 1) * S::kYPlane,
+                  *ym = suby + sub_slot(k - 1) * S::kYPlane;
+      const Win6 w0 = win6(yk + (ly + 4) * kCW, lx), w1 = win6(yk + (ly + 3) * kCW, lx);
+      const Win6 zp0 = win6(yp + (ly + 4) * kCW, lx), zp1 = win6(yp + (ly + 3) * kCW, lx);
+      const Win6 zm0 = win6(ym + (ly + 4) * kCW, lx), zm1 = win6(ym + (ly + 3) * kCW, lx);
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+        el2(D[1], e) = fmaf(P.g11h, (((w0.v[3 + e] - w1.v[3 + e]) + (w0.v[1 + e] - w1.v[1 + e])) +
+                                  ((zp0.v[2 + e] - zp1.v[2 + e]) + (zm0.v[2 + e] - zm1.v[2 + e]))), el2(D[1], e));
+    }
+    {
+      const float *zk = ring + ring_slot(k) * kPl, *zk1 = ring + ring_slot(k - 1) * kPl;
+      const Win6 z0 = win6(zk + (ly + 1) * kCW, lx), z1 = win6(zk1 + (ly + 1) * kCW, lx);
+      const Win6 u0 = win6(zk + (ly + 2) * kCW, lx), u1 = win6(zk1 + (ly + 2) * kCW, lx);
+      const Win6 d0 = win6(zk + ly * kCW, lx), d1 = win6(zk1 + ly * kCW, lx);
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+        el2(D[2], e) = fmaf(P.g11h, (((z0.v[3 + e] - z1.v[3 + e]) + (z0.v[1 + e] - z1.v[1 + e])) +
+                                  ((u0.v[2 + e] - u1.v[2 + e]) + (d0.v[2 + e] - d1.v[2 + e]))), el2(D[2], e));
     }
   }
   const float2 k2 = sldh2(reinterpret_cast<const bf16 *>(st + S::oIk) + o);
   const float2 K = sldh2(reinterpret_cast<const bf16 *>(st + S::oKm) + o);
   float2 ch = make_float2(0.f, 0.f);
   if (P.nl) ch = sldh2(reinterpret_cast<const bf16 *>(st + S::oChi) + o);
-  float2 A[3][N > 0 ? N : 1], B[3][N > 0 ? N : 1];
+  float2 p = sld2(st + S::oP + o);
+  float2 Sd[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) el2(Sd[a], e) = el2(D[a], e) * el2(k2, e);
+  const int xside = EDGE ? R.xs_side(x0) : -1;
+  const bool ys = EDGE && R.ys_row(y0) != INT_MIN, zs = EDGE && R.zs_plane(k) >= 0;
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
     const float2 a = sldh2(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
     const float2 b = sldb2(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      A[q][nu] = a;
-      B[q][nu] = b;
-    }
-  }
-  if (EDGE) {
-#pragma unroll
-    for (int nu = 0; nu < N; ++nu) {
-      if (xs_side >= 0)
-        strip3x_staged(P, reinterpret_cast<const bf16 *>(st + S::oXs),
-                       reinterpret_cast<const bf16 *>(st + S::oXs + XStrip<N>::kHalf), xsL, nu, i0, ly, A[0][nu],
-                       B[0][nu]);
-      else
-        strip3<0, 2>(P, nu, i0, j, k, A[0][nu], B[0][nu]);
-      strip3<1, 2>(P, nu, i0, j, k, A[1][nu], B[1][nu]);
-      strip3<2, 2>(P, nu, i0, j, k, A[2][nu], B[2][nu]);
-    }
-  }
-  float2 p = sld2(st + S::oP + o);
-  float2 S0, S1, S2;
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    el2(S0, e) = el2(Dx, e) * el2(k2, e);
-    el2(S1, e) = el2(Dy, e) * el2(k2, e);
-    el2(S2, e) = el2(Dz, e) * el2(k2, e);
-  }
-#pragma unroll
-  for (int nu = 0; nu < N; ++nu) {
-    const float2 q0 = sld2(st + S::oPsi + nu * kArr + o);
-    const float2 q1 = sld2(st + S::oPsi + (N + nu) * kArr + o);
-    const float2 q2 = sld2(st + S::oPsi + (2 * N + nu) * kArr + o);
-    float2 n0, n1, n2;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      el2(n0, e) = fmaf(el2(B[0][nu], e), el2(q0, e), el2(A[0][nu], e) * el2(Dx, e));
-      el2(n1, e) = fmaf(el2(B[1][nu], e), el2(q1, e), el2(A[1][nu], e) * el2(Dy, e));
-      el2(n2, e) = fmaf(el2(B[2][nu], e), el2(q2, e), el2(A[2][nu], e) * el2(Dz, e));
-      el2(S0, e) += fmaf(P.w_new, el2(n0, e), P.w_old * el2(q0, e));
-      el2(S1, e) += fmaf(P.w_new, el2(n1, e), P.w_old * el2(q1, e));
-      el2(S2, e) += fmaf(P.w_new, el2(n2, e), P.w_old * el2(q2, e));
-    }
-    if (EDGE) {
-      n0 = mask_pad2(n0, i0, P.nx);
-      n1 = mask_pad2(n1, i0, P.nx);
-      n2 = mask_pad2(n2, i0, P.nx);
-    }
-    st_state2(P.psi2[0], nu * Sn + c, n0);
-    st_state2(P.psi2[1], nu * Sn + c, n1);
-    st_state2(P.psi2[2], nu * Sn + c, n2);
+    float2 A[3] = {a, a, a}, B[3] = {b, b, b};
+    if (EDGE) strips_of<N, 2>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A, B);
+    relax3<N>(P, P.psi2, nu * Sn + c, i0, EDGE, q, nu, A, B, D, Sd);
   }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    float upd = P.dt * el2(K, e) * (el2(S0, e) + el2(S1, e) + el2(S2, e));
+    float upd = P.dt * el2(K, e) * (el2(Sd[0], e) + el2(Sd[1], e) + el2(Sd[2], e));
     if (P.nl) upd /= fmaf(el2(ch, e), el2(p, e), 1.f);
     el2(p, e) -= upd;
   }
@@ -635,16 +750,17 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const float *s
 
 // One half step.  Block (32, 16), one per SM; items blockIdx.x,
 // blockIdx.x + gridDim.x, ...; within an item the units k0 .. k1-1 in order.
-template <int N, bool VEL>
+template <int N, bool VEL, bool CROSS>
 __global__ void __launch_bounds__(kThreads, 1)
     pipe3d_kernel(const StepParams P, const Region3 R, const __grid_constant__ PipeMaps T) {
-  using G = Ring3<N, VEL>;
+  using G = Ring3<N, VEL, CROSS>;
   constexpr int kStage = G::kStage;
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int ok[2];  // per stage: thread 0 never rewrites a flag a thread has yet to read
   float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float *ring = smem + 2 * kStage;
+  float *sub = ring + kSlots * G::kPlane;  // cross-tap rings of the pressure half step
   const int tid = threadIdx.y * 32 + threadIdx.x;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -659,10 +775,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   R.item(it, x0, y0, k0, k1);
   int k = k0;
   unsigned phase = 0, pending = 0;
+  const bool nl = P.nl != 0, nlv = VEL && P.nl_vel != 0;
   if (tid == 0)
-    issue3<N, VEL>(T, smem, ring, &bar[0], x0, y0, k, ring_first<VEL>(k), ring_first<VEL>(k) + 7, P.nl != 0,
-                   R.xs_side(x0), R.xsL);
+    issue3<N, VEL, CROSS>(T, R, smem, ring, sub, &bar[0], x0, y0, k, ring_first<VEL>(k), ring_first<VEL>(k) + 7,
+                          k - 1, k + 1, nl, nlv);
   pending |= 1u;
+  // this thread's memory variables, one unit ahead of the compute
+  const int lx = 2 * (tid & 63), ly = tid >> 6;
+  float *const *psi = VEL ? P.psi1 : P.psi2;
+  auto psi_of = [&](int ux0, int uy0, int uk, Psi<N> &q) {
+    const int i0 = ux0 + lx, j = uy0 + ly;
+    load_psi<N>(psi, P.npts_alloc, (long long)uk * P.plane + (long long)j * P.pitch + i0, i0 < P.nx && j < P.ny,
+                q);
+  };
+  Psi<N> qc, qn;
+  psi_of(x0, y0, k, qc);
   int s = 0;
 #pragma unroll 1
   while (true) {
@@ -691,53 +818,57 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (tid < 32) {
         const int kp = ring_first<VEL>(nk) + 7;
         if (tid == 0)
-          issue3<N, VEL>(T, smem + q * kStage, ring, &bar[q], nx0, ny0, nk, kp, kp, P.nl != 0, R.xs_side(nx0),
-                         R.xsL);
-        if (!R.interior(nx0, ny0, nk)) prefetch_strips<N, VEL ? 1 : 2>(P, nx0, ny0, nk, tid, R.xsL > 0);
+          issue3<N, VEL, CROSS>(T, R, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk, kp, kp, nk + 1, nk + 1,
+                                nl, nlv);
+        if (!R.interior(nx0, ny0, nk)) prefetch_strips<N, VEL ? 1 : 2>(P, R, nx0, ny0, nk, tid);
       }
       pending |= 1u << q;
     }
+    if (more) psi_of(nx0, ny0, nk, qn);
     float *cur = smem + s * kStage;
     if (R.interior(x0, y0, k)) {
-      if (VEL) vel3_compute<N, false>(P, cur, ring, x0, y0, k, tid, -1, 0);
-      else prs3_compute<N, false>(P, cur, ring, x0, y0, k, tid, -1, 0);
+      if (VEL) vel3_compute<N, false, CROSS>(P, R, cur, ring, x0, y0, k, tid, qc);
+      else prs3_compute<N, false, CROSS>(P, R, cur, ring, sub, x0, y0, k, tid, qc);
     } else {
-      const int xside = R.xs_side(x0);
-      if (VEL) vel3_compute<N, true>(P, cur, ring, x0, y0, k, tid, xside, R.xsL);
-      else prs3_compute<N, true>(P, cur, ring, x0, y0, k, tid, xside, R.xsL);
+      if (VEL) vel3_compute<N, true, CROSS>(P, R, cur, ring, x0, y0, k, tid, qc);
+      else prs3_compute<N, true, CROSS>(P, R, cur, ring, sub, x0, y0, k, tid, qc);
     }
     if (!more) break;
-    if (fresh) {  // a new column: all eight ring planes, once every thread is done with the ring
+    if (fresh) {  // a new column: all ring planes, once every thread is done with the rings
       __syncthreads();
       if (tid == 0)
-        issue3<N, VEL>(T, smem + q * kStage, ring, &bar[q], nx0, ny0, nk, ring_first<VEL>(nk),
-                       ring_first<VEL>(nk) + 7, P.nl != 0, R.xs_side(nx0), R.xsL);
+        issue3<N, VEL, CROSS>(T, R, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk, ring_first<VEL>(nk),
+                              ring_first<VEL>(nk) + 7, nk - 1, nk + 1, nl, nlv);
       pending |= 1u << q;
     }
     it = nit;
     x0 = nx0; y0 = ny0; k0 = nk0; k1 = nk1; k = nk;
     s = q;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int nu = 0; nu < N; ++nu) qc[a][nu] = qn[a][nu];
   }
 }
 
-template <int N, bool VEL>
+template <int N, bool VEL, bool CROSS>
 cudaError_t pipe3_launch(const StepParams &P, const Region3 &R, int grid, const PipeMaps &T, cudaStream_t st) {
-  constexpr size_t bytes = Ring3<N, VEL>::kBytes;
-  static_assert(bytes <= 227 * 1024, "stages exceed shared memory");
+  constexpr size_t bytes = Ring3<N, VEL, CROSS>::kBytes;
+  static_assert(bytes + 64 <= 227 * 1024, "stages exceed shared memory");
   cudaError_t e =
-      cudaFuncSetAttribute(pipe3d_kernel<N, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      cudaFuncSetAttribute(pipe3d_kernel<N, VEL, CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pipe3d_kernel<N, VEL><<<grid, dim3(32, kThreads / 32), bytes, st>>>(P, R, T);
+  pipe3d_kernel<N, VEL, CROSS><<<grid, dim3(32, kThreads / 32), bytes, st>>>(P, R, T);
   return cudaGetLastError();
 }
 
-template <bool VEL>
+template <bool VEL, bool CROSS>
 cudaError_t pipe3_dispatch(const StepParams &P, const Region3 &R, int grid, const PipeMaps &T, cudaStream_t st) {
   switch (P.n_relax) {
-    case 0: return pipe3_launch<0, VEL>(P, R, grid, T, st);
-    case 1: return pipe3_launch<1, VEL>(P, R, grid, T, st);
-    case 2: return pipe3_launch<2, VEL>(P, R, grid, T, st);
-    case 3: return pipe3_launch<3, VEL>(P, R, grid, T, st);
+    case 0: return pipe3_launch<0, VEL, CROSS>(P, R, grid, T, st);
+    case 1: return pipe3_launch<1, VEL, CROSS>(P, R, grid, T, st);
+    case 2: return pipe3_launch<2, VEL, CROSS>(P, R, grid, T, st);
+    case 3: return pipe3_launch<3, VEL, CROSS>(P, R, grid, T, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -747,7 +878,19 @@ cudaError_t pipe3_dispatch(const StepParams &P, const Region3 &R, int grid, cons
 // most kXsMax), and no unit reaches both sides (nx >= 128 + L).
 bool x_strip_staged(const StepParams &P) {
   const int L = P.L[0];
-  return P.n_relax > 0 && L > 0 && L % 8 == 0 && L <= kXsMax && P.nx >= kTX + L && P.sa1[0] != nullptr;
+  return P.n_relax > 0 && L > 0 && L % 8 == 0 && L <= kXsMax && P.nx >= kTX + L && P.ny >= kHT &&
+         P.sa1[0] != nullptr;
+}
+// The y strip's by TMA when no unit reaches both sides (ny >= 2L + 8) and
+// the strip holds at least a unit's rows; the z strip's always (a unit is
+// one plane).
+bool y_strip_staged(const StepParams &P) {
+  const int L = P.L[1];
+  return P.n_relax > 0 && L >= kHT / 2 && P.ny >= 2 * L + kHT && P.sa1[1] != nullptr;
+}
+bool z_strip_staged(const StepParams &P) {
+  const int L = P.L[2];
+  return P.n_relax > 0 && L > 0 && P.ny >= kHT && P.sa1[2] != nullptr;
 }
 
 // Planes per item: the split of each column into items that minimises the
@@ -764,6 +907,8 @@ Region3 region3_of(const StepParams &P, int grid) {
   R.tnx = (P.nx + kTX - 1) / kTX;
   R.nhy = (P.ny + kHT - 1) / kHT;
   R.xsL = x_strip_staged(P) ? P.L[0] : 0;
+  R.ysL = y_strip_staged(P) ? P.L[1] : 0;
+  R.zsL = z_strip_staged(P) ? P.L[2] : 0;
   const long long ncols = (long long)R.tnx * R.nhy;
   double best = 1e300;
   R.seglen = P.nz;
@@ -786,43 +931,48 @@ Region3 region3_of(const StepParams &P, int grid) {
 }  // namespace
 
 bool pipe3d_supported(const StepParams &P, int map_kind) {
-  // bf16 maps (two stages of ~107 KB fit); N <= 3 keeps the 4D boxes and
-  // the stage within shared memory; no periodic axis; the cross taps are
-  // left to the tile kernels
+  // bf16 maps; N <= 3 keeps the 4D boxes and the stages within shared
+  // memory; no periodic axis
   return P.nz > 1 && map_kind == 1 && P.n_relax >= 0 && P.n_relax <= 3 && !P.periodic[0] && !P.periodic[1] &&
-         !P.periodic[2] && P.g11h == 0.f;
+         !P.periodic[2];
 }
 
 cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why) {
   *vel = PipeMaps{};
   *prs = PipeMaps{};
   const int N = P.n_relax;
+  const bool cross = P.g11h != 0.f;
   using ull = unsigned long long;
   const ull nx = P.nx, ny = P.ny, nz = P.nz, S = P.npts_alloc;
   const ull f3[2] = {(ull)P.pitch * 4, (ull)P.plane * 4}, h3[2] = {(ull)P.pitch * 2, (ull)P.plane * 2};
   const ull f4[3] = {(ull)P.pitch * 4, (ull)P.plane * 4, S * 4}, h4[3] = {(ull)P.pitch * 2, (ull)P.plane * 2, S * 2};
   const ull d3[3] = {nx, ny, nz};
-  const ull dv[4] = {nx, ny, nz, 3}, dpsi[4] = {nx, ny, nz, (ull)(3 * N)}, dab[4] = {nx, ny, nz, (ull)N};
-  const unsigned halo[3] = {kCW, kHT + 7, 1}, rho[3] = {kRWb, kHT + 1, 2},
-                 one[3] = {kTX, kHT, 1}, v4[4] = {kTX, kHT, 1, 3}, psi4[4] = {kTX, kHT, 1, (unsigned)(3 * N)},
-                 ab4[4] = {kTX, kHT, 1, (unsigned)N}, vx[3] = {kCW, kHT, 1}, vy[3] = {kTX, kHT + 7, 1};
+  const ull dv[4] = {nx, ny, nz, 3}, dab[4] = {nx, ny, nz, (ull)N};
+  const unsigned halo[3] = {kCW, kHT + 7, 1}, rho[3] = {kRWb, kHT + 1, 2}, one[3] = {kTX, kHT, 1},
+                 v4[4] = {kTX, kHT, 1, 3}, ab4[4] = {kTX, kHT, 1, (unsigned)N}, vx[3] = {kCW, kHT, 1},
+                 vy[3] = {kTX, kHT + 7, 1}, halo1[3] = {kCW, kHT + 2, 1};
   bool ok = true;
   // velocity half step
   ok = ok && encode_tensor_map(&vel->m[0], P.p, 4, 3, d3, f3, halo);
   ok = ok && encode_tensor_map(&vel->m[2], P.rho, 2, 3, d3, h3, rho);
   ok = ok && encode_tensor_map(&vel->m[3], P.v[0], 4, 4, dv, f4, v4);
-  if (N > 0) ok = ok && encode_tensor_map(&vel->m[4], P.psi1[0], 4, 4, dpsi, f4, psi4);
   ok = ok && encode_tensor_map(&vel->m[5], P.ik1, 2, 3, d3, h3, one);
   if (N > 0) {
     ok = ok && encode_tensor_map(&vel->m[6], P.a1, 2, 4, dab, h4, ab4);
     ok = ok && encode_tensor_map(&vel->m[7], P.b1, 2, 4, dab, h4, ab4);
   }
+  if (P.nl_vel) ok = ok && encode_tensor_map(&vel->m[12], P.K, 2, 3, d3, h3, rho);
   // pressure half step
-  ok = ok && encode_tensor_map(&prs->m[0], P.v[0], 4, 3, d3, f3, vx);
-  ok = ok && encode_tensor_map(&prs->m[1], P.v[1], 4, 3, d3, f3, vy);
-  ok = ok && encode_tensor_map(&prs->m[2], P.v[2], 4, 3, d3, f3, one);
+  if (cross) {
+    ok = ok && encode_tensor_map(&prs->m[0], P.v[0], 4, 3, d3, f3, halo1);
+    ok = ok && encode_tensor_map(&prs->m[1], P.v[1], 4, 3, d3, f3, halo);
+    ok = ok && encode_tensor_map(&prs->m[2], P.v[2], 4, 3, d3, f3, halo1);
+  } else {
+    ok = ok && encode_tensor_map(&prs->m[0], P.v[0], 4, 3, d3, f3, vx);
+    ok = ok && encode_tensor_map(&prs->m[1], P.v[1], 4, 3, d3, f3, vy);
+    ok = ok && encode_tensor_map(&prs->m[2], P.v[2], 4, 3, d3, f3, one);
+  }
   ok = ok && encode_tensor_map(&prs->m[3], P.p, 4, 3, d3, f3, one);
-  if (N > 0) ok = ok && encode_tensor_map(&prs->m[4], P.psi2[0], 4, 4, dpsi, f4, psi4);
   ok = ok && encode_tensor_map(&prs->m[5], P.ik2, 2, 3, d3, h3, one);
   ok = ok && encode_tensor_map(&prs->m[6], P.K, 2, 3, d3, h3, one);
   if (P.nl) ok = ok && encode_tensor_map(&prs->m[7], P.chi, 2, 3, d3, h3, one);
@@ -839,6 +989,24 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
     ok = ok && encode_tensor_map(&prs->m[10], P.sa2[0], 2, 4, dxs, sxs, bxs);
     ok = ok && encode_tensor_map(&prs->m[11], P.sb2[0], 2, 4, dxs, sxs, bxs);
   }
+  if (y_strip_staged(P)) {  // y strips [N][z][2L][x] bf16, boxes 128 x 8 x 1 x N
+    const ull L = (ull)P.L[1];
+    const ull dys[4] = {nx, 2 * L, nz, (ull)N},
+              sys[3] = {(ull)P.pitch * 2, 2 * L * (ull)P.pitch * 2, (ull)P.strip_nu[1] * 2};
+    ok = ok && encode_tensor_map(&vel->m[13], P.sa1[1], 2, 4, dys, sys, ab4);
+    ok = ok && encode_tensor_map(&vel->m[14], P.sb1[1], 2, 4, dys, sys, ab4);
+    ok = ok && encode_tensor_map(&prs->m[13], P.sa2[1], 2, 4, dys, sys, ab4);
+    ok = ok && encode_tensor_map(&prs->m[14], P.sb2[1], 2, 4, dys, sys, ab4);
+  }
+  if (z_strip_staged(P)) {  // z strips [N][2L][y][x] bf16, boxes 128 x 8 x 1 x N
+    const ull L = (ull)P.L[2];
+    const ull dzs[4] = {nx, ny, 2 * L, (ull)N},
+              szs[3] = {(ull)P.pitch * 2, ny * (ull)P.pitch * 2, (ull)P.strip_nu[2] * 2};
+    ok = ok && encode_tensor_map(&vel->m[15], P.sa1[2], 2, 4, dzs, szs, ab4);
+    ok = ok && encode_tensor_map(&vel->m[16], P.sb1[2], 2, 4, dzs, szs, ab4);
+    ok = ok && encode_tensor_map(&prs->m[15], P.sa2[2], 2, 4, dzs, szs, ab4);
+    ok = ok && encode_tensor_map(&prs->m[16], P.sb2[2], 2, 4, dzs, szs, ab4);
+  }
   if (!ok) {
     *why = "cuTensorMapEncodeTiled rejected a 3D map (or the driver entry point is missing)";
     return cudaErrorInvalidValue;
@@ -848,7 +1016,9 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
 
 cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t st) {
   const Region3 R = region3_of(P, grid);
-  return vel ? pipe3_dispatch<true>(P, R, grid, T, st) : pipe3_dispatch<false>(P, R, grid, T, st);
+  if (P.g11h != 0.f)
+    return vel ? pipe3_dispatch<true, true>(P, R, grid, T, st) : pipe3_dispatch<false, true>(P, R, grid, T, st);
+  return vel ? pipe3_dispatch<true, false>(P, R, grid, T, st) : pipe3_dispatch<false, false>(P, R, grid, T, st);
 }
 
 }  // namespace fw2

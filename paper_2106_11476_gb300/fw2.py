@@ -23,7 +23,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 BC = {"zero": 0, "periodic": 1}
 NL = {"off": 0, "pressure": 1, "westervelt": 2, "literal": 3}
 MAP = {"f32": 0, "bf16": 1, "idx": 2}
-PML_READING = {"A": 0, "C": 2}
+PML_READING = {"A": 0, "C": 2, "K": 3}
 MEM_ALIGN = {"centred": 0, "endpoint": 1}
 SRC_KIND = {"p": 0, "vx": 1, "vy": 2, "vz": 3}
 FIELD = {"p": 0, "vx": 1, "vy": 2, "vz": 3, "psi1x": 4, "psi1y": 5, "psi1z": 6,
@@ -63,6 +63,7 @@ EXPORTS = {
                              C.c_int64, C.c_int32]),
     "fw2_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "fw2_destroy": (C.c_int, [C.c_void_p]),
+    "fw2_set_watch": (C.c_int, [C.c_void_p, C.c_int64, C.c_float]),
     "fw2_get_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "fw2_get_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "fw2_set_step": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -86,6 +87,7 @@ EXPORTS = {
     "fw2_batch_synchronize": (C.c_int, [C.c_void_p]),
     "fw2_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "fw2_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "fw2_batch_set_watch": (C.c_int, [C.c_void_p, C.c_int64, C.c_float]),
     "fw2_batch_destroy": (C.c_int, [C.c_void_p]),
     "fw2_last_error": (C.c_char_p, [C.c_void_p]),
     "fw2_abi_version": (C.c_int32, []),
@@ -225,6 +227,12 @@ def fw2_get_dt(ctx) -> float:
     v = C.c_double()
     _check(lib().fw2_get_dt(ctx, C.byref(v)), ctx)
     return v.value
+
+
+def fw2_set_watch(ctx, every: int, bound: float):
+    """Scan p every `every` steps inside fw2_step and stop with EUNSTABLE
+    beyond `bound` (fw2_set_watch; every = 0 switches it off)."""
+    _check(lib().fw2_set_watch(ctx, int(every), float(bound)), ctx)
 
 
 def fw2_get_step(ctx) -> int:
@@ -378,6 +386,11 @@ def fw2_batch_info(batch):
     g, o, n = C.c_int32(), C.c_int32(), C.c_int64()
     _bcheck(lib().fw2_batch_info(batch, C.byref(g), C.byref(o), C.byref(n)), batch)
     return g.value, o.value, n.value
+
+
+def fw2_batch_set_watch(batch, every: int, bound: float):
+    """Scan every context's p every `every` batch steps (fw2_batch_set_watch)."""
+    _bcheck(lib().fw2_batch_set_watch(batch, int(every), float(bound)), batch)
 
 
 def fw2_batch_destroy(batch):

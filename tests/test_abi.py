@@ -62,7 +62,7 @@ def test_abi_version(fw2lib):
     ({"ndim": 3, "n": (64, 64, 64), "map_precision": 2}, fw2.EUNSUPPORTED),
     ({"map_precision": 3}, fw2.EINVAL),
     ({"pml_reading": 1}, fw2.EINVAL),                                      # withdrawn reading
-    ({"pml_reading": 3}, fw2.EINVAL),
+    ({"pml_reading": 4}, fw2.EINVAL),
 ])
 def test_create_rejects_bad_configs(fw2lib, patch, status):
     cfg = fw2.fw2_config_init()

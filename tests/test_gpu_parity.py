@@ -269,8 +269,8 @@ def test_parity_3d(fw2):
 def test_parity_3d_time_space_taps(fw2, maps):
     """The 3D time-space optimised operator (Sec. 3.1; cross taps over both
     transverse axes, library taps for a 3D grid at the problem's Courant
-    number) against the oracle with the same taps; the pipelined 3D half
-    steps leave the cross taps to the tile kernels."""
+    number) against the oracle with the same taps: float maps on the tile
+    kernels, bf16 maps on the pipelined half steps."""
     prob = small_3d(n=(70, 40, 36), steps=80)
     r = float(np.max(prob.c)) * prob.dt / prob.h
     prob.taps = tuple(fw2.fw2_taps_time_space(r, 3))
@@ -278,7 +278,7 @@ def test_parity_3d_time_space_taps(fw2, maps):
     compare_run(fw2, prob, 80, maps=maps, kernel_path="pipe" if maps == "bf16" else "auto")
     sim = fw2.Simulation(prob, map_precision="bf16", kernel_path="pipe")
     sim.step(1)
-    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    assert fw2.fw2_kernel_path(sim.ctx) == "pipe"
     sim.close()
 
 
@@ -329,6 +329,30 @@ def test_pipelined_3d_equals_tile_path_bitwise(fw2, N, nl):
     _pipe_vs_tile(fw2, prob, 40, maps="bf16")
 
 
+@pytest.mark.parametrize("N,nl", [(0, "off"), (3, "westervelt"), (2, "literal"), (3, "literal")])
+def test_pipelined_3d_cross_taps_equal_tile_path_bitwise(fw2, N, nl):
+    """The time-space taps (g11 != 0) on the pipelined 3D half steps: the
+    velocity cross taps come from the operand ring's planes k +- 1, the
+    pressure ones from the v_x, v_y rings and the haloed v_z ring; bitwise
+    what the tile kernels compute, with and without the literal system."""
+    prob = small_3d(n=(300, 70, 45), N=N, nl=nl, steps=40)
+    r = float(np.max(prob.c)) * prob.dt / prob.h
+    prob.taps = tuple(fw2.fw2_taps_time_space(r, 3))
+    if nl == "literal":
+        for s_ in prob.sources:
+            if s_.kind == "p":
+                s_.signal = s_.signal * 20
+    _pipe_vs_tile(fw2, prob, 40, maps="bf16")
+
+
+def test_pipelined_3d_cross_taps_from_random_state_equal_tile_path_bitwise(fw2):
+    """Cross taps on a ragged grid from a random state, every field nonzero
+    from the start (halo rows and planes at every edge carry values)."""
+    prob = small_3d(n=(200, 45, 30), N=2, nl="pressure", steps=20)
+    prob.taps = tuple(fw2.fw2_taps_time_space(0.35, 3))
+    _pipe_vs_tile(fw2, prob, 20, maps="bf16", state=synth.random_state(prob, seed=21))
+
+
 def test_pipelined_3d_x_strip_loaded_per_cell_equals_tile_path_bitwise(fw2):
     """A C-PML of 7 cells: the x strip's coefficient rows are not 16-byte
     multiples, so edge units read them per cell instead of by TMA."""
@@ -337,13 +361,15 @@ def test_pipelined_3d_x_strip_loaded_per_cell_equals_tile_path_bitwise(fw2):
 
 
 @pytest.mark.parametrize("shape,pml", [((100, 40, 20), (6, 2)), ((264, 30, 18), (6, 2)), ((200, 24, 17), (3, 1)),
-                                       ((300, 36, 8), (1, 1))])
+                                       ((300, 36, 8), (1, 1)), ((200, 20, 20), (6, 2))])
 def test_pipelined_3d_small_grids_equal_tile_path_bitwise(fw2, shape, pml):
     """Grids at the limits of the 3D pipeline from a random state: one x tile
     reaching both x strips (nx < 128 + L: the strip read per cell), a ragged
     last x tile holding the whole high strip (staged), a strip that is not a
-    16-byte row (per cell), and the fewest planes a grid may have, eight
-    (most ring planes outside the grid)."""
+    16-byte row (per cell; a y strip of 4 rows, staged), the fewest planes a
+    grid may have, eight (most ring planes outside the grid; y strips of 2
+    rows, read per cell), and units reaching both y strips (ny < 2 L + 8:
+    read per cell)."""
     rng = np.random.default_rng(11)
     h = 1e-4
     prob = synth.homogeneous(shape, h, 0.0, relax=synth.relaxation_sets()["N2_y1.0_a0.5"])
@@ -475,6 +501,7 @@ def _pipe_vs_tile(fw2, prob, steps, maps="f32", state=None):
         if state is not None:
             sim.set_state(state)
         sim.step(steps)
+        assert fw2.fw2_kernel_path(sim.ctx) == path
         out[path] = ({n: sim.field(n) for n in state_names(prob)},
                      sim.trace.cpu().numpy() if sim.trace is not None else None)
         sim.close()
