@@ -257,6 +257,68 @@ const char *fw2_batch_last_error(const fw2_batch *b);
 fw2_status fw2_batch_set_watch(fw2_batch *b, int64_t every, float bound);
 fw2_status fw2_batch_destroy(fw2_batch *b);
 
+/* ---- relaxation fitting (Sec. 4.1) -------------------------------------- */
+
+/* Relaxation parameters that make the multiple-relaxation model follow a
+ * power law: host computation in FP64, no device needed.  The model's
+ * attenuation and phase velocity come from Eq. (dispersion_relations); the
+ * cost is Eq. (relaxation_parameter_optimization),
+ *   J = w_alpha NMSE(alpha_model, alpha_target) + (1 - w_alpha) NMSE(c_model, c_target),
+ * NMSE = mean squared error over the variance of the target, on n_freq
+ * uniform samples of [f_lo, f_hi]; the target is alpha0 f^y (dB/cm, f in MHz)
+ * and its Kramers-Kronig phase velocity in the nearly-local form,
+ * 1/c = 1/c0 + a0 tan(pi y / 2) (w^(y-1) - w_ref^(y-1)) (y = 1: 1/c0 -
+ * (2 / pi) a0 ln(w / w_ref)), which equals c0 at f_ref.  The paper leaves
+ * f_ref unstated; the default is the centre of the band, where Table 2's
+ * own parameters score J = 0.024 (at 3 MHz they would score 2.2).
+ * The search is the paper's: a grid of grid_points values per dimension
+ * over the bounds (kappa linear, d and alpha in log10), then `refinements`
+ * finer grids centred on the best point so far, each range narrower by
+ * `shrink` (grid values beyond a bound move onto it), followed by an optional
+ * Nelder-Mead polish in the same coordinates.  grid_points^(2 + 4N)
+ * evaluations per grid (9.8e6 for N = 2 and 5 points) are spread over
+ * `threads` host threads. */
+#define FW2_FIT_MAX_RELAX 4
+typedef struct {
+  double alpha0;              /* attenuation coefficient [dB/cm/MHz^y] */
+  double y;                   /* power-law exponent, 0 < y < 3 */
+  int32_t n_relax;            /* N mechanisms, 1 .. FW2_FIT_MAX_RELAX */
+  double c0;                  /* phase velocity at f_ref [m/s] */
+  double f_ref;               /* Kramers-Kronig reference [Hz]; <= 0: band centre */
+  double f_lo, f_hi;          /* fitted band [Hz] (default 1 - 20 MHz, Sec. 4.1) */
+  int32_t n_freq;             /* uniform samples of the band (default 77) */
+  double w_alpha;             /* weight of the attenuation term (default 0.1) */
+  double kappa_bounds[2];     /* Table 2 bounds (default 0.8 - 1.2) */
+  double log_d_bounds[2];     /* log10 of the d bounds [1/s] (default 2 - 10) */
+  double log_alpha_bounds[2]; /* log10 of the alpha bounds [1/s] (default 5 - 12) */
+  int32_t grid_points;        /* values per dimension of each grid (default 5) */
+  int32_t refinements;        /* finer grids after the first (default 4) */
+  double shrink;              /* range reduction per finer grid (default 0.3) */
+  int32_t polish_iterations;  /* Nelder-Mead iterations after the grid (default 20000; 0: none) */
+  int32_t threads;            /* host threads (0: all) */
+} fw2_fit_request;
+typedef struct {
+  double kappa1, kappa2;      /* fitted parameters, the layout of fw2_relax_desc */
+  double d1[FW2_FIT_MAX_RELAX], alpha1[FW2_FIT_MAX_RELAX];  /* [1/s] */
+  double d2[FW2_FIT_MAX_RELAX], alpha2[FW2_FIT_MAX_RELAX];
+  double J;                   /* cost of the result */
+  double J_grid;              /* cost after the grid search, before the polish */
+  double f_ref;               /* reference frequency used [Hz] */
+  double max_att_rel_err;     /* max |alpha_model / alpha_target - 1| from 2 MHz up */
+  double max_phase_rel_err;   /* max |c_model / c_target - 1| over the band */
+  int64_t evaluations;        /* cost evaluations */
+} fw2_fit_result;
+/* Defaults above (alpha0 0.5, y 1, N 2, c0 1540: Table 2's target). */
+fw2_status fw2_fit_request_init(fw2_fit_request *req);
+/* Run the search.  EINVAL for arguments out of range or a grid of more than
+ * 2e9 points; EUNSTABLE when no grid point has a finite cost. */
+fw2_status fw2_fit_relaxation(const fw2_fit_request *req, fw2_fit_result *out);
+/* Attenuation [dB/cm] and phase velocity [m/s] of a parameter set (the
+ * first n_relax mechanisms of p) at n frequencies [Hz], from Eq.
+ * (dispersion_relations) with c0 the sound speed of the medium. */
+fw2_status fw2_relaxation_curves(const fw2_fit_result *p, int32_t n_relax, double c0, const double *freqs,
+                                 int64_t n, double *att_db_cm, double *c);
+
 /* ---- helpers ---------------------------------------------------------- */
 
 /* Time step in use (builds the coefficient maps if needed). */

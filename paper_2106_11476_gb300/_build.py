@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfw2.so")
-SOURCES = ["api.cu", "prep.cu", "aux.cu", "step2d.cu", "step2d_pipe.cu", "step3d.cu", "step3d_pipe.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "prep.cu", "aux.cu", "step2d.cu", "step2d_pipe.cu", "step3d.cu", "step3d_pipe.cu", "noalloc.cu", "batch.cu",
+           "fit.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

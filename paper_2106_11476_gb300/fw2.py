@@ -45,6 +45,25 @@ class Config(C.Structure):
                 ("bc", C.c_int32 * 3), ("kernel_path", C.c_int32), ("stream", C.c_void_p)]
 
 
+FIT_MAX_RELAX = 4
+
+
+class FitRequest(C.Structure):
+    _fields_ = [("alpha0", C.c_double), ("y", C.c_double), ("n_relax", C.c_int32), ("c0", C.c_double),
+                ("f_ref", C.c_double), ("f_lo", C.c_double), ("f_hi", C.c_double), ("n_freq", C.c_int32),
+                ("w_alpha", C.c_double), ("kappa_bounds", C.c_double * 2), ("log_d_bounds", C.c_double * 2),
+                ("log_alpha_bounds", C.c_double * 2), ("grid_points", C.c_int32), ("refinements", C.c_int32),
+                ("shrink", C.c_double), ("polish_iterations", C.c_int32), ("threads", C.c_int32)]
+
+
+class FitResult(C.Structure):
+    _fields_ = [("kappa1", C.c_double), ("kappa2", C.c_double), ("d1", C.c_double * FIT_MAX_RELAX),
+                ("alpha1", C.c_double * FIT_MAX_RELAX), ("d2", C.c_double * FIT_MAX_RELAX),
+                ("alpha2", C.c_double * FIT_MAX_RELAX), ("J", C.c_double), ("J_grid", C.c_double),
+                ("f_ref", C.c_double), ("max_att_rel_err", C.c_double), ("max_phase_rel_err", C.c_double),
+                ("evaluations", C.c_int64)]
+
+
 class RelaxDesc(C.Structure):
     _fields_ = [("kappa1", C.c_void_p), ("kappa2", C.c_void_p), ("d1", C.c_void_p), ("alpha1", C.c_void_p),
                 ("d2", C.c_void_p), ("alpha2", C.c_void_p), ("mem_space", C.c_int32)]
@@ -91,6 +110,10 @@ EXPORTS = {
     "fw2_batch_destroy": (C.c_int, [C.c_void_p]),
     "fw2_last_error": (C.c_char_p, [C.c_void_p]),
     "fw2_abi_version": (C.c_int32, []),
+    "fw2_fit_request_init": (C.c_int, [C.POINTER(FitRequest)]),
+    "fw2_fit_relaxation": (C.c_int, [C.POINTER(FitRequest), C.POINTER(FitResult)]),
+    "fw2_relaxation_curves": (C.c_int, [C.POINTER(FitResult), C.c_int32, C.c_double, C.c_void_p, C.c_int64,
+                                        C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -353,6 +376,46 @@ def fw2_field_absmax_noalloc(field, row_len: int, n_rows: int, row_pitch: int, o
         stream = torch.cuda.current_stream(field.device).cuda_stream
     return lib().fw2_field_absmax_noalloc(C.c_void_p(field.data_ptr()), row_len, n_rows, row_pitch,
                                           C.c_void_p(out.data_ptr()), C.c_void_p(stream if stream else 0))
+
+
+def fw2_fit_relaxation(alpha0: float, y: float, n_relax: int, **options) -> dict:
+    """Relaxation parameters for a power-law tissue (fw2_fit_relaxation, Sec.
+    4.1).  Keyword options are fields of fw2_fit_request (c0, f_ref, f_lo,
+    f_hi, n_freq, w_alpha, grid_points, refinements, shrink,
+    polish_iterations, threads, and the bounds as 2-tuples).  Returns the
+    parameter set in the layout of a relaxation description (kappa1,
+    kappa2, d1, alpha1, d2, alpha2) with the cost and the errors."""
+    req = FitRequest()
+    _check(lib().fw2_fit_request_init(C.byref(req)))
+    req.alpha0, req.y, req.n_relax = float(alpha0), float(y), int(n_relax)
+    for k, v in options.items():
+        if k.endswith("_bounds"):
+            getattr(req, k)[0], getattr(req, k)[1] = float(v[0]), float(v[1])
+        else:
+            setattr(req, k, v)
+    res = FitResult()
+    _check(lib().fw2_fit_relaxation(C.byref(req), C.byref(res)))
+    N = int(n_relax)
+    return {"kappa1": res.kappa1, "kappa2": res.kappa2, "d1": list(res.d1[:N]), "alpha1": list(res.alpha1[:N]),
+            "d2": list(res.d2[:N]), "alpha2": list(res.alpha2[:N]), "J": res.J, "J_grid": res.J_grid,
+            "f_ref": res.f_ref, "max_att_rel_err_2_20MHz": res.max_att_rel_err,
+            "max_phase_rel_err": res.max_phase_rel_err, "evaluations": res.evaluations}
+
+
+def fw2_relaxation_curves(params: dict, c0: float, freqs) -> tuple:
+    """(attenuation dB/cm, phase velocity m/s) of a parameter set at freqs [Hz]
+    (fw2_relaxation_curves)."""
+    N = len(params["d1"])
+    res = FitResult()
+    res.kappa1, res.kappa2 = float(params["kappa1"]), float(params["kappa2"])
+    for n in range(N):
+        res.d1[n], res.alpha1[n] = float(params["d1"][n]), float(params["alpha1"][n])
+        res.d2[n], res.alpha2[n] = float(params["d2"][n]), float(params["alpha2"][n])
+    f = np.ascontiguousarray(freqs, np.float64)
+    att, c = np.empty_like(f), np.empty_like(f)
+    _check(lib().fw2_relaxation_curves(C.byref(res), N, float(c0), f.ctypes.data, f.size, att.ctypes.data,
+                                       c.ctypes.data))
+    return att, c
 
 
 def _bcheck(status: int, batch):
