@@ -239,8 +239,18 @@ typedef struct fw2_batch fw2_batch;
  * after changing a context's sources or recording.  EUNSUPPORTED for 3D. */
 fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out);
 /* Advance every context by n_steps (each from its own step counter), on the
- * batch's own stream after the contexts' streams have drained; asynchronous. */
+ * batch's own stream after the contexts' streams have drained; asynchronous
+ * except where the set of active contexts changes (see budgets). */
 fw2_status fw2_batch_step(fw2_batch *b, int64_t n_steps);
+/* Step budgets: context i leaves the batch once its step counter reaches
+ * last_step[i] (< 0: no budget; NULL clears every budget).  fw2_batch_step
+ * then advances each context by at most what its budget leaves; when a
+ * context leaves, the launch tables are rebuilt for those that remain, so
+ * finished contexts cost nothing (the transmit events of a sequence, or
+ * served requests, of uneven lengths). */
+fw2_status fw2_batch_set_budget(fw2_batch *b, const int64_t *last_step);
+/* Number of contexts still short of their budget. */
+fw2_status fw2_batch_active(fw2_batch *b, int32_t *n_active);
 fw2_status fw2_batch_synchronize(fw2_batch *b);
 /* Tuned persistent grid (0 before tuning), tile order (0 context-major,
  * 1 interleaved) and kernel launches (graph replays count their kernels once

@@ -10,6 +10,7 @@
 // steps is captured once as a CUDA graph and replayed.  Each context computes
 // exactly what fw2_step computes for it alone (same tile arithmetic).
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -100,13 +101,15 @@ struct Group {
 
 struct fw2_batch {
   std::vector<fw2_ctx *> ctxs;
+  std::vector<int> active;          // contexts (indices into ctxs) the tables cover
+  std::vector<long long> budget;    // step count at which each context leaves (LLONG_MAX: none)
+  std::vector<void *> table_allocs; // device tables of the active set, rebuilt when it changes
   std::vector<Group> groups;
   cudaStream_t stream = nullptr;
   BatchCtx *d_ctx = nullptr;
   long long *d_step = nullptr;
   int *d_prefix[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // source kinds 0..3, record
   int total[5] = {0, 0, 0, 0, 0};
-  std::vector<void *> allocs;
   std::string err = "no error";
   // launch configuration: persistent grid and tile order, tuned online
   int grid = 0, order = 0;
@@ -147,7 +150,7 @@ fw2_status bupload(fw2_batch *b, const std::vector<T> &v, T **out) {
   const size_t bytes = std::max<size_t>(sizeof(T) * v.size(), 16);
   cudaError_t e = cudaMalloc(&m, bytes);
   if (e != cudaSuccess) return bfail(b, FW2_ENOMEM, "batch allocation", e);
-  b->allocs.push_back(m);
+  b->table_allocs.push_back(m);
   if (!v.empty()) {
     e = cudaMemcpy(m, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bfail(b, FW2_ECUDA, "batch upload", e);
@@ -156,9 +159,9 @@ fw2_status bupload(fw2_batch *b, const std::vector<T> &v, T **out) {
   return FW2_OK;
 }
 
-// one time step of every context (launch sequence of the file header)
+// one time step of every active context (launch sequence of the file header)
 fw2_status enqueue_step(fw2_batch *b, int grid, int order) {
-  const int n_ctx = (int)b->ctxs.size();
+  const int n_ctx = (int)b->active.size();
   for (int half = 0; half < 2; ++half) {
     const bool vel = half == 0;
     for (Group &g : b->groups) {
@@ -192,39 +195,30 @@ fw2_status enqueue_step(fw2_batch *b, int grid, int order) {
   return FW2_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out) {
-  if (!out) return FW2_EINVAL;
-  *out = nullptr;
-  if (!ctxs || n_ctx < 1) return FW2_EINVAL;
-  fw2_batch *b = new (std::nothrow) fw2_batch();
-  if (!b) return FW2_ENOMEM;
-  for (int i = 0; i < n_ctx; ++i) {
-    fw2_ctx *c = ctxs[i];
-    if (!c || c->nd != 2) {
-      fw2_status st = c ? ctx_fail(c, FW2_EUNSUPPORTED, "batches hold 2D contexts") : FW2_EINVAL;
-      delete b;
-      return st;
-    }
-    fw2_status st = ctx_prepare(c);
-    if (st != FW2_OK) {
-      delete b;
-      return st;
-    }
-    b->ctxs.push_back(c);
+// Device tables of the active contexts: per group (mechanism count, map
+// kind) the step parameters, tile tables (context-major and interleaved)
+// and, for the pipelined form, the unit table and tensor maps; the source,
+// recording and step-counter arrays of all active contexts.  Replaces the
+// previous tables (and the captured graph, which points into them).
+fw2_status build_tables(fw2_batch *b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = 0;
   }
-  b->n_sm = b->ctxs[0]->n_sm;
-  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-  if (e != cudaSuccess) {
-    delete b;
-    return FW2_ECUDA;
+  cudaStreamSynchronize(b->stream);
+  for (void *m : b->table_allocs) cudaFree(m);
+  b->table_allocs.clear();
+  b->groups.clear();
+  b->d_ctx = nullptr;
+  b->d_step = nullptr;
+  for (int k = 0; k < 5; ++k) {
+    b->d_prefix[k] = nullptr;
+    b->total[k] = 0;
   }
-  // groups by (mechanism count, map kind)
-  for (int i = 0; i < n_ctx; ++i) {
-    fw2_ctx *c = b->ctxs[i];
+  // groups by (mechanism count, map kind); members index b->active
+  for (int i = 0; i < (int)b->active.size(); ++i) {
+    fw2_ctx *c = b->ctxs[b->active[i]];
     auto it = std::find_if(b->groups.begin(), b->groups.end(),
                            [&](const Group &g) { return g.n_relax == c->N && g.map_kind == c->map_kind; });
     if (it == b->groups.end()) {
@@ -238,7 +232,7 @@ fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out
     std::vector<StepParams> params;
     std::vector<std::vector<int4>> per;
     for (int m = 0; m < (int)g.members.size(); ++m) {
-      fw2_ctx *c = b->ctxs[g.members[m]];
+      fw2_ctx *c = b->ctxs[b->active[g.members[m]]];
       params.push_back(c->P);
       std::vector<int4> t;
       for (int y0 = 0; y0 < c->ny; y0 += kTY)
@@ -284,7 +278,8 @@ fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out
     std::vector<BatchCtx> bc;
     std::vector<int> prefix[5];
     for (int k = 0; k < 5; ++k) prefix[k].push_back(0);
-    for (fw2_ctx *c : b->ctxs) {
+    for (int i : b->active) {
+      fw2_ctx *c = b->ctxs[i];
       BatchCtx x{};
       x.p = c->p;
       for (int q = 0; q < 3; ++q) x.v[q] = c->v[q];
@@ -310,11 +305,47 @@ fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out
       b->total[k] = prefix[k].back();
       st = bupload(b, prefix[k], &b->d_prefix[k]);
     }
-    std::vector<long long> steps(b->ctxs.size(), 0);
+    std::vector<long long> steps(b->active.size(), 0);
     if (st == FW2_OK) st = bupload(b, steps, &b->d_step);
   }
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out) {
+  if (!out) return FW2_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n_ctx < 1) return FW2_EINVAL;
+  fw2_batch *b = new (std::nothrow) fw2_batch();
+  if (!b) return FW2_ENOMEM;
+  for (int i = 0; i < n_ctx; ++i) {
+    fw2_ctx *c = ctxs[i];
+    if (!c || c->nd != 2) {
+      fw2_status st = c ? ctx_fail(c, FW2_EUNSUPPORTED, "batches hold 2D contexts") : FW2_EINVAL;
+      delete b;
+      return st;
+    }
+    fw2_status st = ctx_prepare(c);
+    if (st != FW2_OK) {
+      delete b;
+      return st;
+    }
+    b->ctxs.push_back(c);
+  }
+  b->n_sm = b->ctxs[0]->n_sm;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return FW2_ECUDA;
+  }
+  b->budget.assign(b->ctxs.size(), LLONG_MAX);
+  for (int i = 0; i < n_ctx; ++i) b->active.push_back(i);
+  fw2_status st = build_tables(b);
   if (st != FW2_OK) {
-    for (void *m : b->allocs) cudaFree(m);
+    for (void *m : b->table_allocs) cudaFree(m);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return st;
@@ -424,7 +455,7 @@ fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
 // the first context that holds a non-finite value or exceeds the bound.
 fw2_status batch_scan(fw2_batch *b) {
   std::vector<unsigned int> bits(b->ctxs.size(), 0u);
-  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+  for (int i : b->active) {
     fw2_ctx *c = b->ctxs[i];
     BCK(b, cudaMemsetAsync(c->d_absmax, 0, sizeof(unsigned int), b->stream));
     BCK(b, launch_absmax(c->p, c->nx, c->pitch, (long long)c->ny * c->nz, c->d_absmax, b->stream));
@@ -432,12 +463,12 @@ fw2_status batch_scan(fw2_batch *b) {
     BCK(b, cudaMemcpyAsync(&bits[i], c->d_absmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream));
   }
   BCK(b, cudaStreamSynchronize(b->stream));
-  for (size_t i = 0; i < bits.size(); ++i) {
+  for (int i : b->active) {
     float m;
     std::memcpy(&m, &bits[i], 4);
     if (!(m <= b->watch_bound)) {
       char msg[200];
-      std::snprintf(msg, sizeof msg, "context %zu blew up by batch step %lld: max |p| = %g exceeds the watch bound %g",
+      std::snprintf(msg, sizeof msg, "context %d blew up by batch step %lld: max |p| = %g exceeds the watch bound %g",
                     i, b->steps_done, (double)m, (double)b->watch_bound);
       return bfail(b, FW2_EUNSTABLE, msg);
     }
@@ -467,21 +498,52 @@ extern "C" {
 fw2_status fw2_batch_step(fw2_batch *b, int64_t n_steps) {
   if (!b) return FW2_EINVAL;
   if (n_steps < 0) return bfail(b, FW2_EINVAL, "negative step count");
-  if (n_steps == 0) return FW2_OK;
   // work already queued on the contexts' own streams comes first
-  std::vector<long long> steps;
-  for (fw2_ctx *c : b->ctxs) {
-    BCK(b, cudaStreamSynchronize(c->stream));
-    steps.push_back(c->step);
+  for (fw2_ctx *c : b->ctxs) BCK(b, cudaStreamSynchronize(c->stream));
+  int64_t total = 0;
+  while (total < n_steps) {
+    // the contexts still short of their budget; the tables follow that set
+    std::vector<int> act;
+    int64_t seg = n_steps - total;
+    for (int i = 0; i < (int)b->ctxs.size(); ++i)
+      if (b->ctxs[i]->step < b->budget[i]) {
+        act.push_back(i);
+        seg = std::min<int64_t>(seg, b->budget[i] - b->ctxs[i]->step);
+      }
+    if (act.empty()) break;
+    if (act != b->active) {
+      b->active = act;
+      const fw2_status st = build_tables(b);
+      if (st != FW2_OK) return st;
+    }
+    std::vector<long long> steps;
+    for (int i : b->active) steps.push_back(b->ctxs[i]->step);
+    BCK(b, cudaMemcpyAsync(b->d_step, steps.data(), sizeof(long long) * steps.size(), cudaMemcpyHostToDevice,
+                           b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    int64_t done = 0;
+    const fw2_status st = batch_advance(b, seg, &done);
+    // the steps enqueued before a failure still advance the contexts
+    for (int i : b->active) b->ctxs[i]->step += done;
+    total += done;
+    if (st != FW2_OK) return st;
   }
-  BCK(b, cudaMemcpyAsync(b->d_step, steps.data(), sizeof(long long) * steps.size(), cudaMemcpyHostToDevice,
-                         b->stream));
-  BCK(b, cudaStreamSynchronize(b->stream));
-  int64_t done = 0;
-  const fw2_status st = batch_advance(b, n_steps, &done);
-  // the steps enqueued before a failure still advance the contexts
-  for (fw2_ctx *c : b->ctxs) c->step += done;
-  return st;
+  return FW2_OK;
+}
+
+fw2_status fw2_batch_set_budget(fw2_batch *b, const int64_t *last_step) {
+  if (!b) return FW2_EINVAL;
+  for (size_t i = 0; i < b->ctxs.size(); ++i)
+    b->budget[i] = (last_step && last_step[i] >= 0) ? (long long)last_step[i] : LLONG_MAX;
+  return FW2_OK;
+}
+
+fw2_status fw2_batch_active(fw2_batch *b, int32_t *n_active) {
+  if (!b || !n_active) return FW2_EINVAL;
+  int32_t n = 0;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) n += b->ctxs[i]->step < b->budget[i] ? 1 : 0;
+  *n_active = n;
+  return FW2_OK;
 }
 
 fw2_status fw2_batch_set_watch(fw2_batch *b, int64_t every, float bound) {
@@ -513,7 +575,7 @@ fw2_status fw2_batch_destroy(fw2_batch *b) {
   if (!b) return FW2_OK;
   cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (void *m : b->allocs) cudaFree(m);
+  for (void *m : b->table_allocs) cudaFree(m);
   cudaStreamDestroy(b->stream);
   delete b;
   return FW2_OK;

@@ -107,6 +107,8 @@ EXPORTS = {
     "fw2_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "fw2_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "fw2_batch_set_watch": (C.c_int, [C.c_void_p, C.c_int64, C.c_float]),
+    "fw2_batch_set_budget": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fw2_batch_active": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "fw2_batch_destroy": (C.c_int, [C.c_void_p]),
     "fw2_last_error": (C.c_char_p, [C.c_void_p]),
     "fw2_abi_version": (C.c_int32, []),
@@ -454,6 +456,23 @@ def fw2_batch_info(batch):
 def fw2_batch_set_watch(batch, every: int, bound: float):
     """Scan every context's p every `every` batch steps (fw2_batch_set_watch)."""
     _bcheck(lib().fw2_batch_set_watch(batch, int(every), float(bound)), batch)
+
+
+def fw2_batch_set_budget(batch, last_steps):
+    """Step count at which each context leaves the batch (fw2_batch_set_budget;
+    None clears, a negative entry means no budget)."""
+    if last_steps is None:
+        _bcheck(lib().fw2_batch_set_budget(batch, None), batch)
+        return
+    arr = np.ascontiguousarray(last_steps, np.int64)
+    _bcheck(lib().fw2_batch_set_budget(batch, arr.ctypes.data), batch)
+
+
+def fw2_batch_active(batch) -> int:
+    """Contexts still short of their budget (fw2_batch_active)."""
+    n = C.c_int32()
+    _bcheck(lib().fw2_batch_active(batch, C.byref(n)), batch)
+    return n.value
 
 
 def fw2_batch_destroy(batch):

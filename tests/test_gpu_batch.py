@@ -81,7 +81,7 @@ def test_batch_full_size_equals_each_context_alone(fw2):
     what they hold when stepped alone."""
     import types
     import bench
-    probs = bench.batch_problems(types.SimpleNamespace(warmup=8, steps=8), 0)
+    probs, _ = bench.batch_problems(types.SimpleNamespace(warmup=8, steps=8), 0)
     steps = 16
     sims = [fw2.Simulation(p, map_precision="idx") for p in probs]
     batch = fw2.fw2_batch_create([s.ctx for s in sims])
@@ -101,3 +101,37 @@ def test_batch_full_size_equals_each_context_alone(fw2):
         np.testing.assert_array_equal(got[i][1], s.field("vy"))
         np.testing.assert_array_equal(got[i][2], s.trace.cpu().numpy()[:steps])
         s.close()
+
+
+def test_batch_budgets_let_contexts_leave_and_equal_each_context_alone(fw2):
+    """Uneven step budgets: every context stops at its own budget (the batch
+    rebuilds its launch tables as contexts leave) and holds bitwise what it
+    holds when stepped alone for that many steps."""
+    probs = _problems()
+    budgets = [40, 95, 17, 70, 95, 33, 60, 81]
+    alone = []
+    for (maps, p), n in zip(probs, budgets):
+        s = fw2.Simulation(p, map_precision=maps)
+        s.step(n)
+        alone.append((s.field("p"), s.field("vy"), s.trace.cpu().numpy()[:n]))
+        s.close()
+    sims = [fw2.Simulation(p, map_precision=maps) for maps, p in probs]
+    batch = fw2.fw2_batch_create([s.ctx for s in sims])
+    try:
+        fw2.fw2_batch_set_budget(batch, budgets)
+        assert fw2.fw2_batch_active(batch) == len(sims)
+        fw2.fw2_batch_step(batch, 50)
+        fw2.fw2_batch_synchronize(batch)
+        assert fw2.fw2_batch_active(batch) == sum(b > 50 for b in budgets)
+        fw2.fw2_batch_step(batch, 1000)
+        fw2.fw2_batch_synchronize(batch)
+        assert fw2.fw2_batch_active(batch) == 0
+        for s, n, (p_ref, vy_ref, tr_ref) in zip(sims, budgets, alone):
+            assert fw2.fw2_get_step(s.ctx) == n
+            np.testing.assert_array_equal(s.field("p"), p_ref)
+            np.testing.assert_array_equal(s.field("vy"), vy_ref)
+            np.testing.assert_array_equal(s.trace.cpu().numpy()[:n], tr_ref)
+    finally:
+        fw2.fw2_batch_destroy(batch)
+        for s in sims:
+            s.close()
