@@ -99,8 +99,15 @@ enum { FW2_MEM_CENTRED = 0, FW2_MEM_ENDPOINT = 1 };
  * every tile through shared memory with TMA copies, where they apply (2D
  * float or tissue-index maps; 3D bf16 maps with N <= 3, g_{1,1} cross taps
  * and the literal system included; no periodic axis), and TILE elsewhere;
- * AUTO (default) is PIPE */
-enum { FW2_PATH_AUTO = 0, FW2_PATH_TILE = 1, FW2_PATH_PIPE = 2 };
+ * AUTO (default) is PIPE.  The 3D pipelined half steps have two layouts:
+ * the memory variables staged in shared memory with the other arrays, or
+ * loaded into registers one unit ahead, which leaves room to stage every
+ * C-PML strip (faster where edge units dominate); the cross taps and the
+ * literal system's velocity half step take the register layout only.  PIPE
+ * and AUTO time both on a context's first four steps and keep the faster
+ * per half step (fw2_pipe_layout reports the choice); PIPE_STAGED and
+ * PIPE_REGISTERS fix one (where it applies). */
+enum { FW2_PATH_AUTO = 0, FW2_PATH_TILE = 1, FW2_PATH_PIPE = 2, FW2_PATH_PIPE_STAGED = 3, FW2_PATH_PIPE_REGISTERS = 4 };
 enum { FW2_SRC_P = 0, FW2_SRC_VX = 1, FW2_SRC_VY = 2, FW2_SRC_VZ = 3 };
 enum {
   FW2_FIELD_P = 0, FW2_FIELD_VX = 1, FW2_FIELD_VY = 2, FW2_FIELD_VZ = 3,
@@ -129,7 +136,7 @@ typedef struct {
   int32_t nl_mode;       /* FW2_NL_* */
   int32_t mem_alignment; /* FW2_MEM_CENTRED (default) or FW2_MEM_ENDPOINT */
   int32_t bc[3];         /* FW2_BC_* per axis */
-  int32_t kernel_path;   /* FW2_PATH_AUTO (default), FW2_PATH_TILE or FW2_PATH_PIPE */
+  int32_t kernel_path;   /* FW2_PATH_* (default AUTO) */
   void *stream;          /* cudaStream_t, borrowed; NULL = default stream */
 } fw2_config;
 
@@ -399,6 +406,10 @@ fw2_status fw2_selftest_bounded_wait(int64_t limit_ns, int32_t *timed_out);
  * are built (first fw2_step): FW2_PATH_TILE or FW2_PATH_PIPE; FW2_PATH_AUTO
  * before the first step. */
 fw2_status fw2_kernel_path(fw2_ctx *ctx, int32_t *path);
+/* Layout of the 3D pipelined velocity and pressure half steps: 1 memory
+ * variables staged, 2 in registers, 0 before the choice (or not a 3D
+ * pipelined context). */
+fw2_status fw2_pipe_layout(fw2_ctx *ctx, int32_t *vel, int32_t *prs);
 /* Bytes of device memory held by the context. */
 fw2_status fw2_device_bytes(fw2_ctx *ctx, int64_t *bytes);
 /* Launches of library kernels since creation (all kinds). */

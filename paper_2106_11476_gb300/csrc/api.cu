@@ -227,11 +227,17 @@ fw2_status finalize(fw2_ctx *c) {
   P.tissue = Q.tissue_out;
   P.table = Q.table_out;
   P.status = c->d_status;
+  const bool forced_pipe = cfg.kernel_path >= FW2_PATH_PIPE;
   if (c->nd == 2)
     c->pipe = (cfg.kernel_path == FW2_PATH_AUTO && pipe2d_preferred(P, c->map_kind)) ||
-              (cfg.kernel_path == FW2_PATH_PIPE && pipe2d_supported(P, c->map_kind));
+              (forced_pipe && pipe2d_supported(P, c->map_kind));
   else
     c->pipe = cfg.kernel_path != FW2_PATH_TILE && pipe3d_supported(P, c->map_kind);
+  if (c->nd == 3 && c->pipe && (cfg.kernel_path == FW2_PATH_PIPE_STAGED || cfg.kernel_path == FW2_PATH_PIPE_REGISTERS)) {
+    const int l = cfg.kernel_path == FW2_PATH_PIPE_STAGED ? kLayoutStaged : kLayoutRegisters;
+    c->layout3[0] = pipe3d_layout_allowed(true, P, l) ? l : kLayoutRegisters;
+    c->layout3[1] = pipe3d_layout_allowed(false, P, l) ? l : kLayoutRegisters;
+  }
   if (c->pipe) {
     const char *why = "";
     const cudaError_t e = c->nd == 2 ? build_pipe2d_maps(P, c->map_kind, &c->tm_vel, &c->tm_prs, &why)
@@ -358,19 +364,47 @@ fw2_status ctx_prepare(fw2_ctx *c) {
 }
 fw2_status ctx_fail(fw2_ctx *c, fw2_status s, const char *msg) { return fail(c, s, "%s", msg); }
 
+// Layout of the 3D pipelined half steps for the next step: the tuned one,
+// or during the first four steps of a context the trial one (two steps per
+// layout, the second timed); *timed tells whether to time this step.
+int layout_for_step(fw2_ctx *c, bool *timed) {
+  *timed = false;
+  if (c->nd != 3 || !c->pipe || c->layout3[0] != 0) return -1;
+  const bool choice = pipe3d_layout_allowed(true, c->P, kLayoutStaged) ||
+                      pipe3d_layout_allowed(false, c->P, kLayoutStaged);
+  if (!choice) {  // only the register layout applies
+    c->layout3[0] = c->layout3[1] = kLayoutRegisters;
+    return -1;
+  }
+  const int t = c->layout_trial;
+  *timed = t == 1 || t == 3;
+  return t < 2 ? kLayoutStaged : kLayoutRegisters;
+}
+
 // Enqueue every launch of time step n (Sec. 3.1 order): velocity half step,
 // velocity sources, pressure half step, pressure sources, recording.
 fw2_status enqueue_step(fw2_ctx *c, long long n) {
   const StepParams &P = c->P;
+  bool trial_timed = false;
+  const int trial = layout_for_step(c, &trial_timed);
+  auto lay = [&](bool vel) {
+    const int l = trial > 0 ? trial : c->layout3[vel ? 0 : 1];
+    return pipe3d_layout_allowed(vel, P, l) ? l : kLayoutRegisters;
+  };
+  cudaEvent_t te[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (trial_timed)
+    for (auto &e : te) CK(c, cudaEventCreate(&e));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->profiling) {
     ev = {take_event(c), take_event(c)};
     CK(c, cudaEventRecord(ev.first, c->stream));
   }
+  if (trial_timed) CK(c, cudaEventRecord(te[0], c->stream));
   CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->tm_vel, c->stream)
-                              : launch_pipe3d(true, P, c->n_sm, c->tm_vel, c->stream))
+                              : launch_pipe3d(true, P, c->n_sm, c->tm_vel, c->stream, lay(true)))
                 : c->nd == 2 ? launch_vel2d(P, c->map_kind, c->stream) : launch_vel3d(P, c->map_kind, c->stream));
   c->launches++;
+  if (trial_timed) CK(c, cudaEventRecord(te[1], c->stream));
   if (c->profiling) {
     CK(c, cudaEventRecord(ev.second, c->stream));
     c->ev_vel.push_back(ev);
@@ -385,10 +419,12 @@ fw2_status enqueue_step(fw2_ctx *c, long long n) {
     }
   }
   if (c->profiling) CK(c, cudaEventRecord(ev.first, c->stream));
+  if (trial_timed) CK(c, cudaEventRecord(te[2], c->stream));
   CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->tm_prs, c->stream)
-                              : launch_pipe3d(false, P, c->n_sm, c->tm_prs, c->stream))
+                              : launch_pipe3d(false, P, c->n_sm, c->tm_prs, c->stream, lay(false)))
                 : c->nd == 2 ? launch_prs2d(P, c->map_kind, c->stream) : launch_prs3d(P, c->map_kind, c->stream));
   c->launches++;
+  if (trial_timed) CK(c, cudaEventRecord(te[3], c->stream));
   if (c->profiling) {
     CK(c, cudaEventRecord(ev.second, c->stream));
     c->ev_prs.push_back(ev);
@@ -401,6 +437,23 @@ fw2_status enqueue_step(fw2_ctx *c, long long n) {
   if (c->rec_groups > 0 && n < c->rec_steps) {
     CK(c, launch_record(c->p, c->rec_cell, c->rec_off, c->rec_groups, c->rec_out + n * c->rec_groups, c->stream));
     c->launches++;
+  }
+  if (trial > 0) {
+    if (trial_timed) {
+      CK(c, cudaEventSynchronize(te[3]));
+      float mv = 0.f, mp = 0.f;
+      CK(c, cudaEventElapsedTime(&mv, te[0], te[1]));
+      CK(c, cudaEventElapsedTime(&mp, te[2], te[3]));
+      c->layout_ms[trial - 1][0] = mv;
+      c->layout_ms[trial - 1][1] = mp;
+      for (auto e : te) cudaEventDestroy(e);
+    }
+    if (++c->layout_trial == 4)
+      for (int h = 0; h < 2; ++h) {
+        const bool vel = h == 0;
+        const bool both = pipe3d_layout_allowed(vel, P, kLayoutStaged);
+        c->layout3[h] = both && c->layout_ms[0][h] <= c->layout_ms[1][h] ? kLayoutStaged : kLayoutRegisters;
+      }
   }
   return FW2_OK;
 }
@@ -526,7 +579,7 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
   if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_LITERAL) return fail(nullptr, FW2_EINVAL, "bad nl_mode");
   if (cfg.mem_alignment != FW2_MEM_CENTRED && cfg.mem_alignment != FW2_MEM_ENDPOINT)
     return fail(nullptr, FW2_EINVAL, "bad mem_alignment");
-  if (cfg.kernel_path != FW2_PATH_AUTO && cfg.kernel_path != FW2_PATH_TILE && cfg.kernel_path != FW2_PATH_PIPE)
+  if (cfg.kernel_path < FW2_PATH_AUTO || cfg.kernel_path > FW2_PATH_PIPE_REGISTERS)
     return fail(nullptr, FW2_EINVAL, "bad kernel_path");
   for (int q = 0; q < 3; ++q)
     if (cfg.bc[q] != FW2_BC_ZERO && cfg.bc[q] != FW2_BC_PERIODIC) return fail(nullptr, FW2_EINVAL, "bad bc[%d]", q);
@@ -805,6 +858,13 @@ fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
                     (long long)c->step, m, c->watch_bound);
     }
   }
+  return FW2_OK;
+}
+
+fw2_status fw2_pipe_layout(fw2_ctx *c, int32_t *vel, int32_t *prs) {
+  if (!c || !vel || !prs) return FW2_EINVAL;
+  *vel = c->layout3[0];
+  *prs = c->layout3[1];
   return FW2_OK;
 }
 

@@ -80,6 +80,11 @@ struct fw2_ctx {
   long long step = 0, launches = 0;
   // optional per-kernel event timing
   bool profiling = false;
+  // 3D pipelined layout per half step (velocity, pressure), chosen by timing
+  // both on the first steps: 0 until then, else kLayoutStaged / kLayoutRegisters
+  int layout3[2] = {0, 0};
+  int layout_trial = 0;
+  float layout_ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [layout - 1][half]
   // in-loop blow-up detection: scan p every watch_every steps (0: off)
   long long watch_every = 0;
   float watch_bound = 0.f;

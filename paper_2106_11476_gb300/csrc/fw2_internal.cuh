@@ -133,10 +133,18 @@ constexpr int kPipeHalf = 8;  // rows of a pipelined half tile
 bool pipe2d_interior_half(const StepParams &P, int x0, int y0);
 cudaError_t launch_pipe2d_batched(bool vel, const StepParams *Ps, const PipeMaps *Ts, const int4 *units,
                                   int n_units, int n_relax, int map_kind, int grid, cudaStream_t s);
-// persistent pipelined 3D half step (bf16 maps, N <= 3, no periodic axis)
+// persistent pipelined 3D half step (bf16 maps, N <= 3, no periodic axis),
+// in one of two layouts that compute the same result: the memory variables
+// staged in shared memory with the other arrays (kLayoutStaged; not with
+// cross taps, nor for the literal system's velocity half step), or loaded
+// into registers one unit ahead with every C-PML strip staged
+// (kLayoutRegisters); kLayoutDefault takes the staged one where it applies
+constexpr int kLayoutDefault = 0, kLayoutStaged = 1, kLayoutRegisters = 2;
 bool pipe3d_supported(const StepParams &P, int map_kind);
+bool pipe3d_layout_allowed(bool vel, const StepParams &P, int layout);
 cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why);
-cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t s);
+cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t s,
+                          int layout = kLayoutDefault);
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
 

@@ -60,50 +60,56 @@ __host__ __device__ constexpr int sub_slot(int k) { return ((k % kSub) + kSub) %
 
 // C-PML strip coefficients of a stage (bf16): x strip a then b, each
 // [N][8][L] (L <= kXsMax); y strip a, b and z strip a, b, each [N][8][128]
-template <int N>
+// (not in the layout that stages the memory variables, PS)
+template <int N, bool PS>
 struct Strips {
-  static constexpr int kX = N * kHT * kXsMax / 2;  // floats of the x strip's a (or b)
-  static constexpr int kYZ = N * kArr / 2;         // floats of a y or z strip's a (or b)
+  static constexpr int kX = N * kHT * kXsMax / 2;    // floats of the x strip's a (or b)
+  static constexpr int kYZ = PS ? 0 : N * kArr / 2;  // floats of a y or z strip's a (or b)
   static constexpr int oXa = 0, oXb = kX, oYa = 2 * kX, oYb = oYa + kYZ, oZa = oYb + kYZ, oZb = oZa + kYZ;
   static constexpr int kFloats = oZb + kYZ;
 };
 
 // velocity stage: density bf16 [2][9][136] (planes k, k+1), v [3][8][128],
-// 1/kappa1 bf16 [8][128], a1, b1 bf16 [N][8][128], K bf16 [2][9][136]
-// (literal system), strips; plane ring: p planes [15][136] (rows y0-3 ..
-// y0+11, columns x0-4 ..)
-template <int N>
+// 1/kappa1 bf16 [8][128], a1, b1 bf16 [N][8][128], then either (PS) the 3N
+// memory variables [3N][8][128] and the x strip, or K bf16 [2][9][136]
+// (literal system) and the strips of all axes; plane ring: p planes
+// [15][136] (rows y0-3 .. y0+11, columns x0-4 ..)
+template <int N, bool PS>
 struct Vel3 {
   static constexpr int kRho = round32(fl(2 * (kHT + 1) * kRWb * 2));
   static constexpr int kV = 3 * kArr;
   static constexpr int kK = round32(fl(kArr * 2));
   static constexpr int kAB = round32(fl(N * kArr * 2));
-  static constexpr int oRho = 0, oV = oRho + kRho, oK = oV + kV, oA = oK + kK, oB = oA + kAB, oKm = oB + kAB,
-                       oS = oKm + kRho;
-  static constexpr int kFloats = round32(oS + Strips<N>::kFloats);
-  static constexpr unsigned kBytes = 4u * kV + 2u * (2 * (kHT + 1) * kRWb + kArr + 2 * N * kArr);
+  static constexpr int kPsi = PS ? 3 * N * kArr : 0;
+  static constexpr int kKmF = PS ? 0 : kRho;
+  static constexpr int oRho = 0, oV = oRho + kRho, oK = oV + kV, oA = oK + kK, oB = oA + kAB, oPsi = oB + kAB,
+                       oKm = oPsi + kPsi, oS = oKm + kKmF;
+  static constexpr int kFloats = round32(oS + Strips<N, PS>::kFloats);
+  static constexpr unsigned kBytes = 4u * (kV + kPsi) + 2u * (2 * (kHT + 1) * kRWb + kArr + 2 * N * kArr);
   static constexpr unsigned kKmBytes = 2u * 2 * (kHT + 1) * kRWb;
   static constexpr int kPlane = round32((kHT + 7) * kCW);
   static constexpr unsigned kPlaneBytes = 4u * (kHT + 7) * kCW;
 };
 
 // pressure stage: p [8][128], 1/kappa2, K, chi bf16 [8][128], a2, b2 bf16
-// [N][8][128], strips; without cross taps also v_x [8][136] (x halo) and v_y
-// [15][128] (rows y0-4 ..), with the plane ring of v_z [8][128]; with cross
-// taps the rings hold v_z [10][136] (rows y0-1 .., columns x0-4 ..), v_x
-// [10][136] (rows y0-1 ..) and v_y [15][136] (rows y0-4 ..)
-template <int N, bool CROSS>
+// [N][8][128], then either (PS) the 3N memory variables and the x strip or
+// the strips of all axes; without cross taps also v_x [8][136] (x halo) and
+// v_y [15][128] (rows y0-4 ..), with the plane ring of v_z [8][128]; with
+// cross taps (never PS) the rings hold v_z [10][136] (rows y0-1 .., columns
+// x0-4 ..), v_x [10][136] (rows y0-1 ..) and v_y [15][136] (rows y0-4 ..)
+template <int N, bool CROSS, bool PS>
 struct Prs3 {
   static constexpr int kVx = CROSS ? 0 : round32(kHT * kCW);
   static constexpr int kVy = CROSS ? 0 : round32((kHT + 7) * kTX);
   static constexpr int kP = kArr;
   static constexpr int kK = round32(fl(kArr * 2));
   static constexpr int kAB = round32(fl(N * kArr * 2));
+  static constexpr int kPsi = PS ? 3 * N * kArr : 0;
   static constexpr int oVx = 0, oVy = oVx + kVx, oP = oVy + kVy, oIk = oP + kP, oKm = oIk + kK, oChi = oKm + kK,
-                       oA = oChi + kK, oB = oA + kAB, oS = oB + kAB;
-  static constexpr int kFloats = round32(oS + Strips<N>::kFloats);
+                       oA = oChi + kK, oB = oA + kAB, oPsi = oB + kAB, oS = oPsi + kPsi;
+  static constexpr int kFloats = round32(oS + Strips<N, PS>::kFloats);
   static constexpr unsigned kBytesNoChi =
-      4u * (CROSS ? kP : kHT * kCW + (kHT + 7) * kTX + kP) + 2u * (2 * kArr + 2 * N * kArr);
+      4u * ((CROSS ? kP : kHT * kCW + (kHT + 7) * kTX + kP) + kPsi) + 2u * (2 * kArr + 2 * N * kArr);
   // v_z ring slot; with cross taps also the v_x and v_y ring slots
   static constexpr int kPlane = CROSS ? round32((kHT + 2) * kCW) : kArr;
   static constexpr unsigned kPlaneBytes = 4u * (CROSS ? (kHT + 2) * kCW : kArr);
@@ -113,13 +119,13 @@ struct Prs3 {
   static constexpr unsigned kYPlaneBytes = 4u * (kHT + 7) * kCW;
 };
 
-template <int N, bool VEL, bool CROSS>
+template <int N, bool VEL, bool CROSS, bool PS>
 struct Ring3 {
-  static constexpr int kStage = VEL ? Vel3<N>::kFloats : Prs3<N, CROSS>::kFloats;
-  static constexpr int kPlane = VEL ? Vel3<N>::kPlane : Prs3<N, CROSS>::kPlane;
-  static constexpr unsigned kPlaneBytes = VEL ? Vel3<N>::kPlaneBytes : Prs3<N, CROSS>::kPlaneBytes;
+  static constexpr int kStage = VEL ? Vel3<N, PS>::kFloats : Prs3<N, CROSS, PS>::kFloats;
+  static constexpr int kPlane = VEL ? Vel3<N, PS>::kPlane : Prs3<N, CROSS, PS>::kPlane;
+  static constexpr unsigned kPlaneBytes = VEL ? Vel3<N, PS>::kPlaneBytes : Prs3<N, CROSS, PS>::kPlaneBytes;
   static constexpr int kSubFloats =
-      (!VEL && CROSS) ? kSub * (Prs3<N, CROSS>::kXPlane + Prs3<N, CROSS>::kYPlane) : 0;
+      (!VEL && CROSS) ? kSub * (Prs3<N, CROSS, PS>::kXPlane + Prs3<N, CROSS, PS>::kYPlane) : 0;
   static constexpr size_t kBytes =
       sizeof(float) * (2 * (size_t)kStage + (size_t)kSlots * kPlane + (size_t)kSubFloats) + 128;
 };
@@ -171,12 +177,12 @@ __host__ __device__ constexpr int ring_first(int k) { return VEL ? k - 3 : k - 4
 // k_lo .. k_hi of the plane ring (one plane, or eight for the first unit of
 // an item) and, with cross taps in the pressure half step, the v_x and v_y
 // planes s_lo .. s_hi of their rings, all completing on the stage's mbarrier.
-template <int N, bool VEL, bool CROSS>
+template <int N, bool VEL, bool CROSS, bool PS>
 __device__ __forceinline__ void issue3(const PipeMaps &T, const Region3 &R, float *st, float *ring, float *sub,
                                        uint64_t *bar, int x0, int y0, int k, int k_lo, int k_hi, int s_lo, int s_hi,
                                        bool nl, bool nl_vel) {
-  using G = Ring3<N, VEL, CROSS>;
-  using SS = Strips<N>;
+  using G = Ring3<N, VEL, CROSS, PS>;
+  using SS = Strips<N, PS>;
   fence_proxy_async_smem();
   const unsigned planes = G::kPlaneBytes * (unsigned)(k_hi - k_lo + 1);
   // C-PML strip boxes of the axes the unit reaches (all mechanisms)
@@ -185,7 +191,7 @@ __device__ __forceinline__ void issue3(const PipeMaps &T, const Region3 &R, floa
   const int zpl = N > 0 ? R.zs_plane(k) : -1;
   const unsigned xs = xside >= 0 ? 2u * 2u * (unsigned)(N * kHT * R.xsL) : 0u;
   const unsigned yz = (yrow != INT_MIN ? 2u * 2u * N * kArr : 0u) + (zpl >= 0 ? 2u * 2u * N * kArr : 0u);
-  float *ss = st + (VEL ? Vel3<N>::oS : Prs3<N, CROSS>::oS);
+  float *ss = st + (VEL ? Vel3<N, PS>::oS : Prs3<N, CROSS, PS>::oS);
   auto load_strips = [&] {
     if (xside >= 0) {
       tma_load_4d(ss + SS::oXa, &T.m[10], xside * R.xsL, y0, k, 0, bar);
@@ -201,7 +207,7 @@ __device__ __forceinline__ void issue3(const PipeMaps &T, const Region3 &R, floa
     }
   };
   if (VEL) {
-    using S = Vel3<N>;
+    using S = Vel3<N, PS>;
     mbar_arrive_expect_tx(bar, S::kBytes + (nl_vel ? S::kKmBytes : 0u) + planes + xs + yz);
     load_strips();
     for (int kp = k_lo; kp <= k_hi; ++kp) tma_load_3d(ring + ring_slot(kp) * G::kPlane, &T.m[0], x0 - 4, y0 - 3, kp, bar);
@@ -211,10 +217,11 @@ __device__ __forceinline__ void issue3(const PipeMaps &T, const Region3 &R, floa
     if (N > 0) {
       tma_load_4d(st + S::oA, &T.m[6], x0, y0, k, 0, bar);
       tma_load_4d(st + S::oB, &T.m[7], x0, y0, k, 0, bar);
+      if (PS) tma_load_4d(st + S::oPsi, &T.m[4], x0, y0, k, 0, bar);
     }
-    if (nl_vel) tma_load_3d(st + S::oKm, &T.m[12], x0, y0, k, bar);
+    if (!PS && nl_vel) tma_load_3d(st + S::oKm, &T.m[12], x0, y0, k, bar);
   } else {
-    using S = Prs3<N, CROSS>;
+    using S = Prs3<N, CROSS, PS>;
     const unsigned subs = CROSS ? (S::kXPlaneBytes + S::kYPlaneBytes) * (unsigned)(s_hi - s_lo + 1) : 0u;
     mbar_arrive_expect_tx(bar, S::kBytesNoChi + (nl ? 2u * kArr : 0u) + planes + subs + xs + yz);
     load_strips();
@@ -237,6 +244,7 @@ __device__ __forceinline__ void issue3(const PipeMaps &T, const Region3 &R, floa
     if (N > 0) {
       tma_load_4d(st + S::oA, &T.m[8], x0, y0, k, 0, bar);
       tma_load_4d(st + S::oB, &T.m[9], x0, y0, k, 0, bar);
+      if (PS) tma_load_4d(st + S::oPsi, &T.m[4], x0, y0, k, 0, bar);
     }
   }
 }
@@ -378,11 +386,11 @@ __device__ __forceinline__ void strip3x_staged(const StepParams &P, const bf16 *
 
 // All C-PML coefficient overrides of an edge pair for mechanism nu (axes x,
 // y, z), from the staged boxes where the unit has them, else global memory.
-template <int N, int OP>
+template <int N, int OP, bool PS>
 __device__ __forceinline__ void strips_of(const StepParams &P, const Region3 &R, const float *ss, int xside, bool ys,
                                           bool zs, int nu, int i0, int j, int k, int ly, int lx, float2 (&A)[3],
                                           float2 (&B)[3]) {
-  using SS = Strips<N>;
+  using SS = Strips<N, PS>;
   if (xside >= 0)
     strip3x_staged(P, reinterpret_cast<const bf16 *>(ss + SS::oXa), reinterpret_cast<const bf16 *>(ss + SS::oXb),
                    R.xsL, nu, i0, ly, A[0], B[0]);
@@ -487,28 +495,27 @@ __device__ __forceinline__ Face3 face3(const StepParams &P, const bf16 *rb, int 
 // The memory-variable update of mechanism nu on the three axes and its
 // contribution to the stretched derivatives (Eqs. relaxation4,
 // relaxation_psi), writing psi back; A[a], B[a] are the coefficients of
-// axis a, q the memory variables before the update.
-template <int N>
+// axis a, q[a] its memory variable before the update.
 __device__ __forceinline__ void relax3(const StepParams &P, float *const *psi, long long o, int i0, bool edge,
-                                       const Psi<N> &q, int nu, const float2 (&A)[3], const float2 (&B)[3],
+                                       const float2 (&q)[3], const float2 (&A)[3], const float2 (&B)[3],
                                        const float2 (&D)[3], float2 (&S)[3]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float2 n;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      el2(n, e) = fmaf(el2(B[a], e), el2(q[a][nu], e), el2(A[a], e) * el2(D[a], e));
-      el2(S[a], e) += fmaf(P.w_new, el2(n, e), P.w_old * el2(q[a][nu], e));
+      el2(n, e) = fmaf(el2(B[a], e), el2(q[a], e), el2(A[a], e) * el2(D[a], e));
+      el2(S[a], e) += fmaf(P.w_new, el2(n, e), P.w_old * el2(q[a], e));
     }
     if (edge) n = mask_pad2(n, i0, P.nx);
     st_state2(psi[a], o, n);
   }
 }
 
-template <int N, bool EDGE, bool CROSS>
+template <int N, bool EDGE, bool CROSS, bool PS>
 __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 &R, float *st, const float *ring,
                                              int x0, int y0, int k, int tid, const Psi<N> &q) {
-  using S = Vel3<N>;
+  using S = Vel3<N, PS>;
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
@@ -517,7 +524,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
   const int o = ly * kTX + lx;
   // derivatives: x, y from the halo plane of k (cell e at column lx + 4 + e),
   // z from the same cell of planes k-3 .. k+4 in the ring
-  constexpr int kPl = Vel3<N>::kPlane;
+  constexpr int kPl = S::kPlane;
   const float *sp = ring + ring_slot(k) * kPl;
   const int sy = ly + 3;
   float2 D[3];
@@ -588,8 +595,11 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
     const float2 a = sldh2(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
     const float2 b = sldb2(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
     float2 A[3] = {a, a, a}, B[3] = {b, b, b};
-    if (EDGE) strips_of<N, 1>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A, B);
-    relax3<N>(P, P.psi1, nu * Sn + c, i0, EDGE, q, nu, A, B, D, Sd);
+    if (EDGE) strips_of<N, 1, PS>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A, B);
+    float2 qq[3];
+#pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3) qq[a3] = PS ? sld2(st + S::oPsi + (a3 * N + nu) * kArr + o) : q[a3][nu];
+    relax3(P, P.psi1, nu * Sn + c, i0, EDGE, qq, A, B, D, Sd);
   }
   const Face3 f = face3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), x0, y0, k, lx, ly);
   const float rr[3] = {f.r0, f.r1, f.r2}, ru[2] = {f.u0, f.u1}, rz[2] = {f.z0, f.z1};
@@ -628,10 +638,10 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
   st_state2(P.v[2], c, v2);
 }
 
-template <int N, bool EDGE, bool CROSS>
+template <int N, bool EDGE, bool CROSS, bool PS>
 __device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 &R, const float *st, const float *ring,
                                              const float *sub, int x0, int y0, int k, int tid, const Psi<N> &q) {
-  using S = Prs3<N, CROSS>;
+  using S = Prs3<N, CROSS, PS>;
   const int lx = 2 * (tid & 63), ly = tid >> 6;
   const int i0 = x0 + lx, j = y0 + ly;
   if (EDGE && (i0 >= P.nx || j >= P.ny)) return;
@@ -735,8 +745,11 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 
     const float2 a = sldh2(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
     const float2 b = sldb2(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
     float2 A[3] = {a, a, a}, B[3] = {b, b, b};
-    if (EDGE) strips_of<N, 2>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A, B);
-    relax3<N>(P, P.psi2, nu * Sn + c, i0, EDGE, q, nu, A, B, D, Sd);
+    if (EDGE) strips_of<N, 2, PS>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A, B);
+    float2 qq[3];
+#pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3) qq[a3] = PS ? sld2(st + S::oPsi + (a3 * N + nu) * kArr + o) : q[a3][nu];
+    relax3(P, P.psi2, nu * Sn + c, i0, EDGE, qq, A, B, D, Sd);
   }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -750,10 +763,10 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 
 
 // One half step.  Block (32, 16), one per SM; items blockIdx.x,
 // blockIdx.x + gridDim.x, ...; within an item the units k0 .. k1-1 in order.
-template <int N, bool VEL, bool CROSS>
+template <int N, bool VEL, bool CROSS, bool PS>
 __global__ void __launch_bounds__(kThreads, 1)
     pipe3d_kernel(const StepParams P, const Region3 R, const __grid_constant__ PipeMaps T) {
-  using G = Ring3<N, VEL, CROSS>;
+  using G = Ring3<N, VEL, CROSS, PS>;
   constexpr int kStage = G::kStage;
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -777,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned phase = 0, pending = 0;
   const bool nl = P.nl != 0, nlv = VEL && P.nl_vel != 0;
   if (tid == 0)
-    issue3<N, VEL, CROSS>(T, R, smem, ring, sub, &bar[0], x0, y0, k, ring_first<VEL>(k), ring_first<VEL>(k) + 7,
+    issue3<N, VEL, CROSS, PS>(T, R, smem, ring, sub, &bar[0], x0, y0, k, ring_first<VEL>(k), ring_first<VEL>(k) + 7,
                           k - 1, k + 1, nl, nlv);
   pending |= 1u;
   // this thread's memory variables, one unit ahead of the compute
@@ -789,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 q);
   };
   Psi<N> qc, qn;
-  psi_of(x0, y0, k, qc);
+  if (!PS) psi_of(x0, y0, k, qc);
   int s = 0;
 #pragma unroll 1
   while (true) {
@@ -818,60 +831,68 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (tid < 32) {
         const int kp = ring_first<VEL>(nk) + 7;
         if (tid == 0)
-          issue3<N, VEL, CROSS>(T, R, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk, kp, kp, nk + 1, nk + 1,
+          issue3<N, VEL, CROSS, PS>(T, R, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk, kp, kp, nk + 1, nk + 1,
                                 nl, nlv);
         if (!R.interior(nx0, ny0, nk)) prefetch_strips<N, VEL ? 1 : 2>(P, R, nx0, ny0, nk, tid);
       }
       pending |= 1u << q;
     }
-    if (more) psi_of(nx0, ny0, nk, qn);
+    if (!PS && more) psi_of(nx0, ny0, nk, qn);
     float *cur = smem + s * kStage;
     if (R.interior(x0, y0, k)) {
-      if (VEL) vel3_compute<N, false, CROSS>(P, R, cur, ring, x0, y0, k, tid, qc);
-      else prs3_compute<N, false, CROSS>(P, R, cur, ring, sub, x0, y0, k, tid, qc);
+      if (VEL) vel3_compute<N, false, CROSS, PS>(P, R, cur, ring, x0, y0, k, tid, qc);
+      else prs3_compute<N, false, CROSS, PS>(P, R, cur, ring, sub, x0, y0, k, tid, qc);
     } else {
-      if (VEL) vel3_compute<N, true, CROSS>(P, R, cur, ring, x0, y0, k, tid, qc);
-      else prs3_compute<N, true, CROSS>(P, R, cur, ring, sub, x0, y0, k, tid, qc);
+      if (VEL) vel3_compute<N, true, CROSS, PS>(P, R, cur, ring, x0, y0, k, tid, qc);
+      else prs3_compute<N, true, CROSS, PS>(P, R, cur, ring, sub, x0, y0, k, tid, qc);
     }
     if (!more) break;
     if (fresh) {  // a new column: all ring planes, once every thread is done with the rings
       __syncthreads();
       if (tid == 0)
-        issue3<N, VEL, CROSS>(T, R, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk, ring_first<VEL>(nk),
+        issue3<N, VEL, CROSS, PS>(T, R, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk, ring_first<VEL>(nk),
                               ring_first<VEL>(nk) + 7, nk - 1, nk + 1, nl, nlv);
       pending |= 1u << q;
     }
     it = nit;
     x0 = nx0; y0 = ny0; k0 = nk0; k1 = nk1; k = nk;
     s = q;
+    if (!PS) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int nu = 0; nu < N; ++nu) qc[a][nu] = qn[a][nu];
+        for (int nu = 0; nu < N; ++nu) qc[a][nu] = qn[a][nu];
+    }
   }
 }
 
-template <int N, bool VEL, bool CROSS>
+template <int N, bool VEL, bool CROSS, bool PS>
 cudaError_t pipe3_launch(const StepParams &P, const Region3 &R, int grid, const PipeMaps &T, cudaStream_t st) {
-  constexpr size_t bytes = Ring3<N, VEL, CROSS>::kBytes;
+  constexpr size_t bytes = Ring3<N, VEL, CROSS, PS>::kBytes;
   static_assert(bytes + 64 <= 227 * 1024, "stages exceed shared memory");
-  cudaError_t e =
-      cudaFuncSetAttribute(pipe3d_kernel<N, VEL, CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = cudaFuncSetAttribute(pipe3d_kernel<N, VEL, CROSS, PS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pipe3d_kernel<N, VEL, CROSS><<<grid, dim3(32, kThreads / 32), bytes, st>>>(P, R, T);
+  pipe3d_kernel<N, VEL, CROSS, PS><<<grid, dim3(32, kThreads / 32), bytes, st>>>(P, R, T);
   return cudaGetLastError();
 }
 
-template <bool VEL, bool CROSS>
+template <bool VEL, bool CROSS, bool PS>
 cudaError_t pipe3_dispatch(const StepParams &P, const Region3 &R, int grid, const PipeMaps &T, cudaStream_t st) {
   switch (P.n_relax) {
-    case 0: return pipe3_launch<0, VEL, CROSS>(P, R, grid, T, st);
-    case 1: return pipe3_launch<1, VEL, CROSS>(P, R, grid, T, st);
-    case 2: return pipe3_launch<2, VEL, CROSS>(P, R, grid, T, st);
-    case 3: return pipe3_launch<3, VEL, CROSS>(P, R, grid, T, st);
+    case 0: return pipe3_launch<0, VEL, CROSS, PS>(P, R, grid, T, st);
+    case 1: return pipe3_launch<1, VEL, CROSS, PS>(P, R, grid, T, st);
+    case 2: return pipe3_launch<2, VEL, CROSS, PS>(P, R, grid, T, st);
+    case 3: return pipe3_launch<3, VEL, CROSS, PS>(P, R, grid, T, st);
     default: return cudaErrorInvalidValue;
   }
 }
+
+// The layout of a half step: the memory variables staged with the other
+// arrays (PS) unless the stage needs that room for the cross taps' planes
+// or (velocity) the literal system's K box; then they are loaded into
+// registers one unit ahead and the C-PML strips of every axis are staged.
+bool psi_staged(bool vel, const StepParams &P) { return P.g11h == 0.f && !(vel && P.nl_vel); }
 
 // The x strip's coefficients come by TMA when a box of L values per row
 // starts on a 16-byte boundary and fits the stage (L a multiple of 8, at
@@ -895,8 +916,9 @@ bool z_strip_staged(const StepParams &P) {
 
 // Planes per item: the split of each column into items that minimises the
 // busiest block's work, counting each item's start (eight ring planes and
-// one exposed copy latency) as about 1.5 units.
-Region3 region3_of(const StepParams &P, int grid) {
+// one exposed copy latency) as about 1.5 units.  ps: the layout stages the
+// memory variables, so the y and z strips are read per cell.
+Region3 region3_of(const StepParams &P, int grid, bool ps) {
   Region3 R;
   R.nx = P.nx;
   R.ny = P.ny;
@@ -907,8 +929,8 @@ Region3 region3_of(const StepParams &P, int grid) {
   R.tnx = (P.nx + kTX - 1) / kTX;
   R.nhy = (P.ny + kHT - 1) / kHT;
   R.xsL = x_strip_staged(P) ? P.L[0] : 0;
-  R.ysL = y_strip_staged(P) ? P.L[1] : 0;
-  R.zsL = z_strip_staged(P) ? P.L[2] : 0;
+  R.ysL = !ps && y_strip_staged(P) ? P.L[1] : 0;
+  R.zsL = !ps && z_strip_staged(P) ? P.L[2] : 0;
   const long long ncols = (long long)R.tnx * R.nhy;
   double best = 1e300;
   R.seglen = P.nz;
@@ -947,15 +969,17 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
   const ull f3[2] = {(ull)P.pitch * 4, (ull)P.plane * 4}, h3[2] = {(ull)P.pitch * 2, (ull)P.plane * 2};
   const ull f4[3] = {(ull)P.pitch * 4, (ull)P.plane * 4, S * 4}, h4[3] = {(ull)P.pitch * 2, (ull)P.plane * 2, S * 2};
   const ull d3[3] = {nx, ny, nz};
-  const ull dv[4] = {nx, ny, nz, 3}, dab[4] = {nx, ny, nz, (ull)N};
+  const ull dv[4] = {nx, ny, nz, 3}, dab[4] = {nx, ny, nz, (ull)N}, dpsi[4] = {nx, ny, nz, (ull)(3 * N)};
   const unsigned halo[3] = {kCW, kHT + 7, 1}, rho[3] = {kRWb, kHT + 1, 2}, one[3] = {kTX, kHT, 1},
-                 v4[4] = {kTX, kHT, 1, 3}, ab4[4] = {kTX, kHT, 1, (unsigned)N}, vx[3] = {kCW, kHT, 1},
+                 v4[4] = {kTX, kHT, 1, 3}, ab4[4] = {kTX, kHT, 1, (unsigned)N},
+                 psi4[4] = {kTX, kHT, 1, (unsigned)(3 * N)}, vx[3] = {kCW, kHT, 1},
                  vy[3] = {kTX, kHT + 7, 1}, halo1[3] = {kCW, kHT + 2, 1};
   bool ok = true;
   // velocity half step
   ok = ok && encode_tensor_map(&vel->m[0], P.p, 4, 3, d3, f3, halo);
   ok = ok && encode_tensor_map(&vel->m[2], P.rho, 2, 3, d3, h3, rho);
   ok = ok && encode_tensor_map(&vel->m[3], P.v[0], 4, 4, dv, f4, v4);
+  if (N > 0) ok = ok && encode_tensor_map(&vel->m[4], P.psi1[0], 4, 4, dpsi, f4, psi4);
   ok = ok && encode_tensor_map(&vel->m[5], P.ik1, 2, 3, d3, h3, one);
   if (N > 0) {
     ok = ok && encode_tensor_map(&vel->m[6], P.a1, 2, 4, dab, h4, ab4);
@@ -973,6 +997,7 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
     ok = ok && encode_tensor_map(&prs->m[2], P.v[2], 4, 3, d3, f3, one);
   }
   ok = ok && encode_tensor_map(&prs->m[3], P.p, 4, 3, d3, f3, one);
+  if (N > 0) ok = ok && encode_tensor_map(&prs->m[4], P.psi2[0], 4, 4, dpsi, f4, psi4);
   ok = ok && encode_tensor_map(&prs->m[5], P.ik2, 2, 3, d3, h3, one);
   ok = ok && encode_tensor_map(&prs->m[6], P.K, 2, 3, d3, h3, one);
   if (P.nl) ok = ok && encode_tensor_map(&prs->m[7], P.chi, 2, 3, d3, h3, one);
@@ -1014,11 +1039,20 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
   return cudaSuccess;
 }
 
-cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t st) {
-  const Region3 R = region3_of(P, grid);
+bool pipe3d_layout_allowed(bool vel, const StepParams &P, int layout) {
+  return layout != kLayoutStaged || psi_staged(vel, P);
+}
+
+cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t st, int layout) {
+  const bool ps = layout == kLayoutRegisters ? false : psi_staged(vel, P);
+  const Region3 R = region3_of(P, grid, ps);
   if (P.g11h != 0.f)
-    return vel ? pipe3_dispatch<true, true>(P, R, grid, T, st) : pipe3_dispatch<false, true>(P, R, grid, T, st);
-  return vel ? pipe3_dispatch<true, false>(P, R, grid, T, st) : pipe3_dispatch<false, false>(P, R, grid, T, st);
+    return vel ? pipe3_dispatch<true, true, false>(P, R, grid, T, st)
+               : pipe3_dispatch<false, true, false>(P, R, grid, T, st);
+  if (vel)
+    return ps ? pipe3_dispatch<true, false, true>(P, R, grid, T, st)
+              : pipe3_dispatch<true, false, false>(P, R, grid, T, st);
+  return pipe3_dispatch<false, false, true>(P, R, grid, T, st);
 }
 
 }  // namespace fw2

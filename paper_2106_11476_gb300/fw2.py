@@ -100,6 +100,7 @@ EXPORTS = {
                                            C.c_void_p]),
     "fw2_selftest_bounded_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
     "fw2_kernel_path": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "fw2_pipe_layout": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "fw2_taps_time_space": (C.c_int, [C.c_double, C.c_int32, C.POINTER(C.c_double)]),
     "fw2_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "fw2_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -344,6 +345,15 @@ def fw2_kernel_path(ctx) -> str:
     return {0: "auto", 1: "tile", 2: "pipe"}[v.value]
 
 
+def fw2_pipe_layout(ctx) -> tuple:
+    """(velocity, pressure) layout of the 3D pipelined half steps:
+    'staged', 'registers' or None before the choice (fw2_pipe_layout)."""
+    v, p = C.c_int32(0), C.c_int32(0)
+    _check(lib().fw2_pipe_layout(ctx, C.byref(v), C.byref(p)), ctx)
+    names = {0: None, 1: "staged", 2: "registers"}
+    return names[v.value], names[p.value]
+
+
 def fw2_selftest_bounded_wait(limit_ns: int) -> bool:
     """True when a wait on a barrier nobody arrives on gave up after limit_ns."""
     t = C.c_int32(-1)
@@ -494,7 +504,7 @@ def fw2_abi_version() -> int:
 
 # ------------------------------------------------------------ convenience ---
 
-KERNEL_PATH = {"auto": 0, "tile": 1, "pipe": 2}
+KERNEL_PATH = {"auto": 0, "tile": 1, "pipe": 2, "pipe-staged": 3, "pipe-registers": 4}
 
 
 def config_for(prob, stream: Optional[int] = None, map_precision: str = "f32", kernel_path: str = "auto") -> Config:

@@ -56,7 +56,7 @@ def test_abi_version(fw2lib):
     ({"pml_transition": 4, "n_relax": 0}, fw2.EINVAL),                     # PML needs N >= 1
     ({"nl_mode": 7}, fw2.EINVAL),
     ({"nl_mode": 4}, fw2.EINVAL),                                          # past LITERAL
-    ({"kernel_path": 3}, fw2.EINVAL),
+    ({"kernel_path": 5}, fw2.EINVAL),
     ({"mem_alignment": 2}, fw2.EINVAL),
     ({"map_precision": 5}, fw2.EINVAL),
     ({"ndim": 3, "n": (64, 64, 64), "map_precision": 2}, fw2.EUNSUPPORTED),
