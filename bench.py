@@ -452,6 +452,7 @@ def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=T
     vel_ms, nv, prs_ms, np_ = fw2.fw2_profile_read(sim.ctx)
     fw2.fw2_profile(sim.ctx, False)
     nd = prob.ndim
+    layout = fw2.fw2_pipe_layout(sim.ctx) if nd == 3 else None
     if fw2.fw2_kernel_path(sim.ctx) == "pipe":
         kv, kp = (f"pipe{nd}d_vel", f"pipe{nd}d_prs")
     else:
@@ -498,7 +499,8 @@ def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=T
     return {"value": round(value, 4), "ms_per_step": round(elapsed_max / steps, 5),
             "config": {"workload": desc, "grid": list(prob.shape), "n_relax": prob.nrelax,
                        "nl_mode": prob.nl_mode, "map_precision": maps, "kernel_path": args.kernel_path,
-                       "taps": args.taps, "pml_cells": L},
+                       "taps": args.taps, "pml_cells": L,
+                       **({"pipe_layout": {"velocity": layout[0], "pressure": layout[1]}} if layout else {})},
             "latency": {"p50_ms_per_step": round(float(np.percentile(per_step, 50)), 5),
                         "p99_ms_per_step": round(float(np.percentile(per_step, 99)), 5)},
             "roofline": roof, "parity": parity, "cpu_baseline": cpu, "e2e": e2e,
@@ -880,8 +882,9 @@ def main():
                          "form; skull: 3D 768^3 with bf16 maps; plain: 2D 512^2 homogeneous line source")
     ap.add_argument("--maps", default=None, choices=["f32", "bf16", "idx"],
                     help="override the map storage of the workload")
-    ap.add_argument("--kernel-path", default="auto", choices=["auto", "tile", "pipe"],
-                    help="2D half-step kernels (bitwise the same results)")
+    ap.add_argument("--kernel-path", default="auto", choices=["auto", "tile", "pipe", "pipe-staged", "pipe-registers"],
+                    help="half-step kernels (bitwise the same results); pipe-staged / pipe-registers fix the layout "
+                         "of the 3D pipelined half steps, which auto and pipe choose by timing")
     ap.add_argument("--taps", default="taylor", choices=["taylor", "time-space"],
                     help="staggered taps: 8th-order Taylor, or the time-space optimised set with cross taps")
     ap.add_argument("--nl", default=None, choices=["off", "pressure", "westervelt", "literal"],
