@@ -19,7 +19,7 @@ same way in the same run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fw2|reference]
                   [--workload abdominal|abdominal-idx|skull|plain|batch|serve]
-                  [--configs all|none|plain,skull,batch] [--no-parity]
+                  [--configs all|none|plain,skull,batch,serve] [--no-parity]
                   [--taps taylor|time-space] [--nl off|pressure|westervelt|literal]
 
 Under torchrun each rank simulates its own transmit event (independent
@@ -605,11 +605,12 @@ def run_fw2(args, rank, world, dist):
 def other_configs(args, rank):
     """The other configurations of the workload family, measured in the same
     run (rank 0 of a single-GPU run): the plain 512^2 method for its full
-    1000 steps, the 768^3 transcranial medium for K steps, and the batch of
-    80 transmit events / uneven instances for K steps."""
+    1000 steps, the 768^3 transcranial medium for K steps, the batch of 80
+    transmit events / uneven instances for K steps, and the serving loop on
+    the first 16 arrivals of the full-scale request stream."""
     import torch
     out = {}
-    sel = args.configs.split(",") if args.configs != "all" else ["plain", "skull", "batch"]
+    sel = args.configs.split(",") if args.configs != "all" else ["plain", "skull", "batch", "serve"]
     if "plain" in sel:
         prob, maps, desc = workload_problem(args, "plain", 512, 1000, rank)
         r = measure(args, prob, maps, desc, 1000 - 20, 20, rank, 1, None, want_e2e=True, want_cpu=False,
@@ -626,6 +627,11 @@ def other_configs(args, rank):
         torch.cuda.empty_cache()
     if "batch" in sel:
         out["batch"] = batch_measurement(args, rank, 1, None)
+        torch.cuda.empty_cache()
+    if "serve" in sel:
+        # the first 16 arrivals of the full-scale stream (the whole 200-arrival
+        # window runs with --workload serve)
+        out["serve_16"] = serve_measurement(args, 16, 20.0, 1.0, rank, 1, None)
         torch.cuda.empty_cache()
     return out
 
@@ -749,41 +755,39 @@ def run_batch(args, rank, world, dist):
     print(json.dumps(out), flush=True)
 
 
-def serve_requests(args, rank):
-    """Poisson arrivals (mean `--rate` per s) of seeded requests: 70 % 2D
-    tissue-index abdominal media, 30 % 3D skull-like media (N = 3, bf16
-    maps).  Sizes and step counts are scaled down from the serving
-    configuration (2D sides 512-4096, 1-4k steps; 3D sides 256-512, 1-2k
-    steps) by --serve-scale so that one bench call stays within minutes."""
+def serve_requests(n_requests, rate, scale, rank):
+    """Poisson arrivals (mean `rate` per s) of seeded requests: 70 % 2D
+    tissue-index abdominal media with sides U[512, 4096] and U[1000, 4000]
+    steps, 30 % 3D skull-like media (N = 3, bf16 maps) with sides U[256, 512]
+    and U[1000, 2000] steps; `scale` < 1 shrinks sides and steps alike."""
     import synth
     from paper_2106_11476_gb300.serve import Request
     rng = np.random.default_rng(500 + rank)
-    sc = args.serve_scale
     t = 0.0
     reqs = []
-    for i in range(args.requests):
-        t += rng.exponential(1.0 / args.rate)
+    for i in range(n_requests):
+        t += rng.exponential(1.0 / rate)
         if rng.random() < 0.7:
-            side = int(rng.integers(512, 4097) * sc) // 4 * 4
-            steps = int(rng.integers(1000, 4001) * sc)
+            side = int(rng.integers(512, 4097) * scale) // 4 * 4
+            steps = int(rng.integers(1000, 4001) * scale)
             p = synth.indexed_abdominal_problem(nx=max(side, 256), ny=max(side, 256), n_steps=steps,
                                                 seed=1000 + i, n_elements=min(64, max(side, 256) // 24))
             reqs.append(Request(i, t, p, steps, "idx"))
         else:
-            side = int(rng.integers(256, 513) * sc)
-            steps = int(rng.integers(1000, 2001) * sc)
+            side = int(rng.integers(256, 513) * scale)
+            steps = int(rng.integers(1000, 2001) * scale)
             p = synth.skull_problem(n=max(side, 96), n_steps=steps, seed=2000 + i, pml_cells=16, array_elems=4)
             reqs.append(Request(i, t, p, steps, "bf16"))
     return reqs
 
 
-def run_serve(args, rank, world, dist):
-    import torch
-    from paper_2106_11476_gb300 import _build, fw2
+def serve_measurement(args, n_requests, rate, scale, rank, world, dist):
+    """The serving loop on a seeded request stream against the plain form:
+    the same requests one at a time in arrival order on dense float maps,
+    each measured over all its steps (setup included)."""
+    from paper_2106_11476_gb300 import fw2
     from paper_2106_11476_gb300.serve import Server, latency_stats
-    _build.build()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    reqs = serve_requests(args, rank)
+    reqs = serve_requests(n_requests, rate, scale, rank)
     work = sum(r.cells * r.steps for r in reqs)
     srv = Server(cap_bytes=160e9, slice_steps=args.slice)
     with ClockSampler(device_id_for_smi()) as clk:
@@ -791,40 +795,47 @@ def run_serve(args, rank, world, dist):
         done = srv.run(reqs)
         makespan = time.perf_counter() - t0
     served = latency_stats(done)
-    # plain form, one request at a time in arrival order with float maps:
-    # measured rate per request (a short run), then the FIFO schedule
     t_free, finish = 0.0, []
     for r in sorted(reqs, key=lambda q: q.arrival):
+        start = max(t_free, r.arrival)
         s0 = time.perf_counter()
         sim = fw2.Simulation(r.problem, map_precision="f32")
-        setup = time.perf_counter() - s0
-        k = min(r.steps, 30)
-        sim.step(2); sim.synchronize()
-        s1 = time.perf_counter()
-        sim.step(k); sim.synchronize()
-        run = (time.perf_counter() - s1) * r.steps / k
+        sim.step(r.steps)
+        sim.synchronize()
         sim.close()
-        start = max(t_free, r.arrival)
-        t_free = start + setup + run
+        t_free = start + (time.perf_counter() - s0)
         finish.append(t_free - r.arrival)
     plain_makespan = t_free - min(r.arrival for r in reqs)
+    n3 = sum(len(r.problem.shape) == 3 for r in reqs)
+    return {"value": round(work / makespan / 1e9, 4), "unit": UNIT,
+            "config": {"workload": f"serving: {n_requests} Poisson arrivals at {rate}/s, 70 % 2D tissue-index "
+                                   f"(sides 512-4096, 1-4k steps) / 30 % 3D bf16 (sides 256-512, 1-2k steps), "
+                                   f"scale {scale}, 160 GB admission cap, slices of {args.slice} steps",
+                       "requests_2d": n_requests - n3, "requests_3d": n3,
+                       "makespan_s": round(makespan, 3), "cell_steps": work},
+            "latency": {"p50_time_to_result_s": round(served["p50_s"], 3),
+                        "p99_time_to_result_s": round(served["p99_s"], 3)},
+            "plain_form": {"value": round(work / plain_makespan / 1e9, 4), "unit": UNIT,
+                           "p50_time_to_result_s": round(float(np.percentile(finish, 50)), 3),
+                           "p99_time_to_result_s": round(float(np.percentile(finish, 99)), 3),
+                           "how": "one request at a time in arrival order, float maps, each run in full "
+                                  "(setup, all its steps)"},
+            "clocks": clk.summary()}
+
+
+def run_serve(args, rank, world, dist):
+    import torch
+    from paper_2106_11476_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    r = serve_measurement(args, args.requests, args.rate, args.serve_scale, rank, world, dist)
     if rank != 0:
         return
-    out = {"metric": METRIC, "value": round(work / makespan / 1e9, 4), "unit": UNIT, "n_gpus": world,
-           "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic (seeded request stream)",
-           "config": {"workload": f"serving: {args.requests} Poisson arrivals at {args.rate}/s, 70 % 2D "
-                                  f"tissue-index / 30 % 3D bf16, sizes and steps scaled by {args.serve_scale}, "
-                                  f"160 GB admission cap, slices of {args.slice} steps",
-                      "makespan_s": round(makespan, 3), "cell_steps": work},
-           "latency": {"p50_time_to_result_s": round(served["p50_s"], 3),
-                       "p99_time_to_result_s": round(served["p99_s"], 3)},
-           "plain_form": {"value": round(work / plain_makespan / 1e9, 4), "unit": UNIT,
-                          "p50_time_to_result_s": round(float(np.percentile(finish, 50)), 3),
-                          "p99_time_to_result_s": round(float(np.percentile(finish, 99)), 3),
-                          "how": "one request at a time in arrival order, float maps; each request's run "
-                                 "time from a 30-step measurement scaled to its steps, plus its measured setup"},
-           "clocks": clk.summary()}
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": None, "warmup": 0,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded request stream)"}
+    for k in ("config", "latency", "plain_form", "clocks"):
+        out[k] = r[k]
     print(json.dumps(out), flush=True)
 
 
@@ -872,9 +883,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fw2", choices=["fw2", "reference"])
     ap.add_argument("--n", type=int, default=4096, help="grid side of the workload")
-    ap.add_argument("--requests", type=int, default=24, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
-    ap.add_argument("--serve-scale", type=float, default=0.25, help="serving: size and step scale")
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="serving: size and step scale")
     ap.add_argument("--slice", type=int, default=100, help="serving: steps per slice")
     ap.add_argument("--workload", default="abdominal",
                     choices=["abdominal", "abdominal-idx", "skull", "plain", "batch", "serve"],
@@ -896,7 +907,7 @@ def main():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--configs", default="all",
                     help="other configurations measured after the default workload: all, none, or a comma list "
-                         "of plain, skull, batch")
+                         "of plain, skull, batch, serve")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -5,8 +5,10 @@ The server admits waiting requests in arrival order while their device
 footprint fits under a memory cap, keeps their state resident, and advances
 all active requests in slices: the 2D requests together as one fw2 batch
 (one persistent launch per half step for all of them, rebuilt when the set of
-active requests changes), the 3D requests each on its own stream so that
-their work overlaps on the device.  A request's result is its sensor trace;
+active requests changes; each request's remaining steps are its budget, so a
+slice is not cut short for the others when one request ends inside it), the
+3D requests each on its own stream so that their work overlaps on the
+device.  A request's result is its sensor trace;
 it leaves when its last step is done, freeing memory for waiting requests.
 Every request computes exactly what it would compute alone.
 """
@@ -92,13 +94,14 @@ class Server:
                 continue
             two = [a for a in active if len(a[0].problem.shape) == 2]
             three = [a for a in active if len(a[0].problem.shape) == 3]
-            n2 = min([a[2] for a in two], default=0)
-            step2 = min(self.slice, n2) if two else 0
+            step2 = min(self.slice, max([a[2] for a in two], default=0))
             members = tuple(a[0].rid for a in two)
             if two and members != batch_members:
                 if batch is not None:
                     fw2.fw2_batch_destroy(batch)
                 batch = fw2.fw2_batch_create([a[1].ctx for a in two])
+                # every request stops at its own last step
+                fw2.fw2_batch_set_budget(batch, [a[0].steps for a in two])
                 batch_members = members
             if two and step2 > 0:
                 fw2.fw2_batch_step(batch, step2)
@@ -118,7 +121,7 @@ class Server:
             for a in active:
                 r, sim, rem, fp = a
                 if len(r.problem.shape) == 2:
-                    rem -= step2
+                    rem -= min(step2, rem)
                 else:
                     rem -= steps3[i3]
                     i3 += 1

@@ -63,10 +63,16 @@ def _install_fakes(monkeypatch):
     monkeypatch.setattr(_Sim, "__init__", init)
     _Sim.live = 0
     _Sim.peak = 0
+    budgets = {}
+
+    def bstep(b, n):
+        for s, last in zip(batches[b], budgets.get(b, [None] * len(batches[b]))):
+            s.steps += n if last is None else max(0, min(n, last - s.steps))
     fake = types.SimpleNamespace(
         Simulation=_Sim,
         fw2_batch_create=lambda ctxs: (batches.append([sims[id(c)] for c in ctxs]) or len(batches) - 1),
-        fw2_batch_step=lambda b, n: [setattr(s, "steps", s.steps + n) for s in batches[b]],
+        fw2_batch_set_budget=lambda b, last: budgets.__setitem__(b, list(last)),
+        fw2_batch_step=bstep,
         fw2_batch_synchronize=lambda b: None,
         fw2_batch_destroy=lambda b: None)
     monkeypatch.setattr(serve, "fw2", fake)
@@ -99,6 +105,9 @@ def test_every_request_runs_its_steps_in_slices(monkeypatch):
     for r in done:
         assert r.trace[0] == r.steps and r.finished >= r.admitted >= r.arrival
     assert all(e["steps2d"] <= 100 for e in srv.launch_log)
+    # slices are not cut short by the request that ends first: 2D slices of
+    # 100, 100, 50 (rid 3 stops at 75, rid 1 at 120 inside them)
+    assert [e["steps2d"] for e in srv.launch_log if e["n2d"]] == [100, 100, 50]
     # the 2D set changed as requests finished: batches of 3, then 2 (rid 3 left), then 1
     assert [len(b) for b in batches] == [3, 2, 1]
     assert _Sim.live == 0
