@@ -1052,7 +1052,8 @@ cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMap
   if (vel)
     return ps ? pipe3_dispatch<true, false, true>(P, R, grid, T, st)
               : pipe3_dispatch<true, false, false>(P, R, grid, T, st);
-  return pipe3_dispatch<false, false, true>(P, R, grid, T, st);
+  return ps ? pipe3_dispatch<false, false, true>(P, R, grid, T, st)
+            : pipe3_dispatch<false, false, false>(P, R, grid, T, st);
 }
 
 }  // namespace fw2
