@@ -217,6 +217,44 @@ fw2_status fw2_step(fw2_ctx *ctx, int64_t n_steps);
 /* Release every resource of the context (safe on NULL). */
 fw2_status fw2_destroy(fw2_ctx *ctx);
 
+/* ---- one grid split into subdomains --------------------------------------
+ * The finite-difference step is local (Sec. 5 remarks that this suits
+ * several GPUs): a grid split along its slowest axis (y in 2D, z in 3D) into
+ * slabs advances each slab as its own context, given 4 extra rows on every
+ * side where it borders another slab (the half-width of the 8th-order
+ * operator).  Before each velocity half step those rows of p are copied in
+ * from the neighbours, before each pressure half step those of v_q; the
+ * slabs' own rows then hold exactly (bitwise) what one context of the whole
+ * grid holds.  The extra rows are computed too and overwritten by the next
+ * copy.  paper_2106_11476_gb300/slab.py drives this with contexts on one
+ * device or with one process per device and torch.distributed for the
+ * exchange. */
+
+/* Declare the context's grid (extra rows included) as the box [offset,
+ * offset + n) of a grid of extent global_n (cells per axis): the C-PML
+ * depth of every cell is taken from its coordinate in the whole grid, so
+ * the boundary lies at the whole grid's faces only.  Needs fw2_config.dt > 0
+ * and, with a C-PML, pml_cp > 0 (the whole grid's values: a subdomain cannot
+ * derive them from its own medium).  Call before the first step.  EINVAL
+ * when the box leaves the grid, splits a periodic axis, or dt / pml_cp are
+ * missing. */
+fw2_status fw2_set_subdomain(fw2_ctx *ctx, const int64_t *global_n, const int64_t *offset);
+/* One part of a time step, for an exchange between the half steps: part 0
+ * is the velocity half step with the velocity sources, part 1 the pressure
+ * half step with the pressure sources and the recording, after which the
+ * step counter advances.  Parts alternate starting with 0; fw2_step is
+ * refused (ESTATE) between the two.  Asynchronous like fw2_step. */
+fw2_status fw2_step_part(fw2_ctx *ctx, int32_t part);
+/* Copy rows [row0, row0 + n_rows) along the slowest axis (y rows in 2D, z
+ * planes in 3D) of p or a velocity component (FW2_FIELD_P .. VZ) out to, or
+ * in from, a dense buffer [n_rows][ny (3D)][nx] in host or device memory.
+ * Synchronises the context stream.  EINVAL for other fields or rows outside
+ * the grid. */
+fw2_status fw2_get_rows(fw2_ctx *ctx, int32_t field, int64_t row0, int64_t n_rows, float *out,
+                        int32_t mem_space);
+fw2_status fw2_set_rows(fw2_ctx *ctx, int32_t field, int64_t row0, int64_t n_rows, const float *in,
+                        int32_t mem_space);
+
 /* In-loop blow-up detection (a numerical failure such as the C-PML
  * instability with N >= 2 and no transition layer, Sec. 3.3).  With
  * every > 0, fw2_step scans p after each step whose count is a multiple of

@@ -115,6 +115,11 @@ fw2_status finalize(fw2_ctx *c) {
   Q.c = c->raw_c; Q.rho = c->raw_rho; Q.beta = c->raw_beta;
   Q.k1 = c->raw_k1; Q.k2 = c->raw_k2; Q.d1 = c->raw_d1; Q.al1 = c->raw_al1; Q.d2 = c->raw_d2; Q.al2 = c->raw_al2;
   Q.nl_mode = cfg.nl_mode;
+  const long long ext[3] = {c->nx, c->ny, c->nz};
+  for (int q = 0; q < 3; ++q) {
+    Q.gext[q] = (int)(c->subdomain ? c->gext[q] : ext[q]);
+    Q.goff[q] = (int)(c->subdomain ? c->goff[q] : 0);
+  }
   Q.tissue_in = c->map_kind == FW2_MAP_IDX_U8 ? c->raw_tissue : nullptr;
   Q.n_tissue = c->n_tissue;
   // medium scan: c_max (high-frequency) and validity
@@ -381,16 +386,20 @@ int layout_for_step(fw2_ctx *c, bool *timed) {
   return t < 2 ? kLayoutStaged : kLayoutRegisters;
 }
 
-// Enqueue every launch of time step n (Sec. 3.1 order): velocity half step,
-// velocity sources, pressure half step, pressure sources, recording.
-fw2_status enqueue_step(fw2_ctx *c, long long n) {
+// Enqueue the launches of time step n (Sec. 3.1 order): velocity half step,
+// velocity sources (part 0), pressure half step, pressure sources,
+// recording (part 1); part -1 enqueues both, and only whole steps take part
+// in the choice of the 3D layout.
+fw2_status enqueue_step(fw2_ctx *c, long long n, int part = -1) {
   const StepParams &P = c->P;
   bool trial_timed = false;
-  const int trial = layout_for_step(c, &trial_timed);
+  const int trial = part < 0 ? layout_for_step(c, &trial_timed) : -1;
   auto lay = [&](bool vel) {
     const int l = trial > 0 ? trial : c->layout3[vel ? 0 : 1];
+    if (l == 0) return kLayoutDefault;
     return pipe3d_layout_allowed(vel, P, l) ? l : kLayoutRegisters;
   };
+  const bool do_vel = part != 1, do_prs = part != 0;
   cudaEvent_t te[4] = {nullptr, nullptr, nullptr, nullptr};
   if (trial_timed)
     for (auto &e : te) CK(c, cudaEventCreate(&e));
@@ -399,6 +408,7 @@ fw2_status enqueue_step(fw2_ctx *c, long long n) {
     ev = {take_event(c), take_event(c)};
     CK(c, cudaEventRecord(ev.first, c->stream));
   }
+  if (do_vel) {
   if (trial_timed) CK(c, cudaEventRecord(te[0], c->stream));
   CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(true, P, c->map_kind, c->n_sm, c->tm_vel, c->stream)
                               : launch_pipe3d(true, P, c->n_sm, c->tm_vel, c->stream, lay(true)))
@@ -418,6 +428,15 @@ fw2_status enqueue_step(fw2_ctx *c, long long n) {
       c->launches++;
     }
   }
+  }
+  if (!do_prs) {
+    if (c->profiling) {  // the pair taken for the pressure half step goes back unused
+      c->ev_pool.push_back(ev.first);
+      c->ev_pool.push_back(ev.second);
+    }
+    return FW2_OK;
+  }
+  if (c->profiling && !do_vel) ev = {take_event(c), take_event(c)};
   if (c->profiling) CK(c, cudaEventRecord(ev.first, c->stream));
   if (trial_timed) CK(c, cudaEventRecord(te[2], c->stream));
   CK(c, c->pipe ? (c->nd == 2 ? launch_pipe2d(false, P, c->map_kind, c->n_sm, c->tm_prs, c->stream)
@@ -844,6 +863,7 @@ fw2_status fw2_record(fw2_ctx *c, int64_t n_pts, const int64_t *idx, const int32
 fw2_status fw2_step(fw2_ctx *c, int64_t n_steps) {
   if (!c) return FW2_EINVAL;
   if (n_steps < 0) return fail(c, FW2_EINVAL, "negative step count");
+  if (c->half) return fail(c, FW2_ESTATE, "a step begun with fw2_step_part must be completed first");
   fw2_status st;
   if ((st = finalize(c)) != FW2_OK) return st;
   if ((st = build_sources(c)) != FW2_OK) return st;
@@ -866,6 +886,74 @@ fw2_status fw2_pipe_layout(fw2_ctx *c, int32_t *vel, int32_t *prs) {
   *vel = c->layout3[0];
   *prs = c->layout3[1];
   return FW2_OK;
+}
+
+fw2_status fw2_step_part(fw2_ctx *c, int32_t part) {
+  if (!c) return FW2_EINVAL;
+  if (part != 0 && part != 1) return fail(c, FW2_EINVAL, "part must be 0 (velocity) or 1 (pressure)");
+  if (part != c->half)
+    return fail(c, FW2_ESTATE, "part %d of a step requested while part %d is due", part, c->half);
+  fw2_status st;
+  if ((st = finalize(c)) != FW2_OK) return st;
+  if ((st = build_sources(c)) != FW2_OK) return st;
+  if ((st = enqueue_step(c, c->step, part)) != FW2_OK) return st;
+  c->half = part == 0 ? 1 : 0;
+  if (part == 1) c->step += 1;
+  return FW2_OK;
+}
+
+fw2_status fw2_set_subdomain(fw2_ctx *c, const int64_t *global_n, const int64_t *offset) {
+  if (!c || !global_n || !offset) return FW2_EINVAL;
+  const long long ext[3] = {c->nx, c->ny, c->nz};
+  for (int q = 0; q < 3; ++q) {
+    const long long g = q < c->nd ? global_n[q] : 1, o = q < c->nd ? offset[q] : 0;
+    if (o < 0 || g < ext[q] || o + ext[q] > g)
+      return fail(c, FW2_EINVAL, "axis %d: the grid [%lld, %lld) does not lie in [0, %lld)", q, o, o + ext[q], g);
+    if (q < c->nd && c->cfg.bc[q] == FW2_BC_PERIODIC && (o != 0 || g != ext[q]))
+      return fail(c, FW2_EINVAL, "a periodic axis cannot be split into subdomains");
+    c->gext[q] = g;
+    c->goff[q] = o;
+  }
+  if (!(c->cfg.dt > 0.0))
+    return fail(c, FW2_EINVAL, "a subdomain needs an explicit dt (that of the whole grid)");
+  if (c->cfg.pml_transition + c->cfg.pml_bound > 0 && !(c->cfg.pml_cp > 0.0))
+    return fail(c, FW2_EINVAL, "a subdomain with a C-PML needs an explicit pml_cp (that of the whole grid)");
+  c->subdomain = true;
+  c->finalized = false;
+  return FW2_OK;
+}
+
+// Rows of a state array along the slowest axis (y rows in 2D, z planes in
+// 3D) to or from a dense buffer [n_rows][(ny)][nx]; synchronous.
+static fw2_status copy_rows(fw2_ctx *c, int32_t field, int64_t row0, int64_t n_rows, float *buf, int32_t mem_space,
+                     bool out) {
+  if (!c || !buf) return FW2_EINVAL;
+  if (field < FW2_FIELD_P || field > FW2_FIELD_VZ || (field > FW2_FIELD_P && field - FW2_FIELD_VX >= c->nd))
+    return fail(c, FW2_EINVAL, "rows are copied for p and the velocity components only");
+  const long long rows = c->nd == 3 ? c->nz : c->ny;
+  if (row0 < 0 || n_rows < 0 || row0 + n_rows > rows)
+    return fail(c, FW2_EINVAL, "rows [%lld, %lld) outside [0, %lld)", (long long)row0, (long long)(row0 + n_rows), rows);
+  if (n_rows == 0) return FW2_OK;
+  float *f = field == FW2_FIELD_P ? c->p : c->v[field - FW2_FIELD_VX];
+  const long long per_row = c->nd == 3 ? c->plane : c->pitch;
+  const size_t height = (size_t)n_rows * (c->nd == 3 ? c->ny : 1);
+  float *dev = f + row0 * per_row;
+  const size_t w = sizeof(float) * c->nx, dp = sizeof(float) * c->pitch;
+  const cudaMemcpyKind kind = out ? (mem_space == FW2_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost)
+                                  : (mem_space == FW2_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  if (out) CK(c, cudaMemcpy2DAsync(buf, w, dev, dp, w, height, kind, c->stream));
+  else CK(c, cudaMemcpy2DAsync(dev, dp, buf, w, w, height, kind, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return FW2_OK;
+}
+
+fw2_status fw2_get_rows(fw2_ctx *c, int32_t field, int64_t row0, int64_t n_rows, float *out, int32_t mem_space) {
+  return copy_rows(c, field, row0, n_rows, out, mem_space, true);
+}
+
+fw2_status fw2_set_rows(fw2_ctx *c, int32_t field, int64_t row0, int64_t n_rows, const float *in,
+                        int32_t mem_space) {
+  return copy_rows(c, field, row0, n_rows, const_cast<float *>(in), mem_space, false);
 }
 
 fw2_status fw2_set_watch(fw2_ctx *c, int64_t every, float bound) {
@@ -932,6 +1020,7 @@ fw2_status fw2_reset(fw2_ctx *c) {
   CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->step = 0;
+  c->half = 0;
   return FW2_OK;
 }
 

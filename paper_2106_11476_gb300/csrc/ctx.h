@@ -85,6 +85,12 @@ struct fw2_ctx {
   int layout3[2] = {0, 0};
   int layout_trial = 0;
   float layout_ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [layout - 1][half]
+  // subdomain of a larger grid (fw2_set_subdomain): its extent and this
+  // context's offset along each axis; half = 1 between the two parts of a
+  // step taken with fw2_step_part
+  bool subdomain = false;
+  long long gext[3] = {0, 0, 0}, goff[3] = {0, 0, 0};
+  int half = 0;
   // in-loop blow-up detection: scan p every watch_every steps (0: off)
   long long watch_every = 0;
   float watch_bound = 0.f;

@@ -12,6 +12,10 @@ struct PrepParams {
   double dt;
   int LT, LB, reading;
   double npow, d_target;
+  // the grid this context covers within a larger one (a subdomain): extent
+  // of the whole grid and offset of this context along each axis; the
+  // C-PML depth of a cell comes from its coordinate in the whole grid
+  int gext[3], goff[3];
   int nl_mode;
   // raw inputs, dense [n_pts] (relaxation [N][n_pts]), device; in the
   // tissue-index form they are tables [n_tissue] ([N][n_tissue]) read

@@ -184,8 +184,8 @@ __global__ void strip_maps_kernel(const PrepParams Q, int axis) {
     if (axis == 0) out = ((long long)s[2] * Q.ny + s[1]) * pitch_out + s[0];
     else if (axis == 1) out = ((long long)s[2] * (2 * L) + s[1]) * pitch_out + s[0];
     else out = ((long long)s[2] * Q.ny + s[1]) * pitch_out + s[0];
-    const double dface = depth_of(cell[axis] + 0.5, ext[axis], L);
-    const double dcent = depth_of((double)cell[axis], ext[axis], L);
+    const double dface = depth_of(Q.goff[axis] + cell[axis] + 0.5, Q.gext[axis], L);
+    const double dcent = depth_of((double)(Q.goff[axis] + cell[axis]), Q.gext[axis], L);
     const long long ri = src_of(Q, src), nr = n_src(Q);
     const double k1 = Q.k1[ri], k2 = Q.k2[ri];
     for (int nu = 0; nu < Q.N; ++nu) {

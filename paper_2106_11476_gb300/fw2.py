@@ -83,6 +83,10 @@ EXPORTS = {
     "fw2_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "fw2_destroy": (C.c_int, [C.c_void_p]),
     "fw2_set_watch": (C.c_int, [C.c_void_p, C.c_int64, C.c_float]),
+    "fw2_set_subdomain": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "fw2_step_part": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fw2_get_rows": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_void_p, C.c_int32]),
+    "fw2_set_rows": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_void_p, C.c_int32]),
     "fw2_get_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "fw2_get_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "fw2_set_step": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -259,6 +263,32 @@ def fw2_set_watch(ctx, every: int, bound: float):
     """Scan p every `every` steps inside fw2_step and stop with EUNSTABLE
     beyond `bound` (fw2_set_watch; every = 0 switches it off)."""
     _check(lib().fw2_set_watch(ctx, int(every), float(bound)), ctx)
+
+
+def fw2_set_subdomain(ctx, global_shape, offset):
+    """Declare the context's grid as a box of a larger grid (fw2_set_subdomain)."""
+    g = (C.c_int64 * 3)(*(list(global_shape) + [1] * (3 - len(global_shape))))
+    o = (C.c_int64 * 3)(*(list(offset) + [0] * (3 - len(offset))))
+    _check(lib().fw2_set_subdomain(ctx, g, o), ctx)
+
+
+def fw2_step_part(ctx, part: int):
+    """Velocity (0) or pressure (1) part of a time step (fw2_step_part)."""
+    _check(lib().fw2_step_part(ctx, int(part)), ctx)
+
+
+def fw2_get_rows(ctx, field: str, row0: int, n_rows: int, out):
+    """Rows along the slowest axis of p or v_q into `out` (fw2_get_rows)."""
+    p, space, keep = _ptr(out)
+    _check(lib().fw2_get_rows(ctx, FIELD[field], int(row0), int(n_rows), p, space), ctx)
+    return out
+
+
+def fw2_set_rows(ctx, field: str, row0: int, n_rows: int, arr):
+    """Rows along the slowest axis of p or v_q from `arr` (fw2_set_rows)."""
+    arr = np.ascontiguousarray(arr, np.float32) if isinstance(arr, np.ndarray) else arr
+    p, space, keep = _ptr(arr)
+    _check(lib().fw2_set_rows(ctx, FIELD[field], int(row0), int(n_rows), p, space), ctx)
 
 
 def fw2_get_step(ctx) -> int:
@@ -544,7 +574,7 @@ class Simulation:
     """
 
     def __init__(self, prob, map_precision: str = "f32", device_inputs: bool = False, stream=None,
-                 kernel_path: str = "auto"):
+                 kernel_path: str = "auto", subdomain=None):
         import torch
         self.prob = prob
         self.torch = torch
@@ -555,6 +585,8 @@ class Simulation:
                               kernel_path=kernel_path)
         self.ctx = fw2_create(self.cfg)
         try:
+            if subdomain is not None:          # (shape of the whole grid, offset of this one)
+                fw2_set_subdomain(self.ctx, subdomain[0], subdomain[1])
             conv = (lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()) \
                 if device_inputs else (lambda a: a)
             if map_precision == "idx":
