@@ -590,16 +590,27 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
     for (int e = 0; e < 2; ++e) el2(Sd[a], e) = el2(D[a], e) * el2(k1, e);
   const int xside = EDGE ? R.xs_side(x0) : -1;
   const bool ys = EDGE && R.ys_row(y0) != INT_MIN, zs = EDGE && R.zs_plane(k) >= 0;
+  // coefficients of every mechanism and axis first, C-PML strips included,
+  // so that the strip loads a staged-layout edge unit reads from global
+  // memory are all in flight together
+  float2 A[N > 0 ? N : 1][3], B[N > 0 ? N : 1][3];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
     const float2 a = sldh2(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
     const float2 b = sldb2(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
-    float2 A[3] = {a, a, a}, B[3] = {b, b, b};
-    if (EDGE) strips_of<N, 1, PS>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A, B);
+#pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3) {
+      A[nu][a3] = a;
+      B[nu][a3] = b;
+    }
+    if (EDGE) strips_of<N, 1, PS>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A[nu], B[nu]);
+  }
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
     float2 qq[3];
 #pragma unroll
     for (int a3 = 0; a3 < 3; ++a3) qq[a3] = PS ? sld2(st + S::oPsi + (a3 * N + nu) * kArr + o) : q[a3][nu];
-    relax3(P, P.psi1, nu * Sn + c, i0, EDGE, qq, A, B, D, Sd);
+    relax3(P, P.psi1, nu * Sn + c, i0, EDGE, qq, A[nu], B[nu], D, Sd);
   }
   const Face3 f = face3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oRho), x0, y0, k, lx, ly);
   const float rr[3] = {f.r0, f.r1, f.r2}, ru[2] = {f.u0, f.u1}, rz[2] = {f.z0, f.z1};
@@ -740,16 +751,27 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 
     for (int e = 0; e < 2; ++e) el2(Sd[a], e) = el2(D[a], e) * el2(k2, e);
   const int xside = EDGE ? R.xs_side(x0) : -1;
   const bool ys = EDGE && R.ys_row(y0) != INT_MIN, zs = EDGE && R.zs_plane(k) >= 0;
+  // coefficients of every mechanism and axis first, C-PML strips included,
+  // so that the strip loads a staged-layout edge unit reads from global
+  // memory are all in flight together
+  float2 A[N > 0 ? N : 1][3], B[N > 0 ? N : 1][3];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
     const float2 a = sldh2(reinterpret_cast<const bf16 *>(st + S::oA) + nu * kArr + o);
     const float2 b = sldb2(reinterpret_cast<const bf16 *>(st + S::oB) + nu * kArr + o);
-    float2 A[3] = {a, a, a}, B[3] = {b, b, b};
-    if (EDGE) strips_of<N, 2, PS>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A, B);
+#pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3) {
+      A[nu][a3] = a;
+      B[nu][a3] = b;
+    }
+    if (EDGE) strips_of<N, 2, PS>(P, R, st + S::oS, xside, ys, zs, nu, i0, j, k, ly, lx, A[nu], B[nu]);
+  }
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
     float2 qq[3];
 #pragma unroll
     for (int a3 = 0; a3 < 3; ++a3) qq[a3] = PS ? sld2(st + S::oPsi + (a3 * N + nu) * kArr + o) : q[a3][nu];
-    relax3(P, P.psi2, nu * Sn + c, i0, EDGE, qq, A, B, D, Sd);
+    relax3(P, P.psi2, nu * Sn + c, i0, EDGE, qq, A[nu], B[nu], D, Sd);
   }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
