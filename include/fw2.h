@@ -267,21 +267,24 @@ fw2_status fw2_set_watch(fw2_ctx *ctx, int64_t every, float bound);
 
 /* ---- batches ---------------------------------------------------------- */
 
-/* Many 2D contexts advanced together: the transmit events of a full
+/* Many contexts advanced together: the transmit events of a full
  * synthetic aperture sequence (appendix, abdominal wall imaging: one
  * simulation per transmitting element) or the requests of a serving loop.
  * Each context computes exactly what fw2_step computes for it alone; the
- * batch runs one persistent launch per half step over a tile table of all
- * contexts (grouped by mechanism count and map kind), one launch each for
+ * batch runs one persistent launch per half step over a work table of all
+ * contexts (grouped by dimension, mechanism count and map kind, in 3D also
+ * by the cross taps and the layout of each half step), one launch each for
  * the sources and recordings of all contexts, and replays chunks of steps
  * as a captured CUDA graph.  The first batch step warms up; the next twelve
  * time four launch configurations (persistent grid size x tile order),
  * three steps each, and the one with the fastest median is kept; every
  * configuration computes the same result. */
 typedef struct fw2_batch fw2_batch;
-/* Contexts are borrowed (they must outlive the batch), 2D, with medium set;
+/* Contexts are borrowed (they must outlive the batch), with medium set;
  * their coefficient maps and sources are built here.  Re-create the batch
- * after changing a context's sources or recording.  EUNSUPPORTED for 3D. */
+ * after changing a context's sources or recording.  3D contexts join on the
+ * pipelined path only (bf16 maps, N <= 3, no periodic axis; EUNSUPPORTED
+ * otherwise), each half step in its default layout. */
 fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out);
 /* Advance every context by n_steps (each from its own step counter), on the
  * batch's own stream after the contexts' streams have drained; asynchronous

@@ -86,6 +86,14 @@ __global__ void batch_tick_kernel(long long *steps, int n_ctx) {
 struct Group {
   int n_relax, map_kind;
   std::vector<int> members;
+  // 3D groups (pipelined, bf16 maps): contexts sharing N, the cross taps and
+  // the layout of each half step; per half step a work-layout record per
+  // context and the item table {context, item}
+  int nd = 2;
+  bool cross = false, ps[2] = {false, false};
+  unsigned char *d_regions[2] = {nullptr, nullptr};
+  int2 *d_items[2] = {nullptr, nullptr};
+  int n_items[2] = {0, 0};
   StepParams *d_params = nullptr;
   int4 *d_tiles[2] = {nullptr, nullptr};  // context-major, interleaved
   int n_tiles = 0;
@@ -165,7 +173,10 @@ fw2_status enqueue_step(fw2_batch *b, int grid, int order) {
   for (int half = 0; half < 2; ++half) {
     const bool vel = half == 0;
     for (Group &g : b->groups) {
-      if (g.pipe)
+      if (g.nd == 3)
+        BCK(b, launch_pipe3d_batched(vel, g.cross, g.ps[half], g.n_relax, g.d_params, g.d_regions[half],
+                                     g.d_maps[half], g.d_items[half], g.n_items[half], b->n_sm, b->stream));
+      else if (g.pipe)
         BCK(b, launch_pipe2d_batched(vel, g.d_params, g.d_maps[vel ? 0 : 1], g.d_units, g.n_units, g.n_relax,
                                      g.map_kind, b->n_sm, b->stream));
       else
@@ -216,19 +227,57 @@ fw2_status build_tables(fw2_batch *b) {
     b->d_prefix[k] = nullptr;
     b->total[k] = 0;
   }
-  // groups by (mechanism count, map kind); members index b->active
+  // groups by (dimension, mechanism count, map kind; in 3D the cross taps
+  // and the layouts); members index b->active
   for (int i = 0; i < (int)b->active.size(); ++i) {
     fw2_ctx *c = b->ctxs[b->active[i]];
-    auto it = std::find_if(b->groups.begin(), b->groups.end(),
-                           [&](const Group &g) { return g.n_relax == c->N && g.map_kind == c->map_kind; });
+    const bool cross = c->nd == 3 && c->P.g11h != 0.f;
+    const bool ps0 = c->nd == 3 && pipe3d_staged_layout(true, c->P), ps1 = c->nd == 3 && pipe3d_staged_layout(false, c->P);
+    auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const Group &g) {
+      return g.nd == c->nd && g.n_relax == c->N && g.map_kind == c->map_kind && g.cross == cross && g.ps[0] == ps0 &&
+             g.ps[1] == ps1;
+    });
     if (it == b->groups.end()) {
-      b->groups.push_back(Group{c->N, c->map_kind, {}});
+      Group g{c->N, c->map_kind, {}};
+      g.nd = c->nd;
+      g.cross = cross;
+      g.ps[0] = ps0;
+      g.ps[1] = ps1;
+      b->groups.push_back(g);
       it = b->groups.end() - 1;
     }
     it->members.push_back(i);
   }
   fw2_status st = FW2_OK;
   for (Group &g : b->groups) {
+    if (g.nd == 3) {
+      std::vector<StepParams> params;
+      std::vector<PipeMaps> mv, mp;
+      std::vector<unsigned char> reg[2];
+      std::vector<int2> items[2];
+      const size_t rb = pipe3d_region_bytes();
+      for (int m = 0; m < (int)g.members.size(); ++m) {
+        fw2_ctx *c = b->ctxs[b->active[g.members[m]]];
+        params.push_back(c->P);
+        mv.push_back(c->tm_vel);
+        mp.push_back(c->tm_prs);
+        for (int h = 0; h < 2; ++h) {
+          reg[h].resize((m + 1) * rb);
+          const long long n = pipe3d_region(c->P, b->n_sm, h == 0, reg[h].data() + m * rb);
+          for (long long t = 0; t < n; ++t) items[h].push_back(make_int2(m, (int)t));
+        }
+      }
+      if ((st = bupload(b, params, &g.d_params)) != FW2_OK) break;
+      if ((st = bupload(b, mv, &g.d_maps[0])) != FW2_OK) break;
+      if ((st = bupload(b, mp, &g.d_maps[1])) != FW2_OK) break;
+      for (int h = 0; h < 2 && st == FW2_OK; ++h) {
+        g.n_items[h] = (int)items[h].size();
+        if ((st = bupload(b, reg[h], &g.d_regions[h])) != FW2_OK) break;
+        st = bupload(b, items[h], &g.d_items[h]);
+      }
+      if (st != FW2_OK) break;
+      continue;
+    }
     std::vector<StepParams> params;
     std::vector<std::vector<int4>> per;
     for (int m = 0; m < (int)g.members.size(); ++m) {
@@ -323,12 +372,14 @@ fw2_status fw2_batch_create(fw2_ctx *const *ctxs, int32_t n_ctx, fw2_batch **out
   if (!b) return FW2_ENOMEM;
   for (int i = 0; i < n_ctx; ++i) {
     fw2_ctx *c = ctxs[i];
-    if (!c || c->nd != 2) {
-      fw2_status st = c ? ctx_fail(c, FW2_EUNSUPPORTED, "batches hold 2D contexts") : FW2_EINVAL;
+    if (!c) {
       delete b;
-      return st;
+      return FW2_EINVAL;
     }
     fw2_status st = ctx_prepare(c);
+    if (st == FW2_OK && c->nd == 3 && !c->pipe)
+      st = ctx_fail(c, FW2_EUNSUPPORTED,
+                    "3D contexts join a batch on the pipelined path only (bf16 maps, N <= 3, no periodic axis)");
     if (st != FW2_OK) {
       delete b;
       return st;

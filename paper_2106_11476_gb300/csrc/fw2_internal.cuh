@@ -145,6 +145,17 @@ bool pipe3d_layout_allowed(bool vel, const StepParams &P, int layout);
 cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs, const char **why);
 cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t s,
                           int layout = kLayoutDefault);
+// batched form: per context the parameters, the work layout (an opaque
+// record of pipe3d_region_bytes(), written by pipe3d_region, which returns
+// the context's item count) and the tensor maps, in device memory; items
+// {context, item}; the layout of every context is the default one
+// (pipe3d_staged_layout), which must agree within a launch
+size_t pipe3d_region_bytes();
+long long pipe3d_region(const StepParams &P, int grid, bool vel, void *out);
+bool pipe3d_staged_layout(bool vel, const StepParams &P);
+cudaError_t launch_pipe3d_batched(bool vel, bool cross, bool ps, int n_relax, const StepParams *Ps,
+                                  const void *Rs, const PipeMaps *Ts, const int2 *items, int n_items, int grid,
+                                  cudaStream_t s);
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
 

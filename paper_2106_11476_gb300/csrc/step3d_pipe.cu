@@ -32,6 +32,7 @@
 // along y) and store nothing outside the grid.  Periodic axes are not taken
 // by this path (the tile kernels run them).
 #include <climits>
+#include <cstring>
 
 #include "async.cuh"
 #include "coef.cuh"
@@ -888,6 +889,161 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// The same half step for several contexts in one launch (a batch of 3D
+// problems): a table of work items {context, item of that context}; each
+// block takes a contiguous run of the table, so consecutive items mostly
+// share a context, whose parameters and work layout it keeps in shared
+// memory (the tensor maps stay in global memory).  A new item always reloads
+// the plane rings; the next item's first copies are issued after the
+// current item's last unit, as in the single-context kernel.
+template <int N, bool VEL, bool CROSS, bool PS>
+__global__ void __launch_bounds__(kThreads, 1)
+    pipe3d_batched_kernel(const StepParams *Ps, const Region3 *Rs, const PipeMaps *Ts, const int2 *items,
+                          int n_items) {
+  using G = Ring3<N, VEL, CROSS, PS>;
+  constexpr int kStage = G::kStage;
+  extern __shared__ __align__(128) float smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int ok[2];
+  __shared__ __align__(16) StepParams sP;
+  __shared__ __align__(16) Region3 sR;
+  float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float *ring = smem + 2 * kStage;
+  float *sub = ring + kSlots * G::kPlane;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int h_end = (int)(((long long)n_items * (blockIdx.x + 1)) / gridDim.x);
+  int h = (int)(((long long)n_items * blockIdx.x) / gridDim.x);
+  if (h >= h_end) return;
+  auto load_ctx = [&](int c) {  // every thread; callers put barriers around it
+    const int *ps = reinterpret_cast<const int *>(Ps + c);
+    int *pd = reinterpret_cast<int *>(&sP);
+    for (int w = tid; w < (int)(sizeof(StepParams) / 4); w += kThreads) pd[w] = __ldg(ps + w);
+    const int *rs = reinterpret_cast<const int *>(Rs + c);
+    int *rd = reinterpret_cast<int *>(&sR);
+    for (int w = tid; w < (int)(sizeof(Region3) / 4); w += kThreads) rd[w] = __ldg(rs + w);
+  };
+  int2 e = items[h];
+  int ctx = e.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbarrier_init();
+  }
+  load_ctx(ctx);
+  __syncthreads();
+  int x0, y0, k0, k1;
+  sR.item(e.y, x0, y0, k0, k1);
+  int k = k0;
+  unsigned phase = 0, pending = 0;
+  bool nl = sP.nl != 0, nlv = VEL && sP.nl_vel != 0;
+  if (tid == 0)
+    issue3<N, VEL, CROSS, PS>(Ts[ctx], sR, smem, ring, sub, &bar[0], x0, y0, k, ring_first<VEL>(k),
+                              ring_first<VEL>(k) + 7, k - 1, k + 1, nl, nlv);
+  pending |= 1u;
+  const int lx = 2 * (tid & 63), ly = tid >> 6;
+  auto psi_of = [&](const StepParams &Q, int ux0, int uy0, int uk, Psi<N> &q) {
+    const int i0 = ux0 + lx, j = uy0 + ly;
+    load_psi<N>(VEL ? Q.psi1 : Q.psi2, Q.npts_alloc, (long long)uk * Q.plane + (long long)j * Q.pitch + i0,
+                i0 < Q.nx && j < Q.ny, q);
+  };
+  Psi<N> qc, qn;
+  if (!PS) psi_of(sP, x0, y0, k, qc);
+  int s = 0;
+#pragma unroll 1
+  while (true) {
+    if (tid == 0) ok[s] = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    __syncthreads();
+    if (!ok[s]) {
+      if (tid == 0) {
+        report_status(sP.status, kStatusWaitTimeout);
+        if ((pending >> (s ^ 1)) & 1u) mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u);
+      }
+      return;
+    }
+    phase ^= 1u << s;
+    pending &= ~(1u << s);
+    // the next unit: the next plane of this item, or the first of the next item
+    int nh = h, nctx = ctx, nx0 = x0, ny0 = y0, nk0 = k0, nk1 = k1, nk = k + 1;
+    if (nk >= k1) {
+      nh = h + 1;
+      if (nh < h_end) {
+        const int2 en = items[nh];
+        nctx = en.x;
+        Rs[nctx].item(en.y, nx0, ny0, nk0, nk1);
+      }
+      nk = nk0;
+    }
+    const bool more = nh < h_end, fresh = nh != h;
+    const int q = s ^ 1;
+    if (more && !fresh) {
+      if (tid < 32) {
+        const int kp = ring_first<VEL>(nk) + 7;
+        if (tid == 0)
+          issue3<N, VEL, CROSS, PS>(Ts[ctx], sR, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk, kp, kp,
+                                    nk + 1, nk + 1, nl, nlv);
+        if (!sR.interior(nx0, ny0, nk)) prefetch_strips<N, VEL ? 1 : 2>(sP, sR, nx0, ny0, nk, tid);
+      }
+      pending |= 1u << q;
+    }
+    if (!PS && more) psi_of(nctx == ctx ? sP : Ps[nctx], nx0, ny0, nk, qn);
+    float *cur = smem + s * kStage;
+    if (sR.interior(x0, y0, k)) {
+      if (VEL) vel3_compute<N, false, CROSS, PS>(sP, sR, cur, ring, x0, y0, k, tid, qc);
+      else prs3_compute<N, false, CROSS, PS>(sP, sR, cur, ring, sub, x0, y0, k, tid, qc);
+    } else {
+      if (VEL) vel3_compute<N, true, CROSS, PS>(sP, sR, cur, ring, x0, y0, k, tid, qc);
+      else prs3_compute<N, true, CROSS, PS>(sP, sR, cur, ring, sub, x0, y0, k, tid, qc);
+    }
+    if (!more) break;
+    if (fresh) {  // a new item: every thread is done with the rings (and the context's parameters)
+      __syncthreads();
+      if (nctx != ctx) {
+        load_ctx(nctx);
+        __syncthreads();
+        ctx = nctx;
+        nl = sP.nl != 0;
+        nlv = VEL && sP.nl_vel != 0;
+      }
+      if (tid == 0)
+        issue3<N, VEL, CROSS, PS>(Ts[ctx], sR, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk,
+                                  ring_first<VEL>(nk), ring_first<VEL>(nk) + 7, nk - 1, nk + 1, nl, nlv);
+      pending |= 1u << q;
+    }
+    h = nh;
+    x0 = nx0; y0 = ny0; k0 = nk0; k1 = nk1; k = nk;
+    s = q;
+    if (!PS) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int nu = 0; nu < N; ++nu) qc[a][nu] = qn[a][nu];
+    }
+  }
+}
+
+template <int N, bool VEL, bool CROSS, bool PS>
+cudaError_t pipe3_batched_launch(const StepParams *Ps, const Region3 *Rs, const PipeMaps *Ts, const int2 *items,
+                                 int n_items, int grid, cudaStream_t st) {
+  constexpr size_t bytes = Ring3<N, VEL, CROSS, PS>::kBytes;
+  cudaError_t e = cudaFuncSetAttribute(pipe3d_batched_kernel<N, VEL, CROSS, PS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  pipe3d_batched_kernel<N, VEL, CROSS, PS><<<grid, dim3(32, kThreads / 32), bytes, st>>>(Ps, Rs, Ts, items, n_items);
+  return cudaGetLastError();
+}
+
+template <bool VEL, bool CROSS, bool PS>
+cudaError_t pipe3_batched_dispatch(int n_relax, const StepParams *Ps, const Region3 *Rs, const PipeMaps *Ts,
+                                   const int2 *items, int n_items, int grid, cudaStream_t st) {
+  switch (n_relax) {
+    case 0: return pipe3_batched_launch<0, VEL, CROSS, PS>(Ps, Rs, Ts, items, n_items, grid, st);
+    case 1: return pipe3_batched_launch<1, VEL, CROSS, PS>(Ps, Rs, Ts, items, n_items, grid, st);
+    case 2: return pipe3_batched_launch<2, VEL, CROSS, PS>(Ps, Rs, Ts, items, n_items, grid, st);
+    case 3: return pipe3_batched_launch<3, VEL, CROSS, PS>(Ps, Rs, Ts, items, n_items, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int N, bool VEL, bool CROSS, bool PS>
 cudaError_t pipe3_launch(const StepParams &P, const Region3 &R, int grid, const PipeMaps &T, cudaStream_t st) {
   constexpr size_t bytes = Ring3<N, VEL, CROSS, PS>::kBytes;
@@ -1063,6 +1219,30 @@ cudaError_t build_pipe3d_maps(const StepParams &P, PipeMaps *vel, PipeMaps *prs,
 
 bool pipe3d_layout_allowed(bool vel, const StepParams &P, int layout) {
   return layout != kLayoutStaged || psi_staged(vel, P);
+}
+
+size_t pipe3d_region_bytes() { return sizeof(Region3); }
+
+long long pipe3d_region(const StepParams &P, int grid, bool vel, void *out) {
+  const Region3 R = region3_of(P, grid, psi_staged(vel, P));
+  std::memcpy(out, &R, sizeof R);
+  return (long long)R.tnx * R.nhy * R.nseg;
+}
+
+bool pipe3d_staged_layout(bool vel, const StepParams &P) { return psi_staged(vel, P); }
+
+cudaError_t launch_pipe3d_batched(bool vel, bool cross, bool ps, int n_relax, const StepParams *Ps,
+                                  const void *Rs, const PipeMaps *Ts, const int2 *items, int n_items, int grid,
+                                  cudaStream_t st) {
+  const Region3 *R = static_cast<const Region3 *>(Rs);
+  if (cross)
+    return vel ? pipe3_batched_dispatch<true, true, false>(n_relax, Ps, R, Ts, items, n_items, grid, st)
+               : pipe3_batched_dispatch<false, true, false>(n_relax, Ps, R, Ts, items, n_items, grid, st);
+  if (vel)
+    return ps ? pipe3_batched_dispatch<true, false, true>(n_relax, Ps, R, Ts, items, n_items, grid, st)
+              : pipe3_batched_dispatch<true, false, false>(n_relax, Ps, R, Ts, items, n_items, grid, st);
+  return ps ? pipe3_batched_dispatch<false, false, true>(n_relax, Ps, R, Ts, items, n_items, grid, st)
+            : pipe3_batched_dispatch<false, false, false>(n_relax, Ps, R, Ts, items, n_items, grid, st);
 }
 
 cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t st, int layout) {

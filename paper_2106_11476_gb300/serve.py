@@ -3,12 +3,12 @@
 Simulation requests (2D or 3D problems with a step count) arrive over time.
 The server admits waiting requests in arrival order while their device
 footprint fits under a memory cap, keeps their state resident, and advances
-all active requests in slices: the 2D requests together as one fw2 batch
-(one persistent launch per half step for all of them, rebuilt when the set of
-active requests changes; each request's remaining steps are its budget, so a
-slice is not cut short for the others when one request ends inside it), the
-3D requests each on its own stream so that their work overlaps on the
-device.  A request's result is its sensor trace;
+all active requests in slices: the 2D requests and the 3D requests with
+bf16 maps together as one fw2 batch (one persistent launch per half step
+and group for all of them, rebuilt when the set of active requests changes;
+each request's remaining steps are its budget, so a slice is not cut short
+for the others when one request ends inside it), other 3D requests each on
+its own stream.  A request's result is its sensor trace;
 it leaves when its last step is done, freeing memory for waiting requests.
 Every request computes exactly what it would compute alone.
 """
@@ -55,6 +55,12 @@ def footprint_bytes(prob, maps: str) -> int:
     return state + mp + strips
 
 
+def batchable(r: Request) -> bool:
+    """2D requests, and 3D requests on the pipelined path (bf16 maps), join
+    the batch; the others step on their own."""
+    return len(r.problem.shape) == 2 or r.maps == "bf16"
+
+
 class Server:
     def __init__(self, cap_bytes: float = 160e9, slice_steps: int = 100,
                  clock: Callable[[], float] = time.perf_counter):
@@ -81,7 +87,7 @@ class Server:
                 if used + fp > self.cap and active:
                     break
                 pending.pop(0)
-                stream = torch.cuda.Stream() if len(r.problem.shape) == 3 else torch.cuda.current_stream()
+                stream = torch.cuda.current_stream() if batchable(r) else torch.cuda.Stream()
                 sim = fw2.Simulation(r.problem, map_precision=r.maps, stream=stream)
                 r.admitted = self.clock() - t0
                 active.append((r, sim, r.steps, fp))
@@ -92,8 +98,8 @@ class Server:
                     if wait > 0:
                         time.sleep(min(wait, 0.01))
                 continue
-            two = [a for a in active if len(a[0].problem.shape) == 2]
-            three = [a for a in active if len(a[0].problem.shape) == 3]
+            two = [a for a in active if batchable(a[0])]
+            three = [a for a in active if not batchable(a[0])]
             step2 = min(self.slice, max([a[2] for a in two], default=0))
             members = tuple(a[0].rid for a in two)
             if two and members != batch_members:
@@ -114,13 +120,13 @@ class Server:
                 fw2.fw2_batch_synchronize(batch)
             for a in three:
                 a[1].synchronize()
-            self.launch_log.append({"t": self.clock() - t0, "n2d": len(two), "n3d": len(three), "steps2d": step2})
+            self.launch_log.append({"t": self.clock() - t0, "n_batch": len(two), "n_own": len(three), "steps": step2})
             # bookkeeping
             new_active = []
             i3 = 0
             for a in active:
                 r, sim, rem, fp = a
-                if len(r.problem.shape) == 2:
+                if batchable(r):
                     rem -= min(step2, rem)
                 else:
                     rem -= steps3[i3]

@@ -66,12 +66,48 @@ def test_batch_equals_each_context_alone(fw2):
             s.close()
 
 
-def test_batch_rejects_3d(fw2):
+def test_batch_rejects_3d_contexts_off_the_pipelined_path(fw2):
     from tests.test_gpu_parity import small_3d
-    s = fw2.Simulation(small_3d(steps=5))
+    s = fw2.Simulation(small_3d(steps=5))            # float maps: tile kernels only
     with pytest.raises(fw2.Fw2Error):
         fw2.fw2_batch_create([s.ctx])
     s.close()
+
+
+def test_3d_contexts_in_a_batch_equal_each_alone(fw2):
+    """3D contexts (bf16 maps) of different sizes, mechanism counts, with and
+    without the cross taps and the literal system, batched with 2D ones and
+    uneven budgets: each holds bitwise what it holds alone."""
+    from tests.test_gpu_parity import small_2d, small_3d
+    probs = [("bf16", small_3d(n=(150, 44, 40), N=3, nl="westervelt", steps=60)),
+             ("bf16", small_3d(n=(90, 70, 30), N=2, nl="off", steps=60, seed=5)),
+             ("bf16", small_3d(n=(130, 40, 36), N=3, nl="literal", steps=60, seed=7)),
+             ("bf16", small_3d(n=(100, 50, 32), N=3, nl="pressure", steps=60, seed=9)),
+             ("f32", small_2d(nx=200, ny=136, N=2, steps=60))]
+    r = float(np.max(probs[3][1].c)) * probs[3][1].dt / probs[3][1].h
+    probs[3][1].taps = tuple(fw2.fw2_taps_time_space(r, 3))
+    budgets = [60, 41, 60, 52, 33]
+    alone = []
+    for (maps, p), n in zip(probs, budgets):
+        s = fw2.Simulation(p, map_precision=maps)
+        s.step(n)
+        alone.append((s.field("p"), s.field("vx"), s.trace.cpu().numpy()[:n]))
+        s.close()
+    sims = [fw2.Simulation(p, map_precision=maps) for maps, p in probs]
+    batch = fw2.fw2_batch_create([s.ctx for s in sims])
+    try:
+        fw2.fw2_batch_set_budget(batch, budgets)
+        fw2.fw2_batch_step(batch, 100)
+        fw2.fw2_batch_synchronize(batch)
+        for s, n, (p_ref, vx_ref, tr_ref) in zip(sims, budgets, alone):
+            assert fw2.fw2_get_step(s.ctx) == n
+            np.testing.assert_array_equal(s.field("p"), p_ref)
+            np.testing.assert_array_equal(s.field("vx"), vx_ref)
+            np.testing.assert_array_equal(s.trace.cpu().numpy()[:n], tr_ref)
+    finally:
+        fw2.fw2_batch_destroy(batch)
+        for s in sims:
+            s.close()
 
 
 def test_batch_full_size_equals_each_context_alone(fw2):

@@ -24,10 +24,11 @@ def test_served_results_equal_alone(fw2):
                                                 pml_lambda=(1.0, 0.5))),
         ("f32", small_2d(nx=128, ny=96, N=4, steps=55, pml=(6, 2))),
         ("f32", small_3d(n=(40, 36, 32), steps=50)),
+        ("bf16", small_3d(n=(140, 40, 30), N=2, nl="off", steps=40, seed=6)),   # joins the batch
     ]
     reqs = [Request(i, arrival=0.004 * i, problem=p, steps=p.n_steps, maps=m) for i, (m, p) in enumerate(probs)]
     done = Server(cap_bytes=2e9, slice_steps=16).run(reqs)
-    assert sorted(r.rid for r in done) == [0, 1, 2, 3]
+    assert sorted(r.rid for r in done) == [0, 1, 2, 3, 4]
     for r in done:
         alone = fw2.Simulation(r.problem, map_precision=r.maps)
         alone.step(r.steps)
@@ -46,4 +47,4 @@ def test_admission_respects_the_memory_cap(fw2):
     srv = Server(cap_bytes=2.5 * fp, slice_steps=10)
     done = srv.run(reqs)
     assert len(done) == 4
-    assert max(e["n2d"] for e in srv.launch_log) <= 2
+    assert max(e["n_batch"] for e in srv.launch_log) <= 2

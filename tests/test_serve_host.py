@@ -1,8 +1,8 @@
 """Host logic of the serving loop (serve.py) on the CPU, with the library
 calls replaced by fakes that count steps: admission in arrival order under
-the memory cap, slices of at most `slice_steps`, 2D requests advanced
-together as one batch (rebuilt when the set changes), 3D requests on their
-own, every request stepped exactly its step count."""
+the memory cap, slices of at most `slice_steps`, 2D and bf16 3D requests
+advanced together as one batch (rebuilt when the set changes), other 3D
+requests on their own, every request stepped exactly its step count."""
 import types
 
 import numpy as np
@@ -28,6 +28,7 @@ class _Sim:
 
     def __init__(self, prob, map_precision="f32", stream=None):
         self.prob = prob
+        self.maps = map_precision
         self.ctx = object()
         self.steps = 0
         self.closed = False
@@ -35,7 +36,7 @@ class _Sim:
         _Sim.peak = max(_Sim.peak, _Sim.live)
 
     def step(self, k):
-        assert len(self.prob.shape) == 3, "2D requests advance through the batch"
+        assert self.maps != "bf16" and len(self.prob.shape) == 3, "batchable requests advance through the batch"
         self.steps += k
 
     def synchronize(self):
@@ -104,10 +105,10 @@ def test_every_request_runs_its_steps_in_slices(monkeypatch):
     assert sorted(r.rid for r in done) == [0, 1, 2, 3]
     for r in done:
         assert r.trace[0] == r.steps and r.finished >= r.admitted >= r.arrival
-    assert all(e["steps2d"] <= 100 for e in srv.launch_log)
-    # slices are not cut short by the request that ends first: 2D slices of
+    assert all(e["steps"] <= 100 for e in srv.launch_log)
+    # slices are not cut short by the request that ends first: batch slices of
     # 100, 100, 50 (rid 3 stops at 75, rid 1 at 120 inside them)
-    assert [e["steps2d"] for e in srv.launch_log if e["n2d"]] == [100, 100, 50]
+    assert [e["steps"] for e in srv.launch_log if e["n_batch"]] == [100, 100, 50]
     # the 2D set changed as requests finished: batches of 3, then 2 (rid 3 left), then 1
     assert [len(b) for b in batches] == [3, 2, 1]
     assert _Sim.live == 0
