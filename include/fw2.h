@@ -26,6 +26,11 @@
  *    thread-safe; distinct contexts are independent.
  *  - All device work of a context runs on the stream given in fw2_config
  *    (NULL: the legacy default stream).  fw2_step is asynchronous.
+ *  - Device memory of the contexts comes from a stream-ordered memory pool
+ *    the library keeps per device: memory a destroyed context returns stays
+ *    in the pool for the next context of the process (contexts created one
+ *    after another do not map fresh memory each time) until
+ *    fw2_release_memory returns it to the driver.
  */
 #ifndef FW2_H
 #define FW2_H
@@ -451,6 +456,9 @@ fw2_status fw2_kernel_path(fw2_ctx *ctx, int32_t *path);
  * variables staged, 2 in registers, 0 before the choice (or not a 3D
  * pipelined context). */
 fw2_status fw2_pipe_layout(fw2_ctx *ctx, int32_t *vel, int32_t *prs);
+/* Return the free memory of the library's pool on the current device to
+ * the driver (synchronises the device). */
+fw2_status fw2_release_memory(void);
 /* Bytes of device memory held by the context. */
 fw2_status fw2_device_bytes(fw2_ctx *ctx, int64_t *bytes);
 /* Launches of library kernels since creation (all kinds). */

@@ -1,6 +1,7 @@
 // C ABI of libfw2 (declared in include/fw2.h): context management, input
 // validation and staging, device coefficient build, the time-step loop.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -45,24 +46,64 @@ fw2_status cuda_fail(fw2_ctx *c, cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
+// Device memory of the contexts comes from a stream-ordered pool the library
+// owns, one per device: what a destroyed context (or a finished coefficient
+// build) returns stays in the pool for the next allocation of the process
+// instead of going back to the driver, so contexts created one after another
+// (the transmit events of a sequence, served requests) do not map fresh
+// memory each time.  fw2_release_memory hands the pool's free memory back.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaError_t pool_of_current_device(cudaMemPool_t *pool) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    unsigned long long keep = ~0ull;  // keep freed memory for reuse
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return e;
+    }
+    g_pool[dev] = p;
+  }
+  *pool = g_pool[dev];
+  return cudaSuccess;
+}
+
 fw2_status dalloc(fw2_ctx *c, size_t bytes, void **out) {
   *out = nullptr;
   if (bytes == 0) bytes = 256;
-  cudaError_t e = cudaMalloc(out, bytes);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = pool_of_current_device(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(out, bytes, pool, c->stream);
   if (e != cudaSuccess) {
     *out = nullptr;
-    return fail(c, FW2_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return fail(c, FW2_ENOMEM, "allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
   c->allocs.push_back(*out);
   c->dev_bytes += (long long)bytes;
   return FW2_OK;
 }
 
+// returned to the pool in stream order: work already queued on the context
+// stream that reads the buffer completes first
 void dfree(fw2_ctx *c, void *p) {
   if (!p) return;
   auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
   if (it != c->allocs.end()) c->allocs.erase(it);
-  cudaFree(p);
+  cudaFreeAsync(p, c->stream);
 }
 
 // copy n floats (or other POD) from host or device into a device buffer
@@ -682,9 +723,22 @@ fw2_status fw2_destroy(fw2_ctx *c) {
   cudaStreamSynchronize(c->stream);
   release_events(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  for (void *p : c->allocs) cudaFree(p);
+  for (void *p : c->allocs) cudaFreeAsync(p, c->stream);
   c->allocs.clear();
+  cudaStreamSynchronize(c->stream);
   delete c;
+  return FW2_OK;
+}
+
+fw2_status fw2_release_memory(void) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = pool_of_current_device(&pool);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+  if (e != cudaSuccess) {
+    fw2::set_global_error(cudaGetErrorString(e));
+    return FW2_ECUDA;
+  }
   return FW2_OK;
 }
 

@@ -96,6 +96,7 @@ EXPORTS = {
     "fw2_synchronize": (C.c_int, [C.c_void_p]),
     "fw2_check_field": (C.c_int, [C.c_void_p, C.c_float, C.POINTER(C.c_float)]),
     "fw2_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "fw2_release_memory": (C.c_int, []),
     "fw2_kernel_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "fw2_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "fw2_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
@@ -332,6 +333,11 @@ def fw2_check_field(ctx, bound: float):
     m = C.c_float()
     st = lib().fw2_check_field(ctx, C.c_float(bound), C.byref(m))
     return st, m.value
+
+
+def fw2_release_memory():
+    """Give the free memory of the library's device pool back (fw2_release_memory)."""
+    _check(lib().fw2_release_memory())
 
 
 def fw2_device_bytes(ctx) -> int:

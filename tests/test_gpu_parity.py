@@ -716,3 +716,26 @@ def test_cfl_time_step_matches_oracle_rule(fw2):
     prob.dt = 0.0
     sim = fw2.Simulation(prob)
     assert abs(sim.dt / cf.cfl_time_step(prob, 0.4) - 1) < 1e-15
+
+
+def test_context_memory_is_reused_and_released(fw2):
+    """Device memory comes from the library's pool: a context created after
+    another of the same size was destroyed takes no new memory from the
+    driver, and fw2_release_memory gives the pool's free memory back."""
+    import torch
+    prob = small_2d(nx=512, ny=400, N=4, steps=5)
+    s = fw2.Simulation(prob)
+    s.step(2)
+    s.close()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    s = fw2.Simulation(prob)
+    s.step(2)
+    s.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    held = fw2.fw2_device_bytes(s.ctx)
+    s.close()
+    assert free1 == free0
+    fw2.fw2_release_memory()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 >= free0 + held // 2
