@@ -658,38 +658,66 @@ def batch_problems(args, rank):
     return probs, budgets
 
 
+def batch_order(probs, budgets):
+    """Shortest work (cells x steps) first: the order both forms take the
+    problems in, the one that minimises the mean time to result of a
+    sequence run at a fixed rate."""
+    return sorted(range(len(probs)), key=lambda i: (probs[i].n_pts * budgets[i], i))
+
+
 def batch_measurement(args, rank, world, dist):
     """Batched tissue-index form vs the plain form (dense float maps, one
     context at a time) on the same 80 problems with the same uneven step
-    budgets.  Contexts leave the batch when their budget is spent; each one's
-    time to result is taken when the batch step it finishes in completes."""
+    budgets, both taking them shortest work first.  The batch admits
+    problems in that order while fewer than --batch-cells cells are active
+    (paused ones have a budget equal to their step counter), and a problem
+    leaves when its budget is spent; each one's time to result is taken when
+    the batch step it finishes in completes."""
     import torch
     from paper_2106_11476_gb300 import fw2
     probs, budgets = batch_problems(args, rank)
+    order = batch_order(probs, budgets)
     work = sum(p.n_pts * n for p, n in zip(probs, budgets))
     sims = [fw2.Simulation(p, map_precision="idx") for p in probs]
     batch = fw2.fw2_batch_create([s.ctx for s in sims])
     warm = max(args.warmup, 13)                          # includes the 13 tuning steps
     fw2.fw2_batch_step(batch, warm)
     fw2.fw2_batch_synchronize(batch)
-    grid, order, l0 = fw2.fw2_batch_info(batch)
-    fw2.fw2_batch_set_budget(batch, [warm + n for n in budgets])
+    grid, tile_order, l0 = fw2.fw2_batch_info(batch)
+    at = [warm] * len(sims)                              # each context's step counter
+    last = [warm + n for n in budgets]
+    queue, active = list(order), []
+
+    def admit():
+        cells = sum(probs[i].n_pts for i in active)
+        while queue and (not active or cells + probs[queue[0]].n_pts <= args.batch_cells):
+            i = queue.pop(0)
+            active.append(i)
+            cells += probs[i].n_pts
+        live = set(active)
+        fw2.fw2_batch_set_budget(batch, [last[i] if i in live else at[i] for i in range(len(sims))])
+
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     finish = [None] * len(sims)
+    waves = 0
     with ClockSampler(device_id_for_smi()) as clk:
         t0 = time.perf_counter()
-        done = 0
-        while fw2.fw2_batch_active(batch) > 0:
-            nxt = min(n for n, f in zip(budgets, finish) if f is None) - done
+        admit()
+        while active:
+            nxt = min(last[i] - at[i] for i in active)
             fw2.fw2_batch_step(batch, nxt)
             fw2.fw2_batch_synchronize(batch)
-            done += nxt
             t = time.perf_counter() - t0
-            for i, n in enumerate(budgets):
-                if finish[i] is None and n <= done:
-                    finish[i] = t
+            for i in active:
+                at[i] += nxt
+            done = [i for i in active if at[i] >= last[i]]
+            for i in done:
+                finish[i] = t
+                active.remove(i)
+            waves += 1
+            admit()
         t_batch = time.perf_counter() - t0
     _, _, l1 = fw2.fw2_batch_info(batch)
     fw2.fw2_batch_destroy(batch)
@@ -697,10 +725,11 @@ def batch_measurement(args, rank, world, dist):
         s.close()
     del sims
     torch.cuda.empty_cache()
-    # plain form: the same problems and budgets, dense float maps, one after
-    # the other in the same order, each after a short warm-up of its own
-    t_plain, plain_finish = 0.0, []
-    for p, n in zip(probs, budgets):
+    # plain form: the same problems and budgets in the same order, dense
+    # float maps, one after the other, each after a short warm-up of its own
+    t_plain, plain_finish = 0.0, [None] * len(probs)
+    for i in order:
+        p, n = probs[i], budgets[i]
         s = fw2.Simulation(p, map_precision="f32")
         s.step(3)
         s.synchronize()
@@ -709,7 +738,7 @@ def batch_measurement(args, rank, world, dist):
         s.synchronize()
         t_plain += time.perf_counter() - t1
         s.close()
-        plain_finish.append(t_plain)
+        plain_finish[i] = t_plain
     t_batch = max_over_ranks(t_batch, dist)
     value = world * work / t_batch / 1e9
     if rank != 0:
@@ -720,17 +749,19 @@ def batch_measurement(args, rank, world, dist):
     return {"value": round(value, 4), "unit": UNIT, "steps": args.steps,
             "ms_per_step": round(t_batch / args.steps * 1e3, 4),
             "config": {"workload": "batched: 64 focused transmits over one 2048x1024 tissue-index medium (K steps "
-                                   "each) + 16 instances 512^2..1536^2 (K x U(0.25, 1) steps), contexts leave when "
-                                   "their budget is spent, one persistent launch per half step, graph-captured "
-                                   "step loop, autotuned launch", "cell_steps": work,
-                       "tuned_grid": grid, "tuned_order": order},
+                                   "each) + 16 instances 512^2..1536^2 (K x U(0.25, 1) steps), shortest work first, "
+                                   "at most %d active cells, contexts leave when their budget is spent, one "
+                                   "persistent launch per half step, graph-captured step loop, autotuned launch"
+                                   % args.batch_cells, "cell_steps": work,
+                       "active_cells_cap": args.batch_cells, "segments": waves,
+                       "tuned_grid": grid, "tuned_order": tile_order},
             "roofline": {"bound": "hbm", "kernel": "step (all kernels)", "unit": "GB/s",
                          "achieved": round(vb / t_batch / 1e9, 1), "peak": float(peaks["hbm_gbs"]),
                          "frac": round(vb / t_batch / 1e9 / float(peaks["hbm_gbs"]), 4),
                          "traffic": None},
             "plain_form": {"value": round(work / t_plain / 1e9, 4), "unit": UNIT,
-                           "how": "same problems and budgets, dense float maps, one context at a time in the "
-                                  "same order, each measured over its full budget"},
+                           "how": "same problems and budgets, dense float maps, one context at a time, "
+                                  "shortest work first, each measured over its full budget"},
             "time_to_result_s": {"batched_p50": round(float(np.percentile(finish, 50)), 3),
                                  "batched_p99": round(float(np.percentile(finish, 99)), 3),
                                  "plain_p50": round(float(np.percentile(plain_finish, 50)), 3),
@@ -887,6 +918,8 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serving: size and step scale")
     ap.add_argument("--slice", type=int, default=100, help="serving: steps per slice")
+    ap.add_argument("--batch-cells", type=int, default=16 << 20,
+                    help="batch: most cells advanced at once (admission in shortest-work-first order)")
     ap.add_argument("--workload", default="abdominal",
                     choices=["abdominal", "abdominal-idx", "skull", "plain", "batch", "serve"],
                     help="abdominal: 2D 4096^2 nonlinear (default); abdominal-idx: the same in tissue-index "

@@ -79,6 +79,13 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
+// a tensor map in global memory (written by a host copy before the launch,
+// possibly at an address an earlier table used): order that write before
+// this thread's tensor copies through the map
+__device__ __forceinline__ void fence_tensormap_acquire(const void *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(map) : "memory");
+}
+
 // Tiled tensor copies global -> shared through a tensor map (a kernel
 // parameter declared __grid_constant__): the box at element coordinates
 // (x, y[, z]) lands densely in shared memory (128-byte aligned destination),

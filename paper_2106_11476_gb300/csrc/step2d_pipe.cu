@@ -765,11 +765,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   int h = (int)(((long long)n_units * blockIdx.x) / gridDim.x);
   if (h >= h_end) return;
   unsigned phase = 0, pending = 0;
+  // thread 0: the context whose tensor maps it last acquired (the runs of
+  // units are contiguous per context, so each map is acquired about once)
+  int fenced = -1;
+  auto acquire = [&](int c) {
+    if (c == fenced) return;
+    for (int m = 0; m < kPipeMaps; ++m) fence_tensormap_acquire(&Ts[c].m[m]);
+    fenced = c;
+  };
   int hs = h;
   for (int q = 0; q < G::kAhead; ++q, ++hs) {
     if (hs >= h_end) break;
     if (tid == 0) {
       const int4 e = units[hs];
+      acquire(e.x);
       issue_stage<N, Maps, VEL>(Ps[e.x], Ts[e.x], smem + q * kStage, &bar[q], e.y, e.z);
     }
     pending |= 1u << q;
@@ -813,6 +822,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int4 en = units[hs];
         if (tid == 0) {
           bulk_wait_read<G::kLag>();
+          acquire(en.x);
           issue_stage<N, Maps, VEL>(Ps[en.x], Ts[en.x], smem + q * kStage, &bar[q], en.y, en.z);
         }
         if (!en.w && en.x == cur) prefetch_strips2<N, VEL ? 1 : 2>(sP, en.y, en.z, tid);

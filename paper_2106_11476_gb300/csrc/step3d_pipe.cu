@@ -936,6 +936,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   int k = k0;
   unsigned phase = 0, pending = 0;
   bool nl = sP.nl != 0, nlv = VEL && sP.nl_vel != 0;
+  // thread 0 acquires a context's tensor maps (written by a host copy) before
+  // its first copy through them
+  auto acquire = [&](int c) {
+    for (int m = 0; m < kPipeMaps; ++m) fence_tensormap_acquire(&Ts[c].m[m]);
+  };
+  if (tid == 0) acquire(ctx);
   if (tid == 0)
     issue3<N, VEL, CROSS, PS>(Ts[ctx], sR, smem, ring, sub, &bar[0], x0, y0, k, ring_first<VEL>(k),
                               ring_first<VEL>(k) + 7, k - 1, k + 1, nl, nlv);
@@ -1003,6 +1009,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ctx = nctx;
         nl = sP.nl != 0;
         nlv = VEL && sP.nl_vel != 0;
+        if (tid == 0) acquire(ctx);
       }
       if (tid == 0)
         issue3<N, VEL, CROSS, PS>(Ts[ctx], sR, smem + q * kStage, ring, sub, &bar[q], nx0, ny0, nk,

@@ -2,7 +2,10 @@
 
 Simulation requests (2D or 3D problems with a step count) arrive over time.
 The server admits waiting requests in arrival order while their device
-footprint fits under a memory cap, keeps their state resident, and advances
+footprint fits under a memory cap and their cells under a cap on the cells
+advanced at once (a few requests share the device, the rest keep their
+place in the queue, so the time to result stays close to first-come
+first-served at the batched rate), keeps their state resident, and advances
 all active requests in slices: the 2D requests and the 3D requests with
 bf16 maps together as one fw2 batch (one persistent launch per half step
 and group for all of them, rebuilt when the set of active requests changes;
@@ -63,8 +66,9 @@ def batchable(r: Request) -> bool:
 
 class Server:
     def __init__(self, cap_bytes: float = 160e9, slice_steps: int = 100,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, max_cells: Optional[int] = 32 << 20):
         self.cap = cap_bytes
+        self.max_cells = max_cells        # None: admission by memory alone
         self.slice = slice_steps
         self.clock = clock
         self.launch_log: List[dict] = []
@@ -80,11 +84,14 @@ class Server:
         done: List[Request] = []
         while pending or active:
             now = self.clock() - t0
-            # admission by footprint, in arrival order
+            # admission by footprint and cells, in arrival order (one request
+            # is always admitted when none is active)
+            cells = sum(a[0].cells for a in active)
             while pending and pending[0].arrival <= now:
                 r = pending[0]
                 fp = footprint_bytes(r.problem, r.maps)
-                if used + fp > self.cap and active:
+                over_cells = self.max_cells is not None and cells + r.cells > self.max_cells
+                if active and (used + fp > self.cap or over_cells):
                     break
                 pending.pop(0)
                 stream = torch.cuda.current_stream() if batchable(r) else torch.cuda.Stream()
@@ -92,6 +99,7 @@ class Server:
                 r.admitted = self.clock() - t0
                 active.append((r, sim, r.steps, fp))
                 used += fp
+                cells += r.cells
             if not active:
                 if pending:
                     wait = pending[0].arrival - (self.clock() - t0)

@@ -126,6 +126,26 @@ def test_admission_keeps_the_footprint_under_the_cap(monkeypatch):
     assert order == [0, 1, 2, 3, 4]                        # arrival order
 
 
+def test_admission_keeps_the_active_cells_under_their_cap(monkeypatch):
+    """Three 128^2 requests fit the memory cap together but only two fit the
+    cell cap: the third waits for the first to leave, then keeps its place
+    ahead of a later small one."""
+    _install_fakes(monkeypatch)
+    reqs = [serve.Request(i, 0.0, _prob((128, 128)), 150 + 50 * i) for i in range(3)]
+    reqs.append(serve.Request(3, 0.0, _prob((8, 8)), 50))
+    srv = serve.Server(cap_bytes=1e12, slice_steps=100, clock=_clock(), max_cells=2 * 128 * 128 + 64)
+    done = srv.run(reqs)
+    assert sorted(r.rid for r in done) == [0, 1, 2, 3]
+    assert all(e["n_batch"] <= 3 for e in srv.launch_log)
+    for e in srv.launch_log:
+        live = [r for r in reqs if r.admitted <= e["t"] and (r.finished is None or r.finished >= e["t"])]
+        assert sum(r.cells for r in live) <= 2 * 128 * 128 + 64
+    order = [r.rid for r in sorted(done, key=lambda r: r.admitted)]
+    assert order == [0, 1, 2, 3]
+    by = {r.rid: r for r in done}
+    assert by[2].admitted >= by[0].finished
+
+
 def test_a_request_larger_than_the_cap_still_runs_alone(monkeypatch):
     _install_fakes(monkeypatch)
     reqs = [serve.Request(0, 0.0, _prob((256, 256)), 50), serve.Request(1, 0.0, _prob((16, 16)), 50)]
