@@ -631,7 +631,7 @@ def other_configs(args, rank):
     if "serve" in sel:
         # the first 16 arrivals of the full-scale stream (the whole 200-arrival
         # window runs with --workload serve)
-        out["serve_16"] = serve_measurement(args, 16, 20.0, 1.0, rank, 1, None)
+        out["serve_16"] = serve_measurement(args, 16, [20.0], 1.0, rank, 1, None)
         torch.cuda.empty_cache()
     return out
 
@@ -765,7 +765,9 @@ def batch_measurement(args, rank, world, dist):
             "time_to_result_s": {"batched_p50": round(float(np.percentile(finish, 50)), 3),
                                  "batched_p99": round(float(np.percentile(finish, 99)), 3),
                                  "plain_p50": round(float(np.percentile(plain_finish, 50)), 3),
-                                 "plain_p99": round(float(np.percentile(plain_finish, 99)), 3)},
+                                 "plain_p99": round(float(np.percentile(plain_finish, 99)), 3),
+                                 "batched_per_context": [round(t, 3) for t in finish],
+                                 "plain_per_context": [round(t, 3) for t in plain_finish]},
             "gpu_launches": int(l1 - l0), "clocks": clk.summary()}
 
 
@@ -786,71 +788,152 @@ def run_batch(args, rank, world, dist):
     print(json.dumps(out), flush=True)
 
 
-def serve_requests(n_requests, rate, scale, rank):
-    """Poisson arrivals (mean `rate` per s) of seeded requests: 70 % 2D
-    tissue-index abdominal media with sides U[512, 4096] and U[1000, 4000]
-    steps, 30 % 3D skull-like media (N = 3, bf16 maps) with sides U[256, 512]
-    and U[1000, 2000] steps; `scale` < 1 shrinks sides and steps alike."""
+def serve_requests(n_requests, scale, rank):
+    """Seeded requests of a Poisson stream at one arrival per second (divide
+    the arrival times by the rate): 70 % 2D tissue-index abdominal media with
+    sides U[512, 4096] and U[1000, 4000] steps, 30 % 3D skull-like media
+    (N = 3, bf16 maps) with sides U[256, 512] and U[1000, 2000] steps; `scale`
+    < 1 shrinks sides and steps alike.  Each request carries its grid shape
+    and a function that generates its problem (a 512^3 medium is 8.6 GB of
+    host arrays, so problems are made when they are needed)."""
     import synth
-    from paper_2106_11476_gb300.serve import Request
     rng = np.random.default_rng(500 + rank)
     t = 0.0
-    reqs = []
+    out = []
     for i in range(n_requests):
-        t += rng.exponential(1.0 / rate)
+        t += rng.exponential(1.0)
         if rng.random() < 0.7:
-            side = int(rng.integers(512, 4097) * scale) // 4 * 4
+            side = max(int(rng.integers(512, 4097) * scale) // 4 * 4, 256)
             steps = int(rng.integers(1000, 4001) * scale)
-            p = synth.indexed_abdominal_problem(nx=max(side, 256), ny=max(side, 256), n_steps=steps,
-                                                seed=1000 + i, n_elements=min(64, max(side, 256) // 24))
-            reqs.append(Request(i, t, p, steps, "idx"))
+            make = (lambda side=side, steps=steps, i=i: synth.indexed_abdominal_problem(
+                nx=side, ny=side, n_steps=steps, seed=1000 + i, n_elements=min(64, side // 24)))
+            out.append({"rid": i, "t": t, "shape": (side, side), "steps": steps, "maps": "idx", "make": make})
         else:
-            side = int(rng.integers(256, 513) * scale)
+            side = max(int(rng.integers(256, 513) * scale), 96)
             steps = int(rng.integers(1000, 2001) * scale)
-            p = synth.skull_problem(n=max(side, 96), n_steps=steps, seed=2000 + i, pml_cells=16, array_elems=4)
-            reqs.append(Request(i, t, p, steps, "bf16"))
-    return reqs
+            make = (lambda side=side, steps=steps, i=i: synth.skull_problem(
+                n=side, n_steps=steps, seed=2000 + i, pml_cells=16, array_elems=4))
+            out.append({"rid": i, "t": t, "shape": (side, side, side), "steps": steps, "maps": "bf16",
+                        "make": make})
+    return out
 
 
-def serve_measurement(args, n_requests, rate, scale, rank, world, dist):
-    """The serving loop on a seeded request stream against the plain form:
-    the same requests one at a time in arrival order on dense float maps,
-    each measured over all its steps (setup included)."""
+class InputClock:
+    """Wall clock that stops while a run waits for a request's problem to be
+    generated on the host (input preparation is not the server's work)."""
+
+    def __init__(self):
+        self.stopped = 0.0
+
+    def __call__(self):
+        return time.perf_counter() - self.stopped
+
+
+class ProblemFeed:
+    """The requests' problems generated in arrival order on one host thread,
+    up to `ahead` requests beyond the one asked for; the wait for a problem
+    that is not ready yet stops `clock`."""
+
+    def __init__(self, specs, clock, ahead=2):
+        from concurrent.futures import ThreadPoolExecutor
+        self.specs, self.clock, self.ahead = specs, clock, ahead
+        self.pool = ThreadPoolExecutor(1)
+        self.futs, self.next = {}, 0
+        self.waited = 0.0
+
+    def get(self, i):
+        while self.next < len(self.specs) and self.next <= i + self.ahead:
+            self.futs[self.next] = self.pool.submit(self.specs[self.next]["make"])
+            self.next += 1
+        t = time.perf_counter()
+        prob = self.futs.pop(i).result()
+        dt = time.perf_counter() - t
+        self.waited += dt
+        if self.clock is not None:
+            self.clock.stopped += dt
+        return prob
+
+    def close(self):
+        self.pool.shutdown(wait=True, cancel_futures=True)
+
+
+def fcfs_plain(arrivals, durations):
+    """Times to result of one-at-a-time service in arrival order."""
+    t_free, ttr = 0.0, []
+    for a, d in zip(arrivals, durations):
+        t_free = max(t_free, a) + d
+        ttr.append(t_free - a)
+    return ttr, t_free - min(arrivals)
+
+
+def serve_measurement(args, n_requests, rates, scale, rank, world, dist, sweep_requests=40):
+    """The serving loop on a seeded request stream against the plain form
+    (each request alone, in arrival order, dense float maps, setup and all
+    its steps timed).  The first rate runs all `n_requests` arrivals; each
+    further rate (the sweep) the first `sweep_requests`.  The plain form is
+    run once; its per-request durations give its first-come first-served
+    times to result at every rate.  Problem generation on the host is
+    excluded from both forms' clocks."""
     from paper_2106_11476_gb300 import fw2
-    from paper_2106_11476_gb300.serve import Server, latency_stats
-    reqs = serve_requests(n_requests, rate, scale, rank)
-    work = sum(r.cells * r.steps for r in reqs)
-    srv = Server(cap_bytes=160e9, slice_steps=args.slice)
+    from paper_2106_11476_gb300.serve import Request, Server, latency_stats
+    specs = serve_requests(n_requests, scale, rank)
+    runs = []
     with ClockSampler(device_id_for_smi()) as clk:
-        t0 = time.perf_counter()
-        done = srv.run(reqs)
-        makespan = time.perf_counter() - t0
-    served = latency_stats(done)
-    t_free, finish = 0.0, []
-    for r in sorted(reqs, key=lambda q: q.arrival):
-        start = max(t_free, r.arrival)
-        s0 = time.perf_counter()
-        sim = fw2.Simulation(r.problem, map_precision="f32")
-        sim.step(r.steps)
-        sim.synchronize()
-        sim.close()
-        t_free = start + (time.perf_counter() - s0)
-        finish.append(t_free - r.arrival)
-    plain_makespan = t_free - min(r.arrival for r in reqs)
-    n3 = sum(len(r.problem.shape) == 3 for r in reqs)
-    return {"value": round(work / makespan / 1e9, 4), "unit": UNIT,
-            "config": {"workload": f"serving: {n_requests} Poisson arrivals at {rate}/s, 70 % 2D tissue-index "
+        for j, rate in enumerate(rates):
+            sub = specs if j == 0 else specs[:min(sweep_requests, n_requests)]
+            clock = InputClock()
+            feed = ProblemFeed(sub, clock)
+            reqs = [Request(q["rid"], q["t"] / rate, None, q["steps"], q["maps"], shape=q["shape"]) for q in sub]
+            srv = Server(cap_bytes=160e9, slice_steps=args.slice, clock=clock,
+                         prepare=lambda r, feed=feed: setattr(r, "problem", feed.get(r.rid)))
+            t0 = clock()
+            done = srv.run(reqs)
+            makespan = clock() - t0
+            feed.close()
+            runs.append((rate, sub, done, makespan, feed.waited))
+        # plain form: each request alone, in arrival order
+        feed = ProblemFeed(specs, None)
+        durations = []
+        for i, q in enumerate(specs):
+            prob = feed.get(i)
+            s0 = time.perf_counter()
+            sim = fw2.Simulation(prob, map_precision="f32")
+            sim.step(q["steps"])
+            sim.synchronize()
+            sim.close()
+            durations.append(time.perf_counter() - s0)
+            del prob, sim
+        feed.close()
+    sweep = []
+    for rate, sub, done, makespan, waited in runs:
+        work = sum(int(np.prod(q["shape"])) * q["steps"] for q in sub)
+        st = latency_stats(done)
+        ttr, plain_makespan = fcfs_plain([q["t"] / rate for q in sub], durations[:len(sub)])
+        sweep.append({"rate_per_s": rate, "requests": len(sub), "value": round(work / makespan / 1e9, 4),
+                      "makespan_s": round(makespan, 3), "p50_s": round(st["p50_s"], 3),
+                      "p99_s": round(st["p99_s"], 3),
+                      "plain_value": round(work / plain_makespan / 1e9, 4),
+                      "plain_p50_s": round(float(np.percentile(ttr, 50)), 3),
+                      "plain_p99_s": round(float(np.percentile(ttr, 99)), 3),
+                      "input_generation_wait_s": round(waited, 1)})
+    head = sweep[0]
+    n3 = sum(len(q["shape"]) == 3 for q in specs)
+    work = sum(int(np.prod(q["shape"])) * q["steps"] for q in specs)
+    return {"value": head["value"], "unit": UNIT,
+            "config": {"workload": f"serving: {n_requests} Poisson arrivals at {rates[0]}/s, 70 % 2D tissue-index "
                                    f"(sides 512-4096, 1-4k steps) / 30 % 3D bf16 (sides 256-512, 1-2k steps), "
-                                   f"scale {scale}, 160 GB admission cap, slices of {args.slice} steps",
+                                   f"scale {scale}, 160 GB admission cap, at most 32M cells advanced at once, "
+                                   f"slices of {args.slice} steps",
                        "requests_2d": n_requests - n3, "requests_3d": n3,
-                       "makespan_s": round(makespan, 3), "cell_steps": work},
-            "latency": {"p50_time_to_result_s": round(served["p50_s"], 3),
-                        "p99_time_to_result_s": round(served["p99_s"], 3)},
-            "plain_form": {"value": round(work / plain_makespan / 1e9, 4), "unit": UNIT,
-                           "p50_time_to_result_s": round(float(np.percentile(finish, 50)), 3),
-                           "p99_time_to_result_s": round(float(np.percentile(finish, 99)), 3),
+                       "makespan_s": head["makespan_s"], "cell_steps": work,
+                       "input_generation": "host problem generation excluded from both forms' clocks"},
+            "latency": {"p50_time_to_result_s": head["p50_s"], "p99_time_to_result_s": head["p99_s"]},
+            "plain_form": {"value": head["plain_value"], "unit": UNIT,
+                           "p50_time_to_result_s": head["plain_p50_s"],
+                           "p99_time_to_result_s": head["plain_p99_s"],
                            "how": "one request at a time in arrival order, float maps, each run in full "
-                                  "(setup, all its steps)"},
+                                  "(setup, all its steps); durations measured once, queueing computed per rate"},
+            "rate_sweep": sweep[1:],
             "clocks": clk.summary()}
 
 
@@ -859,13 +942,15 @@ def run_serve(args, rank, world, dist):
     from paper_2106_11476_gb300 import _build
     _build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    r = serve_measurement(args, args.requests, args.rate, args.serve_scale, rank, world, dist)
+    rates = [float(x) for x in args.rates.split(",")]
+    r = serve_measurement(args, args.requests, rates, args.serve_scale, rank, world, dist,
+                          sweep_requests=args.sweep_requests)
     if rank != 0:
         return
     out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": None, "warmup": 0,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded request stream)"}
-    for k in ("config", "latency", "plain_form", "clocks"):
+    for k in ("config", "latency", "plain_form", "rate_sweep", "clocks"):
         out[k] = r[k]
     print(json.dumps(out), flush=True)
 
@@ -915,7 +1000,10 @@ def main():
     ap.add_argument("--impl", default="fw2", choices=["fw2", "reference"])
     ap.add_argument("--n", type=int, default=4096, help="grid side of the workload")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
-    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    ap.add_argument("--rates", default="20,1,0.5,0.25",
+                    help="serving: mean arrivals per second; the first with all --requests arrivals, the others "
+                         "(a sweep) with the first --sweep-requests")
+    ap.add_argument("--sweep-requests", type=int, default=40, help="serving: arrivals of each sweep rate")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serving: size and step scale")
     ap.add_argument("--slice", type=int, default=100, help="serving: steps per slice")
     ap.add_argument("--batch-cells", type=int, default=16 << 20,

@@ -184,8 +184,10 @@ fw2_status enqueue_step(fw2_batch *b, int grid, int order) {
                                 b->stream));
       b->launches++;
     }
-    const int kinds[2][2] = {{1, 2}, {0, -1}};
-    for (int kk = 0; kk < 2; ++kk) {
+    // after the velocity half step the v_x, v_y, v_z sources, after the
+    // pressure half step the p sources
+    const int kinds[2][3] = {{1, 2, 3}, {0, -1, -1}};
+    for (int kk = 0; kk < 3; ++kk) {
       const int kind = kinds[half][kk];
       if (kind < 0 || b->total[kind] == 0) continue;
       batch_inject_kernel<<<(b->total[kind] + 127) / 128, 128, 0, b->stream>>>(b->d_ctx, n_ctx, b->d_prefix[kind],

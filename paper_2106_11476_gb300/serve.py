@@ -30,17 +30,24 @@ from . import fw2
 class Request:
     rid: int
     arrival: float                 # seconds after the start of the run
-    problem: object                # a problem description (synth.Problem shape)
+    problem: object                # a problem description (synth.Problem shape), or None
     steps: int
     maps: str = "f32"
+    # the grid shape, for a request whose problem the server's `prepare`
+    # fills in at admission
+    shape: Optional[tuple] = None
     # filled by the server
     admitted: Optional[float] = None
     finished: Optional[float] = None
     trace: Optional[np.ndarray] = None
 
     @property
+    def grid(self) -> tuple:
+        return tuple(self.problem.shape if self.problem is not None else self.shape)
+
+    @property
     def cells(self) -> int:
-        return int(np.prod(self.problem.shape))
+        return int(np.prod(self.grid))
 
 
 def footprint_bytes(prob, maps: str) -> int:
@@ -61,16 +68,20 @@ def footprint_bytes(prob, maps: str) -> int:
 def batchable(r: Request) -> bool:
     """2D requests, and 3D requests on the pipelined path (bf16 maps), join
     the batch; the others step on their own."""
-    return len(r.problem.shape) == 2 or r.maps == "bf16"
+    return len(r.grid) == 2 or r.maps == "bf16"
 
 
 class Server:
     def __init__(self, cap_bytes: float = 160e9, slice_steps: int = 100,
-                 clock: Callable[[], float] = time.perf_counter, max_cells: Optional[int] = 32 << 20):
+                 clock: Callable[[], float] = time.perf_counter, max_cells: Optional[int] = 32 << 20,
+                 prepare: Optional[Callable[[Request], None]] = None):
         self.cap = cap_bytes
         self.max_cells = max_cells        # None: admission by memory alone
         self.slice = slice_steps
         self.clock = clock
+        # called for a request about to be admitted, to fill in its problem;
+        # with it, a request's problem is dropped again when it leaves
+        self.prepare = prepare
         self.launch_log: List[dict] = []
 
     def run(self, requests: List[Request]) -> List[Request]:
@@ -89,9 +100,13 @@ class Server:
             cells = sum(a[0].cells for a in active)
             while pending and pending[0].arrival <= now:
                 r = pending[0]
-                fp = footprint_bytes(r.problem, r.maps)
                 over_cells = self.max_cells is not None and cells + r.cells > self.max_cells
-                if active and (used + fp > self.cap or over_cells):
+                if active and over_cells:
+                    break
+                if self.prepare is not None and r.problem is None:
+                    self.prepare(r)
+                fp = footprint_bytes(r.problem, r.maps)
+                if active and used + fp > self.cap:
                     break
                 pending.pop(0)
                 stream = torch.cuda.current_stream() if batchable(r) else torch.cuda.Stream()
@@ -143,6 +158,8 @@ class Server:
                     r.trace = sim.trace.cpu().numpy() if sim.trace is not None else None
                     r.finished = self.clock() - t0
                     sim.close()
+                    if self.prepare is not None:
+                        r.problem = None
                     used -= fp
                     done.append(r)
                 else:

@@ -153,8 +153,19 @@ def _fill_relaxation(prob: Problem, tissue_of: np.ndarray, sets: List[dict],
     d2 = np.empty_like(d1); a2 = np.empty_like(d1)
     lut = lambda key, nu=None: np.asarray([s[key] if nu is None else s[key][nu] for s in sets], np.float64)
     flat_t = tissue_of.reshape(-1)
+    # a few tissues: one mask per tissue and masked copies (much faster than
+    # a gather over a large grid); many tissues: the gather
+    masks = [flat_t == t for t in range(1, len(sets))] if len(sets) <= 8 else None
+
     def put(dst, values):
-        dst.reshape(-1)[:] = values.astype(np.float32)[flat_t]
+        v = values.astype(np.float32)
+        d = dst.reshape(-1)
+        if masks is None:
+            d[:] = v[flat_t]
+            return
+        d.fill(v[0])
+        for t, m in enumerate(masks, 1):
+            np.copyto(d, v[t], where=m)
     put(k1, lut("kappa1")); put(k2, lut("kappa2"))
     for nu in range(N):
         put(d1[nu], lut("d1", nu)); put(a1[nu], lut("alpha1", nu))

@@ -98,3 +98,46 @@ def test_committed_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     assert bench.committed_traffic("w:f32:1:pipe2d_vel") is None
     assert bench.committed_traffic("w:bf16:1:pipe3d_vel") is None   # another family's sources
     assert bench.committed_traffic("missing") is None
+
+
+def test_fcfs_plain_queues_behind_earlier_requests():
+    ttr, span = bench.fcfs_plain([0.0, 1.0, 10.0], [3.0, 2.0, 1.0])
+    # the second waits for the first (free at 3), the third finds the device idle
+    assert ttr == [3.0, 4.0, 1.0] and span == 11.0
+
+
+def test_serve_requests_mix_and_rate_free_arrivals():
+    specs = bench.serve_requests(200, 1.0, 0)
+    assert len(specs) == 200 and [q["rid"] for q in specs] == list(range(200))
+    t = [q["t"] for q in specs]
+    assert all(b > a for a, b in zip(t, t[1:]))
+    assert 150 < t[-1] < 250                                # one arrival per second on average
+    n3 = sum(len(q["shape"]) == 3 for q in specs)
+    assert 40 <= n3 <= 80                                   # about 30 % 3D
+    for q in specs:
+        side = q["shape"][0]
+        if len(q["shape"]) == 2:
+            assert 512 <= side <= 4096 and side % 4 == 0 and q["maps"] == "idx"
+            assert 1000 <= q["steps"] <= 4000
+        else:
+            assert 256 <= side <= 512 and q["maps"] == "bf16" and 1000 <= q["steps"] <= 2000
+    # the same seeded stream whatever the scale's effect on sizes
+    small = bench.serve_requests(200, 0.25, 0)
+    assert [q["t"] for q in small] == t
+
+
+def test_problem_feed_hands_out_in_order_and_stops_the_clock():
+    made = []
+
+    def maker(i):
+        def make():
+            made.append(i)
+            return i * 10
+        return make
+    specs = [{"make": maker(i)} for i in range(5)]
+    clock = bench.InputClock()
+    feed = bench.ProblemFeed(specs, clock, ahead=2)
+    assert [feed.get(i) for i in range(5)] == [0, 10, 20, 30, 40]
+    feed.close()
+    assert made == [0, 1, 2, 3, 4]
+    assert clock.stopped == pytest.approx(feed.waited) and clock.stopped >= 0.0

@@ -166,3 +166,21 @@ def test_footprint_counts_state_maps_and_strips(maps):
     mp = {"f32": (5 + 4 * N) * 4 * n, "bf16": (5 + 4 * N) * 2 * n, "idx": n + 21 * 256 * 4}[maps]
     strips = 4 * N * 4 * 2 * L * (ny + nx)
     assert serve.footprint_bytes(p, maps) == state + mp + strips
+
+
+def test_prepare_fills_problems_at_admission_and_drops_them_after(monkeypatch):
+    _install_fakes(monkeypatch)
+    shapes = [(64, 48), (32, 32, 24), (40, 40)]
+    reqs = [serve.Request(i, 0.0, None, 120, shape=s) for i, s in enumerate(shapes)]
+    seen = []
+
+    def prepare(r):
+        assert r.problem is None
+        seen.append(r.rid)
+        r.problem = _prob(r.shape)
+    srv = serve.Server(cap_bytes=1e12, slice_steps=100, clock=_clock(), prepare=prepare)
+    done = srv.run(reqs)
+    assert seen == [0, 1, 2]
+    assert sorted(r.rid for r in done) == [0, 1, 2]
+    assert all(r.problem is None and r.trace[0] == 120 for r in done)
+    assert [r.cells for r in reqs] == [64 * 48, 32 * 32 * 24, 40 * 40]
