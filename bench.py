@@ -466,6 +466,8 @@ def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=T
     dom_bytes, dom_over = (vel_b, vel_o) if dom == kv else (prs_b, prs_o)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     variant = ("" if args.taps == "taylor" else f":{args.taps}") + (f":{args.nl}" if args.nl else "")
+    if layout is not None and dom.startswith("pipe3d"):
+        variant += ":" + str(layout[0] if dom == kv else layout[1])
     traffic = committed_traffic(f"{name or args.workload}:{maps}:{prob.shape[0]}:{dom}{variant}")
     step_b = vel_b + prs_b
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
