@@ -641,22 +641,24 @@ def other_configs(args, rank):
 def batch_problems(args, rank):
     """64 focused transmits over one 2048 x 1024 tissue-index medium (seeded
     lateral foci) and 16 tissue-index instances with sides in [512, 1536];
-    step budgets: K for every transmit, K x U(0.25, 1) for the instances
-    (the uneven lengths of a served mix)."""
+    step budgets: --batch-steps (4000) for every transmit, seeded uniform in
+    [1000, 4000] scaled alike for the instances (the uneven lengths of a
+    served mix)."""
     import synth
     rng = np.random.default_rng(100 + rank)
-    steps = args.warmup + args.steps
+    K = args.batch_steps
+    steps = max(args.warmup, 13) + K
     probs, budgets = [], []
     for e in range(64):
         probs.append(synth.indexed_abdominal_problem(nx=2048, ny=1024, n_steps=steps, seed=1 + rank,
                                                      n_elements=64, focus_mm=float(rng.uniform(15, 35)),
                                                      focus_x_mm=float(rng.uniform(-10, 10))))
-        budgets.append(args.steps)
+        budgets.append(K)
     for e in range(16):
         nx, ny = (int(v) for v in rng.integers(512, 1537, 2))
         probs.append(synth.indexed_abdominal_problem(nx=nx, ny=ny, n_steps=steps, seed=200 + 16 * rank + e,
                                                      n_elements=16))
-        budgets.append(max(1, int(round(args.steps * rng.uniform(0.25, 1.0)))))
+        budgets.append(max(1, int(round(K * rng.uniform(0.25, 1.0)))))
     return probs, budgets
 
 
@@ -671,10 +673,12 @@ def batch_measurement(args, rank, world, dist):
     """Batched tissue-index form vs the plain form (dense float maps, one
     context at a time) on the same 80 problems with the same uneven step
     budgets, both taking them shortest work first.  The batch admits
-    problems in that order while fewer than --batch-cells cells are active
-    (paused ones have a budget equal to their step counter), and a problem
-    leaves when its budget is spent; each one's time to result is taken when
-    the batch step it finishes in completes."""
+    problems in that order while at most --batch-cells cells are active
+    (paused ones have a budget equal to their step counter): with the gang
+    policy a group at a time (the next group once the last member of the
+    previous one has left), with the continuous policy whenever the next one
+    fits.  A problem leaves when its budget is spent; each one's time to
+    result is taken when the batch step it finishes in completes."""
     import torch
     from paper_2106_11476_gb300 import fw2
     probs, budgets = batch_problems(args, rank)
@@ -691,6 +695,10 @@ def batch_measurement(args, rank, world, dist):
     queue, active = list(order), []
 
     def admit():
+        # gang: a new group only when the previous one has left entirely;
+        # continuous: whenever the next problem fits
+        if args.batch_policy == "gang" and active:
+            return
         cells = sum(probs[i].n_pts for i in active)
         while queue and (not active or cells + probs[queue[0]].n_pts <= args.batch_cells):
             i = queue.pop(0)
@@ -748,14 +756,15 @@ def batch_measurement(args, rank, world, dist):
     peaks, _ = measured_peaks()
     vb = sum(n * sum(algorithmic_bytes_indexed(p.shape, p.nrelax, p.pml_transition + p.pml_bound, True))
              for p, n in zip(probs, budgets))
-    return {"value": round(value, 4), "unit": UNIT, "steps": args.steps,
-            "ms_per_step": round(t_batch / args.steps * 1e3, 4),
-            "config": {"workload": "batched: 64 focused transmits over one 2048x1024 tissue-index medium (K steps "
-                                   "each) + 16 instances 512^2..1536^2 (K x U(0.25, 1) steps), shortest work first, "
-                                   "at most %d active cells, contexts leave when their budget is spent, one "
-                                   "persistent launch per half step, graph-captured step loop, autotuned launch"
-                                   % args.batch_cells, "cell_steps": work,
-                       "active_cells_cap": args.batch_cells, "segments": waves,
+    return {"value": round(value, 4), "unit": UNIT, "steps": args.batch_steps,
+            "ms_per_step": round(t_batch / args.batch_steps * 1e3, 4),
+            "config": {"workload": "batched: 64 focused transmits over one 2048x1024 tissue-index medium (%d steps "
+                                   "each) + 16 instances 512^2..1536^2 (U(0.25, 1) x as many steps), shortest work first, "
+                                   % args.batch_steps +
+                                   "at most %d active cells (%s admission), contexts leave when their budget is "
+                                   "spent, one persistent launch per half step, graph-captured step loop, "
+                                   "autotuned launch" % (args.batch_cells, args.batch_policy), "cell_steps": work,
+                       "active_cells_cap": args.batch_cells, "admission": args.batch_policy, "segments": waves,
                        "tuned_grid": grid, "tuned_order": tile_order},
             "roofline": {"bound": "hbm", "kernel": "step (all kernels)", "unit": "GB/s",
                          "achieved": round(vb / t_batch / 1e9, 1), "peak": float(peaks["hbm_gbs"]),
@@ -781,7 +790,7 @@ def run_batch(args, rank, world, dist):
     r = batch_measurement(args, rank, world, dist)
     if rank != 0:
         return
-    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": r["steps"],
            "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded tissue-index abdominal media)"}
@@ -1008,8 +1017,11 @@ def main():
     ap.add_argument("--sweep-requests", type=int, default=40, help="serving: arrivals of each sweep rate")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serving: size and step scale")
     ap.add_argument("--slice", type=int, default=100, help="serving: steps per slice")
-    ap.add_argument("--batch-cells", type=int, default=16 << 20,
+    ap.add_argument("--batch-steps", type=int, default=4000, help="batch: steps of each transmit event")
+    ap.add_argument("--batch-cells", type=int, default=32 << 20,
                     help="batch: most cells advanced at once (admission in shortest-work-first order)")
+    ap.add_argument("--batch-policy", default="gang", choices=["gang", "continuous"],
+                    help="batch: admit a group when the previous one has left, or whenever the next problem fits")
     ap.add_argument("--workload", default="abdominal",
                     choices=["abdominal", "abdominal-idx", "skull", "plain", "batch", "serve"],
                     help="abdominal: 2D 4096^2 nonlinear (default); abdominal-idx: the same in tissue-index "

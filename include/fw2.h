@@ -104,7 +104,7 @@ enum { FW2_MEM_CENTRED = 0, FW2_MEM_ENDPOINT = 1 };
  * every tile through shared memory with TMA copies, where they apply (2D
  * float or tissue-index maps; 3D bf16 maps with N <= 3, g_{1,1} cross taps
  * and the literal system included; no periodic axis), and TILE elsewhere;
- * AUTO (default) is PIPE.  The 3D pipelined half steps have two layouts:
+ * AUTO (default) is PIPE where it applies.  The 3D pipelined half steps have two layouts:
  * the memory variables staged in shared memory with the other arrays, or
  * loaded into registers one unit ahead, which leaves room to stage every
  * C-PML strip (faster where edge units dominate); the cross taps and the
@@ -122,7 +122,11 @@ enum {
 
 typedef struct {
   int32_t ndim;          /* 2 or 3 */
-  int32_t n_relax;       /* N relaxation mechanisms, 0..4 */
+  int32_t n_relax;       /* N relaxation mechanisms, 0..8 (Sec. 2.1: N
+                            memory variables per derivative); the tile
+                            kernels take every N, the pipelined 2D half steps
+                            N <= 4, the 3D ones N <= 3, the tissue-index
+                            tables N <= 4 (FW2_EUNSUPPORTED above) */
   int64_t n[3];          /* nx, ny, nz (nz = 1 in 2D); boundary region included */
   double h;              /* grid spacing [m] */
   double dt;             /* time step [s]; <= 0: cfl * h / c_max, with c_max the

@@ -18,6 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfw2.so")
 SOURCES = ["api.cu", "prep.cu", "aux.cu", "step2d.cu", "step2d_pipe.cu", "step3d.cu", "step3d_pipe.cu", "noalloc.cu", "batch.cu",
            "fit.cpp"]
+# second compilations of a source: (source, object name, extra flags); the
+# tile kernels for 5..8 mechanisms build beside those for 0..4
+VARIANTS = [("step2d.cu", "step2d_wide", ["-DFW2_WIDE_RELAX"]), ("step3d.cu", "step3d_wide", ["-DFW2_WIDE_RELAX"])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,9 +51,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job):
+        src, name, extra = job
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [nvcc] + _flags() + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -58,8 +62,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    jobs = [(src, os.path.splitext(src)[0], []) for src in SOURCES] + VARIANTS
+    # the longest compilations first
+    heavy = ("step3d.cu", "step3d_pipe.cu", "step2d.cu")
+    jobs.sort(key=lambda j: j[0] not in heavy)
+    with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -636,6 +636,8 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
   if (cfg.map_precision == FW2_MAP_IDX_U8 && cfg.ndim != 2)
     return fail(nullptr, FW2_EUNSUPPORTED, "tissue-index maps are implemented for 2D grids");
+  if (cfg.map_precision == FW2_MAP_IDX_U8 && cfg.n_relax > kTabSlots)
+    return fail(nullptr, FW2_EUNSUPPORTED, "tissue-index tables hold up to %d mechanisms", kTabSlots);
   if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_LITERAL) return fail(nullptr, FW2_EINVAL, "bad nl_mode");
   if (cfg.mem_alignment != FW2_MEM_CENTRED && cfg.mem_alignment != FW2_MEM_ENDPOINT)
     return fail(nullptr, FW2_EINVAL, "bad mem_alignment");

@@ -127,6 +127,7 @@ struct fw2_batch {
   std::vector<float> trial_ms[4];
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  bool graph_stale = false;  // the tables changed since the graph was captured
   long long steps_done = 0;  // batch steps since creation
   // blow-up detection: scan every context's p every watch_every steps (0: off)
   long long watch_every = 0;
@@ -212,13 +213,11 @@ fw2_status enqueue_step(fw2_batch *b, int grid, int order) {
 // kind) the step parameters, tile tables (context-major and interleaved)
 // and, for the pipelined form, the unit table and tensor maps; the source,
 // recording and step-counter arrays of all active contexts.  Replaces the
-// previous tables (and the captured graph, which points into them).
+// previous tables (the captured graph, which points into them, is marked
+// stale: the next run re-captures it and updates the executable in place
+// when the launch sequence kept its shape).
 fw2_status build_tables(fw2_batch *b) {
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-    b->graph_steps = 0;
-  }
+  b->graph_stale = true;
   cudaStreamSynchronize(b->stream);
   for (void *m : b->table_allocs) cudaFree(m);
   b->table_allocs.clear();
@@ -414,6 +413,8 @@ namespace {
 // Steps each launch configuration is timed over during tuning; the median
 // of its trials counts.
 constexpr int kTrialReps = 3;
+// Steps per captured graph (replayed; a shorter tail is launched directly).
+constexpr int kGraphSteps = 16;
 
 struct EventPair {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -473,10 +474,8 @@ fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
   }
   const int64_t rest = n_steps - *done;
   if (rest > 0) {
-    const int chunk = (int)std::min<int64_t>(rest, 64);
-    if (!b->graph || b->graph_steps != chunk) {
-      if (b->graph) cudaGraphExecDestroy(b->graph);
-      b->graph = nullptr;
+    const int chunk = (int)std::min<int64_t>(rest, kGraphSteps);
+    if (!b->graph || b->graph_steps != chunk || b->graph_stale) {
       cudaGraph_t g;
       BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       fw2_status st = FW2_OK;
@@ -484,10 +483,23 @@ fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
       cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
       if (st != FW2_OK) return st;
       BCK(b, ec);
-      ec = cudaGraphInstantiate(&b->graph, g, 0);
+      // same number of steps and launches: new parameters into the
+      // executable graph; otherwise a new executable
+      bool updated = false;
+      if (b->graph && b->graph_steps == chunk) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(b->graph, g, &info) == cudaSuccess;
+        if (!updated) (void)cudaGetLastError();
+      }
+      if (!updated) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        ec = cudaGraphInstantiate(&b->graph, g, 0);
+      }
       cudaGraphDestroy(g);
       BCK(b, ec);
       b->graph_steps = chunk;
+      b->graph_stale = false;
     }
     int64_t left = rest;
     while (left >= chunk) {

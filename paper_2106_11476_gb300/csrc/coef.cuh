@@ -124,11 +124,18 @@ __device__ __forceinline__ float4 load_chunk(const StepParams &P, const float *f
   return v;
 }
 
+// Quotients of the half steps (the face coefficient 2 dt / (rho_a + rho_b),
+// the momentum factor, the nonlinear denominator 1 + chi p): the
+// reciprocal-based quotient, within 2 ulp of the rounded one, a few
+// instructions where the rounded division takes a dozen and a slow-path
+// check.  Every kernel of a half step uses it, so all paths agree bitwise.
+__device__ __forceinline__ float qdiv(float x, float y) { return __fdividef(x, y); }
+
 // Momentum factor of the literal nonlinear system (Eq. general5,
 // rho_0 (1 + kappa_0 p)) at the face between cells a and b: 1 + kappa0_face
 // p_face, both the mean of the two cells (kappa0 = 1 / K).
 __device__ __forceinline__ float mom_factor(float Ka, float Kb, float pa, float pb) {
-  return fmaf(0.5f * (1.f / Ka + 1.f / Kb), 0.5f * (pa + pb), 1.f);
+  return fmaf(0.5f * (qdiv(1.f, Ka) + qdiv(1.f, Kb)), 0.5f * (pa + pb), 1.f);
 }
 
 // The velocity update v - b S (Eq. general5, b = 2 dt / (rho_a + rho_b)),
@@ -136,7 +143,7 @@ __device__ __forceinline__ float mom_factor(float Ka, float Kb, float pa, float 
 // multiply-add each, written out so that every kernel of the half step
 // rounds alike whatever the compiler's contraction choices.
 __device__ __forceinline__ float vel_upd(float v, float b, float S) { return fmaf(-b, S, v); }
-__device__ __forceinline__ float vel_upd(float v, float b, float S, float f) { return fmaf(-b, S / f, v); }
+__device__ __forceinline__ float vel_upd(float v, float b, float S, float f) { return fmaf(-b, qdiv(S, f), v); }
 
 // Density used for the face average: cells beyond the last one along an
 // axis take the last cell's value (zero-outside boundary) or wrap (periodic).

@@ -18,7 +18,12 @@
 
 namespace fw2 {
 
-constexpr int kMaxRelax = 4;
+// mechanisms per context: up to 8 on the tile kernels (dense float or bf16
+// maps); the pipelined 2D half steps and the tissue-index tables take up to
+// 4, the pipelined 3D half steps up to 3
+constexpr int kMaxRelax = 8;
+constexpr int kTabSlots = 4;       // mechanism slots of the tissue-index tables
+constexpr int kPipe2dMaxRelax = 4;
 
 struct StepParams {
   int nx, ny, nz;        // logical extent
@@ -112,6 +117,12 @@ constexpr int kBY = 8;
 // map_kind: 0 float maps, 1 bf16 maps, 2 uint8 tissue index + tables
 cudaError_t launch_vel2d(const StepParams &P, int map_kind, cudaStream_t s);
 cudaError_t launch_prs2d(const StepParams &P, int map_kind, cudaStream_t s);
+// the same for 5..8 mechanisms (dense maps; a second compilation of the tile
+// kernels, so the two sets build in parallel)
+cudaError_t launch_vel2d_wide(const StepParams &P, int map_kind, cudaStream_t s);
+cudaError_t launch_prs2d_wide(const StepParams &P, int map_kind, cudaStream_t s);
+cudaError_t launch_batched2d_wide(bool vel, const StepParams *Ps, const int4 *tiles, int n_tiles, int n_relax,
+                                  int map_kind, int grid, cudaStream_t s);
 // persistent batched 2D half step over a tile table {ctx, x0, y0, -} of
 // several contexts sharing N and the map kind (vel: velocity, else pressure)
 cudaError_t launch_batched2d(bool vel, const StepParams *Ps, const int4 *tiles, int n_tiles, int n_relax,
@@ -158,5 +169,7 @@ cudaError_t launch_pipe3d_batched(bool vel, bool cross, bool ps, int n_relax, co
                                   cudaStream_t s);
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
+cudaError_t launch_vel3d_wide(const StepParams &P, int map_bf16, cudaStream_t s);
+cudaError_t launch_prs3d_wide(const StepParams &P, int map_bf16, cudaStream_t s);
 
 }  // namespace fw2

@@ -14,7 +14,7 @@ namespace fw2 {
 // order (then a1[nu], b1[nu], a2[nu], b2[nu] for nu < N).
 enum { kTabK = 0, kTabRho = 1, kTabChi = 2, kTabIk1 = 3, kTabIk2 = 4, kTabRelax = 5 };
 constexpr int kTissues = 256;
-constexpr int kTableFields = kTabRelax + 4 * kMaxRelax;
+constexpr int kTableFields = kTabRelax + 4 * kTabSlots;
 
 template <typename T>
 struct DenseMaps {
@@ -91,14 +91,14 @@ struct IdxMaps {
   __device__ __forceinline__ float4 ik1(Cell x) const { return look(kTabIk1, x); }
   __device__ __forceinline__ float4 ik2(Cell x) const { return look(kTabIk2, x); }
   // relaxation fields: a1[nu] at kTabRelax + nu, b1 at + N, a2 at + 2N, b2 at + 3N
-  // (N = kMaxRelax slots reserved; the prep fills the first n_relax of each)
+  // (kTabSlots slots reserved; the prep fills the first n_relax of each)
   template <int OP>
   __device__ __forceinline__ float4 a(Cell x, int nu) const {
-    return look(kTabRelax + (OP == 1 ? 0 : 2 * kMaxRelax) + nu, x);
+    return look(kTabRelax + (OP == 1 ? 0 : 2 * kTabSlots) + nu, x);
   }
   template <int OP>
   __device__ __forceinline__ float4 b(Cell x, int nu) const {
-    return look(kTabRelax + (OP == 1 ? kMaxRelax : 3 * kMaxRelax) + nu, x);
+    return look(kTabRelax + (OP == 1 ? kTabSlots : 3 * kTabSlots) + nu, x);
   }
   template <int OP>
   __device__ __forceinline__ float a1c(Cell x, int nu, int e) const {

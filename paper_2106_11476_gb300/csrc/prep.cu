@@ -139,10 +139,10 @@ __global__ void table_kernel(const PrepParams Q) {
     double a, b;
     relax_ab(Q.d1[nu * Q.n_tissue + t], Q.al1[nu * Q.n_tissue + t], k1, Q.dt, a, b);
     T[(kTabRelax + nu) * kTissues + t] = (float)a;
-    T[(kTabRelax + kMaxRelax + nu) * kTissues + t] = (float)b;
+    T[(kTabRelax + kTabSlots + nu) * kTissues + t] = (float)b;
     relax_ab(Q.d2[nu * Q.n_tissue + t], Q.al2[nu * Q.n_tissue + t], k2, Q.dt, a, b);
-    T[(kTabRelax + 2 * kMaxRelax + nu) * kTissues + t] = (float)a;
-    T[(kTabRelax + 3 * kMaxRelax + nu) * kTissues + t] = (float)b;
+    T[(kTabRelax + 2 * kTabSlots + nu) * kTissues + t] = (float)a;
+    T[(kTabRelax + 3 * kTabSlots + nu) * kTissues + t] = (float)b;
   }
 }
 

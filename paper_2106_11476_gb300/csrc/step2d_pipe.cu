@@ -487,7 +487,7 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
       A[nu] = look2(tab, kTabRelax + nu, cell);
-      B[nu] = look2(tab, kTabRelax + kMaxRelax + nu, cell);
+      B[nu] = look2(tab, kTabRelax + kTabSlots + nu, cell);
     }
   } else {
     k1 = sld2(own + (2 + 2 * N) * kArr);
@@ -533,15 +533,15 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
   if (P.nl_vel) {
     float2 fx, fy;
     mom_factors2<Maps, EDGE>(P, tab, si, ss + S::kS, sp, ly + 3, lx, ly, x0, y0, fx, fy);
-    vx.x = vel_upd(vx.x, P.two_dt / (fr.r0 + fr.r1), Sx.x, fx.x);
-    vx.y = vel_upd(vx.y, P.two_dt / (fr.r1 + fr.r2), Sx.y, fx.y);
-    vy.x = vel_upd(vy.x, P.two_dt / (fr.r0 + fr.u0), Sy.x, fy.x);
-    vy.y = vel_upd(vy.y, P.two_dt / (fr.r1 + fr.u1), Sy.y, fy.y);
+    vx.x = vel_upd(vx.x, qdiv(P.two_dt, fr.r0 + fr.r1), Sx.x, fx.x);
+    vx.y = vel_upd(vx.y, qdiv(P.two_dt, fr.r1 + fr.r2), Sx.y, fx.y);
+    vy.x = vel_upd(vy.x, qdiv(P.two_dt, fr.r0 + fr.u0), Sy.x, fy.x);
+    vy.y = vel_upd(vy.y, qdiv(P.two_dt, fr.r1 + fr.u1), Sy.y, fy.y);
   } else {
-    vx.x = vel_upd(vx.x, P.two_dt / (fr.r0 + fr.r1), Sx.x);
-    vx.y = vel_upd(vx.y, P.two_dt / (fr.r1 + fr.r2), Sx.y);
-    vy.x = vel_upd(vy.x, P.two_dt / (fr.r0 + fr.u0), Sy.x);
-    vy.y = vel_upd(vy.y, P.two_dt / (fr.r1 + fr.u1), Sy.y);
+    vx.x = vel_upd(vx.x, qdiv(P.two_dt, fr.r0 + fr.r1), Sx.x);
+    vx.y = vel_upd(vx.y, qdiv(P.two_dt, fr.r1 + fr.r2), Sx.y);
+    vy.x = vel_upd(vy.x, qdiv(P.two_dt, fr.r0 + fr.u0), Sy.x);
+    vy.y = vel_upd(vy.y, qdiv(P.two_dt, fr.r1 + fr.u1), Sy.y);
   }
   put2<Maps, EDGE>(own, 0, P.v[0], c, vx, i0, P.nx);
   put2<Maps, EDGE>(own, 1, P.v[1], c, vy, i0, P.nx);
@@ -570,8 +570,8 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const float *ta
     if (P.nl) ch = look2(tab, kTabChi, cell);
 #pragma unroll
     for (int nu = 0; nu < N; ++nu) {
-      A[nu] = look2(tab, kTabRelax + 2 * kMaxRelax + nu, cell);
-      B[nu] = look2(tab, kTabRelax + 3 * kMaxRelax + nu, cell);
+      A[nu] = look2(tab, kTabRelax + 2 * kTabSlots + nu, cell);
+      B[nu] = look2(tab, kTabRelax + 3 * kTabSlots + nu, cell);
     }
   } else {
     k2 = sld2(own + (1 + 2 * N) * kArr);
@@ -616,7 +616,7 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const float *ta
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     float upd = P.dt * el2(K, e) * (el2(Sx, e) + el2(Sy, e));
-    if (P.nl) upd /= fmaf(el2(ch, e), el2(p, e), 1.f);
+    if (P.nl) upd = qdiv(upd, fmaf(el2(ch, e), el2(p, e), 1.f));
     el2(p, e) -= upd;
   }
   put2<Maps, EDGE>(own, 0, P.p, c, p, i0, P.nx);
@@ -911,7 +911,7 @@ Region region_of(const StepParams &P) {
 
 bool pipe2d_supported(const StepParams &P, int map_kind) {
   // the copies read zero outside the grid: the zero-outside boundary only
-  return P.nz == 1 && (map_kind == 0 || map_kind == 2) && P.n_relax >= 0 && P.n_relax <= kMaxRelax &&
+  return P.nz == 1 && (map_kind == 0 || map_kind == 2) && P.n_relax >= 0 && P.n_relax <= kPipe2dMaxRelax &&
          !P.periodic[0] && !P.periodic[1];
 }
 

@@ -223,16 +223,16 @@ __device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp
     mom_factors3<MT>(P, sp, sy, tx, i0, j, k, pz1, fx, fy, fz);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      el(v0, e) = vel_upd(el(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el(S0, e), el(fx, e));
-      el(v1, e) = vel_upd(el(v1, e), P.two_dt / (rr[e] + el(ru, e)), el(S1, e), el(fy, e));
-      el(v2, e) = vel_upd(el(v2, e), P.two_dt / (rr[e] + el(rz, e)), el(S2, e), el(fz, e));
+      el(v0, e) = vel_upd(el(v0, e), qdiv(P.two_dt, rr[e] + rr[e + 1]), el(S0, e), el(fx, e));
+      el(v1, e) = vel_upd(el(v1, e), qdiv(P.two_dt, rr[e] + el(ru, e)), el(S1, e), el(fy, e));
+      el(v2, e) = vel_upd(el(v2, e), qdiv(P.two_dt, rr[e] + el(rz, e)), el(S2, e), el(fz, e));
     }
   } else {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      el(v0, e) = vel_upd(el(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el(S0, e));
-      el(v1, e) = vel_upd(el(v1, e), P.two_dt / (rr[e] + el(ru, e)), el(S1, e));
-      el(v2, e) = vel_upd(el(v2, e), P.two_dt / (rr[e] + el(rz, e)), el(S2, e));
+      el(v0, e) = vel_upd(el(v0, e), qdiv(P.two_dt, rr[e] + rr[e + 1]), el(S0, e));
+      el(v1, e) = vel_upd(el(v1, e), qdiv(P.two_dt, rr[e] + el(ru, e)), el(S1, e));
+      el(v2, e) = vel_upd(el(v2, e), qdiv(P.two_dt, rr[e] + el(rz, e)), el(S2, e));
     }
   }
   st_state4(P.v[0], c, v0);
@@ -326,7 +326,7 @@ __device__ __forceinline__ void prs3d_fast(const StepParams &P, const float (*sv
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     float upd = P.dt * el(K, e) * (el(S0, e) + el(S1, e) + el(S2, e));
-    if (P.nl) upd /= fmaf(el(ch, e), el(p, e), 1.f);
+    if (P.nl) upd = qdiv(upd, fmaf(el(ch, e), el(p, e), 1.f));
     el(p, e) -= upd;
   }
   st_state4(P.p, c, p);
@@ -419,12 +419,12 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
         const int x = min(i0 + e, P.nx - 1);
         el(rz, e) = ldmap(rho, (long long)kz * P.plane + (long long)j * P.pitch + x);
       }
-      bx = make_float4(P.two_dt / (r0.x + r0.y), P.two_dt / (r0.y + r0.z), P.two_dt / (r0.z + r0.w),
-                       P.two_dt / (r0.w + r4));
-      by = make_float4(P.two_dt / (r0.x + ru.x), P.two_dt / (r0.y + ru.y), P.two_dt / (r0.z + ru.z),
-                       P.two_dt / (r0.w + ru.w));
-      bz = make_float4(P.two_dt / (r0.x + rz.x), P.two_dt / (r0.y + rz.y), P.two_dt / (r0.z + rz.z),
-                       P.two_dt / (r0.w + rz.w));
+      bx = make_float4(qdiv(P.two_dt, r0.x + r0.y), qdiv(P.two_dt, r0.y + r0.z), qdiv(P.two_dt, r0.z + r0.w),
+                       qdiv(P.two_dt, r0.w + r4));
+      by = make_float4(qdiv(P.two_dt, r0.x + ru.x), qdiv(P.two_dt, r0.y + ru.y), qdiv(P.two_dt, r0.z + ru.z),
+                       qdiv(P.two_dt, r0.w + ru.w));
+      bz = make_float4(qdiv(P.two_dt, r0.x + rz.x), qdiv(P.two_dt, r0.y + rz.y), qdiv(P.two_dt, r0.z + rz.z),
+                       qdiv(P.two_dt, r0.w + rz.w));
     }
     const float4 k1 = ldmap4(ik1, c);
     float4 fx = make_float4(1.f, 1.f, 1.f, 1.f), fy = fx, fz = fx;
@@ -539,42 +539,56 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
   }
 }
 
-template <typename MT>
-cudaError_t vel3d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
-  switch (P.n_relax) {
-    case 0: vel3d_kernel<0, MT><<<g, b, 0, s>>>(P); break;
-    case 1: vel3d_kernel<1, MT><<<g, b, 0, s>>>(P); break;
-    case 2: vel3d_kernel<2, MT><<<g, b, 0, s>>>(P); break;
-    case 3: vel3d_kernel<3, MT><<<g, b, 0, s>>>(P); break;
-    case 4: vel3d_kernel<4, MT><<<g, b, 0, s>>>(P); break;
-    default: return cudaErrorInvalidValue;
+// The mechanism counts this compilation instantiates: 0..4, or 5..8 when
+// built with FW2_WIDE_RELAX (the second object of this file).
+#ifdef FW2_WIDE_RELAX
+constexpr int kNLo = 5, kNHi = kMaxRelax;
+#else
+constexpr int kNLo = 0, kNHi = 4;
+#endif
+
+template <int N, typename MT>
+cudaError_t vel3d_at(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
+  if constexpr (N > kNHi) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (P.n_relax != N) return vel3d_at<N + 1, MT>(P, g, b, s);
+    vel3d_kernel<N, MT><<<g, b, 0, s>>>(P);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
 }
 
-template <typename MT>
-cudaError_t prs3d_dispatch(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
-  switch (P.n_relax) {
-    case 0: prs3d_kernel<0, MT><<<g, b, 0, s>>>(P); break;
-    case 1: prs3d_kernel<1, MT><<<g, b, 0, s>>>(P); break;
-    case 2: prs3d_kernel<2, MT><<<g, b, 0, s>>>(P); break;
-    case 3: prs3d_kernel<3, MT><<<g, b, 0, s>>>(P); break;
-    case 4: prs3d_kernel<4, MT><<<g, b, 0, s>>>(P); break;
-    default: return cudaErrorInvalidValue;
+template <int N, typename MT>
+cudaError_t prs3d_at(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
+  if constexpr (N > kNHi) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (P.n_relax != N) return prs3d_at<N + 1, MT>(P, g, b, s);
+    prs3d_kernel<N, MT><<<g, b, 0, s>>>(P);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
 }
 
 }  // namespace
 
+#ifdef FW2_WIDE_RELAX
+cudaError_t launch_vel3d_wide(const StepParams &P, int map_bf16, cudaStream_t s) {
+#else
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s) {  // map kind 0 or 1
+  if (P.n_relax > kNHi) return launch_vel3d_wide(P, map_bf16, s);
+#endif
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kBY3);
-  return map_bf16 ? vel3d_dispatch<__nv_bfloat16>(P, g, b, s) : vel3d_dispatch<float>(P, g, b, s);
+  return map_bf16 ? vel3d_at<kNLo, __nv_bfloat16>(P, g, b, s) : vel3d_at<kNLo, float>(P, g, b, s);
 }
 
+#ifdef FW2_WIDE_RELAX
+cudaError_t launch_prs3d_wide(const StepParams &P, int map_bf16, cudaStream_t s) {
+#else
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s) {
+  if (P.n_relax > kNHi) return launch_prs3d_wide(P, map_bf16, s);
+#endif
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kBY3);
-  return map_bf16 ? prs3d_dispatch<__nv_bfloat16>(P, g, b, s) : prs3d_dispatch<float>(P, g, b, s);
+  return map_bf16 ? prs3d_at<kNLo, __nv_bfloat16>(P, g, b, s) : prs3d_at<kNLo, float>(P, g, b, s);
 }
 
 }  // namespace fw2

@@ -628,16 +628,16 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
       const float fx = mom_factor(Kr[e], Kr[e + 1], pr[e], pr[e + 1]);
       const float fy = mom_factor(Kr[e], Ku[e], pr[e], pu[e]);
       const float fz = mom_factor(Kr[e], Kz[e], pr[e], pz[e]);
-      el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(Sd[0], e), fx);
-      el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(Sd[1], e), fy);
-      el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(Sd[2], e), fz);
+      el2(v0, e) = vel_upd(el2(v0, e), qdiv(P.two_dt, rr[e] + rr[e + 1]), el2(Sd[0], e), fx);
+      el2(v1, e) = vel_upd(el2(v1, e), qdiv(P.two_dt, rr[e] + ru[e]), el2(Sd[1], e), fy);
+      el2(v2, e) = vel_upd(el2(v2, e), qdiv(P.two_dt, rr[e] + rz[e]), el2(Sd[2], e), fz);
     }
   } else {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      el2(v0, e) = vel_upd(el2(v0, e), P.two_dt / (rr[e] + rr[e + 1]), el2(Sd[0], e));
-      el2(v1, e) = vel_upd(el2(v1, e), P.two_dt / (rr[e] + ru[e]), el2(Sd[1], e));
-      el2(v2, e) = vel_upd(el2(v2, e), P.two_dt / (rr[e] + rz[e]), el2(Sd[2], e));
+      el2(v0, e) = vel_upd(el2(v0, e), qdiv(P.two_dt, rr[e] + rr[e + 1]), el2(Sd[0], e));
+      el2(v1, e) = vel_upd(el2(v1, e), qdiv(P.two_dt, rr[e] + ru[e]), el2(Sd[1], e));
+      el2(v2, e) = vel_upd(el2(v2, e), qdiv(P.two_dt, rr[e] + rz[e]), el2(Sd[2], e));
     }
   }
   if (EDGE) {
@@ -777,7 +777,7 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     float upd = P.dt * el2(K, e) * (el2(Sd[0], e) + el2(Sd[1], e) + el2(Sd[2], e));
-    if (P.nl) upd /= fmaf(el2(ch, e), el2(p, e), 1.f);
+    if (P.nl) upd = qdiv(upd, fmaf(el2(ch, e), el2(p, e), 1.f));
     el2(p, e) -= upd;
   }
   if (EDGE) p = mask_pad2(p, i0, P.nx);

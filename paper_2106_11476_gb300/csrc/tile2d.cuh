@@ -264,23 +264,23 @@ __device__ __forceinline__ void vel2d_fast_rows(const StepParams &P, const Maps 
     if (P.nl_vel) {
       float4 fx, fy;
       mom_factors(P, M, sp, ly + 3, tx, i0, j, fx, fy);
-      vx.x = vel_upd(vx.x, P.two_dt / (r0.x + r0.y), Sx.x, fx.x);
-      vx.y = vel_upd(vx.y, P.two_dt / (r0.y + r0.z), Sx.y, fx.y);
-      vx.z = vel_upd(vx.z, P.two_dt / (r0.z + r0.w), Sx.z, fx.z);
-      vx.w = vel_upd(vx.w, P.two_dt / (r0.w + r4), Sx.w, fx.w);
-      vy.x = vel_upd(vy.x, P.two_dt / (r0.x + ru.x), Sy.x, fy.x);
-      vy.y = vel_upd(vy.y, P.two_dt / (r0.y + ru.y), Sy.y, fy.y);
-      vy.z = vel_upd(vy.z, P.two_dt / (r0.z + ru.z), Sy.z, fy.z);
-      vy.w = vel_upd(vy.w, P.two_dt / (r0.w + ru.w), Sy.w, fy.w);
+      vx.x = vel_upd(vx.x, qdiv(P.two_dt, r0.x + r0.y), Sx.x, fx.x);
+      vx.y = vel_upd(vx.y, qdiv(P.two_dt, r0.y + r0.z), Sx.y, fx.y);
+      vx.z = vel_upd(vx.z, qdiv(P.two_dt, r0.z + r0.w), Sx.z, fx.z);
+      vx.w = vel_upd(vx.w, qdiv(P.two_dt, r0.w + r4), Sx.w, fx.w);
+      vy.x = vel_upd(vy.x, qdiv(P.two_dt, r0.x + ru.x), Sy.x, fy.x);
+      vy.y = vel_upd(vy.y, qdiv(P.two_dt, r0.y + ru.y), Sy.y, fy.y);
+      vy.z = vel_upd(vy.z, qdiv(P.two_dt, r0.z + ru.z), Sy.z, fy.z);
+      vy.w = vel_upd(vy.w, qdiv(P.two_dt, r0.w + ru.w), Sy.w, fy.w);
     } else {
-      vx.x = vel_upd(vx.x, P.two_dt / (r0.x + r0.y), Sx.x);
-      vx.y = vel_upd(vx.y, P.two_dt / (r0.y + r0.z), Sx.y);
-      vx.z = vel_upd(vx.z, P.two_dt / (r0.z + r0.w), Sx.z);
-      vx.w = vel_upd(vx.w, P.two_dt / (r0.w + r4), Sx.w);
-      vy.x = vel_upd(vy.x, P.two_dt / (r0.x + ru.x), Sy.x);
-      vy.y = vel_upd(vy.y, P.two_dt / (r0.y + ru.y), Sy.y);
-      vy.z = vel_upd(vy.z, P.two_dt / (r0.z + ru.z), Sy.z);
-      vy.w = vel_upd(vy.w, P.two_dt / (r0.w + ru.w), Sy.w);
+      vx.x = vel_upd(vx.x, qdiv(P.two_dt, r0.x + r0.y), Sx.x);
+      vx.y = vel_upd(vx.y, qdiv(P.two_dt, r0.y + r0.z), Sx.y);
+      vx.z = vel_upd(vx.z, qdiv(P.two_dt, r0.z + r0.w), Sx.z);
+      vx.w = vel_upd(vx.w, qdiv(P.two_dt, r0.w + r4), Sx.w);
+      vy.x = vel_upd(vy.x, qdiv(P.two_dt, r0.x + ru.x), Sy.x);
+      vy.y = vel_upd(vy.y, qdiv(P.two_dt, r0.y + ru.y), Sy.y);
+      vy.z = vel_upd(vy.z, qdiv(P.two_dt, r0.z + ru.z), Sy.z);
+      vy.w = vel_upd(vy.w, qdiv(P.two_dt, r0.w + ru.w), Sy.w);
     }
     st_state4(P.v[0], c, vx);
     st_state4(P.v[1], c, vy);
@@ -337,7 +337,7 @@ __device__ __forceinline__ void prs2d_fast_rows(const StepParams &P, const Maps 
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       float upd = P.dt * el(K, e) * (el(Sx, e) + el(Sy, e));
-      if (P.nl) upd /= fmaf(el(ch, e), el(p, e), 1.f);
+      if (P.nl) upd = qdiv(upd, fmaf(el(ch, e), el(p, e), 1.f));
       el(p, e) -= upd;
     }
     st_state4(P.p, c, p);
@@ -396,10 +396,10 @@ __device__ __forceinline__ void vel2d_tile(const StepParams &P, int x0, int y0, 
       const float4 r0 = *reinterpret_cast<const float4 *>(&sr[ly][lx]);
       const float r4 = sr[ly][lx + 4];
       const float4 ru = *reinterpret_cast<const float4 *>(&sr[ly + 1][lx]);
-      bx = make_float4(P.two_dt / (r0.x + r0.y), P.two_dt / (r0.y + r0.z), P.two_dt / (r0.z + r0.w),
-                       P.two_dt / (r0.w + r4));
-      by = make_float4(P.two_dt / (r0.x + ru.x), P.two_dt / (r0.y + ru.y), P.two_dt / (r0.z + ru.z),
-                       P.two_dt / (r0.w + ru.w));
+      bx = make_float4(qdiv(P.two_dt, r0.x + r0.y), qdiv(P.two_dt, r0.y + r0.z), qdiv(P.two_dt, r0.z + r0.w),
+                       qdiv(P.two_dt, r0.w + r4));
+      by = make_float4(qdiv(P.two_dt, r0.x + ru.x), qdiv(P.two_dt, r0.y + ru.y), qdiv(P.two_dt, r0.z + ru.z),
+                       qdiv(P.two_dt, r0.w + ru.w));
     }
     const float4 k1 = M.ik1(cell);
     float4 fx = make_float4(1.f, 1.f, 1.f, 1.f), fy = fx;

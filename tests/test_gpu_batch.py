@@ -27,11 +27,14 @@ def _problems():
     probs.append(("bf16", small_2d(nx=96, ny=96, N=4, steps=95, pml=(6, 2))))
     # both nonlinear factors, grouped with the linear N = 2 context above
     probs.append(("f32", small_2d(nx=180, ny=100, N=2, nl="literal", steps=95, amp=2e7)))
+    # more mechanisms than the pipelined kernels take: batched tile kernels
+    probs.append(("f32", small_2d(nx=140, ny=90, N=6, steps=95, pml=(6, 2))))
+    probs.append(("bf16", small_2d(nx=100, ny=70, N=8, nl="pressure", steps=95, pml=(6, 2))))
     return probs
 
 
 def test_batch_equals_each_context_alone(fw2):
-    steps = 90                     # 13 tuning steps, one 64-step graph, 13 plain
+    steps = 90                     # 13 tuning steps, four 16-step graphs, 13 plain
     probs = _problems()
     alone = []
     for maps, p in probs:

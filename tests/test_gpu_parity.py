@@ -91,13 +91,29 @@ def state_names(prob):
     return names
 
 
+def relax_set(N):
+    """A fitted set of N <= 4 mechanisms; for N > 4 the four-mechanism set
+    with N - 4 more mechanisms at rescaled rates (d / 2, alpha x 3: not a
+    fit; the step computes whatever parameters it is given)."""
+    if N <= 4:
+        key = {1: "N2_y1.0_a0.5", 2: "N2_y1.0_a0.5", 3: "N3_y1.2_brain", 4: "N4_y1.1_a0.5"}[N]
+        s = dict(synth.relaxation_sets()[key])
+        if N == 1:
+            s = {k: (v[:1] if isinstance(v, list) else v) for k, v in s.items()}
+        return s
+    s = dict(synth.relaxation_sets()["N4_y1.1_a0.5"])
+    extra = N - 4
+    for k, f in (("d1", 0.5), ("d2", 0.5), ("alpha1", 3.0), ("alpha2", 3.0)):
+        s[k] = list(s[k]) + [v * f for v in s[k][:extra]]
+    return s
+
+
 def small_2d(nx=200, ny=136, N=2, nl="off", steps=300, seed=0, pml=(12, 4), alignment="centred",
              reading="C", vel_src=False, hetero=True, amp=None):
-    key = {2: "N2_y1.0_a0.5", 3: "N3_y1.2_brain", 4: "N4_y1.1_a0.5"}.get(N)
     rng = np.random.default_rng(seed)
     f0 = 3e6
     h = 1540.0 / f0 / 12
-    relax = synth.relaxation_sets()[key] if N else None
+    relax = relax_set(N) if N else None
     prob = synth.homogeneous((nx, ny), h, 0.0, relax=relax)
     g = prob.grid_shape
     if hetero:
@@ -157,6 +173,9 @@ def compare_run(fw2, prob, steps, state=None, check_trace=True, rel=REL_L2, mx=M
 
 CASES_2D = {
     "base": dict(),
+    # more mechanisms than the pipelined kernels take (tile kernels)
+    "N6-nonlinear": dict(N=6, nl="pressure", steps=250),
+    "N8-literal": dict(N=8, nl="literal", vel_src=True, amp=2e7, steps=200),
     "nonlinear-pressure": dict(nl="pressure"),
     "westervelt-N4": dict(nl="westervelt", N=4),
     "endpoint-readingA": dict(alignment="endpoint", reading="A"),
@@ -240,8 +259,7 @@ def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3, pml=(6, 2))
     rng = np.random.default_rng(seed)
     f0 = 1e6
     h = 1540.0 / f0 / 10
-    key = {2: "N2_y1.0_a0.5", 3: "N3_y1.2_brain"}.get(N)
-    relax = synth.relaxation_sets()[key] if N else None
+    relax = relax_set(N) if N else None
     prob = synth.homogeneous(n, h, 0.0, relax=relax)
     g = prob.grid_shape
     prob.c = (1560.0 * (1 + 0.1 * rng.random(g))).astype(np.float32)
@@ -263,6 +281,22 @@ def small_3d(n=(70, 40, 36), N=3, nl="westervelt", steps=80, seed=3, pml=(6, 2))
 def test_parity_3d(fw2):
     prob = small_3d()
     compare_run(fw2, prob, 80)
+
+
+def test_parity_2d_eight_mechanisms_bf16(fw2):
+    compare_run(fw2, small_2d(N=8, nl="pressure", steps=250), 250, maps="bf16")
+
+
+@pytest.mark.parametrize("N,maps", [(5, "f32"), (8, "bf16")])
+def test_parity_3d_more_mechanisms(fw2, N, maps):
+    """More mechanisms than the pipelined 3D half steps take: the tile
+    kernels, float and bf16 maps."""
+    prob = small_3d(n=(70, 40, 36), N=N, steps=60)
+    sim = fw2.Simulation(prob, map_precision=maps)
+    sim.step(1)
+    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    sim.close()
+    compare_run(fw2, prob, 60, maps=maps)
 
 
 @pytest.mark.parametrize("maps", ["f32", "bf16"])
