@@ -125,11 +125,13 @@ __device__ __forceinline__ float4 load_chunk(const StepParams &P, const float *f
 }
 
 // Quotients of the half steps (the face coefficient 2 dt / (rho_a + rho_b),
-// the momentum factor, the nonlinear denominator 1 + chi p): the
-// reciprocal-based quotient, within 2 ulp of the rounded one, a few
+// the momentum factor, the nonlinear denominator 1 + chi p): x times the
+// approximate reciprocal of y, within 2 ulp of the rounded quotient, two
 // instructions where the rounded division takes a dozen and a slow-path
-// check.  Every kernel of a half step uses it, so all paths agree bitwise.
-__device__ __forceinline__ float qdiv(float x, float y) { return __fdividef(x, y); }
+// check.  The product is rounded on its own (__fmul_rn is never contracted
+// into a neighbouring add), so every kernel of a half step computes the same
+// value whatever its surrounding code: all paths agree bitwise.
+__device__ __forceinline__ float qdiv(float x, float y) { return __fmul_rn(x, __fdividef(1.f, y)); }
 
 // Momentum factor of the literal nonlinear system (Eq. general5,
 // rho_0 (1 + kappa_0 p)) at the face between cells a and b: 1 + kappa0_face

@@ -472,13 +472,18 @@ def _bcheck(status: int, batch):
         raise Fw2Error(status, r.decode() if r else "")
 
 
+# contexts per live batch handle (the budget array must have one entry each)
+_batch_sizes = {}
+
+
 def fw2_batch_create(ctxs) -> int:
-    """One batch over several 2D contexts (fw2_batch_create); returns the handle."""
+    """One batch over several contexts (fw2_batch_create); returns the handle."""
     arr = (C.c_void_p * len(ctxs))(*ctxs)
     h = C.c_void_p()
     st = lib().fw2_batch_create(arr, len(ctxs), C.byref(h))
     if st != OK:
         raise Fw2Error(st, "fw2_batch_create failed")
+    _batch_sizes[h.value] = len(ctxs)
     return h.value
 
 
@@ -511,6 +516,9 @@ def fw2_batch_set_budget(batch, last_steps):
         _bcheck(lib().fw2_batch_set_budget(batch, None), batch)
         return
     arr = np.ascontiguousarray(last_steps, np.int64)
+    n = _batch_sizes.get(batch)
+    if arr.ndim != 1 or (n is not None and arr.size != n):
+        raise ValueError(f"one budget per context of the batch: got {arr.size}, the batch has {n}")
     _bcheck(lib().fw2_batch_set_budget(batch, arr.ctypes.data), batch)
 
 
@@ -524,6 +532,7 @@ def fw2_batch_active(batch) -> int:
 def fw2_batch_destroy(batch):
     """Release the batch (fw2_batch_destroy); the contexts remain."""
     if batch:
+        _batch_sizes.pop(batch, None)
         lib().fw2_batch_destroy(batch)
 
 

@@ -120,7 +120,7 @@ def test_batch_full_size_equals_each_context_alone(fw2):
     what they hold when stepped alone."""
     import types
     import bench
-    probs, _ = bench.batch_problems(types.SimpleNamespace(warmup=8, steps=8), 0)
+    probs, _ = bench.batch_problems(types.SimpleNamespace(warmup=8, steps=8, batch_steps=8), 0)
     steps = 16
     sims = [fw2.Simulation(p, map_precision="idx") for p in probs]
     batch = fw2.fw2_batch_create([s.ctx for s in sims])
@@ -147,7 +147,7 @@ def test_batch_budgets_let_contexts_leave_and_equal_each_context_alone(fw2):
     rebuilds its launch tables as contexts leave) and holds bitwise what it
     holds when stepped alone for that many steps."""
     probs = _problems()
-    budgets = [40, 95, 17, 70, 95, 33, 60, 81]
+    budgets = [40, 95, 17, 70, 95, 33, 60, 81, 52, 29]
     alone = []
     for (maps, p), n in zip(probs, budgets):
         s = fw2.Simulation(p, map_precision=maps)
@@ -157,6 +157,8 @@ def test_batch_budgets_let_contexts_leave_and_equal_each_context_alone(fw2):
     sims = [fw2.Simulation(p, map_precision=maps) for maps, p in probs]
     batch = fw2.fw2_batch_create([s.ctx for s in sims])
     try:
+        with pytest.raises(ValueError):
+            fw2.fw2_batch_set_budget(batch, budgets[:-1])
         fw2.fw2_batch_set_budget(batch, budgets)
         assert fw2.fw2_batch_active(batch) == len(sims)
         fw2.fw2_batch_step(batch, 50)
