@@ -530,8 +530,8 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
                              P.dt * K.z * (Sx.z + Sy.z + Sz.z), P.dt * K.w * (Sx.w + Sy.w + Sz.w));
     if (P.nl) {
       const float4 ch = ldmap4(chim, c);
-      upd.x /= fmaf(ch.x, p.x, 1.f); upd.y /= fmaf(ch.y, p.y, 1.f);
-      upd.z /= fmaf(ch.z, p.z, 1.f); upd.w /= fmaf(ch.w, p.w, 1.f);
+      upd.x = qdiv(upd.x, fmaf(ch.x, p.x, 1.f)); upd.y = qdiv(upd.y, fmaf(ch.y, p.y, 1.f));
+      upd.z = qdiv(upd.z, fmaf(ch.z, p.z, 1.f)); upd.w = qdiv(upd.w, fmaf(ch.w, p.w, 1.f));
     }
     p.x -= upd.x; p.y -= upd.y; p.z -= upd.z; p.w -= upd.w;
     st_state4(P.p, c, mask_pad(p, i0, P.nx));

@@ -478,8 +478,8 @@ __device__ __forceinline__ void prs2d_tile(const StepParams &P, int x0, int y0, 
                              P.dt * K.z * (Sx.z + Sy.z), P.dt * K.w * (Sx.w + Sy.w));
     if (P.nl) {
       const float4 ch = M.chiv(cell);
-      upd.x /= fmaf(ch.x, p.x, 1.f); upd.y /= fmaf(ch.y, p.y, 1.f);
-      upd.z /= fmaf(ch.z, p.z, 1.f); upd.w /= fmaf(ch.w, p.w, 1.f);
+      upd.x = qdiv(upd.x, fmaf(ch.x, p.x, 1.f)); upd.y = qdiv(upd.y, fmaf(ch.y, p.y, 1.f));
+      upd.z = qdiv(upd.z, fmaf(ch.z, p.z, 1.f)); upd.w = qdiv(upd.w, fmaf(ch.w, p.w, 1.f));
     }
     p.x -= upd.x; p.y -= upd.y; p.z -= upd.z; p.w -= upd.w;
     st_state4(P.p, c, mask_pad(p, i0, P.nx));
