@@ -690,6 +690,7 @@ def batch_measurement(args, rank, world, dist):
     fw2.fw2_batch_step(batch, warm)
     fw2.fw2_batch_synchronize(batch)
     grid, tile_order, l0 = fw2.fw2_batch_info(batch)
+    edge_weight = fw2.fw2_batch_edge_weight(batch)
     at = [warm] * len(sims)                              # each context's step counter
     last = [warm + n for n in budgets]
     queue, active = list(order), []
@@ -765,7 +766,7 @@ def batch_measurement(args, rank, world, dist):
                                    "spent, one persistent launch per half step, graph-captured step loop, "
                                    "autotuned launch" % (args.batch_cells, args.batch_policy), "cell_steps": work,
                        "active_cells_cap": args.batch_cells, "admission": args.batch_policy, "segments": waves,
-                       "tuned_grid": grid, "tuned_order": tile_order},
+                       "tuned_grid": grid, "tuned_order": tile_order, "tuned_edge_weight": edge_weight},
             "roofline": {"bound": "hbm", "kernel": "step (all kernels)", "unit": "GB/s",
                          "achieved": round(vb / t_batch / 1e9, 1), "peak": float(peaks["hbm_gbs"]),
                          "frac": round(vb / t_batch / 1e9 / float(peaks["hbm_gbs"]), 4),

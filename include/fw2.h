@@ -285,9 +285,12 @@ fw2_status fw2_set_watch(fw2_ctx *ctx, int64_t every, float bound);
  * by the cross taps and the layout of each half step), one launch each for
  * the sources and recordings of all contexts, and replays chunks of steps
  * as a captured CUDA graph.  The first batch step warms up; the next twelve
- * time four launch configurations (persistent grid size x tile order),
- * three steps each, and the one with the fastest median is kept; every
- * configuration computes the same result. */
+ * time four launch configurations, three steps each, and the one with the
+ * fastest median is kept; every configuration computes the same result.  A
+ * configuration is a persistent grid size and tile order for the tile path
+ * and, for the pipelined groups, the cost of an edge unit (C-PML strips,
+ * clamps) relative to an interior one, 1, 1.5, 2 or 3, by which the work
+ * table is split into the blocks' contiguous runs of about equal cost. */
 typedef struct fw2_batch fw2_batch;
 /* Contexts are borrowed (they must outlive the batch), with medium set;
  * their coefficient maps and sources are built here.  Re-create the batch
@@ -313,6 +316,8 @@ fw2_status fw2_batch_synchronize(fw2_batch *b);
  * 1 interleaved) and kernel launches (graph replays count their kernels once
  * at capture). */
 fw2_status fw2_batch_info(fw2_batch *b, int32_t *grid, int32_t *order, int64_t *launches);
+/* Tuned edge-unit cost of the pipelined groups' runs (0 before tuning). */
+fw2_status fw2_batch_edge_weight(fw2_batch *b, double *weight);
 const char *fw2_batch_last_error(const fw2_batch *b);
 /* Blow-up detection for the batch (as fw2_set_watch): with every > 0, after
  * each batch step whose count (steps since the batch's first) is a multiple

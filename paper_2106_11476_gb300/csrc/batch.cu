@@ -94,6 +94,7 @@ struct Group {
   unsigned char *d_regions[2] = {nullptr, nullptr};
   int2 *d_items[2] = {nullptr, nullptr};
   int n_items[2] = {0, 0};
+  int *d_runs3[2][4] = {};  // per half step and edge weight: the blocks' runs of items
   StepParams *d_params = nullptr;
   int4 *d_tiles[2] = {nullptr, nullptr};  // context-major, interleaved
   int n_tiles = 0;
@@ -102,6 +103,7 @@ struct Group {
   bool pipe = false;
   int4 *d_units = nullptr;
   int n_units = 0;
+  int *d_runs[4] = {};  // per edge weight: the blocks' runs of units
   PipeMaps *d_maps[2] = {nullptr, nullptr};  // velocity, pressure
 };
 
@@ -120,7 +122,7 @@ struct fw2_batch {
   int total[5] = {0, 0, 0, 0, 0};
   std::string err = "no error";
   // launch configuration: persistent grid and tile order, tuned online
-  int grid = 0, order = 0;
+  int grid = 0, order = 0, cand = 0;
   int n_sm = 152;
   bool tuned = false, warmed = false;
   int trial = 0;
@@ -137,7 +139,29 @@ struct fw2_batch {
 
 namespace {
 
-const int kCandidates[4][2] = {{152 * 2, 0}, {152 * 2, 1}, {152, 0}, {152 * 4, 1}};
+// Launch configurations the tuner times: persistent grid and tile order of
+// the tile path, and the cost of an edge unit relative to an interior one
+// (tenths) by which the pipelined groups split their unit tables into the
+// blocks' contiguous runs (edge units read C-PML strips and clamp; a run
+// of them takes longer than a run of interior units of the same length).
+const int kCandidates[4][3] = {{152 * 2, 0, 10}, {152 * 2, 1, 15}, {152, 0, 20}, {152 * 4, 1, 30}};
+
+// Boundaries of `grid` contiguous runs of the weighted items with about
+// equal weight each (grid + 1 entries, runs[0] = 0, runs[grid] = n).
+std::vector<int> balanced_runs(const std::vector<double> &w, int grid) {
+  const int n = (int)w.size();
+  double total = 0.0;
+  for (double x : w) total += x;
+  std::vector<int> runs(grid + 1, n);
+  runs[0] = 0;
+  double acc = 0.0;
+  int b = 1;
+  for (int i = 0; i < n && b < grid; ++i) {
+    acc += w[i];
+    while (b < grid && acc >= total * b / grid) runs[b++] = i + 1;
+  }
+  return runs;
+}
 
 fw2_status bfail(fw2_batch *b, fw2_status s, const char *what, cudaError_t e = cudaSuccess) {
   char buf[512];
@@ -169,16 +193,19 @@ fw2_status bupload(fw2_batch *b, const std::vector<T> &v, T **out) {
 }
 
 // one time step of every active context (launch sequence of the file header)
-fw2_status enqueue_step(fw2_batch *b, int grid, int order) {
+fw2_status enqueue_step(fw2_batch *b, int cand) {
+  const int grid = kCandidates[cand][0], order = kCandidates[cand][1];
   const int n_ctx = (int)b->active.size();
   for (int half = 0; half < 2; ++half) {
     const bool vel = half == 0;
     for (Group &g : b->groups) {
       if (g.nd == 3)
         BCK(b, launch_pipe3d_batched(vel, g.cross, g.ps[half], g.n_relax, g.d_params, g.d_regions[half],
-                                     g.d_maps[half], g.d_items[half], g.n_items[half], b->n_sm, b->stream));
+                                     g.d_maps[half], g.d_items[half], g.d_runs3[half][cand], b->n_sm,
+                                     b->stream));
       else if (g.pipe)
-        BCK(b, launch_pipe2d_batched(vel, g.d_params, g.d_maps[vel ? 0 : 1], g.d_units, g.n_units, g.n_relax,
+        BCK(b, launch_pipe2d_batched(vel, g.d_params, g.d_maps[vel ? 0 : 1], g.d_units, g.n_units, g.d_runs[cand],
+                                     g.n_relax,
                                      g.map_kind, b->n_sm, b->stream));
       else
         BCK(b, launch_batched2d(vel, g.d_params, g.d_tiles[order], g.n_tiles, g.n_relax, g.map_kind, grid,
@@ -256,6 +283,7 @@ fw2_status build_tables(fw2_batch *b) {
       std::vector<PipeMaps> mv, mp;
       std::vector<unsigned char> reg[2];
       std::vector<int2> items[2];
+      std::vector<int2> units3[2];  // per item: {edge units, units}
       const size_t rb = pipe3d_region_bytes();
       for (int m = 0; m < (int)g.members.size(); ++m) {
         fw2_ctx *c = b->ctxs[b->active[g.members[m]]];
@@ -266,6 +294,9 @@ fw2_status build_tables(fw2_batch *b) {
           reg[h].resize((m + 1) * rb);
           const long long n = pipe3d_region(c->P, b->n_sm, h == 0, reg[h].data() + m * rb);
           for (long long t = 0; t < n; ++t) items[h].push_back(make_int2(m, (int)t));
+          std::vector<int> ne(n), na(n);
+          pipe3d_item_units(c->P, b->n_sm, h == 0, ne.data(), na.data());
+          for (long long t = 0; t < n; ++t) units3[h].push_back(make_int2(ne[t], na[t]));
         }
       }
       if ((st = bupload(b, params, &g.d_params)) != FW2_OK) break;
@@ -274,7 +305,13 @@ fw2_status build_tables(fw2_batch *b) {
       for (int h = 0; h < 2 && st == FW2_OK; ++h) {
         g.n_items[h] = (int)items[h].size();
         if ((st = bupload(b, reg[h], &g.d_regions[h])) != FW2_OK) break;
-        st = bupload(b, items[h], &g.d_items[h]);
+        if ((st = bupload(b, items[h], &g.d_items[h])) != FW2_OK) break;
+        for (int w = 0; w < 4 && st == FW2_OK; ++w) {
+          std::vector<double> wt(units3[h].size());
+          for (size_t i = 0; i < wt.size(); ++i)
+            wt[i] = (units3[h][i].y - units3[h][i].x) + units3[h][i].x * (kCandidates[w][2] / 10.0);
+          st = bupload(b, balanced_runs(wt, b->n_sm), &g.d_runs3[h][w]);
+        }
       }
       if (st != FW2_OK) break;
       continue;
@@ -319,6 +356,12 @@ fw2_status build_tables(fw2_batch *b) {
       if (g.pipe) {
         g.n_units = (int)units.size();
         if ((st = bupload(b, units, &g.d_units)) != FW2_OK) break;
+        for (int w = 0; w < 4 && st == FW2_OK; ++w) {
+          std::vector<double> wt(units.size());
+          for (size_t i = 0; i < units.size(); ++i) wt[i] = units[i].w ? 1.0 : kCandidates[w][2] / 10.0;
+          st = bupload(b, balanced_runs(wt, b->n_sm), &g.d_runs[w]);
+        }
+        if (st != FW2_OK) break;
         if ((st = bupload(b, mv, &g.d_maps[0])) != FW2_OK) break;
         if ((st = bupload(b, mp, &g.d_maps[1])) != FW2_OK) break;
       }
@@ -444,7 +487,7 @@ fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
   // then each launch configuration for kTrialReps steps (every
   // configuration computes the same result); the fastest median wins
   if (!b->warmed && *done < n_steps) {
-    fw2_status st = enqueue_step(b, kCandidates[0][0], kCandidates[0][1]);
+    fw2_status st = enqueue_step(b, 0);
     if (st != FW2_OK) return st;
     ++*done;
     b->warmed = true;
@@ -455,7 +498,7 @@ fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
     BCK(b, cudaEventCreate(&ev.e0));
     BCK(b, cudaEventCreate(&ev.e1));
     BCK(b, cudaEventRecord(ev.e0, b->stream));
-    fw2_status st = enqueue_step(b, kCandidates[k][0], kCandidates[k][1]);
+    fw2_status st = enqueue_step(b, k);
     if (st != FW2_OK) return st;
     ++*done;
     BCK(b, cudaEventRecord(ev.e1, b->stream));
@@ -469,6 +512,7 @@ fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
         if (median_of(b->trial_ms[c]) < median_of(b->trial_ms[best])) best = c;
       b->grid = kCandidates[best][0];
       b->order = kCandidates[best][1];
+      b->cand = best;
       b->tuned = true;
     }
   }
@@ -479,7 +523,7 @@ fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
       cudaGraph_t g;
       BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       fw2_status st = FW2_OK;
-      for (int s = 0; s < chunk && st == FW2_OK; ++s) st = enqueue_step(b, b->grid, b->order);
+      for (int s = 0; s < chunk && st == FW2_OK; ++s) st = enqueue_step(b, b->cand);
       cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
       if (st != FW2_OK) return st;
       BCK(b, ec);
@@ -508,7 +552,7 @@ fw2_status batch_run(fw2_batch *b, int64_t n_steps, int64_t *done) {
       left -= chunk;
     }
     for (int64_t s = 0; s < left; ++s) {
-      fw2_status st = enqueue_step(b, b->grid, b->order);
+      fw2_status st = enqueue_step(b, b->cand);
       if (st != FW2_OK) return st;
       ++*done;
     }
@@ -631,6 +675,12 @@ fw2_status fw2_batch_info(fw2_batch *b, int32_t *grid, int32_t *order, int64_t *
   if (grid) *grid = b->tuned ? b->grid : 0;
   if (order) *order = b->tuned ? b->order : -1;
   if (launches) *launches = b->launches;
+  return FW2_OK;
+}
+
+fw2_status fw2_batch_edge_weight(fw2_batch *b, double *weight) {
+  if (!b || !weight) return FW2_EINVAL;
+  *weight = b->tuned ? kCandidates[b->cand][2] / 10.0 : 0.0;
   return FW2_OK;
 }
 

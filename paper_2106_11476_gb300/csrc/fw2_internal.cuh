@@ -139,11 +139,13 @@ cudaError_t build_pipe2d_maps(const StepParams &P, int map_kind, PipeMaps *vel, 
 cudaError_t launch_pipe2d(bool vel, const StepParams &P, int map_kind, int grid, const PipeMaps &T,
                           cudaStream_t s);
 // batched form over a unit table {ctx, x0, y0, interior} of 128 x 8 half
-// tiles (no periodic context); Ps and Ts in device memory, one per context
+// tiles (no periodic context); Ps and Ts in device memory, one per context;
+// block b takes the units runs[b] .. runs[b + 1] - 1 (grid + 1 entries)
 constexpr int kPipeHalf = 8;  // rows of a pipelined half tile
 bool pipe2d_interior_half(const StepParams &P, int x0, int y0);
 cudaError_t launch_pipe2d_batched(bool vel, const StepParams *Ps, const PipeMaps *Ts, const int4 *units,
-                                  int n_units, int n_relax, int map_kind, int grid, cudaStream_t s);
+                                  int n_units, const int *runs, int n_relax, int map_kind, int grid,
+                                  cudaStream_t s);
 // persistent pipelined 3D half step (bf16 maps, N <= 3, no periodic axis),
 // in one of two layouts that compute the same result: the memory variables
 // staged in shared memory with the other arrays (kLayoutStaged; not with
@@ -163,10 +165,14 @@ cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMap
 // (pipe3d_staged_layout), which must agree within a launch
 size_t pipe3d_region_bytes();
 long long pipe3d_region(const StepParams &P, int grid, bool vel, void *out);
+// edge units of each of the context's items (n_edge) and units per item
+// (n_all), arrays of the item count pipe3d_region returns
+void pipe3d_item_units(const StepParams &P, int grid, bool vel, int *n_edge, int *n_all);
 bool pipe3d_staged_layout(bool vel, const StepParams &P);
+// block b takes the items runs[b] .. runs[b + 1] - 1 (grid + 1 entries)
 cudaError_t launch_pipe3d_batched(bool vel, bool cross, bool ps, int n_relax, const StepParams *Ps,
-                                  const void *Rs, const PipeMaps *Ts, const int2 *items, int n_items, int grid,
-                                  cudaStream_t s);
+                                  const void *Rs, const PipeMaps *Ts, const int2 *items, const int *runs,
+                                  int grid, cudaStream_t s);
 cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
 cudaError_t launch_vel3d_wide(const StepParams &P, int map_bf16, cudaStream_t s);

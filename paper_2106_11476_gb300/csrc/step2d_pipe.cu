@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // memory, and stages its tissue-index table, when the context changes.
 template <int N, typename Maps, bool VEL>
 __global__ void __launch_bounds__(kThreads, 1)
-    pipe2d_batched_kernel(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, int n_units) {
+    pipe2d_batched_kernel(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, const int *runs) {
   using G = Ring<N, Maps, VEL>;
   constexpr int kS = G::kStages, kStage = G::kStage;
   extern __shared__ __align__(128) float smem_raw[];
@@ -759,10 +759,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_mbarrier_init();
   }
   __syncthreads();
-  // a contiguous run of units per block: consecutive units share a context
+  // a contiguous run of units per block (runs[b] .. runs[b + 1]; the host
+  // balances the runs by the units' cost): consecutive units share a context
   // (one parameter and table load per context) and halo rows (L2)
-  const int h_end = (int)(((long long)n_units * (blockIdx.x + 1)) / gridDim.x);
-  int h = (int)(((long long)n_units * blockIdx.x) / gridDim.x);
+  const int h_end = runs[blockIdx.x + 1];
+  int h = runs[blockIdx.x];
   if (h >= h_end) return;
   unsigned phase = 0, pending = 0;
   // thread 0: the context whose tensor maps it last acquired (the runs of
@@ -851,25 +852,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int N, typename Maps, bool VEL>
-cudaError_t pipe_batched_launch(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, int n_units, int grid,
+cudaError_t pipe_batched_launch(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, const int *runs, int grid,
                                 cudaStream_t st) {
   constexpr size_t bytes = Ring<N, Maps, VEL>::kBytes;
   cudaError_t e = cudaFuncSetAttribute(pipe2d_batched_kernel<N, Maps, VEL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pipe2d_batched_kernel<N, Maps, VEL><<<grid, dim3(32, kThreads / 32), bytes, st>>>(Ps, Ts, units, n_units);
+  pipe2d_batched_kernel<N, Maps, VEL><<<grid, dim3(32, kThreads / 32), bytes, st>>>(Ps, Ts, units, runs);
   return cudaGetLastError();
 }
 
 template <typename Maps, bool VEL>
-cudaError_t pipe_batched_dispatch(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, int n_units,
+cudaError_t pipe_batched_dispatch(const StepParams *Ps, const PipeMaps *Ts, const int4 *units, const int *runs,
                                   int n_relax, int grid, cudaStream_t st) {
   switch (n_relax) {
-    case 0: return pipe_batched_launch<0, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
-    case 1: return pipe_batched_launch<1, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
-    case 2: return pipe_batched_launch<2, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
-    case 3: return pipe_batched_launch<3, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
-    case 4: return pipe_batched_launch<4, Maps, VEL>(Ps, Ts, units, n_units, grid, st);
+    case 0: return pipe_batched_launch<0, Maps, VEL>(Ps, Ts, units, runs, grid, st);
+    case 1: return pipe_batched_launch<1, Maps, VEL>(Ps, Ts, units, runs, grid, st);
+    case 2: return pipe_batched_launch<2, Maps, VEL>(Ps, Ts, units, runs, grid, st);
+    case 3: return pipe_batched_launch<3, Maps, VEL>(Ps, Ts, units, runs, grid, st);
+    case 4: return pipe_batched_launch<4, Maps, VEL>(Ps, Ts, units, runs, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -923,14 +924,15 @@ bool pipe2d_interior_half(const StepParams &P, int x0, int y0) {
 }
 
 cudaError_t launch_pipe2d_batched(bool vel, const StepParams *Ps, const PipeMaps *Ts, const int4 *units,
-                                  int n_units, int n_relax, int map_kind, int grid, cudaStream_t st) {
+                                  int n_units, const int *runs, int n_relax, int map_kind, int grid,
+                                  cudaStream_t st) {
   if (n_units <= 0) return cudaSuccess;
   if (map_kind == 2)
-    return vel ? pipe_batched_dispatch<IdxMaps, true>(Ps, Ts, units, n_units, n_relax, grid, st)
-               : pipe_batched_dispatch<IdxMaps, false>(Ps, Ts, units, n_units, n_relax, grid, st);
+    return vel ? pipe_batched_dispatch<IdxMaps, true>(Ps, Ts, units, runs, n_relax, grid, st)
+               : pipe_batched_dispatch<IdxMaps, false>(Ps, Ts, units, runs, n_relax, grid, st);
   if (map_kind == 0)
-    return vel ? pipe_batched_dispatch<DenseMaps<float>, true>(Ps, Ts, units, n_units, n_relax, grid, st)
-               : pipe_batched_dispatch<DenseMaps<float>, false>(Ps, Ts, units, n_units, n_relax, grid, st);
+    return vel ? pipe_batched_dispatch<DenseMaps<float>, true>(Ps, Ts, units, runs, n_relax, grid, st)
+               : pipe_batched_dispatch<DenseMaps<float>, false>(Ps, Ts, units, runs, n_relax, grid, st);
   return cudaErrorInvalidValue;
 }
 

@@ -57,7 +57,14 @@ constexpr int kSub = 4;    // cross-tap rings of v_x, v_y: planes k-1 .. k+1 and
 constexpr int kXsMax = 64; // widest x C-PML strip (cells per side) staged by TMA
 
 __host__ __device__ constexpr int ring_slot(int k) { return ((k % kSlots) + kSlots) % kSlots; }
-__host__ __device__ constexpr int sub_slot(int k) { return ((k % kSub) + kSub) % kSub; }
+static_assert((kSub & (kSub - 1)) == 0, "the sub-rings index by a mask");
+__host__ __device__ constexpr int sub_slot(int k) { return k & (kSub - 1); }
+// slot of plane k0 + m (0 <= m < kSlots) from the slot s0 of plane k0: one
+// modulo per unit instead of one per plane
+__device__ __forceinline__ int slot_after(int s0, int m) {
+  const int s = s0 + m;
+  return s >= kSlots ? s - kSlots : s;
+}
 
 // C-PML strip coefficients of a stage (bf16): x strip a then b, each
 // [N][8][L] (L <= kXsMax); y strip a, b and z strip a, b, each [N][8][128]
@@ -156,16 +163,16 @@ struct Region3 {
     if (zsL == 0) return -1;
     return strip_coord(k, nz, zsL);
   }
-  __device__ __forceinline__ long long items() const { return (long long)tnx * nhy * nseg; }
-  __device__ __forceinline__ void item(long long it, int &x0, int &y0, int &k0, int &k1) const {
+  __host__ __device__ __forceinline__ long long items() const { return (long long)tnx * nhy * nseg; }
+  __host__ __device__ __forceinline__ void item(long long it, int &x0, int &y0, int &k0, int &k1) const {
     const int ncols = tnx * nhy;
     const int col = (int)(it % ncols), seg = (int)(it / ncols);
     x0 = (col % tnx) * kTX;
     y0 = (col / tnx) * kHT;
     k0 = seg * seglen;
-    k1 = min(nz, k0 + seglen);
+    k1 = k0 + seglen < nz ? k0 + seglen : nz;
   }
-  __device__ __forceinline__ bool interior(int x0, int y0, int k) const {
+  __host__ __device__ __forceinline__ bool interior(int x0, int y0, int k) const {
     return x0 >= Lx && x0 + kTX + Lx <= nx && y0 >= Ly && y0 + kHT + Ly <= ny && k >= Lz && k + Lz < nz;
   }
 };
@@ -526,7 +533,8 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
   // derivatives: x, y from the halo plane of k (cell e at column lx + 4 + e),
   // z from the same cell of planes k-3 .. k+4 in the ring
   constexpr int kPl = S::kPlane;
-  const float *sp = ring + ring_slot(k) * kPl;
+  const int s0 = ring_slot(k - 3);  // planes k-3 .. k+4 of the ring: slots s0 + 0 .. 7
+  const float *sp = ring + slot_after(s0, 3) * kPl;
   const int sy = ly + 3;
   float2 D[3];
   {
@@ -554,7 +562,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
   {
     float2 zc[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) zc[m] = sld2(ring + ring_slot(k - 3 + m) * kPl + sy * kCW + lx + 4);
+    for (int m = 0; m < 8; ++m) zc[m] = sld2(ring + slot_after(s0, m) * kPl + sy * kCW + lx + 4);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       float d = 0.f;
@@ -567,7 +575,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
     // cross taps (Sec. 3.1) over both transverse axes, in the order of the
     // tile kernels: w row j, up / dn rows j +- 1 of plane k; zp, zm row j of
     // planes k +- 1; zp_up, zm_up row j+1, zp_dn row j-1 of those planes
-    const float *pp = ring + ring_slot(k + 1) * kPl, *pm = ring + ring_slot(k - 1) * kPl;
+    const float *pp = ring + slot_after(s0, 4) * kPl, *pm = ring + slot_after(s0, 2) * kPl;
     const Win6 w = win6(sp + sy * kCW, lx), up = win6(sp + (sy + 1) * kCW, lx), dn = win6(sp + (sy - 1) * kCW, lx);
     const Win6 zp = win6(pp + sy * kCW, lx), zm = win6(pm + sy * kCW, lx);
     const Win6 zp_up = win6(pp + (sy + 1) * kCW, lx), zm_up = win6(pm + (sy + 1) * kCW, lx);
@@ -622,7 +630,7 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
     const Face3 g = face3<true>(P, reinterpret_cast<const bf16 *>(st + S::oKm), x0, y0, k, lx, ly);
     const float Kr[3] = {g.r0, g.r1, g.r2}, Ku[2] = {g.u0, g.u1}, Kz[2] = {g.z0, g.z1};
     const float *pr = sp + sy * kCW + lx + 4, *pu = sp + (sy + 1) * kCW + lx + 4;
-    const float *pz = ring + ring_slot(k + 1) * kPl + sy * kCW + lx + 4;
+    const float *pz = ring + slot_after(s0, 4) * kPl + sy * kCW + lx + 4;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const float fx = mom_factor(Kr[e], Kr[e + 1], pr[e], pr[e + 1]);
@@ -661,6 +669,7 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 
   const long long Sn = P.npts_alloc;
   const int o = ly * kTX + lx;
   constexpr int kPl = S::kPlane;
+  const int s0 = ring_slot(k - 4);  // planes k-4 .. k+3 of the ring: slots s0 + 0 .. 7
   const float *subx = sub, *suby = sub + kSub * S::kXPlane;
   float2 D[3];
   {
@@ -695,8 +704,8 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 
     float2 zc[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m)
-      zc[m] = CROSS ? sld2(ring + ring_slot(k - 4 + m) * kPl + (ly + 1) * kCW + lx + 4)
-                    : sld2(ring + ring_slot(k - 4 + m) * kPl + o);
+      zc[m] = CROSS ? sld2(ring + slot_after(s0, m) * kPl + (ly + 1) * kCW + lx + 4)
+                    : sld2(ring + slot_after(s0, m) * kPl + o);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       float d = 0.f;
@@ -730,7 +739,7 @@ __device__ __forceinline__ void prs3_compute(const StepParams &P, const Region3 
                                   ((zp0.v[2 + e] - zp1.v[2 + e]) + (zm0.v[2 + e] - zm1.v[2 + e]))), el2(D[1], e));
     }
     {
-      const float *zk = ring + ring_slot(k) * kPl, *zk1 = ring + ring_slot(k - 1) * kPl;
+      const float *zk = ring + slot_after(s0, 4) * kPl, *zk1 = ring + slot_after(s0, 3) * kPl;
       const Win6 z0 = win6(zk + (ly + 1) * kCW, lx), z1 = win6(zk1 + (ly + 1) * kCW, lx);
       const Win6 u0 = win6(zk + (ly + 2) * kCW, lx), u1 = win6(zk1 + (ly + 2) * kCW, lx);
       const Win6 d0 = win6(zk + ly * kCW, lx), d1 = win6(zk1 + ly * kCW, lx);
@@ -899,7 +908,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int N, bool VEL, bool CROSS, bool PS>
 __global__ void __launch_bounds__(kThreads, 1)
     pipe3d_batched_kernel(const StepParams *Ps, const Region3 *Rs, const PipeMaps *Ts, const int2 *items,
-                          int n_items) {
+                          const int *runs) {
   using G = Ring3<N, VEL, CROSS, PS>;
   constexpr int kStage = G::kStage;
   extern __shared__ __align__(128) float smem_raw[];
@@ -911,8 +920,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *ring = smem + 2 * kStage;
   float *sub = ring + kSlots * G::kPlane;
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int h_end = (int)(((long long)n_items * (blockIdx.x + 1)) / gridDim.x);
-  int h = (int)(((long long)n_items * blockIdx.x) / gridDim.x);
+  // a contiguous run of items per block, balanced by the host over the
+  // items' edge and interior units
+  const int h_end = runs[blockIdx.x + 1];
+  int h = runs[blockIdx.x];
   if (h >= h_end) return;
   auto load_ctx = [&](int c) {  // every thread; callers put barriers around it
     const int *ps = reinterpret_cast<const int *>(Ps + c);
@@ -1030,23 +1041,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int N, bool VEL, bool CROSS, bool PS>
 cudaError_t pipe3_batched_launch(const StepParams *Ps, const Region3 *Rs, const PipeMaps *Ts, const int2 *items,
-                                 int n_items, int grid, cudaStream_t st) {
+                                 const int *runs, int grid, cudaStream_t st) {
   constexpr size_t bytes = Ring3<N, VEL, CROSS, PS>::kBytes;
   cudaError_t e = cudaFuncSetAttribute(pipe3d_batched_kernel<N, VEL, CROSS, PS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pipe3d_batched_kernel<N, VEL, CROSS, PS><<<grid, dim3(32, kThreads / 32), bytes, st>>>(Ps, Rs, Ts, items, n_items);
+  pipe3d_batched_kernel<N, VEL, CROSS, PS><<<grid, dim3(32, kThreads / 32), bytes, st>>>(Ps, Rs, Ts, items, runs);
   return cudaGetLastError();
 }
 
 template <bool VEL, bool CROSS, bool PS>
 cudaError_t pipe3_batched_dispatch(int n_relax, const StepParams *Ps, const Region3 *Rs, const PipeMaps *Ts,
-                                   const int2 *items, int n_items, int grid, cudaStream_t st) {
+                                   const int2 *items, const int *runs, int grid, cudaStream_t st) {
   switch (n_relax) {
-    case 0: return pipe3_batched_launch<0, VEL, CROSS, PS>(Ps, Rs, Ts, items, n_items, grid, st);
-    case 1: return pipe3_batched_launch<1, VEL, CROSS, PS>(Ps, Rs, Ts, items, n_items, grid, st);
-    case 2: return pipe3_batched_launch<2, VEL, CROSS, PS>(Ps, Rs, Ts, items, n_items, grid, st);
-    case 3: return pipe3_batched_launch<3, VEL, CROSS, PS>(Ps, Rs, Ts, items, n_items, grid, st);
+    case 0: return pipe3_batched_launch<0, VEL, CROSS, PS>(Ps, Rs, Ts, items, runs, grid, st);
+    case 1: return pipe3_batched_launch<1, VEL, CROSS, PS>(Ps, Rs, Ts, items, runs, grid, st);
+    case 2: return pipe3_batched_launch<2, VEL, CROSS, PS>(Ps, Rs, Ts, items, runs, grid, st);
+    case 3: return pipe3_batched_launch<3, VEL, CROSS, PS>(Ps, Rs, Ts, items, runs, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1238,18 +1249,31 @@ long long pipe3d_region(const StepParams &P, int grid, bool vel, void *out) {
 
 bool pipe3d_staged_layout(bool vel, const StepParams &P) { return psi_staged(vel, P); }
 
+void pipe3d_item_units(const StepParams &P, int grid, bool vel, int *n_edge, int *n_all) {
+  const Region3 R = region3_of(P, grid, psi_staged(vel, P));
+  const long long n = R.items();
+  for (long long it = 0; it < n; ++it) {
+    int x0, y0, k0, k1;
+    R.item(it, x0, y0, k0, k1);
+    int e = 0;
+    for (int k = k0; k < k1; ++k) e += R.interior(x0, y0, k) ? 0 : 1;
+    n_edge[it] = e;
+    n_all[it] = k1 - k0;
+  }
+}
+
 cudaError_t launch_pipe3d_batched(bool vel, bool cross, bool ps, int n_relax, const StepParams *Ps,
-                                  const void *Rs, const PipeMaps *Ts, const int2 *items, int n_items, int grid,
+                                  const void *Rs, const PipeMaps *Ts, const int2 *items, const int *runs, int grid,
                                   cudaStream_t st) {
   const Region3 *R = static_cast<const Region3 *>(Rs);
   if (cross)
-    return vel ? pipe3_batched_dispatch<true, true, false>(n_relax, Ps, R, Ts, items, n_items, grid, st)
-               : pipe3_batched_dispatch<false, true, false>(n_relax, Ps, R, Ts, items, n_items, grid, st);
+    return vel ? pipe3_batched_dispatch<true, true, false>(n_relax, Ps, R, Ts, items, runs, grid, st)
+               : pipe3_batched_dispatch<false, true, false>(n_relax, Ps, R, Ts, items, runs, grid, st);
   if (vel)
-    return ps ? pipe3_batched_dispatch<true, false, true>(n_relax, Ps, R, Ts, items, n_items, grid, st)
-              : pipe3_batched_dispatch<true, false, false>(n_relax, Ps, R, Ts, items, n_items, grid, st);
-  return ps ? pipe3_batched_dispatch<false, false, true>(n_relax, Ps, R, Ts, items, n_items, grid, st)
-            : pipe3_batched_dispatch<false, false, false>(n_relax, Ps, R, Ts, items, n_items, grid, st);
+    return ps ? pipe3_batched_dispatch<true, false, true>(n_relax, Ps, R, Ts, items, runs, grid, st)
+              : pipe3_batched_dispatch<true, false, false>(n_relax, Ps, R, Ts, items, runs, grid, st);
+  return ps ? pipe3_batched_dispatch<false, false, true>(n_relax, Ps, R, Ts, items, runs, grid, st)
+            : pipe3_batched_dispatch<false, false, false>(n_relax, Ps, R, Ts, items, runs, grid, st);
 }
 
 cudaError_t launch_pipe3d(bool vel, const StepParams &P, int grid, const PipeMaps &T, cudaStream_t st, int layout) {

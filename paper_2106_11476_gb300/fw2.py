@@ -111,6 +111,7 @@ EXPORTS = {
     "fw2_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "fw2_batch_synchronize": (C.c_int, [C.c_void_p]),
     "fw2_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "fw2_batch_edge_weight": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "fw2_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "fw2_batch_set_watch": (C.c_int, [C.c_void_p, C.c_int64, C.c_float]),
     "fw2_batch_set_budget": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -527,6 +528,14 @@ def fw2_batch_active(batch) -> int:
     n = C.c_int32()
     _bcheck(lib().fw2_batch_active(batch, C.byref(n)), batch)
     return n.value
+
+
+def fw2_batch_edge_weight(batch) -> float:
+    """Tuned edge-unit cost of the pipelined groups' runs, 0 before tuning
+    (fw2_batch_edge_weight)."""
+    w = C.c_double()
+    _bcheck(lib().fw2_batch_edge_weight(batch, C.byref(w)), batch)
+    return w.value
 
 
 def fw2_batch_destroy(batch):

@@ -56,6 +56,7 @@ def test_batch_equals_each_context_alone(fw2):
         fw2.fw2_batch_synchronize(batch)
         grid, order, launches = fw2.fw2_batch_info(batch)
         assert grid > 0 and order in (0, 1) and launches > 0
+        assert fw2.fw2_batch_edge_weight(batch) in (1.0, 1.5, 2.0, 3.0)
         for (p_ref, vx_ref, tr_ref), s in zip(alone, sims):
             np.testing.assert_array_equal(s.field("p"), p_ref)
             np.testing.assert_array_equal(s.field("vx"), vx_ref)
