@@ -102,25 +102,25 @@ def algorithmic_bytes(shape, N, L, nl, map_bytes=4, nl_vel=False):
     return vel, prs
 
 
-def algorithmic_bytes_indexed(shape, N, L, nl):
-    """As algorithmic_bytes for the tissue-index form: one uint8 index per
-    cell replaces the interior maps (the tables live in shared memory) and is
-    charged to the velocity half step; cells inside a C-PML strip still read
-    that axis' float a, b."""
+def algorithmic_bytes_indexed(shape, N, L, nl, index_bytes=1):
+    """As algorithmic_bytes for the tissue-index form: one index per cell
+    (uint8, or uint16 with index_bytes = 2) replaces the interior maps (the
+    tables live in shared memory or L2) and is charged to the velocity half
+    step; cells inside a C-PML strip still read that axis' float a, b."""
     nd = len(shape)
     coef = sum(cnt * len(axes_in) * 2 * N * 4 for axes_in, cnt in strip_cell_counts(shape, L).items())
     n = int(np.prod(shape))
-    vel = n * (1 + nd * 8 + nd * N * 8) + coef
+    vel = n * (index_bytes + nd * 8 + nd * N * 8) + coef
     prs = n * (8 + nd * N * 8) + coef
     return vel, prs
 
 
-def split_overhead_bytes(shape, indexed=False):
+def split_overhead_bytes(shape, indexed=False, index_bytes=1):
     """Bytes per launch that the two-launch split reads beyond the step's
     minimum: p again in the velocity half step, v_q again in the pressure
     half step (and the tissue index again there)."""
     n = int(np.prod(shape))
-    return 4 * n, 4 * len(shape) * n + (n if indexed else 0)
+    return 4 * n, 4 * len(shape) * n + (index_bytes * n if indexed else 0)
 
 
 # --------------------------------------------------------------------------
@@ -236,7 +236,7 @@ def device_id_for_smi():
 def _round_of(maps):
     """The oracle's model of the maps the kernels stream (the index form's
     coefficients are the float maps gathered from its tables)."""
-    return "f32" if maps == "idx" else maps
+    return "f32" if maps in ("idx", "idx16") else maps
 
 
 def oracle_baseline(prob, steps, window, maps="f32", media=True):
@@ -386,11 +386,12 @@ def job_rate(world: int, cells: int, steps: int, seconds: float) -> float:
 def workload_problem(args, name, n, total_steps, rank):
     """(problem, maps, description) of a single-grid workload."""
     import synth
-    if name == "abdominal-idx":
+    if name in ("abdominal-idx", "abdominal-idx16"):
+        levels = 64 if name == "abdominal-idx" else 1024
         prob = synth.indexed_abdominal_problem(nx=n, ny=n, n_steps=total_steps, seed=1 + rank, n_elements=128,
-                                               focus_mm=40.0)
-        maps = args.maps or "idx"
-        desc = (f"2D heterogeneous nonlinear abdominal wall in tissue-index form (class x 64 scatterer "
+                                               focus_mm=40.0, levels=levels)
+        maps = args.maps or ("idx" if name == "abdominal-idx" else "idx16")
+        desc = (f"2D heterogeneous nonlinear abdominal wall in tissue-index form (class x {levels} scatterer "
                 f"levels), {n}x{n} cells at lambda/12 for 3 MHz, N=4, 128-element focused array, {maps} maps")
     elif name == "skull":
         prob = synth.skull_problem(n=n, n_steps=total_steps, seed=2 + rank)
@@ -422,12 +423,13 @@ def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=T
     total_steps = warmup + steps
     prob = synth.with_steps(prob, total_steps + (parity_steps if want_parity else 0))
     L = prob.pml_transition + prob.pml_bound
-    if maps == "idx":
-        vel_b, prs_b = algorithmic_bytes_indexed(prob.shape, prob.nrelax, L, prob.nl_mode != "off")
+    ib = {"idx": 1, "idx16": 2}.get(maps, 0)
+    if ib:
+        vel_b, prs_b = algorithmic_bytes_indexed(prob.shape, prob.nrelax, L, prob.nl_mode != "off", index_bytes=ib)
     else:
         vel_b, prs_b = algorithmic_bytes(prob.shape, prob.nrelax, L, prob.nl_mode != "off",
                                          map_bytes={"f32": 4, "bf16": 2}[maps], nl_vel=prob.nl_mode == "literal")
-    vel_o, prs_o = split_overhead_bytes(prob.shape, indexed=maps == "idx")
+    vel_o, prs_o = split_overhead_bytes(prob.shape, indexed=ib > 0, index_bytes=max(ib, 1))
     stream = torch.cuda.current_stream()
     sim = fw2.Simulation(prob, stream=stream, map_precision=maps, kernel_path=args.kernel_path)
     sim.step(warmup)
@@ -524,9 +526,10 @@ def end_to_end(args, prob, maps, steps, world, dist, stream):
         t_ = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         pinned[id(t_)] = t_
         return t_
-    if maps == "idx":
+    if maps in ("idx", "idx16"):
         tabs = {k: pin(v) for k, v in prob.tables.items()}
-        hp = dataclasses.replace(prob, tissue=pin(prob.tissue), tables=tabs)
+        hp = dataclasses.replace(prob, tissue=pin(prob.tissue.astype(np.uint16).view(np.int16)
+                                                  if maps == "idx16" else prob.tissue), tables=tabs)
         used = [hp.tissue] + [tabs[k] for k in ("c", "rho", "kappa1", "kappa2", "d1", "alpha1", "d2", "alpha2")]
         if prob.nl_mode != "off":
             used.append(tabs["beta"])
@@ -1024,10 +1027,10 @@ def main():
     ap.add_argument("--batch-policy", default="gang", choices=["gang", "continuous"],
                     help="batch: admit a group when the previous one has left, or whenever the next problem fits")
     ap.add_argument("--workload", default="abdominal",
-                    choices=["abdominal", "abdominal-idx", "skull", "plain", "batch", "serve"],
+                    choices=["abdominal", "abdominal-idx", "abdominal-idx16", "skull", "plain", "batch", "serve"],
                     help="abdominal: 2D 4096^2 nonlinear (default); abdominal-idx: the same in tissue-index "
                          "form; skull: 3D 768^3 with bf16 maps; plain: 2D 512^2 homogeneous line source")
-    ap.add_argument("--maps", default=None, choices=["f32", "bf16", "idx"],
+    ap.add_argument("--maps", default=None, choices=["f32", "bf16", "idx", "idx16"],
                     help="override the map storage of the workload")
     ap.add_argument("--kernel-path", default="auto", choices=["auto", "tile", "pipe", "pipe-staged", "pipe-registers"],
                     help="half-step kernels (bitwise the same results); pipe-staged / pipe-registers fix the layout "

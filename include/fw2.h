@@ -66,9 +66,11 @@ enum { FW2_BC_ZERO = 0, FW2_BC_PERIODIC = 1 };
  * propagates with speed c0 + (beta - 1) v. */
 enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2, FW2_NL_LITERAL = 3 };
 /* storage of the coefficient maps: float, bf16 (b kept as 1 - b), or a
- * uint8 tissue index per cell into per-tissue float tables (2D only; set the
- * medium with fw2_set_medium_indexed) */
-enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1, FW2_MAP_IDX_U8 = 2 };
+ * tissue index per cell into per-tissue float tables (2D only, N <= 4; set
+ * the medium with fw2_set_medium_indexed): uint8 for up to 256 tissues (the
+ * tables in shared memory, pipelined or tile kernels) or uint16 for up to
+ * 65536 (the tables read through L2, tile kernels) */
+enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1, FW2_MAP_IDX_U8 = 2, FW2_MAP_IDX_U16 = 3 };
 /* C-PML geometry (Sec. 3.3, Table 1).  In both readings the nu >= 2
  * parameters fall to zero over the inner L_T cells with the cosine transition
  * and kappa is kept, and d^{nu=1} ramps as a polynomial over all L_T + L_B
@@ -138,7 +140,7 @@ typedef struct {
   int32_t pml_transition;/* L_T, cells per side (Sec. 3.3) */
   int32_t pml_bound;     /* L_B, cells per side */
   int32_t pml_reading;   /* FW2_PML_C (default), FW2_PML_A or FW2_PML_NO_TRANSITION */
-  int32_t map_precision; /* FW2_MAP_F32, FW2_MAP_BF16 or FW2_MAP_IDX_U8 (2D) storage of the maps */
+  int32_t map_precision; /* FW2_MAP_F32, FW2_MAP_BF16, FW2_MAP_IDX_U8 or FW2_MAP_IDX_U16 (2D) storage of the maps */
   double pml_rc;         /* reflection target R_c of Table 1 (default 1e-3) */
   double pml_npow;       /* polynomial order of the d ramp (default 2) */
   double pml_cp;         /* c_p of Table 1 [m/s]; <= 0: largest c of the medium */
@@ -178,15 +180,16 @@ fw2_status fw2_create(const fw2_config *cfg, fw2_ctx **out);
 fw2_status fw2_set_medium(fw2_ctx *ctx, const float *c, const float *rho,
                           const float *beta, int32_t mem_space);
 
-/* Reduced-storage medium (map_precision FW2_MAP_IDX_U8): every cell holds a
- * tissue index tissue[n_pts] < n_tissue <= 256, and the material and
+/* Reduced-storage medium (map_precision FW2_MAP_IDX_U8 or FW2_MAP_IDX_U16):
+ * every cell holds a tissue index tissue[n_pts] < n_tissue, uint8 with
+ * n_tissue <= 256 or uint16 with n_tissue <= 65536, and the material and
  * relaxation parameters of Eqs. (wave1)-(general6) and Sec. 3.2 are
  * per-tissue tables: c, rho, beta (nullable when linear) [n_tissue];
  * relax->kappa1, kappa2 [n_tissue]; relax->d1, alpha1, d2, alpha2
  * [N][n_tissue].  The result equals fw2_set_medium + fw2_set_relaxation with
  * the tables gathered per cell; the C-PML still ramps per cell.  Replaces
  * both calls.  EINVAL on an index >= n_tissue or bad sizes. */
-fw2_status fw2_set_medium_indexed(fw2_ctx *ctx, const uint8_t *tissue, int32_t n_tissue,
+fw2_status fw2_set_medium_indexed(fw2_ctx *ctx, const void *tissue, int32_t n_tissue,
                                   const float *c, const float *rho, const float *beta,
                                   const fw2_relax_desc *relax, int32_t mem_space);
 
@@ -289,7 +292,7 @@ fw2_status fw2_set_watch(fw2_ctx *ctx, int64_t every, float bound);
  * fastest median is kept; every configuration computes the same result.  A
  * configuration is a persistent grid size and tile order for the tile path
  * and, for the pipelined groups, the cost of an edge unit (C-PML strips,
- * clamps) relative to an interior one, 1, 1.5, 2 or 3, by which the work
+ * clamps) relative to an interior one, 1.5, 2.5, 3.5 or 5, by which the work
  * table is split into the blocks' contiguous runs of about equal cost. */
 typedef struct fw2_batch fw2_batch;
 /* Contexts are borrowed (they must outlive the batch), with medium set;

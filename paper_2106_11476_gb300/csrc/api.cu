@@ -161,8 +161,14 @@ fw2_status finalize(fw2_ctx *c) {
     Q.gext[q] = (int)(c->subdomain ? c->gext[q] : ext[q]);
     Q.goff[q] = (int)(c->subdomain ? c->goff[q] : 0);
   }
-  Q.tissue_in = c->map_kind == FW2_MAP_IDX_U8 ? c->raw_tissue : nullptr;
+  const bool indexed = c->map_kind == FW2_MAP_IDX_U8 || c->map_kind == FW2_MAP_IDX_U16;
+  const bool wide = c->map_kind == FW2_MAP_IDX_U16;
+  Q.tissue_in = indexed ? c->raw_tissue : nullptr;
+  Q.tissue_wide = wide ? 1 : 0;
   Q.n_tissue = c->n_tissue;
+  // table field stride: 256 for the uint8 form (its kernels stage the table
+  // at that stride), the tissue count rounded up to 4 for the uint16 form
+  Q.tab_stride = wide ? (c->n_tissue + 3) / 4 * 4 : kTissues;
   // medium scan: c_max (high-frequency) and validity
   CK(c, cudaMemsetAsync(c->d_scan, 0, 2 * sizeof(unsigned long long), c->stream));
   CK(c, cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream));
@@ -191,8 +197,7 @@ fw2_status finalize(fw2_ctx *c) {
   const double cp = cfg.pml_cp > 0.0 ? cfg.pml_cp : cm;
   Q.d_target = L > 0 ? -(cfg.pml_npow + 1.0) * cp * std::log(cfg.pml_rc) / (2.0 * L * cfg.h) : 0.0;
   // map allocation: 5 cell maps + 4N interior + strips (dense forms), or the
-  // per-tissue table + the pitched uint8 index + strips (index form)
-  const bool indexed = c->map_kind == FW2_MAP_IDX_U8;
+  // per-tissue table + the pitched index + strips (index form)
   const size_t es = c->map_kind == FW2_MAP_BF16 ? 2 : 4;
   const size_t cell_bytes = indexed ? 0 : align256(es * (size_t)c->npts_alloc);
   long long strip_nu[3] = {0, 0, 0};
@@ -202,8 +207,8 @@ fw2_status finalize(fw2_ctx *c) {
     strip_nu[1] = (long long)c->nz * 2 * L * c->pitch;
     if (c->nd == 3) strip_nu[2] = (long long)2 * L * c->ny * c->pitch;
   }
-  const size_t table_bytes = indexed ? align256(sizeof(float) * kTableFields * kTissues) : 0;
-  const size_t index_bytes = indexed ? align256((size_t)c->npts_alloc) : 0;
+  const size_t table_bytes = indexed ? align256(sizeof(float) * kTableFields * (size_t)Q.tab_stride) : 0;
+  const size_t index_bytes = indexed ? align256((wide ? 2 : 1) * (size_t)c->npts_alloc) : 0;
   size_t total = 5 * cell_bytes + 4 * (size_t)c->N * cell_bytes + table_bytes + index_bytes;
   size_t strip_bytes[3];
   for (int q = 0; q < 3; ++q) {
@@ -222,7 +227,7 @@ fw2_status finalize(fw2_ctx *c) {
   char *cur = c->maps;
   auto take = [&](size_t b) { char *r = cur; cur += b; return (void *)r; };
   Q.table_out = indexed ? (float *)take(table_bytes) : nullptr;
-  Q.tissue_out = indexed ? (unsigned char *)take(index_bytes) : nullptr;
+  Q.tissue_out = indexed ? take(index_bytes) : nullptr;
   Q.K = take(cell_bytes); Q.rho_o = take(cell_bytes); Q.chi = take(cell_bytes);
   Q.ik1 = take(cell_bytes); Q.ik2 = take(cell_bytes);
   const size_t iso = (size_t)c->N * cell_bytes;
@@ -270,8 +275,9 @@ fw2_status finalize(fw2_ctx *c) {
   P.p = c->p;
   P.K = Q.K; P.rho = Q.rho_o; P.chi = Q.chi; P.ik1 = Q.ik1; P.ik2 = Q.ik2;
   P.a1 = Q.a1; P.b1 = Q.b1; P.a2 = Q.a2; P.b2 = Q.b2;
-  P.tissue = Q.tissue_out;
+  P.tissue = static_cast<const unsigned char *>(Q.tissue_out);
   P.table = Q.table_out;
+  P.tab_stride = Q.tab_stride;
   P.status = c->d_status;
   const bool forced_pipe = cfg.kernel_path >= FW2_PATH_PIPE;
   if (c->nd == 2)
@@ -632,11 +638,12 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
   }
   if (cfg.pml_reading != FW2_PML_A && cfg.pml_reading != FW2_PML_C && cfg.pml_reading != FW2_PML_NO_TRANSITION)
     return fail(nullptr, FW2_EINVAL, "bad pml_reading (FW2_PML_A = 0, FW2_PML_C = 2 or FW2_PML_NO_TRANSITION = 3)");
-  if (cfg.map_precision < FW2_MAP_F32 || cfg.map_precision > FW2_MAP_IDX_U8)
+  if (cfg.map_precision < FW2_MAP_F32 || cfg.map_precision > FW2_MAP_IDX_U16)
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
-  if (cfg.map_precision == FW2_MAP_IDX_U8 && cfg.ndim != 2)
+  const bool idx_form = cfg.map_precision == FW2_MAP_IDX_U8 || cfg.map_precision == FW2_MAP_IDX_U16;
+  if (idx_form && cfg.ndim != 2)
     return fail(nullptr, FW2_EUNSUPPORTED, "tissue-index maps are implemented for 2D grids");
-  if (cfg.map_precision == FW2_MAP_IDX_U8 && cfg.n_relax > kTabSlots)
+  if (idx_form && cfg.n_relax > kTabSlots)
     return fail(nullptr, FW2_EUNSUPPORTED, "tissue-index tables hold up to %d mechanisms", kTabSlots);
   if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_LITERAL) return fail(nullptr, FW2_EINVAL, "bad nl_mode");
   if (cfg.mem_alignment != FW2_MEM_CENTRED && cfg.mem_alignment != FW2_MEM_ENDPOINT)
@@ -746,7 +753,8 @@ fw2_status fw2_release_memory(void) {
 
 fw2_status fw2_set_medium(fw2_ctx *c, const float *cc, const float *rho, const float *beta, int32_t mem_space) {
   if (!c) return FW2_EINVAL;
-  if (c->map_kind == FW2_MAP_IDX_U8) return fail(c, FW2_EINVAL, "tissue-index contexts take fw2_set_medium_indexed");
+  if (c->map_kind == FW2_MAP_IDX_U8 || c->map_kind == FW2_MAP_IDX_U16)
+    return fail(c, FW2_EINVAL, "tissue-index contexts take fw2_set_medium_indexed");
   if (!cc || !rho) return fail(c, FW2_EINVAL, "c and rho are required");
   if (c->cfg.nl_mode != FW2_NL_OFF && !beta) return fail(c, FW2_EINVAL, "beta is required when nl_mode != OFF");
   if (mem_space != FW2_MEM_HOST && mem_space != FW2_MEM_DEVICE) return fail(c, FW2_EINVAL, "bad mem_space");
@@ -768,7 +776,8 @@ fw2_status fw2_set_medium(fw2_ctx *c, const float *cc, const float *rho, const f
 
 fw2_status fw2_set_relaxation(fw2_ctx *c, const fw2_relax_desc *d) {
   if (!c) return FW2_EINVAL;
-  if (c->map_kind == FW2_MAP_IDX_U8) return fail(c, FW2_EINVAL, "tissue-index contexts take fw2_set_medium_indexed");
+  if (c->map_kind == FW2_MAP_IDX_U8 || c->map_kind == FW2_MAP_IDX_U16)
+    return fail(c, FW2_EINVAL, "tissue-index contexts take fw2_set_medium_indexed");
   if (!d) return fail(c, FW2_EINVAL, "relaxation descriptor is null");
   if (c->N == 0) return fail(c, FW2_EINVAL, "n_relax is 0: no relaxation parameters to set");
   if (!d->kappa1 || !d->kappa2 || !d->d1 || !d->alpha1 || !d->d2 || !d->alpha2)
@@ -788,13 +797,17 @@ fw2_status fw2_set_relaxation(fw2_ctx *c, const fw2_relax_desc *d) {
   return FW2_OK;
 }
 
-fw2_status fw2_set_medium_indexed(fw2_ctx *c, const uint8_t *tissue, int32_t n_tissue, const float *cc,
+fw2_status fw2_set_medium_indexed(fw2_ctx *c, const void *tissue, int32_t n_tissue, const float *cc,
                                   const float *rho, const float *beta, const fw2_relax_desc *relax,
                                   int32_t mem_space) {
   if (!c) return FW2_EINVAL;
-  if (c->map_kind != FW2_MAP_IDX_U8) return fail(c, FW2_EINVAL, "fw2_set_medium_indexed needs map_precision FW2_MAP_IDX_U8");
+  if (c->map_kind != FW2_MAP_IDX_U8 && c->map_kind != FW2_MAP_IDX_U16)
+    return fail(c, FW2_EINVAL, "fw2_set_medium_indexed needs map_precision FW2_MAP_IDX_U8 or FW2_MAP_IDX_U16");
   if (!tissue || !cc || !rho) return fail(c, FW2_EINVAL, "tissue, c and rho are required");
-  if (n_tissue < 1 || n_tissue > kTissues) return fail(c, FW2_EINVAL, "n_tissue = %d outside [1, 256]", n_tissue);
+  const bool wide = c->map_kind == FW2_MAP_IDX_U16;
+  const int max_tissue = wide ? 65536 : kTissues;
+  if (n_tissue < 1 || n_tissue > max_tissue)
+    return fail(c, FW2_EINVAL, "n_tissue = %d outside [1, %d]", n_tissue, max_tissue);
   if (c->cfg.nl_mode != FW2_NL_OFF && !beta) return fail(c, FW2_EINVAL, "beta is required when nl_mode != OFF");
   if (c->N > 0 && (!relax || !relax->kappa1 || !relax->kappa2 || !relax->d1 || !relax->alpha1 || !relax->d2 ||
                    !relax->alpha2))
@@ -811,9 +824,10 @@ fw2_status fw2_set_medium_indexed(fw2_ctx *c, const uint8_t *tissue, int32_t n_t
   c->raw_tissue = nullptr;
   void *m;
   fw2_status st;
-  if ((st = dalloc(c, (size_t)c->n_pts, &m)) != FW2_OK) return st;
-  c->raw_tissue = (unsigned char *)m;
-  if ((st = copy_in(c, c->raw_tissue, tissue, (size_t)c->n_pts, mem_space)) != FW2_OK) return st;
+  const size_t index_bytes = (wide ? 2 : 1) * (size_t)c->n_pts;
+  if ((st = dalloc(c, index_bytes, &m)) != FW2_OK) return st;
+  c->raw_tissue = m;
+  if ((st = copy_in(c, c->raw_tissue, tissue, index_bytes, mem_space)) != FW2_OK) return st;
   const size_t bt = sizeof(float) * (size_t)n_tissue, btN = bt * c->N;
   struct Item { float **dst; const float *src; size_t bytes; };
   std::vector<Item> items = {{&c->raw_c, cc, bt}, {&c->raw_rho, rho, bt}};

@@ -144,7 +144,7 @@ namespace {
 // (tenths) by which the pipelined groups split their unit tables into the
 // blocks' contiguous runs (edge units read C-PML strips and clamp; a run
 // of them takes longer than a run of interior units of the same length).
-const int kCandidates[4][3] = {{152 * 2, 0, 10}, {152 * 2, 1, 15}, {152, 0, 20}, {152 * 4, 1, 30}};
+const int kCandidates[4][3] = {{152 * 2, 0, 15}, {152 * 2, 1, 25}, {152, 0, 35}, {152 * 4, 1, 50}};
 
 // Boundaries of `grid` contiguous runs of the weighted items with about
 // equal weight each (grid + 1 entries, runs[0] = 0, runs[grid] = n).

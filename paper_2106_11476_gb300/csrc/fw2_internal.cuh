@@ -52,10 +52,12 @@ struct StepParams {
   const void *a1, *b1, *a2, *b2;          // interior [N][npts_alloc]
   const void *sa1[3], *sb1[3], *sa2[3], *sb2[3];  // strips
   long long strip_nu[3]; // elements between mechanisms in a strip array
-  // tissue-index form: uint8 index per cell and per-tissue tables
-  // ([field][256] floats, field order of maps.cuh)
+  // tissue-index form: index per cell (uint8, or uint16 for the wide form)
+  // and per-tissue tables ([field][tab_stride] floats, field order of
+  // maps.cuh; tab_stride 256 for uint8)
   const unsigned char *tissue;
   const float *table;
+  int tab_stride;
   unsigned int *status;  // device status word: bit 0 set when a bounded wait gave up
 };
 
@@ -114,7 +116,8 @@ constexpr int kTX = 128;
 constexpr int kTY = 16;
 constexpr int kBY = 8;
 
-// map_kind: 0 float maps, 1 bf16 maps, 2 uint8 tissue index + tables
+// map_kind: 0 float maps, 1 bf16 maps, 2 uint8 tissue index + tables in
+// shared memory, 3 uint16 tissue index + tables read through L2 (tile path)
 cudaError_t launch_vel2d(const StepParams &P, int map_kind, cudaStream_t s);
 cudaError_t launch_prs2d(const StepParams &P, int map_kind, cudaStream_t s);
 // the same for 5..8 mechanisms (dense maps; a second compilation of the tile

@@ -21,10 +21,12 @@ struct PrepParams {
   // tissue-index form they are tables [n_tissue] ([N][n_tissue]) read
   // through tissue_in[n_pts]
   const float *c, *rho, *beta, *k1, *k2, *d1, *al1, *d2, *al2;
-  const unsigned char *tissue_in;  // null: dense inputs
+  const void *tissue_in;           // null: dense inputs (uint8, or uint16 when wide)
   int n_tissue;
-  unsigned char *tissue_out;       // pitched uint8 index (index form)
-  float *table_out;                // [kTableFields][256] (index form)
+  int tissue_wide;                 // 1: uint16 index
+  void *tissue_out;                // pitched index (index form)
+  float *table_out;                // [kTableFields][tab_stride] (index form)
+  int tab_stride;
   // outputs (float or bf16)
   void *K, *rho_o, *chi, *ik1, *ik2, *a1, *b1, *a2, *b2;
   void *sa1[3], *sb1[3], *sa2[3], *sb2[3];
@@ -33,7 +35,7 @@ struct PrepParams {
 
 cudaError_t launch_medium_scan(const PrepParams &Q, unsigned long long *maxbits, int *bad,
                                cudaStream_t s);
-// map_kind: 0 float, 1 bf16, 2 tissue index
+// map_kind: 0 float, 1 bf16, 2 uint8 tissue index, 3 uint16 tissue index
 cudaError_t launch_prep(const PrepParams &Q, int map_kind, cudaStream_t s);
 
 // sources: field[tgt[u]] += sum_{e in [off[u], off[u+1])} row[col[e]]

@@ -110,4 +110,52 @@ struct IdxMaps {
   }
 };
 
+// IdxMaps16: one uint16 tissue index per cell (up to 65536 tissues); the
+// per-tissue tables ([field][tab_stride] floats, up to 5.5 MB) stay in global
+// memory and are read through L2 and the read-only cache.  Same table values
+// and arithmetic as IdxMaps.
+struct IdxMaps16 {
+  using StripT = float;
+  static constexpr int kSmemFloats = 1;
+  struct Cell {
+    ushort4 t;
+  };
+  const unsigned short *idx;
+  const float *tab;
+  int S;  // field stride of the table
+  __device__ __forceinline__ explicit IdxMaps16(const StepParams &P)
+      : idx(reinterpret_cast<const unsigned short *>(P.tissue)), tab(P.table), S(P.tab_stride) {}
+  __device__ __forceinline__ void stage(const StepParams &, float *, int) const {}
+  __device__ __forceinline__ void bind(const float *) {}
+  __device__ __forceinline__ Cell cell(long long c) const {
+    return {__ldg(reinterpret_cast<const ushort4 *>(idx + c))};
+  }
+  __device__ __forceinline__ float at(int field, int t) const { return __ldg(tab + field * S + t); }
+  __device__ __forceinline__ float4 look(int field, Cell x) const {
+    return make_float4(at(field, x.t.x), at(field, x.t.y), at(field, x.t.z), at(field, x.t.w));
+  }
+  __device__ __forceinline__ float rho_at(long long gidx) const { return at(kTabRho, __ldg(idx + gidx)); }
+  __device__ __forceinline__ float K_at(long long gidx) const { return at(kTabK, __ldg(idx + gidx)); }
+  __device__ __forceinline__ float4 Kv(Cell x) const { return look(kTabK, x); }
+  __device__ __forceinline__ float4 chiv(Cell x) const { return look(kTabChi, x); }
+  __device__ __forceinline__ float4 ik1(Cell x) const { return look(kTabIk1, x); }
+  __device__ __forceinline__ float4 ik2(Cell x) const { return look(kTabIk2, x); }
+  template <int OP>
+  __device__ __forceinline__ float4 a(Cell x, int nu) const {
+    return look(kTabRelax + (OP == 1 ? 0 : 2 * kTabSlots) + nu, x);
+  }
+  template <int OP>
+  __device__ __forceinline__ float4 b(Cell x, int nu) const {
+    return look(kTabRelax + (OP == 1 ? kTabSlots : 3 * kTabSlots) + nu, x);
+  }
+  template <int OP>
+  __device__ __forceinline__ float a1c(Cell x, int nu, int e) const {
+    return el(a<OP>(x, nu), e);
+  }
+  template <int OP>
+  __device__ __forceinline__ float b1c(Cell x, int nu, int e) const {
+    return el(b<OP>(x, nu), e);
+  }
+};
+
 }  // namespace fw2

@@ -21,9 +21,14 @@ namespace fw2 {
 
 namespace {
 
+// tissue index of input cell t (index form)
+__device__ __forceinline__ int tissue_at(const PrepParams &Q, long long t) {
+  return Q.tissue_wide ? (int)static_cast<const unsigned short *>(Q.tissue_in)[t]
+                       : (int)static_cast<const unsigned char *>(Q.tissue_in)[t];
+}
 // raw parameter of cell t (dense inputs) or of its tissue (index form)
 __device__ __forceinline__ long long src_of(const PrepParams &Q, long long t) {
-  return Q.tissue_in ? (long long)Q.tissue_in[t] : t;
+  return Q.tissue_in ? (long long)tissue_at(Q, t) : t;
 }
 __device__ __forceinline__ long long n_src(const PrepParams &Q) {
   return Q.tissue_in ? (long long)Q.n_tissue : (long long)Q.nx * Q.ny * Q.nz;
@@ -117,32 +122,33 @@ __global__ void cell_maps_kernel(const PrepParams Q) {
   }
 }
 
-// Tissue-index form: per-tissue coefficient table ([field][256], field order
-// of maps.cuh) with the same arithmetic as the per-cell maps, and the index
-// copied into the pitched cell layout.
+// Tissue-index form: per-tissue coefficient table ([field][tab_stride],
+// field order of maps.cuh) with the same arithmetic as the per-cell maps, and
+// the index copied into the pitched cell layout.
 __global__ void table_kernel(const PrepParams Q) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Q.n_tissue) return;
   float *T = Q.table_out;
+  const int S = Q.tab_stride;  // field stride of this table
   const double c = Q.c[t], rho = Q.rho[t];
   const double K = rho * c * c;
-  T[kTabK * kTissues + t] = (float)K;
-  T[kTabRho * kTissues + t] = (float)rho;
+  T[kTabK * S + t] = (float)K;
+  T[kTabRho * S + t] = (float)rho;
   if (Q.nl_mode != 0) {
     const double beta = Q.beta[t];
-    T[kTabChi * kTissues + t] = (float)(Q.nl_mode != 2 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K);
+    T[kTabChi * S + t] = (float)(Q.nl_mode != 2 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K);
   }
   const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
-  T[kTabIk1 * kTissues + t] = (float)(1.0 / k1);
-  T[kTabIk2 * kTissues + t] = (float)(1.0 / k2);
+  T[kTabIk1 * S + t] = (float)(1.0 / k1);
+  T[kTabIk2 * S + t] = (float)(1.0 / k2);
   for (int nu = 0; nu < Q.N; ++nu) {
     double a, b;
     relax_ab(Q.d1[nu * Q.n_tissue + t], Q.al1[nu * Q.n_tissue + t], k1, Q.dt, a, b);
-    T[(kTabRelax + nu) * kTissues + t] = (float)a;
-    T[(kTabRelax + kTabSlots + nu) * kTissues + t] = (float)b;
+    T[(kTabRelax + nu) * S + t] = (float)a;
+    T[(kTabRelax + kTabSlots + nu) * S + t] = (float)b;
     relax_ab(Q.d2[nu * Q.n_tissue + t], Q.al2[nu * Q.n_tissue + t], k2, Q.dt, a, b);
-    T[(kTabRelax + 2 * kTabSlots + nu) * kTissues + t] = (float)a;
-    T[(kTabRelax + 3 * kTabSlots + nu) * kTissues + t] = (float)b;
+    T[(kTabRelax + 2 * kTabSlots + nu) * S + t] = (float)a;
+    T[(kTabRelax + 3 * kTabSlots + nu) * S + t] = (float)b;
   }
 }
 
@@ -154,7 +160,9 @@ __global__ void index_copy_kernel(const PrepParams Q) {
     const long long r = t / Q.nx;
     const int j = (int)(r % Q.ny);
     const int k = (int)(r / Q.ny);
-    Q.tissue_out[(long long)k * Q.plane + (long long)j * Q.pitch + i] = Q.tissue_in[t];
+    const long long o = (long long)k * Q.plane + (long long)j * Q.pitch + i;
+    if (Q.tissue_wide) static_cast<unsigned short *>(Q.tissue_out)[o] = (unsigned short)tissue_at(Q, t);
+    else static_cast<unsigned char *>(Q.tissue_out)[o] = (unsigned char)tissue_at(Q, t);
   }
 }
 
@@ -212,7 +220,7 @@ __global__ void medium_scan_kernel(const PrepParams Q, unsigned long long *maxbi
   int nbad = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    if (Q.tissue_in && Q.tissue_in[t] >= Q.n_tissue) {
+    if (Q.tissue_in && tissue_at(Q, t) >= Q.n_tissue) {
       ++nbad;
       continue;
     }
@@ -256,8 +264,8 @@ cudaError_t launch_medium_scan(const PrepParams &Q, unsigned long long *maxbits,
 
 cudaError_t launch_prep(const PrepParams &Q, int map_kind, cudaStream_t s) {
   const long long n = (long long)Q.nx * Q.ny * Q.nz;
-  if (map_kind == 2) {
-    table_kernel<<<1, 256, 0, s>>>(Q);
+  if (map_kind == 2 || map_kind == 3) {
+    table_kernel<<<(Q.n_tissue + 255) / 256, 256, 0, s>>>(Q);
     index_copy_kernel<<<grid_for(n), 256, 0, s>>>(Q);
   } else if (map_kind == 1) {
     cell_maps_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, s>>>(Q);

@@ -80,7 +80,8 @@ constexpr int kNLo = 0, kNHi = 4;
 
 // tissue-index tables hold kTabSlots mechanisms
 template <int N, typename Maps>
-constexpr bool kHasN = !(std::is_same<Maps, IdxMaps>::value && N > kTabSlots);
+constexpr bool kHasN = !((std::is_same<Maps, IdxMaps>::value || std::is_same<Maps, IdxMaps16>::value) &&
+                         N > kTabSlots);
 
 template <int N, typename Maps>
 cudaError_t vel2d_at(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
@@ -148,6 +149,7 @@ cudaError_t launch_vel2d(const StepParams &P, int map_kind, cudaStream_t s) {
 #endif
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY), b(32, kBY);
   if (map_kind == 2) return vel2d_dispatch<IdxMaps>(P, g, b, s);
+  if (map_kind == 3) return vel2d_dispatch<IdxMaps16>(P, g, b, s);
   return map_kind ? vel2d_dispatch<DenseMaps<__nv_bfloat16>>(P, g, b, s) : vel2d_dispatch<DenseMaps<float>>(P, g, b, s);
 }
 
@@ -159,6 +161,7 @@ cudaError_t launch_prs2d(const StepParams &P, int map_kind, cudaStream_t s) {
 #endif
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY), b(32, kBY);
   if (map_kind == 2) return prs2d_dispatch<IdxMaps>(P, g, b, s);
+  if (map_kind == 3) return prs2d_dispatch<IdxMaps16>(P, g, b, s);
   return map_kind ? prs2d_dispatch<DenseMaps<__nv_bfloat16>>(P, g, b, s) : prs2d_dispatch<DenseMaps<float>>(P, g, b, s);
 }
 
@@ -172,6 +175,7 @@ cudaError_t launch_batched2d(bool vel, const StepParams *Ps, const int4 *tiles, 
 #endif
   if (n_tiles <= 0) return cudaSuccess;
   if (map_kind == 2) return batched_dispatch<IdxMaps>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
+  if (map_kind == 3) return batched_dispatch<IdxMaps16>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
   if (map_kind == 1) return batched_dispatch<DenseMaps<__nv_bfloat16>>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
   return batched_dispatch<DenseMaps<float>>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
 }

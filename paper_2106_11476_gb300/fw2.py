@@ -22,7 +22,7 @@ STATUS_NAMES = ["FW2_OK", "FW2_EINVAL", "FW2_ENOMEM", "FW2_ECUDA", "FW2_ESTATE",
 MEM_HOST, MEM_DEVICE = 0, 1
 BC = {"zero": 0, "periodic": 1}
 NL = {"off": 0, "pressure": 1, "westervelt": 2, "literal": 3}
-MAP = {"f32": 0, "bf16": 1, "idx": 2}
+MAP = {"f32": 0, "bf16": 1, "idx": 2, "idx16": 3}
 PML_READING = {"A": 0, "C": 2, "K": 3}
 MEM_ALIGN = {"centred": 0, "endpoint": 1}
 SRC_KIND = {"p": 0, "vx": 1, "vy": 2, "vz": 3}
@@ -205,9 +205,19 @@ def fw2_set_relaxation(ctx, kappa1, kappa2, d1, alpha1, d2, alpha2):
     _check(lib().fw2_set_relaxation(ctx, C.byref(desc)), ctx)
 
 
-def fw2_set_medium_indexed(ctx, tissue, n_tissue: int, c, rho, beta, kappa1, kappa2, d1, alpha1, d2, alpha2):
-    """Tissue-index medium: uint8 index per cell, per-tissue tables."""
-    tissue = np.asarray(tissue, np.uint8) if isinstance(tissue, np.ndarray) else tissue
+def fw2_set_medium_indexed(ctx, tissue, n_tissue: int, c, rho, beta, kappa1, kappa2, d1, alpha1, d2, alpha2,
+                           wide: bool = False):
+    """Tissue-index medium: uint8 (wide: uint16) index per cell, per-tissue
+    tables (fw2_set_medium_indexed)."""
+    size = 2 if wide else 1
+    if isinstance(tissue, np.ndarray):
+        if wide and tissue.dtype == np.int16:
+            tissue = tissue.view(np.uint16)
+        if tissue.size and (tissue.min() < 0 or tissue.max() >= (1 << (8 * size))):
+            raise ValueError(f"tissue index outside the range of {8 * size} bits")
+        tissue = np.asarray(tissue, np.uint16 if wide else np.uint8)
+    elif tissue.element_size() != size:
+        raise ValueError(f"the tissue tensor must hold {size}-byte indices")
     tabs = [np.asarray(x, np.float32) if isinstance(x, np.ndarray) else x
             for x in (c, rho, beta, kappa1, kappa2, d1, alpha1, d2, alpha2)]
     space = _same_space(tissue, *tabs)
@@ -613,12 +623,22 @@ class Simulation:
                 fw2_set_subdomain(self.ctx, subdomain[0], subdomain[1])
             conv = (lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()) \
                 if device_inputs else (lambda a: a)
-            if map_precision == "idx":
+            if map_precision in ("idx", "idx16"):
                 t = prob.tables
-                fw2_set_medium_indexed(self.ctx, conv(prob.tissue), len(t["c"]), conv(t["c"]), conv(t["rho"]),
+                wide = map_precision == "idx16"
+                if isinstance(prob.tissue, np.ndarray):
+                    tissue = prob.tissue
+                    if tissue.size and tissue.max() >= (65536 if wide else 256):
+                        raise ValueError(f"tissue index beyond the {map_precision} form")
+                    tissue = tissue.astype(np.uint16) if wide else tissue.astype(np.uint8)
+                    # uint16 indices travel to the device as the same bits in int16
+                    targ = conv(tissue.view(np.int16)) if (wide and device_inputs) else conv(tissue)
+                else:                          # a tensor of 1- or 2-byte indices, passed as it is
+                    targ = prob.tissue
+                fw2_set_medium_indexed(self.ctx, targ, len(t["c"]), conv(t["c"]), conv(t["rho"]),
                                        conv(t["beta"]) if prob.nl_mode != "off" else None,
                                        conv(t["kappa1"]), conv(t["kappa2"]), conv(t["d1"]), conv(t["alpha1"]),
-                                       conv(t["d2"]), conv(t["alpha2"]))
+                                       conv(t["d2"]), conv(t["alpha2"]), wide=wide)
             else:
                 fw2_set_medium(self.ctx, conv(prob.c), conv(prob.rho),
                                conv(prob.beta) if prob.nl_mode != "off" else None)

@@ -85,7 +85,7 @@ class Problem:
     sensors: Optional[Sensors] = None
     n_steps: int = 0
     name: str = ""
-    # tissue-index form of the same medium (optional): uint8 index per cell
+    # tissue-index form of the same medium (optional): uint8 or uint16 index per cell
     # and per-tissue tables; the dense arrays above are these tables gathered
     tissue: Optional[np.ndarray] = None
     tables: Optional[dict] = None
@@ -513,14 +513,16 @@ def indexed_abdominal_problem(nx: int = 2048, ny: int = 1024, n_steps: int = 400
                               n_elements: int = 64, focus_mm: float = 30.0, focus_x_mm: float = 0.0,
                               nl: str = "pressure",
                               scatterers_per_cell: float = 20.0,
-                              pml_lambda: Tuple[float, float] = (3.0, 1.0), transmit: int = -1) -> Problem:
+                              pml_lambda: Tuple[float, float] = (3.0, 1.0), transmit: int = -1,
+                              levels: int = LEVELS) -> Problem:
     """Abdominal-wall-like medium in tissue-index form (reduced storage).
 
     Layered fat / muscle / connective tissue under a water coupling layer as
     in `abdominal_problem`, with one beta per tissue class, and sub-resolution
-    scatterers whose +-2 % c / rho perturbation is quantised to 63 levels: each
-    cell stores index = class * 64 + level into per-entry tables.  The dense
-    per-cell arrays are the tables gathered.  `transmit` >= 0 fires only that
+    scatterers whose +-2 % c / rho perturbation is quantised to `levels` - 1
+    levels (63 by default): each cell stores index = class * levels + level
+    into per-entry tables (uint8 while 4 * levels <= 256, else uint16).  The
+    dense per-cell arrays are the tables gathered.  `transmit` >= 0 fires only that
     element (a full-synthetic-aperture transmit event); -1 fires the focused
     array, focused at depth `focus_mm` and lateral offset `focus_x_mm` from
     the array centre.
@@ -550,21 +552,23 @@ def indexed_abdominal_problem(nx: int = 2048, ny: int = 1024, n_steps: int = 400
     n_sc = int(scatterers_per_cell / (ppw * ppw) * nx * ny)
     sy = rng.integers(0, ny, n_sc); sx = rng.integers(0, nx, n_sc)
     pert = np.clip(0.02 * rng.standard_normal(n_sc), -0.0799, 0.0799)
-    lv = (np.round((pert + 0.08) / 0.16 * 62) + 1).astype(np.uint8)      # 1..63
+    top_level = levels - 2
+    lv = np.round((pert + 0.08) / 0.16 * top_level).astype(np.int64) + 1   # 1 .. levels - 1
     keep = cls[sy, sx] != 0
+    level = level.astype(np.int64)
     level[sy[keep], sx[keep]] = lv[keep]
-    tissue = (cls.astype(np.uint16) * LEVELS + level).astype(np.uint8)
+    T = len(INDEXED_TISSUES) * levels
+    tissue = (cls.astype(np.int64) * levels + level).astype(np.uint8 if T <= 256 else np.uint16)
     sets_all = relaxation_sets()
-    T = len(INDEXED_TISSUES) * LEVELS
     tab = {k: np.zeros(T, np.float32) for k in ("c", "rho", "beta", "kappa1", "kappa2")}
     N = len(sets_all["N4_y1.1_fat"]["d1"])
     for k in ("d1", "alpha1", "d2", "alpha2"):
         tab[k] = np.zeros((N, T), np.float32)
     for ci, (name, c0, r0, a0, beta, key) in enumerate(INDEXED_TISSUES):
         sset = sets_all[key]
-        for lvl in range(LEVELS):
-            e = ci * LEVELS + lvl
-            f = 1.0 if lvl == 0 else 1.0 + (-0.08 + (lvl - 1) / 62 * 0.16)
+        for lvl in range(levels):
+            e = ci * levels + lvl
+            f = 1.0 if lvl == 0 else 1.0 + (-0.08 + (lvl - 1) / top_level * 0.16)
             tab["c"][e] = c0 * f; tab["rho"][e] = r0 * f; tab["beta"][e] = beta
             tab["kappa1"][e] = sset["kappa1"]; tab["kappa2"][e] = sset["kappa2"]
             for nu in range(N):

@@ -156,7 +156,7 @@ def compare_run(fw2, prob, steps, state=None, check_trace=True, rel=REL_L2, mx=M
         sim.set_state(state)
     sim.step(steps)
     sim.synchronize()
-    orc = OracleSim(prob, round_to="f32" if maps == "idx" else maps)
+    orc = OracleSim(prob, round_to="f32" if maps in ("idx", "idx16") else maps)
     if state is not None:
         orc.set_state(state)
     orc.run(steps)
@@ -602,6 +602,38 @@ def test_pipelined_path_equals_tile_path_tissue_index(fw2, nl):
 def test_parity_tissue_index_form(fw2):
     prob = synth.indexed_abdominal_problem(nx=320, ny=256, n_steps=300, n_elements=16)
     compare_run(fw2, prob, 300, maps="idx")
+
+
+def test_parity_wide_tissue_index_form(fw2):
+    """The uint16 index with more than 256 tissues (scatterer levels of 1023
+    steps per class), tables read through L2 by the tile kernels."""
+    prob = synth.indexed_abdominal_problem(nx=320, ny=256, n_steps=300, n_elements=16, levels=1024)
+    assert prob.tissue.dtype == np.uint16 and len(np.unique(prob.tissue)) > 256
+    sim = fw2.Simulation(prob, map_precision="idx16")
+    sim.step(1)
+    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    sim.close()
+    compare_run(fw2, prob, 300, maps="idx16")
+    with pytest.raises(ValueError):
+        fw2.Simulation(prob, map_precision="idx")        # beyond the uint8 form
+
+
+@pytest.mark.parametrize("nl", ["pressure", "literal"])
+def test_wide_tissue_index_equals_uint8_index_bitwise(fw2, nl):
+    """The same medium of at most 256 tissues as a uint16 index: the same
+    fields and traces as the uint8 form (tile and pipelined kernels)."""
+    prob = synth.indexed_abdominal_problem(nx=650, ny=300, n_steps=150, n_elements=16, nl=nl)
+    out = {}
+    for maps, path in (("idx", "tile"), ("idx", "pipe"), ("idx16", "auto")):
+        sim = fw2.Simulation(prob, map_precision=maps, kernel_path=path)
+        sim.step(150)
+        out[(maps, path)] = ({n: sim.field(n) for n in ("p", "vx", "vy")}, sim.trace.cpu().numpy())
+        sim.close()
+    ref = out[("idx16", "auto")]
+    for key in (("idx", "tile"), ("idx", "pipe")):
+        for n in ("p", "vx", "vy"):
+            np.testing.assert_array_equal(out[key][0][n], ref[0][n], err_msg=f"{key}: {n}")
+        np.testing.assert_array_equal(out[key][1], ref[1])
 
 
 def test_deterministic_bitwise(fw2):
