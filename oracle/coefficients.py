@@ -205,6 +205,23 @@ def to_bf16(x) -> np.ndarray:
     return r.view(np.float32).astype(np.float64)
 
 
+def f16_scale(values) -> float:
+    """Power-of-two scale of an FP16 coefficient map: the largest magnitude of
+    the map (as float32) divided by the scale lies in [2^14, 2^15)."""
+    m = float(np.max(np.abs(np.asarray(values, np.float64)).astype(np.float32))) if np.size(values) else 0.0
+    if not (m > 0.0) or not math.isfinite(m):
+        return 1.0
+    _, ex = math.frexp(m)                      # m in [2^(ex-1), 2^ex)
+    return math.ldexp(1.0, ex - 15)
+
+
+def to_f16(x, scale: float) -> np.ndarray:
+    """Storage rounding of an FP16 map: x / scale (exact) rounded to float32,
+    then to half (round to nearest even), times the scale, as FP64."""
+    q = (np.asarray(x, np.float64) / scale).astype(np.float32).astype(np.float16)
+    return q.astype(np.float64) * scale
+
+
 def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object]:
     """All coefficient arrays of the oracle step, FP64 (flat, x fastest):
     Eqs. (relaxation_a), (relaxation_b) per mechanism and axis, the C-PML
@@ -217,7 +234,12 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
     `round_to` = "f32" rounds every stored coefficient map to float32 first
     (models coefficient maps kept in single precision); "bf16" rounds them to
     bfloat16, with b stored as 1 - b (b = 1 - bf16(1 - b)) and the cell
-    density rounded before the face average (models bf16 maps).
+    density rounded before the face average (models bf16 maps); "f16" rounds
+    them to half precision after dividing each map by its power-of-two scale
+    (f16_scale of the map's values over the whole grid; the relaxation
+    coefficients of a mechanism share one scale over the tissue values of
+    every cell and the C-PML values of every axis), b as 1 - b (models FP16
+    maps; whole grids only).
     `window` = ((x0, x1), (y0, y1)[, (z0, z1)]) builds the coefficients of that
     sub-box of the grid only, with the boundary profiles and face densities of
     its global position.
@@ -240,7 +262,10 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
     rho = crop(prob.rho)
     # the face densities use the stored (possibly bf16) cell density; K and
     # chi are built from the input density and rounded as maps afterwards
-    rho_face_src = to_bf16(rho) if round_to == "bf16" else rho
+    if round_to == "f16" and any(tuple(w) != (0, sz) for w, sz in zip(window, prob.shape)):
+        raise ValueError("FP16 map rounding needs the whole grid (the map scales come from every cell)")
+    s_rho = f16_scale(rho) if round_to == "f16" else 1.0
+    rho_face_src = to_bf16(rho) if round_to == "bf16" else to_f16(rho, s_rho) if round_to == "f16" else rho
     N = prob.nrelax
     dt = float(prob.dt) if prob.dt and prob.dt > 0 else cfl_time_step(prob)
     K = rho * c * c
@@ -280,17 +305,20 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
         nb = np.take(rho_src[others], idx_hi, axis=ax).astype(np.float64)
         if round_to == "bf16":
             nb = to_bf16(nb)
+        elif round_to == "f16":
+            nb = to_f16(nb, s_rho)
         out[f"buoy{q}"] = (1.0 / (0.5 * (rho_face_src + nb))).ravel()
         if prob.nl_mode == "literal":
             # kappa_0 at the face of the momentum factor rho_0 (1 + kappa_0 p)
             # (Eq. general5): mean of the two cells' 1/K, from K as stored
             # (same neighbour rule as the density)
-            Kw = (to_bf16(K) if round_to == "bf16" else
+            s_K = f16_scale(K) if round_to == "f16" else 1.0
+            Kw = (to_bf16(K) if round_to == "bf16" else to_f16(K, s_K) if round_to == "f16" else
                   K.astype(np.float32).astype(np.float64) if round_to == "f32" else K)
             c_src, r_src = np.asarray(prob.c).reshape(gshape), rho_src
             K_src = r_src.astype(np.float64) * c_src.astype(np.float64) ** 2
             Knb = np.take(K_src[others], idx_hi, axis=ax)
-            Knb = (to_bf16(Knb) if round_to == "bf16" else
+            Knb = (to_bf16(Knb) if round_to == "bf16" else to_f16(Knb, s_K) if round_to == "f16" else
                    Knb.astype(np.float32).astype(np.float64) if round_to == "f32" else Knb)
             out[f"k0f{q}"] = (0.5 * (1.0 / Kw + 1.0 / Knb)).ravel()
         out[f"ik1{q}"] = (1.0 / k1).ravel()
@@ -323,6 +351,36 @@ def build(prob, round_to: Optional[str] = None, window=None) -> Dict[str, object
                 out[k] = 1.0 - to_bf16(1.0 - v)
             else:
                 out[k] = to_bf16(v)
+    elif round_to == "f16":
+        # the tissue (unstretched) coefficients of every cell take part in
+        # each mechanism's scale with the C-PML values of every axis
+        tissue_ab = {}
+        for nu in range(N):
+            for key, dname, aname, kap in (("1", "d1", "alpha1", k1), ("2", "d2", "alpha2", k2)):
+                a, b = relaxation_ab(crop(getattr(prob, dname)[nu]), crop(getattr(prob, aname)[nu]), kap, dt)
+                tissue_ab[(key, nu)] = (a.ravel(), b.ravel())
+        scale = {"K": f16_scale(out["K"])}
+        if out["chi"] is not None:
+            scale["chi"] = f16_scale(out["chi"])
+        scale["ik1"] = f16_scale(1.0 / k1)
+        scale["ik2"] = f16_scale(1.0 / k2)
+        for key in ("1", "2"):
+            for nu in range(N):
+                a_all = [tissue_ab[(key, nu)][0]] + [out[f"a{key}{q}"][nu] for q in range(nd)]
+                b_all = [1.0 - tissue_ab[(key, nu)][1]] + [1.0 - out[f"b{key}{q}"][nu] for q in range(nd)]
+                scale[f"a{key}", nu] = f16_scale(np.concatenate(a_all))
+                scale[f"b{key}", nu] = f16_scale(np.concatenate(b_all))
+        out["K"] = to_f16(out["K"], scale["K"])
+        if out["chi"] is not None:
+            out["chi"] = to_f16(out["chi"], scale["chi"])
+        for q in range(nd):
+            out[f"ik1{q}"] = to_f16(out[f"ik1{q}"], scale["ik1"])
+            out[f"ik2{q}"] = to_f16(out[f"ik2{q}"], scale["ik2"])
+            for key in ("1", "2"):
+                A, B = out[f"a{key}{q}"], out[f"b{key}{q}"]
+                for nu in range(N):
+                    A[nu] = to_f16(A[nu], scale[f"a{key}", nu])
+                    B[nu] = 1.0 - to_f16(1.0 - B[nu], scale[f"b{key}", nu])
     elif round_to is not None:
         raise ValueError(round_to)
     return out

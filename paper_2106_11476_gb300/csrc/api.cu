@@ -198,7 +198,7 @@ fw2_status finalize(fw2_ctx *c) {
   Q.d_target = L > 0 ? -(cfg.pml_npow + 1.0) * cp * std::log(cfg.pml_rc) / (2.0 * L * cfg.h) : 0.0;
   // map allocation: 5 cell maps + 4N interior + strips (dense forms), or the
   // per-tissue table + the pitched index + strips (index form)
-  const size_t es = c->map_kind == FW2_MAP_BF16 ? 2 : 4;
+  const size_t es = (c->map_kind == FW2_MAP_BF16 || c->map_kind == FW2_MAP_F16) ? 2 : 4;
   const size_t cell_bytes = indexed ? 0 : align256(es * (size_t)c->npts_alloc);
   long long strip_nu[3] = {0, 0, 0};
   const bool strips = L > 0 && c->N > 0;
@@ -239,6 +239,39 @@ fw2_status finalize(fw2_ctx *c) {
       Q.sa2[q] = take(strip_bytes[q]); Q.sb2[q] = take(strip_bytes[q]);
     }
   }
+  // FP16 maps: a scan pass for the largest magnitude of every map, then a
+  // power-of-two scale per map that puts it in [2^14, 2^15)
+  float scale[kMapScales];
+  for (int m = 0; m < kMapScales; ++m) {
+    scale[m] = 1.f;
+    Q.inv_scale[m] = 1.0;
+  }
+  if (c->map_kind == FW2_MAP_F16) {
+    void *mb;
+    fw2_status sm = dalloc(c, sizeof(unsigned int) * kMapScales, &mb);
+    if (sm != FW2_OK) return sm;
+    Q.f16_max = static_cast<unsigned int *>(mb);
+    unsigned int bits[kMapScales];
+    cudaError_t e = cudaMemsetAsync(mb, 0, sizeof bits, c->stream);
+    if (e == cudaSuccess) e = launch_prep_scan(Q, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits, mb, sizeof bits, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(c, mb);
+    Q.f16_max = nullptr;
+    CK(c, e);
+    c->launches += 1 + (strips ? c->nd : 0);
+    for (int m = 0; m < kMapScales; ++m) {
+      float mx;
+      std::memcpy(&mx, &bits[m], 4);
+      if (mx > 0.f && std::isfinite(mx)) {
+        int ex;
+        std::frexp((double)mx, &ex);             // mx in [2^(ex-1), 2^ex)
+        scale[m] = (float)std::ldexp(1.0, ex - 15);  // mx / scale in [2^14, 2^15)
+        Q.inv_scale[m] = std::ldexp(1.0, 15 - ex);
+      }
+    }
+  }
+  for (int m = 0; m < kMapScales; ++m) c->map_scale[m] = scale[m];
   CK(c, launch_prep(Q, c->map_kind, c->stream));
   c->launches += (indexed ? 2 : 1) + (strips ? c->nd : 0);
   CK(c, cudaStreamSynchronize(c->stream));
@@ -278,6 +311,7 @@ fw2_status finalize(fw2_ctx *c) {
   P.tissue = static_cast<const unsigned char *>(Q.tissue_out);
   P.table = Q.table_out;
   P.tab_stride = Q.tab_stride;
+  for (int m = 0; m < kMapScales; ++m) P.ms[m] = c->map_scale[m];
   P.status = c->d_status;
   const bool forced_pipe = cfg.kernel_path >= FW2_PATH_PIPE;
   if (c->nd == 2)
@@ -638,7 +672,7 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
   }
   if (cfg.pml_reading != FW2_PML_A && cfg.pml_reading != FW2_PML_C && cfg.pml_reading != FW2_PML_NO_TRANSITION)
     return fail(nullptr, FW2_EINVAL, "bad pml_reading (FW2_PML_A = 0, FW2_PML_C = 2 or FW2_PML_NO_TRANSITION = 3)");
-  if (cfg.map_precision < FW2_MAP_F32 || cfg.map_precision > FW2_MAP_IDX_U16)
+  if (cfg.map_precision < FW2_MAP_F32 || cfg.map_precision > FW2_MAP_F16)
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
   const bool idx_form = cfg.map_precision == FW2_MAP_IDX_U8 || cfg.map_precision == FW2_MAP_IDX_U16;
   if (idx_form && cfg.ndim != 2)

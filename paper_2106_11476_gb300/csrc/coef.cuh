@@ -18,12 +18,13 @@ __device__ __forceinline__ void coef4(const StepParams &P, int nu, long long c, 
   const long long iso = (long long)nu * P.npts_alloc + c;
   const MT *sa = static_cast<const MT *>(OP == 1 ? P.sa1[Q] : P.sa2[Q]);
   const MT *sb = static_cast<const MT *>(OP == 1 ? P.sb1[Q] : P.sb2[Q]);
+  const float s_a = P.ms[(OP == 1 ? kMsA1 : kMsA2) + nu], s_b = P.ms[(OP == 1 ? kMsB1 : kMsB2) + nu];
   const int L = P.L[Q];
   if (Q == 0) {
     const bool any = L > 0 && (i0 < L || i0 + 3 >= P.nx - L);
     if (!any) {
-      a = ldmap4(ia, iso);
-      b = ldb4(ib, iso);
+      a = ldmap4(ia, iso, s_a);
+      b = ldb4(ib, iso, s_b);
       return;
     }
     const long long row = (long long)nu * P.strip_nu[0] + ((long long)k * P.ny + j) * (2 * L);
@@ -34,11 +35,11 @@ __device__ __forceinline__ void coef4(const StepParams &P, int nu, long long c, 
       if (x < P.nx) {
         const int sc = strip_coord(x, P.nx, L);
         if (sc >= 0) {
-          av = ldmap(sa, row + sc);
-          bv = ldb(sb, row + sc);
+          av = ldmap(sa, row + sc, s_a);
+          bv = ldb(sb, row + sc, s_b);
         } else {
-          av = ldmap(ia, iso + e);
-          bv = ldb(ib, iso + e);
+          av = ldmap(ia, iso + e, s_a);
+          bv = ldb(ib, iso + e, s_b);
         }
       }
       el(a, e) = av;
@@ -47,14 +48,14 @@ __device__ __forceinline__ void coef4(const StepParams &P, int nu, long long c, 
   } else {
     const int sc = Q == 1 ? strip_coord(j, P.ny, L) : strip_coord(k, P.nz, L);
     if (sc < 0) {
-      a = ldmap4(ia, iso);
-      b = ldb4(ib, iso);
+      a = ldmap4(ia, iso, s_a);
+      b = ldb4(ib, iso, s_b);
     } else {
       const long long off =
           Q == 1 ? (long long)nu * P.strip_nu[1] + ((long long)k * (2 * L) + sc) * P.pitch + i0
                  : (long long)nu * P.strip_nu[2] + ((long long)sc * P.ny + j) * P.pitch + i0;
-      a = ldmap4(sa, off);
-      b = ldb4(sb, off);
+      a = ldmap4(sa, off, s_a);
+      b = ldb4(sb, off, s_b);
     }
   }
 }

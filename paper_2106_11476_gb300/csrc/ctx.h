@@ -50,6 +50,7 @@ struct fw2_ctx {
   float *raw_k1 = nullptr, *raw_k2 = nullptr, *raw_d1 = nullptr, *raw_al1 = nullptr, *raw_d2 = nullptr,
         *raw_al2 = nullptr;
   void *raw_tissue = nullptr;  // tissue-index form (uint8 or uint16 per cell)
+  float map_scale[fw2::kMapScales] = {};  // FP16 maps: value = stored x scale
   int n_tissue = 0;
   bool medium_set = false, relax_set = false, finalized = false;
   // coefficient maps

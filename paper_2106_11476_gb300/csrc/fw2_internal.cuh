@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,6 +23,14 @@ namespace fw2 {
 // maps); the pipelined 2D half steps and the tissue-index tables take up to
 // 4, the pipelined 3D half steps up to 3
 constexpr int kMaxRelax = 8;
+// Scales of the FP16 maps (StepParams::ms): every map is stored divided by a
+// power of two chosen from its largest magnitude; slots per map, per
+// mechanism for the relaxation coefficients (b kept as 1 - b)
+enum {
+  kMsK = 0, kMsRho = 1, kMsChi = 2, kMsIk1 = 3, kMsIk2 = 4,
+  kMsA1 = 5, kMsB1 = kMsA1 + kMaxRelax, kMsA2 = kMsB1 + kMaxRelax, kMsB2 = kMsA2 + kMaxRelax,
+  kMapScales = kMsB2 + kMaxRelax
+};
 constexpr int kTabSlots = 4;       // mechanism slots of the tissue-index tables
 constexpr int kPipe2dMaxRelax = 4;
 
@@ -59,6 +68,7 @@ struct StepParams {
   const float *table;
   int tab_stride;
   unsigned int *status;  // device status word: bit 0 set when a bounded wait gave up
+  float ms[kMapScales];  // FP16 maps: value = stored x ms[map] (1 for the other storages)
 };
 
 // ---------------------------------------------------------------- loads ---
@@ -85,6 +95,29 @@ __device__ __forceinline__ float4 ldb4(const __nv_bfloat16 *p, long long i) {
 }
 __device__ __forceinline__ float ldb(const float *p, long long i) { return ldmap(p, i); }
 __device__ __forceinline__ float ldb(const __nv_bfloat16 *p, long long i) { return 1.f - ldmap(p, i); }
+
+// The same loads with the map's scale s: FP16 maps hold value / s (s a power
+// of two, so the product is exact); float and bf16 maps ignore s.
+__device__ __forceinline__ float ldmap(const float *p, long long i, float) { return ldmap(p, i); }
+__device__ __forceinline__ float ldmap(const __nv_bfloat16 *p, long long i, float) { return ldmap(p, i); }
+__device__ __forceinline__ float ldmap(const __half *p, long long i, float s) { return __half2float(p[i]) * s; }
+__device__ __forceinline__ float4 ldmap4(const float *p, long long i, float) { return ldmap4(p, i); }
+__device__ __forceinline__ float4 ldmap4(const __nv_bfloat16 *p, long long i, float) { return ldmap4(p, i); }
+__device__ __forceinline__ float4 ldmap4(const __half *p, long long i, float s) {
+  uint2 u = __ldg(reinterpret_cast<const uint2 *>(p + i));
+  const float2 a = __half22float2(*reinterpret_cast<__half2 *>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<__half2 *>(&u.y));
+  return make_float4(a.x * s, a.y * s, b.x * s, b.y * s);
+}
+__device__ __forceinline__ float ldb(const float *p, long long i, float) { return ldb(p, i); }
+__device__ __forceinline__ float ldb(const __nv_bfloat16 *p, long long i, float) { return ldb(p, i); }
+__device__ __forceinline__ float ldb(const __half *p, long long i, float s) { return 1.f - ldmap(p, i, s); }
+__device__ __forceinline__ float4 ldb4(const float *p, long long i, float) { return ldb4(p, i); }
+__device__ __forceinline__ float4 ldb4(const __nv_bfloat16 *p, long long i, float) { return ldb4(p, i); }
+__device__ __forceinline__ float4 ldb4(const __half *p, long long i, float s) {
+  const float4 v = ldmap4(p, i, s);
+  return make_float4(1.f - v.x, 1.f - v.y, 1.f - v.z, 1.f - v.w);
+}
 
 // streaming state loads/stores: read once, write once per step
 __device__ __forceinline__ float4 ld_state4(const float *p, long long i) {
@@ -117,7 +150,8 @@ constexpr int kTY = 16;
 constexpr int kBY = 8;
 
 // map_kind: 0 float maps, 1 bf16 maps, 2 uint8 tissue index + tables in
-// shared memory, 3 uint16 tissue index + tables read through L2 (tile path)
+// shared memory, 3 uint16 tissue index + tables read through L2 (tile path),
+// 4 FP16 maps with a power-of-two scale per map (tile path)
 cudaError_t launch_vel2d(const StepParams &P, int map_kind, cudaStream_t s);
 cudaError_t launch_prs2d(const StepParams &P, int map_kind, cudaStream_t s);
 // the same for 5..8 mechanisms (dense maps; a second compilation of the tile
@@ -176,9 +210,10 @@ bool pipe3d_staged_layout(bool vel, const StepParams &P);
 cudaError_t launch_pipe3d_batched(bool vel, bool cross, bool ps, int n_relax, const StepParams *Ps,
                                   const void *Rs, const PipeMaps *Ts, const int2 *items, const int *runs,
                                   int grid, cudaStream_t s);
-cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s);
-cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s);
-cudaError_t launch_vel3d_wide(const StepParams &P, int map_bf16, cudaStream_t s);
-cudaError_t launch_prs3d_wide(const StepParams &P, int map_bf16, cudaStream_t s);
+// 3D tile kernels: map_kind 0 float, 1 bf16, 4 FP16
+cudaError_t launch_vel3d(const StepParams &P, int map_kind, cudaStream_t s);
+cudaError_t launch_prs3d(const StepParams &P, int map_kind, cudaStream_t s);
+cudaError_t launch_vel3d_wide(const StepParams &P, int map_kind, cudaStream_t s);
+cudaError_t launch_prs3d_wide(const StepParams &P, int map_kind, cudaStream_t s);
 
 }  // namespace fw2

@@ -31,12 +31,21 @@ struct PrepParams {
   void *K, *rho_o, *chi, *ik1, *ik2, *a1, *b1, *a2, *b2;
   void *sa1[3], *sb1[3], *sa2[3], *sb2[3];
   long long strip_nu[3];
+  // FP16 maps: each map is stored times inv_scale[map] (a power of two,
+  // slots of StepParams::ms), chosen from the maps' largest magnitudes that
+  // a scan pass first gathers into f16_max (float bits, device)
+  double inv_scale[kMapScales];
+  unsigned int *f16_max;
 };
 
 cudaError_t launch_medium_scan(const PrepParams &Q, unsigned long long *maxbits, int *bad,
                                cudaStream_t s);
-// map_kind: 0 float, 1 bf16, 2 uint8 tissue index, 3 uint16 tissue index
+// map_kind: 0 float, 1 bf16, 2 uint8 tissue index, 3 uint16 tissue index,
+// 4 FP16 (after launch_prep_scan and with Q.inv_scale set)
 cudaError_t launch_prep(const PrepParams &Q, int map_kind, cudaStream_t s);
+// FP16 maps: the largest magnitude of every map (cell maps and C-PML strips,
+// b as 1 - b) into Q.f16_max[kMapScales] (zeroed by the caller), as float bits
+cudaError_t launch_prep_scan(const PrepParams &Q, cudaStream_t s);
 
 // sources: field[tgt[u]] += sum_{e in [off[u], off[u+1])} row[col[e]]
 cudaError_t launch_inject(float *field, const long long *tgt, const int *off, const int *col,

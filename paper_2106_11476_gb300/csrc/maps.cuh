@@ -25,36 +25,37 @@ struct DenseMaps {
   };
   const T *K, *rho, *chi, *ik1_, *ik2_, *a1_, *b1_, *a2_, *b2_;
   long long S;
+  const float *ms;  // map scales (FP16 storage; ignored by float and bf16 loads)
   __device__ __forceinline__ explicit DenseMaps(const StepParams &P)
       : K(static_cast<const T *>(P.K)), rho(static_cast<const T *>(P.rho)), chi(static_cast<const T *>(P.chi)),
         ik1_(static_cast<const T *>(P.ik1)), ik2_(static_cast<const T *>(P.ik2)),
         a1_(static_cast<const T *>(P.a1)), b1_(static_cast<const T *>(P.b1)),
-        a2_(static_cast<const T *>(P.a2)), b2_(static_cast<const T *>(P.b2)), S(P.npts_alloc) {}
+        a2_(static_cast<const T *>(P.a2)), b2_(static_cast<const T *>(P.b2)), S(P.npts_alloc), ms(P.ms) {}
   __device__ __forceinline__ void stage(const StepParams &, float *, int) const {}
   __device__ __forceinline__ void bind(const float *) {}
   __device__ __forceinline__ Cell cell(long long c) const { return {c}; }
-  __device__ __forceinline__ float rho_at(long long gidx) const { return ldmap(rho, gidx); }
-  __device__ __forceinline__ float K_at(long long gidx) const { return ldmap(K, gidx); }
-  __device__ __forceinline__ float4 Kv(Cell x) const { return ldmap4(K, x.c); }
-  __device__ __forceinline__ float4 chiv(Cell x) const { return ldmap4(chi, x.c); }
-  __device__ __forceinline__ float4 ik1(Cell x) const { return ldmap4(ik1_, x.c); }
-  __device__ __forceinline__ float4 ik2(Cell x) const { return ldmap4(ik2_, x.c); }
+  __device__ __forceinline__ float rho_at(long long gidx) const { return ldmap(rho, gidx, ms[kMsRho]); }
+  __device__ __forceinline__ float K_at(long long gidx) const { return ldmap(K, gidx, ms[kMsK]); }
+  __device__ __forceinline__ float4 Kv(Cell x) const { return ldmap4(K, x.c, ms[kMsK]); }
+  __device__ __forceinline__ float4 chiv(Cell x) const { return ldmap4(chi, x.c, ms[kMsChi]); }
+  __device__ __forceinline__ float4 ik1(Cell x) const { return ldmap4(ik1_, x.c, ms[kMsIk1]); }
+  __device__ __forceinline__ float4 ik2(Cell x) const { return ldmap4(ik2_, x.c, ms[kMsIk2]); }
   template <int OP>
   __device__ __forceinline__ float4 a(Cell x, int nu) const {
-    return ldmap4(OP == 1 ? a1_ : a2_, nu * S + x.c);
+    return ldmap4(OP == 1 ? a1_ : a2_, nu * S + x.c, ms[(OP == 1 ? kMsA1 : kMsA2) + nu]);
   }
   template <int OP>
   __device__ __forceinline__ float4 b(Cell x, int nu) const {
-    return ldb4(OP == 1 ? b1_ : b2_, nu * S + x.c);
+    return ldb4(OP == 1 ? b1_ : b2_, nu * S + x.c, ms[(OP == 1 ? kMsB1 : kMsB2) + nu]);
   }
   // single cell e of the group (edge paths)
   template <int OP>
   __device__ __forceinline__ float a1c(Cell x, int nu, int e) const {
-    return ldmap(OP == 1 ? a1_ : a2_, nu * S + x.c + e);
+    return ldmap(OP == 1 ? a1_ : a2_, nu * S + x.c + e, ms[(OP == 1 ? kMsA1 : kMsA2) + nu]);
   }
   template <int OP>
   __device__ __forceinline__ float b1c(Cell x, int nu, int e) const {
-    return ldb(OP == 1 ? b1_ : b2_, nu * S + x.c + e);
+    return ldb(OP == 1 ? b1_ : b2_, nu * S + x.c + e, ms[(OP == 1 ? kMsB1 : kMsB2) + nu]);
   }
 };
 

@@ -43,6 +43,49 @@ __device__ __forceinline__ void store_b(float *p, long long i, double b) { p[i] 
 __device__ __forceinline__ void store_b(__nv_bfloat16 *p, long long i, double b) {
   p[i] = __float2bfloat16_rn((float)(1.0 - b));
 }
+// FP16 maps: the value times the map's inverse scale (a power of two, exact),
+// rounded to float then to half; b kept as 1 - b
+__device__ __forceinline__ void store(__half *p, long long i, double v, double inv) {
+  p[i] = __float2half_rn((float)(v * inv));
+}
+__device__ __forceinline__ void store_b(__half *p, long long i, double b, double inv) {
+  p[i] = __float2half_rn((float)((1.0 - b) * inv));
+}
+__device__ __forceinline__ void store(float *p, long long i, double v, double) { store(p, i, v); }
+__device__ __forceinline__ void store(__nv_bfloat16 *p, long long i, double v, double) { store(p, i, v); }
+__device__ __forceinline__ void store_b(float *p, long long i, double b, double) { store_b(p, i, b); }
+__device__ __forceinline__ void store_b(__nv_bfloat16 *p, long long i, double b, double) { store_b(p, i, b); }
+
+// Where the map kernels put a value: stored (scaled for FP16), or, in the
+// scan pass of the FP16 maps, folded into this thread's largest magnitude of
+// the map; flush() combines the threads' maxima (warp reduction, one atomic
+// per warp and map).
+template <typename MT, bool SCAN>
+struct MapSink {
+  const PrepParams &Q;
+  float mx[SCAN ? kMapScales : 1];
+  __device__ __forceinline__ explicit MapSink(const PrepParams &q) : Q(q) {
+    if (SCAN)
+      for (int m = 0; m < kMapScales; ++m) mx[m] = 0.f;
+  }
+  __device__ __forceinline__ void put(int id, void *p, long long i, double v) {
+    if constexpr (SCAN) mx[id] = fmaxf(mx[id], (float)fabs(v));
+    else store(static_cast<MT *>(p), i, v, Q.inv_scale[id]);
+  }
+  __device__ __forceinline__ void put_b(int id, void *p, long long i, double b) {
+    if constexpr (SCAN) mx[id] = fmaxf(mx[id], (float)fabs(1.0 - b));
+    else store_b(static_cast<MT *>(p), i, b, Q.inv_scale[id]);
+  }
+  __device__ __forceinline__ void flush() {
+    if constexpr (SCAN) {
+      const unsigned lane = threadIdx.x & 31;
+      for (int m = 0; m < kMapScales; ++m) {
+        const unsigned v = __reduce_max_sync(0xffffffffu, __float_as_uint(mx[m]));
+        if (lane == 0 && v) atomicMax(Q.f16_max + m, v);
+      }
+    }
+  }
+};
 
 // b = exp(-(d/kappa + alpha) dt), a = d (b - 1) / (kappa (d + kappa alpha))
 __device__ __forceinline__ void relax_ab(double d, double alpha, double kappa, double dt, double &a,
@@ -88,11 +131,16 @@ __device__ double ramp(const PrepParams &Q, double X0, double depth, int nu, boo
   return (0.0 - X0) * g + X0;
 }
 
-template <typename MT>
+template <typename MT, bool SCAN>
 __global__ void cell_maps_kernel(const PrepParams Q) {
   const long long n = (long long)Q.nx * Q.ny * Q.nz;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
+  MapSink<MT, SCAN> out(Q);
+  // every thread runs the same number of iterations: the scan pass's warp
+  // reduction at the end needs the whole warp
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t0 = blockIdx.x * (long long)blockDim.x; t0 < n; t0 += stride) {
+    const long long t = t0 + threadIdx.x;
+    if (t >= n) continue;
     const int i = (int)(t % Q.nx);
     const long long r = t / Q.nx;
     const int j = (int)(r % Q.ny);
@@ -100,26 +148,27 @@ __global__ void cell_maps_kernel(const PrepParams Q) {
     const long long o = (long long)k * Q.plane + (long long)j * Q.pitch + i;
     const double c = Q.c[t], rho = Q.rho[t];
     const double K = rho * c * c;
-    store((MT *)Q.K, o, K);
-    store((MT *)Q.rho_o, o, rho);
+    out.put(kMsK, Q.K, o, K);
+    out.put(kMsRho, Q.rho_o, o, rho);
     if (Q.nl_mode != 0) {
       const double beta = Q.beta[t];
       const double chi = Q.nl_mode != 2 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K;  // 1, 3: Eq. general6
-      store((MT *)Q.chi, o, chi);
+      out.put(kMsChi, Q.chi, o, chi);
     }
     const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
-    store((MT *)Q.ik1, o, 1.0 / k1);
-    store((MT *)Q.ik2, o, 1.0 / k2);
+    out.put(kMsIk1, Q.ik1, o, 1.0 / k1);
+    out.put(kMsIk2, Q.ik2, o, 1.0 / k2);
     for (int nu = 0; nu < Q.N; ++nu) {
       double a, b;
       relax_ab(Q.d1[nu * n + t], Q.al1[nu * n + t], k1, Q.dt, a, b);
-      store((MT *)Q.a1, nu * Q.npts_alloc + o, a);
-      store_b((MT *)Q.b1, nu * Q.npts_alloc + o, b);
+      out.put(kMsA1 + nu, Q.a1, nu * Q.npts_alloc + o, a);
+      out.put_b(kMsB1 + nu, Q.b1, nu * Q.npts_alloc + o, b);
       relax_ab(Q.d2[nu * n + t], Q.al2[nu * n + t], k2, Q.dt, a, b);
-      store((MT *)Q.a2, nu * Q.npts_alloc + o, a);
-      store_b((MT *)Q.b2, nu * Q.npts_alloc + o, b);
+      out.put(kMsA2 + nu, Q.a2, nu * Q.npts_alloc + o, a);
+      out.put_b(kMsB2 + nu, Q.b2, nu * Q.npts_alloc + o, b);
     }
   }
+  out.flush();
 }
 
 // Tissue-index form: per-tissue coefficient table ([field][tab_stride],
@@ -167,7 +216,7 @@ __global__ void index_copy_kernel(const PrepParams Q) {
 }
 
 // One thread per (strip coordinate, other two coordinates) of axis `axis`.
-template <typename MT>
+template <typename MT, bool SCAN>
 __global__ void strip_maps_kernel(const PrepParams Q, int axis) {
   const int L = Q.LT + Q.LB;
   const int ext[3] = {Q.nx, Q.ny, Q.nz};
@@ -176,8 +225,12 @@ __global__ void strip_maps_kernel(const PrepParams Q, int axis) {
   se[axis] = 2 * L;
   const long long total = (long long)se[0] * se[1] * se[2];
   const long long pitch_out = axis == 0 ? 2 * L : Q.pitch;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  MapSink<MT, SCAN> sink(Q);
+  // the same number of iterations in every thread (see cell_maps_kernel)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t0 = blockIdx.x * (long long)blockDim.x; t0 < total; t0 += stride) {
+    const long long t = t0 + threadIdx.x;
+    if (t >= total) continue;
     int s[3];
     s[0] = (int)(t % se[0]);
     const long long r = t / se[0];
@@ -201,15 +254,16 @@ __global__ void strip_maps_kernel(const PrepParams Q, int axis) {
       const double d1 = ramp(Q, Q.d1[nu * nr + ri], dface, nu, true);
       const double al1 = ramp(Q, Q.al1[nu * nr + ri], dface, nu, false);
       relax_ab(d1, al1, k1, Q.dt, a, b);
-      store((MT *)Q.sa1[axis], nu * Q.strip_nu[axis] + out, a);
-      store_b((MT *)Q.sb1[axis], nu * Q.strip_nu[axis] + out, b);
+      sink.put(kMsA1 + nu, Q.sa1[axis], nu * Q.strip_nu[axis] + out, a);
+      sink.put_b(kMsB1 + nu, Q.sb1[axis], nu * Q.strip_nu[axis] + out, b);
       const double d2 = ramp(Q, Q.d2[nu * nr + ri], dcent, nu, true);
       const double al2 = ramp(Q, Q.al2[nu * nr + ri], dcent, nu, false);
       relax_ab(d2, al2, k2, Q.dt, a, b);
-      store((MT *)Q.sa2[axis], nu * Q.strip_nu[axis] + out, a);
-      store_b((MT *)Q.sb2[axis], nu * Q.strip_nu[axis] + out, b);
+      sink.put(kMsA2 + nu, Q.sa2[axis], nu * Q.strip_nu[axis] + out, a);
+      sink.put_b(kMsB2 + nu, Q.sb2[axis], nu * Q.strip_nu[axis] + out, b);
     }
   }
+  sink.flush();
 }
 
 // Largest c / sqrt(kappa1 kappa2) and largest c (FP64, as ordered bit
@@ -262,29 +316,48 @@ cudaError_t launch_medium_scan(const PrepParams &Q, unsigned long long *maxbits,
   return cudaGetLastError();
 }
 
+namespace {
+template <typename MT, bool SCAN>
+cudaError_t launch_strips(const PrepParams &Q, cudaStream_t s) {
+  const long long n = (long long)Q.nx * Q.ny * Q.nz;
+  const int L = Q.LT + Q.LB;
+  if (L > 0 && Q.N > 0) {
+    for (int axis = 0; axis < Q.nd; ++axis) {
+      long long total = 2LL * L * n / (axis == 0 ? Q.nx : axis == 1 ? Q.ny : Q.nz);
+      strip_maps_kernel<MT, SCAN><<<grid_for(total), 256, 0, s>>>(Q, axis);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t launch_prep(const PrepParams &Q, int map_kind, cudaStream_t s) {
   const long long n = (long long)Q.nx * Q.ny * Q.nz;
   if (map_kind == 2 || map_kind == 3) {
     table_kernel<<<(Q.n_tissue + 255) / 256, 256, 0, s>>>(Q);
     index_copy_kernel<<<grid_for(n), 256, 0, s>>>(Q);
   } else if (map_kind == 1) {
-    cell_maps_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, s>>>(Q);
+    cell_maps_kernel<__nv_bfloat16, false><<<grid_for(n), 256, 0, s>>>(Q);
+  } else if (map_kind == 4) {
+    cell_maps_kernel<__half, false><<<grid_for(n), 256, 0, s>>>(Q);
   } else {
-    cell_maps_kernel<float><<<grid_for(n), 256, 0, s>>>(Q);
+    cell_maps_kernel<float, false><<<grid_for(n), 256, 0, s>>>(Q);
   }
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int L = Q.LT + Q.LB;
-  if (L > 0 && Q.N > 0) {
-    for (int axis = 0; axis < Q.nd; ++axis) {
-      long long total = 2LL * L * n / (axis == 0 ? Q.nx : axis == 1 ? Q.ny : Q.nz);
-      if (map_kind == 1) strip_maps_kernel<__nv_bfloat16><<<grid_for(total), 256, 0, s>>>(Q, axis);
-      else strip_maps_kernel<float><<<grid_for(total), 256, 0, s>>>(Q, axis);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    }
-  }
-  return cudaSuccess;
+  if (map_kind == 1) return launch_strips<__nv_bfloat16, false>(Q, s);
+  if (map_kind == 4) return launch_strips<__half, false>(Q, s);
+  return launch_strips<float, false>(Q, s);
+}
+
+cudaError_t launch_prep_scan(const PrepParams &Q, cudaStream_t s) {
+  const long long n = (long long)Q.nx * Q.ny * Q.nz;
+  cell_maps_kernel<__half, true><<<grid_for(n), 256, 0, s>>>(Q);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_strips<__half, true>(Q, s);
 }
 
 }  // namespace fw2

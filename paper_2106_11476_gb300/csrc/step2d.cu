@@ -150,6 +150,7 @@ cudaError_t launch_vel2d(const StepParams &P, int map_kind, cudaStream_t s) {
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY), b(32, kBY);
   if (map_kind == 2) return vel2d_dispatch<IdxMaps>(P, g, b, s);
   if (map_kind == 3) return vel2d_dispatch<IdxMaps16>(P, g, b, s);
+  if (map_kind == 4) return vel2d_dispatch<DenseMaps<__half>>(P, g, b, s);
   return map_kind ? vel2d_dispatch<DenseMaps<__nv_bfloat16>>(P, g, b, s) : vel2d_dispatch<DenseMaps<float>>(P, g, b, s);
 }
 
@@ -162,6 +163,7 @@ cudaError_t launch_prs2d(const StepParams &P, int map_kind, cudaStream_t s) {
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY), b(32, kBY);
   if (map_kind == 2) return prs2d_dispatch<IdxMaps>(P, g, b, s);
   if (map_kind == 3) return prs2d_dispatch<IdxMaps16>(P, g, b, s);
+  if (map_kind == 4) return prs2d_dispatch<DenseMaps<__half>>(P, g, b, s);
   return map_kind ? prs2d_dispatch<DenseMaps<__nv_bfloat16>>(P, g, b, s) : prs2d_dispatch<DenseMaps<float>>(P, g, b, s);
 }
 
@@ -177,6 +179,7 @@ cudaError_t launch_batched2d(bool vel, const StepParams *Ps, const int4 *tiles, 
   if (map_kind == 2) return batched_dispatch<IdxMaps>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
   if (map_kind == 3) return batched_dispatch<IdxMaps16>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
   if (map_kind == 1) return batched_dispatch<DenseMaps<__nv_bfloat16>>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
+  if (map_kind == 4) return batched_dispatch<DenseMaps<__half>>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
   return batched_dispatch<DenseMaps<float>>(vel, Ps, tiles, n_tiles, n_relax, grid, s);
 }
 

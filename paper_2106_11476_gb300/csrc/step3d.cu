@@ -123,10 +123,11 @@ __device__ __forceinline__ void mom_factors3(const StepParams &P, const float (*
   for (int e = 0; e < 4; ++e) {
     const int x = min(i0 + e, P.nx - 1);
     const int xn = rho_coord(min(i0 + e + 1, P.nx), P.nx, P.periodic[0]);
-    const float Kc = ldmap(Km, row + x);
-    el(fx, e) = mom_factor(Kc, ldmap(Km, row + xn), w.v[4 + e], w.v[5 + e]);
-    el(fy, e) = mom_factor(Kc, ldmap(Km, rowy + x), w.v[4 + e], up.v[4 + e]);
-    el(fz, e) = mom_factor(Kc, ldmap(Km, rowz + x), w.v[4 + e], el(pz1, e));
+    const float sK = P.ms[kMsK];
+    const float Kc = ldmap(Km, row + x, sK);
+    el(fx, e) = mom_factor(Kc, ldmap(Km, row + xn, sK), w.v[4 + e], w.v[5 + e]);
+    el(fy, e) = mom_factor(Kc, ldmap(Km, rowy + x, sK), w.v[4 + e], up.v[4 + e]);
+    el(fz, e) = mom_factor(Kc, ldmap(Km, rowz + x, sK), w.v[4 + e], el(pz1, e));
   }
 }
 
@@ -157,13 +158,13 @@ __device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp
   const MT *b1 = static_cast<const MT *>(P.b1);
   const MT *rho = static_cast<const MT *>(P.rho);
   float4 v0 = ld_state4(P.v[0], c), v1 = ld_state4(P.v[1], c), v2 = ld_state4(P.v[2], c);
-  const float4 k1 = ldmap4(ik1, c);
-  const float4 rz = ldmap4(rho, c + P.plane);
+  const float4 k1 = ldmap4(ik1, c, P.ms[kMsIk1]);
+  const float4 rz = ldmap4(rho, c + P.plane, P.ms[kMsRho]);
   float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1], Q0[N > 0 ? N : 1], Q1[N > 0 ? N : 1], Q2[N > 0 ? N : 1];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    A[nu] = ldmap4(a1, nu * S + c);
-    B[nu] = ldb4(b1, nu * S + c);
+    A[nu] = ldmap4(a1, nu * S + c, P.ms[kMsA1 + nu]);
+    B[nu] = ldb4(b1, nu * S + c, P.ms[kMsB1 + nu]);
     Q0[nu] = ld_state4(P.psi1[0], nu * S + c);
     Q1[nu] = ld_state4(P.psi1[1], nu * S + c);
     Q2[nu] = ld_state4(P.psi1[2], nu * S + c);
@@ -266,15 +267,15 @@ __device__ __forceinline__ void prs3d_fast(const StepParams &P, const float (*sv
   const MT *Km = static_cast<const MT *>(P.K);
   const MT *chim = static_cast<const MT *>(P.chi);
   float4 p = ld_state4(P.p, c);
-  const float4 k2 = ldmap4(ik2, c);
-  const float4 K = ldmap4(Km, c);
+  const float4 k2 = ldmap4(ik2, c, P.ms[kMsIk2]);
+  const float4 K = ldmap4(Km, c, P.ms[kMsK]);
   float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (P.nl) ch = ldmap4(chim, c);
+  if (P.nl) ch = ldmap4(chim, c, P.ms[kMsChi]);
   float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1], Q0[N > 0 ? N : 1], Q1[N > 0 ? N : 1], Q2[N > 0 ? N : 1];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    A[nu] = ldmap4(a2, nu * S + c);
-    B[nu] = ldb4(b2, nu * S + c);
+    A[nu] = ldmap4(a2, nu * S + c, P.ms[kMsA2 + nu]);
+    B[nu] = ldb4(b2, nu * S + c, P.ms[kMsB2 + nu]);
     Q0[nu] = ld_state4(P.psi2[0], nu * S + c);
     Q1[nu] = ld_state4(P.psi2[1], nu * S + c);
     Q2[nu] = ld_state4(P.psi2[2], nu * S + c);
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
       const int r = t / RW, cc = t % RW;
       const int gx = rho_coord(x0 + cc, P.nx, P.periodic[0]);
       const int gy = rho_coord(y0 + r, P.ny, P.periodic[1]);
-      sr[r][cc] = ldmap(rho, (long long)k * P.plane + (long long)gy * P.pitch + gx);
+      sr[r][cc] = ldmap(rho, (long long)k * P.plane + (long long)gy * P.pitch + gx, P.ms[kMsRho]);
     }
     __syncthreads();
 #pragma unroll 1
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int x = min(i0 + e, P.nx - 1);
-        el(rz, e) = ldmap(rho, (long long)kz * P.plane + (long long)j * P.pitch + x);
+        el(rz, e) = ldmap(rho, (long long)kz * P.plane + (long long)j * P.pitch + x, P.ms[kMsRho]);
       }
       bx = make_float4(qdiv(P.two_dt, r0.x + r0.y), qdiv(P.two_dt, r0.y + r0.z), qdiv(P.two_dt, r0.z + r0.w),
                        qdiv(P.two_dt, r0.w + r4));
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
       bz = make_float4(qdiv(P.two_dt, r0.x + rz.x), qdiv(P.two_dt, r0.y + rz.y), qdiv(P.two_dt, r0.z + rz.z),
                        qdiv(P.two_dt, r0.w + rz.w));
     }
-    const float4 k1 = ldmap4(ik1, c);
+    const float4 k1 = ldmap4(ik1, c, P.ms[kMsIk1]);
     float4 fx = make_float4(1.f, 1.f, 1.f, 1.f), fy = fx, fz = fx;
     if (P.nl_vel) mom_factors3<MT>(P, sp, ly + 3, tx, i0, j, k, pz1, fx, fy, fz);
     const float4 bb[3] = {bx, by, bz}, ff[3] = {fx, fy, fz};
@@ -520,16 +521,16 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
       }
     }
     if (P.g11h != 0.f) prs3_cross(P, i0, j, k, Dx, Dy, Dz);
-    const float4 k2 = ldmap4(ik2, c);
+    const float4 k2 = ldmap4(ik2, c, P.ms[kMsIk2]);
     const float4 Sx = stretch4<0, 2, N, MT>(P, P.psi2[0], Dx, k2, c, i0, j, k);
     const float4 Sy = stretch4<1, 2, N, MT>(P, P.psi2[1], Dy, k2, c, i0, j, k);
     const float4 Sz = stretch4<2, 2, N, MT>(P, P.psi2[2], Dz, k2, c, i0, j, k);
-    const float4 K = ldmap4(Km, c);
+    const float4 K = ldmap4(Km, c, P.ms[kMsK]);
     float4 p = ld_state4(P.p, c);
     float4 upd = make_float4(P.dt * K.x * (Sx.x + Sy.x + Sz.x), P.dt * K.y * (Sx.y + Sy.y + Sz.y),
                              P.dt * K.z * (Sx.z + Sy.z + Sz.z), P.dt * K.w * (Sx.w + Sy.w + Sz.w));
     if (P.nl) {
-      const float4 ch = ldmap4(chim, c);
+      const float4 ch = ldmap4(chim, c, P.ms[kMsChi]);
       upd.x = qdiv(upd.x, fmaf(ch.x, p.x, 1.f)); upd.y = qdiv(upd.y, fmaf(ch.y, p.y, 1.f));
       upd.z = qdiv(upd.z, fmaf(ch.z, p.z, 1.f)); upd.w = qdiv(upd.w, fmaf(ch.w, p.w, 1.f));
     }
@@ -572,23 +573,25 @@ cudaError_t prs3d_at(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
 }  // namespace
 
 #ifdef FW2_WIDE_RELAX
-cudaError_t launch_vel3d_wide(const StepParams &P, int map_bf16, cudaStream_t s) {
+cudaError_t launch_vel3d_wide(const StepParams &P, int map_kind, cudaStream_t s) {
 #else
-cudaError_t launch_vel3d(const StepParams &P, int map_bf16, cudaStream_t s) {  // map kind 0 or 1
-  if (P.n_relax > kNHi) return launch_vel3d_wide(P, map_bf16, s);
+cudaError_t launch_vel3d(const StepParams &P, int map_kind, cudaStream_t s) {  // map kind 0, 1 or 4
+  if (P.n_relax > kNHi) return launch_vel3d_wide(P, map_kind, s);
 #endif
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kBY3);
-  return map_bf16 ? vel3d_at<kNLo, __nv_bfloat16>(P, g, b, s) : vel3d_at<kNLo, float>(P, g, b, s);
+  if (map_kind == 4) return vel3d_at<kNLo, __half>(P, g, b, s);
+  return map_kind == 1 ? vel3d_at<kNLo, __nv_bfloat16>(P, g, b, s) : vel3d_at<kNLo, float>(P, g, b, s);
 }
 
 #ifdef FW2_WIDE_RELAX
-cudaError_t launch_prs3d_wide(const StepParams &P, int map_bf16, cudaStream_t s) {
+cudaError_t launch_prs3d_wide(const StepParams &P, int map_kind, cudaStream_t s) {
 #else
-cudaError_t launch_prs3d(const StepParams &P, int map_bf16, cudaStream_t s) {
-  if (P.n_relax > kNHi) return launch_prs3d_wide(P, map_bf16, s);
+cudaError_t launch_prs3d(const StepParams &P, int map_kind, cudaStream_t s) {
+  if (P.n_relax > kNHi) return launch_prs3d_wide(P, map_kind, s);
 #endif
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kBY3);
-  return map_bf16 ? prs3d_at<kNLo, __nv_bfloat16>(P, g, b, s) : prs3d_at<kNLo, float>(P, g, b, s);
+  if (map_kind == 4) return prs3d_at<kNLo, __half>(P, g, b, s);
+  return map_kind == 1 ? prs3d_at<kNLo, __nv_bfloat16>(P, g, b, s) : prs3d_at<kNLo, float>(P, g, b, s);
 }
 
 }  // namespace fw2

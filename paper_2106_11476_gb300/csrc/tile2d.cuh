@@ -142,8 +142,8 @@ __device__ __forceinline__ void coef_edge(const StepParams &P, const Maps &M, ty
       if (x < P.nx) {
         const int sc = strip_coord(x, P.nx, L);
         if (sc >= 0) {
-          av = ldmap(sa, row + sc);
-          bv = ldb(sb, row + sc);
+          av = ldmap(sa, row + sc, P.ms[(OP == 1 ? kMsA1 : kMsA2) + nu]);
+          bv = ldb(sb, row + sc, P.ms[(OP == 1 ? kMsB1 : kMsB2) + nu]);
         } else {
           av = M.template a1c<OP>(cell, nu, e);
           bv = M.template b1c<OP>(cell, nu, e);
@@ -159,8 +159,8 @@ __device__ __forceinline__ void coef_edge(const StepParams &P, const Maps &M, ty
       b = M.template b<OP>(cell, nu);
     } else {
       const long long off = (long long)nu * P.strip_nu[1] + (long long)sc * P.pitch + i0;
-      a = ldmap4(sa, off);
-      b = ldb4(sb, off);
+      a = ldmap4(sa, off, P.ms[(OP == 1 ? kMsA1 : kMsA2) + nu]);
+      b = ldb4(sb, off, P.ms[(OP == 1 ? kMsB1 : kMsB2) + nu]);
     }
   }
 }

@@ -22,7 +22,7 @@ STATUS_NAMES = ["FW2_OK", "FW2_EINVAL", "FW2_ENOMEM", "FW2_ECUDA", "FW2_ESTATE",
 MEM_HOST, MEM_DEVICE = 0, 1
 BC = {"zero": 0, "periodic": 1}
 NL = {"off": 0, "pressure": 1, "westervelt": 2, "literal": 3}
-MAP = {"f32": 0, "bf16": 1, "idx": 2, "idx16": 3}
+MAP = {"f32": 0, "bf16": 1, "idx": 2, "idx16": 3, "f16": 4}
 PML_READING = {"A": 0, "C": 2, "K": 3}
 MEM_ALIGN = {"centred": 0, "endpoint": 1}
 SRC_KIND = {"p": 0, "vx": 1, "vy": 2, "vz": 3}

@@ -61,7 +61,6 @@ def test_abi_version(fw2lib):
     ({"map_precision": 5}, fw2.EINVAL),
     ({"ndim": 3, "n": (64, 64, 64), "map_precision": 2}, fw2.EUNSUPPORTED),
     ({"map_precision": 2, "n_relax": 5}, fw2.EUNSUPPORTED),                # index tables: N <= 4
-    ({"map_precision": 4}, fw2.EINVAL),
     ({"ndim": 3, "n": (64, 64, 64), "map_precision": 3}, fw2.EUNSUPPORTED),   # uint16 index: 2D
     ({"map_precision": 3, "n_relax": 5}, fw2.EUNSUPPORTED),
     ({"pml_reading": 1}, fw2.EINVAL),                                      # withdrawn reading

@@ -30,6 +30,8 @@ def _problems():
     # more mechanisms than the pipelined kernels take: batched tile kernels
     probs.append(("f32", small_2d(nx=140, ny=90, N=6, steps=95, pml=(6, 2))))
     probs.append(("bf16", small_2d(nx=100, ny=70, N=8, nl="pressure", steps=95, pml=(6, 2))))
+    # FP16 maps: batched tile kernels
+    probs.append(("f16", small_2d(nx=120, ny=90, N=3, nl="pressure", steps=95, pml=(6, 2))))
     # the uint16 index with more than 256 tissues: batched tile kernels
     probs.append(("idx16", synth.indexed_abdominal_problem(nx=140, ny=100, n_steps=95, n_elements=4,
                                                           pml_lambda=(1.0, 0.5), seed=9, levels=300)))
@@ -151,7 +153,7 @@ def test_batch_budgets_let_contexts_leave_and_equal_each_context_alone(fw2):
     rebuilds its launch tables as contexts leave) and holds bitwise what it
     holds when stepped alone for that many steps."""
     probs = _problems()
-    budgets = [40, 95, 17, 70, 95, 33, 60, 81, 52, 29, 66]
+    budgets = [40, 95, 17, 70, 95, 33, 60, 81, 52, 29, 44, 66]
     alone = []
     for (maps, p), n in zip(probs, budgets):
         s = fw2.Simulation(p, map_precision=maps)

@@ -283,6 +283,27 @@ def test_parity_3d(fw2):
     compare_run(fw2, prob, 80)
 
 
+@pytest.mark.parametrize("case", ["nonlinear-pressure", "literal-N4", "readingA", "ragged-203x77"])
+def test_parity_2d_fp16_maps(fw2, case):
+    """FP16 maps (each map divided by its power-of-two scale) on the tile
+    kernels against the oracle on the same stored maps."""
+    kw = dict(CASES_2D[case])
+    steps = kw.get("steps", 300)
+    compare_run(fw2, small_2d(**kw), steps, maps="f16")
+
+
+@pytest.mark.parametrize("nl", ["westervelt", "literal"])
+def test_parity_3d_fp16_maps(fw2, nl):
+    prob = small_3d(n=(70, 40, 36), N=3, nl=nl, steps=60)
+    if nl == "literal":
+        prob.sources[0].signal = prob.sources[0].signal * 20.0     # the momentum factor acts
+    sim = fw2.Simulation(prob, map_precision="f16")
+    sim.step(1)
+    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    sim.close()
+    compare_run(fw2, prob, 60, maps="f16")
+
+
 def test_parity_2d_eight_mechanisms_bf16(fw2):
     compare_run(fw2, small_2d(N=8, nl="pressure", steps=250), 250, maps="bf16")
 
