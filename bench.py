@@ -428,7 +428,8 @@ def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=T
         vel_b, prs_b = algorithmic_bytes_indexed(prob.shape, prob.nrelax, L, prob.nl_mode != "off", index_bytes=ib)
     else:
         vel_b, prs_b = algorithmic_bytes(prob.shape, prob.nrelax, L, prob.nl_mode != "off",
-                                         map_bytes={"f32": 4, "bf16": 2}[maps], nl_vel=prob.nl_mode == "literal")
+                                         map_bytes={"f32": 4, "bf16": 2, "f16": 2}[maps],
+                                         nl_vel=prob.nl_mode == "literal")
     vel_o, prs_o = split_overhead_bytes(prob.shape, indexed=ib > 0, index_bytes=max(ib, 1))
     stream = torch.cuda.current_stream()
     sim = fw2.Simulation(prob, stream=stream, map_precision=maps, kernel_path=args.kernel_path)
@@ -487,8 +488,11 @@ def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=T
             "vel_ms": round(vel_ms / nv, 5), "prs_ms": round(prs_ms / np_, 5)}
     win = parity_window(prob)
     parity = None
-    if want_parity and rank == 0:
+    if want_parity and rank == 0 and maps != "f16":
         parity = parity_after_run(sim, prob, maps, win, extra=parity_steps)
+    elif want_parity and rank == 0:
+        parity = {"skipped": "the FP16 map scales come from the whole grid, which the oracle's window does not "
+                             "hold; the tests compare whole grids"}
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -497,7 +501,7 @@ def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=T
         e2e = end_to_end(args, prob, maps, steps, world, dist, stream)
     cpu = None
     if want_cpu and rank == 0 and world == 1:
-        cpu = oracle_baseline(prob, args.cpu_steps, win, maps)
+        cpu = oracle_baseline(prob, args.cpu_steps, win, "f32" if maps == "f16" else maps)
     if rank != 0:
         return None
     return {"value": round(value, 4), "ms_per_step": round(elapsed_max / steps, 5),
@@ -1030,7 +1034,7 @@ def main():
                     choices=["abdominal", "abdominal-idx", "abdominal-idx16", "skull", "plain", "batch", "serve"],
                     help="abdominal: 2D 4096^2 nonlinear (default); abdominal-idx: the same in tissue-index "
                          "form; skull: 3D 768^3 with bf16 maps; plain: 2D 512^2 homogeneous line source")
-    ap.add_argument("--maps", default=None, choices=["f32", "bf16", "idx", "idx16"],
+    ap.add_argument("--maps", default=None, choices=["f32", "bf16", "f16", "idx", "idx16"],
                     help="override the map storage of the workload")
     ap.add_argument("--kernel-path", default="auto", choices=["auto", "tile", "pipe", "pipe-staged", "pipe-registers"],
                     help="half-step kernels (bitwise the same results); pipe-staged / pipe-registers fix the layout "
