@@ -207,8 +207,7 @@ fw2_status finalize(fw2_ctx *c) {
     strip_nu[1] = (long long)c->nz * 2 * L * c->pitch;
     if (c->nd == 3) strip_nu[2] = (long long)2 * L * c->ny * c->pitch;
   }
-  const size_t table_bytes =
-      !indexed ? 0 : align256(sizeof(float) * (wide ? kTableFields * (size_t)Q.tab_stride : (size_t)kTableFloatsU8));
+  const size_t table_bytes = indexed ? align256(sizeof(float) * kTableFields * (size_t)Q.tab_stride) : 0;
   const size_t index_bytes = indexed ? align256((wide ? 2 : 1) * (size_t)c->npts_alloc) : 0;
   size_t total = 5 * cell_bytes + 4 * (size_t)c->N * cell_bytes + table_bytes + index_bytes;
   size_t strip_bytes[3];

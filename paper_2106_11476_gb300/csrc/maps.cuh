@@ -10,30 +10,11 @@
 
 namespace fw2 {
 
-// Fields of the index form's per-tissue coefficients, in this order (then
-// a1[nu], b1[nu], a2[nu], b2[nu], kTabSlots slots each).
+// Table layout of the index form: [field][kTissues] floats, fields in this
+// order (then a1[nu], b1[nu], a2[nu], b2[nu] for nu < N).
 enum { kTabK = 0, kTabRho = 1, kTabChi = 2, kTabIk1 = 3, kTabIk2 = 4, kTabRelax = 5 };
 constexpr int kTissues = 256;
 constexpr int kTableFields = kTabRelax + 4 * kTabSlots;
-static_assert(kTabSlots == 4, "a tissue record keeps four mechanisms per 16-byte group");
-
-// uint8 form: one record of kRec floats per tissue, grouped for 16-byte
-// loads (a cell's coefficients of a half step in three): [0..3] a1 of the
-// mechanisms, [4..7] b1, [8..11] {1/kappa1, 1/kappa2, K, chi}, [12..15] a2,
-// [16..19] b2; the records [256][kRec] are followed by rho[256] (the same
-// size as a [field][256] table).  The uint16 form keeps [field][stride]
-// (each field's entries contiguous) in global memory.
-constexpr int kRec = 20;
-enum { kRecA1 = 0, kRecB1 = 4, kRecC = 8, kRecA2 = 12, kRecB2 = 16 };
-constexpr int kRecRho = kTissues * kRec;  // offset of the rho array
-constexpr int kTableFloatsU8 = kTissues * kRec + kTissues;
-// offset in the uint8 table of a field (the order above) of tissue t
-__host__ __device__ constexpr int rec_at(int field, int t) {
-  return field == kTabRho ? kRecRho + t
-       : t * kRec + (field == kTabK ? kRecC + 2 : field == kTabChi ? kRecC + 3 : field == kTabIk1 ? kRecC
-                    : field == kTabIk2 ? kRecC + 1
-                    : (field - kTabRelax < 2 * kTabSlots ? field - kTabRelax : field - kTabRelax + 4));
-}
 
 template <typename T>
 struct DenseMaps {
@@ -80,18 +61,18 @@ struct DenseMaps {
 
 struct IdxMaps {
   using StripT = float;
-  static constexpr int kSmemFloats = kTableFloatsU8;
+  static constexpr int kSmemFloats = kTissues * kTableFields;
   struct Cell {
     uchar4 t;
   };
   const unsigned char *idx;
   const float *tab;  // table in shared memory once bound
   __device__ __forceinline__ explicit IdxMaps(const StepParams &P) : idx(P.tissue), tab(nullptr) {}
-  // copy the per-tissue records (global, [256][kRec]) into shared memory
+  // copy the per-tissue table (global, [field][256]) into shared memory
   __device__ __forceinline__ void stage(const StepParams &P, float *s, int tid) const {
     const float4 *src = reinterpret_cast<const float4 *>(P.table);
     float4 *dst = reinterpret_cast<float4 *>(s);
-    constexpr int n4 = kTableFloatsU8 / 4;
+    constexpr int n4 = kTableFields * kTissues / 4;
     for (int t = tid; t < n4; t += 256) dst[t] = __ldg(src + t);
   }
   __device__ __forceinline__ void bind(const float *s) { tab = s; }
@@ -99,11 +80,13 @@ struct IdxMaps {
     return {__ldg(reinterpret_cast<const uchar4 *>(idx + c))};
   }
   __device__ __forceinline__ float4 look(int field, Cell x) const {
-    return make_float4(tab[rec_at(field, x.t.x)], tab[rec_at(field, x.t.y)], tab[rec_at(field, x.t.z)],
-                       tab[rec_at(field, x.t.w)]);
+    const float *f = tab + field * kTissues;
+    return make_float4(f[x.t.x], f[x.t.y], f[x.t.z], f[x.t.w]);
   }
-  __device__ __forceinline__ float rho_at(long long gidx) const { return tab[kRecRho + __ldg(idx + gidx)]; }
-  __device__ __forceinline__ float K_at(long long gidx) const { return tab[rec_at(kTabK, __ldg(idx + gidx))]; }
+  __device__ __forceinline__ float rho_at(long long gidx) const {
+    return tab[kTabRho * kTissues + __ldg(idx + gidx)];
+  }
+  __device__ __forceinline__ float K_at(long long gidx) const { return tab[kTabK * kTissues + __ldg(idx + gidx)]; }
   __device__ __forceinline__ float4 Kv(Cell x) const { return look(kTabK, x); }
   __device__ __forceinline__ float4 chiv(Cell x) const { return look(kTabChi, x); }
   __device__ __forceinline__ float4 ik1(Cell x) const { return look(kTabIk1, x); }

@@ -171,37 +171,33 @@ __global__ void cell_maps_kernel(const PrepParams Q) {
   out.flush();
 }
 
-// Tissue-index form: per-tissue coefficients (records of the uint8 form, or
-// [field][tab_stride] for the uint16 form; maps.cuh) with the same arithmetic
-// as the per-cell maps, and the index copied into the pitched cell layout.
+// Tissue-index form: per-tissue coefficient table ([field][tab_stride],
+// field order of maps.cuh) with the same arithmetic as the per-cell maps, and
+// the index copied into the pitched cell layout.
 __global__ void table_kernel(const PrepParams Q) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Q.n_tissue) return;
   float *T = Q.table_out;
-  // uint8 form: records [256][kRec]; uint16 form: [field][tab_stride]
-  auto put = [&](int field, double v) {
-    if (Q.tissue_wide) T[(long long)field * Q.tab_stride + t] = (float)v;
-    else T[rec_at(field, t)] = (float)v;
-  };
+  const int S = Q.tab_stride;  // field stride of this table
   const double c = Q.c[t], rho = Q.rho[t];
   const double K = rho * c * c;
-  put(kTabK, K);
-  put(kTabRho, rho);
+  T[kTabK * S + t] = (float)K;
+  T[kTabRho * S + t] = (float)rho;
   if (Q.nl_mode != 0) {
     const double beta = Q.beta[t];
-    put(kTabChi, Q.nl_mode != 2 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K);
+    T[kTabChi * S + t] = (float)(Q.nl_mode != 2 ? (1.0 - 2.0 * beta) / K : -2.0 * beta / K);
   }
   const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
-  put(kTabIk1, 1.0 / k1);
-  put(kTabIk2, 1.0 / k2);
+  T[kTabIk1 * S + t] = (float)(1.0 / k1);
+  T[kTabIk2 * S + t] = (float)(1.0 / k2);
   for (int nu = 0; nu < Q.N; ++nu) {
     double a, b;
     relax_ab(Q.d1[nu * Q.n_tissue + t], Q.al1[nu * Q.n_tissue + t], k1, Q.dt, a, b);
-    put(kTabRelax + nu, a);
-    put(kTabRelax + kTabSlots + nu, b);
+    T[(kTabRelax + nu) * S + t] = (float)a;
+    T[(kTabRelax + kTabSlots + nu) * S + t] = (float)b;
     relax_ab(Q.d2[nu * Q.n_tissue + t], Q.al2[nu * Q.n_tissue + t], k2, Q.dt, a, b);
-    put(kTabRelax + 2 * kTabSlots + nu, a);
-    put(kTabRelax + 3 * kTabSlots + nu, b);
+    T[(kTabRelax + 2 * kTabSlots + nu) * S + t] = (float)a;
+    T[(kTabRelax + 3 * kTabSlots + nu) * S + t] = (float)b;
   }
 }
 

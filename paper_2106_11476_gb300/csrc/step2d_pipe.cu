@@ -316,13 +316,14 @@ __device__ __forceinline__ void stage_table(const StepParams &P, float *tab, int
   if constexpr (IsIdx<Maps>::value) {
     const float4 *src = reinterpret_cast<const float4 *>(P.table);
     float4 *dst = reinterpret_cast<float4 *>(tab);
-    for (int t = tid; t < kTableFloatsU8 / 4; t += kThreads) dst[t] = __ldg(src + t);
+    for (int t = tid; t < kTableFields * kTissues / 4; t += kThreads) dst[t] = __ldg(src + t);
   }
 }
 
-// 16-byte group g of the record of tissue t (index form)
-__device__ __forceinline__ float4 rec4(const float *tab, int t, int g) {
-  return *reinterpret_cast<const float4 *>(tab + t * kRec + 4 * g);
+// coefficient of field f at the two cells of a pair (index form)
+__device__ __forceinline__ float2 look2(const float *tab, int f, uchar2 t) {
+  const float *r = tab + f * kTissues;
+  return make_float2(r[t.x], r[t.y]);
 }
 
 // Densities at the faces of a pair, read where the thread needs them: cells
@@ -346,7 +347,7 @@ __device__ __forceinline__ FaceRho face_rho(const StepParams &P, const float *ta
     r1 = min(r1, my);
   }
   auto at = [&](int r, int cc) -> float {
-    if constexpr (IsIdx<Maps>::value) return tab[kRecRho + si[r * kIW + cc]];
+    if constexpr (IsIdx<Maps>::value) return tab[kTabRho * kTissues + si[r * kIW + cc]];
     else return sr[r * kRWp + cc];
   };
   return FaceRho{at(r0, c0), at(r0, c1), at(r0, c2), at(r1, c0), at(r1, c1)};
@@ -365,7 +366,7 @@ __device__ __forceinline__ void mom_factors2(const StepParams &P, const float *t
   const int mx = P.nx - 1 - x0, my = P.ny - 1 - y0;
   const int r1 = EDGE ? min(ly + 1, my) : ly + 1;
   auto K = [&](int r, int cc) -> float {
-    if constexpr (IsIdx<Maps>::value) return tab[rec_at(kTabK, si[r * kIW + cc])];
+    if constexpr (IsIdx<Maps>::value) return tab[kTabK * kTissues + si[r * kIW + cc]];
     else return sk[r * kRWp + cc];
   };
 #pragma unroll
@@ -482,17 +483,11 @@ __device__ __forceinline__ void vel_compute(const StepParams &P, const float *ta
   float2 k1, A[N > 0 ? N : 1], B[N > 0 ? N : 1];
   if constexpr (S::kIdx) {
     const uchar2 cell = *reinterpret_cast<const uchar2 *>(si + ly * kIW + lx);
-    // three 16-byte loads per cell: a1 of the mechanisms, b1, {1/kappa1, ..}
-    const float4 cx = rec4(tab, cell.x, kRecC / 4), cy = rec4(tab, cell.y, kRecC / 4);
-    k1 = make_float2(cx.x, cy.x);
-    if constexpr (N > 0) {
-      const float4 ax = rec4(tab, cell.x, kRecA1 / 4), ay = rec4(tab, cell.y, kRecA1 / 4);
-      const float4 bx = rec4(tab, cell.x, kRecB1 / 4), by = rec4(tab, cell.y, kRecB1 / 4);
+    k1 = look2(tab, kTabIk1, cell);
 #pragma unroll
-      for (int nu = 0; nu < N; ++nu) {
-        A[nu] = make_float2(el(ax, nu), el(ay, nu));
-        B[nu] = make_float2(el(bx, nu), el(by, nu));
-      }
+    for (int nu = 0; nu < N; ++nu) {
+      A[nu] = look2(tab, kTabRelax + nu, cell);
+      B[nu] = look2(tab, kTabRelax + kTabSlots + nu, cell);
     }
   } else {
     k1 = sld2(own + (2 + 2 * N) * kArr);
@@ -570,19 +565,13 @@ __device__ __forceinline__ void prs_compute(const StepParams &P, const float *ta
   if constexpr (S::kIdx) {
     const uchar2 cell =
         *reinterpret_cast<const uchar2 *>(reinterpret_cast<const unsigned char *>(ss + S::kS) + ly * kTX + lx);
-    // three 16-byte loads per cell: {.., 1/kappa2, K, chi}, a2, b2
-    const float4 cx = rec4(tab, cell.x, kRecC / 4), cy = rec4(tab, cell.y, kRecC / 4);
-    k2 = make_float2(cx.y, cy.y);
-    K = make_float2(cx.z, cy.z);
-    if (P.nl) ch = make_float2(cx.w, cy.w);
-    if constexpr (N > 0) {
-      const float4 ax = rec4(tab, cell.x, kRecA2 / 4), ay = rec4(tab, cell.y, kRecA2 / 4);
-      const float4 bx = rec4(tab, cell.x, kRecB2 / 4), by = rec4(tab, cell.y, kRecB2 / 4);
+    k2 = look2(tab, kTabIk2, cell);
+    K = look2(tab, kTabK, cell);
+    if (P.nl) ch = look2(tab, kTabChi, cell);
 #pragma unroll
-      for (int nu = 0; nu < N; ++nu) {
-        A[nu] = make_float2(el(ax, nu), el(ay, nu));
-        B[nu] = make_float2(el(bx, nu), el(by, nu));
-      }
+    for (int nu = 0; nu < N; ++nu) {
+      A[nu] = look2(tab, kTabRelax + 2 * kTabSlots + nu, cell);
+      B[nu] = look2(tab, kTabRelax + 3 * kTabSlots + nu, cell);
     }
   } else {
     k2 = sld2(own + (1 + 2 * N) * kArr);
