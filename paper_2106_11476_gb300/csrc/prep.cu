@@ -88,11 +88,15 @@ struct MapSink {
 };
 
 // b = exp(-(d/kappa + alpha) dt), a = d (b - 1) / (kappa (d + kappa alpha))
-__device__ __forceinline__ void relax_ab(double d, double alpha, double kappa, double dt, double &a,
+// with d / kappa = d ik (ik = 1 / kappa, computed once per cell) and
+// a = (d / kappa) (b - 1) / (d + kappa alpha): one FP64 division besides the
+// exponential (FP64 throughput bounds the coefficient build)
+__device__ __forceinline__ void relax_ab(double d, double alpha, double kappa, double ik, double dt, double &a,
                                          double &b) {
-  b = exp(-(d / kappa + alpha) * dt);
-  const double den = kappa * (d + kappa * alpha);
-  a = (d == 0.0 || den == 0.0) ? 0.0 : d / den * (b - 1.0);
+  const double dk = d * ik;
+  b = exp(-(dk + alpha) * dt);
+  const double den = d + kappa * alpha;
+  a = (d == 0.0 || den == 0.0) ? 0.0 : dk * (b - 1.0) / den;
 }
 
 // depth (cells, 0..L) into the boundary region of coordinate x on an axis of
@@ -156,14 +160,15 @@ __global__ void cell_maps_kernel(const PrepParams Q) {
       out.put(kMsChi, Q.chi, o, chi);
     }
     const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
-    out.put(kMsIk1, Q.ik1, o, 1.0 / k1);
-    out.put(kMsIk2, Q.ik2, o, 1.0 / k2);
+    const double ik1 = 1.0 / k1, ik2 = 1.0 / k2;
+    out.put(kMsIk1, Q.ik1, o, ik1);
+    out.put(kMsIk2, Q.ik2, o, ik2);
     for (int nu = 0; nu < Q.N; ++nu) {
       double a, b;
-      relax_ab(Q.d1[nu * n + t], Q.al1[nu * n + t], k1, Q.dt, a, b);
+      relax_ab(Q.d1[nu * n + t], Q.al1[nu * n + t], k1, ik1, Q.dt, a, b);
       out.put(kMsA1 + nu, Q.a1, nu * Q.npts_alloc + o, a);
       out.put_b(kMsB1 + nu, Q.b1, nu * Q.npts_alloc + o, b);
-      relax_ab(Q.d2[nu * n + t], Q.al2[nu * n + t], k2, Q.dt, a, b);
+      relax_ab(Q.d2[nu * n + t], Q.al2[nu * n + t], k2, ik2, Q.dt, a, b);
       out.put(kMsA2 + nu, Q.a2, nu * Q.npts_alloc + o, a);
       out.put_b(kMsB2 + nu, Q.b2, nu * Q.npts_alloc + o, b);
     }
@@ -192,10 +197,10 @@ __global__ void table_kernel(const PrepParams Q) {
   T[kTabIk2 * S + t] = (float)(1.0 / k2);
   for (int nu = 0; nu < Q.N; ++nu) {
     double a, b;
-    relax_ab(Q.d1[nu * Q.n_tissue + t], Q.al1[nu * Q.n_tissue + t], k1, Q.dt, a, b);
+    relax_ab(Q.d1[nu * Q.n_tissue + t], Q.al1[nu * Q.n_tissue + t], k1, 1.0 / k1, Q.dt, a, b);
     T[(kTabRelax + nu) * S + t] = (float)a;
     T[(kTabRelax + kTabSlots + nu) * S + t] = (float)b;
-    relax_ab(Q.d2[nu * Q.n_tissue + t], Q.al2[nu * Q.n_tissue + t], k2, Q.dt, a, b);
+    relax_ab(Q.d2[nu * Q.n_tissue + t], Q.al2[nu * Q.n_tissue + t], k2, 1.0 / k2, Q.dt, a, b);
     T[(kTabRelax + 2 * kTabSlots + nu) * S + t] = (float)a;
     T[(kTabRelax + 3 * kTabSlots + nu) * S + t] = (float)b;
   }
@@ -249,16 +254,17 @@ __global__ void strip_maps_kernel(const PrepParams Q, int axis) {
     const double dcent = depth_of((double)(Q.goff[axis] + cell[axis]), Q.gext[axis], L);
     const long long ri = src_of(Q, src), nr = n_src(Q);
     const double k1 = Q.k1[ri], k2 = Q.k2[ri];
+    const double ik1 = 1.0 / k1, ik2 = 1.0 / k2;
     for (int nu = 0; nu < Q.N; ++nu) {
       double a, b;
       const double d1 = ramp(Q, Q.d1[nu * nr + ri], dface, nu, true);
       const double al1 = ramp(Q, Q.al1[nu * nr + ri], dface, nu, false);
-      relax_ab(d1, al1, k1, Q.dt, a, b);
+      relax_ab(d1, al1, k1, ik1, Q.dt, a, b);
       sink.put(kMsA1 + nu, Q.sa1[axis], nu * Q.strip_nu[axis] + out, a);
       sink.put_b(kMsB1 + nu, Q.sb1[axis], nu * Q.strip_nu[axis] + out, b);
       const double d2 = ramp(Q, Q.d2[nu * nr + ri], dcent, nu, true);
       const double al2 = ramp(Q, Q.al2[nu * nr + ri], dcent, nu, false);
-      relax_ab(d2, al2, k2, Q.dt, a, b);
+      relax_ab(d2, al2, k2, ik2, Q.dt, a, b);
       sink.put(kMsA2 + nu, Q.sa2[axis], nu * Q.strip_nu[axis] + out, a);
       sink.put_b(kMsB2 + nu, Q.sb2[axis], nu * Q.strip_nu[axis] + out, b);
     }
