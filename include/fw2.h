@@ -252,7 +252,9 @@ fw2_status fw2_destroy(fw2_ctx *ctx);
  * and, with a C-PML, pml_cp > 0 (the whole grid's values: a subdomain cannot
  * derive them from its own medium).  Call before the first step.  EINVAL
  * when the box leaves the grid, splits a periodic axis, or dt / pml_cp are
- * missing. */
+ * missing.  FP16 maps take their scales from the context's own cells, so
+ * FP16 subdomains agree with the whole grid to the maps' rounding, not
+ * bitwise (the other storages agree bitwise). */
 fw2_status fw2_set_subdomain(fw2_ctx *ctx, const int64_t *global_n, const int64_t *offset);
 /* One part of a time step, for an exchange between the half steps: part 0
  * is the velocity half step with the velocity sources, part 1 the pressure
