@@ -476,6 +476,12 @@ __device__ __forceinline__ void prefetch_strips(const StepParams &P, const Regio
   }
 }
 
+// mom_factor (coef.cuh) from the reciprocals 1 / K of the two cells, taken
+// once per cell: the same value for the same operands
+__device__ __forceinline__ float mom_factor_ik(float ika, float ikb, float pa, float pb) {
+  return fmaf(0.5f * (ika + ikb), 0.5f * (pa + pb), 1.f);
+}
+
 // Values at the faces of a pair read from a staged bf16 box [2][9][136]
 // (planes k, k + 1: the density, or K): plane k row ly at lx .. lx+2, row
 // ly+1 at lx, lx+1; plane k+1 row ly at lx, lx+1.  Cells beyond the last one
@@ -627,15 +633,17 @@ __device__ __forceinline__ void vel3_compute(const StepParams &P, const Region3 
     // momentum factors of the literal system (Eq. general5) at the x, y, z
     // faces: p from the staged planes (zero beyond the grid), K of the cell
     // and of its +1 neighbours from the staged K box, clamped to the last cell
-    const Face3 g = face3<true>(P, reinterpret_cast<const bf16 *>(st + S::oKm), x0, y0, k, lx, ly);
-    const float Kr[3] = {g.r0, g.r1, g.r2}, Ku[2] = {g.u0, g.u1}, Kz[2] = {g.z0, g.z1};
+    const Face3 g = face3<EDGE>(P, reinterpret_cast<const bf16 *>(st + S::oKm), x0, y0, k, lx, ly);
+    // 1 / K of each of the seven cells once (mom_factor takes them the same way)
+    const float Kr[3] = {qdiv(1.f, g.r0), qdiv(1.f, g.r1), qdiv(1.f, g.r2)};
+    const float Ku[2] = {qdiv(1.f, g.u0), qdiv(1.f, g.u1)}, Kz[2] = {qdiv(1.f, g.z0), qdiv(1.f, g.z1)};
     const float *pr = sp + sy * kCW + lx + 4, *pu = sp + (sy + 1) * kCW + lx + 4;
     const float *pz = ring + slot_after(s0, 4) * kPl + sy * kCW + lx + 4;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      const float fx = mom_factor(Kr[e], Kr[e + 1], pr[e], pr[e + 1]);
-      const float fy = mom_factor(Kr[e], Ku[e], pr[e], pu[e]);
-      const float fz = mom_factor(Kr[e], Kz[e], pr[e], pz[e]);
+      const float fx = mom_factor_ik(Kr[e], Kr[e + 1], pr[e], pr[e + 1]);
+      const float fy = mom_factor_ik(Kr[e], Ku[e], pr[e], pu[e]);
+      const float fz = mom_factor_ik(Kr[e], Kz[e], pr[e], pz[e]);
       el2(v0, e) = vel_upd(el2(v0, e), qdiv(P.two_dt, rr[e] + rr[e + 1]), el2(Sd[0], e), fx);
       el2(v1, e) = vel_upd(el2(v1, e), qdiv(P.two_dt, rr[e] + ru[e]), el2(Sd[1], e), fy);
       el2(v2, e) = vel_upd(el2(v2, e), qdiv(P.two_dt, rr[e] + rz[e]), el2(Sd[2], e), fz);
