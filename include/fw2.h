@@ -69,10 +69,11 @@ enum { FW2_NL_OFF = 0, FW2_NL_PRESSURE = 1, FW2_NL_WESTERVELT = 2, FW2_NL_LITERA
  * (every map, and the C-PML strips of a mechanism with its interior map,
  * divided by a power of two chosen from the map's largest magnitude so that
  * it lies in [2^14, 2^15); b kept as 1 - b; tile kernels), or a tissue index
- * per cell into per-tissue float tables (2D only, N <= 4; set the medium with
- * fw2_set_medium_indexed): uint8 for up to 256 tissues (the tables in shared
- * memory, pipelined or tile kernels) or uint16 for up to 65536 (the tables
- * read through L2, tile kernels) */
+ * per cell into per-tissue float tables (N <= 4; set the medium with
+ * fw2_set_medium_indexed): uint8 for up to 256 tissues or uint16 for up to
+ * 65536.  In 2D the uint8 tables sit in shared memory (pipelined or tile
+ * kernels); the uint16 tables, and every table in 3D, are read through L2 by
+ * the tile kernels. */
 enum { FW2_MAP_F32 = 0, FW2_MAP_BF16 = 1, FW2_MAP_IDX_U8 = 2, FW2_MAP_IDX_U16 = 3, FW2_MAP_F16 = 4 };
 /* C-PML geometry (Sec. 3.3, Table 1).  In both readings the nu >= 2
  * parameters fall to zero over the inner L_T cells with the cosine transition
@@ -143,7 +144,7 @@ typedef struct {
   int32_t pml_transition;/* L_T, cells per side (Sec. 3.3) */
   int32_t pml_bound;     /* L_B, cells per side */
   int32_t pml_reading;   /* FW2_PML_C (default), FW2_PML_A or FW2_PML_NO_TRANSITION */
-  int32_t map_precision; /* FW2_MAP_F32, FW2_MAP_BF16, FW2_MAP_F16, FW2_MAP_IDX_U8 or FW2_MAP_IDX_U16 (2D) */
+  int32_t map_precision; /* FW2_MAP_F32, FW2_MAP_BF16, FW2_MAP_F16, FW2_MAP_IDX_U8 or FW2_MAP_IDX_U16 */
   double pml_rc;         /* reflection target R_c of Table 1 (default 1e-3) */
   double pml_npow;       /* polynomial order of the d ramp (default 2) */
   double pml_cp;         /* c_p of Table 1 [m/s]; <= 0: largest c of the medium */

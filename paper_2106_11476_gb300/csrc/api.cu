@@ -675,8 +675,6 @@ fw2_status fw2_create(const fw2_config *cfg_in, fw2_ctx **out) {
   if (cfg.map_precision < FW2_MAP_F32 || cfg.map_precision > FW2_MAP_F16)
     return fail(nullptr, FW2_EINVAL, "bad map_precision");
   const bool idx_form = cfg.map_precision == FW2_MAP_IDX_U8 || cfg.map_precision == FW2_MAP_IDX_U16;
-  if (idx_form && cfg.ndim != 2)
-    return fail(nullptr, FW2_EUNSUPPORTED, "tissue-index maps are implemented for 2D grids");
   if (idx_form && cfg.n_relax > kTabSlots)
     return fail(nullptr, FW2_EUNSUPPORTED, "tissue-index tables hold up to %d mechanisms", kTabSlots);
   if (cfg.nl_mode < FW2_NL_OFF || cfg.nl_mode > FW2_NL_LITERAL) return fail(nullptr, FW2_EINVAL, "bad nl_mode");

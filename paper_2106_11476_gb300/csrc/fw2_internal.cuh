@@ -210,7 +210,8 @@ bool pipe3d_staged_layout(bool vel, const StepParams &P);
 cudaError_t launch_pipe3d_batched(bool vel, bool cross, bool ps, int n_relax, const StepParams *Ps,
                                   const void *Rs, const PipeMaps *Ts, const int2 *items, const int *runs,
                                   int grid, cudaStream_t s);
-// 3D tile kernels: map_kind 0 float, 1 bf16, 4 FP16
+// 3D tile kernels: map_kind 0 float, 1 bf16, 4 FP16, 2 and 3 the uint8 and
+// uint16 tissue index (tables read through L2)
 cudaError_t launch_vel3d(const StepParams &P, int map_kind, cudaStream_t s);
 cudaError_t launch_prs3d(const StepParams &P, int map_kind, cudaStream_t s);
 cudaError_t launch_vel3d_wide(const StepParams &P, int map_kind, cudaStream_t s);

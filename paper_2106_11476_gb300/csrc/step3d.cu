@@ -6,11 +6,158 @@
 // planes along z; the xy stencil
 // operand of the current plane is staged in shared memory with its halo, the
 // z taps of each cell's own column are read through L2.
+#include <type_traits>
+
 #include "coef.cuh"
+#include "maps.cuh"
 
 namespace fw2 {
 
 namespace {
+
+// Map access of the 3D tile kernels; a map is named by its slot of
+// StepParams::ms (kMsK, kMsRho, kMsChi, kMsIk1, kMsIk2, kMsA1 + nu, kMsB1 +
+// nu, kMsA2 + nu, kMsB2 + nu), and v1 / v4 give its value at one cell / at
+// the four cells c .. c + 3 (b as b).
+// Dense3<MT>: one value per cell (float, bf16 or FP16 with the map's scale;
+// bf16 and FP16 keep b as 1 - b).
+template <typename MT>
+struct Dense3 {
+  using StripT = MT;
+  static __device__ __forceinline__ const MT *base(const StepParams &P, int id, long long &off) {
+    const long long S = P.npts_alloc;
+    if (id >= kMsB2) { off = (id - kMsB2) * S; return static_cast<const MT *>(P.b2); }
+    if (id >= kMsA2) { off = (id - kMsA2) * S; return static_cast<const MT *>(P.a2); }
+    if (id >= kMsB1) { off = (id - kMsB1) * S; return static_cast<const MT *>(P.b1); }
+    if (id >= kMsA1) { off = (id - kMsA1) * S; return static_cast<const MT *>(P.a1); }
+    off = 0;
+    return static_cast<const MT *>(id == kMsK ? P.K : id == kMsRho ? P.rho : id == kMsChi ? P.chi
+                                   : id == kMsIk1 ? P.ik1 : P.ik2);
+  }
+  static __device__ __forceinline__ bool is_b(int id) {
+    return (id >= kMsB1 && id < kMsA2) || id >= kMsB2;
+  }
+  static __device__ __forceinline__ float v1(const StepParams &P, int id, long long c) {
+    long long off;
+    const MT *p = base(P, id, off);
+    return is_b(id) ? ldb(p, off + c, P.ms[id]) : ldmap(p, off + c, P.ms[id]);
+  }
+  static __device__ __forceinline__ float4 v4(const StepParams &P, int id, long long c) {
+    long long off;
+    const MT *p = base(P, id, off);
+    return is_b(id) ? ldb4(p, off + c, P.ms[id]) : ldmap4(p, off + c, P.ms[id]);
+  }
+};
+// Idx3<IT>: a tissue index per cell (uint8 or uint16) into the per-tissue
+// float tables ([field][tab_stride] in global memory, read through L2 and the
+// read-only cache; maps.cuh field order); the C-PML strips stay per cell.
+template <typename IT>
+struct Idx3 {
+  using StripT = float;
+  static __device__ __forceinline__ int field(int id) {
+    return id == kMsK ? kTabK : id == kMsRho ? kTabRho : id == kMsChi ? kTabChi : id == kMsIk1 ? kTabIk1
+         : id == kMsIk2 ? kTabIk2 : id < kMsB1 ? kTabRelax + (id - kMsA1)
+         : id < kMsA2 ? kTabRelax + kTabSlots + (id - kMsB1) : id < kMsB2 ? kTabRelax + 2 * kTabSlots + (id - kMsA2)
+                      : kTabRelax + 3 * kTabSlots + (id - kMsB2);
+  }
+  static __device__ __forceinline__ float v1(const StepParams &P, int id, long long c) {
+    const int t = __ldg(reinterpret_cast<const IT *>(P.tissue) + c);
+    return __ldg(P.table + (long long)field(id) * P.tab_stride + t);
+  }
+  static __device__ __forceinline__ float4 v4(const StepParams &P, int id, long long c) {
+    const float *f = P.table + (long long)field(id) * P.tab_stride;
+    if constexpr (sizeof(IT) == 1) {
+      const uchar4 t = __ldg(reinterpret_cast<const uchar4 *>(P.tissue + c));
+      return make_float4(__ldg(f + t.x), __ldg(f + t.y), __ldg(f + t.z), __ldg(f + t.w));
+    } else {
+      const ushort4 t = __ldg(reinterpret_cast<const ushort4 *>(reinterpret_cast<const IT *>(P.tissue) + c));
+      return make_float4(__ldg(f + t.x), __ldg(f + t.y), __ldg(f + t.z), __ldg(f + t.w));
+    }
+  }
+};
+template <typename M>
+constexpr bool kIndexed3 = std::is_same<M, Idx3<unsigned char>>::value || std::is_same<M, Idx3<unsigned short>>::value;
+
+// a, b of mechanism nu for the derivative along axis Q at the four cells
+// i0..i0+3 of row (j, k): from the boundary strip of axis Q when the cell
+// lies inside the C-PML region of that axis (Sec. 3.3: each axis' parameters
+// depend on the distance along that axis only), else from the interior maps.
+// OP = 1: nabla_1 (faces), OP = 2: nabla_2 (centres).
+template <int Q, int OP, typename M>
+__device__ __forceinline__ void coef4(const StepParams &P, int nu, long long c, int i0, int j, int k, float4 &a,
+                                      float4 &b) {
+  using ST = typename M::StripT;
+  const int ia = (OP == 1 ? kMsA1 : kMsA2) + nu, ib = (OP == 1 ? kMsB1 : kMsB2) + nu;
+  const ST *sa = static_cast<const ST *>(OP == 1 ? P.sa1[Q] : P.sa2[Q]);
+  const ST *sb = static_cast<const ST *>(OP == 1 ? P.sb1[Q] : P.sb2[Q]);
+  const float s_a = P.ms[ia], s_b = P.ms[ib];
+  const int L = P.L[Q];
+  if (Q == 0) {
+    const bool any = L > 0 && (i0 < L || i0 + 3 >= P.nx - L);
+    if (!any) {
+      a = M::v4(P, ia, c);
+      b = M::v4(P, ib, c);
+      return;
+    }
+    const long long row = (long long)nu * P.strip_nu[0] + ((long long)k * P.ny + j) * (2 * L);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int x = i0 + e;
+      float av = 0.f, bv = 0.f;
+      if (x < P.nx) {
+        const int sc = strip_coord(x, P.nx, L);
+        if (sc >= 0) {
+          av = ldmap(sa, row + sc, s_a);
+          bv = ldb(sb, row + sc, s_b);
+        } else {
+          av = M::v1(P, ia, c + e);
+          bv = M::v1(P, ib, c + e);
+        }
+      }
+      el(a, e) = av;
+      el(b, e) = bv;
+    }
+  } else {
+    const int sc = Q == 1 ? strip_coord(j, P.ny, L) : strip_coord(k, P.nz, L);
+    if (sc < 0) {
+      a = M::v4(P, ia, c);
+      b = M::v4(P, ib, c);
+    } else {
+      const long long off =
+          Q == 1 ? (long long)nu * P.strip_nu[1] + ((long long)k * (2 * L) + sc) * P.pitch + i0
+                 : (long long)nu * P.strip_nu[2] + ((long long)sc * P.ny + j) * P.pitch + i0;
+      a = ldmap4(sa, off, s_a);
+      b = ldb4(sb, off, s_b);
+    }
+  }
+}
+
+// Stretched derivative of Eq. (relaxation4) for four cells:
+//   S = D / kappa + sum_nu (w_new psi_new + w_old psi_old),
+//   psi_new = b psi_old + a D    (Eq. relaxation_psi), psi written back.
+template <int Q, int OP, int N, typename M>
+__device__ __forceinline__ float4 stretch4(const StepParams &P, float *psi, float4 D, float4 ik, long long c, int i0,
+                                           int j, int k) {
+  float4 S = make_float4(D.x * ik.x, D.y * ik.y, D.z * ik.z, D.w * ik.w);
+#pragma unroll
+  for (int nu = 0; nu < N; ++nu) {
+    float4 a, b;
+    coef4<Q, OP, M>(P, nu, c, i0, j, k, a, b);
+    const long long o = (long long)nu * P.npts_alloc + c;
+    const float4 ps = ld_state4(psi, o);
+    float4 pn;
+    pn.x = fmaf(b.x, ps.x, a.x * D.x);
+    pn.y = fmaf(b.y, ps.y, a.y * D.y);
+    pn.z = fmaf(b.z, ps.z, a.z * D.z);
+    pn.w = fmaf(b.w, ps.w, a.w * D.w);
+    S.x += fmaf(P.w_new, pn.x, P.w_old * ps.x);
+    S.y += fmaf(P.w_new, pn.y, P.w_old * ps.y);
+    S.z += fmaf(P.w_new, pn.z, P.w_old * ps.z);
+    S.w += fmaf(P.w_new, pn.w, P.w_old * ps.w);
+    st_state4(psi, o, pn);
+  }
+  return S;
+}
 
 constexpr int kTY3 = 16;  // tile rows (two per thread row)
 constexpr int kBY3 = 8;   // thread rows
@@ -110,10 +257,9 @@ __device__ __forceinline__ void prs3_cross(const StepParams &P, int i0, int j, i
 // and z faces of the four cells i0..i0+3 of row (j, k): p from the staged
 // plane (row sy of sp) and the z column (pz1 = p at k+1), K from the map with
 // the density's neighbour rule; cells past nx are clamped (masked later).
-template <typename MT>
+template <typename M>
 __device__ __forceinline__ void mom_factors3(const StepParams &P, const float (*sp)[kTX + 8], int sy, int tx, int i0,
                                              int j, int k, const float4 &pz1, float4 &fx, float4 &fy, float4 &fz) {
-  const MT *Km = static_cast<const MT *>(P.K);
   const Win12 w = win12(sp[sy], tx), up = win12(sp[sy + 1], tx);
   const int jn = rho_coord(j + 1, P.ny, P.periodic[1]), kn = rho_coord(k + 1, P.nz, P.periodic[2]);
   const long long row = (long long)k * P.plane + (long long)j * P.pitch;
@@ -123,17 +269,16 @@ __device__ __forceinline__ void mom_factors3(const StepParams &P, const float (*
   for (int e = 0; e < 4; ++e) {
     const int x = min(i0 + e, P.nx - 1);
     const int xn = rho_coord(min(i0 + e + 1, P.nx), P.nx, P.periodic[0]);
-    const float sK = P.ms[kMsK];
-    const float Kc = ldmap(Km, row + x, sK);
-    el(fx, e) = mom_factor(Kc, ldmap(Km, row + xn, sK), w.v[4 + e], w.v[5 + e]);
-    el(fy, e) = mom_factor(Kc, ldmap(Km, rowy + x, sK), w.v[4 + e], up.v[4 + e]);
-    el(fz, e) = mom_factor(Kc, ldmap(Km, rowz + x, sK), w.v[4 + e], el(pz1, e));
+    const float Kc = M::v1(P, kMsK, row + x);
+    el(fx, e) = mom_factor(Kc, M::v1(P, kMsK, row + xn), w.v[4 + e], w.v[5 + e]);
+    el(fy, e) = mom_factor(Kc, M::v1(P, kMsK, rowy + x), w.v[4 + e], up.v[4 + e]);
+    el(fz, e) = mom_factor(Kc, M::v1(P, kMsK, rowz + x), w.v[4 + e], el(pz1, e));
   }
 }
 
 // Interior plane of the velocity half step: z taps first (L2), then every
 // streaming load of the plane row before any store.
-template <int N, typename MT>
+template <int N, typename M>
 __device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp)[kTX + 8],
                                            const float (*sr)[kTX + 4], int i0, int j, int k, int tx, int ty) {
   const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
@@ -153,18 +298,14 @@ __device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp
       el(Dz, e) = d;
     }
   }
-  const MT *ik1 = static_cast<const MT *>(P.ik1);
-  const MT *a1 = static_cast<const MT *>(P.a1);
-  const MT *b1 = static_cast<const MT *>(P.b1);
-  const MT *rho = static_cast<const MT *>(P.rho);
   float4 v0 = ld_state4(P.v[0], c), v1 = ld_state4(P.v[1], c), v2 = ld_state4(P.v[2], c);
-  const float4 k1 = ldmap4(ik1, c, P.ms[kMsIk1]);
-  const float4 rz = ldmap4(rho, c + P.plane, P.ms[kMsRho]);
+  const float4 k1 = M::v4(P, kMsIk1, c);
+  const float4 rz = M::v4(P, kMsRho, c + P.plane);
   float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1], Q0[N > 0 ? N : 1], Q1[N > 0 ? N : 1], Q2[N > 0 ? N : 1];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    A[nu] = ldmap4(a1, nu * S + c, P.ms[kMsA1 + nu]);
-    B[nu] = ldb4(b1, nu * S + c, P.ms[kMsB1 + nu]);
+    A[nu] = M::v4(P, kMsA1 + nu, c);
+    B[nu] = M::v4(P, kMsB1 + nu, c);
     Q0[nu] = ld_state4(P.psi1[0], nu * S + c);
     Q1[nu] = ld_state4(P.psi1[1], nu * S + c);
     Q2[nu] = ld_state4(P.psi1[2], nu * S + c);
@@ -221,7 +362,7 @@ __device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp
   const float rr[5] = {r0.x, r0.y, r0.z, r0.w, r4};
   if (P.nl_vel) {
     float4 fx, fy, fz;
-    mom_factors3<MT>(P, sp, sy, tx, i0, j, k, pz1, fx, fy, fz);
+    mom_factors3<M>(P, sp, sy, tx, i0, j, k, pz1, fx, fy, fz);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       el(v0, e) = vel_upd(el(v0, e), qdiv(P.two_dt, rr[e] + rr[e + 1]), el(S0, e), el(fx, e));
@@ -242,7 +383,7 @@ __device__ __forceinline__ void vel3d_fast(const StepParams &P, const float (*sp
 }
 
 // Interior plane of the pressure half step (same structure).
-template <int N, typename MT>
+template <int N, typename M>
 __device__ __forceinline__ void prs3d_fast(const StepParams &P, const float (*svx)[kTX + 8],
                                            const float (*svy)[kTX + 8], int i0, int j, int k, int tx, int ty) {
   const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
@@ -261,21 +402,16 @@ __device__ __forceinline__ void prs3d_fast(const StepParams &P, const float (*sv
       el(Dz, e) = d;
     }
   }
-  const MT *ik2 = static_cast<const MT *>(P.ik2);
-  const MT *a2 = static_cast<const MT *>(P.a2);
-  const MT *b2 = static_cast<const MT *>(P.b2);
-  const MT *Km = static_cast<const MT *>(P.K);
-  const MT *chim = static_cast<const MT *>(P.chi);
   float4 p = ld_state4(P.p, c);
-  const float4 k2 = ldmap4(ik2, c, P.ms[kMsIk2]);
-  const float4 K = ldmap4(Km, c, P.ms[kMsK]);
+  const float4 k2 = M::v4(P, kMsIk2, c);
+  const float4 K = M::v4(P, kMsK, c);
   float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (P.nl) ch = ldmap4(chim, c, P.ms[kMsChi]);
+  if (P.nl) ch = M::v4(P, kMsChi, c);
   float4 A[N > 0 ? N : 1], B[N > 0 ? N : 1], Q0[N > 0 ? N : 1], Q1[N > 0 ? N : 1], Q2[N > 0 ? N : 1];
 #pragma unroll
   for (int nu = 0; nu < N; ++nu) {
-    A[nu] = ldmap4(a2, nu * S + c, P.ms[kMsA2 + nu]);
-    B[nu] = ldb4(b2, nu * S + c, P.ms[kMsB2 + nu]);
+    A[nu] = M::v4(P, kMsA2 + nu, c);
+    B[nu] = M::v4(P, kMsB2 + nu, c);
     Q0[nu] = ld_state4(P.psi2[0], nu * S + c);
     Q1[nu] = ld_state4(P.psi2[1], nu * S + c);
     Q2[nu] = ld_state4(P.psi2[2], nu * S + c);
@@ -333,7 +469,7 @@ __device__ __forceinline__ void prs3d_fast(const StepParams &P, const float (*sv
   st_state4(P.p, c, p);
 }
 
-template <int N, typename MT>
+template <int N, typename M>
 __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
   constexpr int PW = kTX + 8, PH = kTY3 + 7;  // p plane tile: x0-4.., y0-3..
   constexpr int RW = kTX + 4, RH = kTY3 + 1;  // rho plane tile: x0.., y0..
@@ -341,8 +477,6 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
   __shared__ __align__(16) float sr[RH][RW];
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY3, z0 = blockIdx.z * kTZ;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const MT *rho = static_cast<const MT *>(P.rho);
-  const MT *ik1 = static_cast<const MT *>(P.ik1);
   const int i0 = x0 + 4 * tx;
   const bool fast_xy = interior_xy(P, x0, y0) && P.g11h == 0.f;  // cross taps: general path
   const int zend = min(z0 + kTZ, P.nz);
@@ -357,7 +491,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
       const int r = t / RW, cc = t % RW;
       const int gx = rho_coord(x0 + cc, P.nx, P.periodic[0]);
       const int gy = rho_coord(y0 + r, P.ny, P.periodic[1]);
-      sr[r][cc] = ldmap(rho, (long long)k * P.plane + (long long)gy * P.pitch + gx, P.ms[kMsRho]);
+      sr[r][cc] = M::v1(P, kMsRho, (long long)k * P.plane + (long long)gy * P.pitch + gx);
     }
     __syncthreads();
 #pragma unroll 1
@@ -365,7 +499,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
     const int ly = ty + rr * kBY3, j = y0 + ly;
     if (i0 >= P.nx || j >= P.ny) continue;
     if (fast_xy && interior_z(P, k)) {
-      vel3d_fast<N, MT>(P, sp, sr, i0, j, k, tx, ly);
+      vel3d_fast<N, M>(P, sp, sr, i0, j, k, tx, ly);
       continue;
     }
     const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
@@ -418,7 +552,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int x = min(i0 + e, P.nx - 1);
-        el(rz, e) = ldmap(rho, (long long)kz * P.plane + (long long)j * P.pitch + x, P.ms[kMsRho]);
+        el(rz, e) = M::v1(P, kMsRho, (long long)kz * P.plane + (long long)j * P.pitch + x);
       }
       bx = make_float4(qdiv(P.two_dt, r0.x + r0.y), qdiv(P.two_dt, r0.y + r0.z), qdiv(P.two_dt, r0.z + r0.w),
                        qdiv(P.two_dt, r0.w + r4));
@@ -427,15 +561,15 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
       bz = make_float4(qdiv(P.two_dt, r0.x + rz.x), qdiv(P.two_dt, r0.y + rz.y), qdiv(P.two_dt, r0.z + rz.z),
                        qdiv(P.two_dt, r0.w + rz.w));
     }
-    const float4 k1 = ldmap4(ik1, c, P.ms[kMsIk1]);
+    const float4 k1 = M::v4(P, kMsIk1, c);
     float4 fx = make_float4(1.f, 1.f, 1.f, 1.f), fy = fx, fz = fx;
-    if (P.nl_vel) mom_factors3<MT>(P, sp, ly + 3, tx, i0, j, k, pz1, fx, fy, fz);
+    if (P.nl_vel) mom_factors3<M>(P, sp, ly + 3, tx, i0, j, k, pz1, fx, fy, fz);
     const float4 bb[3] = {bx, by, bz}, ff[3] = {fx, fy, fz};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const float4 S = q == 0 ? stretch4<0, 1, N, MT>(P, P.psi1[0], Dx, k1, c, i0, j, k)
-                     : q == 1 ? stretch4<1, 1, N, MT>(P, P.psi1[1], Dy, k1, c, i0, j, k)
-                              : stretch4<2, 1, N, MT>(P, P.psi1[2], Dz, k1, c, i0, j, k);
+      const float4 S = q == 0 ? stretch4<0, 1, N, M>(P, P.psi1[0], Dx, k1, c, i0, j, k)
+                     : q == 1 ? stretch4<1, 1, N, M>(P, P.psi1[1], Dy, k1, c, i0, j, k)
+                              : stretch4<2, 1, N, M>(P, P.psi1[2], Dz, k1, c, i0, j, k);
       float4 v = ld_state4(P.v[q], c);
       if (P.nl_vel) {
 #pragma unroll
@@ -450,7 +584,7 @@ __global__ void __launch_bounds__(256, 2) vel3d_kernel(const StepParams P) {
   }
 }
 
-template <int N, typename MT>
+template <int N, typename M>
 __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
   constexpr int W = kTX + 8;
   constexpr int HX = kTY3;      // v_x rows y0 .. y0+TY-1
@@ -459,9 +593,6 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
   __shared__ __align__(16) float svy[HY][W];
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY3, z0 = blockIdx.z * kTZ;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const MT *ik2 = static_cast<const MT *>(P.ik2);
-  const MT *Km = static_cast<const MT *>(P.K);
-  const MT *chim = static_cast<const MT *>(P.chi);
   const int i0 = x0 + 4 * tx;
   const bool fast_xy = interior_xy(P, x0, y0) && P.g11h == 0.f;  // cross taps: general path
   const int zend = min(z0 + kTZ, P.nz);
@@ -482,7 +613,7 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
     const int ly = ty + rr * kBY3, j = y0 + ly;
     if (i0 >= P.nx || j >= P.ny) continue;
     if (fast_xy && interior_z(P, k)) {
-      prs3d_fast<N, MT>(P, svx, svy, i0, j, k, tx, ly);
+      prs3d_fast<N, M>(P, svx, svy, i0, j, k, tx, ly);
       continue;
     }
     const long long c = (long long)k * P.plane + (long long)j * P.pitch + i0;
@@ -521,16 +652,16 @@ __global__ void __launch_bounds__(256, 2) prs3d_kernel(const StepParams P) {
       }
     }
     if (P.g11h != 0.f) prs3_cross(P, i0, j, k, Dx, Dy, Dz);
-    const float4 k2 = ldmap4(ik2, c, P.ms[kMsIk2]);
-    const float4 Sx = stretch4<0, 2, N, MT>(P, P.psi2[0], Dx, k2, c, i0, j, k);
-    const float4 Sy = stretch4<1, 2, N, MT>(P, P.psi2[1], Dy, k2, c, i0, j, k);
-    const float4 Sz = stretch4<2, 2, N, MT>(P, P.psi2[2], Dz, k2, c, i0, j, k);
-    const float4 K = ldmap4(Km, c, P.ms[kMsK]);
+    const float4 k2 = M::v4(P, kMsIk2, c);
+    const float4 Sx = stretch4<0, 2, N, M>(P, P.psi2[0], Dx, k2, c, i0, j, k);
+    const float4 Sy = stretch4<1, 2, N, M>(P, P.psi2[1], Dy, k2, c, i0, j, k);
+    const float4 Sz = stretch4<2, 2, N, M>(P, P.psi2[2], Dz, k2, c, i0, j, k);
+    const float4 K = M::v4(P, kMsK, c);
     float4 p = ld_state4(P.p, c);
     float4 upd = make_float4(P.dt * K.x * (Sx.x + Sy.x + Sz.x), P.dt * K.y * (Sx.y + Sy.y + Sz.y),
                              P.dt * K.z * (Sx.z + Sy.z + Sz.z), P.dt * K.w * (Sx.w + Sy.w + Sz.w));
     if (P.nl) {
-      const float4 ch = ldmap4(chim, c, P.ms[kMsChi]);
+      const float4 ch = M::v4(P, kMsChi, c);
       upd.x = qdiv(upd.x, fmaf(ch.x, p.x, 1.f)); upd.y = qdiv(upd.y, fmaf(ch.y, p.y, 1.f));
       upd.z = qdiv(upd.z, fmaf(ch.z, p.z, 1.f)); upd.w = qdiv(upd.w, fmaf(ch.w, p.w, 1.f));
     }
@@ -548,24 +679,26 @@ constexpr int kNLo = 5, kNHi = kMaxRelax;
 constexpr int kNLo = 0, kNHi = 4;
 #endif
 
-template <int N, typename MT>
+template <int N, typename M>
 cudaError_t vel3d_at(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
   if constexpr (N > kNHi) {
     return cudaErrorInvalidValue;
   } else {
-    if (P.n_relax != N) return vel3d_at<N + 1, MT>(P, g, b, s);
-    vel3d_kernel<N, MT><<<g, b, 0, s>>>(P);
+    if (P.n_relax != N) return vel3d_at<N + 1, M>(P, g, b, s);
+    if constexpr (kIndexed3<M> && N > kTabSlots) return cudaErrorInvalidValue;  // tables hold kTabSlots
+    else vel3d_kernel<N, M><<<g, b, 0, s>>>(P);
     return cudaGetLastError();
   }
 }
 
-template <int N, typename MT>
+template <int N, typename M>
 cudaError_t prs3d_at(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
   if constexpr (N > kNHi) {
     return cudaErrorInvalidValue;
   } else {
-    if (P.n_relax != N) return prs3d_at<N + 1, MT>(P, g, b, s);
-    prs3d_kernel<N, MT><<<g, b, 0, s>>>(P);
+    if (P.n_relax != N) return prs3d_at<N + 1, M>(P, g, b, s);
+    if constexpr (kIndexed3<M> && N > kTabSlots) return cudaErrorInvalidValue;  // tables hold kTabSlots
+    else prs3d_kernel<N, M><<<g, b, 0, s>>>(P);
     return cudaGetLastError();
   }
 }
@@ -575,12 +708,18 @@ cudaError_t prs3d_at(const StepParams &P, dim3 g, dim3 b, cudaStream_t s) {
 #ifdef FW2_WIDE_RELAX
 cudaError_t launch_vel3d_wide(const StepParams &P, int map_kind, cudaStream_t s) {
 #else
-cudaError_t launch_vel3d(const StepParams &P, int map_kind, cudaStream_t s) {  // map kind 0, 1 or 4
+cudaError_t launch_vel3d(const StepParams &P, int map_kind, cudaStream_t s) {
   if (P.n_relax > kNHi) return launch_vel3d_wide(P, map_kind, s);
 #endif
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kBY3);
-  if (map_kind == 4) return vel3d_at<kNLo, __half>(P, g, b, s);
-  return map_kind == 1 ? vel3d_at<kNLo, __nv_bfloat16>(P, g, b, s) : vel3d_at<kNLo, float>(P, g, b, s);
+  switch (map_kind) {
+    case 0: return vel3d_at<kNLo, Dense3<float>>(P, g, b, s);
+    case 1: return vel3d_at<kNLo, Dense3<__nv_bfloat16>>(P, g, b, s);
+    case 2: return vel3d_at<kNLo, Idx3<unsigned char>>(P, g, b, s);
+    case 3: return vel3d_at<kNLo, Idx3<unsigned short>>(P, g, b, s);
+    case 4: return vel3d_at<kNLo, Dense3<__half>>(P, g, b, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 #ifdef FW2_WIDE_RELAX
@@ -590,8 +729,14 @@ cudaError_t launch_prs3d(const StepParams &P, int map_kind, cudaStream_t s) {
   if (P.n_relax > kNHi) return launch_prs3d_wide(P, map_kind, s);
 #endif
   dim3 g((P.nx + kTX - 1) / kTX, (P.ny + kTY3 - 1) / kTY3, (P.nz + kTZ - 1) / kTZ), b(32, kBY3);
-  if (map_kind == 4) return prs3d_at<kNLo, __half>(P, g, b, s);
-  return map_kind == 1 ? prs3d_at<kNLo, __nv_bfloat16>(P, g, b, s) : prs3d_at<kNLo, float>(P, g, b, s);
+  switch (map_kind) {
+    case 0: return prs3d_at<kNLo, Dense3<float>>(P, g, b, s);
+    case 1: return prs3d_at<kNLo, Dense3<__nv_bfloat16>>(P, g, b, s);
+    case 2: return prs3d_at<kNLo, Idx3<unsigned char>>(P, g, b, s);
+    case 3: return prs3d_at<kNLo, Idx3<unsigned short>>(P, g, b, s);
+    case 4: return prs3d_at<kNLo, Dense3<__half>>(P, g, b, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace fw2

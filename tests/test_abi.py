@@ -59,10 +59,9 @@ def test_abi_version(fw2lib):
     ({"kernel_path": 5}, fw2.EINVAL),
     ({"mem_alignment": 2}, fw2.EINVAL),
     ({"map_precision": 5}, fw2.EINVAL),
-    ({"ndim": 3, "n": (64, 64, 64), "map_precision": 2}, fw2.EUNSUPPORTED),
     ({"map_precision": 2, "n_relax": 5}, fw2.EUNSUPPORTED),                # index tables: N <= 4
-    ({"ndim": 3, "n": (64, 64, 64), "map_precision": 3}, fw2.EUNSUPPORTED),   # uint16 index: 2D
     ({"map_precision": 3, "n_relax": 5}, fw2.EUNSUPPORTED),
+    ({"ndim": 3, "n": (64, 64, 64), "map_precision": 2, "n_relax": 6}, fw2.EUNSUPPORTED),
     ({"pml_reading": 1}, fw2.EINVAL),                                      # withdrawn reading
     ({"pml_reading": 4}, fw2.EINVAL),
 ])

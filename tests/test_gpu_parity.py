@@ -283,6 +283,58 @@ def test_parity_3d(fw2):
     compare_run(fw2, prob, 80)
 
 
+def indexed_3d(n=(70, 40, 36), N=3, n_tissue=6, seed=11, nl="westervelt", steps=60):
+    """small_3d's grid, sources and sensors over a seeded tissue-index medium:
+    n_tissue tissues with their own c, rho, beta and relaxation rates (the
+    brain set scaled per tissue), a random tissue per cell (uint8, or uint16
+    beyond 256 tissues); the dense arrays are the tables gathered."""
+    prob = small_3d(n=n, N=N, nl=nl, steps=steps, seed=seed)
+    rng = np.random.default_rng(seed)
+    base = relax_set(N)
+    tab = {"c": (1500 + 120 * rng.random(n_tissue)).astype(np.float32),
+           "rho": (1000 + 150 * rng.random(n_tissue)).astype(np.float32),
+           "beta": rng.uniform(3, 6, n_tissue).astype(np.float32),
+           "kappa1": np.full(n_tissue, base["kappa1"], np.float32),
+           "kappa2": np.full(n_tissue, base["kappa2"], np.float32)}
+    f = rng.uniform(0.8, 1.2, (4, N, n_tissue))
+    for i, key in enumerate(("d1", "alpha1", "d2", "alpha2")):
+        tab[key] = (np.asarray(base[key][:N], np.float64)[:, None] * f[i]).astype(np.float32)
+    t = rng.integers(0, n_tissue, prob.grid_shape)
+    prob.tissue = t.astype(np.uint8 if n_tissue <= 256 else np.uint16)
+    prob.tables = tab
+    prob.c, prob.rho, prob.beta = tab["c"][t], tab["rho"][t], tab["beta"][t]
+    prob.kappa1, prob.kappa2 = tab["kappa1"][t], tab["kappa2"][t]
+    prob.d1, prob.alpha1 = tab["d1"][:, t], tab["alpha1"][:, t]
+    prob.d2, prob.alpha2 = tab["d2"][:, t], tab["alpha2"][:, t]
+    prob.dt = 0.4 * prob.h / float(tab["c"].max()) * 0.95
+    return prob
+
+
+@pytest.mark.parametrize("maps,n_tissue,nl", [("idx", 6, "westervelt"), ("idx16", 300, "literal")])
+def test_parity_3d_tissue_index(fw2, maps, n_tissue, nl):
+    """The tissue index in 3D (tables through L2, tile kernels) against the
+    oracle; the uint8 form also bitwise against the same medium as dense float
+    maps (the tables gathered per cell)."""
+    prob = indexed_3d(n_tissue=n_tissue, nl=nl)
+    if nl == "literal":
+        prob.sources[0].signal = prob.sources[0].signal * 20.0
+    sim = fw2.Simulation(prob, map_precision=maps)
+    sim.step(1)
+    assert fw2.fw2_kernel_path(sim.ctx) == "tile"
+    sim.close()
+    compare_run(fw2, prob, 60, maps=maps)
+    if maps == "idx":
+        out = {}
+        for m in ("idx", "f32"):
+            s = fw2.Simulation(prob, map_precision=m, kernel_path="tile")
+            s.step(60)
+            out[m] = ({n: s.field(n) for n in ("p", "vx", "vz")}, s.trace.cpu().numpy())
+            s.close()
+        for n in ("p", "vx", "vz"):
+            np.testing.assert_array_equal(out["idx"][0][n], out["f32"][0][n], err_msg=n)
+        np.testing.assert_array_equal(out["idx"][1], out["f32"][1])
+
+
 @pytest.mark.parametrize("case", ["nonlinear-pressure", "literal-N4", "readingA", "ragged-203x77"])
 def test_parity_2d_fp16_maps(fw2, case):
     """FP16 maps (each map divided by its power-of-two scale) on the tile
