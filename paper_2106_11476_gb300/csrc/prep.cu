@@ -15,6 +15,8 @@
 // The profile of a face is evaluated at its exact staggered coordinate; the
 // relaxation parameters of a face are those of its lower-index cell.
 #include "fw2_prep.cuh"
+#include <type_traits>
+
 #include "maps.cuh"
 
 namespace fw2 {
@@ -76,6 +78,18 @@ struct MapSink {
     if constexpr (SCAN) mx[id] = fmaxf(mx[id], (float)fabs(1.0 - b));
     else store_b(static_cast<MT *>(p), i, b, Q.inv_scale[id]);
   }
+  // the same with 1 - b given (float maps keep b, the others 1 - b)
+  __device__ __forceinline__ void put_b2(int id, void *p, long long i, float b, float omb) {
+    if constexpr (SCAN) {
+      mx[id] = fmaxf(mx[id], fabsf(omb));
+    } else if constexpr (std::is_same<MT, float>::value) {
+      static_cast<float *>(p)[i] = b;
+    } else if constexpr (std::is_same<MT, __nv_bfloat16>::value) {
+      static_cast<__nv_bfloat16 *>(p)[i] = __float2bfloat16_rn(omb);
+    } else {
+      static_cast<__half *>(p)[i] = __float2half_rn((float)((double)omb * Q.inv_scale[id]));
+    }
+  }
   __device__ __forceinline__ void flush() {
     if constexpr (SCAN) {
       const unsigned lane = threadIdx.x & 31;
@@ -86,6 +100,23 @@ struct MapSink {
     }
   }
 };
+
+// The cell maps' relaxation coefficients in float arithmetic (the cell maps
+// dominate the build; GB300's FP64 rate would make it an order of magnitude
+// slower): em = expm1(-(d/kappa + alpha) dt) keeps b - 1 accurate when
+// b is near 1; b = 1 + em, 1 - b = -em (what bf16 and FP16 maps store),
+// a = (d/kappa) em / (d + kappa alpha).  A few float ulps from the FP64
+// values, far inside the parity bound; the per-tissue tables use the same
+// function, so the index form stays bitwise equal to the gathered dense maps.
+__device__ __forceinline__ void relax_ab32(float d, float alpha, float kappa, float ik, float dt, float &a,
+                                           float &b, float &omb) {
+  const float dk = d * ik;
+  const float em = expm1f(-(dk + alpha) * dt);
+  b = 1.f + em;
+  omb = -em;
+  const float den = d + kappa * alpha;
+  a = (d == 0.f || den == 0.f) ? 0.f : dk * em / den;
+}
 
 // b = exp(-(d/kappa + alpha) dt), a = d (b - 1) / (kappa (d + kappa alpha))
 // with d / kappa = d ik (ik = 1 / kappa, computed once per cell) and
@@ -163,14 +194,15 @@ __global__ void cell_maps_kernel(const PrepParams Q) {
     const double ik1 = 1.0 / k1, ik2 = 1.0 / k2;
     out.put(kMsIk1, Q.ik1, o, ik1);
     out.put(kMsIk2, Q.ik2, o, ik2);
+    const float dt = (float)Q.dt;
     for (int nu = 0; nu < Q.N; ++nu) {
-      double a, b;
-      relax_ab(Q.d1[nu * n + t], Q.al1[nu * n + t], k1, ik1, Q.dt, a, b);
+      float a, b, omb;
+      relax_ab32(Q.d1[nu * n + t], Q.al1[nu * n + t], (float)k1, (float)ik1, dt, a, b, omb);
       out.put(kMsA1 + nu, Q.a1, nu * Q.npts_alloc + o, a);
-      out.put_b(kMsB1 + nu, Q.b1, nu * Q.npts_alloc + o, b);
-      relax_ab(Q.d2[nu * n + t], Q.al2[nu * n + t], k2, ik2, Q.dt, a, b);
+      out.put_b2(kMsB1 + nu, Q.b1, nu * Q.npts_alloc + o, b, omb);
+      relax_ab32(Q.d2[nu * n + t], Q.al2[nu * n + t], (float)k2, (float)ik2, dt, a, b, omb);
       out.put(kMsA2 + nu, Q.a2, nu * Q.npts_alloc + o, a);
-      out.put_b(kMsB2 + nu, Q.b2, nu * Q.npts_alloc + o, b);
+      out.put_b2(kMsB2 + nu, Q.b2, nu * Q.npts_alloc + o, b, omb);
     }
   }
   out.flush();
@@ -195,14 +227,15 @@ __global__ void table_kernel(const PrepParams Q) {
   const double k1 = Q.N ? (double)Q.k1[t] : 1.0, k2 = Q.N ? (double)Q.k2[t] : 1.0;
   T[kTabIk1 * S + t] = (float)(1.0 / k1);
   T[kTabIk2 * S + t] = (float)(1.0 / k2);
+  const float dt = (float)Q.dt;
   for (int nu = 0; nu < Q.N; ++nu) {
-    double a, b;
-    relax_ab(Q.d1[nu * Q.n_tissue + t], Q.al1[nu * Q.n_tissue + t], k1, 1.0 / k1, Q.dt, a, b);
-    T[(kTabRelax + nu) * S + t] = (float)a;
-    T[(kTabRelax + kTabSlots + nu) * S + t] = (float)b;
-    relax_ab(Q.d2[nu * Q.n_tissue + t], Q.al2[nu * Q.n_tissue + t], k2, 1.0 / k2, Q.dt, a, b);
-    T[(kTabRelax + 2 * kTabSlots + nu) * S + t] = (float)a;
-    T[(kTabRelax + 3 * kTabSlots + nu) * S + t] = (float)b;
+    float a, b, omb;
+    relax_ab32(Q.d1[nu * Q.n_tissue + t], Q.al1[nu * Q.n_tissue + t], (float)k1, (float)(1.0 / k1), dt, a, b, omb);
+    T[(kTabRelax + nu) * S + t] = a;
+    T[(kTabRelax + kTabSlots + nu) * S + t] = b;
+    relax_ab32(Q.d2[nu * Q.n_tissue + t], Q.al2[nu * Q.n_tissue + t], (float)k2, (float)(1.0 / k2), dt, a, b, omb);
+    T[(kTabRelax + 2 * kTabSlots + nu) * S + t] = a;
+    T[(kTabRelax + 3 * kTabSlots + nu) * S + t] = b;
   }
 }
 
