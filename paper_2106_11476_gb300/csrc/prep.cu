@@ -40,23 +40,13 @@ __device__ __forceinline__ void store(float *p, long long i, double v) { p[i] = 
 __device__ __forceinline__ void store(__nv_bfloat16 *p, long long i, double v) {
   p[i] = __float2bfloat16_rn((float)v);
 }
-// decay factor b: float maps hold b, bf16 maps hold 1 - b
-__device__ __forceinline__ void store_b(float *p, long long i, double b) { p[i] = (float)b; }
-__device__ __forceinline__ void store_b(__nv_bfloat16 *p, long long i, double b) {
-  p[i] = __float2bfloat16_rn((float)(1.0 - b));
-}
 // FP16 maps: the value times the map's inverse scale (a power of two, exact),
-// rounded to float then to half; b kept as 1 - b
+// rounded to float then to half
 __device__ __forceinline__ void store(__half *p, long long i, double v, double inv) {
   p[i] = __float2half_rn((float)(v * inv));
 }
-__device__ __forceinline__ void store_b(__half *p, long long i, double b, double inv) {
-  p[i] = __float2half_rn((float)((1.0 - b) * inv));
-}
 __device__ __forceinline__ void store(float *p, long long i, double v, double) { store(p, i, v); }
 __device__ __forceinline__ void store(__nv_bfloat16 *p, long long i, double v, double) { store(p, i, v); }
-__device__ __forceinline__ void store_b(float *p, long long i, double b, double) { store_b(p, i, b); }
-__device__ __forceinline__ void store_b(__nv_bfloat16 *p, long long i, double b, double) { store_b(p, i, b); }
 
 // Where the map kernels put a value: stored (scaled for FP16), or, in the
 // scan pass of the FP16 maps, folded into this thread's largest magnitude of
@@ -74,11 +64,8 @@ struct MapSink {
     if constexpr (SCAN) mx[id] = fmaxf(mx[id], (float)fabs(v));
     else store(static_cast<MT *>(p), i, v, Q.inv_scale[id]);
   }
-  __device__ __forceinline__ void put_b(int id, void *p, long long i, double b) {
-    if constexpr (SCAN) mx[id] = fmaxf(mx[id], (float)fabs(1.0 - b));
-    else store_b(static_cast<MT *>(p), i, b, Q.inv_scale[id]);
-  }
-  // the same with 1 - b given (float maps keep b, the others 1 - b)
+  // decay factor b with 1 - b given: float maps keep b, bf16 and FP16 maps
+  // 1 - b (FP16 times the map's inverse scale)
   __device__ __forceinline__ void put_b2(int id, void *p, long long i, float b, float omb) {
     if constexpr (SCAN) {
       mx[id] = fmaxf(mx[id], fabsf(omb));
@@ -101,13 +88,17 @@ struct MapSink {
   }
 };
 
-// The cell maps' relaxation coefficients in float arithmetic (the cell maps
-// dominate the build; GB300's FP64 rate would make it an order of magnitude
-// slower): em = expm1(-(d/kappa + alpha) dt) keeps b - 1 accurate when
-// b is near 1; b = 1 + em, 1 - b = -em (what bf16 and FP16 maps store),
+// Relaxation coefficients of Eqs. (relaxation_a), (relaxation_b) (Sec. 3.2)
+// in float arithmetic, for the cell maps, the C-PML strips and the tissue
+// tables alike (GB300's FP64 rate would make the build an order of magnitude
+// slower):
+//   b = exp(-(d/kappa + alpha) dt),  a = d (b - 1) / (kappa (d + kappa alpha)).
+// em = expm1(-(d/kappa + alpha) dt) keeps b - 1 accurate when b is near 1;
+// b = 1 + em, 1 - b = -em (what bf16 and FP16 maps store), and
 // a = (d/kappa) em / (d + kappa alpha).  A few float ulps from the FP64
-// values, far inside the parity bound; the per-tissue tables use the same
-// function, so the index form stays bitwise equal to the gathered dense maps.
+// values, far inside the parity bound.  One function everywhere keeps the
+// index form bitwise equal to the gathered dense maps, and a strip cell at
+// depth 0 (a subdomain's cut side) equal to the interior cell it continues.
 __device__ __forceinline__ void relax_ab32(float d, float alpha, float kappa, float ik, float dt, float &a,
                                            float &b, float &omb) {
   const float dk = d * ik;
@@ -116,18 +107,6 @@ __device__ __forceinline__ void relax_ab32(float d, float alpha, float kappa, fl
   omb = -em;
   const float den = d + kappa * alpha;
   a = (d == 0.f || den == 0.f) ? 0.f : dk * em / den;
-}
-
-// b = exp(-(d/kappa + alpha) dt), a = d (b - 1) / (kappa (d + kappa alpha))
-// with d / kappa = d ik (ik = 1 / kappa, computed once per cell) and
-// a = (d / kappa) (b - 1) / (d + kappa alpha): one FP64 division besides the
-// exponential (FP64 throughput bounds the coefficient build)
-__device__ __forceinline__ void relax_ab(double d, double alpha, double kappa, double ik, double dt, double &a,
-                                         double &b) {
-  const double dk = d * ik;
-  b = exp(-(dk + alpha) * dt);
-  const double den = d + kappa * alpha;
-  a = (d == 0.0 || den == 0.0) ? 0.0 : dk * (b - 1.0) / den;
 }
 
 // depth (cells, 0..L) into the boundary region of coordinate x on an axis of
@@ -287,19 +266,20 @@ __global__ void strip_maps_kernel(const PrepParams Q, int axis) {
     const double dcent = depth_of((double)(Q.goff[axis] + cell[axis]), Q.gext[axis], L);
     const long long ri = src_of(Q, src), nr = n_src(Q);
     const double k1 = Q.k1[ri], k2 = Q.k2[ri];
-    const double ik1 = 1.0 / k1, ik2 = 1.0 / k2;
+    const float ik1 = (float)(1.0 / k1), ik2 = (float)(1.0 / k2), dt = (float)Q.dt;
+    // the ramped parameters (FP64) through the float coefficients of the cells
     for (int nu = 0; nu < Q.N; ++nu) {
-      double a, b;
+      float a, b, omb;
       const double d1 = ramp(Q, Q.d1[nu * nr + ri], dface, nu, true);
       const double al1 = ramp(Q, Q.al1[nu * nr + ri], dface, nu, false);
-      relax_ab(d1, al1, k1, ik1, Q.dt, a, b);
+      relax_ab32((float)d1, (float)al1, (float)k1, ik1, dt, a, b, omb);
       sink.put(kMsA1 + nu, Q.sa1[axis], nu * Q.strip_nu[axis] + out, a);
-      sink.put_b(kMsB1 + nu, Q.sb1[axis], nu * Q.strip_nu[axis] + out, b);
+      sink.put_b2(kMsB1 + nu, Q.sb1[axis], nu * Q.strip_nu[axis] + out, b, omb);
       const double d2 = ramp(Q, Q.d2[nu * nr + ri], dcent, nu, true);
       const double al2 = ramp(Q, Q.al2[nu * nr + ri], dcent, nu, false);
-      relax_ab(d2, al2, k2, ik2, Q.dt, a, b);
+      relax_ab32((float)d2, (float)al2, (float)k2, ik2, dt, a, b, omb);
       sink.put(kMsA2 + nu, Q.sa2[axis], nu * Q.strip_nu[axis] + out, a);
-      sink.put_b(kMsB2 + nu, Q.sb2[axis], nu * Q.strip_nu[axis] + out, b);
+      sink.put_b2(kMsB2 + nu, Q.sb2[axis], nu * Q.strip_nu[axis] + out, b, omb);
     }
   }
   sink.flush();
