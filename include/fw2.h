@@ -200,8 +200,10 @@ fw2_status fw2_set_medium_indexed(fw2_ctx *ctx, const void *tissue, int32_t n_ti
 /* Relaxation parameters (Sec. 3.2, Table 2 shape); required when N > 0.
  * The coefficient maps (b = exp(-(d/kappa + alpha) dt),
  * a = d (b - 1) / (kappa (d + kappa alpha)), Eqs. relaxation_a/b; the C-PML
- * ramps of Table 1) are built on the device in FP64 at the first fw2_step
- * (or fw2_get_dt) after medium and relaxation are set. */
+ * ramps of Table 1) are built on the device at the first fw2_step (or
+ * fw2_get_dt) after medium and relaxation are set: K, rho, chi, 1/kappa and
+ * the ramped d, alpha in FP64, rounded once; a and b in float (b - 1 through
+ * expm1), a few float ulps from their FP64 values. */
 fw2_status fw2_set_relaxation(fw2_ctx *ctx, const fw2_relax_desc *desc);
 
 /* Add an additive source (the paper's transmit events, Sec. 4 and the

@@ -1,4 +1,5 @@
-// One-time coefficient preparation on the device, in FP64 (Sec. 3.2, 3.3).
+// One-time coefficient preparation on the device (Sec. 3.2, 3.3): FP64 for
+// everything but the relaxation pair a, b, which is float (relax_ab32).
 //
 // From the raw per-cell medium (c, rho, beta) and relaxation parameters
 // (kappa1, kappa2, d^nu, alpha^nu for nabla_1 and nabla_2) it writes the maps
