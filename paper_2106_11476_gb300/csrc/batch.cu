@@ -1,14 +1,19 @@
-// Batched stepping of many 2D contexts (transmit events, requests of a
-// serving loop) in persistent launches, with a CUDA-graph-captured step loop.
+// Batched stepping of many contexts (transmit events, requests of a serving
+// loop) in persistent launches, with a CUDA-graph-captured step loop.
 //
-// Per time step, for every group of contexts sharing the mechanism count and
-// the map kind: one persistent velocity launch over the group's tile table,
-// one launch injecting the velocity sources of all contexts, one persistent
-// pressure launch, one launch for the pressure sources, one for the
-// recordings, and a tick of the per-context step counters kept on the
-// device.  Since every per-step index comes from those counters, a chunk of
-// steps is captured once as a CUDA graph and replayed.  Each context computes
-// exactly what fw2_step computes for it alone (same tile arithmetic).
+// The active contexts form groups that share the dimension, the mechanism
+// count and the map kind (in 3D also the cross taps and the layout of each
+// half step).  Per time step: for every group one persistent velocity launch
+// over the group's work table (2D pipelined: units of 128 x 8 cells; 2D tile
+// path: tiles; 3D: the z-marching items of every context), one launch per
+// velocity source kind present (v_x, v_y, v_z) over all contexts, one
+// persistent pressure launch per group, one launch for the pressure
+// sources, one for the recordings, and a tick of the per-context step
+// counters kept on the device.  Since every per-step index comes from those
+// counters, a chunk of steps is captured once as a CUDA graph and replayed.
+// Each context computes exactly what fw2_step computes for it alone (same
+// per-cell arithmetic).  Contexts leave the tables when they reach their
+// step budget.
 #include <algorithm>
 #include <climits>
 #include <cstdio>
