@@ -239,7 +239,43 @@ def _round_of(maps):
     return "f32" if maps in ("idx", "idx16") else maps
 
 
-def oracle_baseline(prob, steps, window, maps="f32", media=True):
+def _openmp():
+    """The OpenMP runtime the oracle's stepper runs its loops on, or None."""
+    import ctypes
+    try:
+        return ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        return None
+
+
+def oracle_threads():
+    """Threads the oracle's parallel loops use (the OpenMP runtime's count)."""
+    omp = _openmp()
+    if omp is not None:
+        return int(omp.omp_get_max_threads())
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def oracle_single_core(orc, steps):
+    """`steps` more steps of an oracle run on one thread: the per-core rate
+    beside the all-core figure, or None without an OpenMP runtime."""
+    omp = _openmp()
+    if omp is None or steps < 1:
+        return None
+    old = int(omp.omp_get_max_threads())
+    omp.omp_set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        orc.run(steps)
+        dt = time.perf_counter() - t0
+    finally:
+        omp.omp_set_num_threads(old)
+    pts = int(np.prod(orc.wshape))
+    return {"value": pts * steps / dt / 1e9, "unit": UNIT, "cores": 1,
+            "sample": f"the same window, {steps} steps, {dt:.1f} s"}
+
+
+def oracle_baseline(prob, steps, window, maps="f32", media=True, single_core=True):
     """The FP64 oracle, as it stands, on a window of the workload (host
     cores).  With `media`, the same window is also run on the unrounded
     inputs: how far the stored (float32 or bf16) medium moves the result, a
@@ -251,7 +287,7 @@ def oracle_baseline(prob, steps, window, maps="f32", media=True):
     orc.run(steps)
     dt = time.perf_counter() - t0
     pts = int(np.prod(orc.wshape))
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = oracle_threads()
     out = {"value": pts * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": f"{'x'.join(str(w) for w in orc.wshape)} window of the workload around the array "
                      f"(sources inside), {steps} steps, {dt:.1f} s"}
@@ -268,6 +304,11 @@ def oracle_baseline(prob, steps, window, maps="f32", media=True):
         dev["how"] = (f"oracle on the {maps} maps the kernels stream vs the oracle on the unrounded inputs, "
                       f"same window, {2 + steps} steps from rest")
         out["media_deviation"] = dev
+    if single_core and threads > 1:
+        # about half the all-core sample's time on one core
+        one = oracle_single_core(orc, max(1, steps // (2 * threads)))
+        if one is not None:
+            out["single_core"] = one
     return out
 
 
@@ -996,7 +1037,7 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     pts = int(np.prod(orc.wshape))
     value = pts * args.steps / dt / 1e9
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = oracle_threads()
     sample = f"256x256 window of the {n}x{n} workload around the array, one oracle time step per bench step"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,

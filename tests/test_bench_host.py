@@ -141,3 +141,19 @@ def test_problem_feed_hands_out_in_order_and_stops_the_clock():
     feed.close()
     assert made == [0, 1, 2, 3, 4]
     assert clock.stopped == pytest.approx(feed.waited) and clock.stopped >= 0.0
+
+
+def test_oracle_baseline_reports_the_threads_used_and_a_single_core_rate():
+    """The cpu_baseline leg states the OpenMP threads the oracle ran on and,
+    beside the all-core rate, the rate on one core; the thread count is back
+    to what it was afterwards."""
+    import synth
+    before = bench.oracle_threads()
+    prob = synth.line_source_problem(n=160, n_steps=40, seed=0)
+    out = bench.oracle_baseline(prob, 16, ((0, 160), (0, 160)), media=False)
+    assert out["kind"] == "oracle" and out["value"] > 0
+    assert out["cores"] == before >= 1
+    if before > 1 and bench._openmp() is not None:
+        one = out["single_core"]
+        assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == out["unit"]
+    assert bench.oracle_threads() == before
