@@ -127,6 +127,11 @@ def split_overhead_bytes(shape, indexed=False, index_bytes=1):
 # helpers
 # --------------------------------------------------------------------------
 
+# GB300's nominal HBM3e bandwidth; the roofline's denominator is the measured
+# copy bandwidth, this one is reported beside it
+NOMINAL_HBM_GBS = 7900.0
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -524,6 +529,7 @@ def measure(args, prob, maps, desc, steps, warmup, rank, world, dist, want_e2e=T
             "algorithmic_bytes_per_cell_step": round(step_b / prob.n_pts, 2),
             "avg_launch_ms": round(dom_ms, 5),
             "peak_source": f"{peak_kind} copy bandwidth hbm_gbs",
+            "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "nominal_gbs": NOMINAL_HBM_GBS,
             "step_frac": round(step_b / ((vel_ms / nv + prs_ms / np_) * 1e-3) / 1e9 / peak, 4),
             "step_frac_of_ms_per_step": round(step_b * steps / (elapsed_max * 1e-3) / 1e9 / peak, 4),
             "vel_ms": round(vel_ms / nv, 5), "prs_ms": round(prs_ms / np_, 5)}
