@@ -163,6 +163,54 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+# Grid of every context created through this binding, by handle: (nx, ny,
+# nz, ndim, n_relax).  The C ABI takes bare pointers whose extents follow the
+# grid, so the binding checks each buffer against it before the call (a short
+# buffer would let the library read or write past it).
+_GRIDS = {}
+
+
+def _grid_cells(ctx):
+    """(cells of the grid, cells of one row along the slowest axis, n_relax),
+    or None for a context this binding did not create."""
+    g = _GRIDS.get(ctx)
+    if g is None:
+        return None
+    nx, ny, nz, nd, N = g
+    return nx * ny * (nz if nd == 3 else 1), nx * (ny if nd == 3 else 1), N
+
+
+def _want(a, dtype, count, name, out=False, exact=False):
+    """Check one buffer of a call.  Host inputs (numpy) are converted to
+    `dtype`; tensors must already hold it.  Output buffers must be contiguous
+    (a copy would take the library's writes) and, numpy ones, writable.
+    `count` (None: unknown) is the number of elements the library reads or
+    writes through the buffer: it must hold at least that many (exactly
+    that many with `exact`)."""
+    if a is None:
+        return None
+    dt = np.dtype(dtype)
+    if isinstance(a, np.ndarray):
+        if out:
+            if a.dtype != dt or not a.flags.c_contiguous or not a.flags.writeable:
+                raise ValueError(f"{name} must be a writable C-contiguous {dt.name} array")
+        else:
+            a = np.ascontiguousarray(a, dt)
+        n = a.size
+    else:
+        import torch
+        if not isinstance(a, torch.Tensor):
+            raise TypeError(f"{name}: a numpy array or a torch tensor, not {type(a).__name__}")
+        if a.dtype != getattr(torch, dt.name):
+            raise ValueError(f"{name} must hold {dt.name}, not {a.dtype}")
+        if out and not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        n = a.numel()
+    if count is not None and (n != count if exact else n < count):
+        raise ValueError(f"{name} holds {n} elements; the call {'writes' if out else 'reads'} {count}")
+    return a
+
+
 def _same_space(*arrays):
     spaces = {_ptr(a)[1] for a in arrays if a is not None}
     if len(spaces) > 1:
@@ -183,22 +231,29 @@ def fw2_create(cfg: Config) -> int:
     """Create a context for one grid (fw2_create); returns the handle."""
     h = C.c_void_p()
     _check(lib().fw2_create(C.byref(cfg), C.byref(h)))
+    _GRIDS[h.value] = (int(cfg.n[0]), int(cfg.n[1]), int(cfg.n[2]), int(cfg.ndim), int(cfg.n_relax))
     return h.value
 
 
 def fw2_set_medium(ctx, c, rho, beta=None):
     """c, rho and beta of every cell, host or device arrays (fw2_set_medium)."""
+    g = _grid_cells(ctx)
+    n = g[0] if g else None
+    c, rho, beta = (_want(a, np.float32, n, nm, exact=True) for a, nm in ((c, "c"), (rho, "rho"), (beta, "beta")))
     space = _same_space(c, rho, beta)
-    pc, _, kc = _ptr(np.asarray(c, np.float32) if isinstance(c, np.ndarray) else c)
-    pr, _, kr = _ptr(np.asarray(rho, np.float32) if isinstance(rho, np.ndarray) else rho)
-    pb, _, kb = _ptr(np.asarray(beta, np.float32) if isinstance(beta, np.ndarray) else beta)
+    pc, _, kc = _ptr(c)
+    pr, _, kr = _ptr(rho)
+    pb, _, kb = _ptr(beta)
     _check(lib().fw2_set_medium(ctx, pc, pr, pb, space), ctx)
 
 
 def fw2_set_relaxation(ctx, kappa1, kappa2, d1, alpha1, d2, alpha2):
     """Interior relaxation parameters of every cell (fw2_set_relaxation)."""
-    arrs = [np.asarray(x, np.float32) if isinstance(x, np.ndarray) else x
-            for x in (kappa1, kappa2, d1, alpha1, d2, alpha2)]
+    g = _grid_cells(ctx)
+    counts = (g[0], g[0]) + (g[2] * g[0],) * 4 if g else (None,) * 6
+    names = ("kappa1", "kappa2", "d1", "alpha1", "d2", "alpha2")
+    arrs = [_want(x, np.float32, k, nm, exact=True)
+            for x, k, nm in zip((kappa1, kappa2, d1, alpha1, d2, alpha2), counts, names)]
     space = _same_space(*arrs)
     ptrs = [_ptr(a) for a in arrs]
     desc = RelaxDesc(*[p[0] for p in ptrs], space)
@@ -218,8 +273,16 @@ def fw2_set_medium_indexed(ctx, tissue, n_tissue: int, c, rho, beta, kappa1, kap
         tissue = np.asarray(tissue, np.uint16 if wide else np.uint8)
     elif tissue.element_size() != size:
         raise ValueError(f"the tissue tensor must hold {size}-byte indices")
-    tabs = [np.asarray(x, np.float32) if isinstance(x, np.ndarray) else x
-            for x in (c, rho, beta, kappa1, kappa2, d1, alpha1, d2, alpha2)]
+    g = _grid_cells(ctx)
+    if g is not None:
+        n_idx = tissue.size if isinstance(tissue, np.ndarray) else tissue.numel()
+        if n_idx != g[0]:
+            raise ValueError(f"tissue holds {n_idx} indices; the grid has {g[0]} cells")
+    nt = int(n_tissue)
+    counts = (nt,) * 5 + ((g[2] * nt,) * 4 if g else (None,) * 4)
+    names = ("c", "rho", "beta", "kappa1", "kappa2", "d1", "alpha1", "d2", "alpha2")
+    tabs = [_want(x, np.float32, k, nm)
+            for x, k, nm in zip((c, rho, beta, kappa1, kappa2, d1, alpha1, d2, alpha2), counts, names)]
     space = _same_space(tissue, *tabs)
     pt, _, kt = _ptr(tissue)
     ptrs = [_ptr(a) for a in tabs]
@@ -230,9 +293,12 @@ def fw2_set_medium_indexed(ctx, tissue, n_tissue: int, c, rho, beta, kappa1, kap
 
 def fw2_add_source(ctx, kind: str, idx, group, signal):
     """Add an additive source of kind FW2_SRC_* (fw2_add_source)."""
-    idx = np.asarray(idx, np.int64) if isinstance(idx, np.ndarray) else idx
-    group = np.asarray(group, np.int32) if isinstance(group, np.ndarray) else group
-    signal = np.asarray(signal, np.float32) if isinstance(signal, np.ndarray) else signal
+    idx = _want(idx, np.int64, None, "idx")
+    n = int(idx.shape[0])
+    group = _want(group, np.int32, n, "group", exact=True)
+    signal = _want(signal, np.float32, None, "signal")
+    if signal.ndim != 2:
+        raise ValueError("signal is [n_steps][n_groups]")
     space = _same_space(idx, group, signal)
     pi, _, ki = _ptr(idx)
     pg, _, kg = _ptr(group)
@@ -243,9 +309,18 @@ def fw2_add_source(ctx, kind: str, idx, group, signal):
 
 
 def fw2_record(ctx, idx, group, n_groups: int, out, n_steps: int):
-    """Record p after every step into a caller-owned device buffer (fw2_record)."""
-    idx = np.asarray(idx, np.int64) if isinstance(idx, np.ndarray) else idx
-    group = np.asarray(group, np.int32) if isinstance(group, np.ndarray) else group
+    """Record p after every step into a caller-owned device buffer (fw2_record).
+
+    `out` is a contiguous float32 CUDA tensor of at least n_steps x n_groups
+    elements (n_groups = the number of sensor points without `group`)."""
+    idx = _want(idx, np.int64, None, "idx")
+    n = int(idx.shape[0])
+    group = _want(group, np.int32, n, "group", exact=True)
+    if out is not None:
+        rows = max(int(n_steps), 0) * (int(n_groups) if group is not None else n)
+        _want(out, np.float32, rows if n else None, "out", out=True)
+        if isinstance(out, np.ndarray) or not out.is_cuda:
+            raise ValueError("out must be a CUDA tensor: the recording kernel writes it")
     space = _same_space(idx, group)
     pi, _, ki = _ptr(idx)
     pg, _, kg = _ptr(group)
@@ -261,6 +336,7 @@ def fw2_step(ctx, n_steps: int):
 def fw2_destroy(ctx):
     """Release the context (fw2_destroy)."""
     if ctx:
+        _GRIDS.pop(ctx, None)
         lib().fw2_destroy(ctx)
 
 
@@ -291,6 +367,8 @@ def fw2_step_part(ctx, part: int):
 
 def fw2_get_rows(ctx, field: str, row0: int, n_rows: int, out):
     """Rows along the slowest axis of p or v_q into `out` (fw2_get_rows)."""
+    g = _grid_cells(ctx)
+    _want(out, np.float32, max(int(n_rows), 0) * g[1] if g else None, "out", out=True)
     p, space, keep = _ptr(out)
     _check(lib().fw2_get_rows(ctx, FIELD[field], int(row0), int(n_rows), p, space), ctx)
     return out
@@ -298,7 +376,8 @@ def fw2_get_rows(ctx, field: str, row0: int, n_rows: int, out):
 
 def fw2_set_rows(ctx, field: str, row0: int, n_rows: int, arr):
     """Rows along the slowest axis of p or v_q from `arr` (fw2_set_rows)."""
-    arr = np.ascontiguousarray(arr, np.float32) if isinstance(arr, np.ndarray) else arr
+    g = _grid_cells(ctx)
+    arr = _want(arr, np.float32, max(int(n_rows), 0) * g[1] if g else None, "arr")
     p, space, keep = _ptr(arr)
     _check(lib().fw2_set_rows(ctx, FIELD[field], int(row0), int(n_rows), p, space), ctx)
 
@@ -315,8 +394,17 @@ def fw2_set_step(ctx, step: int):
     _check(lib().fw2_set_step(ctx, int(step)), ctx)
 
 
+def _field_cells(ctx, field: str):
+    """Elements of a state array (N per cell for the memory variables)."""
+    g = _grid_cells(ctx)
+    if g is None:
+        return None
+    return g[0] * (g[2] if field.startswith("psi") else 1)
+
+
 def fw2_get_field(ctx, field: str, out):
     """Copy a state array out (fw2_get_field)."""
+    _want(out, np.float32, _field_cells(ctx, field), "out", out=True)
     p, space, keep = _ptr(out)
     _check(lib().fw2_get_field(ctx, FIELD[field], p, space), ctx)
     return out
@@ -324,7 +412,7 @@ def fw2_get_field(ctx, field: str, out):
 
 def fw2_set_field(ctx, field: str, arr):
     """Copy a state array in (fw2_set_field)."""
-    arr = np.asarray(arr, np.float32) if isinstance(arr, np.ndarray) else arr
+    arr = _want(arr, np.float32, _field_cells(ctx, field), "arr", exact=True)
     p, space, keep = _ptr(arr)
     _check(lib().fw2_set_field(ctx, FIELD[field], p, space), ctx)
 

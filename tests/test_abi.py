@@ -4,6 +4,8 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_2106_11476_gb300 import fw2
@@ -116,3 +118,54 @@ def test_time_space_taps_match_the_oracle(fw2lib, r, ndim):
 def test_time_space_taps_reject_bad_arguments(fw2lib, r, ndim):
     with pytest.raises(fw2.Fw2Error):
         fw2.fw2_taps_time_space(r, ndim)
+
+
+def test_binding_checks_buffers_against_the_grid_before_calling(monkeypatch):
+    """The C ABI takes bare pointers whose extents follow the grid; the
+    binding rejects a buffer of the wrong type, a short one, or a
+    non-contiguous output before it calls into the library (every case
+    below raises before any C call: the handle is not a real context)."""
+    import torch
+    h = 0x5EED
+    monkeypatch.setitem(fw2._GRIDS, h, (64, 48, 1, 2, 4))
+    n = 64 * 48
+    one = np.ones(n, np.float32)
+    with pytest.raises(ValueError):
+        fw2.fw2_set_medium(h, one[:-1], one)                      # short c
+    with pytest.raises(ValueError):
+        fw2.fw2_set_medium(h, one, torch.ones(n, dtype=torch.float64))   # wrong dtype
+    with pytest.raises(ValueError):
+        fw2.fw2_set_relaxation(h, one, one, one, one, one, one)   # d, alpha are [N][cells]
+    with pytest.raises(ValueError):
+        fw2.fw2_set_medium_indexed(h, np.zeros(n - 1, np.uint8), 3, *([np.ones(3, np.float32)] * 5),
+                                   *([np.ones(12, np.float32)] * 4))
+    with pytest.raises(ValueError):
+        fw2.fw2_set_medium_indexed(h, np.zeros(n, np.uint8), 3, *([np.ones(3, np.float32)] * 5),
+                                   *([np.ones(11, np.float32)] * 4))   # tables of N x n_tissue
+    with pytest.raises(ValueError):
+        fw2.fw2_get_field(h, "p", np.empty(n - 1, np.float32))
+    with pytest.raises(ValueError):
+        fw2.fw2_get_field(h, "psi1x", np.empty(n, np.float32))   # N planes
+    with pytest.raises(ValueError):
+        fw2.fw2_get_field(h, "p", np.empty(n, np.float64))
+    with pytest.raises(ValueError):
+        fw2.fw2_get_field(h, "p", np.empty((48, 128), np.float32)[:, ::2])   # a copy would take the writes
+    with pytest.raises(ValueError):
+        fw2.fw2_set_field(h, "p", np.empty(n + 1, np.float32))
+    with pytest.raises(ValueError):
+        fw2.fw2_get_rows(h, "p", 0, 4, np.empty((3, 64), np.float32))
+    with pytest.raises(ValueError):
+        fw2.fw2_set_rows(h, "p", 0, 4, np.empty((3, 64), np.float32))
+    idx = np.arange(8, dtype=np.int64)
+    with pytest.raises(ValueError):
+        fw2.fw2_record(h, idx, np.zeros(7, np.int32), 1, torch.empty(100), 10)   # group per point
+    with pytest.raises(ValueError):
+        fw2.fw2_record(h, idx, None, 8, torch.empty(79), 10)                      # 10 x 8 outputs
+    with pytest.raises(ValueError):
+        fw2.fw2_record(h, idx, None, 8, torch.empty(80), 10)                      # host tensor
+    with pytest.raises(ValueError):
+        fw2.fw2_record(h, idx, None, 8, np.empty(80, np.float32), 10)             # host array
+    with pytest.raises(ValueError):
+        fw2.fw2_add_source(h, "p", idx, np.zeros(9, np.int32), np.zeros((10, 1), np.float32))
+    with pytest.raises(ValueError):
+        fw2.fw2_add_source(h, "p", idx, None, np.zeros(10, np.float32))           # [n_steps][n_groups]
