@@ -481,9 +481,16 @@ fw2_status enqueue_step(fw2_ctx *c, long long n, int part = -1) {
     return pipe3d_layout_allowed(vel, P, l) ? l : kLayoutRegisters;
   };
   const bool do_vel = part != 1, do_prs = part != 0;
-  cudaEvent_t te[4] = {nullptr, nullptr, nullptr, nullptr};
+  struct TrialEvents {  // destroyed on every return, error paths included
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~TrialEvents() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } trial_ev;
+  cudaEvent_t *te = trial_ev.e;
   if (trial_timed)
-    for (auto &e : te) CK(c, cudaEventCreate(&e));
+    for (int i = 0; i < 4; ++i) CK(c, cudaEventCreate(&te[i]));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->profiling) {
     ev = {take_event(c), take_event(c)};
@@ -546,7 +553,6 @@ fw2_status enqueue_step(fw2_ctx *c, long long n, int part = -1) {
       CK(c, cudaEventElapsedTime(&mp, te[2], te[3]));
       c->layout_ms[trial - 1][0] = mv;
       c->layout_ms[trial - 1][1] = mp;
-      for (auto e : te) cudaEventDestroy(e);
     }
     if (++c->layout_trial == 4)
       for (int h = 0; h < 2; ++h) {
