@@ -180,11 +180,6 @@ def _fill_relaxation(prob: Problem, tissue_of: np.ndarray, sets: List[dict],
     prob.d1, prob.alpha1, prob.d2, prob.alpha2 = d1, a1, d2, a2
 
 
-def table2_set() -> dict:
-    s = dict(TABLE2)
-    return s
-
-
 def homogeneous(shape: Sequence[int], h: float, dt: float, c: float = 1540.0,
                 rho: float = 1000.0, relax: Optional[dict] = None,
                 beta: Optional[float] = None) -> Problem:
