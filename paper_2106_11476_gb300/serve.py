@@ -51,24 +51,40 @@ class Request:
 
 
 def footprint_bytes(prob, maps: str) -> int:
-    """Device bytes of a request: state, coefficient maps and C-PML strips."""
+    """Device bytes of a request as the library allocates them (up to
+    alignment): the state, the coefficient maps (per cell in float, bf16 or
+    FP16; or the index with its per-tissue tables of 21 fields) and the C-PML
+    strips (4 arrays of N values per strip cell, in the maps' type; float for
+    the index forms)."""
     nd = len(prob.shape)
     n = int(np.prod(prob.shape))
     N = prob.nrelax
     state = (1 + nd + 2 * nd * N) * 4 * n
-    if maps == "idx":
-        mp = n + 21 * 256 * 4
+    es = 2 if maps in ("bf16", "f16") else 4
+    if maps in ("idx", "idx16"):
+        if maps == "idx":
+            tissues, index_bytes = 256, 1
+        else:
+            tables = getattr(prob, "tables", None)
+            tissues = -(-len(tables["c"]) // 4) * 4 if tables else 65536
+            index_bytes = 2
+        mp = index_bytes * n + 21 * tissues * 4
     else:
-        mp = (5 + 4 * N) * (2 if maps == "bf16" else 4) * n
+        mp = (5 + 4 * N) * es * n
     L = prob.pml_transition + prob.pml_bound
-    strips = sum(4 * N * 4 * 2 * L * n // s for s in prob.shape) if L else 0
+    strips = sum(4 * N * es * 2 * L * n // s for s in prob.shape) if L else 0
     return state + mp + strips
 
 
 def batchable(r: Request) -> bool:
-    """2D requests, and 3D requests on the pipelined path (bf16 maps), join
-    the batch; the others step on their own."""
-    return len(r.grid) == 2 or r.maps == "bf16"
+    """2D requests, and the 3D requests the pipelined 3D half steps take
+    (bf16 maps, at most 3 mechanisms, no periodic axis), join the batch; the
+    others step on their own."""
+    if len(r.grid) == 2:
+        return True
+    p = r.problem
+    return (r.maps == "bf16" and p is not None and p.nrelax <= 3
+            and all(b != "periodic" for b in getattr(p, "bc", ("zero",) * 3)))
 
 
 class Server:

@@ -154,18 +154,37 @@ def test_a_request_larger_than_the_cap_still_runs_alone(monkeypatch):
     assert [r.rid for r in done] == [0, 1] and _Sim.peak == 1
 
 
-@pytest.mark.parametrize("maps", ["f32", "bf16", "idx"])
+@pytest.mark.parametrize("maps", ["f32", "bf16", "f16", "idx", "idx16"])
 def test_footprint_counts_state_maps_and_strips(maps):
-    """State 1 + D + 2DN float arrays; maps 5 + 4N values per cell (float or
-    bf16) or one index byte plus the tables; strips 4 arrays of N x 2L cells
-    per row of each axis."""
+    """State 1 + D + 2DN float arrays; maps 5 + 4N values per cell (float,
+    bf16 or FP16) or the index (1 or 2 bytes) plus tables of 21 fields; strips
+    4 arrays of N x 2L cells per row of each axis, in the maps' type (float for
+    the index forms)."""
     nx, ny, N, L = 200, 100, 3, 10
-    p = types.SimpleNamespace(shape=(nx, ny), nrelax=N, pml_transition=L, pml_bound=0)
+    p = types.SimpleNamespace(shape=(nx, ny), nrelax=N, pml_transition=L, pml_bound=0,
+                              tables={"c": np.zeros(1157)})
     n = nx * ny
     state = (1 + 2 + 4 * N) * 4 * n
-    mp = {"f32": (5 + 4 * N) * 4 * n, "bf16": (5 + 4 * N) * 2 * n, "idx": n + 21 * 256 * 4}[maps]
-    strips = 4 * N * 4 * 2 * L * (ny + nx)
+    mp = {"f32": (5 + 4 * N) * 4 * n, "bf16": (5 + 4 * N) * 2 * n, "f16": (5 + 4 * N) * 2 * n,
+          "idx": n + 21 * 256 * 4, "idx16": 2 * n + 21 * 1160 * 4}[maps]
+    es = 2 if maps in ("bf16", "f16") else 4
+    strips = 4 * N * es * 2 * L * (ny + nx)
     assert serve.footprint_bytes(p, maps) == state + mp + strips
+
+
+def test_only_3d_requests_of_the_pipelined_path_join_the_batch():
+    """bf16 3D requests with at most 3 mechanisms and no periodic axis join
+    the batch (fw2_batch_create takes 3D contexts on that path only); 2D
+    requests always do."""
+    def req(shape, maps, N=3, bc=("zero",) * 3):
+        prob = types.SimpleNamespace(shape=shape, nrelax=N, pml_transition=3, pml_bound=1, bc=bc)
+        return serve.Request(0, 0.0, prob, 10, maps=maps)
+    assert serve.batchable(req((64, 48), "f32", N=8))
+    assert serve.batchable(req((32, 32, 24), "bf16"))
+    assert not serve.batchable(req((32, 32, 24), "bf16", N=4))
+    assert not serve.batchable(req((32, 32, 24), "bf16", bc=("zero", "periodic", "zero")))
+    assert not serve.batchable(req((32, 32, 24), "f32"))
+    assert not serve.batchable(req((32, 32, 24), "idx"))
 
 
 def test_prepare_fills_problems_at_admission_and_drops_them_after(monkeypatch):
