@@ -439,6 +439,20 @@ def test_cfl_uses_high_frequency_speed():
     assert abs(dt / (0.4 * 1e-4 / (1540.0 / math.sqrt(k1 * k2))) - 1) < 1e-14
 
 
+def test_high_frequency_speed_is_the_limit_of_the_dispersion_relation():
+    """c_max of the CFL rule is the omega -> infinity phase speed of Eq.
+    (dispersion_relations): evaluated there, far above every relaxation
+    frequency, the relation's phase velocity equals c / sqrt(kappa1 kappa2)
+    (and not c, nor c / kappa1)."""
+    p = synth.TABLE2
+    w = 2 * math.pi * 1e16
+    k = an.wavenumber(w, 1540.0, p["kappa1"], p["kappa2"], np.asarray(p["d1"]), np.asarray(p["alpha1"]),
+                      np.asarray(p["d2"]), np.asarray(p["alpha2"]))
+    c_inf = float(an.phase_velocity(w, k))
+    assert abs(c_inf / cf.high_frequency_speed(1540.0, p["kappa1"], p["kappa2"]) - 1) < 1e-6
+    assert abs(c_inf / 1540.0 - 1) > 1e-3          # 0.3 % above c for Table 2
+
+
 def test_window_run_equals_full_run_inside():
     """The windowed oracle reproduces the full-grid oracle away from the cut
     edges (8 cells per step), including PML strips, face densities, sources
