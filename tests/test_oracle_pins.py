@@ -439,6 +439,24 @@ def test_cfl_uses_high_frequency_speed():
     assert abs(dt / (0.4 * 1e-4 / (1540.0 / math.sqrt(k1 * k2))) - 1) < 1e-14
 
 
+def test_kramers_kronig_target_is_continuous_at_y_1_and_causal():
+    """The y = 1 branch of the nearly-local Kramers-Kronig target (reading
+    R1) is the limit of the y != 1 branch from both sides (tan(pi y / 2)
+    diverges there: a wrong sign or factor in either branch breaks the
+    match); the target passes through c0 at f_ref, and a positive power law
+    gives a phase velocity rising with frequency."""
+    f = np.linspace(0.5e6, 20e6, 60)
+    for y0 in (1.0, 1.1, 1.5):
+        c = an.kk_phase_velocity(f, 0.5, y0, 1540.0, 5e6)
+        assert np.all(np.diff(c) > 0), y0
+        assert abs(an.kk_phase_velocity(np.array([5e6]), 0.5, y0, 1540.0, 5e6)[0] / 1540.0 - 1) < 1e-14
+    c1 = an.kk_phase_velocity(f, 0.5, 1.0, 1540.0, 5e6)
+    for eps in (1e-5, -1e-5):
+        ce = an.kk_phase_velocity(f, 0.5, 1.0 + eps, 1540.0, 5e6)
+        assert np.max(np.abs(ce / c1 - 1)) < 1e-7, eps
+    assert np.max(np.abs(c1 / 1540.0 - 1)) > 1e-3
+
+
 def test_high_frequency_speed_is_the_limit_of_the_dispersion_relation():
     """c_max of the CFL rule is the omega -> infinity phase speed of Eq.
     (dispersion_relations): evaluated there, far above every relaxation
