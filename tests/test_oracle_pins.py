@@ -568,6 +568,34 @@ def _harmonic_mags(sig, dt, f0, n=7):
     return np.array([abs(F[int(np.argmin(np.abs(f - k * f0)))]) for k in range(1, n + 1)])
 
 
+@pytest.mark.parametrize("sigma", [0.3, 0.5, 0.9])
+def test_poisson_solution_equals_the_fubini_series(sigma):
+    """The pre-shock Burgers solution (the Sec. 4.5 reference) of a
+    continuous sine at distance sigma x_shock has the textbook Fubini
+    harmonics b_n = 2 J_n(n sigma) / (n sigma) P0 (sine terms only; cosine
+    terms vanish).  With beta of the opposite sign (a planted sign error)
+    J_n(-n sigma) = (-1)^n J_n(n sigma) flips the even harmonics, which the
+    comparison detects."""
+    from scipy.special import jv
+    P0, f0, rho0, c0, beta = 1e5, 1e6, 1000.0, 1500.0, 3.5
+    w = 2 * math.pi * f0
+    x = sigma * rho0 * c0 ** 3 / (beta * w * P0)
+    M = 4096
+    tau = np.arange(M) / M / f0
+
+    def harmonics(b):
+        p = an.burgers_poisson(lambda t: P0 * np.sin(w * t), tau + x / c0, x, b, rho0, c0)
+        sin_n = np.array([2 / M * np.sum(p * np.sin(n * w * tau)) for n in range(1, 8)])
+        cos_n = np.array([2 / M * np.sum(p * np.cos(n * w * tau)) for n in range(1, 8)])
+        return sin_n, cos_n
+    fubini = np.array([2 * jv(n, n * sigma) / (n * sigma) * P0 for n in range(1, 8)])
+    sin_n, cos_n = harmonics(beta)
+    assert np.max(np.abs(sin_n - fubini)) < 1e-9 * P0
+    assert np.max(np.abs(cos_n)) < 1e-9 * P0
+    flipped, _ = harmonics(-beta)
+    assert np.max(np.abs(flipped - fubini)) > 1e-2 * P0
+
+
 @pytest.mark.parametrize("sigma", [0.5, 0.7, 0.9])
 def test_rusanov_burgers_matches_the_poisson_solution(sigma):
     """The Rusanov reference solver of Sec. 4.5 at 150 points per period (the
