@@ -26,7 +26,11 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   removes (the counterfactual planted in the oracle grows, the scheme decays).
 * nonlinear term (Eq. general6): pinned by the first 7 harmonics of the
   pre-shock Poisson solution of the inviscid Burgers equation (Sec. 4.5),
-  with the effective coefficient of each nonlinear mode.
+  with the effective coefficient of each nonlinear mode; the Poisson
+  solution itself by the textbook Fubini series.
+* Kramers-Kronig target and CFL speed: the y = 1 branch as the limit of the
+  general one; c / sqrt(kappa1 kappa2) as the high-frequency limit of the
+  dispersion relation.
 * staggered-grid placement of rho, kappa, the relaxation parameters and the
   PML coordinate (not printed in the paper): pinned by the discrete energy
   conservation (K with the cell centres, the face density as the mean of the
