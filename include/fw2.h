@@ -52,7 +52,7 @@ typedef enum {
   FW2_ESTATE = 4,       /* call out of order (e.g. step before set_medium) */
   FW2_EUNSTABLE = 5,    /* non-finite or exploding field detected */
   FW2_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
-  FW2_EUNSUPPORTED = 7  /* valid request this build does not implement */
+  FW2_EUNSUPPORTED = 7  /* valid request the library does not implement */
 } fw2_status;
 
 enum { FW2_MEM_HOST = 0, FW2_MEM_DEVICE = 1 };
