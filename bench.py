@@ -310,8 +310,10 @@ def oracle_baseline(prob, steps, window, maps="f32", media=True, single_core=Tru
                       f"same window, {2 + steps} steps from rest")
         out["media_deviation"] = dev
     if single_core and threads > 1:
-        # about half the all-core sample's time on one core
-        one = oracle_single_core(orc, max(1, steps // (2 * threads)))
+        # about 5 s on one core, estimated from the all-core rate (one core
+        # runs at least 1/threads of it), at most half the sample's steps
+        per_core = out["value"] * 1e9 / threads
+        one = oracle_single_core(orc, max(1, min(steps // 2, int(5.0 * per_core / pts))))
         if one is not None:
             out["single_core"] = one
     return out
