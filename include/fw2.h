@@ -412,14 +412,25 @@ fw2_status fw2_get_step(fw2_ctx *ctx, int64_t *step);
  * fw2_set_field this restores a checkpoint taken with fw2_get_step and
  * fw2_get_field. EINVAL when negative. */
 fw2_status fw2_set_step(fw2_ctx *ctx, int64_t step);
-/* Copy a state array out (dense, x fastest; memory variables [N][n_pts]).
- * Synchronises the context stream. */
+/* Copy a state array (FW2_FIELD_*: p and v_q at the step's end, the memory
+ * variables psi1_q, psi2_q of Eq. relaxation_psi) out into a caller-owned
+ * buffer in host or device memory (mem_space) of n_pts floats, dense with x
+ * fastest; the memory variables take N x n_pts ([N][n_pts]).  The buffer
+ * must hold that many floats: the library cannot check its extent.
+ * Synchronises the context stream.  Errors: FW2_EINVAL (a field the context
+ * does not have, e.g. v_z of a 2D grid or psi with N = 0; null pointer),
+ * FW2_ECUDA. */
 fw2_status fw2_get_field(fw2_ctx *ctx, int32_t field, float *out, int32_t mem_space);
-/* Overwrite a state array (same layout); used for checkpoint / restore. */
+/* Overwrite a state array from a buffer of the same layout and extent (read
+ * at call time; the caller keeps it); with fw2_set_step it restores a
+ * checkpoint.  Errors as fw2_get_field. */
 fw2_status fw2_set_field(fw2_ctx *ctx, int32_t field, const float *in, int32_t mem_space);
 /* Zero every state array and the step counter. */
 fw2_status fw2_reset(fw2_ctx *ctx);
-/* Wait for the context stream. */
+/* Wait for the context stream.  FW2_ETIMEOUT when a bounded device-side
+ * wait of a pipelined kernel gave up since the last fw2_reset (the state is
+ * then incomplete; fw2_reset zeroes it and clears the flag), FW2_ECUDA on a
+ * failed launch. */
 fw2_status fw2_synchronize(fw2_ctx *ctx);
 /* Scan p for non-finite values or |p| > bound (a numerical blow-up such as
  * the C-PML instability with N >= 2 and no transition layer, Sec. 3.3).
